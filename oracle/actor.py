@@ -1,0 +1,83 @@
+"""Actor objective (DDPG-style policy extraction with an entropy term) and its gradient.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+What the paper fixes
+--------------------
+* Eq. 3 (§3.2): the goal-conditioned policy pi_theta(a | s, g) maximises
+  E[f(s, a', g)] with a' ~ pi_theta(. | s, g), (s, a) uniform from the buffer
+  and g from the future of the same trajectory (random-goal weight 0, App. C).
+* §5.1: the methods use "a tuneable entropy coefficient".
+* Algorithm 1: the policy update follows the critic update of the same step,
+  so the critic parameters are the freshly updated ones; the critic is not
+  changed by the actor loss.
+
+Readings where the paper is silent
+----------------------------------
+P1  The policy is a tanh-squashed diagonal Gaussian: the MLP on concat(s, g)
+    outputs (mu, l) of width 2A, l is clipped to [-5, 2], sigma = exp(l),
+    u = mu + sigma * eps with eps ~ N(0, I) (passed in), a' = tanh(u).
+P2  log pi(a'|s, g) = sum_d [ -eps_d^2 / 2 - log(2 pi) / 2 - l_d
+                              - 2 (log 2 - u_d - softplus(-2 u_d)) ],
+    the Gaussian log-density minus log|det da'/du| = sum log(1 - tanh(u)^2),
+    written in the overflow-free form.
+P3  L_actor = mean_i [ alpha * log pi_i - F_ii ], F_ii = f(phi(s_i, a'_i), psi(g_i)) / tau
+    with the critic's energy and temperature; alpha is given.
+P4  The clip passes the gradient only strictly inside (-5, 2).
+"""
+
+import numpy as np
+
+from . import critic, mlp
+
+LOG_STD_MIN = -5.0
+LOG_STD_MAX = 2.0
+
+
+def softplus(x):
+    return np.logaddexp(0.0, x)
+
+
+def policy_head(out, eps):
+    """Reading P1 / P2: (a', log pi, intermediates) from the MLP output [B][2A]."""
+    A = out.shape[1] // 2
+    mu, l_raw = out[:, :A], out[:, A:]
+    ell = np.clip(l_raw, LOG_STD_MIN, LOG_STD_MAX)
+    sigma = np.exp(ell)
+    u = mu + sigma * eps
+    a_new = np.tanh(u)
+    logpi = (-0.5 * eps ** 2 - 0.5 * np.log(2.0 * np.pi) - ell
+             - 2.0 * (np.log(2.0) - u - softplus(-2.0 * u))).sum(axis=1)
+    return a_new, logpi, {"l_raw": l_raw, "sigma": sigma, "u": u, "a": a_new}
+
+
+def actor_loss_and_grad(pi_net, phi_net, psi_net, s, g, eps, energy="l2", tau=1.0, alpha=0.1):
+    """L_actor (reading P3) and its gradient with respect to the actor parameters.
+
+    Returns dict: loss, logpi_mean, f_mean, grads (like ``pi_net``), a_new.
+    """
+    s = np.asarray(s, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    eps = np.asarray(eps, dtype=np.float64)
+    B, D = s.shape
+    out, pi_cache = mlp.forward(pi_net, np.concatenate([s, g], axis=1))
+    a_new, logpi, hc = policy_head(out, eps)
+    phi, phi_cache = mlp.forward(phi_net, np.concatenate([s, a_new], axis=1))
+    psi, _ = mlp.forward(psi_net, g)
+    f = critic.energy_diagonal(phi, psi, energy, tau)
+    loss = np.mean(alpha * logpi - f)
+
+    # d loss / d f_i = -1/B ; through phi only (psi does not depend on theta).
+    dphi, _ = critic.energy_diagonal_backward(phi, psi, -np.ones(B) / B, energy, tau)
+    _, dx = mlp.backward(phi_net, phi_cache, dphi)
+    da = dx[:, D:]
+    u, sigma, a = hc["u"], hc["sigma"], hc["a"]
+    # d logpi / du = 2 tanh(u); d logpi / dl = -1 (plus the u path)
+    du = da * (1.0 - a ** 2) + (alpha / B) * 2.0 * a
+    dmu = du
+    dl = du * sigma * eps - (alpha / B)
+    inside = (hc["l_raw"] > LOG_STD_MIN) & (hc["l_raw"] < LOG_STD_MAX)
+    dl_raw = np.where(inside, dl, 0.0)
+    grads, _ = mlp.backward(pi_net, pi_cache, np.concatenate([dmu, dl_raw], axis=1))
+    return {"loss": loss, "logpi_mean": float(np.mean(logpi)), "f_mean": float(np.mean(f)),
+            "grads": grads, "a_new": a_new, "logpi": logpi}

@@ -1,0 +1,203 @@
+"""Energy functions, InfoNCE objectives and the logsumexp penalty, with their gradient.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+What the paper fixes
+--------------------
+* §3.1: the critic is an energy f(s, a, g) of phi(s, a) and psi(g); the loss
+  is a function of the B x B matrix {f(s_i, a_i, g_j)}; the base loss is
+  symmetric InfoNCE with an L2 energy.
+* App. A.2 lists the energies: cosine, dot, -L1, -L2, -L2^2; and the InfoNCE
+  objectives: forward (softmax over goals j for each (s_i, a_i)), backward
+  (softmax over state-actions j for each goal g_i) and symmetric (their sum).
+* Algorithm 1 adds beta * L_logsumexp to the critic loss; §5.3 and App. B.3
+  set beta = 0.1.
+
+Readings where the paper is silent or inconsistent
+---------------------------------------------------
+C1  L2 energy carries the minus sign of App. A.2, f = -||phi - psi||_2 (the
+    formula under §3.1 drops it, which would make the positive pair the least
+    likely one; treated as a typo).
+C2  F_ij = f(phi_i, psi_j) / tau with a temperature tau (tau = 1 unless set).
+C3  The negatives are all B in-batch goals / state-actions, the positive
+    included (K = |B|, as in the FlatNCE rows of App. A.2).
+C4  The objectives are averaged over the batch (mean instead of the sum
+    inside the batch expectation), so that equal representations give log B.
+C5  Symmetric InfoNCE: the paper writes the sum of the two directions
+    ("sum"); the default reduction here is their mean ("mean"), and both are
+    available: L_sym,sum = 2 * L_sym,mean = L_fwd + L_bwd.
+C6  The logsumexp penalty is not defined in the paper.  Reading: the mean
+    over the batch of the squared row logsumexp, r_i = LSE_j F_ij, times beta
+    ("row"); "col" uses c_j = LSE_i F_ij; "both" averages the two.
+C7  The L2 gradient is undefined where phi_i = psi_j; the subgradient 0 is
+    taken there (distances below 1e-12).
+"""
+
+import numpy as np
+
+ENERGIES = ("l2", "dot", "cos", "l1", "l2sq")
+LOSSES = ("fwd", "bwd", "sym")
+
+
+def energy_matrix(phi, psi, energy="l2", tau=1.0):
+    """F [B][B] with F_ij = f(phi_i, psi_j) / tau (App. A.2; readings C1, C2)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    psi = np.asarray(psi, dtype=np.float64)
+    diff = phi[:, None, :] - psi[None, :, :]
+    if energy == "l2":
+        f = -np.sqrt((diff ** 2).sum(axis=2))
+    elif energy == "l2sq":
+        f = -(diff ** 2).sum(axis=2)
+    elif energy == "l1":
+        f = -np.abs(diff).sum(axis=2)
+    elif energy == "dot":
+        f = phi @ psi.T
+    elif energy == "cos":
+        f = (phi @ psi.T) / np.outer(np.linalg.norm(phi, axis=1), np.linalg.norm(psi, axis=1))
+    else:
+        raise ValueError(energy)
+    return f / tau
+
+
+def energy_diagonal(phi, psi, energy="l2", tau=1.0):
+    """f(phi_i, psi_i) / tau for each i (the positive pairs)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    psi = np.asarray(psi, dtype=np.float64)
+    d = phi - psi
+    if energy == "l2":
+        f = -np.sqrt((d ** 2).sum(axis=1))
+    elif energy == "l2sq":
+        f = -(d ** 2).sum(axis=1)
+    elif energy == "l1":
+        f = -np.abs(d).sum(axis=1)
+    elif energy == "dot":
+        f = (phi * psi).sum(axis=1)
+    elif energy == "cos":
+        f = (phi * psi).sum(axis=1) / (np.linalg.norm(phi, axis=1) * np.linalg.norm(psi, axis=1))
+    else:
+        raise ValueError(energy)
+    return f / tau
+
+
+def logsumexp(x, axis):
+    """Stable log(sum(exp(x))) along ``axis``."""
+    m = x.max(axis=axis, keepdims=True)
+    return (m + np.log(np.exp(x - m).sum(axis=axis, keepdims=True))).squeeze(axis)
+
+
+def direction_weights(loss, sym_reduction):
+    """(w_fwd, w_bwd) of the two InfoNCE directions (App. A.2; reading C5)."""
+    if loss == "fwd":
+        return 1.0, 0.0
+    if loss == "bwd":
+        return 0.0, 1.0
+    if loss == "sym":
+        return (0.5, 0.5) if sym_reduction == "mean" else (1.0, 1.0)
+    raise ValueError(loss)
+
+
+def penalty_weights(penalty_axis):
+    """(w_row, w_col) of the squared-logsumexp penalty (reading C6)."""
+    return {"row": (1.0, 0.0), "col": (0.0, 1.0), "both": (0.5, 0.5)}[penalty_axis]
+
+
+def infonce_loss(F, loss="sym", sym_reduction="mean", beta=0.1, penalty_axis="row"):
+    """Loss parts from the energy matrix (App. A.2, Algorithm 1; readings C3-C6).
+
+    Returns dict with total, fwd, bwd, contrastive, penalty, and r, c (the row
+    and column logsumexp vectors).
+    """
+    F = np.asarray(F, dtype=np.float64)
+    r = logsumexp(F, axis=1)
+    c = logsumexp(F, axis=0)
+    diag = np.diagonal(F)
+    l_fwd = np.mean(r - diag)
+    l_bwd = np.mean(c - diag)
+    wf, wb = direction_weights(loss, sym_reduction)
+    contrastive = wf * l_fwd + wb * l_bwd
+    pr, pc = penalty_weights(penalty_axis)
+    penalty = beta * (pr * np.mean(r ** 2) + pc * np.mean(c ** 2))
+    return {"total": contrastive + penalty, "fwd": l_fwd, "bwd": l_bwd,
+            "contrastive": contrastive, "penalty": penalty, "r": r, "c": c}
+
+
+def infonce_grad_F(F, loss="sym", sym_reduction="mean", beta=0.1, penalty_axis="row"):
+    """dL/dF [B][B] of ``infonce_loss``'s total.
+
+    With P_ij = exp(F_ij - r_i) (row softmax) and Q_ij = exp(F_ij - c_j)
+    (column softmax):
+      dL_fwd/dF = (P - I) / B,   dL_bwd/dF = (Q - I) / B,
+      d(beta mean r^2)/dF = 2 beta r_i P_ij / B,  d(beta mean c^2)/dF = 2 beta c_j Q_ij / B.
+    """
+    F = np.asarray(F, dtype=np.float64)
+    B = F.shape[0]
+    r = logsumexp(F, axis=1)
+    c = logsumexp(F, axis=0)
+    P = np.exp(F - r[:, None])
+    Q = np.exp(F - c[None, :])
+    eye = np.eye(B)
+    wf, wb = direction_weights(loss, sym_reduction)
+    pr, pc = penalty_weights(penalty_axis)
+    G = wf * (P - eye) + wb * (Q - eye)
+    G = G + 2.0 * beta * (pr * r[:, None] * P + pc * c[None, :] * Q)
+    return G / B
+
+
+def energy_backward(phi, psi, G, energy="l2", tau=1.0):
+    """Given G = dL/dF, return (dphi [B][R], dpsi [B][R]) for F = f(phi_i, psi_j) / tau."""
+    phi = np.asarray(phi, dtype=np.float64)
+    psi = np.asarray(psi, dtype=np.float64)
+    if energy == "dot":
+        return G @ psi / tau, G.T @ phi / tau
+    if energy == "cos":
+        nphi = np.linalg.norm(phi, axis=1, keepdims=True)
+        npsi = np.linalg.norm(psi, axis=1, keepdims=True)
+        x, y = phi / nphi, psi / npsi
+        dx = G @ y / tau
+        dy = G.T @ x / tau
+        dphi = (dx - x * (x * dx).sum(axis=1, keepdims=True)) / nphi
+        dpsi = (dy - y * (y * dy).sum(axis=1, keepdims=True)) / npsi
+        return dphi, dpsi
+    diff = phi[:, None, :] - psi[None, :, :]          # [i][j][r]
+    if energy == "l2":
+        d = np.sqrt((diff ** 2).sum(axis=2))
+        safe = d >= 1e-12                              # reading C7
+        H = np.where(safe, G / (tau * np.where(safe, d, 1.0)), 0.0)
+        # dF_ij/dphi_i = -(phi_i - psi_j) / (tau d_ij)
+        dphi = -(H[:, :, None] * diff).sum(axis=1)
+        dpsi = (H[:, :, None] * diff).sum(axis=0)
+        return dphi, dpsi
+    if energy == "l2sq":
+        W = 2.0 * G / tau
+        return -(W[:, :, None] * diff).sum(axis=1), (W[:, :, None] * diff).sum(axis=0)
+    if energy == "l1":
+        S = np.sign(diff) * (G / tau)[:, :, None]
+        return -S.sum(axis=1), S.sum(axis=0)
+    raise ValueError(energy)
+
+
+def energy_diagonal_backward(phi, psi, gdiag, energy="l2", tau=1.0):
+    """Given gdiag_i = dL/dF_ii, return (dphi, dpsi) for the positive pairs only."""
+    phi = np.asarray(phi, dtype=np.float64)
+    psi = np.asarray(psi, dtype=np.float64)
+    g = np.asarray(gdiag, dtype=np.float64)[:, None]
+    if energy == "dot":
+        return g * psi / tau, g * phi / tau
+    if energy == "cos":
+        nphi = np.linalg.norm(phi, axis=1, keepdims=True)
+        npsi = np.linalg.norm(psi, axis=1, keepdims=True)
+        x, y = phi / nphi, psi / npsi
+        dx, dy = g * y / tau, g * x / tau
+        return ((dx - x * (x * dx).sum(axis=1, keepdims=True)) / nphi,
+                (dy - y * (y * dy).sum(axis=1, keepdims=True)) / npsi)
+    diff = phi - psi
+    if energy == "l2":
+        d = np.sqrt((diff ** 2).sum(axis=1, keepdims=True))
+        safe = d >= 1e-12
+        h = np.where(safe, g / (tau * np.where(safe, d, 1.0)), 0.0)
+        return -h * diff, h * diff
+    if energy == "l2sq":
+        return -2.0 * g * diff / tau, 2.0 * g * diff / tau
+    if energy == "l1":
+        return -g * np.sign(diff) / tau, g * np.sign(diff) / tau
+    raise ValueError(energy)
