@@ -1,0 +1,322 @@
+"""Benchmark of the CRL update step (arXiv 2408.11052, Algorithm 1 update body).
+
+One step = insert one time slice for all environments -> sample + relabel a
+batch -> critic step (encoders, energy + InfoNCE + penalty, backward, Adam)
+-> actor step (policy, objective, backward, Adam), through the library's
+public call crl_update_step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload ant|small|humanoid|large] [--precision fp32|fp64]
+                  [--trace gemm|energy|relabel|adam|aux|insert]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs its own
+independent agent (its own Philox key and buffer): weak scaling, no data-path
+collective; timing takes the max over ranks.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2408_11052_gb300 import workload  # noqa: E402
+
+WORKLOADS = {"ant": workload.ANT_AUTOGRAD, "small": workload.SMALL_FP32, "humanoid": workload.HUMANOID_BF16,
+             "large": workload.LARGE_BATCH}
+METRIC = "CRL update steps/sec and relabeled samples/sec, BF16 fused vs FP32 plain at stated error"
+L2_FLUSH_BYTES = 256 << 20         # > 129 MB L2
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(w, n_steps, budget_s=20.0):
+    """The FP64 oracle's update step on this host's cores: (steps/s, steps done, cores)."""
+    import oracle
+    nets = workload.init_agent(w)
+    nets = {k: [{kk: vv.astype(np.float64) for kk, vv in l.items()} for l in v] for k, v in nets.items()}
+    buf = oracle.relabel.ReplayBuffer(w.E, w.T, w.D, w.A)
+    obs, act, done = workload.buffer_contents(w, mean_len=None)
+    buf.insert(obs, act, done)
+    extra = workload.buffer_contents(w, n=n_steps, mean_len=None, seed_offset=1)
+    state = oracle.step.AgentState(nets["phi"], nets["psi"], nets["pi"])
+    cfg = dict(seed=w.seed, agent=0, B=w.B, goal_idx=w.goals(), gamma=w.gamma, energy=w.energy, tau=w.tau,
+               loss=w.loss, sym_reduction=w.sym_reduction, beta=w.beta, penalty_axis=w.penalty_axis, alpha=w.alpha,
+               lr_critic=w.lr_critic, lr_actor=w.lr_actor)
+    done_steps = 0
+    t0 = time.perf_counter()
+    for i in range(n_steps):
+        buf.insert(extra[0][i:i + 1], extra[1][i:i + 1], extra[2][i:i + 1])
+        eps = oracle.actor.gaussian_noise(w.seed, 0, i, w.B, w.A)
+        oracle.step.update_step(state, buf, cfg, i, eps)
+        done_steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            cores = max(i.get("num_threads", 1) for i in info)
+    except ImportError:
+        pass
+    return done_steps / dt, done_steps, cores
+
+
+def run_reference(args, w):
+    """--impl reference: the FP64 CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.warmup + args.steps
+    rate, steps, cores = cpu_oracle_rate(w, n, budget_s=240.0)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "update steps/s", "n_gpus": 0,
+            "steps": steps, "warmup": 0, "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random-walk buffer, random-init nets)",
+            "samples_per_s": rate * w.B,
+            "config": {"workload": w.name, "batch": w.B, "envs": w.E, "steps_per_env": w.T,
+                       "sample": f"{steps} full update steps (insert+relabel+critic+actor+Adam) of the workload"},
+            "cpu_baseline": {"value": rate, "unit": "update steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} update steps"},
+            "e2e": {"value": rate, "unit": "update steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ant", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--trace", default="gemm", choices=["gemm", "energy", "relabel", "adam", "aux", "insert"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    from paper_2408_11052_gb300 import api
+
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    ctx = api.CRLContext(w, precision=args.precision, agent=rank)
+    for k, v in workload.init_agent(w).items():
+        ctx.load_network(k, v)
+    obs, act, done = workload.buffer_contents(w, mean_len=None, seed_offset=rank)
+    ctx.insert(torch.from_numpy(obs).to(dev), torch.from_numpy(act).to(dev), torch.from_numpy(done).to(dev))
+    del obs, act, done
+    n_all = args.warmup + 2 * args.steps + 8
+    ins = workload.buffer_contents(w, n=n_all, mean_len=None, seed_offset=100 + rank)
+    d_obs, d_act, d_done = (torch.from_numpy(x).to(dev) for x in ins)
+    h_obs, h_act, h_done = (torch.from_numpy(x).pin_memory() for x in ins)
+    loss_dev = torch.zeros(6, dtype=torch.float32, device=dev)
+    loss_host = torch.zeros(6, dtype=torch.float32).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    cursor = [0]
+
+    def step_device():
+        i = cursor[0]
+        cursor[0] += 1
+        ctx.update_step(d_obs[i:i + 1], d_act[i:i + 1], d_done[i:i + 1], loss_out=loss_dev)
+
+    def step_host():
+        i = cursor[0]
+        cursor[0] += 1
+        ctx.update_step(h_obs[i:i + 1].numpy(), h_act[i:i + 1].numpy(), h_done[i:i + 1].numpy(), loss_out=loss_host)
+
+    def timed(fn, K, trace=None):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        barrier(world)
+        torch.cuda.synchronize()
+        if trace:
+            ctx.trace_start(trace, 64 * K)
+        for k in range(K):
+            flush.fill_(k & 0xFF)                 # evict L2 between steps (not timed)
+            starts[k].record(stream)
+            fn()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        tr = ctx.trace_stop() if trace else None
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        return ms, tr
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    rc, status = ctx.sync_status()
+    assert rc == api.OK, f"warm-up status {status}"
+
+    # kernels per step: count every traced class over one untimed step
+    launches = 0
+    for cls in api.TRACE:
+        ctx.trace_start(cls, 4096)
+        step_device()
+        launches += ctx.trace_stop()[0]
+
+    with ClockSampler(dev.index) as clk:
+        ms, tr = timed(step_device, args.steps, trace=args.trace)
+    ms = max_over_ranks(ms, world)
+    value = world * args.steps / (ms / 1e3)
+
+    for _ in range(3):
+        step_host()
+    e2e_ms, _ = timed(step_host, args.steps)
+    e2e_ms = max_over_ranks(e2e_ms, world)
+    rc, status = ctx.sync_status()
+    assert rc == api.OK, f"status {status}"
+
+    peaks, peak_src = load_peaks()
+    n_tr, tr_ms, tr_work = tr
+    if args.trace in ("gemm", "energy"):
+        achieved = tr_work / (tr_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                "kernel_class": args.trace, "launches": n_tr, "avg_launch_us": 1e3 * tr_ms / max(n_tr, 1),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    else:
+        achieved = tr_work / (tr_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel_class": args.trace,
+                "launches": n_tr, "avg_launch_us": 1e3 * tr_ms / max(n_tr, 1), "peak_source": peak_src}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, steps, cores = cpu_oracle_rate(w, 200, budget_s=15.0)
+        cpu = {"value": rate, "unit": "update steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{steps} full update steps of the same workload (FP64 numpy oracle)"}
+
+    h2d = w.E * (w.D + w.A) * 4 + w.E
+    line = {"metric": METRIC, "value": value, "unit": "update steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic (seeded random-walk buffer, random-init nets)",
+            "samples_per_s": value * w.B,
+            "config": {"workload": w.name, "batch": w.B, "envs": w.E, "steps_per_env": w.T, "obs": w.D,
+                       "action": w.A, "goal": w.G, "hidden": [w.hidden] * w.layers, "repr": w.repr,
+                       "energy": w.energy, "loss": w.loss, "precision": args.precision, "path": "plain",
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "step": "insert 1 slice + relabel + critic fwd/bwd + Adam + actor fwd/bwd + Adam",
+                       "parallelism": f"{world} independent agents"},
+            "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "update steps/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
+            "gpu_launches": launches * args.steps,
+            "roofline": roof,
+            "clocks": clk.summary()}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -43,13 +43,17 @@ def energy_matrix(phi, psi, energy="l2", tau=1.0):
     """F [B][B] with F_ij = f(phi_i, psi_j) / tau (App. A.2; readings C1, C2)."""
     phi = np.asarray(phi, dtype=np.float64)
     psi = np.asarray(psi, dtype=np.float64)
-    diff = phi[:, None, :] - psi[None, :, :]
-    if energy == "l2":
-        f = -np.sqrt((diff ** 2).sum(axis=2))
-    elif energy == "l2sq":
-        f = -(diff ** 2).sum(axis=2)
-    elif energy == "l1":
-        f = -np.abs(diff).sum(axis=2)
+    if energy in ("l2", "l2sq", "l1"):
+        # one row i at a time: f(phi_i, psi_j) from the difference phi_i - psi_j
+        f = np.empty((phi.shape[0], psi.shape[0]))
+        for i in range(phi.shape[0]):
+            d = phi[i][None, :] - psi
+            if energy == "l2":
+                f[i] = -np.sqrt((d ** 2).sum(axis=1))
+            elif energy == "l2sq":
+                f[i] = -(d ** 2).sum(axis=1)
+            else:
+                f[i] = -np.abs(d).sum(axis=1)
     elif energy == "dot":
         f = phi @ psi.T
     elif energy == "cos":
@@ -158,22 +162,29 @@ def energy_backward(phi, psi, G, energy="l2", tau=1.0):
         dphi = (dx - x * (x * dx).sum(axis=1, keepdims=True)) / nphi
         dpsi = (dy - y * (y * dy).sum(axis=1, keepdims=True)) / npsi
         return dphi, dpsi
-    diff = phi[:, None, :] - psi[None, :, :]          # [i][j][r]
-    if energy == "l2":
-        d = np.sqrt((diff ** 2).sum(axis=2))
-        safe = d >= 1e-12                              # reading C7
-        H = np.where(safe, G / (tau * np.where(safe, d, 1.0)), 0.0)
-        # dF_ij/dphi_i = -(phi_i - psi_j) / (tau d_ij)
-        dphi = -(H[:, :, None] * diff).sum(axis=1)
-        dpsi = (H[:, :, None] * diff).sum(axis=0)
-        return dphi, dpsi
-    if energy == "l2sq":
-        W = 2.0 * G / tau
-        return -(W[:, :, None] * diff).sum(axis=1), (W[:, :, None] * diff).sum(axis=0)
-    if energy == "l1":
-        S = np.sign(diff) * (G / tau)[:, :, None]
-        return -S.sum(axis=1), S.sum(axis=0)
-    raise ValueError(energy)
+    if energy not in ("l2", "l2sq", "l1"):
+        raise ValueError(energy)
+    # One row i at a time over the differences phi_i - psi_j:
+    #   L2:   dF_ij/dphi_i = -(phi_i - psi_j) / (tau d_ij)   (0 where d_ij = 0, reading C7)
+    #   L2^2: dF_ij/dphi_i = -2 (phi_i - psi_j) / tau
+    #   L1:   dF_ij/dphi_i = -sign(phi_i - psi_j) / tau
+    # and dF_ij/dpsi_j is the negative of each.
+    dphi = np.zeros_like(phi)
+    dpsi = np.zeros_like(psi)
+    for i in range(phi.shape[0]):
+        diff = phi[i][None, :] - psi                   # [j][r]
+        if energy == "l2":
+            d = np.sqrt((diff ** 2).sum(axis=1))
+            safe = d >= 1e-12
+            h = np.where(safe, G[i] / (tau * np.where(safe, d, 1.0)), 0.0)
+            term = h[:, None] * diff
+        elif energy == "l2sq":
+            term = (2.0 * G[i] / tau)[:, None] * diff
+        else:
+            term = (G[i] / tau)[:, None] * np.sign(diff)
+        dphi[i] = -term.sum(axis=0)
+        dpsi += term
+    return dphi, dpsi
 
 
 def energy_diagonal_backward(phi, psi, gdiag, energy="l2", tau=1.0):

@@ -65,7 +65,8 @@ def update_step(state, buf, cfg, step, eps):
     """One full update step in place on ``state``; returns a dict of loss parts.
 
     cfg keys: seed, agent, B, goal_idx, gamma, offset_min, energy, tau, loss,
-    sym_reduction, beta, penalty_axis, alpha, lr_critic, lr_actor.
+    sym_reduction, beta, penalty_axis, alpha, lr_critic, lr_actor, and optionally
+    adam_beta1, adam_beta2, adam_eps (textbook defaults).
     eps [B][A]: the actor's Gaussian noise, drawn by the caller.
     """
     s, a, g, idx = relabel.sample_relabel(buf, cfg["seed"], cfg.get("agent", 0), step, cfg["B"],
@@ -73,13 +74,14 @@ def update_step(state, buf, cfg, step, eps):
     parts, gphi, gpsi, _, _ = critic_loss_and_grad(
         state.nets["phi"], state.nets["psi"], s, a, g, cfg["energy"], cfg["tau"], cfg["loss"],
         cfg["sym_reduction"], cfg["beta"], cfg["penalty_axis"])
+    betas = (cfg.get("adam_beta1", 0.9), cfg.get("adam_beta2", 0.999), cfg.get("adam_eps", 1e-8))
     state.t_critic += 1
     for name, grads in (("phi", gphi), ("psi", gpsi)):
         state.nets[name], state.m[name], state.v[name] = adam_net(
-            state.nets[name], grads, state.m[name], state.v[name], state.t_critic, cfg["lr_critic"])
+            state.nets[name], grads, state.m[name], state.v[name], state.t_critic, cfg["lr_critic"], *betas)
     act = actor.actor_loss_and_grad(state.nets["pi"], state.nets["phi"], state.nets["psi"], s, g, eps,
                                     cfg["energy"], cfg["tau"], cfg["alpha"])
     state.t_actor += 1
     state.nets["pi"], state.m["pi"], state.v["pi"] = adam_net(
-        state.nets["pi"], act["grads"], state.m["pi"], state.v["pi"], state.t_actor, cfg["lr_actor"])
+        state.nets["pi"], act["grads"], state.m["pi"], state.v["pi"], state.t_actor, cfg["lr_actor"], *betas)
     return {"critic": parts, "actor_loss": act["loss"], "logpi_mean": act["logpi_mean"], "idx": idx}

@@ -1,0 +1,182 @@
+// Replay buffer insert and hindsight future-goal relabelling (Algorithm 1 of
+// arXiv 2408.11052: "store the trajectory", then "sample with discount a batch
+// of state-action pairs and goals from their future"; §3: the future offset is
+// T ~ Geom(1 - gamma); §3.1/§3.2: goals come from the same trajectory).
+//
+// Layout: one ring of T rows per environment; a row holds the step's
+// observation, action and the absolute index of the last step of its episode
+// (see BufferDev in internal.h).  All environments insert in lockstep.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "philox.cuh"
+#include "trace.h"
+
+namespace crl {
+
+// ---------------------------------------------------------------------------
+// Insert: copy the newest min(n, T) slices into their ring slots with the
+// episode marked open (-1).  One warp per (slice, env) row.
+__global__ void __launch_bounds__(128) insert_rows_kernel(BufferDev bd, const float* __restrict__ obs,
+                                                         const float* __restrict__ act, int n, int i0,
+                                                         long long total_before) {
+  const int lane = threadIdx.x % kWarp;
+  const long long row = (long long)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const long long nrows = (long long)(n - i0) * bd.E;
+  if (row >= nrows) return;
+  const int i = i0 + (int)(row / bd.E);
+  const int e = (int)(row % bd.E);
+  const long long abs_i = total_before + i;
+  float* dst = bd.rows + ((size_t)e * bd.T + (size_t)(abs_i % bd.T)) * bd.W;
+  const float* so = obs + ((size_t)i * bd.E + e) * bd.D;
+  const float* sa = act + ((size_t)i * bd.E + e) * bd.A;
+  for (int c = lane; c < bd.W; c += kWarp) {
+    float v;
+    if (c < bd.D) v = so[c];
+    else if (c < bd.D + bd.A) v = sa[c - bd.D];
+    else if (c == bd.D + bd.A) v = __int_as_float(-1);
+    else v = 0.f;
+    dst[c] = v;
+  }
+}
+
+// Close episodes: for every done flag, stamp the episode's stored steps with
+// the absolute index of its last step.  One warp per environment walks its n
+// flags in order; the stamping of one episode is spread over the lanes.
+__global__ void __launch_bounds__(128) close_episodes_kernel(BufferDev bd, const uint8_t* __restrict__ done,
+                                                            int n, long long total_before) {
+  const int lane = threadIdx.x % kWarp;
+  const int e = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const long long total_after = total_before + n;
+  const long long size_after = total_after < bd.T ? total_after : bd.T;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    bd.state[0] = (int32_t)size_after;
+    bd.state[1] = (int32_t)total_after;
+  }
+  if (e >= bd.E) return;
+  const long long win_lo = total_after - size_after;
+  long long start = bd.ep_start[e];
+  for (int i = 0; i < n; ++i) {
+    if (done[(size_t)i * bd.E + e]) {
+      const long long last = total_before + i;
+      const long long lo = start > win_lo ? start : win_lo;
+      for (long long a = lo + lane; a <= last; a += kWarp)
+        bd.rows[((size_t)e * bd.T + (size_t)(a % bd.T)) * bd.W + bd.D + bd.A] = __int_as_float((int)last);
+      start = last + 1;
+    }
+  }
+  if (lane == 0) bd.ep_start[e] = (int32_t)start;
+}
+
+void launch_buffer_insert(const BufferDev& bd, const float* obs, const float* act, const uint8_t* done,
+                          int n, int64_t total_before, cudaStream_t st) {
+  const int i0 = n > bd.T ? n - bd.T : 0;
+  const long long rows = (long long)(n - i0) * bd.E;
+  {
+    // algorithmic bytes: read obs and act, write the rows (obs, act, episode end)
+    TraceLaunch tr(CRL_TRACE_INSERT, st, (double)rows * ((bd.D + bd.A) * 4.0 + (bd.D + bd.A + 1) * 4.0));
+    insert_rows_kernel<<<ceil_div(rows, 4), 128, 0, st>>>(bd, obs, act, n, i0, total_before);
+  }
+  TraceLaunch tr(CRL_TRACE_INSERT, st, (double)n * bd.E);  // read the done flags
+  close_episodes_kernel<<<ceil_div(bd.E, 4), 128, 0, st>>>(bd, done, n, total_before);
+}
+
+// ---------------------------------------------------------------------------
+// Discount table: G[0] = 2^32, G[k] = floor(G[k-1] * gq / 2^32), gq = round(gamma 2^32).
+// G[k] ~ gamma^k 2^32 in exact integer arithmetic, so the inverse CDF below
+// takes the same decision as any other implementation of the same rule.
+void build_discount_table(float gamma, int n, unsigned long long* out) {
+  const double scaled = (double)gamma * 4294967296.0;  // exact for a float gamma
+  const unsigned long long gq = (unsigned long long)(scaled + 0.5);  // round half up (scaled >= 0)
+  out[0] = 1ull << 32;
+  for (int k = 1; k < n; ++k) {
+    // (G * gq) < 2^64 because G <= 2^32 and gq < 2^32.
+    out[k] = (out[k - 1] * gq) >> 32;
+  }
+}
+
+// Smallest offset k in [m, L] with  v * (G0 - G[L+1-m]) < (G0 - G[k+1-m]) * 2^32,
+// i.e. the inverse CDF of the geometric distribution truncated to the episode.
+// The right side reaches 2^64 only when G[k+1-m] == 0, where the test is true.
+__device__ __forceinline__ int geometric_offset(unsigned long long v, int L, int m,
+                                                const unsigned long long* __restrict__ gq) {
+  if (L == 0 && m == 1) return 0;
+  const unsigned long long g0 = gq[0];
+  const unsigned long long lhs = v * (g0 - __ldg(gq + L + 1 - m));
+  int lo = m, hi = L;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const unsigned long long gk = __ldg(gq + mid + 1 - m);
+    const bool ok = (gk == 0ull) || (lhs < ((g0 - gk) << 32));
+    if (ok) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// One warp per sample: lane 0 draws the Philox block and the offset, the warp
+// copies the state-action row and the goal dims.
+__global__ void __launch_bounds__(256) relabel_kernel(BufferDev bd, RelabelArgs ra) {
+  const int lane = threadIdx.x % kWarp;
+  const int b = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const unsigned long long step = (ra.step == CRL_STEP_AUTO) ? *ra.step_dev : ra.step;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && ra.last_step_dev != nullptr) *ra.last_step_dev = step;
+  if (b >= ra.B) return;
+  const int size = bd.state[0];
+  const long long total = bd.state[1];
+  if (size <= 0) {
+    if (lane == 0) atomicOr(ra.status, CRL_STATUS_BAD_INDEX);
+    return;
+  }
+  int e = 0, t = 0, k = 0;
+  if (lane == 0) {
+    const Philox4 r = philox4x64_10(step, (unsigned long long)b, 0ull, 0ull, ra.seed, ra.agent);
+    const unsigned long long nstored = (unsigned long long)size * (unsigned long long)bd.E;
+    const unsigned long long idx = __umul64hi(r.w[0], nstored);
+    e = (int)(idx / (unsigned long long)size);
+    t = (int)(idx % (unsigned long long)size);
+    const long long abs_t = total - size + t;
+    const float* row = bd.rows + ((size_t)e * bd.T + (size_t)(abs_t % bd.T)) * bd.W;
+    const int ep_end = __float_as_int(row[bd.D + bd.A]);
+    int L = (ep_end < 0) ? (size - 1 - t) : (int)(ep_end - abs_t);
+    if (L < 0 || L > size - 1 - t) {
+      atomicOr(ra.status, CRL_STATUS_BAD_INDEX);
+      L = L < 0 ? 0 : size - 1 - t;
+    }
+    k = geometric_offset(r.w[1] >> 32, L, ra.offset_min, bd.gq);
+  }
+  e = __shfl_sync(0xffffffffu, e, 0);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  k = __shfl_sync(0xffffffffu, k, 0);
+  const long long abs_t = total - size + t;
+  const float* row = bd.rows + ((size_t)e * bd.T + (size_t)(abs_t % bd.T)) * bd.W;
+  const float* grow = bd.rows + ((size_t)e * bd.T + (size_t)((abs_t + k) % bd.T)) * bd.W;
+  for (int c = lane; c < bd.D + bd.A; c += kWarp) {
+    const float v = row[c];
+    if (c < bd.D) ra.s[(size_t)b * bd.D + c] = v;
+    else ra.a[(size_t)b * bd.A + (c - bd.D)] = v;
+  }
+  if (lane < ra.G) ra.g[(size_t)b * ra.G + lane] = grow[ra.goal_idx[lane]];
+  if (ra.idx != nullptr && lane == 0) {
+    ra.idx[3 * (size_t)b + 0] = e;
+    ra.idx[3 * (size_t)b + 1] = t;
+    ra.idx[3 * (size_t)b + 2] = k;
+  }
+}
+
+void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st) {
+  // algorithmic bytes per sample: read obs + act + episode end + goal dims, write s, a, g (+ idx)
+  const double per = (bd.D + bd.A + 1 + ra.G) * 4.0 + (bd.D + bd.A + ra.G) * 4.0 + (ra.idx ? 12.0 : 0.0);
+  TraceLaunch tr(CRL_TRACE_RELABEL, st, per * ra.B);
+  relabel_kernel<<<ceil_div(ra.B, 8), 256, 0, st>>>(bd, ra);
+}
+
+__global__ void bump_u64_kernel(unsigned long long* c) { *c += 1ull; }
+
+void launch_bump_u64(unsigned long long* ctr, cudaStream_t st) {
+  TraceLaunch tr(CRL_TRACE_AUX, st, 8.0);
+  bump_u64_kernel<<<1, 1, 0, st>>>(ctr);
+}
+
+}  // namespace crl

@@ -1,0 +1,329 @@
+// Energy matrix + InfoNCE + logsumexp penalty, forward and backward: the plain
+// SIMT path (FP32 / FP64), which writes the B x B matrix to HBM.
+//
+// arXiv 2408.11052: §3.1 (critic objective: symmetric InfoNCE over the batch,
+// L2 energy), App. A.2 (energies cos, dot, -L1, -L2, -L2^2; InfoNCE forward,
+// backward, symmetric), Algorithm 1 (critic loss + beta * logsumexp penalty).
+// Readings: F_ij = f(phi_i, psi_j) / tau; losses averaged over the batch;
+// symmetric = mean (or sum) of the two directions; penalty = beta * mean of
+// the squared row (or column) logsumexp.
+//
+// Gradient: with P = row softmax of F, Q = column softmax, r / c the row /
+// column logsumexp and (wf, wb), (pr, pc) the direction and penalty weights,
+//   dL/dF_ij = (1/B) [wf (P_ij - d_ij) + wb (Q_ij - d_ij) + 2 beta (pr r_i P_ij + pc c_j Q_ij)].
+// Chain rule through the energy, with H the per-pair coefficient:
+//   dot:  dphi = (G/tau) psi,            dpsi = (G/tau)^T phi
+//   L2:   H = G / (tau d),  dphi_i = (H psi)_i - (sum_j H_ij) phi_i,
+//                           dpsi_j = (H^T phi)_j - (sum_i H_ij) psi_j   (H = 0 where d = 0)
+//   L2^2: the same with H = 2 G / tau
+//   cos:  the dot form on x = phi/|phi|, then dphi = (dx - x <x, dx>) / |phi|.
+#include <algorithm>
+
+#include "common.cuh"
+#include "gemm_simt.cuh"
+#include "internal.h"
+#include "trace.h"
+
+namespace crl {
+
+namespace {
+
+template <typename T>
+struct PlainWs {
+  T* F;       // [B][B] energies, then the coefficient matrix H
+  T* rsum;    // [B]
+  T* csum;    // [B]
+  T* inx;     // [B] 1/|phi_i|
+  T* iny;     // [B] 1/|psi_j|
+  T* xh;      // [B][R] phi / |phi|
+  T* yh;      // [B][R] psi / |psi|
+};
+
+template <typename T>
+PlainWs<T> carve_plain(int B, int R, void* ws) {
+  PlainWs<T> w;
+  T* p = static_cast<T*>(ws);
+  w.F = p;
+  p += (size_t)B * B;
+  w.rsum = p;
+  p += B;
+  w.csum = p;
+  p += B;
+  w.inx = p;
+  p += B;
+  w.iny = p;
+  p += B;
+  w.xh = p;
+  p += (size_t)B * R;
+  w.yh = p;
+  return w;
+}
+
+template <typename T>
+struct EpiEnergy {
+  T* F;
+  int ld;
+  int energy;
+  T inv_tau;
+  const T* inx;
+  const T* iny;
+  __device__ void operator()(int m, int n, T acc) const {
+    T v;
+    switch (energy) {
+      case CRL_ENERGY_L2: v = -dev_sqrt(acc); break;
+      case CRL_ENERGY_COS: v = acc * inx[m] * iny[n]; break;
+      case CRL_ENERGY_DOT: v = acc; break;
+      default: v = -acc; break;  // L1, L2^2
+    }
+    F[(size_t)m * ld + n] = v * inv_tau;
+  }
+};
+
+// Row normalisation: inv[i] = 1/|x_i|, xh = x * inv.  One warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) normalize_rows_kernel(int B, int R, const T* __restrict__ x,
+                                                            T* __restrict__ inv, T* __restrict__ xh) {
+  const int lane = threadIdx.x % kWarp;
+  const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  if (row >= B) return;
+  T s = 0;
+  for (int c = lane; c < R; c += kWarp) {
+    const T v = x[(size_t)row * R + c];
+    s += v * v;
+  }
+  const T iv = T(1) / dev_sqrt(warp_sum(s));
+  for (int c = lane; c < R; c += kWarp) xh[(size_t)row * R + c] = x[(size_t)row * R + c] * iv;
+  if (lane == 0) inv[row] = iv;
+}
+
+// r_i = LSE_j F_ij.  One warp per row, two passes.
+template <typename T>
+__global__ void __launch_bounds__(256) row_lse_kernel(int B, const T* __restrict__ F, T* __restrict__ r) {
+  const int lane = threadIdx.x % kWarp;
+  const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  if (row >= B) return;
+  const T* f = F + (size_t)row * B;
+  T m = -INFINITY;
+  for (int c = lane; c < B; c += kWarp) m = fmax(m, f[c]);
+  m = warp_max(m);
+  T s = 0;
+  for (int c = lane; c < B; c += kWarp) s += dev_exp(f[c] - m);
+  s = warp_sum(s);
+  if (lane == 0) r[row] = m + dev_log(s);
+}
+
+// c_j = LSE_i F_ij.  One thread per column, single pass with a running max.
+template <typename T>
+__global__ void __launch_bounds__(256) col_lse_kernel(int B, const T* __restrict__ F, T* __restrict__ c) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B) return;
+  T m = -INFINITY, s = 0;
+  for (int i = 0; i < B; ++i) {
+    const T x = F[(size_t)i * B + j];
+    if (x > m) {
+      s = s * dev_exp(m - x) + T(1);
+      m = x;
+    } else {
+      s += dev_exp(x - m);
+    }
+  }
+  c[j] = m + dev_log(s);
+}
+
+// Row sums (warp per row) and column sums (thread per column) of H.
+template <typename T>
+__global__ void __launch_bounds__(256) row_sum_kernel(int B, const T* __restrict__ H, T* __restrict__ out) {
+  const int lane = threadIdx.x % kWarp;
+  const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  if (row >= B) return;
+  T s = 0;
+  for (int c = lane; c < B; c += kWarp) s += H[(size_t)row * B + c];
+  s = warp_sum(s);
+  if (lane == 0) out[row] = s;
+}
+template <typename T>
+__global__ void __launch_bounds__(256) col_sum_kernel(int B, const T* __restrict__ H, T* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B) return;
+  T s = 0;
+  for (int i = 0; i < B; ++i) s += H[(size_t)i * B + j];
+  out[j] = s;
+}
+
+struct DirWeights {
+  double wf, wb, pr, pc;
+};
+inline DirWeights weights(const LossSpec& ls) {
+  DirWeights w{0, 0, 0, 0};
+  if (ls.loss == CRL_LOSS_FWD) w.wf = 1;
+  else if (ls.loss == CRL_LOSS_BWD) w.wb = 1;
+  else w.wf = w.wb = (ls.sym_reduction == CRL_SYM_SUM) ? 1.0 : 0.5;
+  if (ls.penalty_axis == CRL_PENALTY_ROW) w.pr = 1;
+  else if (ls.penalty_axis == CRL_PENALTY_COL) w.pc = 1;
+  else w.pr = w.pc = 0.5;
+  return w;
+}
+
+// Loss parts from the diagonal of F and the row / column logsumexp.  One block.
+template <typename T>
+__global__ void __launch_bounds__(1024) loss_kernel(int B, const T* __restrict__ F, int ldf, const T* __restrict__ r,
+                                                   const T* __restrict__ c, DirWeights w, double beta,
+                                                   T* __restrict__ loss4, unsigned* status, int* t_bump) {
+  __shared__ T sm[32];
+  T a_f = 0, a_b = 0, a_r2 = 0, a_c2 = 0;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    const T d = F[(size_t)i * ldf + i];
+    a_f += r[i] - d;
+    a_b += c[i] - d;
+    a_r2 += r[i] * r[i];
+    a_c2 += c[i] * c[i];
+  }
+  a_f = block_sum(a_f, sm);
+  a_b = block_sum(a_b, sm);
+  a_r2 = block_sum(a_r2, sm);
+  a_c2 = block_sum(a_c2, sm);
+  if (threadIdx.x == 0) {
+    const T inv = T(1) / T(B);
+    const T lf = a_f * inv, lb = a_b * inv;
+    const T pen = T(beta) * (T(w.pr) * a_r2 * inv + T(w.pc) * a_c2 * inv);
+    const T total = T(w.wf) * lf + T(w.wb) * lb + pen;
+    loss4[0] = total;
+    loss4[1] = lf;
+    loss4[2] = lb;
+    loss4[3] = pen;
+    if (status && !finite_val(total)) atomicOr(status, CRL_STATUS_NONFINITE);
+    if (t_bump) *t_bump += 1;
+  }
+}
+
+// F -> H in place (see the header comment).
+template <typename T>
+__global__ void __launch_bounds__(256) grad_coeff_kernel(int B, T* __restrict__ F, const T* __restrict__ r,
+                                                        const T* __restrict__ c, DirWeights w, double beta,
+                                                        double dtotal, int energy, double tau) {
+  const size_t n = (size_t)B * B;
+  const T scale = T(dtotal / B);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / B), j = (int)(e % B);
+    const T f = F[e];
+    const T P = dev_exp(f - r[i]);
+    const T Q = dev_exp(f - c[j]);
+    const T dlt = (i == j) ? T(1) : T(0);
+    T g = T(w.wf) * (P - dlt) + T(w.wb) * (Q - dlt) + T(2.0 * beta) * (T(w.pr) * r[i] * P + T(w.pc) * c[j] * Q);
+    g *= scale;
+    T h;
+    switch (energy) {
+      case CRL_ENERGY_L2: {
+        const T d = -f * T(tau);
+        h = (d >= T(1e-12)) ? g / (T(tau) * d) : T(0);
+        break;
+      }
+      case CRL_ENERGY_L2SQ: h = T(2) * g / T(tau); break;
+      default: h = g / T(tau); break;  // dot, cos
+    }
+    F[e] = h;
+  }
+}
+
+// dphi_i = (dx_i - x_i <x_i, dx_i>) * inv_i, in place on dx.  One warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) project_rows_kernel(int B, int R, const T* __restrict__ xh,
+                                                          const T* __restrict__ inv, T* __restrict__ dx) {
+  const int lane = threadIdx.x % kWarp;
+  const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  if (row >= B) return;
+  T s = 0;
+  for (int c = lane; c < R; c += kWarp) s += xh[(size_t)row * R + c] * dx[(size_t)row * R + c];
+  s = warp_sum(s);
+  const T iv = inv[row];
+  for (int c = lane; c < R; c += kWarp) {
+    const size_t o = (size_t)row * R + c;
+    dx[o] = (dx[o] - xh[o] * s) * iv;
+  }
+}
+
+}  // namespace
+
+size_t infonce_ws_bytes(const LossSpec& ls, int B, int R, size_t elem, int path) {
+  (void)ls;
+  (void)path;
+  return ((size_t)B * B + 4 * (size_t)B + 2 * (size_t)B * R) * elem;
+}
+
+template <typename T>
+void infonce_forward(const LossSpec& ls, const T* phi, const T* psi, int B, int R, T* loss4, T* row_lse, T* col_lse,
+                     void* ws, int path, unsigned* status, int* t_bump, cudaStream_t st) {
+  (void)path;
+  PlainWs<T> w = carve_plain<T>(B, R, ws);
+  const int nb = ceil_div(B, 8);
+  if (ls.energy == CRL_ENERGY_COS) {
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); normalize_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, phi, w.inx, w.xh); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); normalize_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, psi, w.iny, w.yh); }
+  }
+  EpiEnergy<T> ep{w.F, B, ls.energy, T(1.0 / ls.tau), w.inx, w.iny};
+  LoadMK<T> la{phi, R};
+  LoadNK<T> lb{psi, R};
+  switch (ls.energy) {
+    case CRL_ENERGY_L2:
+    case CRL_ENERGY_L2SQ: gemm<T, InnerOp::kSqDiff>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
+    case CRL_ENERGY_L1: gemm<T, InnerOp::kAbsDiff>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
+    default: gemm<T, InnerOp::kMul>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
+  }
+  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); row_lse_kernel<T><<<nb, 256, 0, st>>>(B, w.F, row_lse); }
+  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); col_lse_kernel<T><<<ceil_div(B, 256), 256, 0, st>>>(B, w.F, col_lse); }
+  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); loss_kernel<T><<<1, 1024, 0, st>>>(B, w.F, B, row_lse, col_lse, weights(ls), ls.beta, loss4, status, t_bump); }
+}
+
+template <typename T>
+void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int R, const T* row_lse,
+                      const T* col_lse, double dtotal, T* dphi, T* dpsi, void* ws, int path, cudaStream_t st) {
+  (void)path;
+  PlainWs<T> w = carve_plain<T>(B, R, ws);
+  const int nb = ceil_div(B, 8);
+  // Recompute F (the forward's copy may have been overwritten by another call).
+  if (ls.energy == CRL_ENERGY_COS) {
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); normalize_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, phi, w.inx, w.xh); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); normalize_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, psi, w.iny, w.yh); }
+  }
+  {
+    EpiEnergy<T> ep{w.F, B, ls.energy, T(1.0 / ls.tau), w.inx, w.iny};
+    LoadMK<T> la{phi, R};
+    LoadNK<T> lb{psi, R};
+    switch (ls.energy) {
+      case CRL_ENERGY_L2:
+      case CRL_ENERGY_L2SQ: gemm<T, InnerOp::kSqDiff>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
+      default: gemm<T, InnerOp::kMul>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
+    }
+  }
+  const int ge = (int)std::min<int64_t>(ceil_div((int64_t)B * B, 256), 152 * 16);
+  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); grad_coeff_kernel<T><<<ge, 256, 0, st>>>(B, w.F, row_lse, col_lse, weights(ls), ls.beta, dtotal, ls.energy,
+                                           ls.tau); }
+  const T* H = w.F;
+  if (ls.energy == CRL_ENERGY_L2 || ls.energy == CRL_ENERGY_L2SQ) {
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); row_sum_kernel<T><<<nb, 256, 0, st>>>(B, H, w.rsum); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); col_sum_kernel<T><<<ceil_div(B, 256), 256, 0, st>>>(B, H, w.csum); }
+    gemm<T>(B, R, B, LoadMK<T>{H, B}, LoadKN<T>{psi, R}, EpiSubRowScaled<T>{dphi, R, T(1), w.rsum, phi, R}, st,
+            CRL_TRACE_ENERGY);
+    gemm<T>(B, R, B, LoadTrans<T>{H, B}, LoadKN<T>{phi, R}, EpiSubRowScaled<T>{dpsi, R, T(1), w.csum, psi, R},
+            st, CRL_TRACE_ENERGY);
+  } else if (ls.energy == CRL_ENERGY_COS) {
+    gemm<T>(B, R, B, LoadMK<T>{H, B}, LoadKN<T>{w.yh, R}, EpiScale<T>{dphi, R, T(1)}, st, CRL_TRACE_ENERGY);
+    gemm<T>(B, R, B, LoadTrans<T>{H, B}, LoadKN<T>{w.xh, R}, EpiScale<T>{dpsi, R, T(1)}, st, CRL_TRACE_ENERGY);
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); project_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, w.xh, w.inx, dphi); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); project_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, w.yh, w.iny, dpsi); }
+  } else {  // dot
+    gemm<T>(B, R, B, LoadMK<T>{H, B}, LoadKN<T>{psi, R}, EpiScale<T>{dphi, R, T(1)}, st, CRL_TRACE_ENERGY);
+    gemm<T>(B, R, B, LoadTrans<T>{H, B}, LoadKN<T>{phi, R}, EpiScale<T>{dpsi, R, T(1)}, st, CRL_TRACE_ENERGY);
+  }
+}
+
+template void infonce_forward<float>(const LossSpec&, const float*, const float*, int, int, float*, float*, float*,
+                                     void*, int, unsigned*, int*, cudaStream_t);
+template void infonce_forward<double>(const LossSpec&, const double*, const double*, int, int, double*, double*,
+                                      double*, void*, int, unsigned*, int*, cudaStream_t);
+template void infonce_backward<float>(const LossSpec&, const float*, const float*, int, int, const float*,
+                                      const float*, double, float*, float*, void*, int, cudaStream_t);
+template void infonce_backward<double>(const LossSpec&, const double*, const double*, int, int, const double*,
+                                       const double*, double, double*, double*, void*, int, cudaStream_t);
+
+}  // namespace crl

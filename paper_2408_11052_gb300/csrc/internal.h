@@ -1,0 +1,103 @@
+// Internal interfaces between the translation units of libcrl (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/crl.h"
+
+namespace crl {
+
+// ---------------------------------------------------------------- replay buffer
+// Row layout of the ring: [obs (D) | act (A) | ep_end (1, int32 bits) | pad] with
+// W = roundup(D + A + 1, 4) floats, so every row starts on a 16-byte boundary.
+// ep_end holds the absolute insertion index of the last step of the row's
+// episode, or -1 while that episode is open.
+struct BufferDev {
+  float* rows;                      // [E][T][W]
+  int32_t* ep_start;                // [E] absolute index of each env's open episode start
+  int32_t* state;                   // [2] device copy of {size, total}
+  const unsigned long long* gq;     // [T + 2] fixed-point discount table (see relabel)
+  int E, T, D, A, W;
+};
+
+struct RelabelArgs {
+  uint64_t seed, agent;
+  uint64_t step;                    // CRL_STEP_AUTO: read *step_dev
+  unsigned long long* step_dev;     // device step counter
+  unsigned long long* last_step_dev;  // receives the step used (read by the actor's Philox noise)
+  int B, G, offset_min;
+  int goal_idx[CRL_MAX_GOAL_DIMS];
+  float *s, *a, *g;                 // [B][D], [B][A], [B][G]
+  int32_t* idx;                     // [B][3] or null
+  unsigned* status;                 // device status word
+};
+
+void launch_buffer_insert(const BufferDev& bd, const float* obs, const float* act, const uint8_t* done,
+                          int n, int64_t total_before, cudaStream_t st);
+void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st);
+void build_discount_table(float gamma, int n, unsigned long long* out);  // host
+
+// ---------------------------------------------------------------- MLPs
+struct MlpShape {
+  int in0, in1, hidden, layers, out, layernorm;
+  int in() const { return in0 + in1; }
+};
+struct LayerOffsets {
+  int64_t W, b, g, beta;            // g/beta = -1 without LayerNorm
+  int in, out;
+};
+// Layout of the flat parameter array; returns the element count (64-element aligned tensors).
+int64_t mlp_layout(const MlpShape& s, LayerOffsets* lay /* layers + 1 entries */);
+size_t mlp_saved_bytes(const MlpShape& s, int M, size_t elem);
+
+template <typename T, typename TX1>
+void mlp_forward(const MlpShape& s, const T* params, const float* x0, const TX1* x1, int M, T* y,
+                 void* saved, cudaStream_t st);
+// dparams / dx0 / dx1 may be null.
+template <typename T, typename TX1>
+void mlp_backward(const MlpShape& s, const T* params, const float* x0, const TX1* x1, int M,
+                  const void* saved, const T* dy, T* dparams, T* dx0, T* dx1, cudaStream_t st);
+
+// ---------------------------------------------------------------- energy + InfoNCE
+struct LossSpec {
+  int energy, loss, sym_reduction, penalty_axis;
+  double tau, beta;
+};
+size_t infonce_ws_bytes(const LossSpec& ls, int B, int R, size_t elem, int path);
+// loss4 = {total, fwd, bwd, penalty}.  t_bump: if non-null, ++*t_bump (Adam step counter).
+template <typename T>
+void infonce_forward(const LossSpec& ls, const T* phi, const T* psi, int B, int R, T* loss4, T* row_lse,
+                     T* col_lse, void* ws, int path, unsigned* status, int* t_bump, cudaStream_t st);
+template <typename T>
+void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int R, const T* row_lse,
+                      const T* col_lse, double dtotal, T* dphi, T* dpsi, void* ws, int path,
+                      cudaStream_t st);
+
+// ---------------------------------------------------------------- actor head
+struct ActorSpec {
+  int A, energy;
+  double tau, alpha;
+};
+// eps: explicit [B][A] (may be float for a T = double path) or null -> Philox noise.
+template <typename T>
+void actor_head_forward(const ActorSpec& as, const T* pi_out, const float* eps,
+                        const unsigned long long* step_dev, uint64_t seed, uint64_t agent, int B,
+                        T* a_new, T* logpi, T* eps_used, cudaStream_t st);
+template <typename T>
+void actor_energy_and_loss(const ActorSpec& as, const T* phi, const T* psi, const T* logpi, int B, int R,
+                           T* dphi, T* fdiag, T* loss2, unsigned* status, int* t_bump, cudaStream_t st);
+template <typename T>
+void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used, const T* da, int B,
+                         T* dout, cudaStream_t st);
+
+// ---------------------------------------------------------------- Adam
+template <typename T>
+void adam_update(T* p, const T* g, T* m, T* v, int64_t n, const int* t_dev, int t_host, float lr,
+                 float b1, float b2, float eps, cudaStream_t st);
+
+// Small device utilities.
+void launch_bump_u64(unsigned long long* ctr, cudaStream_t st);
+
+}  // namespace crl

@@ -1,0 +1,45 @@
+// Per-context kernel tracing (crl_trace_start / crl_trace_stop): CUDA events
+// around every launch of one kernel class, plus its algorithmic work.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace crl {
+
+struct Tracer {
+  int cls = 0;
+  int cap = 0;
+  int n = 0;
+  cudaEvent_t* ev = nullptr;  // 2 * cap events
+  double work = 0.0;
+};
+
+// Set by each C-ABI entry point of a context for the duration of the call.
+extern thread_local Tracer* g_tracer;
+
+// RAII bracket around one launch of class `cls` with `work` algorithmic units.
+class TraceLaunch {
+ public:
+  TraceLaunch(int cls, cudaStream_t st, double work) : st_(st) {
+    Tracer* t = g_tracer;
+    if (t && t->cls == cls && t->n < t->cap) {
+      t_ = t;
+      cudaEventRecord(t->ev[2 * t->n], st);
+      t->work += work;
+    }
+  }
+  ~TraceLaunch() {
+    if (t_) {
+      cudaEventRecord(t_->ev[2 * t_->n + 1], st_);
+      t_->n += 1;
+    }
+  }
+  TraceLaunch(const TraceLaunch&) = delete;
+  TraceLaunch& operator=(const TraceLaunch&) = delete;
+
+ private:
+  Tracer* t_ = nullptr;
+  cudaStream_t st_;
+};
+
+}  // namespace crl

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every function include/crl.h declares.
+
+Runs without a GPU: only host-side entry points are called (config defaults
+and the parameter layout), never a kernel.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2408_11052_gb300 import api, build, workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "crl.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return api.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(crl_[a-z0-9_]+)\s*\(", text))
+    assert names, "no declarations found"
+    return sorted(names)
+
+
+def test_every_declared_function_is_exported(lib):
+    raw = ctypes.CDLL(api.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(raw, n)]
+    assert not missing, missing
+    assert set(declared_functions()) == set(api._SIGNATURES), "binding signatures out of sync with the header"
+
+
+def test_config_default_layout_matches_binding(lib):
+    c = api.CrlConfig()
+    lib.crl_config_default(ctypes.byref(c))
+    assert (c.E, c.T, c.D, c.A, c.G, c.B) == (1024, 1000, 29, 8, 2, 256)
+    assert (c.hidden, c.layers, c.repr) == (256, 2, 64)
+    assert list(c.goal_idx)[:3] == [0, 1, 2]
+    assert c.gamma == pytest.approx(0.99) and c.beta_lse == pytest.approx(0.1)
+    assert c.lr_critic == pytest.approx(3e-4) and c.lr_actor == pytest.approx(6e-4)
+    assert c.adam_eps == pytest.approx(1e-8) and c.offset_min == 1
+    assert c.seed == 0 and c.agent == 0
+    assert ctypes.sizeof(api.CrlConfig) == 184
+
+
+@pytest.mark.parametrize("w", [workload.ANT_AUTOGRAD, workload.HUMANOID_BF16, workload.LARGE_BATCH])
+@pytest.mark.parametrize("net", ["phi", "psi", "pi"])
+def test_param_layout_is_consistent(lib, w, net):
+    cfg = api.make_config(w)
+    n, tensors = api.param_layout(cfg, net)
+    ins, out = workload.network_shapes(w, net)
+    dims = [ins] + [w.hidden] * w.layers + [out]
+    expect = []
+    for li in range(w.layers + 1):
+        expect.append((li, "W", dims[li + 1], dims[li]))
+        expect.append((li, "b", dims[li + 1], 1))
+        if w.layernorm and li < w.layers:
+            expect += [(li, "ln_g", dims[li + 1], 1), (li, "ln_b", dims[li + 1], 1)]
+    assert [(t["layer"], t["kind"], t["rows"], t["cols"]) for t in tensors] == expect
+    end = 0
+    for t in tensors:
+        assert t["offset"] % 64 == 0 and t["offset"] >= end
+        end = t["offset"] + t["rows"] * t["cols"]
+    assert end <= n
+
+
+def test_host_side_errors_without_gpu(lib):
+    cfg = api.make_config(workload.SMALL_FP32)
+    out = ctypes.c_int64()
+    assert lib.crl_param_count(ctypes.byref(cfg), 7, ctypes.byref(out)) == api.E_INVALID_ARG
+    info = api.CrlTensorInfo()
+    assert lib.crl_param_tensor(ctypes.byref(cfg), 0, 99, ctypes.byref(info)) == api.E_INVALID_ARG
+    assert b"out of range" in lib.crl_last_error(None)

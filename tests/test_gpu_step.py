@@ -1,0 +1,127 @@
+"""Full update steps (insert -> relabel -> critic + Adam -> actor + Adam) through
+crl_update_step against the oracle's update step, and the status / error paths."""
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2408_11052_gb300 import api, workload
+
+from parity_helpers import KINK_MARGIN, batch_margin, hp, setup, small
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_steps(w, nets, buf, n_steps, start_step, inserts, check_kinks=False):
+    """Run the oracle's update step n_steps times; with check_kinks, None if a batch is near a kink."""
+    h = hp(w)
+    state = oracle.step.AgentState(nets["phi"], nets["psi"], nets["pi"])
+    cfg = dict(seed=w.seed, agent=0, B=w.B, goal_idx=w.goals(), gamma=w.gamma, energy=w.energy, tau=h["tau"],
+               loss=w.loss, sym_reduction=w.sym_reduction, beta=h["beta"], penalty_axis=w.penalty_axis,
+               alpha=h["alpha"], lr_critic=h["lr_critic"], lr_actor=h["lr_actor"], adam_beta1=h["adam_beta1"],
+               adam_beta2=h["adam_beta2"], adam_eps=h["adam_eps"])
+    outs = []
+    for i in range(n_steps):
+        buf.insert(*inserts[i])
+        eps = oracle.actor.gaussian_noise(w.seed, 0, start_step + i, w.B, w.A)
+        if check_kinks:
+            s, a, g, _ = oracle.relabel.sample_relabel(buf, w.seed, 0, start_step + i, w.B, w.goals(), w.gamma)
+            pre = {"phi": state.nets["phi"], "psi": state.nets["psi"], "pi": state.nets["pi"]}
+            if batch_margin(w, pre, s, a, g, eps) < KINK_MARGIN:
+                return None
+        outs.append(oracle.step.update_step(state, buf, cfg, start_step + i, eps))
+    return state, outs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("host_inputs", [False, True])
+def test_update_steps_match_oracle(precision, host_inputs):
+    w = small(B=64)
+    ctx, nets, buf = setup(w, precision=precision, n=60)
+    extra = workload.buffer_contents(w, n=3, mean_len=9.0, seed_offset=99)
+    inserts = [tuple(x[i:i + 1] for x in extra) for i in range(3)]
+    start = None
+    for cand in range(0, 48):
+        trial = oracle.relabel.ReplayBuffer(w.E, w.T, w.D, w.A)
+        trial.obs, trial.act, trial.done = buf.obs.copy(), buf.act.copy(), buf.done.copy()
+        if oracle_steps(w, nets, trial, 3, cand, inserts, check_kinks=True) is not None:
+            start = cand
+            break
+    assert start is not None
+    ctx.set_step(start)
+    kw = dict(dtype=torch.float32)
+    loss_out = torch.zeros(6, **kw) if host_inputs else torch.zeros(6, device=ctx.device, **kw)
+    losses = []
+    for obs, act, done in inserts:
+        if host_inputs:
+            ctx.update_step(obs, act, done, loss_out=loss_out)
+        else:
+            d = ctx.device
+            ctx.update_step(torch.from_numpy(obs).to(d), torch.from_numpy(act).to(d), torch.from_numpy(done).to(d),
+                            loss_out=loss_out)
+        torch.cuda.synchronize()
+        losses.append(loss_out.cpu().numpy().astype(np.float64).copy())
+    state, outs = oracle_steps(w, nets, buf, 3, start, inserts)
+    rtol = 1.2e-7 if precision == "fp64" else 2e-4
+    for got, ref in zip(losses, outs):
+        c = ref["critic"]
+        np.testing.assert_allclose(got[:4], [c["total"], c["fwd"], c["bwd"], c["penalty"]], rtol=rtol, atol=1e-7)
+        np.testing.assert_allclose(got[4:6], [ref["actor_loss"], ref["logpi_mean"]], rtol=rtol, atol=1e-6)
+    # Parameters after three Adam steps.  FP32: Adam's first steps move every weight by
+    # about lr * sign(g), so coordinates whose true gradient is near zero may move the
+    # other way; allow 2 lr there and 1e-3 lr elsewhere.
+    for net in ("phi", "psi", "pi"):
+        lr = w.lr_actor if net == "pi" else w.lr_critic
+        for gl, rl in zip(ctx.network(net), state.nets[net]):
+            for k in rl:
+                if precision == "fp64":
+                    np.testing.assert_allclose(gl[k], rl[k], rtol=1e-9, atol=1e-12)
+                else:
+                    err = np.abs(gl[k] - rl[k])
+                    assert np.mean(err <= 1e-3 * lr + 1e-7) > 0.98, (net, k)
+                    assert err.max() <= 6 * lr + 1e-6, (net, k)
+    assert ctx.sync_status() == (0, 0)
+    assert ctx.get_step() == start + 3
+
+
+def test_nonfinite_loss_sets_status():
+    w = small(B=32)
+    ctx, _, _ = setup(w, n=40)
+    ctx.views("phi")[-1]["b"][0] = float("nan")
+    s, a, g, _ = ctx.sample(step=0)
+    ctx.critic_step(s, a, g)
+    rc, status = ctx.sync_status()
+    assert rc == api.E_NONFINITE and status & api.STATUS_NONFINITE
+    assert ctx.sync_status() == (0, 0)          # cleared by the read
+
+
+def test_bad_sizes_and_configs_are_rejected():
+    w = small(B=32)
+    ctx, _, _ = setup(w, n=40)
+    big = [torch.zeros(33, n, device=ctx.device) for n in (w.D, w.A, w.G)]
+    with pytest.raises(api.CRLError) as e:
+        ctx.critic_step(*big)
+    assert e.value.code == api.E_SHAPE
+    h = ctypes.c_void_p()
+    for bad in (api.make_config(w, gamma=1.0), api.make_config(w, temperature=0.0),
+                api.make_config(w, layers=0), api.make_config(w, offset_min=2)):
+        assert api.lib().crl_create(ctypes.byref(bad), ctypes.byref(h)) == api.E_INVALID_ARG
+        assert h.value is None
+    cfg = api.make_config(w)
+    cfg.goal_idx[1] = w.D                      # goal dim outside the observation
+    assert api.lib().crl_create(ctypes.byref(cfg), ctypes.byref(h)) == api.E_INVALID_ARG
+
+
+def test_tracing_counts_relabel_bytes():
+    w = small(B=64)
+    ctx, _, _ = setup(w, n=40)
+    ctx.trace_start("relabel", 16)
+    for step in range(3):
+        ctx.sample(step=step)
+    n, ms, work = ctx.trace_stop()
+    assert n == 3 and ms > 0
+    per = (w.D + w.A + 1 + w.G) * 4 + (w.D + w.A + w.G) * 4 + 12
+    assert work == pytest.approx(3 * w.B * per)

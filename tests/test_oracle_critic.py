@@ -149,3 +149,17 @@ def test_l2_gradient_zero_at_coincident_points():
     G = np.ones((3, 3))
     dphi, dpsi = critic.energy_backward(phi, phi.copy(), G, "l2", 1.0)
     assert np.all(dphi == 0) and np.all(dpsi == 0)
+
+
+def test_row_wise_energies_match_dense_broadcast():
+    """The row-at-a-time evaluation equals the dense [i][j][r] broadcast of the definition."""
+    phi, psi = reps(9, 6, 11)
+    diff = phi[:, None, :] - psi[None, :, :]
+    np.testing.assert_allclose(critic.energy_matrix(phi, psi, "l2"), -np.sqrt((diff ** 2).sum(2)), rtol=1e-14)
+    np.testing.assert_allclose(critic.energy_matrix(phi, psi, "l1"), -np.abs(diff).sum(2), rtol=1e-14)
+    G = np.random.default_rng(12).standard_normal((9, 9))
+    d = np.sqrt((diff ** 2).sum(2))
+    H = G / d
+    dphi, dpsi = critic.energy_backward(phi, psi, G, "l2", 1.0)
+    np.testing.assert_allclose(dphi, -(H[:, :, None] * diff).sum(1), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(dpsi, (H[:, :, None] * diff).sum(0), rtol=1e-12, atol=1e-13)

@@ -13,8 +13,6 @@ import torch
 from oracle import actor, adam, critic, mlp, step
 from paper_2408_11052_gb300 import workload
 
-torch.set_default_dtype(torch.float64)
-
 
 def small(layernorm, **kw):
     return workload.Workload("t", E=4, T=20, D=6, A=3, G=2, B=12, hidden=16, layers=2, repr=5,
@@ -230,3 +228,15 @@ def test_update_step_runs_and_orders_critic_before_actor():
     np.testing.assert_array_equal(out["idx"], idx)
     assert np.isfinite(out["critic"]["total"])
     assert critic.infonce_loss  # module used above
+
+
+def test_gaussian_noise_is_standard_normal():
+    """Box-Muller draws from Philox: moments and a Kolmogorov-Smirnov test against N(0, 1)."""
+    from scipy import stats
+    eps = actor.gaussian_noise(3, 0, 5, 600, 7).ravel()
+    assert abs(eps.mean()) < 5 / np.sqrt(eps.size)
+    assert abs(eps.std() - 1.0) < 0.05
+    assert stats.kstest(eps, "norm").pvalue > 1e-3
+    again = actor.gaussian_noise(3, 0, 5, 4, 7)
+    np.testing.assert_array_equal(again, eps.reshape(600, 7)[:4])
+    assert (actor.gaussian_noise(3, 0, 6, 4, 7) != again).all()
