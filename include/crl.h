@@ -303,6 +303,24 @@ int crl_infonce_backward(const crl_loss_desc* d, const void* phi, const void* ps
                          const void* row_lse, const void* col_lse, double dtotal, void* dphi,
                          void* dpsi, void* ws, size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of crl_infonce_forward (the paper has no
+ * counterpart; this is a library service).  For callers that must not
+ * allocate device memory when they evaluate the loss -- e.g. code running
+ * while another framework captures a CUDA graph, a host that fixes its device
+ * memory at start-up, or a plugin inside a runtime that owns the allocator.
+ * Same arguments and results as crl_infonce_forward, minus the workspace: the
+ * scratch is a fixed 4 MiB array inside the library, held on every GPU that
+ * loads it until the process exits; sizes whose scratch would exceed it
+ * (crl_infonce_workspace_bytes > 4194304, e.g. B > ~900 at R = 64 in FP32)
+ * are rejected with CRL_E_SHAPE.  Allocates nothing (no cudaMalloc/cudaFree).
+ * The first call on each device does a one-time set-up (looks up the array's
+ * device address); make that first call before any stream capture.  Every
+ * call shares the one array: calls whose work may overlap on the GPU (other
+ * streams or threads without ordering) race and give wrong results.
+ * dtype CRL_PREC_FP32 / CRL_PREC_FP64, path CRL_PATH_PLAIN. */
+int crl_infonce_forward_noalloc(const crl_loss_desc* d, const void* phi, const void* psi, int32_t B, int32_t R,
+                                void* loss4, void* row_lse, void* col_lse, void* stream);
+
 /* One Adam step on n elements at step number t (1-based), dtype as above. */
 int crl_adam_update(int32_t dtype, void* params, const void* grads, void* m, void* v, int64_t n,
                     int32_t t, float lr, float beta1, float beta2, float eps, void* stream);

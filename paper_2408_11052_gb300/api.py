@@ -94,6 +94,8 @@ _SIGNATURES = {
                                       c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "crl_infonce_backward": (c_int32, [POINTER(CrlLossDesc), c_void_p, c_void_p, c_int32, c_int32, c_void_p,
                                        c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "crl_infonce_forward_noalloc": (c_int32, [POINTER(CrlLossDesc), c_void_p, c_void_p, c_int32, c_int32, c_void_p,
+                                              c_void_p, c_void_p, c_void_p]),
     "crl_adam_update": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_float,
                                   c_float, c_float, c_float, c_void_p]),
 }

@@ -172,6 +172,10 @@ struct crl_ctx {
   }
 };
 
+namespace crl {
+void set_thread_error(const std::string& msg) { g_thread_error = msg; }
+}  // namespace crl
+
 namespace {
 
 int fail(crl_ctx* ctx, const Failure& f) {

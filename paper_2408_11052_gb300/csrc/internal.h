@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/crl.h"
 
 namespace crl {
@@ -99,5 +101,8 @@ void adam_update(T* p, const T* g, T* m, T* v, int64_t n, const int* t_dev, int 
 
 // Small device utilities.
 void launch_bump_u64(unsigned long long* ctr, cudaStream_t st);
+
+// Sets the message crl_last_error(NULL) returns on the calling thread.
+void set_thread_error(const std::string& msg);
 
 }  // namespace crl
