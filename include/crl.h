@@ -226,7 +226,13 @@ int crl_actor_step(crl_ctx* ctx, const float* s, const float* g, const float* ep
  * -> actor step (Philox noise), with Adam for both; the batch lives in
  * library workspaces.  obs/act/done as crl_buffer_insert (host or device).
  * loss_out: 6 floats {critic total, fwd, bwd, penalty, actor loss,
- * mean log pi}, host or device, or NULL.  B = cfg.B. */
+ * mean log pi}, host or device, or NULL.  B = cfg.B.
+ * From the second call on a non-default stream (and while tracing is off) the
+ * relabel -> critic -> actor sequence is captured once as a CUDA graph and
+ * replayed; crl_bind_params discards the graph.  Between crl_update_step
+ * calls the library assumes it is the only writer of the parameters (the
+ * BF16 weight shadows follow them through Adam); after changing parameters
+ * from outside, call crl_bind_params again. */
 int crl_update_step(crl_ctx* ctx, const float* obs, const float* act, const uint8_t* done,
                     int32_t n_insert, float* loss_out, void* stream);
 

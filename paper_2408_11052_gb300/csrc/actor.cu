@@ -28,18 +28,28 @@ namespace {
 // N(0, 1) noise for element d of row b: Box-Muller on Philox4x64-10 block
 // (step, b, 1, d / 4); words (0, 1) feed elements 4q, 4q+1 and words (2, 3)
 // feed 4q+2, 4q+3 (cos / sin branch).
-__device__ double philox_normal(unsigned long long step, int b, int d, unsigned long long seed,
-                                unsigned long long agent) {
+// The FP64 path draws the noise in double; the FP32 path in float (same
+// Philox words, so the two agree to float rounding).
+template <typename T>
+__device__ T philox_normal(unsigned long long step, int b, int d, unsigned long long seed, unsigned long long agent) {
   const Philox4 r = philox4x64_10(step, (unsigned long long)b, 1ull, (unsigned long long)(d / 4), seed, agent);
   const int pair = (d % 4) / 2;
   const double u1 = u64_to_unit_open(r.w[2 * pair]);
   const double u2 = u64_to_unit_open(r.w[2 * pair + 1]);
-  const double rad = sqrt(-2.0 * log(u1));
-  double s, c;
-  sincos(kTwoPi * u2, &s, &c);
-  return (d % 2 == 0) ? rad * c : rad * s;
+  if constexpr (sizeof(T) == 8) {
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincos(kTwoPi * u2, &s, &c);
+    return (d % 2 == 0) ? rad * c : rad * s;
+  } else {
+    const float rad = sqrtf(-2.0f * logf((float)u1));
+    float s, c;
+    sincosf((float)(kTwoPi * u2), &s, &c);
+    return (d % 2 == 0) ? rad * c : rad * s;
+  }
 }
 
+// One warp per row b, lanes over the action dims.
 template <typename T>
 __global__ void __launch_bounds__(256) head_forward_kernel(int B, int A, const T* __restrict__ out,
                                                           const float* __restrict__ eps,
@@ -47,21 +57,23 @@ __global__ void __launch_bounds__(256) head_forward_kernel(int B, int A, const T
                                                           unsigned long long seed, unsigned long long agent,
                                                           T* __restrict__ a_new, T* __restrict__ logpi,
                                                           T* __restrict__ eps_used) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x % kWarp;
+  const int b = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (b >= B) return;
   const unsigned long long step = eps ? 0ull : *step_dev;
   T lp = 0;
-  for (int d = 0; d < A; ++d) {
+  for (int d = lane; d < A; d += kWarp) {
     const T mu = out[(size_t)b * 2 * A + d];
     const T lraw = out[(size_t)b * 2 * A + A + d];
     const T l = fmin(fmax(lraw, T(kLogStdMin)), T(kLogStdMax));
-    const T e = eps ? T(eps[(size_t)b * A + d]) : T(philox_normal(step, b, d, seed, agent));
+    const T e = eps ? T(eps[(size_t)b * A + d]) : philox_normal<T>(step, b, d, seed, agent);
     const T u = mu + dev_exp(l) * e;
     a_new[(size_t)b * A + d] = dev_tanh(u);
     eps_used[(size_t)b * A + d] = e;
     lp += -T(0.5) * e * e - T(kHalfLog2Pi) - l - T(2) * (T(kLog2) - u - softplus(T(-2) * u));
   }
-  logpi[b] = lp;
+  lp = warp_sum(lp);
+  if (lane == 0) logpi[b] = lp;
 }
 
 // f_i = f(phi_i, psi_i) / tau and dphi_i = -(1/B) df_i/dphi_i.  One warp per row.
@@ -166,7 +178,7 @@ template <typename T>
 void actor_head_forward(const ActorSpec& as, const T* pi_out, const float* eps, const unsigned long long* step_dev,
                         uint64_t seed, uint64_t agent, int B, T* a_new, T* logpi, T* eps_used, cudaStream_t st) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 5);
-  head_forward_kernel<T><<<ceil_div(B, 256), 256, 0, st>>>(B, as.A, pi_out, eps, step_dev, seed, agent, a_new,
+  head_forward_kernel<T><<<ceil_div(B, 8), 256, 0, st>>>(B, as.A, pi_out, eps, step_dev, seed, agent, a_new,
                                                            logpi, eps_used);
 }
 

@@ -18,12 +18,17 @@ template <typename T>
 __global__ void __launch_bounds__(256) adam_kernel(T* __restrict__ p, const T* __restrict__ g, T* __restrict__ m,
                                                   T* __restrict__ v, long long n, const int* __restrict__ t_dev,
                                                   int t_host, float lr, float b1, float b2, float eps) {
-  const int t = t_dev ? *t_dev : t_host;
-  // Bias corrections in double: 1 - b^t loses most of its digits in float for small t.
-  const double bc1 = 1.0 - pow((double)b1, (double)t);
-  const double bc2 = 1.0 - pow((double)b2, (double)t);
-  const T step = T((double)lr / bc1);
-  const T ibc2 = T(1.0 / bc2);
+  // Bias corrections in double (1 - b^t loses most of its digits in float for
+  // small t), computed once per block.
+  __shared__ double s_corr[2];
+  if (threadIdx.x == 0) {
+    const int t = t_dev ? *t_dev : t_host;
+    s_corr[0] = (double)lr / (1.0 - pow((double)b1, (double)t));
+    s_corr[1] = 1.0 / (1.0 - pow((double)b2, (double)t));
+  }
+  __syncthreads();
+  const T step = T(s_corr[0]);
+  const T ibc2 = T(s_corr[1]);
   const T tb1 = T(b1), tb2 = T(b2), one = T(1);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const T gi = g[i];

@@ -11,7 +11,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "energy_tc.cuh"
 #include "internal.h"
+#include "mlp_bf16.cuh"
 #include "trace.h"
 
 using namespace crl;
@@ -108,8 +110,16 @@ void validate_config(const crl_config& c) {
   CRL_REQUIRE(c.offset_min == 0 || c.offset_min == 1, CRL_E_INVALID_ARG, "offset_min must be 0 or 1");
   CRL_REQUIRE(c.precision >= CRL_PREC_FP32 && c.precision <= CRL_PREC_FP64, CRL_E_INVALID_ARG, "unknown precision");
   CRL_REQUIRE(c.path == CRL_PATH_PLAIN || c.path == CRL_PATH_FUSED, CRL_E_INVALID_ARG, "unknown path");
-  CRL_REQUIRE(c.precision != CRL_PREC_BF16 && c.path == CRL_PATH_PLAIN, CRL_E_UNSUPPORTED,
-              "only the plain FP32 / FP64 path is available in this build");
+  if (c.path == CRL_PATH_FUSED) {
+    CRL_REQUIRE(c.precision == CRL_PREC_BF16, CRL_E_UNSUPPORTED, "the fused energy path runs in BF16 only");
+    const char* why = nullptr;
+    LossSpec ls{c.energy, c.loss, c.sym_reduction, c.penalty_axis, c.temperature, c.beta_lse};
+    CRL_REQUIRE(energy_tc_supported(ls, c.B, c.repr, &why), CRL_E_UNSUPPORTED, why);
+  }
+  if (c.precision == CRL_PREC_BF16) {
+    CRL_REQUIRE(c.B % 8 == 0 && c.hidden % 8 == 0, CRL_E_UNSUPPORTED,
+                "the BF16 path needs B and hidden to be multiples of 8 (16-byte TMA rows)");
+  }
   CRL_REQUIRE(c.energy != CRL_ENERGY_L1, CRL_E_UNSUPPORTED, "the L1 energy backward is not implemented");
   CRL_REQUIRE(c.lr_critic >= 0.f && c.lr_actor >= 0.f && c.adam_eps > 0.f && c.adam_beta1 >= 0.f &&
                   c.adam_beta1 < 1.f && c.adam_beta2 >= 0.f && c.adam_beta2 < 1.f,
@@ -150,6 +160,20 @@ struct crl_ctx {
   void* stage = nullptr;
   size_t stage_bytes = 0;
   Tracer tracer;
+  // BF16 tensor-core networks (precision CRL_PREC_BF16)
+  bool bf16 = false;
+  BfNet bf[3];
+  bool shadow_ok[3] = {false, false, false};  // BF16 shadows match the FP32 master weights
+  bool fused = false;
+  EnergyTc etc;
+  void* etc_ws = nullptr;
+  // second stream for the independent phi / psi chains (fork / join through events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev[4] = {};
+  // CUDA graph of relabel -> critic -> actor, replayed by crl_update_step
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  int update_calls = 0;
   std::string err;
 
   void* dalloc(size_t bytes) {
@@ -165,8 +189,17 @@ struct crl_ctx {
     }
     tracer = Tracer();
   }
+  void drop_graph() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    graph_stream = nullptr;
+  }
   ~crl_ctx() {
+    drop_graph();
     drop_trace_events();
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (side) cudaStreamDestroy(side);
     for (void* p : allocs) cudaFree(p);
     if (stage) cudaFree(stage);
   }
@@ -306,6 +339,160 @@ void actor_impl(crl_ctx* c, const float* s, const float* g, const float* eps, in
   check_launch("actor step");
 }
 
+void* ctx_alloc(void* owner, size_t bytes) {
+  try {
+    return static_cast<crl_ctx*>(owner)->dalloc(bytes);
+  } catch (...) {
+    return nullptr;
+  }
+}
+
+void bf_maps(crl_ctx* c, int net, int B) {
+  const char* e = bf_net_maps(c->bf[net], B);
+  if (e) throw Failure(CRL_E_CUDA, std::string("tensor map: ") + e);
+}
+
+// Fork: `side` waits for everything issued so far on `st`.  Join: `st` waits for `side`.
+void fork_to_side(crl_ctx* c, cudaStream_t st, int k) {
+  CRL_CHECK_CUDA(cudaEventRecord(c->ev[k], st));
+  CRL_CHECK_CUDA(cudaStreamWaitEvent(c->side, c->ev[k], 0));
+}
+void join_from_side(crl_ctx* c, cudaStream_t st, int k) {
+  CRL_CHECK_CUDA(cudaEventRecord(c->ev[k], c->side));
+  CRL_CHECK_CUDA(cudaStreamWaitEvent(st, c->ev[k], 0));
+}
+
+// Refresh the BF16 shadows of `net` unless they are known to match (refresh forces it).
+void bf_refresh(crl_ctx* c, int net, bool refresh, cudaStream_t st) {
+  if (refresh || !c->shadow_ok[net]) {
+    bf_net_shadow(c->bf[net], static_cast<const float*>(c->nets[net].params), st);
+    c->shadow_ok[net] = true;
+  }
+}
+
+AdamShadowNet adam_net_of(crl_ctx* c, int net, const int* t, float lr) {
+  const crl_net_ptrs& np = c->nets[net];
+  return AdamShadowNet{static_cast<float*>(np.params), static_cast<const float*>(np.grads),
+                       static_cast<float*>(np.adam_m), static_cast<float*>(np.adam_v), c->counts[net], t, lr,
+                       &c->bf[net]};
+}
+
+// Critic step with BF16 tensor-core encoders (FP32 master weights).  refresh:
+// rebuild the BF16 weight shadows first (the caller may have changed the weights).
+void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g, int B, int apply, cudaStream_t st,
+                      bool refresh = true, bool packed = false) {
+  const crl_config& cf = c->cfg;
+  unsigned* status = &c->ctr->status;
+  BfNet& P = c->bf[CRL_NET_PHI];
+  BfNet& Q = c->bf[CRL_NET_PSI];
+  const float* pphi = static_cast<const float*>(c->nets[CRL_NET_PHI].params);
+  const float* ppsi = static_cast<const float*>(c->nets[CRL_NET_PSI].params);
+  bf_maps(c, CRL_NET_PHI, B);
+  bf_maps(c, CRL_NET_PSI, B);
+  bf_refresh(c, CRL_NET_PHI, refresh, st);
+  bf_refresh(c, CRL_NET_PSI, refresh, st);
+  if (!packed) {
+    bf_net_pack_input(P, s, a, B, st);
+    bf_net_pack_input(Q, g, nullptr, B, st);
+  }
+  // phi and psi forward in parallel
+  fork_to_side(c, st, 0);
+  bf_net_forward(P, pphi, B, status, st);
+  bf_net_forward(Q, ppsi, B, status, c->side);
+  join_from_side(c, st, 1);
+  float* rl = static_cast<float*>(c->row_lse);
+  float* cl = static_cast<float*>(c->col_lse);
+  float* loss = static_cast<float*>(c->loss);
+  float* dphi = static_cast<float*>(c->dphi);
+  float* dpsi = static_cast<float*>(c->dpsi);
+  const LossSpec ls = loss_spec(cf);
+  if (c->fused) {
+    // fused tcgen05 energy stage: no B x B matrix; the gradients land in the encoders' dy buffers
+    const char* e = energy_tc_maps(c->etc, B);
+    if (e) throw Failure(CRL_E_CUDA, std::string("tensor map: ") + e);
+    energy_tc_prepare(c->etc, ls, P.y, Q.y, B, st);
+    energy_tc_forward(c->etc, ls, B, loss, rl, cl, c->etc_ws, status, apply ? &c->ctr->t_critic : nullptr, st);
+    energy_tc_backward(c->etc, ls, B, P.y, Q.y, rl, cl, 1.0, P.dz[0], P.dzT[0], Q.dz[0], Q.dzT[0], P.Mmax, status,
+                       st);
+  } else {
+    infonce_forward<float>(ls, P.y, Q.y, B, cf.repr, loss, rl, cl, c->ws, CRL_PATH_PLAIN, status,
+                           apply ? &c->ctr->t_critic : nullptr, st);
+    infonce_backward<float>(ls, P.y, Q.y, B, cf.repr, rl, cl, 1.0, dphi, dpsi, c->ws, CRL_PATH_PLAIN, st);
+    bf_net_load_dy(P, dphi, B, st);
+    bf_net_load_dy(Q, dpsi, B, st);
+  }
+  // phi and psi backward in parallel
+  fork_to_side(c, st, 2);
+  bf_net_backward(P, pphi, B, static_cast<float*>(c->nets[CRL_NET_PHI].grads), nullptr, status, st);
+  bf_net_backward(Q, ppsi, B, static_cast<float*>(c->nets[CRL_NET_PSI].grads), nullptr, status, c->side);
+  join_from_side(c, st, 3);
+  if (apply) {
+    // Adam for phi and psi in one launch, refreshing their BF16 shadows
+    const AdamShadowNet an[2] = {adam_net_of(c, CRL_NET_PHI, &c->ctr->t_critic, cf.lr_critic),
+                                 adam_net_of(c, CRL_NET_PSI, &c->ctr->t_critic, cf.lr_critic)};
+    adam_shadow_update(an, 2, cf.adam_beta1, cf.adam_beta2, cf.adam_eps, st);
+  }
+  {
+    TraceLaunch tr(CRL_TRACE_AUX, st, 32.0);
+    to_float_kernel<float><<<1, 32, 0, st>>>(loss, c->loss_f, 4);
+  }
+  check_launch("critic step (bf16)");
+}
+
+// Actor step with BF16 tensor-core networks.
+void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* eps, int B, int apply, cudaStream_t st,
+                     bool refresh = true, bool packed = false) {
+  const crl_config& cf = c->cfg;
+  unsigned* status = &c->ctr->status;
+  BfNet& PI = c->bf[CRL_NET_PI];
+  BfNet& P = c->bf[CRL_NET_PHI];
+  BfNet& Q = c->bf[CRL_NET_PSI];
+  const float* ppi = static_cast<const float*>(c->nets[CRL_NET_PI].params);
+  const float* pphi = static_cast<const float*>(c->nets[CRL_NET_PHI].params);
+  const float* ppsi = static_cast<const float*>(c->nets[CRL_NET_PSI].params);
+  for (int net = 0; net < 3; ++net) {
+    bf_maps(c, net, B);
+    bf_refresh(c, net, refresh, st);
+  }
+  float* a_new = static_cast<float*>(c->a_new);
+  float* logpi = static_cast<float*>(c->logpi);
+  float* eps_used = static_cast<float*>(c->eps_used);
+  float* dphi = static_cast<float*>(c->dphi);
+  float* da = static_cast<float*>(c->da);
+  float* dout = static_cast<float*>(c->dout);
+  float* loss = static_cast<float*>(c->loss) + 4;
+  ActorSpec as{cf.A, cf.energy, (double)cf.temperature, (double)cf.alpha};
+  if (!packed) {
+    bf_net_pack_input(PI, s, g, B, st);
+    bf_net_pack_input(Q, g, nullptr, B, st);
+  }
+  // psi(g) does not depend on the policy: it runs beside pi -> head -> phi
+  fork_to_side(c, st, 0);
+  bf_net_forward(Q, ppsi, B, status, c->side);
+  bf_net_forward(PI, ppi, B, status, st);
+  actor_head_forward<float>(as, PI.y, eps, &c->ctr->last_step, cf.seed, cf.agent, B, a_new, logpi, eps_used, st);
+  bf_net_pack_input(P, s, a_new, B, st);
+  bf_net_forward(P, pphi, B, status, st);
+  join_from_side(c, st, 1);
+  actor_energy_and_loss<float>(as, P.y, Q.y, logpi, B, cf.repr, dphi, static_cast<float*>(c->fdiag), loss, status,
+                               apply ? &c->ctr->t_actor : nullptr, st);
+  bf_net_load_dy(P, dphi, B, st);
+  bf_net_backward(P, pphi, B, nullptr, da, status, st);
+  actor_head_backward<float>(as, PI.y, eps_used, da, B, dout, st);
+  bf_net_load_dy(PI, dout, B, st);
+  const crl_net_ptrs& np = c->nets[CRL_NET_PI];
+  bf_net_backward(PI, ppi, B, static_cast<float*>(np.grads), nullptr, status, st);
+  if (apply) {
+    const AdamShadowNet an = adam_net_of(c, CRL_NET_PI, &c->ctr->t_actor, cf.lr_actor);
+    adam_shadow_update(&an, 1, cf.adam_beta1, cf.adam_beta2, cf.adam_eps, st);
+  }
+  {
+    TraceLaunch tr(CRL_TRACE_AUX, st, 16.0);
+    to_float_kernel<float><<<1, 32, 0, st>>>(loss, c->loss_f + 4, 2);
+  }
+  check_launch("actor step (bf16)");
+}
+
 void insert_impl(crl_ctx* c, const float* obs, const float* act, const uint8_t* done, int n, cudaStream_t st) {
   const crl_config& cf = c->cfg;
   CRL_REQUIRE(obs && act && done, CRL_E_INVALID_ARG, "obs, act and done must be non-null");
@@ -349,7 +536,8 @@ void insert_impl(crl_ctx* c, const float* obs, const float* act, const uint8_t* 
   c->size_host = (int32_t)(c->total_host < cf.T ? c->total_host : cf.T);
 }
 
-void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g, int32_t* idx, cudaStream_t st) {
+void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g, int32_t* idx, cudaStream_t st,
+                  bool pack_bf16 = false) {
   const crl_config& cf = c->cfg;
   CRL_REQUIRE(s && a && g, CRL_E_INVALID_ARG, "s, a and g must be non-null");
   CRL_REQUIRE(B >= 1 && B <= cf.B, CRL_E_SHAPE, "B must lie in [1, cfg.B]");
@@ -369,6 +557,12 @@ void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g
   ra.g = g;
   ra.idx = idx;
   ra.status = &c->ctr->status;
+  if (pack_bf16) {
+    for (int k = 0; k < 3; ++k) {
+      BfNet& n = c->bf[k];
+      ra.pack[k] = RelabelPack{n.x0, bf_net_x0_ld(n), n.x0T, n.Mmax};
+    }
+  }
   launch_relabel(c->bd, ra, st);
   if (step == CRL_STEP_AUTO) launch_bump_u64(&c->ctr->step, st);
   check_launch("sample relabel");
@@ -517,6 +711,29 @@ int crl_create(const crl_config* cfg, crl_ctx** out) {
     c->ba = static_cast<float*>(c->dalloc((size_t)B * cf.A * sizeof(float)));
     c->bg = static_cast<float*>(c->dalloc((size_t)B * cf.G * sizeof(float)));
     CRL_CHECK_CUDA(cudaMemset(c->loss_f, 0, 8 * sizeof(float)));
+    CRL_CHECK_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : c->ev) CRL_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (cf.precision == CRL_PREC_BF16) {
+      c->bf16 = true;
+      for (int net = 0; net < 3; ++net) {
+        const char* e = bf_net_init(c->bf[net], c->shapes[net], B, ctx_alloc, c);
+        if (e) throw Failure(CRL_E_CUDA, std::string("BF16 network set-up: ") + e);
+      }
+    }
+    if (cf.path == CRL_PATH_FUSED) {
+      c->fused = true;
+      EnergyTc& e = c->etc;
+      e.R = R;
+      e.Bmax = B;
+      e.ldt = B;
+      e.X = static_cast<__nv_bfloat16*>(c->dalloc((size_t)B * R * 2));
+      e.Y = static_cast<__nv_bfloat16*>(c->dalloc((size_t)B * R * 2));
+      e.XT = static_cast<__nv_bfloat16*>(c->dalloc((size_t)B * R * 2));
+      e.YT = static_cast<__nv_bfloat16*>(c->dalloc((size_t)B * R * 2));
+      e.auxX = static_cast<float*>(c->dalloc((size_t)B * 4));
+      e.auxY = static_cast<float*>(c->dalloc((size_t)B * 4));
+      c->etc_ws = c->dalloc(energy_tc_ws_bytes(B));
+    }
     CRL_CHECK_CUDA(cudaDeviceSynchronize());
   });
   if (rc != CRL_OK) {
@@ -547,6 +764,9 @@ int crl_bind_params(crl_ctx* ctx, const crl_net_ptrs nets[3]) {
     }
     CRL_CHECK_CUDA(cudaMemset(&ctx->ctr->t_critic, 0, 2 * sizeof(int)));
     CRL_CHECK_CUDA(cudaDeviceSynchronize());
+    ctx->drop_graph();
+    ctx->update_calls = 0;
+    for (int i = 0; i < 3; ++i) ctx->shadow_ok[i] = false;
     ctx->bound = true;
   });
 }
@@ -583,6 +803,7 @@ int crl_critic_step(crl_ctx* ctx, const float* s, const float* a, const float* g
     CRL_REQUIRE(B >= 1 && B <= ctx->cfg.B, CRL_E_SHAPE, "B must lie in [1, cfg.B]");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (ctx->cfg.precision == CRL_PREC_FP64) critic_impl<double>(ctx, s, a, g, B, apply_update, st);
+    else if (ctx->bf16) critic_impl_bf16(ctx, s, a, g, B, apply_update, st);
     else critic_impl<float>(ctx, s, a, g, B, apply_update, st);
     deliver_floats(loss_out, ctx->loss_f, 4, st);
   });
@@ -597,10 +818,31 @@ int crl_actor_step(crl_ctx* ctx, const float* s, const float* g, const float* ep
     CRL_REQUIRE(B >= 1 && B <= ctx->cfg.B, CRL_E_SHAPE, "B must lie in [1, cfg.B]");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (ctx->cfg.precision == CRL_PREC_FP64) actor_impl<double>(ctx, s, g, eps, B, apply_update, st);
+    else if (ctx->bf16) actor_impl_bf16(ctx, s, g, eps, B, apply_update, st);
     else actor_impl<float>(ctx, s, g, eps, B, apply_update, st);
     deliver_floats(loss_out, ctx->loss_f + 4, 2, st);
   });
 }
+
+namespace {
+// relabel (device step counter) -> critic + Adam -> actor + Adam on the batch workspaces
+void update_body(crl_ctx* ctx, cudaStream_t st) {
+  const int B = ctx->cfg.B;
+  // the BF16 path has the relabel kernel pack the network inputs directly
+  relabel_impl(ctx, CRL_STEP_AUTO, B, ctx->bs, ctx->ba, ctx->bg, nullptr, st, ctx->bf16);
+  if (ctx->cfg.precision == CRL_PREC_FP64) {
+    critic_impl<double>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
+    actor_impl<double>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st);
+  } else if (ctx->bf16) {
+    // the shadows follow the weights through the fused Adam; only the first call refreshes
+    critic_impl_bf16(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st, false, true);
+    actor_impl_bf16(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st, false, true);
+  } else {
+    critic_impl<float>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
+    actor_impl<float>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st);
+  }
+}
+}  // namespace
 
 int crl_update_step(crl_ctx* ctx, const float* obs, const float* act, const uint8_t* done, int32_t n_insert,
                     float* loss_out, void* stream) {
@@ -610,15 +852,36 @@ int crl_update_step(crl_ctx* ctx, const float* obs, const float* act, const uint
     CRL_REQUIRE(n_insert >= 0, CRL_E_INVALID_ARG, "n_insert must be >= 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n_insert > 0) insert_impl(ctx, obs, act, done, n_insert, st);
-    const int B = ctx->cfg.B;
-    relabel_impl(ctx, CRL_STEP_AUTO, B, ctx->bs, ctx->ba, ctx->bg, nullptr, st);
-    if (ctx->cfg.precision == CRL_PREC_FP64) {
-      critic_impl<double>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
-      actor_impl<double>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st);
+    CRL_REQUIRE(ctx->size_host > 0, CRL_E_BUFFER_EMPTY, "the replay buffer is empty");
+    // Every argument of the body is fixed (device counters, library workspaces,
+    // bound parameters), so after one eager call it is captured once and
+    // replayed.  The legacy default stream cannot be captured, and tracing needs
+    // eager launches: those run eagerly.
+    const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread &&
+                            ctx->tracer.cls == 0;
+    if (capturable && ctx->graph && ctx->graph_stream == st) {
+      CRL_CHECK_CUDA(cudaGraphLaunch(ctx->graph, st));
+    } else if (capturable && ctx->update_calls > 0) {
+      ctx->drop_graph();
+      cudaGraph_t g = nullptr;
+      CRL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      try {
+        update_body(ctx, st);
+      } catch (...) {
+        cudaStreamEndCapture(st, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      CRL_CHECK_CUDA(cudaStreamEndCapture(st, &g));
+      const cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+      cudaGraphDestroy(g);
+      CRL_CHECK_CUDA(e);
+      ctx->graph_stream = st;
+      CRL_CHECK_CUDA(cudaGraphLaunch(ctx->graph, st));
     } else {
-      critic_impl<float>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
-      actor_impl<float>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st);
+      update_body(ctx, st);
     }
+    ctx->update_calls += 1;
     deliver_floats(loss_out, ctx->loss_f, 6, st);
   });
 }

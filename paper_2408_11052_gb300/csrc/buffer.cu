@@ -8,6 +8,8 @@
 // (see BufferDev in internal.h).  All environments insert in lockstep.
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 #include "philox.cuh"
@@ -158,6 +160,26 @@ __global__ void __launch_bounds__(256) relabel_kernel(BufferDev bd, RelabelArgs 
     else ra.a[(size_t)b * bd.A + (c - bd.D)] = v;
   }
   if (lane < ra.G) ra.g[(size_t)b * ra.G + lane] = grow[ra.goal_idx[lane]];
+  // BF16 split packs of the network inputs (hi, lo interleaved; transposed copy)
+  for (int k = 0; k < 3; ++k) {
+    const RelabelPack& pk = ra.pack[k];
+    if (pk.x0 == nullptr) continue;
+    const int ncol = (k == 0) ? bd.D + bd.A : (k == 1 ? ra.G : bd.D + ra.G);
+    __nv_bfloat16* x0 = static_cast<__nv_bfloat16*>(pk.x0);
+    __nv_bfloat16* xT = static_cast<__nv_bfloat16*>(pk.x0T);
+    for (int c = lane; c < ncol; c += kWarp) {
+      float v;
+      if (k == 0) v = row[c];
+      else if (k == 1) v = grow[ra.goal_idx[c]];
+      else v = c < bd.D ? row[c] : grow[ra.goal_idx[c - bd.D]];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      x0[(size_t)b * pk.ld + 2 * c] = hi;
+      x0[(size_t)b * pk.ld + 2 * c + 1] = lo;
+      xT[(size_t)(2 * c) * pk.ldt + b] = hi;
+      xT[(size_t)(2 * c + 1) * pk.ldt + b] = lo;
+    }
+  }
   if (ra.idx != nullptr && lane == 0) {
     ra.idx[3 * (size_t)b + 0] = e;
     ra.idx[3 * (size_t)b + 1] = t;

@@ -112,22 +112,36 @@ __global__ void __launch_bounds__(256) row_lse_kernel(int B, const T* __restrict
   if (lane == 0) r[row] = m + dev_log(s);
 }
 
-// c_j = LSE_i F_ij.  One thread per column, single pass with a running max.
+// c_j = LSE_i F_ij.  Block = 32 columns x 8 row groups; each thread keeps a
+// running (max, sum) over its rows, then the 8 partials of a column are merged.
 template <typename T>
 __global__ void __launch_bounds__(256) col_lse_kernel(int B, const T* __restrict__ F, T* __restrict__ c) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= B) return;
+  __shared__ T sm_m[8][33], sm_s[8][33];
+  const int cx = threadIdx.x % 32, ry = threadIdx.x / 32;
+  const int j = blockIdx.x * 32 + cx;
   T m = -INFINITY, s = 0;
-  for (int i = 0; i < B; ++i) {
-    const T x = F[(size_t)i * B + j];
-    if (x > m) {
-      s = s * dev_exp(m - x) + T(1);
-      m = x;
-    } else {
-      s += dev_exp(x - m);
+  if (j < B) {
+    for (int i = ry; i < B; i += 8) {
+      const T x = F[(size_t)i * B + j];
+      if (x > m) {
+        s = s * dev_exp(m - x) + T(1);
+        m = x;
+      } else {
+        s += dev_exp(x - m);
+      }
     }
   }
-  c[j] = m + dev_log(s);
+  sm_m[ry][cx] = m;
+  sm_s[ry][cx] = s;
+  __syncthreads();
+  if (ry == 0 && j < B) {
+    T mm = sm_m[0][cx];
+    for (int r = 1; r < 8; ++r) mm = fmax(mm, sm_m[r][cx]);
+    T ss = 0;
+    for (int r = 0; r < 8; ++r)
+      if (sm_s[r][cx] > T(0)) ss += sm_s[r][cx] * dev_exp(sm_m[r][cx] - mm);
+    c[j] = mm + dev_log(ss);
+  }
 }
 
 // Row sums (warp per row) and column sums (thread per column) of H.
@@ -270,7 +284,7 @@ void infonce_forward(const LossSpec& ls, const T* phi, const T* psi, int B, int 
     default: gemm<T, InnerOp::kMul>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
   }
   { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); row_lse_kernel<T><<<nb, 256, 0, st>>>(B, w.F, row_lse); }
-  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); col_lse_kernel<T><<<ceil_div(B, 256), 256, 0, st>>>(B, w.F, col_lse); }
+  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); col_lse_kernel<T><<<ceil_div(B, 32), 256, 0, st>>>(B, w.F, col_lse); }
   { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); loss_kernel<T><<<1, 1024, 0, st>>>(B, w.F, B, row_lse, col_lse, weights(ls), ls.beta, loss4, status, t_bump); }
 }
 

@@ -1,0 +1,673 @@
+// Fused energy + InfoNCE + logsumexp penalty on tcgen05 (the BF16 fused path):
+// the B x B energy matrix is never written to HBM.
+//
+// arXiv 2408.11052: §3.1 critic objective, App. A.2 energies and InfoNCE
+// directions, Algorithm 1 (critic loss + beta * logsumexp penalty).  Readings as
+// in the plain path (C1-C7): F_ij = f(phi_i, psi_j) / tau, batch means, the
+// penalty on the squared row (or column) logsumexp.
+//
+// Representations enter as BF16 X = phi (or phi / |phi| for cos) and Y = psi,
+// plus a per-row FP32 auxiliary: |x|^2 of the BF16-rounded row (L2, L2^2) or
+// 1 / |phi| (cos).  S = X Y^T is formed 128 x 128 at a time in TMEM; the L2
+// energies use d^2 = |x|^2 + |y|^2 - 2 S (clamped at 0).
+//
+// forward:  one CTA per (row tile I, column tile J): S -> F tile in shared
+//           memory -> per-row (max, sum) over the tile's columns and per-column
+//           (max, sum) over the tile's rows, written as partials; the diagonal
+//           entries F_ii.  A one-block finalize merges the partials into
+//           r_i = LSE_j F_ij, c_j = LSE_i F_ij and the loss parts.
+// backward: the "row pass" (one CTA per 128 rows of phi) loops over column
+//           tiles: S -> coefficient tile H (dL/dF times the energy's chain-rule
+//           factor) written as a BF16 K-major operand in shared memory ->
+//           acc += H psi (TMEM).  dphi = acc - rowsum(H) phi (L2, L2^2), acc
+//           (dot), or the tangent projection of acc (cos).  The "column pass"
+//           is the same kernel with the roles of phi and psi (and of r and c)
+//           exchanged.  Both write their result as BF16 dy [B][R] and dy^T
+//           [R][B], the layout the encoder backward consumes.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "energy_tc.cuh"
+#include "tc_common.cuh"
+#include "tc_host.h"
+#include "trace.h"
+
+namespace crl {
+
+using bf16 = __nv_bfloat16;
+
+namespace {
+
+constexpr int kTile = 128;
+
+struct Weights {
+  float wf, wb, pr, pc;
+};
+
+Weights loss_weights(const LossSpec& ls) {
+  Weights w{0, 0, 0, 0};
+  if (ls.loss == CRL_LOSS_FWD) w.wf = 1;
+  else if (ls.loss == CRL_LOSS_BWD) w.wb = 1;
+  else w.wf = w.wb = (ls.sym_reduction == CRL_SYM_SUM) ? 1.f : 0.5f;
+  if (ls.penalty_axis == CRL_PENALTY_ROW) w.pr = 1;
+  else if (ls.penalty_axis == CRL_PENALTY_COL) w.pc = 1;
+  else w.pr = w.pc = 0.5f;
+  return w;
+}
+
+__device__ __forceinline__ float energy_of(int energy, float s, float ax, float ay, float inv_tau) {
+  switch (energy) {
+    case CRL_ENERGY_L2: return -sqrtf(fmaxf(ax + ay - 2.f * s, 0.f)) * inv_tau;
+    case CRL_ENERGY_L2SQ: return -fmaxf(ax + ay - 2.f * s, 0.f) * inv_tau;
+    default: return s * inv_tau;  // dot, cos (normalised operands)
+  }
+}
+
+// ---- representation preparation ------------------------------------------------
+// y [B][R] FP32 -> X [B][R] BF16 (normalised for cos), X^T [R][ldt] BF16, aux [B].
+// Block = 32 rows, one warp per row; the transposed copy goes through a shared tile.
+__global__ void __launch_bounds__(1024) prep_kernel(int B, int R, int energy, const float* __restrict__ y,
+                                                   bf16* __restrict__ X, bf16* __restrict__ XT, int ldt,
+                                                   float* __restrict__ aux) {
+  __shared__ float tile[32][33];
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int row = blockIdx.x * 32 + w;
+  float scale = 1.f;
+  if (row < B) {
+    const float* yr = y + (size_t)row * R;
+    float q = 0.f;
+    for (int c = lane; c < R; c += 32) {
+      const float v = yr[c];
+      if (energy == CRL_ENERGY_COS) {
+        q += v * v;
+      } else {
+        const float b = __bfloat162float(__float2bfloat16_rn(v));
+        q += b * b;
+      }
+    }
+    q = warp_sum(q);
+    if (energy == CRL_ENERGY_COS) scale = rsqrtf(q);
+    if (lane == 0) aux[row] = (energy == CRL_ENERGY_COS) ? scale : q;
+  }
+  for (int c0 = 0; c0 < R; c0 += 32) {
+    const int c = c0 + lane;
+    float v = 0.f;
+    if (row < B && c < R) {
+      v = y[(size_t)row * R + c] * scale;
+      X[(size_t)row * R + c] = __float2bfloat16_rn(v);
+    }
+    tile[w][lane] = v;
+    __syncthreads();
+    const int cc = c0 + w, rr = blockIdx.x * 32 + lane;
+    if (cc < R && rr < B) XT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
+    __syncthreads();
+  }
+}
+
+// ---- forward ----------------------------------------------------------------------
+// 512 threads: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows) and handles
+// columns 32 (w / 4) .. + 31 of the 128-wide tile.
+constexpr int kThreads = 512;
+
+struct FwdArgs {
+  int B, R, energy;
+  float inv_tau;
+  const float* auxX;
+  const float* auxY;
+  float* rowpart;  // [nJ][B][2]
+  float* colpart;  // [nI][B][2]
+  float* diag;     // [B]
+  unsigned* status;
+};
+
+__device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2) {
+  if (s2 <= 0.f) return;
+  if (s <= 0.f) {
+    m = m2;
+    s = s2;
+    return;
+  }
+  const float M = fmaxf(m, m2);
+  s = s * __expf(m - M) + s2 * __expf(m2 - M);
+  m = M;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmY, FwdArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = tc::align1024(smem_raw);
+  const int nk = a.R / 64;
+  uint8_t* Xs = smem;
+  uint8_t* Ys = smem + nk * 16384;
+  float* Ft = reinterpret_cast<float*>(smem);  // reused after the MMA: [128][129]
+  const size_t opnd = (size_t)2 * nk * 16384, ftile = (size_t)kTile * 129 * 4;
+  float* part = reinterpret_cast<float*>(smem + (opnd > ftile ? opnd : ftile));  // [2][4][128] (m, s)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(part + 2 * 4 * kTile);
+  uint64_t* load_bar = bars;
+  uint64_t* mma_bar = bars + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int lg = warp % 4, q = warp / 4;
+  const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
+  if (tid == 0) {
+    tc::prefetch_tmap(&tmX);
+    tc::prefetch_tmap(&tmY);
+    tc::mbar_init(load_bar, 1);
+    tc::mbar_init(mma_bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, 128);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (tid == 0) {
+    tc::mbar_arrive_expect_tx(load_bar, (uint32_t)(2 * nk * 16384));
+    for (int kb = 0; kb < nk; ++kb)
+      for (int r = 0; r < 2; ++r) {
+        tc::tma_load_2d(Xs + kb * 16384 + r * 8192, &tmX, load_bar, kb * 64, i0 + 64 * r);
+        tc::tma_load_2d(Ys + kb * 16384 + r * 8192, &tmY, load_bar, kb * 64, j0 + 64 * r);
+      }
+  } else if (tid == 32) {
+    if (tc::mbar_wait(load_bar, 0)) {
+      tc::fence_after_sync();
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+      for (int kb = 0; kb < nk; ++kb) {
+        const uint64_t dx = tc::sdesc_kmajor_sw128(Xs + kb * 16384);
+        const uint64_t dy = tc::sdesc_kmajor_sw128(Ys + kb * 16384);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
+      }
+      tc::mma_commit(mma_bar);
+    } else {
+      atomicOr(a.status, CRL_STATUS_TIMEOUT);
+    }
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(mma_bar, 0) ? 1 : 0) != 0;
+  tc::fence_after_sync();
+  // every warp must agree before the operand smem is reused for the F tile
+  const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  const int r = lg * 32 + lane;  // row of this thread within the tile
+  if (all_ok) {
+    const int i = i0 + r;
+    const float ax = (i < a.B) ? a.auxX[i] : 0.f;
+    float v[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + q * 32, v);
+    float m = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const int j = j0 + q * 32 + k;
+      float f = -INFINITY;
+      if (i < a.B && j < a.B) {
+        f = energy_of(a.energy, v[k], ax, a.auxY[j], a.inv_tau);
+        if (i == j) a.diag[i] = f;
+      }
+      v[k] = f;
+      Ft[r * 129 + q * 32 + k] = f;
+      m = fmaxf(m, f);
+    }
+    float sum = 0.f;
+    if (m > -INFINITY) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) sum += __expf(v[k] - m);
+    }
+    part[(0 * 4 + q) * kTile + r] = m;
+    part[(1 * 4 + q) * kTile + r] = sum;
+  } else if (tid == 0) {
+    atomicOr(a.status, CRL_STATUS_TIMEOUT);
+  }
+  __syncthreads();
+  if (all_ok) {
+    if (tid < kTile) {
+      // merge the four column-group partials of row tid
+      const int i = i0 + tid;
+      float m = part[tid], s = part[4 * kTile + tid];
+      for (int g = 1; g < 4; ++g) lse_merge(m, s, part[g * kTile + tid], part[(4 + g) * kTile + tid]);
+      if (i < a.B) {
+        float* rp = a.rowpart + ((size_t)blockIdx.x * a.B + i) * 2;
+        rp[0] = m;
+        rp[1] = s;
+      }
+    }
+  }
+  __syncthreads();
+  if (all_ok) {
+    // column partials: thread (column c, row group g) over rows 32 g .. 32 g + 31
+    const int c = tid % kTile, g = tid / kTile;
+    float m = -INFINITY;
+    for (int rr = 0; rr < 32; ++rr) m = fmaxf(m, Ft[(32 * g + rr) * 129 + c]);
+    float sum = 0.f;
+    if (m > -INFINITY)
+      for (int rr = 0; rr < 32; ++rr) sum += __expf(Ft[(32 * g + rr) * 129 + c] - m);
+    part[g * kTile + c] = m;
+    part[(4 + g) * kTile + c] = sum;
+  }
+  __syncthreads();
+  if (all_ok && tid < kTile) {
+    const int j = j0 + tid;
+    float m = part[tid], s = part[4 * kTile + tid];
+    for (int g = 1; g < 4; ++g) lse_merge(m, s, part[g * kTile + tid], part[(4 + g) * kTile + tid]);
+    if (j < a.B) {
+      float* cp = a.colpart + ((size_t)blockIdx.y * a.B + j) * 2;
+      cp[0] = m;
+      cp[1] = s;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// Merge the partials, compute r, c and the loss parts.  One block.
+__global__ void __launch_bounds__(1024) finalize_kernel(int B, int nI, int nJ, const float* __restrict__ rowpart,
+                                                       const float* __restrict__ colpart,
+                                                       const float* __restrict__ diag, Weights w, float beta,
+                                                       float* __restrict__ r_out, float* __restrict__ c_out,
+                                                       float* __restrict__ loss4, unsigned* status, int* t_bump) {
+  __shared__ float sm[32];
+  float af = 0.f, ab = 0.f, ar2 = 0.f, ac2 = 0.f;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    float m = -INFINITY, s = 0.f;
+    for (int J = 0; J < nJ; ++J) {
+      const float* p = rowpart + ((size_t)J * B + i) * 2;
+      lse_merge(m, s, p[0], p[1]);
+    }
+    const float r = m + __logf(s);
+    m = -INFINITY;
+    s = 0.f;
+    for (int I = 0; I < nI; ++I) {
+      const float* p = colpart + ((size_t)I * B + i) * 2;
+      lse_merge(m, s, p[0], p[1]);
+    }
+    const float c = m + __logf(s);
+    r_out[i] = r;
+    c_out[i] = c;
+    af += r - diag[i];
+    ab += c - diag[i];
+    ar2 += r * r;
+    ac2 += c * c;
+  }
+  af = block_sum(af, sm);
+  ab = block_sum(ab, sm);
+  ar2 = block_sum(ar2, sm);
+  ac2 = block_sum(ac2, sm);
+  if (threadIdx.x == 0) {
+    const float inv = 1.f / B;
+    const float lf = af * inv, lb = ab * inv;
+    const float pen = beta * (w.pr * ar2 * inv + w.pc * ac2 * inv);
+    const float total = w.wf * lf + w.wb * lb + pen;
+    loss4[0] = total;
+    loss4[1] = lf;
+    loss4[2] = lb;
+    loss4[3] = pen;
+    if (status && !isfinite(total)) atomicOr(status, CRL_STATUS_NONFINITE);
+    if (t_bump) *t_bump += 1;
+  }
+}
+
+// ---- backward ---------------------------------------------------------------------
+struct BwdArgs {
+  int B, R, energy, transposed;  // transposed: own = psi (the column pass)
+  float inv_tau, beta, scale;    // scale = dtotal / B
+  Weights w;
+  const float* aux_own;
+  const float* aux_other;
+  const float* lse_own;    // r (row pass) or c (column pass)
+  const float* lse_other;  // c (row pass) or r (column pass)
+  const float* own_f32;    // [B][R] FP32 representation (cos: unnormalised)
+  bf16* d_out;             // [B][R]
+  bf16* d_outT;            // [R][ldt]
+  int ldt;
+  unsigned* status;
+};
+
+// Offset in a 128-byte-swizzled K-major tile (8-row groups of 1024 bytes) of
+// the 16-byte chunk `chunk` (8 BF16 along K) of row `row`.
+__device__ __forceinline__ uint32_t sw128_offset(int row, int chunk) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+// Per iteration (128 columns of the other side): the other tile arrives
+// (TMA), S = own other^T (MMA), then while other^T is loaded into the same
+// shared region, the 16 warps turn S into the BF16 coefficient tile H (warp w:
+// rows 32 (w % 4) .., columns 32 (w / 4) ..), and the MMA adds H other into
+// the TMEM accumulator.
+__global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant__ CUtensorMap tmOwn,
+                                                          const __grid_constant__ CUtensorMap tmOther,
+                                                          const __grid_constant__ CUtensorMap tmOtherT, BwdArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = tc::align1024(smem_raw);
+  const int nk = a.R / 64;
+  uint8_t* Xs = smem;                                  // own tile                 nk x 16 KiB
+  uint8_t* Ys = Xs + nk * 16384;                       // other tile, then other^T  max(nk x 16 KiB, 2 R 128 B)
+  const int ybytes = (nk * 16384 > 2 * a.R * 128) ? nk * 16384 : 2 * a.R * 128;
+  uint8_t* Hs = Ys + ybytes;                           // H tile                   2 x 16 KiB
+  float* s_lse = reinterpret_cast<float*>(Hs + 2 * 16384);  // [128] column logsumexp of the other side
+  float* s_aux = s_lse + kTile;                             // [128]
+  float* s_red = s_aux + kTile;                             // [4][128] partial sums
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_red + 4 * kTile);
+  uint64_t* xload = bars;
+  uint64_t* yload = bars + 1;
+  uint64_t* ytload = bars + 2;
+  uint64_t* s_done = bars + 3;
+  uint64_t* h_done = bars + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
+  const uint32_t tcols = (128 + a.R <= 256) ? 256u : 512u;
+
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int lg = warp % 4, q = warp / 4;
+  const int r = lg * 32 + lane;  // row of this thread within the tile
+  const int u0 = blockIdx.x * kTile;
+  const int nV = (a.B + kTile - 1) / kTile;
+  if (tid == 0) {
+    tc::prefetch_tmap(&tmOwn);
+    tc::prefetch_tmap(&tmOther);
+    tc::prefetch_tmap(&tmOtherT);
+    tc::mbar_init(xload, 1);
+    tc::mbar_init(yload, 1);
+    tc::mbar_init(ytload, 1);
+    tc::mbar_init(s_done, 1);
+    tc::mbar_init(h_done, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, tcols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tS = tmem, tAcc = tmem + 128;
+  const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
+
+  if (tid == 0) {
+    tc::mbar_arrive_expect_tx(xload, (uint32_t)(nk * 16384));
+    for (int kb = 0; kb < nk; ++kb)
+      for (int rr = 0; rr < 2; ++rr)
+        tc::tma_load_2d(Xs + kb * 16384 + rr * 8192, &tmOwn, xload, kb * 64, u0 + 64 * rr);
+  }
+
+  const int u = u0 + r;
+  const float a_own = (u < a.B) ? a.aux_own[u] : 0.f;
+  const float l_own = (u < a.B) ? a.lse_own[u] : 0.f;
+  float rowsum = 0.f;
+  bool ok = true;
+  for (int vt = 0; vt < nV && ok; ++vt) {
+    const int v0 = vt * kTile;
+    // the previous iteration's MMAs must be done with Ys (other^T) and Hs
+    if (vt > 0) ok = tc::mbar_wait(h_done, (vt - 1) & 1);
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (!ok) break;
+    if (tid < kTile) {
+      const int v = v0 + tid;
+      s_lse[tid] = (v < a.B) ? a.lse_other[v] : 0.f;
+      s_aux[tid] = (v < a.B) ? a.aux_other[v] : 0.f;
+    }
+    if (tid == 0) {
+      tc::mbar_arrive_expect_tx(yload, (uint32_t)(nk * 16384));
+      for (int kb = 0; kb < nk; ++kb)
+        for (int rr = 0; rr < 2; ++rr)
+          tc::tma_load_2d(Ys + kb * 16384 + rr * 8192, &tmOther, yload, kb * 64, v0 + 64 * rr);
+    } else if (tid == 32) {
+      bool good = (vt > 0) || tc::mbar_wait(xload, 0);
+      good = good && tc::mbar_wait(yload, vt & 1);
+      if (good) {
+        tc::fence_after_sync();
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+        for (int kb = 0; kb < nk; ++kb) {
+          const uint64_t dx = tc::sdesc_kmajor_sw128(Xs + kb * 16384);
+          const uint64_t dy = tc::sdesc_kmajor_sw128(Ys + kb * 16384);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) tc::mma_bf16(tS, dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
+        }
+        tc::mma_commit(s_done);
+      } else {
+        atomicOr(a.status, CRL_STATUS_TIMEOUT);
+      }
+    }
+    __syncwarp();
+    ok = __all_sync(0xffffffffu, tc::mbar_wait(s_done, vt & 1) ? 1 : 0) != 0;
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (!ok) break;
+    tc::fence_after_sync();
+    if (tid == 0) {
+      // S is done with the other tile: bring in other^T (2 K-blocks over v, R rows) in its place
+      tc::mbar_arrive_expect_tx(ytload, (uint32_t)(2 * a.R * 128));
+      for (int kb = 0; kb < 2; ++kb)
+        for (int qq = 0; qq < a.R / 64; ++qq)
+          tc::tma_load_2d(Ys + kb * a.R * 128 + qq * 8192, &tmOtherT, ytload, v0 + 64 * kb, 64 * qq);
+    }
+    // coefficient tile H: this thread's row r, columns 32 q .. 32 q + 31
+    {
+      float sv[32];
+      tc::tmem_ld32(tS + lane_off + q * 32, sv);
+      uint32_t packed[16];
+#pragma unroll
+      for (int k = 0; k < 32; k += 2) {
+        float h2[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int cl = q * 32 + k + e;
+          const int v = v0 + cl;
+          float h = 0.f;
+          if (u < a.B && v < a.B) {
+            const float ao = s_aux[cl];
+            const float f = energy_of(a.energy, sv[k + e], a_own, ao, a.inv_tau);
+            const float lr = a.transposed ? s_lse[cl] : l_own;   // row logsumexp r_i
+            const float lc = a.transposed ? l_own : s_lse[cl];   // column logsumexp c_j
+            const float P = __expf(f - lr), Q = __expf(f - lc);
+            const float dl = (u == v) ? 1.f : 0.f;
+            float g = a.w.wf * (P - dl) + a.w.wb * (Q - dl) + 2.f * a.beta * (a.w.pr * lr * P + a.w.pc * lc * Q);
+            g *= a.scale;
+            if (a.energy == CRL_ENERGY_L2) {
+              const float d = sqrtf(fmaxf(a_own + ao - 2.f * sv[k + e], 0.f));
+              h = (d >= 1e-12f) ? g * a.inv_tau / d : 0.f;
+            } else if (a.energy == CRL_ENERGY_L2SQ) {
+              h = 2.f * g * a.inv_tau;
+            } else {
+              h = g * a.inv_tau;
+            }
+          }
+          h2[e] = h;
+        }
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn(h2[0], h2[1]);
+        // the row sum takes the BF16-rounded coefficients the MMA multiplies, so
+        // acc - rowsum * own stays a sum of H (other - own) terms
+        rowsum += __low2float(p2) + __high2float(p2);
+        packed[k / 2] = *reinterpret_cast<const uint32_t*>(&p2);
+      }
+      // columns 32 q .. +31 = K-block q / 2, 16-byte chunks (q % 2) * 4 .. +3
+      uint8_t* hb = Hs + (q / 2) * 16384;
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const uint4 val = make_uint4(packed[4 * c4], packed[4 * c4 + 1], packed[4 * c4 + 2], packed[4 * c4 + 3]);
+        *reinterpret_cast<uint4*>(hb + sw128_offset(r, (q % 2) * 4 + c4)) = val;
+      }
+    }
+    // make the generic-proxy H writes visible to the tensor core, then acc += H other
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 32) {
+      tc::fence_after_sync();
+      if (tc::mbar_wait(ytload, vt & 1)) {
+        const uint32_t idesc = tc::idesc_bf16_f32(128, a.R);
+        for (int kb = 0; kb < 2; ++kb) {
+          const uint64_t dh = tc::sdesc_kmajor_sw128(Hs + kb * 16384);
+          const uint64_t dt = tc::sdesc_kmajor_sw128(Ys + kb * a.R * 128);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) tc::mma_bf16(tAcc, dh + 2 * k, dt + 2 * k, idesc, (vt | kb | k) ? 1u : 0u);
+        }
+        tc::mma_commit(h_done);
+      } else {
+        atomicOr(a.status, CRL_STATUS_TIMEOUT);
+      }
+    }
+    __syncwarp();
+  }
+  if (ok) ok = __all_sync(0xffffffffu, tc::mbar_wait(h_done, (nV - 1) & 1) ? 1 : 0) != 0;
+  // row sums of the four column groups
+  s_red[q * kTile + r] = rowsum;
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  tc::fence_after_sync();
+  if (ok) {
+    const float rs = s_red[r] + s_red[kTile + r] + s_red[2 * kTile + r] + s_red[3 * kTile + r];
+    const float* own = a.own_f32 + (size_t)(u < a.B ? u : 0) * a.R;
+    float proj = 0.f;
+    if (a.energy == CRL_ENERGY_COS) {
+      // <x_hat, acc> over all R columns: partial per column group, then combined
+      float pp = 0.f;
+      for (int c = q * 32; c < a.R; c += 128) {
+        float v[32];
+        tc::tmem_ld32(tAcc + lane_off + c, v);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) pp += own[c + k] * a_own * v[k];
+      }
+      __syncthreads();
+      s_red[q * kTile + r] = pp;
+      __syncthreads();
+      proj = s_red[r] + s_red[kTile + r] + s_red[2 * kTile + r] + s_red[3 * kTile + r];
+    }
+    for (int c = q * 32; c < a.R; c += 128) {
+      float v[32];
+      tc::tmem_ld32(tAcc + lane_off + c, v);
+      if (u < a.B) {
+        alignas(16) bf16 o[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          float d = v[k];
+          if (a.energy == CRL_ENERGY_L2 || a.energy == CRL_ENERGY_L2SQ) d -= rs * own[c + k];
+          else if (a.energy == CRL_ENERGY_COS) d = (d - own[c + k] * a_own * proj) * a_own;
+          o[k] = __float2bfloat16_rn(d);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(a.d_out + (size_t)u * a.R + c);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4*>(o)[k];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) a.d_outT[(size_t)(c + k) * a.ldt + u] = o[k];
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(a.status, CRL_STATUS_TIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, tcols);
+}
+
+size_t fwd_smem(int R) {
+  const size_t opnd = (size_t)2 * (R / 64) * 16384, ftile = (size_t)kTile * 129 * 4;
+  return (opnd > ftile ? opnd : ftile) + 2 * 4 * kTile * 4 + 1024 + 64;
+}
+size_t bwd_smem(int R) {
+  const size_t ybytes = std::max<size_t>((size_t)(R / 64) * 16384, (size_t)2 * R * 128);
+  return (size_t)(R / 64) * 16384 + ybytes + 2 * 16384 + (2 + 4) * kTile * 4 + 1024 + 64;
+}
+
+const char* mk(CUtensorMap* m, const void* base, int inner, int rows, int stride) {
+  const char* err = nullptr;
+  if (!tc::make_tmap_bf16(m, base, (uint64_t)inner, (uint64_t)rows, (uint64_t)stride, 64, &err)) return err;
+  return nullptr;
+}
+
+}  // namespace
+
+size_t energy_tc_ws_bytes(int B) {
+  const int n = (B + kTile - 1) / kTile;
+  return ((size_t)2 * n * B * 2 + B) * sizeof(float) + 256;
+}
+
+bool energy_tc_supported(const LossSpec& ls, int B, int R, const char** why) {
+  if (ls.energy == CRL_ENERGY_L1) {
+    *why = "the fused path has no L1 energy";
+    return false;
+  }
+  if (R % 64 != 0 || R > 256) {
+    *why = "the fused path needs repr to be 64, 128, 192 or 256";
+    return false;
+  }
+  if (B % 8 != 0) {
+    *why = "the fused path needs B to be a multiple of 8";
+    return false;
+  }
+  return true;
+}
+
+const char* energy_tc_maps(EnergyTc& e, int B) {
+  if (e.tm_B == B) return nullptr;
+  const char* err;
+  if ((err = mk(&e.tmX, e.X, e.R, B, e.R))) return err;
+  if ((err = mk(&e.tmY, e.Y, e.R, B, e.R))) return err;
+  if ((err = mk(&e.tmXT, e.XT, B, e.R, e.ldt))) return err;
+  if ((err = mk(&e.tmYT, e.YT, B, e.R, e.ldt))) return err;
+  e.tm_B = B;
+  return nullptr;
+}
+
+void energy_tc_prepare(EnergyTc& e, const LossSpec& ls, const float* phi, const float* psi, int B, cudaStream_t st) {
+  TraceLaunch tr(CRL_TRACE_ENERGY, st, 0.0);
+  prep_kernel<<<ceil_div(B, 32), 1024, 0, st>>>(B, e.R, ls.energy, phi, e.X, e.XT, e.ldt, e.auxX);
+  prep_kernel<<<ceil_div(B, 32), 1024, 0, st>>>(B, e.R, ls.energy, psi, e.Y, e.YT, e.ldt, e.auxY);
+}
+
+void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, float* r, float* c, void* ws,
+                       unsigned* status, int* t_bump, cudaStream_t st) {
+  const int n = (B + kTile - 1) / kTile;
+  float* rowpart = static_cast<float*>(ws);
+  float* colpart = rowpart + (size_t)2 * n * B;
+  float* diag = colpart + (size_t)2 * n * B;
+  FwdArgs a{B, e.R, ls.energy, (float)(1.0 / ls.tau), e.auxX, e.auxY, rowpart, colpart, diag, status};
+  const size_t sm = fwd_smem(e.R);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
+    attr = true;
+  }
+  {
+    TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * B * e.R);
+    fwd_kernel<<<dim3(n, n), kThreads, sm, st>>>(e.tmX, e.tmY, a);
+  }
+  TraceLaunch tr(CRL_TRACE_ENERGY, st, 0.0);
+  finalize_kernel<<<1, 1024, 0, st>>>(B, n, n, rowpart, colpart, diag, loss_weights(ls), (float)ls.beta, r, c, loss4,
+                                      status, t_bump);
+}
+
+void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
+                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dphiT,
+                        __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, unsigned* status, cudaStream_t st) {
+  const int n = (B + kTile - 1) / kTile;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(256));
+    attr = true;
+  }
+  const size_t sm = bwd_smem(e.R);
+  BwdArgs a{B, e.R, ls.energy, 0, (float)(1.0 / ls.tau), (float)ls.beta, (float)(dtotal / B), loss_weights(ls),
+            e.auxX, e.auxY, r, c, phi, dphi, dphiT, ldt, status};
+  {
+    TraceLaunch tr(CRL_TRACE_ENERGY, st, 4.0 * B * B * e.R);
+    bwd_kernel<<<n, kThreads, sm, st>>>(e.tmX, e.tmY, e.tmYT, a);
+  }
+  BwdArgs b = a;
+  b.transposed = 1;
+  b.aux_own = e.auxY;
+  b.aux_other = e.auxX;
+  b.lse_own = c;
+  b.lse_other = r;
+  b.own_f32 = psi;
+  b.d_out = dpsi;
+  b.d_outT = dpsiT;
+  TraceLaunch tr(CRL_TRACE_ENERGY, st, 4.0 * B * B * e.R);
+  bwd_kernel<<<n, kThreads, sm, st>>>(e.tmY, e.tmX, e.tmXT, b);
+}
+
+}  // namespace crl

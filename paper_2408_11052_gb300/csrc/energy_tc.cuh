@@ -1,0 +1,33 @@
+// Fused tcgen05 energy + InfoNCE + logsumexp penalty (see energy_tc.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace crl {
+
+// BF16 operands and per-row auxiliaries of the fused energy stage for batches up to Bmax.
+struct EnergyTc {
+  int R = 0, Bmax = 0, ldt = 0;
+  __nv_bfloat16 *X = nullptr, *XT = nullptr, *Y = nullptr, *YT = nullptr;  // [Bmax][R], [R][Bmax]
+  float *auxX = nullptr, *auxY = nullptr;                                    // [Bmax]
+  CUtensorMap tmX, tmY, tmXT, tmYT;
+  int tm_B = -1;
+};
+
+bool energy_tc_supported(const LossSpec& ls, int B, int R, const char** why);
+size_t energy_tc_ws_bytes(int B);
+const char* energy_tc_maps(EnergyTc& e, int B);
+// phi, psi [B][R] FP32 -> BF16 operands, transposes and auxiliaries.
+void energy_tc_prepare(EnergyTc& e, const LossSpec& ls, const float* phi, const float* psi, int B, cudaStream_t st);
+// loss4 = {total, fwd, bwd, penalty}; r, c = row / column logsumexp.  ws: energy_tc_ws_bytes(B).
+void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, float* r, float* c, void* ws,
+                       unsigned* status, int* t_bump, cudaStream_t st);
+// dphi / dpsi as BF16 [B][R] and transposed [R][ldt] (the encoders' dy layout), scaled by dtotal.
+void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
+                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dphiT,
+                        __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, unsigned* status, cudaStream_t st);
+
+}  // namespace crl

@@ -5,9 +5,6 @@
 // A and B are read through small loader functors, so one kernel serves
 // x W^T (forward), dY W (input gradient), dY^T X (weight gradient) and the
 // energy matrices (op = product, squared difference or absolute difference).
-// 64 x 64 output tile, 16-deep k slices staged in shared memory, 256 threads,
-// 4 x 4 outputs per thread strided by 16 so that shared-memory reads are
-// conflict free.
 #pragma once
 
 #include "common.cuh"
@@ -25,71 +22,115 @@ __device__ __forceinline__ T inner(T a, T b) {
   else return fabs(a - b);
 }
 
-template <typename T, InnerOp OP, class LA, class LB, class EP>
+// Tile BM x BN (64 x 64 or 32 x 32), 32-deep k slices, 256 threads, each
+// thread TM x TN outputs strided by 16 rows / columns (conflict-free shared
+// reads).  The next slice is prefetched into registers while the current one
+// is multiplied out of the other shared-memory buffer, so each slice costs one
+// barrier and the global-load latency overlaps the arithmetic.
+template <typename T, InnerOp OP, int BM, int BN, class LA, class LB, class EP>
 __global__ void __launch_bounds__(256) gemm_tile_kernel(int M, int N, int K, LA la, LB lb, EP ep) {
-  constexpr int BM = 64, BN = 64, BK = 16;
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
+  constexpr int BK = 32;
+  constexpr int TM = BM / 16, TN = BN / 16;
+  constexpr int LDA = BM * BK / 256, LDB = BN * BK / 256;  // elements each thread loads per slice
+  __shared__ T As[2][BK][BM + 1];
+  __shared__ T Bs[2][BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  T acc[4][4];
+  T acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
-  for (int k0 = 0; k0 < K; k0 += BK) {
+  T ra[LDA], rb[LDB];
+  auto load = [&](int k0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < LDA; ++r) {
       const int e = tid + r * 256;
       int mm, kk;
       if constexpr (LA::kContigK) { kk = e % BK; mm = e / BK; }
       else { mm = e % BM; kk = e / BM; }
       const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < K) ? la(m, k) : T(0);
+      ra[r] = (m < M && k < K) ? la(m, k) : T(0);
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < LDB; ++r) {
       const int e = tid + r * 256;
       int nn, kk;
       if constexpr (LB::kContigK) { kk = e % BK; nn = e / BK; }
       else { nn = e % BN; kk = e / BN; }
       const int n = n0 + nn, k = k0 + kk;
-      Bs[kk][nn] = (n < N && k < K) ? lb(k, n) : T(0);
+      rb[r] = (n < N && k < K) ? lb(k, n) : T(0);
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < LDA; ++r) {
+      const int e = tid + r * 256;
+      int mm, kk;
+      if constexpr (LA::kContigK) { kk = e % BK; mm = e / BK; }
+      else { mm = e % BM; kk = e / BM; }
+      As[buf][kk][mm] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < LDB; ++r) {
+      const int e = tid + r * 256;
+      int nn, kk;
+      if constexpr (LB::kContigK) { kk = e % BK; nn = e / BK; }
+      else { nn = e % BN; kk = e / BN; }
+      Bs[buf][kk][nn] = rb[r];
+    }
+  };
+
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const bool more = k0 + BK < K;
+    if (more) load(k0 + BK);
     // Padded k entries are zero on both sides, so they add 0 for every inner op.
-#pragma unroll
+#pragma unroll 8
     for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+      T a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += inner<T, OP>(a[i], b[j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] += inner<T, OP>(a[i], b[j]);
     }
+    if (more) store(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
       if (m < M && n < N) ep(m, n, acc[i][j]);
     }
 }
 
-// Launch; traced as class `cls` (CRL_TRACE_*) with 2 M N K flops of work.
+// Launch; traced as class `cls` (CRL_TRACE_*) with 2 M N K flops of work.  The
+// 32 x 32 tile is used when 64 x 64 tiles would leave most of the 152 SMs idle.
 template <typename T, InnerOp OP = InnerOp::kMul, class LA, class LB, class EP>
 void gemm(int M, int N, int K, const LA& la, const LB& lb, const EP& ep, cudaStream_t st, int cls = CRL_TRACE_GEMM) {
   if (M <= 0 || N <= 0) return;
   TraceLaunch tr(cls, st, 2.0 * M * N * K);
-  dim3 grid(ceil_div(N, 64), ceil_div(M, 64));
-  gemm_tile_kernel<T, OP, LA, LB, EP><<<grid, 256, 0, st>>>(M, N, K, la, lb, ep);
+  const long long tiles64 = (long long)ceil_div(N, 64) * ceil_div(M, 64);
+  // FP64 always takes the 32 x 32 tile: its 64 x 64 double buffers exceed 48 KiB of static shared memory.
+  if (sizeof(T) == 8 || tiles64 < 2 * 152) {
+    dim3 grid(ceil_div(N, 32), ceil_div(M, 32));
+    gemm_tile_kernel<T, OP, 32, 32, LA, LB, EP><<<grid, 256, 0, st>>>(M, N, K, la, lb, ep);
+  } else if constexpr (sizeof(T) == 4) {
+    dim3 grid(ceil_div(N, 64), ceil_div(M, 64));
+    gemm_tile_kernel<T, OP, 64, 64, LA, LB, EP><<<grid, 256, 0, st>>>(M, N, K, la, lb, ep);
+  }
 }
 
 // ---- loaders ---------------------------------------------------------------

@@ -24,6 +24,17 @@ struct BufferDev {
   int E, T, D, A, W;
 };
 
+// Optional BF16 packing of a network input by the relabel kernel: the split
+// (hi, lo) interleaved row-major copy x0 [Mmax][ld] and its transpose x0T
+// [2 in][ldt] (see mlp_bf16.cuh).  Source columns: kind 0 = concat(s, a),
+// 1 = g, 2 = concat(s, g).
+struct RelabelPack {
+  void* x0;
+  int ld;
+  void* x0T;
+  int ldt;
+};
+
 struct RelabelArgs {
   uint64_t seed, agent;
   uint64_t step;                    // CRL_STEP_AUTO: read *step_dev
@@ -34,6 +45,7 @@ struct RelabelArgs {
   float *s, *a, *g;                 // [B][D], [B][A], [B][G]
   int32_t* idx;                     // [B][3] or null
   unsigned* status;                 // device status word
+  RelabelPack pack[3];              // phi (s, a), psi (g), pi (s, g); x0 == null: not written
 };
 
 void launch_buffer_insert(const BufferDev& bd, const float* obs, const float* act, const uint8_t* done,

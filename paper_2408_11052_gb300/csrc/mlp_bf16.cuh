@@ -1,0 +1,109 @@
+// BF16 tensor-core MLP (encoders phi, psi and the policy pi): buffers and entry points.
+//
+// Every product is a "TN" GEMM on tcgen05 (both operands K-major, BF16 in,
+// FP32 accumulate in TMEM):
+//   forward      z_l  = h_{l-1} W_l^T          A = h_{l-1} [M][K],    B = W_l  [N][K]
+//   input grad   dh   = dz_l W_l               A = dz_l    [M][N],    B = Wt_l [K][N]
+//   weight grad  dW_l = dz_l^T [h_{l-1} | 1]   A = dz_l^T  [N][M],    B = h^T  [K+1][M]
+// so the forward epilogue writes each activation twice, row-major h [M][H]
+// and transposed h^T [H+1][M], whose last row is all ones: the weight-grad
+// GEMM then returns the bias gradient (sum over the batch) as its last column.
+//
+// The network input (observations, actions, goals: O(1..10) values with a
+// large common component across the batch) is split into a BF16 high part and
+// a BF16 residual, interleaved along K (x0 = [hi_0, lo_0, hi_1, lo_1, ...]),
+// with the first-layer weight shadow duplicated to match ([w_0, w_0, w_1, ...]):
+// the first product then sees the input with ~16 mantissa bits.  Rounding the
+// raw input to plain BF16 was the dominant error of the BF16 path (gradient
+// cosine 0.992 instead of 0.9998 on small batches).
+//
+// Forward products use the weights as a BF16 pair W = W_hi + W_lo (W_lo =
+// bf16(W - W_hi)), stored [W_hi | W_lo] along K; each activation tile meets
+// both halves, doubling the forward tensor work.  Rounding the weights to a
+// single BF16 was the next largest error (first-layer weight-gradient cosine
+// 0.998 on 96-wide networks; 0.9993+ with the pair).  The backward uses single
+// BF16 shadows Wt [in][out] (its rounding hardly moves the gradient).
+// The backward epilogue likewise writes dz and dz^T.  The shadows are refreshed
+// from the FP32 master weights before each step.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace crl {
+
+struct BfLayer {
+  int in, out, in_pad, out_pad;   // pads: multiples of 8 (16-byte rows)
+  int kin;                        // K of the forward product: in, or 2 in for the split first layer
+  int kp;                         // kin rounded up to 64: W_lo starts at column kp
+  int64_t oW, ob, og, obeta;      // offsets into the FP32 master array (og/obeta < 0: no LayerNorm)
+  __nv_bfloat16* W;               // [out][2 kp] = [W_hi | W_lo] (first layer: columns duplicated)
+  __nv_bfloat16* Wt;              // [in][out_pad]
+  CUtensorMap tmW, tmWt;
+};
+
+// One network's BF16 state for batches of up to Mmax rows.
+struct BfNet {
+  MlpShape s;
+  int Mmax = 0;
+  int layers = 0;
+  BfLayer L[CRL_MAX_LAYERS + 1];
+  // activations
+  __nv_bfloat16* x0 = nullptr;    // [Mmax][pad8(2 in)]  split input (hi, lo interleaved)
+  __nv_bfloat16* x0T = nullptr;   // [2 in + 1][Mmax]    transposed, last row ones
+  __nv_bfloat16* h[CRL_MAX_LAYERS] = {};   // [Mmax][H]
+  __nv_bfloat16* hT[CRL_MAX_LAYERS] = {};  // [H + 1][Mmax], last row ones
+  float* z[CRL_MAX_LAYERS] = {};           // LayerNorm: pre-norm [Mmax][H], then zhat in place
+  float* rstd[CRL_MAX_LAYERS] = {};        // LayerNorm: [Mmax]
+  float* y = nullptr;                      // [Mmax][out] output (FP32)
+  // backward
+  __nv_bfloat16* dz[2] = {};               // [Mmax][max(H, out_pad)]
+  __nv_bfloat16* dzT[2] = {};              // [max(H, out)][Mmax]
+  float* du = nullptr;                     // LayerNorm backward input [Mmax][H]
+  // tensor maps, built for the batch size M of the last call
+  int tm_M = -1;
+  CUtensorMap tm_x0A, tm_x0TB;
+  CUtensorMap tm_hA[CRL_MAX_LAYERS], tm_hTB[CRL_MAX_LAYERS];
+  CUtensorMap tm_dzA[2], tm_dzTA[2];
+};
+
+// Allocates the network's BF16 buffers (cudaMalloc through `alloc`) and writes the ones rows.
+// Returns an error message or nullptr.
+using DevAlloc = void* (*)(void* owner, size_t bytes);
+const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner);
+// (Re)build the activation tensor maps for batch M (no-op when M is unchanged).
+const char* bf_net_maps(BfNet& n, int M);
+// Refresh W / Wt shadows from the FP32 master parameters.
+void bf_net_shadow(BfNet& n, const float* params, cudaStream_t st);
+// Row length of x0 (the split input): pad8(2 in).
+int bf_net_x0_ld(const BfNet& n);
+// Pack the FP32 input concat(x0 [M][in0], x1 [M][in1]) into x0 / x0T.
+void bf_net_pack_input(BfNet& n, const float* x0, const float* x1, int M, cudaStream_t st);
+// Forward: y [M][out] FP32 (n.y).  Optionally also writes a BF16 copy of y.
+void bf_net_forward(BfNet& n, const float* params, int M, unsigned* status, cudaStream_t st);
+// Backward from dy (BF16 [M][out_pad] and dy^T [out][M], in n.dz[0] / n.dzT[0]):
+// writes FP32 grads (flat layout) when `grads` is non-null, and the FP32
+// gradient of the input columns [in0, in0 + in1) into dx1 [M][in1] when non-null.
+void bf_net_backward(BfNet& n, const float* params, int M, float* grads, float* dx1, unsigned* status,
+                     cudaStream_t st);
+// Store an FP32 gradient dy [M][out] into n.dz[0] / n.dzT[0] (BF16, both layouts).
+void bf_net_load_dy(BfNet& n, const float* dy, int M, cudaStream_t st);
+
+// Adam on the FP32 master parameters of up to two networks in one launch, also
+// refreshing each network's BF16 shadows (W_hi / W_lo and Wt) from the updated
+// weights.  grads / m / v share the flat layout of params.
+struct AdamShadowNet {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  int64_t n;
+  const int* t_dev;   // Adam step counter (already incremented for this step)
+  float lr;
+  BfNet* net;
+};
+void adam_shadow_update(const AdamShadowNet* nets, int count, float b1, float b2, float eps, cudaStream_t st);
+
+}  // namespace crl

@@ -53,9 +53,10 @@ def to64(nets):
     return {k: [{kk: vv.astype(np.float64) for kk, vv in l.items()} for l in v] for k, v in nets.items()}
 
 
-def setup(w, precision="fp32", n=None, mean_len=9.0, agent=0, offset_min=1, perturb=True, nets=None, **over):
+def setup(w, precision="fp32", n=None, mean_len=9.0, agent=0, offset_min=1, perturb=True, nets=None, path="plain",
+          **over):
     """Context with seeded networks and buffer; the oracle's buffer and networks alongside."""
-    ctx = api.CRLContext(w, precision=precision, agent=agent, offset_min=offset_min, **over)
+    ctx = api.CRLContext(w, precision=precision, path=path, agent=agent, offset_min=offset_min, **over)
     nets = workload.init_agent(w, perturb=perturb) if nets is None else nets
     for k, v in nets.items():
         ctx.load_network(k, v)

@@ -1,0 +1,202 @@
+"""GPU parity of the BF16 tensor-core path (tcgen05 GEMMs, FP32 accumulation) against
+the FP64 oracle: loss relative error <= 2e-2 and gradient cosine >= 0.999 per tensor
+(the BF16 tolerances of the parity contract)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2408_11052_gb300 import workload
+
+from parity_helpers import hp, pick_step, setup, small
+
+pytestmark = pytest.mark.gpu
+
+BF16_LOSS_RTOL = 2e-2
+BF16_GRAD_COS = 0.999
+
+
+def cosine(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    na, nb = np.linalg.norm(a), np.linalg.norm(b)
+    if na == 0 and nb == 0:
+        return 1.0
+    return float(a @ b / (na * nb))
+
+
+def assert_grads_cosine(got_net, ref_net, label):
+    worst = 1.0
+    for li, (g, r) in enumerate(zip(got_net, ref_net)):
+        for k in r:
+            c = cosine(g[k], r[k])
+            worst = min(worst, c)
+            assert c >= BF16_GRAD_COS, f"{label} layer {li} {k}: cosine {c:.6f} < {BF16_GRAD_COS}"
+    return worst
+
+
+def bf16_small(**kw):
+    base = dict(E=6, T=48, D=29, A=8, G=2, B=96, hidden=96, layers=2, repr=24, seed=31)
+    base.update(kw)
+    return workload.Workload("bf16", **base)
+
+
+def run_critic(w, nets=None, n=70, mean_len=9.0):
+    ctx, nets, buf = setup(w, precision="bf16", n=n, mean_len=mean_len, nets=nets)
+    step = pick_step(w, nets, buf, 4)
+    s, a, g, _ = ctx.sample(step=step)
+    loss = ctx.critic_step(s, a, g, apply_update=False).cpu().numpy()
+    torch.cuda.synchronize()
+    s_o, a_o, g_o, _ = oracle.relabel.sample_relabel(buf, w.seed, 0, step, w.B, w.goals(), w.gamma)
+    h = hp(w)
+    ref = oracle.step.critic_loss_and_grad(nets["phi"], nets["psi"], s_o, a_o, g_o, w.energy, h["tau"], w.loss,
+                                           w.sym_reduction, h["beta"], w.penalty_axis)
+    return ctx, loss, ref
+
+
+@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq"])
+@pytest.mark.parametrize("layernorm", [False, True])
+def test_bf16_critic_matches_oracle(energy, layernorm):
+    w = bf16_small(energy=energy, layernorm=layernorm, tau=0.7 if energy == "cos" else 1.0)
+    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w)
+    assert abs(got[0] - parts["total"]) <= BF16_LOSS_RTOL * abs(parts["total"])
+    assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
+    assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
+    assert ctx.sync_status() == (0, 0)
+
+
+@pytest.mark.parametrize("B", [8, 64, 136, 256])
+def test_bf16_critic_batch_sizes(B):
+    w = bf16_small(B=B, hidden=64, repr=16)
+    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w)
+    assert abs(got[0] - parts["total"]) <= BF16_LOSS_RTOL * abs(parts["total"])
+    assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
+    assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
+
+
+def test_bf16_critic_full_size_ant():
+    w = workload.ANT_AUTOGRAD
+    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w, mean_len=None)
+    assert abs(got[0] - parts["total"]) <= BF16_LOSS_RTOL * abs(parts["total"])
+    assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
+    assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
+
+
+def test_bf16_critic_full_size_humanoid():
+    w = workload.HUMANOID_BF16
+    nets = workload.init_agent(w, perturb=True)
+    for net in ("phi", "psi"):
+        for layer in nets[net][:-1]:
+            layer["ln_b"] = layer["ln_b"] + np.float32(4.0)
+    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w, nets=nets, mean_len=None)
+    assert abs(got[0] - parts["total"]) <= BF16_LOSS_RTOL * abs(parts["total"])
+    assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
+    assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
+
+
+@pytest.mark.parametrize("energy", ["l2", "cos"])
+@pytest.mark.parametrize("layernorm", [False, True])
+def test_bf16_actor_matches_oracle(energy, layernorm):
+    w = bf16_small(energy=energy, layernorm=layernorm, tau=0.8)
+    raw = workload.init_agent(w, perturb=True)
+    ctx, nets, buf = setup(w, precision="bf16", n=70, nets=raw)
+    eps = workload.actor_noise(w.B, w.A, 3)
+    step = pick_step(w, nets, buf, 5, eps=eps.astype(np.float64))
+    s, a, g, _ = ctx.sample(step=step)
+    out = ctx.actor_step(s, g, torch.from_numpy(eps).to(ctx.device), apply_update=False).cpu().numpy()
+    s_o, _, g_o, _ = oracle.relabel.sample_relabel(buf, w.seed, 0, step, w.B, w.goals(), w.gamma)
+    h = hp(w)
+    ref = oracle.actor.actor_loss_and_grad(nets["pi"], nets["phi"], nets["psi"], s_o, g_o, eps.astype(np.float64),
+                                           w.energy, h["tau"], h["alpha"])
+    assert abs(out[0] - ref["loss"]) <= BF16_LOSS_RTOL * abs(ref["loss"]) + 1e-3
+    assert_grads_cosine(ctx.network("pi", "grads"), ref["grads"], "pi")
+
+
+def test_bf16_update_steps_track_oracle():
+    w = bf16_small(B=64)
+    ctx, nets, buf = setup(w, precision="bf16", n=60)
+    extra = workload.buffer_contents(w, n=3, mean_len=9.0, seed_offset=99)
+    state = oracle.step.AgentState(nets["phi"], nets["psi"], nets["pi"])
+    h = hp(w)
+    cfg = dict(seed=w.seed, agent=0, B=w.B, goal_idx=w.goals(), gamma=w.gamma, energy=w.energy, tau=h["tau"],
+               loss=w.loss, sym_reduction=w.sym_reduction, beta=h["beta"], penalty_axis=w.penalty_axis,
+               alpha=h["alpha"], lr_critic=h["lr_critic"], lr_actor=h["lr_actor"])
+    loss_out = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+    for i in range(3):
+        ins = tuple(x[i:i + 1] for x in extra)
+        ctx.update_step(*(torch.from_numpy(x).to(ctx.device) for x in ins), loss_out=loss_out)
+        got = loss_out.cpu().numpy()
+        buf.insert(*ins)
+        ref = oracle.step.update_step(state, buf, cfg, i, oracle.actor.gaussian_noise(w.seed, 0, i, w.B, w.A))
+        assert abs(got[0] - ref["critic"]["total"]) <= BF16_LOSS_RTOL * abs(ref["critic"]["total"])
+        assert abs(got[4] - ref["actor_loss"]) <= BF16_LOSS_RTOL * abs(ref["actor_loss"]) + 1e-2
+    assert ctx.sync_status() == (0, 0)
+
+
+# ---- fused tensor-core energy stage (path "fused": the B x B matrix is never written) ----
+
+def run_critic_fused(w, nets=None, n=70, mean_len=9.0, start=4, kink_free=True):
+    ctx, nets, buf = setup(w, precision="bf16", path="fused", n=n, mean_len=mean_len, nets=nets)
+    step = pick_step(w, nets, buf, start) if kink_free else start
+    s, a, g, _ = ctx.sample(step=step)
+    loss = ctx.critic_step(s, a, g, apply_update=False).cpu().numpy()
+    torch.cuda.synchronize()
+    s_o, a_o, g_o, _ = oracle.relabel.sample_relabel(buf, w.seed, 0, step, w.B, w.goals(), w.gamma)
+    h = hp(w)
+    ref = oracle.step.critic_loss_and_grad(nets["phi"], nets["psi"], s_o, a_o, g_o, w.energy, h["tau"], w.loss,
+                                           w.sym_reduction, h["beta"], w.penalty_axis)
+    return ctx, loss, ref
+
+
+def check_fused(ctx, got, ref):
+    parts, gphi, gpsi, _, _ = ref
+    for i, k in enumerate(("total", "fwd", "bwd", "penalty")):
+        assert abs(got[i] - parts[k]) <= BF16_LOSS_RTOL * abs(parts[k]) + 1e-4, (k, got[i], parts[k])
+    assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
+    assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
+    assert ctx.sync_status() == (0, 0)
+
+
+@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq"])
+@pytest.mark.parametrize("loss", ["fwd", "bwd", "sym"])
+def test_fused_critic_matches_oracle(energy, loss):
+    w = bf16_small(energy=energy, loss=loss, repr=64, tau=0.7 if energy == "cos" else 1.0)
+    ctx, got, ref = run_critic_fused(w)
+    check_fused(ctx, got, ref)
+
+
+@pytest.mark.parametrize("B,penalty", [(8, "row"), (136, "col"), (264, "both"), (512, "row")])
+def test_fused_critic_ragged_tiles(B, penalty):
+    w = bf16_small(B=B, repr=128, penalty_axis=penalty)
+    ctx, got, ref = run_critic_fused(w)
+    check_fused(ctx, got, ref)
+
+
+def test_fused_critic_full_size_ant():
+    ctx, got, ref = run_critic_fused(workload.ANT_AUTOGRAD, mean_len=None)
+    check_fused(ctx, got, ref)
+
+
+def test_fused_critic_full_size_humanoid():
+    w = workload.HUMANOID_BF16
+    nets = workload.init_agent(w, perturb=True)
+    for net in ("phi", "psi"):
+        for layer in nets[net][:-1]:
+            layer["ln_b"] = layer["ln_b"] + np.float32(4.0)
+    ctx, got, ref = run_critic_fused(w, nets=nets, mean_len=None)
+    check_fused(ctx, got, ref)
+
+
+def test_fused_critic_full_size_large_batch():
+    """Batch 8192, repr 256, 2 x 512 MLPs, L2 energy, forward InfoNCE (the B x B matrix
+    would be 268 MB in FP32; the fused path never writes it)."""
+    w = workload.LARGE_BATCH
+    # 16.8M hidden units: no batch is kink-free, so the hidden biases are raised by
+    # 4 (every unit ~4 sigma from its kink), as in the Humanoid tests
+    nets = workload.init_agent(w, perturb=True)
+    for net in ("phi", "psi"):
+        for layer in nets[net][:-1]:
+            layer["b"] = layer["b"] + np.float32(4.0)
+    ctx, got, ref = run_critic_fused(w, nets=nets, n=40, mean_len=None, kink_free=False)
+    check_fused(ctx, got, ref)

@@ -125,3 +125,29 @@ def test_tracing_counts_relabel_bytes():
     assert n == 3 and ms > 0
     per = (w.D + w.A + 1 + w.G) * 4 + (w.D + w.A + w.G) * 4 + 12
     assert work == pytest.approx(3 * w.B * per)
+
+
+@pytest.mark.parametrize("precision,path", [("fp32", "plain"), ("bf16", "plain"), ("bf16", "fused")])
+def test_graph_replay_matches_eager(precision, path):
+    """crl_update_step on a side stream (captured once, then replayed as a CUDA graph)
+    gives bit-identical losses and parameters to eager calls on the default stream."""
+    w = small(B=64, repr=64)
+    runs = []
+    for side in (False, True):
+        ctx, _, _ = setup(w, precision=precision, path=path, n=60)
+        extra = workload.buffer_contents(w, n=5, mean_len=9.0, seed_offset=7)
+        torch.cuda.synchronize()                 # the set-up ran on the default stream
+        stream = torch.cuda.Stream() if side else torch.cuda.current_stream()
+        loss = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+        hist = []
+        with torch.cuda.stream(stream):
+            for i in range(5):
+                ins = [torch.from_numpy(x[i:i + 1]).to(ctx.device) for x in extra]
+                ctx.update_step(*ins, loss_out=loss)
+                hist.append(loss.cpu().numpy().copy())
+        torch.cuda.synchronize()
+        runs.append((np.array(hist), {n: ctx.store[n]["params"].cpu().numpy() for n in ("phi", "psi", "pi")}))
+        assert ctx.sync_status() == (0, 0)
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    for n in ("phi", "psi", "pi"):
+        np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
