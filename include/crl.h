@@ -174,7 +174,8 @@ typedef struct crl_net_ptrs {
   void* adam_v;
 } crl_net_ptrs;
 /* Bind the three networks (index CRL_NET_*).  Moments must start at zero for
- * a fresh optimiser.  Resets the Adam step counters to 0. */
+ * a fresh optimiser.  Resets the Adam step counters to 0.  Every array must
+ * start on a 16-byte boundary (CRL_E_INVALID_ARG otherwise). */
 int crl_bind_params(crl_ctx* ctx, const crl_net_ptrs nets[3]);
 
 /* ---- replay buffer (Algorithm 1 "store trajectory"; App. B.3 capacity) -----
@@ -264,6 +265,16 @@ const char* crl_last_error(const crl_ctx* ctx);
 #define CRL_TRACE_AUX 6      /* LayerNorm, reductions, actor head, counters   */
 int crl_trace_start(crl_ctx* ctx, int32_t kernel_class, int32_t max_launches);
 int crl_trace_stop(crl_ctx* ctx, int32_t* launches, double* total_ms, double* work);
+
+/* ---- launch overlap (library extension; the paper has no counterpart) -----
+ * Process-wide.  enable = 1 (the default): every kernel of the library is
+ * launched with programmatic stream serialisation, so it is scheduled while
+ * its predecessor on the stream drains and waits on the device
+ * (griddepcontrol.wait) before it touches memory; results are identical.
+ * enable = 0: plain stream order.  Takes effect for launches made (and CUDA
+ * graphs captured) after the call; a context whose update-step graph was
+ * captured before keeps replaying it.  Returns the previous setting. */
+int32_t crl_set_launch_overlap(int32_t enable);
 
 /* ---- op-level entry points (stateless; used by torch.autograd.Function) ---
  * Same kernels as the step calls.  dtype: CRL_PREC_FP32 (float) or

@@ -84,6 +84,7 @@ _SIGNATURES = {
     "crl_last_error": (ctypes.c_char_p, [c_void_p]),
     "crl_trace_start": (c_int32, [c_void_p, c_int32, c_int32]),
     "crl_trace_stop": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_double), POINTER(c_double)]),
+    "crl_set_launch_overlap": (c_int32, [c_int32]),
     "crl_mlp_saved_bytes": (c_int32, [POINTER(CrlMlpDesc), c_int32, POINTER(c_size_t)]),
     "crl_mlp_forward": (c_int32, [POINTER(CrlMlpDesc), c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
                                   c_void_p]),
@@ -142,6 +143,12 @@ def ptr(t):
     if isinstance(t, np.ndarray):
         return t.ctypes.data
     return t.data_ptr()
+
+
+def set_launch_overlap(enable):
+    """Process-wide: launch every kernel with programmatic stream serialisation
+    (True, the default) or in plain stream order.  Returns the previous setting."""
+    return bool(lib().crl_set_launch_overlap(1 if enable else 0))
 
 
 def stream_handle(stream=None):

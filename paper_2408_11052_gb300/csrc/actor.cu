@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(256) head_forward_kernel(int B, int A, const T
                                                           unsigned long long seed, unsigned long long agent,
                                                           T* __restrict__ a_new, T* __restrict__ logpi,
                                                           T* __restrict__ eps_used) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int b = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (b >= B) return;
@@ -81,6 +82,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) diag_energy_kernel(int B, int R, int energy, double tau,
                                                          const T* __restrict__ phi, const T* __restrict__ psi,
                                                          T* __restrict__ fdiag, T* __restrict__ dphi) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int i = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (i >= B) return;
@@ -134,6 +136,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) actor_loss_kernel(int B, double alpha, const T* __restrict__ logpi,
                                                          const T* __restrict__ fdiag, T* __restrict__ loss2,
                                                          unsigned* status, int* t_bump) {
+  pdl_enter();
   __shared__ T sm[32];
   T a = 0, l = 0;
   for (int i = threadIdx.x; i < B; i += blockDim.x) {
@@ -154,6 +157,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) head_backward_kernel(int B, int A, double alpha, const T* __restrict__ out,
                                                            const T* __restrict__ eps_used,
                                                            const T* __restrict__ da, T* __restrict__ dout) {
+  pdl_enter();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const T ab = T(alpha / B);
@@ -178,7 +182,7 @@ template <typename T>
 void actor_head_forward(const ActorSpec& as, const T* pi_out, const float* eps, const unsigned long long* step_dev,
                         uint64_t seed, uint64_t agent, int B, T* a_new, T* logpi, T* eps_used, cudaStream_t st) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 5);
-  head_forward_kernel<T><<<ceil_div(B, 8), 256, 0, st>>>(B, as.A, pi_out, eps, step_dev, seed, agent, a_new,
+  launch_k(head_forward_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, B, as.A, pi_out, eps, step_dev, seed, agent, a_new,
                                                            logpi, eps_used);
 }
 
@@ -187,17 +191,17 @@ void actor_energy_and_loss(const ActorSpec& as, const T* phi, const T* psi, cons
                            T* fdiag, T* loss2, unsigned* status, int* t_bump, cudaStream_t st) {
   {
     TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * R);
-    diag_energy_kernel<T><<<ceil_div(B, 8), 256, 0, st>>>(B, R, as.energy, as.tau, phi, psi, fdiag, dphi);
+    launch_k(diag_energy_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, B, R, as.energy, as.tau, phi, psi, fdiag, dphi);
   }
   TraceLaunch tr(CRL_TRACE_AUX, st, 2.0 * B * sizeof(T));
-  actor_loss_kernel<T><<<1, 1024, 0, st>>>(B, as.alpha, logpi, fdiag, loss2, status, t_bump);
+  launch_k(actor_loss_kernel<T>, dim3(1), dim3(1024), 0, st, B, as.alpha, logpi, fdiag, loss2, status, t_bump);
 }
 
 template <typename T>
 void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used, const T* da, int B, T* dout,
                          cudaStream_t st) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 6);
-  head_backward_kernel<T><<<ceil_div(B, 256), 256, 0, st>>>(B, as.A, as.alpha, pi_out, eps_used, da, dout);
+  launch_k(head_backward_kernel<T>, dim3(ceil_div(B, 256)), dim3(256), 0, st, B, as.A, as.alpha, pi_out, eps_used, da, dout);
 }
 
 #define CRL_INST_ACTOR(T)                                                                                        \

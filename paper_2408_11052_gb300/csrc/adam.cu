@@ -18,6 +18,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) adam_kernel(T* __restrict__ p, const T* __restrict__ g, T* __restrict__ m,
                                                   T* __restrict__ v, long long n, const int* __restrict__ t_dev,
                                                   int t_host, float lr, float b1, float b2, float eps) {
+  pdl_enter();
   // Bias corrections in double (1 - b^t loses most of its digits in float for
   // small t), computed once per block.
   __shared__ double s_corr[2];
@@ -48,7 +49,7 @@ void adam_update(T* p, const T* g, T* m, T* v, int64_t n, const int* t_dev, int 
   if (n <= 0) return;
   const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
   TraceLaunch tr(CRL_TRACE_ADAM, st, 7.0 * sizeof(T) * n);  // read p, g, m, v; write p, m, v
-  adam_kernel<T><<<blocks, 256, 0, st>>>(p, g, m, v, n, t_dev, t_host, lr, b1, b2, eps);
+  launch_k(adam_kernel<T>, dim3(blocks), dim3(256), 0, st, p, g, m, v, n, t_dev, t_host, lr, b1, b2, eps);
 }
 
 template void adam_update<float>(float*, const float*, float*, float*, int64_t, const int*, int, float, float, float,

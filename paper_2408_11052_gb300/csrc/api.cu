@@ -20,6 +20,7 @@ using namespace crl;
 
 namespace crl {
 thread_local Tracer* g_tracer = nullptr;
+int g_launch_overlap = 1;
 }
 
 namespace {
@@ -167,9 +168,8 @@ struct crl_ctx {
   bool fused = false;
   EnergyTc etc;
   void* etc_ws = nullptr;
-  // second stream for the independent phi / psi chains (fork / join through events)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev[4] = {};
+  // device problem tables of the grouped tensor-core GEMMs
+  GemmGroups groups;
   // CUDA graph of relabel -> critic -> actor, replayed by crl_update_step
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -197,9 +197,6 @@ struct crl_ctx {
   ~crl_ctx() {
     drop_graph();
     drop_trace_events();
-    for (cudaEvent_t e : ev)
-      if (e) cudaEventDestroy(e);
-    if (side) cudaStreamDestroy(side);
     for (void* p : allocs) cudaFree(p);
     if (stage) cudaFree(stage);
   }
@@ -250,6 +247,7 @@ LossSpec loss_spec(const crl_config& c) {
 
 template <typename T>
 __global__ void to_float_kernel(const T* __restrict__ src, float* __restrict__ dst, int n) {
+  pdl_enter();
   const int i = threadIdx.x;
   if (i < n) dst[i] = (float)src[i];
 }
@@ -291,9 +289,9 @@ void critic_impl(crl_ctx* c, const float* s, const float* a, const float* g, int
                      cf.adam_beta2, cf.adam_eps, st);
     }
   }
-  {
+  if constexpr (sizeof(T) != sizeof(float)) {
     TraceLaunch tr(CRL_TRACE_AUX, st, 4.0 * (sizeof(T) + 4));
-    to_float_kernel<T><<<1, 32, 0, st>>>(loss, c->loss_f, 4);
+    launch_k(to_float_kernel<T>, dim3(1), dim3(32), 0, st, loss, c->loss_f, 4);
   }
   check_launch("critic step");
 }
@@ -332,9 +330,9 @@ void actor_impl(crl_ctx* c, const float* s, const float* g, const float* eps, in
                    static_cast<T*>(np.adam_v), c->counts[CRL_NET_PI], &c->ctr->t_actor, 0, cf.lr_actor,
                    cf.adam_beta1, cf.adam_beta2, cf.adam_eps, st);
   }
-  {
+  if constexpr (sizeof(T) != sizeof(float)) {
     TraceLaunch tr(CRL_TRACE_AUX, st, 2.0 * (sizeof(T) + 4));
-    to_float_kernel<T><<<1, 32, 0, st>>>(loss, c->loss_f + 4, 2);
+    launch_k(to_float_kernel<T>, dim3(1), dim3(32), 0, st, loss, c->loss_f + 4, 2);
   }
   check_launch("actor step");
 }
@@ -352,14 +350,8 @@ void bf_maps(crl_ctx* c, int net, int B) {
   if (e) throw Failure(CRL_E_CUDA, std::string("tensor map: ") + e);
 }
 
-// Fork: `side` waits for everything issued so far on `st`.  Join: `st` waits for `side`.
-void fork_to_side(crl_ctx* c, cudaStream_t st, int k) {
-  CRL_CHECK_CUDA(cudaEventRecord(c->ev[k], st));
-  CRL_CHECK_CUDA(cudaStreamWaitEvent(c->side, c->ev[k], 0));
-}
-void join_from_side(crl_ctx* c, cudaStream_t st, int k) {
-  CRL_CHECK_CUDA(cudaEventRecord(c->ev[k], c->side));
-  CRL_CHECK_CUDA(cudaStreamWaitEvent(st, c->ev[k], 0));
+void bf_check(const char* err) {
+  if (err) throw Failure(CRL_E_CUDA, std::string("BF16 network pass: ") + err);
 }
 
 // Refresh the BF16 shadows of `net` unless they are known to match (refresh forces it).
@@ -378,7 +370,9 @@ AdamShadowNet adam_net_of(crl_ctx* c, int net, const int* t, float lr) {
 }
 
 // Critic step with BF16 tensor-core encoders (FP32 master weights).  refresh:
-// rebuild the BF16 weight shadows first (the caller may have changed the weights).
+// rebuild the BF16 weight shadows first (the caller may have changed the
+// weights).  packed: the relabel kernel already wrote the split network inputs.
+// phi and psi run side by side as grouped launches (one per layer).
 void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g, int B, int apply, cudaStream_t st,
                       bool refresh = true, bool packed = false) {
   const crl_config& cf = c->cfg;
@@ -395,11 +389,9 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     bf_net_pack_input(P, s, a, B, st);
     bf_net_pack_input(Q, g, nullptr, B, st);
   }
-  // phi and psi forward in parallel
-  fork_to_side(c, st, 0);
-  bf_net_forward(P, pphi, B, status, st);
-  bf_net_forward(Q, ppsi, B, status, c->side);
-  join_from_side(c, st, 1);
+  const BfPass pass[2] = {{&P, pphi, static_cast<float*>(c->nets[CRL_NET_PHI].grads), nullptr},
+                          {&Q, ppsi, static_cast<float*>(c->nets[CRL_NET_PSI].grads), nullptr}};
+  bf_check(bf_forward(c->groups, pass, 2, B, status, st));
   float* rl = static_cast<float*>(c->row_lse);
   float* cl = static_cast<float*>(c->col_lse);
   float* loss = static_cast<float*>(c->loss);
@@ -412,8 +404,8 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     if (e) throw Failure(CRL_E_CUDA, std::string("tensor map: ") + e);
     energy_tc_prepare(c->etc, ls, P.y, Q.y, B, st);
     energy_tc_forward(c->etc, ls, B, loss, rl, cl, c->etc_ws, status, apply ? &c->ctr->t_critic : nullptr, st);
-    energy_tc_backward(c->etc, ls, B, P.y, Q.y, rl, cl, 1.0, P.dz[0], P.dzT[0], Q.dz[0], Q.dzT[0], P.Mmax, status,
-                       st);
+    energy_tc_backward(c->etc, ls, B, P.y, Q.y, rl, cl, 1.0, P.dz[P.layers], P.dzT[P.layers], Q.dz[Q.layers],
+                       Q.dzT[Q.layers], P.Mmax, status, st);
   } else {
     infonce_forward<float>(ls, P.y, Q.y, B, cf.repr, loss, rl, cl, c->ws, CRL_PATH_PLAIN, status,
                            apply ? &c->ctr->t_critic : nullptr, st);
@@ -421,25 +413,19 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     bf_net_load_dy(P, dphi, B, st);
     bf_net_load_dy(Q, dpsi, B, st);
   }
-  // phi and psi backward in parallel
-  fork_to_side(c, st, 2);
-  bf_net_backward(P, pphi, B, static_cast<float*>(c->nets[CRL_NET_PHI].grads), nullptr, status, st);
-  bf_net_backward(Q, ppsi, B, static_cast<float*>(c->nets[CRL_NET_PSI].grads), nullptr, status, c->side);
-  join_from_side(c, st, 3);
+  bf_check(bf_backward(c->groups, pass, 2, B, status, st));
   if (apply) {
     // Adam for phi and psi in one launch, refreshing their BF16 shadows
     const AdamShadowNet an[2] = {adam_net_of(c, CRL_NET_PHI, &c->ctr->t_critic, cf.lr_critic),
                                  adam_net_of(c, CRL_NET_PSI, &c->ctr->t_critic, cf.lr_critic)};
     adam_shadow_update(an, 2, cf.adam_beta1, cf.adam_beta2, cf.adam_eps, st);
   }
-  {
-    TraceLaunch tr(CRL_TRACE_AUX, st, 32.0);
-    to_float_kernel<float><<<1, 32, 0, st>>>(loss, c->loss_f, 4);
-  }
   check_launch("critic step (bf16)");
 }
 
-// Actor step with BF16 tensor-core networks.
+// Actor step with BF16 tensor-core networks.  pi(s, g) and psi(g) run side by
+// side (psi does not depend on the policy), then the head, phi(s, a'), the
+// diagonal energy and the backward through phi (input gradient only) and pi.
 void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* eps, int B, int apply, cudaStream_t st,
                      bool refresh = true, bool packed = false) {
   const crl_config& cf = c->cfg;
@@ -466,29 +452,23 @@ void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* ep
     bf_net_pack_input(PI, s, g, B, st);
     bf_net_pack_input(Q, g, nullptr, B, st);
   }
-  // psi(g) does not depend on the policy: it runs beside pi -> head -> phi
-  fork_to_side(c, st, 0);
-  bf_net_forward(Q, ppsi, B, status, c->side);
-  bf_net_forward(PI, ppi, B, status, st);
+  const BfPass fwd1[2] = {{&PI, ppi, nullptr, nullptr}, {&Q, ppsi, nullptr, nullptr}};
+  bf_check(bf_forward(c->groups, fwd1, 2, B, status, st));
   actor_head_forward<float>(as, PI.y, eps, &c->ctr->last_step, cf.seed, cf.agent, B, a_new, logpi, eps_used, st);
   bf_net_pack_input(P, s, a_new, B, st);
-  bf_net_forward(P, pphi, B, status, st);
-  join_from_side(c, st, 1);
+  const BfPass phi_pass[1] = {{&P, pphi, nullptr, da}};
+  bf_check(bf_forward(c->groups, phi_pass, 1, B, status, st));
   actor_energy_and_loss<float>(as, P.y, Q.y, logpi, B, cf.repr, dphi, static_cast<float*>(c->fdiag), loss, status,
                                apply ? &c->ctr->t_actor : nullptr, st);
   bf_net_load_dy(P, dphi, B, st);
-  bf_net_backward(P, pphi, B, nullptr, da, status, st);
+  bf_check(bf_backward(c->groups, phi_pass, 1, B, status, st));
   actor_head_backward<float>(as, PI.y, eps_used, da, B, dout, st);
   bf_net_load_dy(PI, dout, B, st);
-  const crl_net_ptrs& np = c->nets[CRL_NET_PI];
-  bf_net_backward(PI, ppi, B, static_cast<float*>(np.grads), nullptr, status, st);
+  const BfPass pi_pass[1] = {{&PI, ppi, static_cast<float*>(c->nets[CRL_NET_PI].grads), nullptr}};
+  bf_check(bf_backward(c->groups, pi_pass, 1, B, status, st));
   if (apply) {
     const AdamShadowNet an = adam_net_of(c, CRL_NET_PI, &c->ctr->t_actor, cf.lr_actor);
     adam_shadow_update(&an, 1, cf.adam_beta1, cf.adam_beta2, cf.adam_eps, st);
-  }
-  {
-    TraceLaunch tr(CRL_TRACE_AUX, st, 16.0);
-    to_float_kernel<float><<<1, 32, 0, st>>>(loss, c->loss_f + 4, 2);
   }
   check_launch("actor step (bf16)");
 }
@@ -706,13 +686,13 @@ int crl_create(const crl_config* cfg, crl_ctx** out) {
     c->fdiag = c->dalloc((size_t)B * e);
     c->da = c->dalloc((size_t)B * A * e);
     c->dout = c->dalloc((size_t)B * 2 * A * e);
-    c->loss_f = static_cast<float*>(c->dalloc(8 * sizeof(float)));
+    // FP32 / BF16: the loss parts are already float and land in the ABI's float buffer directly
+    c->loss_f = (e == sizeof(float)) ? static_cast<float*>(c->loss) : static_cast<float*>(c->dalloc(8 * sizeof(float)));
     c->bs = static_cast<float*>(c->dalloc((size_t)B * cf.D * sizeof(float)));
     c->ba = static_cast<float*>(c->dalloc((size_t)B * cf.A * sizeof(float)));
     c->bg = static_cast<float*>(c->dalloc((size_t)B * cf.G * sizeof(float)));
+    CRL_CHECK_CUDA(cudaMemset(c->loss, 0, 8 * e));
     CRL_CHECK_CUDA(cudaMemset(c->loss_f, 0, 8 * sizeof(float)));
-    CRL_CHECK_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-    for (cudaEvent_t& e : c->ev) CRL_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (cf.precision == CRL_PREC_BF16) {
       c->bf16 = true;
       for (int net = 0; net < 3; ++net) {
@@ -733,6 +713,7 @@ int crl_create(const crl_config* cfg, crl_ctx** out) {
       e.auxX = static_cast<float*>(c->dalloc((size_t)B * 4));
       e.auxY = static_cast<float*>(c->dalloc((size_t)B * 4));
       c->etc_ws = c->dalloc(energy_tc_ws_bytes(B));
+      CRL_CHECK_CUDA(cudaMemset(c->etc_ws, 0, energy_tc_ws_bytes(B)));   // the finalize ticket starts at 0
     }
     CRL_CHECK_CUDA(cudaDeviceSynchronize());
   });
@@ -758,6 +739,12 @@ int crl_bind_params(crl_ctx* ctx, const crl_net_ptrs nets[3]) {
       CRL_REQUIRE(nets[i].params && nets[i].grads && nets[i].adam_m && nets[i].adam_v, CRL_E_INVALID_ARG,
                   "every network needs params, grads, adam_m and adam_v");
     for (int i = 0; i < 3; ++i) {
+      const void* p[4] = {nets[i].params, nets[i].grads, nets[i].adam_m, nets[i].adam_v};
+      for (const void* q : p)
+        CRL_REQUIRE((reinterpret_cast<uintptr_t>(q) & 15) == 0, CRL_E_INVALID_ARG,
+                    "parameter, gradient and Adam arrays must be 16-byte aligned");
+    }
+    for (int i = 0; i < 3; ++i) {
       ctx->nets[i] = nets[i];
       // Padding between tensors never receives a gradient; keep it at zero.
       CRL_CHECK_CUDA(cudaMemset(nets[i].grads, 0, (size_t)ctx->counts[i] * ctx->esz));
@@ -765,6 +752,7 @@ int crl_bind_params(crl_ctx* ctx, const crl_net_ptrs nets[3]) {
     CRL_CHECK_CUDA(cudaMemset(&ctx->ctr->t_critic, 0, 2 * sizeof(int)));
     CRL_CHECK_CUDA(cudaDeviceSynchronize());
     ctx->drop_graph();
+    ctx->groups.reset();   // tables hold parameter pointers
     ctx->update_calls = 0;
     for (int i = 0; i < 3; ++i) ctx->shadow_ok[i] = false;
     ctx->bound = true;
@@ -921,6 +909,12 @@ int crl_sync_status(crl_ctx* ctx, void* stream, uint32_t* status) {
 }
 
 const char* crl_last_error(const crl_ctx* ctx) { return ctx ? ctx->err.c_str() : g_thread_error.c_str(); }
+
+int32_t crl_set_launch_overlap(int32_t enable) {
+  const int32_t prev = g_launch_overlap;
+  g_launch_overlap = enable ? 1 : 0;
+  return prev;
+}
 
 int crl_trace_start(crl_ctx* ctx, int32_t kernel_class, int32_t max_launches) {
   return guarded(ctx, [&] {

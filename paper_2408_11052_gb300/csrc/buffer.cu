@@ -23,6 +23,7 @@ namespace crl {
 __global__ void __launch_bounds__(128) insert_rows_kernel(BufferDev bd, const float* __restrict__ obs,
                                                          const float* __restrict__ act, int n, int i0,
                                                          long long total_before) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const long long row = (long long)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   const long long nrows = (long long)(n - i0) * bd.E;
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(128) insert_rows_kernel(BufferDev bd, const fl
 // flags in order; the stamping of one episode is spread over the lanes.
 __global__ void __launch_bounds__(128) close_episodes_kernel(BufferDev bd, const uint8_t* __restrict__ done,
                                                             int n, long long total_before) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int e = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   const long long total_after = total_before + n;
@@ -78,10 +80,10 @@ void launch_buffer_insert(const BufferDev& bd, const float* obs, const float* ac
   {
     // algorithmic bytes: read obs and act, write the rows (obs, act, episode end)
     TraceLaunch tr(CRL_TRACE_INSERT, st, (double)rows * ((bd.D + bd.A) * 4.0 + (bd.D + bd.A + 1) * 4.0));
-    insert_rows_kernel<<<ceil_div(rows, 4), 128, 0, st>>>(bd, obs, act, n, i0, total_before);
+    launch_k(insert_rows_kernel, dim3(ceil_div(rows, 4)), dim3(128), 0, st, bd, obs, act, n, i0, total_before);
   }
   TraceLaunch tr(CRL_TRACE_INSERT, st, (double)n * bd.E);  // read the done flags
-  close_episodes_kernel<<<ceil_div(bd.E, 4), 128, 0, st>>>(bd, done, n, total_before);
+  launch_k(close_episodes_kernel, dim3(ceil_div(bd.E, 4)), dim3(128), 0, st, bd, done, n, total_before);
 }
 
 // ---------------------------------------------------------------------------
@@ -120,6 +122,7 @@ __device__ __forceinline__ int geometric_offset(unsigned long long v, int L, int
 // One warp per sample: lane 0 draws the Philox block and the offset, the warp
 // copies the state-action row and the goal dims.
 __global__ void __launch_bounds__(256) relabel_kernel(BufferDev bd, RelabelArgs ra) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int b = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   const unsigned long long step = (ra.step == CRL_STEP_AUTO) ? *ra.step_dev : ra.step;
@@ -191,14 +194,17 @@ void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st)
   // algorithmic bytes per sample: read obs + act + episode end + goal dims, write s, a, g (+ idx)
   const double per = (bd.D + bd.A + 1 + ra.G) * 4.0 + (bd.D + bd.A + ra.G) * 4.0 + (ra.idx ? 12.0 : 0.0);
   TraceLaunch tr(CRL_TRACE_RELABEL, st, per * ra.B);
-  relabel_kernel<<<ceil_div(ra.B, 8), 256, 0, st>>>(bd, ra);
+  launch_k(relabel_kernel, dim3(ceil_div(ra.B, 8)), dim3(256), 0, st, bd, ra);
 }
 
-__global__ void bump_u64_kernel(unsigned long long* c) { *c += 1ull; }
+__global__ void bump_u64_kernel(unsigned long long* c) {
+  pdl_enter();
+  *c += 1ull;
+}
 
 void launch_bump_u64(unsigned long long* ctr, cudaStream_t st) {
   TraceLaunch tr(CRL_TRACE_AUX, st, 8.0);
-  bump_u64_kernel<<<1, 1, 0, st>>>(ctr);
+  launch_k(bump_u64_kernel, dim3(1), dim3(1), 0, st, ctr);
 }
 
 }  // namespace crl

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <utility>
 
 namespace crl {
 
@@ -64,5 +65,41 @@ __device__ __forceinline__ T softplus(T x) {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ---- programmatic dependent launch ---------------------------------------------
+// Every libcrl kernel is launched with programmatic stream serialisation
+// allowed (launch_k), so it may start while its predecessor on the stream is
+// still running.  Before its first global-memory access every kernel calls
+// pdl_wait(), which returns once all prerequisite grids have completed and
+// their writes are visible; pdl_trigger() then lets the next kernel of the
+// stream be scheduled (it will in turn block in its own pdl_wait).  Kernels
+// that allocate tensor memory trigger only after the allocation, so a waiting
+// successor never holds TMEM that its predecessor still needs.
+// Both instructions are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  pdl_trigger();
+}
+
+// Process-wide switch (crl_set_launch_overlap); 1 = launch with the attribute.
+extern int g_launch_overlap;
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = g_launch_overlap ? 1 : 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 }  // namespace crl

@@ -83,6 +83,7 @@ struct EpiEnergy {
 template <typename T>
 __global__ void __launch_bounds__(256) normalize_rows_kernel(int B, int R, const T* __restrict__ x,
                                                             T* __restrict__ inv, T* __restrict__ xh) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (row >= B) return;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(256) normalize_rows_kernel(int B, int R, const
 // r_i = LSE_j F_ij.  One warp per row, two passes.
 template <typename T>
 __global__ void __launch_bounds__(256) row_lse_kernel(int B, const T* __restrict__ F, T* __restrict__ r) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (row >= B) return;
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(256) row_lse_kernel(int B, const T* __restrict
 // running (max, sum) over its rows, then the 8 partials of a column are merged.
 template <typename T>
 __global__ void __launch_bounds__(256) col_lse_kernel(int B, const T* __restrict__ F, T* __restrict__ c) {
+  pdl_enter();
   __shared__ T sm_m[8][33], sm_s[8][33];
   const int cx = threadIdx.x % 32, ry = threadIdx.x / 32;
   const int j = blockIdx.x * 32 + cx;
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(256) col_lse_kernel(int B, const T* __restrict
 // Row sums (warp per row) and column sums (thread per column) of H.
 template <typename T>
 __global__ void __launch_bounds__(256) row_sum_kernel(int B, const T* __restrict__ H, T* __restrict__ out) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (row >= B) return;
@@ -157,6 +161,7 @@ __global__ void __launch_bounds__(256) row_sum_kernel(int B, const T* __restrict
 }
 template <typename T>
 __global__ void __launch_bounds__(256) col_sum_kernel(int B, const T* __restrict__ H, T* __restrict__ out) {
+  pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= B) return;
   T s = 0;
@@ -183,6 +188,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) loss_kernel(int B, const T* __restrict__ F, int ldf, const T* __restrict__ r,
                                                    const T* __restrict__ c, DirWeights w, double beta,
                                                    T* __restrict__ loss4, unsigned* status, int* t_bump) {
+  pdl_enter();
   __shared__ T sm[32];
   T a_f = 0, a_b = 0, a_r2 = 0, a_c2 = 0;
   for (int i = threadIdx.x; i < B; i += blockDim.x) {
@@ -215,6 +221,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) grad_coeff_kernel(int B, T* __restrict__ F, const T* __restrict__ r,
                                                         const T* __restrict__ c, DirWeights w, double beta,
                                                         double dtotal, int energy, double tau) {
+  pdl_enter();
   const size_t n = (size_t)B * B;
   const T scale = T(dtotal / B);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -243,6 +250,7 @@ __global__ void __launch_bounds__(256) grad_coeff_kernel(int B, T* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256) project_rows_kernel(int B, int R, const T* __restrict__ xh,
                                                           const T* __restrict__ inv, T* __restrict__ dx) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (row >= B) return;
@@ -271,8 +279,8 @@ void infonce_forward(const LossSpec& ls, const T* phi, const T* psi, int B, int 
   PlainWs<T> w = carve_plain<T>(B, R, ws);
   const int nb = ceil_div(B, 8);
   if (ls.energy == CRL_ENERGY_COS) {
-    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); normalize_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, phi, w.inx, w.xh); }
-    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); normalize_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, psi, w.iny, w.yh); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(normalize_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, R, phi, w.inx, w.xh); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(normalize_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, R, psi, w.iny, w.yh); }
   }
   EpiEnergy<T> ep{w.F, B, ls.energy, T(1.0 / ls.tau), w.inx, w.iny};
   LoadMK<T> la{phi, R};
@@ -283,9 +291,9 @@ void infonce_forward(const LossSpec& ls, const T* phi, const T* psi, int B, int 
     case CRL_ENERGY_L1: gemm<T, InnerOp::kAbsDiff>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
     default: gemm<T, InnerOp::kMul>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
   }
-  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); row_lse_kernel<T><<<nb, 256, 0, st>>>(B, w.F, row_lse); }
-  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); col_lse_kernel<T><<<ceil_div(B, 32), 256, 0, st>>>(B, w.F, col_lse); }
-  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); loss_kernel<T><<<1, 1024, 0, st>>>(B, w.F, B, row_lse, col_lse, weights(ls), ls.beta, loss4, status, t_bump); }
+  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(row_lse_kernel<T>, dim3(nb), dim3(256), 0, st, B, w.F, row_lse); }
+  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(col_lse_kernel<T>, dim3(ceil_div(B, 32)), dim3(256), 0, st, B, w.F, col_lse); }
+  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(loss_kernel<T>, dim3(1), dim3(1024), 0, st, B, w.F, B, row_lse, col_lse, weights(ls), ls.beta, loss4, status, t_bump); }
 }
 
 template <typename T>
@@ -296,8 +304,8 @@ void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int
   const int nb = ceil_div(B, 8);
   // Recompute F (the forward's copy may have been overwritten by another call).
   if (ls.energy == CRL_ENERGY_COS) {
-    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); normalize_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, phi, w.inx, w.xh); }
-    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); normalize_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, psi, w.iny, w.yh); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(normalize_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, R, phi, w.inx, w.xh); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(normalize_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, R, psi, w.iny, w.yh); }
   }
   {
     EpiEnergy<T> ep{w.F, B, ls.energy, T(1.0 / ls.tau), w.inx, w.iny};
@@ -310,12 +318,12 @@ void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int
     }
   }
   const int ge = (int)std::min<int64_t>(ceil_div((int64_t)B * B, 256), 152 * 16);
-  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); grad_coeff_kernel<T><<<ge, 256, 0, st>>>(B, w.F, row_lse, col_lse, weights(ls), ls.beta, dtotal, ls.energy,
+  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(grad_coeff_kernel<T>, dim3(ge), dim3(256), 0, st, B, w.F, row_lse, col_lse, weights(ls), ls.beta, dtotal, ls.energy,
                                            ls.tau); }
   const T* H = w.F;
   if (ls.energy == CRL_ENERGY_L2 || ls.energy == CRL_ENERGY_L2SQ) {
-    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); row_sum_kernel<T><<<nb, 256, 0, st>>>(B, H, w.rsum); }
-    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); col_sum_kernel<T><<<ceil_div(B, 256), 256, 0, st>>>(B, H, w.csum); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(row_sum_kernel<T>, dim3(nb), dim3(256), 0, st, B, H, w.rsum); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(col_sum_kernel<T>, dim3(ceil_div(B, 256)), dim3(256), 0, st, B, H, w.csum); }
     gemm<T>(B, R, B, LoadMK<T>{H, B}, LoadKN<T>{psi, R}, EpiSubRowScaled<T>{dphi, R, T(1), w.rsum, phi, R}, st,
             CRL_TRACE_ENERGY);
     gemm<T>(B, R, B, LoadTrans<T>{H, B}, LoadKN<T>{phi, R}, EpiSubRowScaled<T>{dpsi, R, T(1), w.csum, psi, R},
@@ -323,8 +331,8 @@ void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int
   } else if (ls.energy == CRL_ENERGY_COS) {
     gemm<T>(B, R, B, LoadMK<T>{H, B}, LoadKN<T>{w.yh, R}, EpiScale<T>{dphi, R, T(1)}, st, CRL_TRACE_ENERGY);
     gemm<T>(B, R, B, LoadTrans<T>{H, B}, LoadKN<T>{w.xh, R}, EpiScale<T>{dpsi, R, T(1)}, st, CRL_TRACE_ENERGY);
-    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); project_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, w.xh, w.inx, dphi); }
-    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); project_rows_kernel<T><<<nb, 256, 0, st>>>(B, R, w.yh, w.iny, dpsi); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(project_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, R, w.xh, w.inx, dphi); }
+    { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(project_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, R, w.yh, w.iny, dpsi); }
   } else {  // dot
     gemm<T>(B, R, B, LoadMK<T>{H, B}, LoadKN<T>{psi, R}, EpiScale<T>{dphi, R, T(1)}, st, CRL_TRACE_ENERGY);
     gemm<T>(B, R, B, LoadTrans<T>{H, B}, LoadKN<T>{phi, R}, EpiScale<T>{dpsi, R, T(1)}, st, CRL_TRACE_ENERGY);

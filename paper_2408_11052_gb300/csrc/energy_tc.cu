@@ -66,11 +66,23 @@ __device__ __forceinline__ float energy_of(int energy, float s, float ax, float 
 }
 
 // ---- representation preparation ------------------------------------------------
-// y [B][R] FP32 -> X [B][R] BF16 (normalised for cos), X^T [R][ldt] BF16, aux [B].
-// Block = 32 rows, one warp per row; the transposed copy goes through a shared tile.
-__global__ void __launch_bounds__(1024) prep_kernel(int B, int R, int energy, const float* __restrict__ y,
-                                                   bf16* __restrict__ X, bf16* __restrict__ XT, int ldt,
-                                                   float* __restrict__ aux) {
+// y [B][R] FP32 -> X [B][R] BF16 (normalised for cos), X^T [R][ldt] BF16, aux [B],
+// for phi and psi in one launch.  Block = 32 rows, one warp per row; the
+// transposed copy goes through a shared tile.
+struct PrepSide {
+  const float* y;
+  bf16* X;
+  bf16* XT;
+  float* aux;
+};
+// blockIdx.y = 0: phi -> X, 1: psi -> Y.
+__global__ void __launch_bounds__(1024) prep_kernel(int B, int R, int energy, int ldt, PrepSide s0, PrepSide s1) {
+  pdl_enter();
+  const PrepSide p = blockIdx.y ? s1 : s0;
+  const float* __restrict__ y = p.y;
+  bf16* __restrict__ X = p.X;
+  bf16* __restrict__ XT = p.XT;
+  float* __restrict__ aux = p.aux;
   __shared__ float tile[32][33];
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   const int row = blockIdx.x * 32 + w;
@@ -120,6 +132,14 @@ struct FwdArgs {
   float* colpart;  // [nI][B][2]
   float* diag;     // [B]
   unsigned* status;
+  // finalize (run by the last CTA to finish)
+  Weights w;
+  float beta;
+  float* r_out;
+  float* c_out;
+  float* loss4;
+  int* t_bump;
+  unsigned* ticket;  // zero between launches
 };
 
 __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2) {
@@ -132,6 +152,51 @@ __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2
   const float M = fmaxf(m, m2);
   s = s * __expf(m - M) + s2 * __expf(m2 - M);
   m = M;
+}
+
+// Merge the partials into r, c and the loss parts (one block of any size).
+__device__ void finalize_block(const FwdArgs& a, int nI, int nJ) {
+  __shared__ float sm[32];
+  const int B = a.B;
+  float af = 0.f, ab = 0.f, ar2 = 0.f, ac2 = 0.f;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    float m = -INFINITY, s = 0.f;
+    for (int J = 0; J < nJ; ++J) {
+      const float* p = a.rowpart + ((size_t)J * B + i) * 2;
+      lse_merge(m, s, __ldcg(p), __ldcg(p + 1));
+    }
+    const float r = m + __logf(s);
+    m = -INFINITY;
+    s = 0.f;
+    for (int I = 0; I < nI; ++I) {
+      const float* p = a.colpart + ((size_t)I * B + i) * 2;
+      lse_merge(m, s, __ldcg(p), __ldcg(p + 1));
+    }
+    const float c = m + __logf(s);
+    const float d = __ldcg(a.diag + i);
+    a.r_out[i] = r;
+    a.c_out[i] = c;
+    af += r - d;
+    ab += c - d;
+    ar2 += r * r;
+    ac2 += c * c;
+  }
+  af = block_sum(af, sm);
+  ab = block_sum(ab, sm);
+  ar2 = block_sum(ar2, sm);
+  ac2 = block_sum(ac2, sm);
+  if (threadIdx.x == 0) {
+    const float inv = 1.f / B;
+    const float lf = af * inv, lb = ab * inv;
+    const float pen = a.beta * (a.w.pr * ar2 * inv + a.w.pc * ac2 * inv);
+    const float total = a.w.wf * lf + a.w.wb * lb + pen;
+    a.loss4[0] = total;
+    a.loss4[1] = lf;
+    a.loss4[2] = lb;
+    a.loss4[3] = pen;
+    if (a.status && !isfinite(total)) atomicOr(a.status, CRL_STATUS_NONFINITE);
+    if (a.t_bump) *a.t_bump += 1;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
@@ -167,6 +232,8 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant_
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();
+  pdl_trigger();
 
   if (tid == 0) {
     tc::mbar_arrive_expect_tx(load_bar, (uint32_t)(2 * nk * 16384));
@@ -264,52 +331,16 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant_
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
-}
-
-// Merge the partials, compute r, c and the loss parts.  One block.
-__global__ void __launch_bounds__(1024) finalize_kernel(int B, int nI, int nJ, const float* __restrict__ rowpart,
-                                                       const float* __restrict__ colpart,
-                                                       const float* __restrict__ diag, Weights w, float beta,
-                                                       float* __restrict__ r_out, float* __restrict__ c_out,
-                                                       float* __restrict__ loss4, unsigned* status, int* t_bump) {
-  __shared__ float sm[32];
-  float af = 0.f, ab = 0.f, ar2 = 0.f, ac2 = 0.f;
-  for (int i = threadIdx.x; i < B; i += blockDim.x) {
-    float m = -INFINITY, s = 0.f;
-    for (int J = 0; J < nJ; ++J) {
-      const float* p = rowpart + ((size_t)J * B + i) * 2;
-      lse_merge(m, s, p[0], p[1]);
-    }
-    const float r = m + __logf(s);
-    m = -INFINITY;
-    s = 0.f;
-    for (int I = 0; I < nI; ++I) {
-      const float* p = colpart + ((size_t)I * B + i) * 2;
-      lse_merge(m, s, p[0], p[1]);
-    }
-    const float c = m + __logf(s);
-    r_out[i] = r;
-    c_out[i] = c;
-    af += r - diag[i];
-    ab += c - diag[i];
-    ar2 += r * r;
-    ac2 += c * c;
-  }
-  af = block_sum(af, sm);
-  ab = block_sum(ab, sm);
-  ar2 = block_sum(ar2, sm);
-  ac2 = block_sum(ac2, sm);
-  if (threadIdx.x == 0) {
-    const float inv = 1.f / B;
-    const float lf = af * inv, lb = ab * inv;
-    const float pen = beta * (w.pr * ar2 * inv + w.pc * ac2 * inv);
-    const float total = w.wf * lf + w.wb * lb + pen;
-    loss4[0] = total;
-    loss4[1] = lf;
-    loss4[2] = lb;
-    loss4[3] = pen;
-    if (status && !isfinite(total)) atomicOr(status, CRL_STATUS_NONFINITE);
-    if (t_bump) *t_bump += 1;
+  // the last CTA to finish merges every CTA's partials (no CTA waits for another)
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y - 1) ? 1 : 0;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    finalize_block(a, gridDim.y, gridDim.x);
+    if (tid == 0) *a.ticket = 0u;
   }
 }
 
@@ -340,9 +371,17 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int chunk) {
 // shared region, the 16 warps turn S into the BF16 coefficient tile H (warp w:
 // rows 32 (w % 4) .., columns 32 (w / 4) ..), and the MMA adds H other into
 // the TMEM accumulator.
-__global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant__ CUtensorMap tmOwn,
-                                                          const __grid_constant__ CUtensorMap tmOther,
-                                                          const __grid_constant__ CUtensorMap tmOtherT, BwdArgs a) {
+// CTAs [0, nrow) run the row pass (own = phi), CTAs [nrow, 2 nrow) the column pass (own = psi).
+__global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmY,
+                                                          const __grid_constant__ CUtensorMap tmXT,
+                                                          const __grid_constant__ CUtensorMap tmYT, BwdArgs row,
+                                                          BwdArgs col, int nrow) {
+  const bool colpass = (int)blockIdx.x >= nrow;
+  const BwdArgs a = colpass ? col : row;
+  const CUtensorMap* tmOwn = colpass ? &tmY : &tmX;
+  const CUtensorMap* tmOther = colpass ? &tmX : &tmY;
+  const CUtensorMap* tmOtherT = colpass ? &tmXT : &tmYT;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   const int nk = a.R / 64;
@@ -365,12 +404,12 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant_
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int lg = warp % 4, q = warp / 4;
   const int r = lg * 32 + lane;  // row of this thread within the tile
-  const int u0 = blockIdx.x * kTile;
+  const int u0 = ((int)blockIdx.x - (colpass ? nrow : 0)) * kTile;
   const int nV = (a.B + kTile - 1) / kTile;
   if (tid == 0) {
-    tc::prefetch_tmap(&tmOwn);
-    tc::prefetch_tmap(&tmOther);
-    tc::prefetch_tmap(&tmOtherT);
+    tc::prefetch_tmap(tmOwn);
+    tc::prefetch_tmap(tmOther);
+    tc::prefetch_tmap(tmOtherT);
     tc::mbar_init(xload, 1);
     tc::mbar_init(yload, 1);
     tc::mbar_init(ytload, 1);
@@ -388,12 +427,14 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant_
   const uint32_t tmem = *tmem_slot;
   const uint32_t tS = tmem, tAcc = tmem + 128;
   const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
+  pdl_wait();
+  pdl_trigger();
 
   if (tid == 0) {
     tc::mbar_arrive_expect_tx(xload, (uint32_t)(nk * 16384));
     for (int kb = 0; kb < nk; ++kb)
       for (int rr = 0; rr < 2; ++rr)
-        tc::tma_load_2d(Xs + kb * 16384 + rr * 8192, &tmOwn, xload, kb * 64, u0 + 64 * rr);
+        tc::tma_load_2d(Xs + kb * 16384 + rr * 8192, tmOwn, xload, kb * 64, u0 + 64 * rr);
   }
 
   const int u = u0 + r;
@@ -416,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant_
       tc::mbar_arrive_expect_tx(yload, (uint32_t)(nk * 16384));
       for (int kb = 0; kb < nk; ++kb)
         for (int rr = 0; rr < 2; ++rr)
-          tc::tma_load_2d(Ys + kb * 16384 + rr * 8192, &tmOther, yload, kb * 64, v0 + 64 * rr);
+          tc::tma_load_2d(Ys + kb * 16384 + rr * 8192, tmOther, yload, kb * 64, v0 + 64 * rr);
     } else if (tid == 32) {
       bool good = (vt > 0) || tc::mbar_wait(xload, 0);
       good = good && tc::mbar_wait(yload, vt & 1);
@@ -444,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant_
       tc::mbar_arrive_expect_tx(ytload, (uint32_t)(2 * a.R * 128));
       for (int kb = 0; kb < 2; ++kb)
         for (int qq = 0; qq < a.R / 64; ++qq)
-          tc::tma_load_2d(Ys + kb * a.R * 128 + qq * 8192, &tmOtherT, ytload, v0 + 64 * kb, 64 * qq);
+          tc::tma_load_2d(Ys + kb * a.R * 128 + qq * 8192, tmOtherT, ytload, v0 + 64 * kb, 64 * qq);
     }
     // coefficient tile H: this thread's row r, columns 32 q .. 32 q + 31
     {
@@ -581,6 +622,9 @@ const char* mk(CUtensorMap* m, const void* base, int inner, int rows, int stride
 
 }  // namespace
 
+// The finalize ticket (first 256 bytes; zeroed when the workspace is created,
+// reset by each launch's last CTA), then rowpart [nJ][B][2], colpart
+// [nI][B][2] and diag [B].
 size_t energy_tc_ws_bytes(int B) {
   const int n = (B + kTile - 1) / kTile;
   return ((size_t)2 * n * B * 2 + B) * sizeof(float) + 256;
@@ -615,30 +659,27 @@ const char* energy_tc_maps(EnergyTc& e, int B) {
 
 void energy_tc_prepare(EnergyTc& e, const LossSpec& ls, const float* phi, const float* psi, int B, cudaStream_t st) {
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 0.0);
-  prep_kernel<<<ceil_div(B, 32), 1024, 0, st>>>(B, e.R, ls.energy, phi, e.X, e.XT, e.ldt, e.auxX);
-  prep_kernel<<<ceil_div(B, 32), 1024, 0, st>>>(B, e.R, ls.energy, psi, e.Y, e.YT, e.ldt, e.auxY);
+  launch_k(prep_kernel, dim3(ceil_div(B, 32), 2), dim3(1024), 0, st, B, e.R, ls.energy, e.ldt,
+           PrepSide{phi, e.X, e.XT, e.auxX}, PrepSide{psi, e.Y, e.YT, e.auxY});
 }
 
 void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, float* r, float* c, void* ws,
                        unsigned* status, int* t_bump, cudaStream_t st) {
   const int n = (B + kTile - 1) / kTile;
-  float* rowpart = static_cast<float*>(ws);
+  unsigned* ticket = static_cast<unsigned*>(ws);
+  float* rowpart = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
   float* colpart = rowpart + (size_t)2 * n * B;
   float* diag = colpart + (size_t)2 * n * B;
-  FwdArgs a{B, e.R, ls.energy, (float)(1.0 / ls.tau), e.auxX, e.auxY, rowpart, colpart, diag, status};
+  FwdArgs a{B,     e.R,  ls.energy, (float)(1.0 / ls.tau), e.auxX, e.auxY, rowpart, colpart, diag, status,
+            loss_weights(ls), (float)ls.beta, r, c, loss4, t_bump, ticket};
   const size_t sm = fwd_smem(e.R);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
     attr = true;
   }
-  {
-    TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * B * e.R);
-    fwd_kernel<<<dim3(n, n), kThreads, sm, st>>>(e.tmX, e.tmY, a);
-  }
-  TraceLaunch tr(CRL_TRACE_ENERGY, st, 0.0);
-  finalize_kernel<<<1, 1024, 0, st>>>(B, n, n, rowpart, colpart, diag, loss_weights(ls), (float)ls.beta, r, c, loss4,
-                                      status, t_bump);
+  TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * B * e.R);
+  launch_k(fwd_kernel, dim3(n, n), dim3(kThreads), sm, st, e.tmX, e.tmY, a);
 }
 
 void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
@@ -653,10 +694,6 @@ void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi
   const size_t sm = bwd_smem(e.R);
   BwdArgs a{B, e.R, ls.energy, 0, (float)(1.0 / ls.tau), (float)ls.beta, (float)(dtotal / B), loss_weights(ls),
             e.auxX, e.auxY, r, c, phi, dphi, dphiT, ldt, status};
-  {
-    TraceLaunch tr(CRL_TRACE_ENERGY, st, 4.0 * B * B * e.R);
-    bwd_kernel<<<n, kThreads, sm, st>>>(e.tmX, e.tmY, e.tmYT, a);
-  }
   BwdArgs b = a;
   b.transposed = 1;
   b.aux_own = e.auxY;
@@ -666,8 +703,8 @@ void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi
   b.own_f32 = psi;
   b.d_out = dpsi;
   b.d_outT = dpsiT;
-  TraceLaunch tr(CRL_TRACE_ENERGY, st, 4.0 * B * B * e.R);
-  bwd_kernel<<<n, kThreads, sm, st>>>(e.tmY, e.tmX, e.tmXT, b);
+  TraceLaunch tr(CRL_TRACE_ENERGY, st, 8.0 * B * B * e.R);
+  launch_k(bwd_kernel, dim3(2 * n), dim3(kThreads), sm, st, e.tmX, e.tmY, e.tmXT, e.tmYT, a, b, n);
 }
 
 }  // namespace crl

@@ -29,6 +29,7 @@ __device__ __forceinline__ T inner(T a, T b) {
 // barrier and the global-load latency overlaps the arithmetic.
 template <typename T, InnerOp OP, int BM, int BN, class LA, class LB, class EP>
 __global__ void __launch_bounds__(256) gemm_tile_kernel(int M, int N, int K, LA la, LB lb, EP ep) {
+  pdl_enter();
   constexpr int BK = 32;
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LDA = BM * BK / 256, LDB = BN * BK / 256;  // elements each thread loads per slice
@@ -126,10 +127,10 @@ void gemm(int M, int N, int K, const LA& la, const LB& lb, const EP& ep, cudaStr
   // FP64 always takes the 32 x 32 tile: its 64 x 64 double buffers exceed 48 KiB of static shared memory.
   if (sizeof(T) == 8 || tiles64 < 2 * 152) {
     dim3 grid(ceil_div(N, 32), ceil_div(M, 32));
-    gemm_tile_kernel<T, OP, 32, 32, LA, LB, EP><<<grid, 256, 0, st>>>(M, N, K, la, lb, ep);
+    launch_k(gemm_tile_kernel<T, OP, 32, 32, LA, LB, EP>, dim3(grid), dim3(256), 0, st, M, N, K, la, lb, ep);
   } else if constexpr (sizeof(T) == 4) {
     dim3 grid(ceil_div(N, 64), ceil_div(M, 64));
-    gemm_tile_kernel<T, OP, 64, 64, LA, LB, EP><<<grid, 256, 0, st>>>(M, N, K, la, lb, ep);
+    launch_k(gemm_tile_kernel<T, OP, 64, 64, LA, LB, EP>, dim3(grid), dim3(256), 0, st, M, N, K, la, lb, ep);
   }
 }
 

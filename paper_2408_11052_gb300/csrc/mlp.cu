@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(256) layernorm_relu_kernel(int M, int N, T* __
                                                             T* __restrict__ rstd, T* __restrict__ h,
                                                             const T* __restrict__ gain,
                                                             const T* __restrict__ bias) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (row >= M) return;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(256) layernorm_bwd_kernel(int M, int N, const 
                                                            const T* __restrict__ zhat,
                                                            const T* __restrict__ rstd,
                                                            const T* __restrict__ gain, T* __restrict__ dz) {
+  pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (row >= M) return;
@@ -149,6 +151,7 @@ __global__ void __launch_bounds__(256) colsum_kernel(int M, int N, const T* __re
                                                     const T* __restrict__ Y, const T* __restrict__ Z,
                                                     T* __restrict__ out1, T* __restrict__ out2,
                                                     T* __restrict__ out3) {
+  pdl_enter();
   __shared__ T sm[3][8][33];
   const int cx = threadIdx.x % 32, ry = threadIdx.x / 32;
   const int n = blockIdx.x * 32 + cx;
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(256) colsum_kernel(int M, int N, const T* __re
 template <typename T>
 void colsum(int M, int N, const T* X, const T* Y, const T* Z, T* o1, T* o2, T* o3, cudaStream_t st) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)M * N * sizeof(T) * (1 + (Y != nullptr) + (Z != nullptr)));
-  colsum_kernel<T><<<ceil_div(N, 32), 256, 0, st>>>(M, N, X, Y, Z, o1, o2, o3);
+  launch_k(colsum_kernel<T>, dim3(ceil_div(N, 32)), dim3(256), 0, st, M, N, X, Y, Z, o1, o2, o3);
 }
 
 }  // namespace
@@ -210,7 +213,7 @@ void mlp_forward(const MlpShape& s, const T* params, const float* x0, const TX1*
     }
     if (!last && s.layernorm) {
       TraceLaunch tr(CRL_TRACE_AUX, st, 4.0 * M * H * sizeof(T));
-      layernorm_relu_kernel<T><<<ceil_div(M, 8), 256, 0, st>>>(M, H, sv.zhat[l], sv.rstd[l], sv.h[l],
+      launch_k(layernorm_relu_kernel<T>, dim3(ceil_div(M, 8)), dim3(256), 0, st, M, H, sv.zhat[l], sv.rstd[l], sv.h[l],
                                                                params + L.g, params + L.beta);
     }
   }
@@ -261,7 +264,7 @@ void mlp_backward(const MlpShape& s, const T* params, const float* x0, const TX1
       T* dz = sv.scratch[2];
       {
         TraceLaunch tr(CRL_TRACE_AUX, st, 3.0 * M * H * sizeof(T));
-        layernorm_bwd_kernel<T><<<ceil_div(M, 8), 256, 0, st>>>(M, H, du, sv.zhat[l - 1], sv.rstd[l - 1],
+        launch_k(layernorm_bwd_kernel<T>, dim3(ceil_div(M, 8)), dim3(256), 0, st, M, H, du, sv.zhat[l - 1], sv.rstd[l - 1],
                                                                 params + P.g, dz);
       }
       if (dparams)

@@ -7,6 +7,8 @@
 // ReLU, W stored [out][in].
 #include <cuda_bf16.h>
 
+#include <string.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -25,160 +27,13 @@ constexpr float kLnEpsF = 1e-6f;
 
 inline int pad8(int x) { return (x + 7) / 8 * 8; }
 
-// ---- epilogues -----------------------------------------------------------------
-// hidden layer without LayerNorm: h = ReLU(acc + b), written row-major and transposed
-struct EpiFwdHidden {
-  const float* bias;
-  bf16* h;
-  int ldh;
-  bf16* hT;
-  int ldt;
-  __device__ void operator()(int row, int col0, const float (&v)[32], int M, int N) const {
-    if (row >= M) return;
-    if (col0 + 32 <= N) {
-      alignas(16) bf16 o[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) o[i] = __float2bfloat16_rn(fmaxf(v[i] + bias[col0 + i], 0.f));
-      uint4* dst = reinterpret_cast<uint4*>(h + (size_t)row * ldh + col0);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) hT[(size_t)(col0 + i) * ldt + row] = o[i];
-    } else {
-      for (int i = 0; i < 32 && col0 + i < N; ++i) {
-        const bf16 o = __float2bfloat16_rn(fmaxf(v[i] + bias[col0 + i], 0.f));
-        h[(size_t)row * ldh + col0 + i] = o;
-        hT[(size_t)(col0 + i) * ldt + row] = o;
-      }
-    }
-  }
-};
-
-// hidden layer with LayerNorm: z = acc + b (FP32), normalised by the LayerNorm kernel
-struct EpiFwdPreLN {
-  const float* bias;
-  float* z;
-  int ldz;
-  __device__ void operator()(int row, int col0, const float (&v)[32], int M, int N) const {
-    if (row >= M) return;
-    for (int i = 0; i < 32 && col0 + i < N; ++i) z[(size_t)row * ldz + col0 + i] = v[i] + bias[col0 + i];
-  }
-};
-
-// output layer: y = acc + b (FP32)
-struct EpiFwdOut {
-  const float* bias;
-  float* y;
-  int ldy;
-  __device__ void operator()(int row, int col0, const float (&v)[32], int M, int N) const {
-    if (row >= M) return;
-    for (int i = 0; i < 32 && col0 + i < N; ++i) y[(size_t)row * ldy + col0 + i] = v[i] + bias[col0 + i];
-  }
-};
-
-// input gradient of a hidden layer: du = acc * [h > 0]; BF16 dz / dz^T (no LayerNorm) or FP32 du
-struct EpiBwdDX {
-  const bf16* hmask;
-  int ldm;
-  bf16* dz;
-  int ldz;
-  bf16* dzT;
-  int ldt;
-  float* du;  // non-null: LayerNorm layer, write FP32 du instead
-  __device__ void operator()(int row, int col0, const float (&v)[32], int M, int N) const {
-    if (row >= M) return;
-    for (int i = 0; i < 32 && col0 + i < N; ++i) {
-      const int c = col0 + i;
-      const float x = __bfloat162float(hmask[(size_t)row * ldm + c]) > 0.f ? v[i] : 0.f;
-      if (du) {
-        du[(size_t)row * ldz + c] = x;
-      } else {
-        const bf16 o = __float2bfloat16_rn(x);
-        dz[(size_t)row * ldz + c] = o;
-        dzT[(size_t)c * ldt + row] = o;
-      }
-    }
-  }
-};
-
-// weight gradient: rows = output units, columns = inputs plus the ones column (bias)
-struct EpiBwdDW {
-  float* dW;
-  float* db;
-  int kin;
-  __device__ void operator()(int row, int col0, const float (&v)[32], int M, int N) const {
-    if (row >= M) return;
-    for (int i = 0; i < 32 && col0 + i < N; ++i) {
-      const int c = col0 + i;
-      if (c < kin) dW[(size_t)row * kin + c] = v[i];
-      else db[row] = v[i];
-    }
-  }
-};
-
-// weight gradient of the split first layer: columns 2k (hi) and 2k+1 (lo) both
-// multiply input k; column 2 kin is the ones column (bias)
-struct EpiBwdDW0 {
-  float* dW;
-  float* db;
-  int kin;
-  __device__ void operator()(int row, int col0, const float (&v)[32], int M, int N) const {
-    if (row >= M) return;
-#pragma unroll
-    for (int i = 0; i < 32; i += 2) {
-      const int c = col0 + i;
-      if (c + 1 < 2 * kin + 1 && c < 2 * kin) dW[(size_t)row * kin + c / 2] = v[i] + v[i + 1];
-      else if (c == 2 * kin) db[row] = v[i];
-    }
-  }
-};
-
-// input gradient of the first layer, columns [c0, c0 + nc) only
-struct EpiDX0 {
-  float* dx;
-  int c0, nc;
-  __device__ void operator()(int row, int col0, const float (&v)[32], int M, int N) const {
-    if (row >= M) return;
-    for (int i = 0; i < 32 && col0 + i < N; ++i) {
-      const int c = col0 + i - c0;
-      if (c >= 0 && c < nc) dx[(size_t)row * nc + c] = v[i];
-    }
-  }
-};
-
-// ---- launch ---------------------------------------------------------------------
-template <int BN, class Epi>
-void launch_gemm_bn(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, int nkA, const Epi& epi,
-                    unsigned* status, cudaStream_t st) {
-  using S = tc::GemmSmem<BN>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc::tc_gemm_kernel<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
-    attr = true;
-  }
-  dim3 grid(ceil_div(N, BN), ceil_div(M, tc::kBM));
-  tc::tc_gemm_kernel<BN, Epi><<<grid, 128, S::kBytes, st>>>(a, b, M, N, K, nkA, epi, status);
-}
-
-// BN 64 unless 128-wide tiles already fill the 152 SMs.
-// nkA > 0: the split-weight forward (K = 2 * 64 * nkA, see tc_gemm_kernel); the
-// traced work is the algorithmic 2 M N K of the unsplit product.
-template <class Epi>
-void tc_gemm(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, const Epi& epi, unsigned* status,
-             cudaStream_t st, int nkA = 0, int k_alg = -1) {
-  if (M <= 0 || N <= 0) return;
-  TraceLaunch tr(CRL_TRACE_GEMM, st, 2.0 * M * N * (k_alg >= 0 ? k_alg : K));
-  const long long ctas128 = (long long)ceil_div(M, 128) * ceil_div(N, 128);
-  if (ctas128 >= 148) launch_gemm_bn<128>(a, b, M, N, K, nkA, epi, status, st);
-  else launch_gemm_bn<64>(a, b, M, N, K, nkA, epi, status, st);
-}
-
 // ---- element kernels ----------------------------------------------------------------
 // 32 x 32 tile transpose-and-pack: src = concat(s0 [rows][n0], s1 [rows][n1]) (FP32)
 // -> dst [rows][ld] (BF16, optional) and dstT [n0 + n1][ldt] (BF16, optional).
 __global__ void __launch_bounds__(256) pack_kernel(int rows, const float* __restrict__ s0, int ld0, int n0,
                                                   const float* __restrict__ s1, int ld1, int n1, bf16* __restrict__ dst,
                                                   int ld, bf16* __restrict__ dstT, int ldt) {
+  pdl_enter();
   __shared__ float tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
@@ -206,6 +61,7 @@ __global__ void __launch_bounds__(256) pack_split_kernel(int rows, const float* 
                                                         const float* __restrict__ s1, int ld1, int n1,
                                                         bf16* __restrict__ dst, int ld, bf16* __restrict__ dstT,
                                                         int ldt) {
+  pdl_enter();
   __shared__ float tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
@@ -223,6 +79,7 @@ __global__ void __launch_bounds__(256) pack_split_kernel(int rows, const float* 
     }
   }
   __syncthreads();
+  if (!dstT) return;
   for (int c = ty; c < 32; c += 8) {
     const int col = c0 + c, row = r0 + tx;
     if (col < ncol && row < rows) {
@@ -241,6 +98,7 @@ __global__ void __launch_bounds__(256) pack_split_kernel(int rows, const float* 
 __global__ void __launch_bounds__(256) pack_weights_kernel(int rows, int ncol, int rep, const float* __restrict__ W,
                                                           bf16* __restrict__ W2, int kp, bf16* __restrict__ Wt,
                                                           int ldt) {
+  pdl_enter();
   __shared__ float tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
@@ -270,15 +128,29 @@ void pack(int rows, const float* s0, int ld0, int n0, const float* s1, int ld1, 
           int ldt, cudaStream_t st) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)rows * (n0 + n1) * (4.0 + (dst ? 2 : 0) + (dstT ? 2 : 0)));
   dim3 grid(ceil_div(n0 + n1, 32), ceil_div(rows, 32));
-  pack_kernel<<<grid, 256, 0, st>>>(rows, s0, ld0, n0, s1, ld1, n1, dst, ld, dstT, ldt);
+  launch_k(pack_kernel, grid, dim3(256), 0, st, rows, s0, ld0, n0, s1, ld1, n1, dst, ld, dstT, ldt);
 }
+
+// ---- LayerNorm (grouped over the networks of a pass: blockIdx.y = network) ----------
+struct LnFwdNet {
+  float* z;
+  float* rstd;
+  const float* g;
+  const float* beta;
+  bf16* h;
+  bf16* hT;
+};
+struct LnFwdGroup {
+  LnFwdNet n[kMaxGroupNets];
+};
 
 // LayerNorm forward over rows of z [M][H] (FP32, replaced by zhat), rstd [M],
 // h = ReLU(zhat * g + beta) written as BF16 [M][H] and, through a shared tile,
 // transposed [H][ldt].  Block = 32 rows (one warp each).
-__global__ void __launch_bounds__(1024) ln_fwd_kernel(int M, int H, float* __restrict__ z, float* __restrict__ rstd,
-                                                     const float* __restrict__ g, const float* __restrict__ beta,
-                                                     bf16* __restrict__ h, bf16* __restrict__ hT, int ldt) {
+__global__ void __launch_bounds__(1024) ln_fwd_kernel(int M, int H, int ldt, LnFwdGroup grp) {
+  pdl_enter();
+  const LnFwdNet& a = grp.n[blockIdx.y];
+  float* __restrict__ z = a.z;
   __shared__ float tile[32][33];
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   const int row = blockIdx.x * 32 + w;
@@ -294,7 +166,7 @@ __global__ void __launch_bounds__(1024) ln_fwd_kernel(int M, int H, float* __res
       q += d * d;
     }
     rs = rsqrtf(warp_sum(q) / H + kLnEpsF);
-    if (lane == 0) rstd[row] = rs;
+    if (lane == 0) a.rstd[row] = rs;
   }
   for (int c0 = 0; c0 < H; c0 += 32) {
     const int c = c0 + lane;
@@ -303,24 +175,40 @@ __global__ void __launch_bounds__(1024) ln_fwd_kernel(int M, int H, float* __res
       const size_t o = (size_t)row * H + c;
       const float zh = (z[o] - mean) * rs;
       z[o] = zh;
-      hv = fmaxf(zh * g[c] + beta[c], 0.f);
-      h[o] = __float2bfloat16_rn(hv);
+      hv = fmaxf(zh * a.g[c] + a.beta[c], 0.f);
+      a.h[o] = __float2bfloat16_rn(hv);
     }
     tile[w][lane] = hv;
     __syncthreads();
     // warp w writes column c0 + w for the block's 32 rows
     const int cc = c0 + w, rr = blockIdx.x * 32 + lane;
-    if (cc < H && rr < M) hT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
+    if (cc < H && rr < M) a.hT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
     __syncthreads();
   }
 }
 
+struct LnBwdNet {
+  const float* du;
+  const float* zhat;
+  const float* rstd;
+  const float* g;
+  bf16* dz;
+  bf16* dzT;
+  float* dg;   // ln_param_grad_kernel only
+  float* db;
+};
+struct LnBwdGroup {
+  LnBwdNet n[kMaxGroupNets];
+};
+
 // LayerNorm backward: du (ReLU-masked, FP32) -> dz = rstd (g du - mean(g du) - zhat mean(g du zhat)),
 // written BF16 [M][H] and transposed.  Block = 32 rows.
-__global__ void __launch_bounds__(1024) ln_bwd_kernel(int M, int H, const float* __restrict__ du,
-                                                     const float* __restrict__ zhat, const float* __restrict__ rstd,
-                                                     const float* __restrict__ g, bf16* __restrict__ dz,
-                                                     bf16* __restrict__ dzT, int ldt) {
+__global__ void __launch_bounds__(1024) ln_bwd_kernel(int M, int H, int ldt, LnBwdGroup grp) {
+  pdl_enter();
+  const LnBwdNet& a = grp.n[blockIdx.y];
+  const float* __restrict__ du = a.du;
+  const float* __restrict__ zhat = a.zhat;
+  const float* __restrict__ g = a.g;
   __shared__ float tile[32][33];
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   const int row = blockIdx.x * 32 + w;
@@ -334,7 +222,7 @@ __global__ void __launch_bounds__(1024) ln_bwd_kernel(int M, int H, const float*
     }
     s1 = warp_sum(s1) / H;
     s2 = warp_sum(s2) / H;
-    rs = rstd[row];
+    rs = a.rstd[row];
   }
   for (int c0 = 0; c0 < H; c0 += 32) {
     const int c = c0 + lane;
@@ -342,20 +230,22 @@ __global__ void __launch_bounds__(1024) ln_bwd_kernel(int M, int H, const float*
     if (row < M && c < H) {
       const size_t o = (size_t)row * H + c;
       v = rs * (du[o] * g[c] - s1 - zhat[o] * s2);
-      dz[o] = __float2bfloat16_rn(v);
+      a.dz[o] = __float2bfloat16_rn(v);
     }
     tile[w][lane] = v;
     __syncthreads();
     const int cc = c0 + w, rr = blockIdx.x * 32 + lane;
-    if (cc < H && rr < M) dzT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
+    if (cc < H && rr < M) a.dzT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
     __syncthreads();
   }
 }
 
 // dgain[n] = sum_m du * zhat, dbeta[n] = sum_m du.  Block = 32 columns x 8 row groups.
-__global__ void __launch_bounds__(256) ln_param_grad_kernel(int M, int H, const float* __restrict__ du,
-                                                           const float* __restrict__ zhat, float* __restrict__ dg,
-                                                           float* __restrict__ db) {
+__global__ void __launch_bounds__(256) ln_param_grad_kernel(int M, int H, LnBwdGroup grp) {
+  pdl_enter();
+  const LnBwdNet& p = grp.n[blockIdx.y];
+  const float* __restrict__ du = p.du;
+  const float* __restrict__ zhat = p.zhat;
   __shared__ float sa[8][33], sb[8][33];
   const int cx = threadIdx.x % 32, ry = threadIdx.x / 32;
   const int n = blockIdx.x * 32 + cx;
@@ -375,8 +265,8 @@ __global__ void __launch_bounds__(256) ln_param_grad_kernel(int M, int H, const 
       a += sa[r][cx];
       b += sb[r][cx];
     }
-    dg[n] = a;
-    db[n] = b;
+    p.dg[n] = a;
+    p.db[n] = b;
   }
 }
 
@@ -391,7 +281,123 @@ const char* mk(CUtensorMap* m, const void* base, int inner, int rows, int stride
   return nullptr;
 }
 
+
+
+uint64_t fnv1a(const void* data, size_t n) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+tc::EpiDesc epi_of(int kind) {
+  tc::EpiDesc e;
+  memset(&e, 0, sizeof(e));
+  e.kind = kind;
+  return e;
+}
+
+tc::GemmProblem problem(const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K, int nkA,
+                        const tc::EpiDesc& e) {
+  tc::GemmProblem p;
+  memset(&p, 0, sizeof(p));
+  p.a = a;
+  p.b = b;
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  p.nkA = nkA;
+  p.epi = e;
+  return p;
+}
+
+template <int BN>
+void launch_gemm_bn(const tc::GemmProblem* table, int nprob, int tiles, unsigned* status, cudaStream_t st) {
+  using S = tc::GemmSmem<BN>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc::tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+    attr = true;
+  }
+  launch_k(tc::tc_gemm_kernel<BN>, dim3(tiles), dim3(128), S::kBytes, st, table, nprob, status);
+}
+
+// One grouped launch of `probs`: 128 x 64 tiles unless 128 x 128 tiles already
+// fill the 152 SMs.  `flops` is the algorithmic work (2 M N K of the unsplit
+// products) for tracing.
+const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, double flops, unsigned* status,
+                         cudaStream_t st) {
+  if (probs.empty()) return nullptr;
+  long long ctas128 = 0;
+  for (const auto& p : probs) ctas128 += (long long)ceil_div(p.M, 128) * ceil_div(p.N, 128);
+  const int BN = ctas128 >= 148 ? 128 : 64;
+  int tiles = 0;
+  const char* err = nullptr;
+  const tc::GemmProblem* t = gg.table(probs, BN, &tiles, st, &err);
+  if (!t) return err;
+  if (tiles == 0) return nullptr;
+  TraceLaunch tr(CRL_TRACE_GEMM, st, flops);
+  if (BN == 128) launch_gemm_bn<128>(t, (int)probs.size(), tiles, status, st);
+  else launch_gemm_bn<64>(t, (int)probs.size(), tiles, status, st);
+  return nullptr;
+}
+
 }  // namespace
+
+const tc::GemmProblem* GemmGroups::table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles,
+                                         cudaStream_t st, const char** err) {
+  int tiles = 0;
+  for (auto& p : probs) {
+    p.tiles_n = ceil_div(p.N, BN);
+    p.tile_begin = tiles;
+    tiles += ceil_div(p.M, tc::kBM) * p.tiles_n;
+  }
+  *total_tiles = tiles;
+  const size_t bytes = probs.size() * sizeof(tc::GemmProblem);
+  const uint64_t h = fnv1a(probs.data(), bytes);
+  auto it = map_.find(h);
+  if (it != map_.end()) {
+    for (const Entry& e : it->second)
+      if (e.host.size() == probs.size() && memcmp(e.host.data(), probs.data(), bytes) == 0) return e.dev;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    *err = "a grouped-GEMM problem table was first needed while the stream was being captured";
+    return nullptr;
+  }
+  const int n = (int)probs.size();
+  if (used_ + n > cap_) {
+    const int cap = std::max(256, n);
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, (size_t)cap * sizeof(tc::GemmProblem)) != cudaSuccess) {
+      *err = "device allocation of a grouped-GEMM problem table failed";
+      return nullptr;
+    }
+    chunks_.push_back(mem);
+    cur_ = static_cast<tc::GemmProblem*>(mem);
+    used_ = 0;
+    cap_ = cap;
+  }
+  tc::GemmProblem* dev = cur_ + used_;
+  if (cudaMemcpy(dev, probs.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    *err = "copying a grouped-GEMM problem table failed";
+    return nullptr;
+  }
+  used_ += n;
+  map_[h].push_back(Entry{dev, tiles, probs});
+  return dev;
+}
+
+void GemmGroups::reset() {
+  for (void* p : chunks_) cudaFree(p);
+  chunks_.clear();
+  map_.clear();
+  cur_ = nullptr;
+  used_ = cap_ = 0;
+}
 
 const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner) {
   n.s = s;
@@ -435,15 +441,14 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
     }
   }
   n.y = static_cast<float*>(A((size_t)Mmax * out * 4));
-  const int wmax = std::max(H, pad8(out));
-  for (int b = 0; b < 2; ++b) {
-    n.dz[b] = static_cast<bf16*>(A((size_t)Mmax * wmax * 2));
-    n.dzT[b] = static_cast<bf16*>(A((size_t)wmax * Mmax * 2));
+  for (int l = 0; l <= s.layers; ++l) {
+    const size_t w = (l == s.layers) ? (size_t)pad8(out) : (size_t)H;
+    n.dz[l] = static_cast<bf16*>(A((size_t)Mmax * w * 2));
+    n.dzT[l] = static_cast<bf16*>(A(w * Mmax * 2));
+    if (cudaMemset(n.dz[l], 0, (size_t)Mmax * w * 2) != cudaSuccess) return "cudaMemset failed";
   }
   if (s.layernorm) n.du = static_cast<float*>(A((size_t)Mmax * H * 4));
   if (cudaMemset(n.x0, 0, (size_t)Mmax * pad8(2 * in) * 2) != cudaSuccess) return "cudaMemset failed";
-  for (int b = 0; b < 2; ++b)
-    if (cudaMemset(n.dz[b], 0, (size_t)Mmax * wmax * 2) != cudaSuccess) return "cudaMemset failed";
   // the ones rows of the transposed activations (never overwritten)
   fill_bf16_kernel<<<ceil_div(Mmax, 256), 256>>>(n.x0T + (size_t)(2 * in) * Mmax, Mmax, 1.f);
   for (int l = 0; l < s.layers; ++l) fill_bf16_kernel<<<ceil_div(Mmax, 256), 256>>>(n.hT[l] + (size_t)H * Mmax, Mmax, 1.f);
@@ -461,12 +466,11 @@ const char* bf_net_maps(BfNet& n, int M) {
     if ((e = mk(&n.tm_hA[l], n.h[l], H, M, H))) return e;
     if ((e = mk(&n.tm_hTB[l], n.hT[l], M, H + 1, Mx))) return e;
   }
-  // dz[0] doubles as dy of the output layer (ld out_pad); both buffers serve the hidden layers (ld H)
-  if ((e = mk(&n.tm_dzA[0], n.dz[0], H, M, H))) return e;
-  if ((e = mk(&n.tm_dzA[1], n.dz[1], H, M, H))) return e;
-  if ((e = mk(&n.tm_dzTA[0], n.dzT[0], M, H, Mx))) return e;
-  if ((e = mk(&n.tm_dzTA[1], n.dzT[1], M, H, Mx))) return e;
-  (void)out;
+  for (int l = 0; l <= n.layers; ++l) {
+    const int width = (l == n.layers) ? out : H, ld = (l == n.layers) ? pad8(out) : H;
+    if ((e = mk(&n.tm_dzA[l], n.dz[l], width, M, ld))) return e;
+    if ((e = mk(&n.tm_dzTA[l], n.dzT[l], M, width, Mx))) return e;
+  }
   n.tm_M = M;
   return nullptr;
 }
@@ -476,7 +480,8 @@ void bf_net_shadow(BfNet& n, const float* params, cudaStream_t st) {
     BfLayer& L = n.L[l];
     TraceLaunch tr(CRL_TRACE_AUX, st, (double)L.out * L.in * 10.0);
     dim3 grid(ceil_div(L.in, 32), ceil_div(L.out, 32));
-    pack_weights_kernel<<<grid, 256, 0, st>>>(L.out, L.in, l == 0 ? 2 : 1, params + L.oW, L.W, L.kp, L.Wt, L.out_pad);
+    launch_k(pack_weights_kernel, grid, dim3(256), 0, st, L.out, L.in, l == 0 ? 2 : 1, params + L.oW, L.W, L.kp,
+             L.Wt, L.out_pad);
   }
 }
 
@@ -486,80 +491,146 @@ void bf_net_pack_input(BfNet& n, const float* x0, const float* x1, int M, cudaSt
   const int in = n.s.in();
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)M * in * 12.0);
   dim3 grid(ceil_div(in, 32), ceil_div(M, 32));
-  pack_split_kernel<<<grid, 256, 0, st>>>(M, x0, n.s.in0, n.s.in0, x1, n.s.in1, n.s.in1, n.x0, pad8(2 * in), n.x0T,
-                                          n.Mmax);
+  launch_k(pack_split_kernel, grid, dim3(256), 0, st, M, x0, n.s.in0, n.s.in0, x1, n.s.in1, n.s.in1, n.x0,
+           pad8(2 * in), n.x0T, n.Mmax);
 }
 
 void bf_net_load_dy(BfNet& n, const float* dy, int M, cudaStream_t st) {
   const int out = n.s.out;
-  pack(M, dy, out, out, nullptr, 0, 0, n.dz[0], pad8(out), n.dzT[0], n.Mmax, st);
+  pack(M, dy, out, out, nullptr, 0, 0, n.dz[n.layers], pad8(out), n.dzT[n.layers], n.Mmax, st);
 }
 
-void bf_net_forward(BfNet& n, const float* params, int M, unsigned* status, cudaStream_t st) {
-  const int H = n.s.hidden;
-  const CUtensorMap* A = &n.tm_x0A;
-  for (int l = 0; l < n.layers; ++l) {
-    const BfLayer& L = n.L[l];
-    if (n.s.layernorm) {
-      tc_gemm(*A, L.tmW, M, H, 2 * L.kp, EpiFwdPreLN{params + L.ob, n.z[l], H}, status, st, L.kp / 64, L.in);
-      TraceLaunch tr(CRL_TRACE_AUX, st, (double)M * H * 12.0);
-      ln_fwd_kernel<<<ceil_div(M, 32), 1024, 0, st>>>(M, H, n.z[l], n.rstd[l], params + L.og, params + L.obeta,
-                                                     n.h[l], n.hT[l], n.Mmax);
-    } else {
-      tc_gemm(*A, L.tmW, M, H, 2 * L.kp, EpiFwdHidden{params + L.ob, n.h[l], H, n.hT[l], n.Mmax}, status, st,
-              L.kp / 64, L.in);
+const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, int M, unsigned* status, cudaStream_t st) {
+  if (M <= 0 || count <= 0) return nullptr;
+  if (count > kMaxGroupNets) return "too many networks in one grouped pass";
+  const BfNet& n0 = *nets[0].net;
+  const int H = n0.s.hidden, layers = n0.layers;
+  const bool ln = n0.s.layernorm != 0;
+  std::vector<tc::GemmProblem> probs;
+  for (int l = 0; l <= layers; ++l) {
+    probs.clear();
+    double flops = 0.0;
+    for (int k = 0; k < count; ++k) {
+      BfNet& n = *nets[k].net;
+      const BfLayer& L = n.L[l];
+      const float* params = nets[k].params;
+      const CUtensorMap& A = (l == 0) ? n.tm_x0A : n.tm_hA[l - 1];
+      tc::EpiDesc e;
+      if (l == layers) {
+        e = epi_of(tc::kEpiFwdOut);
+        e.ld0 = L.out;
+        e.out0 = n.y;
+      } else if (ln) {
+        e = epi_of(tc::kEpiFwdPreLN);
+        e.ld0 = H;
+        e.out0 = n.z[l];
+      } else {
+        e = epi_of(tc::kEpiFwdHidden);
+        e.ld0 = H;
+        e.out0 = n.h[l];
+        e.ld1 = n.Mmax;
+        e.out1 = n.hT[l];
+      }
+      e.bias = params + L.ob;
+      probs.push_back(problem(A, L.tmW, M, L.out, 2 * L.kp, L.kp / 64, e));
+      flops += 2.0 * M * L.out * L.in;
     }
-    A = &n.tm_hA[l];
+    if (const char* err = launch_group(gg, probs, flops, status, st)) return err;
+    if (l < layers && ln) {
+      LnFwdGroup grp;
+      memset(&grp, 0, sizeof(grp));
+      for (int k = 0; k < count; ++k) {
+        BfNet& n = *nets[k].net;
+        const BfLayer& L = n.L[l];
+        grp.n[k] = LnFwdNet{n.z[l], n.rstd[l], nets[k].params + L.og, nets[k].params + L.obeta, n.h[l], n.hT[l]};
+      }
+      TraceLaunch tr(CRL_TRACE_AUX, st, (double)count * M * H * 12.0);
+      launch_k(ln_fwd_kernel, dim3(ceil_div(M, 32), count), dim3(1024), 0, st, M, H, n0.Mmax, grp);
+    }
   }
-  const BfLayer& O = n.L[n.layers];
-  tc_gemm(*A, O.tmW, M, O.out, 2 * O.kp, EpiFwdOut{params + O.ob, n.y, O.out}, status, st, O.kp / 64, O.in);
+  return nullptr;
 }
 
-void bf_net_backward(BfNet& n, const float* params, int M, float* grads, float* dx1, unsigned* status,
-                     cudaStream_t st) {
-  const int H = n.s.hidden;
-  // maps of the output-layer gradient dy (dz[0] with row stride out_pad)
-  const BfLayer& O = n.L[n.layers];
-  CUtensorMap tm_dyA, tm_dyTA;
-  mk(&tm_dyA, n.dz[0], O.out, M, O.out_pad);
-  mk(&tm_dyTA, n.dzT[0], M, O.out, n.Mmax);
-  const CUtensorMap* curA = &tm_dyA;
-  const CUtensorMap* curT = &tm_dyTA;
-  int nout = O.out;
-  int b = 1;  // next dz buffer to write
-  for (int l = n.layers; l >= 0; --l) {
-    const BfLayer& L = n.L[l];
-    if (grads) {
-      if (l == 0)
-        tc_gemm(*curT, n.tm_x0TB, nout, 2 * L.in + 1, M, EpiBwdDW0{grads + L.oW, grads + L.ob, L.in}, status, st);
-      else
-        tc_gemm(*curT, n.tm_hTB[l - 1], nout, L.in + 1, M, EpiBwdDW{grads + L.oW, grads + L.ob, L.in}, status, st);
-    }
-    if (l == 0) {
-      if (dx1) tc_gemm(*curA, L.tmWt, M, L.in, nout, EpiDX0{dx1, n.s.in0, n.s.in1}, status, st);
-      break;
-    }
-    const BfLayer& P = n.L[l - 1];
-    if (n.s.layernorm) {
-      tc_gemm(*curA, L.tmWt, M, H, nout, EpiBwdDX{n.h[l - 1], H, nullptr, H, nullptr, 0, n.du}, status, st);
-      {
-        TraceLaunch tr(CRL_TRACE_AUX, st, (double)M * H * 16.0);
-        ln_bwd_kernel<<<ceil_div(M, 32), 1024, 0, st>>>(M, H, n.du, n.z[l - 1], n.rstd[l - 1], params + P.og,
-                                                       n.dz[b], n.dzT[b], n.Mmax);
+const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, int M, unsigned* status, cudaStream_t st) {
+  if (M <= 0 || count <= 0) return nullptr;
+  if (count > kMaxGroupNets) return "too many networks in one grouped pass";
+  const BfNet& n0 = *nets[0].net;
+  const int H = n0.s.hidden, layers = n0.layers;
+  const bool ln = n0.s.layernorm != 0;
+  std::vector<tc::GemmProblem> probs;
+  // input-gradient chain: dz[l] -> dz[l - 1]
+  for (int l = layers; l >= 1; --l) {
+    probs.clear();
+    double flops = 0.0;
+    for (int k = 0; k < count; ++k) {
+      BfNet& n = *nets[k].net;
+      const BfLayer& L = n.L[l];
+      tc::EpiDesc e = epi_of(ln ? tc::kEpiBwdDXLN : tc::kEpiBwdDX);
+      e.mask = n.h[l - 1];
+      e.ldm = H;
+      e.ld0 = H;
+      if (ln) {
+        e.out0 = n.du;
+      } else {
+        e.out0 = n.dz[l - 1];
+        e.out1 = n.dzT[l - 1];
+        e.ld1 = n.Mmax;
       }
-      if (grads) {
-        TraceLaunch tr(CRL_TRACE_AUX, st, (double)M * H * 8.0);
-        ln_param_grad_kernel<<<ceil_div(H, 32), 256, 0, st>>>(M, H, n.du, n.z[l - 1], grads + P.og,
-                                                              grads + P.obeta);
-      }
-    } else {
-      tc_gemm(*curA, L.tmWt, M, H, nout, EpiBwdDX{n.h[l - 1], H, n.dz[b], H, n.dzT[b], n.Mmax, nullptr}, status, st);
+      probs.push_back(problem(n.tm_dzA[l], L.tmWt, M, H, L.out, 0, e));
+      flops += 2.0 * M * H * L.out;
     }
-    curA = &n.tm_dzA[b];
-    curT = &n.tm_dzTA[b];
-    nout = H;
-    b ^= 1;
+    if (const char* err = launch_group(gg, probs, flops, status, st)) return err;
+    if (ln) {
+      LnBwdGroup grp, pg;
+      memset(&grp, 0, sizeof(grp));
+      memset(&pg, 0, sizeof(pg));
+      int np = 0;
+      for (int k = 0; k < count; ++k) {
+        BfNet& n = *nets[k].net;
+        const BfLayer& P = n.L[l - 1];
+        const LnBwdNet b{n.du, n.z[l - 1], n.rstd[l - 1], nets[k].params + P.og, n.dz[l - 1], n.dzT[l - 1],
+                         nets[k].grads ? nets[k].grads + P.og : nullptr,
+                         nets[k].grads ? nets[k].grads + P.obeta : nullptr};
+        grp.n[k] = b;
+        if (nets[k].grads) pg.n[np++] = b;
+      }
+      // the parameter gradients read du before the next layer's launch overwrites it
+      if (np > 0) {
+        TraceLaunch tr(CRL_TRACE_AUX, st, (double)np * M * H * 8.0);
+        launch_k(ln_param_grad_kernel, dim3(ceil_div(H, 32), np), dim3(256), 0, st, M, H, pg);
+      }
+      TraceLaunch tr(CRL_TRACE_AUX, st, (double)count * M * H * 16.0);
+      launch_k(ln_bwd_kernel, dim3(ceil_div(M, 32), count), dim3(1024), 0, st, M, H, n0.Mmax, grp);
+    }
   }
+  // every weight gradient, and the first-layer input gradients, in one launch
+  probs.clear();
+  double flops = 0.0;
+  for (int k = 0; k < count; ++k) {
+    BfNet& n = *nets[k].net;
+    if (float* grads = nets[k].grads) {
+      for (int l = 0; l <= layers; ++l) {
+        const BfLayer& L = n.L[l];
+        tc::EpiDesc e = epi_of(l == 0 ? tc::kEpiBwdDW0 : tc::kEpiBwdDW);
+        e.kin = L.in;
+        e.out0 = grads + L.oW;
+        e.out1 = grads + L.ob;
+        if (l == 0) probs.push_back(problem(n.tm_dzTA[0], n.tm_x0TB, L.out, 2 * L.in + 1, M, 0, e));
+        else probs.push_back(problem(n.tm_dzTA[l], n.tm_hTB[l - 1], L.out, L.in + 1, M, 0, e));
+        flops += 2.0 * L.out * (L.in + 1) * M;
+      }
+    }
+    if (nets[k].dx1) {
+      const BfLayer& L = n.L[0];
+      tc::EpiDesc e = epi_of(tc::kEpiDX0);
+      e.out0 = nets[k].dx1;
+      e.c0 = n.s.in0;
+      e.nc = n.s.in1;
+      probs.push_back(problem(n.tm_dzA[0], L.tmWt, M, L.in, L.out, 0, e));
+      flops += 2.0 * M * L.in * L.out;
+    }
+  }
+  return launch_group(gg, probs, flops, status, st);
 }
 
 namespace {
@@ -588,6 +659,7 @@ struct AdamPair {
 };
 
 __global__ void __launch_bounds__(256) adam_shadow_kernel(AdamPair ap) {
+  pdl_enter();
   __shared__ float s_corr[2][2];
   if (threadIdx.x < ap.count) {
     const AdamNetDev& a = ap.a[threadIdx.x];
@@ -656,7 +728,7 @@ void adam_shadow_update(const AdamShadowNet* nets, int count, float b1, float b2
   }
   TraceLaunch tr(CRL_TRACE_ADAM, st, 28.0 * ntot);
   const int blocks = (int)std::min<long long>((ntot + 255) / 256, 152 * 8);
-  adam_shadow_kernel<<<blocks, 256, 0, st>>>(ap);
+  launch_k(adam_shadow_kernel, dim3(blocks), dim3(256), 0, st, ap);
 }
 
 }  // namespace crl

@@ -25,14 +25,24 @@
 // BF16 shadows Wt [in][out] (its rounding hardly moves the gradient).
 // The backward epilogue likewise writes dz and dz^T.  The shadows are refreshed
 // from the FP32 master weights before each step.
+//
+// The same layer of several networks (phi and psi; pi and psi) runs as one
+// grouped launch, and the weight gradients of all layers run as one launch
+// after the input-gradient chain (they are off its critical path).
 #pragma once
 
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <unordered_map>
+#include <vector>
+
 #include "internal.h"
+#include "tc_gemm.cuh"
 
 namespace crl {
+
+constexpr int kMaxGroupNets = 4;
 
 struct BfLayer {
   int in, out, in_pad, out_pad;   // pads: multiples of 8 (16-byte rows)
@@ -58,15 +68,47 @@ struct BfNet {
   float* z[CRL_MAX_LAYERS] = {};           // LayerNorm: pre-norm [Mmax][H], then zhat in place
   float* rstd[CRL_MAX_LAYERS] = {};        // LayerNorm: [Mmax]
   float* y = nullptr;                      // [Mmax][out] output (FP32)
-  // backward
-  __nv_bfloat16* dz[2] = {};               // [Mmax][max(H, out_pad)]
-  __nv_bfloat16* dzT[2] = {};              // [max(H, out)][Mmax]
+  // backward: dz[l] = gradient at the output of layer l (pre-activation of a
+  // hidden layer, y for l = layers), BF16 [Mmax][ld] with ld = H (hidden) or
+  // out_pad (output), and transposed [width][Mmax]
+  __nv_bfloat16* dz[CRL_MAX_LAYERS + 1] = {};
+  __nv_bfloat16* dzT[CRL_MAX_LAYERS + 1] = {};
   float* du = nullptr;                     // LayerNorm backward input [Mmax][H]
   // tensor maps, built for the batch size M of the last call
   int tm_M = -1;
   CUtensorMap tm_x0A, tm_x0TB;
   CUtensorMap tm_hA[CRL_MAX_LAYERS], tm_hTB[CRL_MAX_LAYERS];
-  CUtensorMap tm_dzA[2], tm_dzTA[2];
+  CUtensorMap tm_dzA[CRL_MAX_LAYERS + 1], tm_dzTA[CRL_MAX_LAYERS + 1];
+};
+
+// Device problem tables of the grouped GEMM, one per distinct list of problems
+// (keyed by content: tensor maps, sizes and epilogue pointers).  A table is
+// written once, before its first launch, and never changed, so a captured
+// CUDA graph may keep replaying it.  Building a table is a synchronous copy:
+// it must not happen while the stream is being captured.
+class GemmGroups {
+ public:
+  GemmGroups() = default;
+  GemmGroups(const GemmGroups&) = delete;
+  GemmGroups& operator=(const GemmGroups&) = delete;
+  ~GemmGroups() { reset(); }
+  // Fills tiles_n / tile_begin of `probs` for tile width BN and returns the
+  // device table; nullptr (and *err) on failure.
+  const tc::GemmProblem* table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles, cudaStream_t st,
+                               const char** err);
+  // Frees every table (synchronises the device).
+  void reset();
+
+ private:
+  struct Entry {
+    const tc::GemmProblem* dev;
+    int tiles;
+    std::vector<tc::GemmProblem> host;
+  };
+  std::unordered_map<uint64_t, std::vector<Entry>> map_;
+  std::vector<void*> chunks_;
+  tc::GemmProblem* cur_ = nullptr;
+  int used_ = 0, cap_ = 0;
 };
 
 // Allocates the network's BF16 buffers (cudaMalloc through `alloc`) and writes the ones rows.
@@ -81,15 +123,23 @@ void bf_net_shadow(BfNet& n, const float* params, cudaStream_t st);
 int bf_net_x0_ld(const BfNet& n);
 // Pack the FP32 input concat(x0 [M][in0], x1 [M][in1]) into x0 / x0T.
 void bf_net_pack_input(BfNet& n, const float* x0, const float* x1, int M, cudaStream_t st);
-// Forward: y [M][out] FP32 (n.y).  Optionally also writes a BF16 copy of y.
-void bf_net_forward(BfNet& n, const float* params, int M, unsigned* status, cudaStream_t st);
-// Backward from dy (BF16 [M][out_pad] and dy^T [out][M], in n.dz[0] / n.dzT[0]):
-// writes FP32 grads (flat layout) when `grads` is non-null, and the FP32
-// gradient of the input columns [in0, in0 + in1) into dx1 [M][in1] when non-null.
-void bf_net_backward(BfNet& n, const float* params, int M, float* grads, float* dx1, unsigned* status,
-                     cudaStream_t st);
-// Store an FP32 gradient dy [M][out] into n.dz[0] / n.dzT[0] (BF16, both layouts).
+// Store an FP32 gradient dy [M][out] into dz[layers] / dzT[layers] (BF16, both layouts).
 void bf_net_load_dy(BfNet& n, const float* dy, int M, cudaStream_t st);
+
+// One network of a grouped pass.  All networks of a group have the same
+// number of layers and the same hidden width and LayerNorm setting.
+struct BfPass {
+  BfNet* net;
+  const float* params;
+  float* grads;   // backward: FP32 gradients in the flat layout, or null (no weight gradients)
+  float* dx1;     // backward: FP32 gradient of input columns [in0, in0 + in1) as [M][in1], or null
+};
+// Forward of `count` networks (one grouped launch per layer): y [M][out] FP32 in net->y.
+const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, int M, unsigned* status, cudaStream_t st);
+// Backward of `count` networks from their dz[layers] / dzT[layers]: one grouped
+// input-gradient launch per hidden layer, then one launch with every weight
+// gradient and first-layer input gradient.
+const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, int M, unsigned* status, cudaStream_t st);
 
 // Adam on the FP32 master parameters of up to two networks in one launch, also
 // refreshing each network's BF16 shadows (W_hi / W_lo and Wt) from the updated

@@ -1,18 +1,29 @@
-// BF16 tensor-core GEMM on tcgen05 with TMEM accumulators and TMA operand loads:
+// Grouped BF16 tensor-core GEMM on tcgen05 with TMEM accumulators and TMA
+// operand loads.  One launch runs a list of independent problems
 //
-//   C(m, n) = epilogue(m, n, sum_k A[m][k] * B[n][k])      A, B: BF16, K-major
+//   C_p(m, n) = epilogue_p(m, n, sum_k A_p[m][k] * B_p[n][k])      A, B: BF16, K-major
 //
-// One CTA computes a 128 x BN tile (BN in {64, 128, 256}); 128 threads:
+// (the same layer of several networks, or all weight gradients of a network),
+// each split into 128 x BN tiles; CTA t finds its problem by a binary search of
+// the tiles' prefix sums in the problem table.  The table (tensor maps,
+// sizes, epilogue descriptor) lives in device memory and is never written
+// while kernels run.
+//
+// One CTA computes one 128 x BN tile (BN in {64, 128}); 128 threads:
 //   warp 0 / lane 0 -- TMA producer: 64-wide K slices of A and B (as 64-row
 //                      boxes: every tensor map has box {64, 64}) into a
 //                      4-stage shared-memory ring (128-byte swizzle);
 //   warp 1 / lane 0 -- MMA issuer: 4 x tcgen05.mma (K = 16 each) per slice
 //                      into the FP32 accumulator in TMEM (128 lanes x BN cols);
 //   all 4 warps     -- epilogue: warp w reads TMEM lanes 32w..32w+31 (rows)
-//                      in chunks of 32 columns and hands them to the functor.
+//                      in chunks of 32 columns and applies the problem's
+//                      epilogue (vectorised row stores, coalesced transposed
+//                      stores).
 // Out-of-range rows and columns of the operands are zero-filled by TMA; the
-// epilogue functor clips its stores to M x N.
+// epilogue clips its stores to M x N.
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "tc_common.cuh"
@@ -23,6 +34,33 @@ namespace tc {
 constexpr int kBM = 128;
 constexpr int kBK = 64;
 constexpr int kStages = 4;
+
+// What the FP32 accumulator tile of a problem becomes.
+enum EpiKind : int {
+  kEpiFwdHidden = 0,  // h = ReLU(acc + b): BF16 h [M][ld0] and h^T [N][ld1]
+  kEpiFwdPreLN = 1,   // z = acc + b: FP32 [M][ld0] (LayerNorm follows)
+  kEpiFwdOut = 2,     // y = acc + b: FP32 [M][ld0]
+  kEpiBwdDX = 3,      // dz = acc * [mask > 0]: BF16 dz [M][ld0] and dz^T [N][ld1]
+  kEpiBwdDXLN = 4,    // du = acc * [mask > 0]: FP32 [M][ld0]
+  kEpiBwdDW = 5,      // dW [M][kin] (columns < kin), db [M] (column kin: the ones row)
+  kEpiBwdDW0 = 6,     // split first layer: dW[m][c] = acc[2c] + acc[2c+1], db[m] = acc[2 kin]
+  kEpiDX0 = 7,        // dx [M][nc] = acc columns [c0, c0 + nc)
+};
+
+struct EpiDesc {
+  int kind, ld0, ld1, kin, c0, nc, ldm, pad;
+  const float* bias;
+  const __nv_bfloat16* mask;  // [M][ldm], BF16 post-ReLU activation (> 0 where the unit is active)
+  void* out0;
+  void* out1;
+};
+
+struct alignas(64) GemmProblem {
+  CUtensorMap a, b;
+  int M, N, K, nkA;   // nkA > 0: split-weight product (see tc_gemm_kernel)
+  int tiles_n, tile_begin, pad0, pad1;
+  EpiDesc epi;
+};
 
 template <int BN>
 struct GemmSmem {
@@ -35,12 +73,178 @@ struct GemmSmem {
   static_assert(BN % 64 == 0 && BN <= 256, "BN must be 64, 128 or 256");
 };
 
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
+               : "memory");
+}
+
+// 32 BF16 values -> four 16-byte stores (dst 16-byte aligned)
+__device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float (&x)[32]) {
+  uint32_t w[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+    w[i] = *reinterpret_cast<const uint32_t*>(&p);
+  }
+  uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) d[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+}
+__device__ __forceinline__ void store_f32x32(float* dst, const float (&x)[32]) {
+  float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) d[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+}
+__device__ __forceinline__ void load_bias32(const float* b, float (&x)[32]) {
+  const float4* s = reinterpret_cast<const float4*>(b);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 t = __ldg(s + q);
+    x[4 * q] = t.x;
+    x[4 * q + 1] = t.y;
+    x[4 * q + 2] = t.z;
+    x[4 * q + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void load_mask32(const __nv_bfloat16* m, bool (&on)[32]) {
+  const uint4* s = reinterpret_cast<const uint4*>(m);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint4 t = s[q];
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 p = *reinterpret_cast<const __nv_bfloat162*>(&w[j]);
+      on[8 * q + 2 * j] = __low2float(p) > 0.f;
+      on[8 * q + 2 * j + 1] = __high2float(p) > 0.f;
+    }
+  }
+}
+
+// Epilogue of one 32-column chunk (columns col0 .. col0 + 31) of row `row`.
+// The full-chunk paths use 16-byte accesses; they need 16-byte aligned rows:
+// leading dimensions a multiple of 8 BF16 / 4 FP32 elements (hidden widths
+// are multiples of 8; other widths are tested here) and 16-byte aligned base
+// pointers (library buffers come from cudaMalloc; crl_bind_params rejects
+// parameter and gradient arrays that are not 16-byte aligned).
+__device__ __forceinline__ void epilogue_chunk(const EpiDesc& e, int row, int col0, float (&v)[32], int M, int N) {
+  if (row >= M) return;
+  const bool full = col0 + 32 <= N;
+  using bf16 = __nv_bfloat16;
+  switch (e.kind) {
+    case kEpiFwdHidden: {
+      bf16* h = static_cast<bf16*>(e.out0);
+      bf16* hT = static_cast<bf16*>(e.out1);
+      if (full) {
+        float b[32];
+        load_bias32(e.bias + col0, b);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + b[i], 0.f);
+        store_bf16x32(h + (size_t)row * e.ld0 + col0, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) hT[(size_t)(col0 + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          if (col0 + i >= N) break;
+          const bf16 o = __float2bfloat16_rn(fmaxf(v[i] + e.bias[col0 + i], 0.f));
+          h[(size_t)row * e.ld0 + col0 + i] = o;
+          hT[(size_t)(col0 + i) * e.ld1 + row] = o;
+        }
+      }
+      break;
+    }
+    case kEpiFwdPreLN:
+    case kEpiFwdOut: {
+      float* z = static_cast<float*>(e.out0) + (size_t)row * e.ld0;
+      if (full && (e.ld0 & 3) == 0) {
+        float b[32];
+        load_bias32(e.bias + col0, b);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += b[i];
+        store_f32x32(z + col0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (col0 + i < N) z[col0 + i] = v[i] + e.bias[col0 + i];
+      }
+      break;
+    }
+    case kEpiBwdDX:
+    case kEpiBwdDXLN: {
+      const bf16* mrow = e.mask + (size_t)row * e.ldm;
+      if (full) {
+        bool on[32];
+        load_mask32(mrow + col0, on);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = on[i] ? v[i] : 0.f;
+        if (e.kind == kEpiBwdDXLN) {
+          store_f32x32(static_cast<float*>(e.out0) + (size_t)row * e.ld0 + col0, v);
+        } else {
+          store_bf16x32(static_cast<bf16*>(e.out0) + (size_t)row * e.ld0 + col0, v);
+          bf16* dzT = static_cast<bf16*>(e.out1);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) dzT[(size_t)(col0 + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int c = col0 + i;
+          if (c >= N) break;
+          const float x = __bfloat162float(mrow[c]) > 0.f ? v[i] : 0.f;
+          if (e.kind == kEpiBwdDXLN) {
+            static_cast<float*>(e.out0)[(size_t)row * e.ld0 + c] = x;
+          } else {
+            const bf16 o = __float2bfloat16_rn(x);
+            static_cast<bf16*>(e.out0)[(size_t)row * e.ld0 + c] = o;
+            static_cast<bf16*>(e.out1)[(size_t)c * e.ld1 + row] = o;
+          }
+        }
+      }
+      break;
+    }
+    case kEpiBwdDW: {
+      float* dW = static_cast<float*>(e.out0) + (size_t)row * e.kin;
+      if (col0 + 32 <= e.kin && (e.kin & 3) == 0) {
+        store_f32x32(dW + col0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int c = col0 + i;
+          if (c >= N) break;
+          if (c < e.kin) dW[c] = v[i];
+          else static_cast<float*>(e.out1)[row] = v[i];
+        }
+      }
+      break;
+    }
+    case kEpiBwdDW0: {
+      float* dW = static_cast<float*>(e.out0) + (size_t)row * e.kin;
+#pragma unroll
+      for (int i = 0; i < 32; i += 2) {
+        const int c = col0 + i;
+        if (c < 2 * e.kin) dW[c / 2] = v[i] + v[i + 1];
+        else if (c == 2 * e.kin) static_cast<float*>(e.out1)[row] = v[i];
+      }
+      break;
+    }
+    default: {  // kEpiDX0
+      float* dx = static_cast<float*>(e.out0) + (size_t)row * e.nc;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int c = col0 + i - e.c0;
+        if (col0 + i < N && c >= 0 && c < e.nc) dx[c] = v[i];
+      }
+      break;
+    }
+  }
+}
+
 // nkA > 0: A has only nkA K-slices and slice kb of B multiplies slice kb % nkA of
 // A -- B holds [W_hi | W_lo] along K and each A tile is used against both halves.
-template <int BN, class Epi>
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-                   int K, int nkA, Epi epi, unsigned* status) {
+    tc_gemm_kernel(const GemmProblem* __restrict__ probs, int nprob, unsigned* status) {
   using S = GemmSmem<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -51,13 +255,29 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* done = empty + kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
+  // problem of this CTA: the last p with tile_begin <= blockIdx.x (the table is immutable)
+  int lo = 0, hi = nprob - 1;
+  const int t = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (probs[mid].tile_begin <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmProblem* P = probs + lo;
+  const int lt = t - P->tile_begin;
+  const int M = P->M, N = P->N, K = P->K, nkA = P->nkA;
+  const int m0 = (lt / P->tiles_n) * kBM, n0 = (lt % P->tiles_n) * BN;
+  const CUtensorMap* tmA = &P->a;
+  const CUtensorMap* tmB = &P->b;
+
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
   const int nk = (K + kBK - 1) / kBK;
 
   if (threadIdx.x == 0) {
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmB);
+    tmap_acquire(tmA);
+    tmap_acquire(tmB);
+    prefetch_tmap(tmA);
+    prefetch_tmap(tmB);
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
@@ -73,6 +293,9 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  // operands come from the predecessor; the epilogue may overwrite what it read
+  pdl_wait();
+  pdl_trigger();
 
   if (warp == 0 && lane == 0) {
     // TMA producer
@@ -88,10 +311,10 @@ __global__ void __launch_bounds__(128, 1)
       const int ka = nkA > 0 ? kb % nkA : kb;
 #pragma unroll
       for (int r = 0; r < kBM / 64; ++r)
-        tma_load_2d(sA + s * S::kABytes + r * 8192, &tmA, &full[s], ka * kBK, m0 + 64 * r);
+        tma_load_2d(sA + s * S::kABytes + r * 8192, tmA, &full[s], ka * kBK, m0 + 64 * r);
 #pragma unroll
       for (int r = 0; r < BN / 64; ++r)
-        tma_load_2d(sB + s * S::kBBytes + r * 8192, &tmB, &full[s], kb * kBK, n0 + 64 * r);
+        tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kb * kBK, n0 + 64 * r);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -122,13 +345,15 @@ __global__ void __launch_bounds__(128, 1)
   const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0) ? 1 : 0) != 0;
   fence_after_sync();
   if (ok) {
+    const EpiDesc e = P->epi;
     const int row = m0 + warp * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const int ncol = (N - n0 < BN) ? N - n0 : BN;
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
+    for (int c = 0; c < ncol; c += 32) {
       float v[32];
       tmem_ld32(lane_base + c, v);
-      epi(row, n0 + c, v, M, N);
+      epilogue_chunk(e, row, n0 + c, v, M, N);
     }
   } else if (threadIdx.x == 0) {
     atomicOr(status, CRL_STATUS_TIMEOUT);

@@ -1,6 +1,8 @@
 // Host helpers for the tcgen05 kernels (see tc_host.h).
 #include <cudaTypedefs.h>
 
+#include <string.h>
+
 #include <mutex>
 
 #include "tc_host.h"
@@ -32,6 +34,8 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t
     *err = "TMA operand must start on a 16-byte boundary with a 16-byte multiple row stride";
     return false;
   }
+  // zero first: the map's bytes key the grouped-GEMM table cache
+  memset(map, 0, sizeof(*map));
   const cuuint64_t dims[2] = {inner, rows};
   const cuuint64_t strides[1] = {row_stride_elems * 2};
   const cuuint32_t box[2] = {64, box_rows};
