@@ -6,8 +6,14 @@ batch -> critic step (encoders, energy + InfoNCE + penalty, backward, Adam)
 public call crl_update_step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ant|small|humanoid|large] [--precision fp32|fp64]
-                  [--trace gemm|energy|relabel|adam|aux|insert]
+                  [--workload ant|small|humanoid|large] [--precision bf16|fp32|fp64]
+                  [--path fused|plain] [--trace gemm|energy|relabel|adam|aux|insert]
+                  [--no-comparator] [--no-relabel] [--no-cpu-baseline]
+
+The headline is the BF16 fused path; the FP32 plain path runs on the same
+workload in the same process as "comparator".  "relabel" reports the
+standalone sample + relabel kernel at 2^20 and 2^22 samples per launch on
+Humanoid-shaped rows (its HBM roofline).
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs its own
 independent agent (its own Philox key and buffer): weak scaling, no data-path
@@ -180,33 +186,38 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ant", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
-    ap.add_argument("--path", default="plain", choices=["plain", "fused"])
-    ap.add_argument("--trace", default="gemm", choices=["gemm", "energy", "relabel", "adam", "aux", "insert"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    w = WORKLOADS[args.workload]
-    if args.impl == "reference":
-        run_reference(args, w)
-        return
+RELABEL_ROWS = workload.Workload("relabel_humanoid_rows_E1024xT1000_D268_A17_G3", E=1024, T=1000, D=268, A=17,
+                                 G=3, B=256, hidden=64, layers=1, repr=64, seed=5)
 
+
+def traffic_record(kernel_class, workload_name, precision, path):
+    """DRAM bytes per launch of the dominant kernel class from the committed ncu
+    summary, or None when the summary is missing or its kernel source changed."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            table = json.load(f)
+    except OSError:
+        return None
+    rec = table.get(f"{kernel_class}|{workload_name}|{precision}|{path}")
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for rel in rec["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return rec["bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+
+
+def run_arm(args, w, precision, path, dev, world, rank, flush, full):
+    """Prefill, warm up and time one configuration of the update step.  full:
+    also the traced roofline pass, the end-to-end (host-buffer) pass and the
+    launch count."""
     import torch
     from paper_2408_11052_gb300 import api
 
-    rank, world, local = dist_setup(args.gpus)
-    dev = torch.device("cuda", local if world > 1 else 0)
-    # one non-default stream for everything: the library replays the update step
-    # as a CUDA graph there (the legacy default stream cannot be captured)
-    torch.cuda.set_stream(torch.cuda.Stream(device=dev))
-    ctx = api.CRLContext(w, precision=args.precision, path=args.path, agent=rank)
+    stream = torch.cuda.current_stream()
+    ctx = api.CRLContext(w, precision=precision, path=path, agent=rank)
     for k, v in workload.init_agent(w).items():
         ctx.load_network(k, v)
     obs, act, done = workload.buffer_contents(w, mean_len=None, seed_offset=rank)
@@ -218,8 +229,6 @@ def main():
     h_obs, h_act, h_done = (torch.from_numpy(x).pin_memory() for x in ins)
     loss_dev = torch.zeros(6, dtype=torch.float32, device=dev)
     loss_host = torch.zeros(6, dtype=torch.float32).pin_memory()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
     cursor = [0]
 
     def step_device():
@@ -255,50 +264,152 @@ def main():
     torch.cuda.synchronize()
     rc, status = ctx.sync_status()
     assert rc == api.OK, f"warm-up status {status}"
-
-    # kernels per step: count every traced class over one untimed step
-    launches = 0
-    for cls in api.TRACE:
-        ctx.trace_start(cls, 4096)
-        step_device()
-        launches += ctx.trace_stop()[0]
+    out = {}
+    if full:
+        # kernels per step: count every traced class over one untimed step
+        launches = 0
+        for cls in api.TRACE:
+            ctx.trace_start(cls, 4096)
+            step_device()
+            launches += ctx.trace_stop()[0]
+        out["launches_per_step"] = launches
 
     # timed region: graph-replayed steps, no tracing (tracing forces eager launches)
     with ClockSampler(dev.index) as clk:
         ms, _ = timed(step_device, args.steps)
-    ms = max_over_ranks(ms, world)
-    value = world * args.steps / (ms / 1e3)
-    # roofline pass: the same K steps again, eager, with CUDA events around every
-    # launch of the traced kernel class
-    _, tr = timed(step_device, args.steps, trace=args.trace)
-
-    for _ in range(3):
-        step_host()
-    e2e_ms, _ = timed(step_host, args.steps)
-    e2e_ms = max_over_ranks(e2e_ms, world)
+    out["ms"] = max_over_ranks(ms, world)
+    out["clocks"] = clk.summary()
+    if full:
+        # roofline pass: the same K steps again, eager, with CUDA events around
+        # every launch of the traced kernel class
+        _, out["trace"] = timed(step_device, args.steps, trace=args.trace)
+        for _ in range(3):
+            step_host()
+        e2e_ms, _ = timed(step_host, args.steps)
+        out["e2e_ms"] = max_over_ranks(e2e_ms, world)
     rc, status = ctx.sync_status()
     assert rc == api.OK, f"status {status}"
+    ctx.close()
+    return out
+
+
+def relabel_throughput(dev, flush, sizes=(1 << 20, 1 << 22), K=10, W=3):
+    """Standalone sample + relabel launches on Humanoid-shaped rows (HBM-bound):
+    samples/s and achieved GB/s per batch size."""
+    import torch
+    from paper_2408_11052_gb300 import api
+
+    w = RELABEL_ROWS
+    stream = torch.cuda.current_stream()
+    ctx = api.CRLContext(w, precision="fp32")
+    obs, act, done = workload.buffer_contents(w, mean_len=None)
+    ctx.insert(torch.from_numpy(obs).to(dev), torch.from_numpy(act).to(dev), torch.from_numpy(done).to(dev))
+    del obs, act, done
+    per = (w.D + w.A + 1 + w.G) * 4 + (w.D + w.A + w.G) * 4   # read row + episode end + goal dims, write s, a, g
+    res = []
+    for n in sizes:
+        kw = dict(dtype=torch.float32, device=dev)
+        out = (torch.empty(n, w.D, **kw), torch.empty(n, w.A, **kw), torch.empty(n, w.G, **kw), None)
+        for i in range(W):
+            ctx.sample(step=i, B=n, out=out)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            ctx.sample(step=100 + k, B=n, out=out)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K
+        res.append({"samples_per_launch": n, "value": n / (ms / 1e3), "unit": "samples/s", "us_per_launch": 1e3 * ms,
+                    "achieved_gbs": per * n / (ms / 1e3) / 1e9,
+                    "bytes_per_sample": per})
+        del out
+    rc, status = ctx.sync_status()
+    assert rc == api.OK, f"relabel status {status}"
+    ctx.close()
+    return w, res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ant", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--path", default="fused", choices=["plain", "fused"])
+    ap.add_argument("--trace", default="gemm", choices=["gemm", "energy", "relabel", "adam", "aux", "insert"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true", help="skip the FP32 plain arm")
+    ap.add_argument("--no-relabel", action="store_true", help="skip the standalone relabel throughput")
+    ap.add_argument("--only-relabel", action="store_true",
+                    help="run only the standalone relabel throughput (a short command for ncu captures)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    # one non-default stream for everything: the library replays the update step
+    # as a CUDA graph there (the legacy default stream cannot be captured)
+    torch.cuda.set_stream(torch.cuda.Stream(device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if args.only_relabel:
+        rw, res = relabel_throughput(dev, flush, sizes=(1 << 20,), K=3, W=1)
+        print(json.dumps({"relabel": {"workload": rw.name, "results": res}}), flush=True)
+        return
+
+    main_arm = run_arm(args, w, args.precision, args.path, dev, world, rank, flush, full=True)
+    ms = main_arm["ms"]
+    value = world * args.steps / (ms / 1e3)
+    comparator = None
+    if not args.no_comparator and (args.precision, args.path) != ("fp32", "plain"):
+        comp = run_arm(args, w, "fp32", "plain", dev, world, rank, flush, full=False)
+        cv = world * args.steps / (comp["ms"] / 1e3)
+        comparator = {"precision": "fp32", "path": "plain", "value": cv, "unit": "update steps/s",
+                      "ms_per_step": comp["ms"] / args.steps, "speedup": value / cv, "clocks": comp["clocks"],
+                      "note": "same workload, timing and launch mode; plain SIMT FP32 kernels, B x B materialised"}
 
     peaks, peak_src = load_peaks()
-    n_tr, tr_ms, tr_work = tr
+    n_tr, tr_ms, tr_work = main_arm["trace"]
+    traffic = traffic_record(args.trace, w.name, args.precision, args.path)
+    common = {"kernel_class": args.trace, "launches": n_tr, "avg_launch_us": 1e3 * tr_ms / max(n_tr, 1),
+              "timing": "eager traced pass of the same K steps (CUDA events around every launch of the class)",
+              "traffic": traffic}
     if args.trace == "gemm" and args.precision == "bf16":
         achieved = tr_work / (tr_ms / 1e3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel_class": args.trace, "launches": n_tr,
-                "avg_launch_us": 1e3 * tr_ms / max(n_tr, 1), "timing": "eager traced pass of the same K steps",
-                "peak_source": f"{peak_src} bf16_tflops_sustained (kernel timed inside a long step)"}
+                "peak_source": f"{peak_src} bf16_tflops_sustained (kernel timed inside a long step)", **common}
     elif args.trace in ("gemm", "energy"):
         achieved = tr_work / (tr_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": None,
-                "kernel_class": args.trace, "launches": n_tr, "avg_launch_us": 1e3 * tr_ms / max(n_tr, 1),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+                "frac": achieved / FP32_ALU_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz", **common}
     else:
         achieved = tr_work / (tr_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel_class": args.trace,
-                "launches": n_tr, "avg_launch_us": 1e3 * tr_ms / max(n_tr, 1), "peak_source": peak_src}
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} hbm_gbs", **common}
+    if traffic is not None:
+        roof["traffic"] = traffic
+        roof["traffic_source"] = "profiles/roofline_traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+
+    relabel = None
+    if rank == 0 and world == 1 and not args.no_relabel:
+        rw, res = relabel_throughput(dev, flush)
+        for r in res:
+            r["roofline"] = {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": r["achieved_gbs"] / peaks["hbm_gbs"], "peak_source": f"{peak_src} hbm_gbs"}
+        relabel = {"workload": rw.name, "kernel": "relabel_kernel (crl_sample_relabel, one launch per batch)",
+                   "l2": "flushed between launches", "results": res}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -318,16 +429,19 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "step": "insert 1 slice + relabel + critic fwd/bwd + Adam + actor fwd/bwd + Adam",
                        "parallelism": f"{world} independent agents"},
-            "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "update steps/s",
+            "e2e": {"value": world * args.steps / (main_arm["e2e_ms"] / 1e3), "unit": "update steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
-            "gpu_launches": launches * args.steps,
+            "gpu_launches": main_arm["launches_per_step"] * args.steps,
             "roofline": roof,
-            "clocks": clk.summary()}
+            "clocks": main_arm["clocks"]}
+    if comparator is not None:
+        line["comparator"] = comparator
+    if relabel is not None:
+        line["relabel"] = relabel
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

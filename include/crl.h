@@ -196,8 +196,9 @@ int crl_buffer_size(const crl_ctx* ctx, int32_t* size, int64_t* total);
  * CDF).  Writes s [B][D] = obs[e][t], a [B][A] = act[e][t],
  * g [B][G] = obs[e][t+k][goal_idx] and, if idx != NULL, idx [B][3] = (e, t, k)
  * with t counted from the oldest stored step.  step == CRL_STEP_AUTO uses the
- * context's device step counter and advances it.  Device pointers.
- * CRL_E_BUFFER_EMPTY if nothing is stored; CRL_E_SHAPE if B > cfg.B. */
+ * context's device step counter and advances it.  Device pointers.  B may
+ * exceed cfg.B (the outputs are the caller's; B x D < 2^31).
+ * CRL_E_BUFFER_EMPTY if nothing is stored; CRL_E_SHAPE if B < 1. */
 int crl_sample_relabel(crl_ctx* ctx, uint64_t step, int32_t B, float* s, float* a, float* g,
                        int32_t* idx, void* stream);
 

@@ -10,6 +10,8 @@
 //   L = mean_i [alpha log pi_i - f(phi(s_i, a'_i), psi(g_i)) / tau].
 // Gradients: d log pi / du = 2 tanh(u); d log pi / dl = -1 (plus the u path,
 // du/dl = sigma eps); the clip passes gradient only strictly inside (-5, 2).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 #include "philox.cuh"
@@ -50,13 +52,16 @@ __device__ T philox_normal(unsigned long long step, int b, int d, unsigned long 
 }
 
 // One warp per row b, lanes over the action dims.
+// x0 != null: a' also goes into columns [x0_col, x0_col + A) of the split BF16
+// network input x0 (hi, lo interleaved: element c at 2c, 2c + 1).
 template <typename T>
 __global__ void __launch_bounds__(256) head_forward_kernel(int B, int A, const T* __restrict__ out,
                                                           const float* __restrict__ eps,
                                                           const unsigned long long* __restrict__ step_dev,
                                                           unsigned long long seed, unsigned long long agent,
                                                           T* __restrict__ a_new, T* __restrict__ logpi,
-                                                          T* __restrict__ eps_used) {
+                                                          T* __restrict__ eps_used, __nv_bfloat16* __restrict__ x0,
+                                                          int x0_ld, int x0_col) {
   pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int b = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
@@ -69,7 +74,15 @@ __global__ void __launch_bounds__(256) head_forward_kernel(int B, int A, const T
     const T l = fmin(fmax(lraw, T(kLogStdMin)), T(kLogStdMax));
     const T e = eps ? T(eps[(size_t)b * A + d]) : philox_normal<T>(step, b, d, seed, agent);
     const T u = mu + dev_exp(l) * e;
-    a_new[(size_t)b * A + d] = dev_tanh(u);
+    const T act = dev_tanh(u);
+    a_new[(size_t)b * A + d] = act;
+    if (x0) {
+      const float v = (float)act;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      __nv_bfloat16* dst = x0 + (size_t)b * x0_ld + 2 * (x0_col + d);
+      dst[0] = hi;
+      dst[1] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
     eps_used[(size_t)b * A + d] = e;
     lp += -T(0.5) * e * e - T(kHalfLog2Pi) - l - T(2) * (T(kLog2) - u - softplus(T(-2) * u));
   }
@@ -77,86 +90,117 @@ __global__ void __launch_bounds__(256) head_forward_kernel(int B, int A, const T
   if (lane == 0) logpi[b] = lp;
 }
 
-// f_i = f(phi_i, psi_i) / tau and dphi_i = -(1/B) df_i/dphi_i.  One warp per row.
+// f_i = f(phi_i, psi_i) / tau and dphi_i = -(1/B) df_i/dphi_i, one warp per
+// row (8 rows per block), and the loss loss2 = {mean(alpha log pi - f),
+// mean log pi}: each block writes its partial sums, and the last block to
+// finish (ticket) adds the partials in block order, so the result does not
+// depend on which block finishes last.  dz != null: dphi is written as BF16
+// [B][ldz] (the phi network's output gradient) instead of T.
 template <typename T>
-__global__ void __launch_bounds__(256) diag_energy_kernel(int B, int R, int energy, double tau,
-                                                         const T* __restrict__ phi, const T* __restrict__ psi,
-                                                         T* __restrict__ fdiag, T* __restrict__ dphi) {
+__global__ void __launch_bounds__(256) diag_energy_loss_kernel(ActorLossArgs<T> p) {
   pdl_enter();
-  const int lane = threadIdx.x % kWarp;
-  const int i = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
-  if (i >= B) return;
-  const T* x = phi + (size_t)i * R;
-  const T* y = psi + (size_t)i * R;
-  T sxy = 0, sxx = 0, syy = 0, sdd = 0, sad = 0;
-  for (int c = lane; c < R; c += kWarp) {
-    const T a = x[c], b = y[c], d = a - b;
-    sxy += a * b;
-    sxx += a * a;
-    syy += b * b;
-    sdd += d * d;
-    sad += fabs(d);
-  }
-  sxy = warp_sum(sxy);
-  sxx = warp_sum(sxx);
-  syy = warp_sum(syy);
-  sdd = warp_sum(sdd);
-  sad = warp_sum(sad);
-  const T it = T(1.0 / tau), ib = T(-1.0 / B);
-  T f;
-  switch (energy) {
-    case CRL_ENERGY_DOT: f = sxy; break;
-    case CRL_ENERGY_COS: f = sxy / (dev_sqrt(sxx) * dev_sqrt(syy)); break;
-    case CRL_ENERGY_L2: f = -dev_sqrt(sdd); break;
-    case CRL_ENERGY_L2SQ: f = -sdd; break;
-    default: f = -sad; break;
-  }
-  if (lane == 0) fdiag[i] = f * it;
-  const T nx = dev_sqrt(sxx), ny = dev_sqrt(syy), dist = dev_sqrt(sdd);
-  for (int c = lane; c < R; c += kWarp) {
-    const T a = x[c], b = y[c], d = a - b;
-    T g;
-    switch (energy) {
-      case CRL_ENERGY_DOT: g = b; break;
-      case CRL_ENERGY_COS: {
-        const T xh = a / nx, yh = b / ny;
-        g = (yh - xh * (sxy / (nx * ny))) / nx;
-        break;
-      }
-      case CRL_ENERGY_L2: g = (dist >= T(1e-12)) ? -d / dist : T(0); break;
-      case CRL_ENERGY_L2SQ: g = T(-2) * d; break;
-      default: g = (d > T(0)) ? T(-1) : ((d < T(0)) ? T(1) : T(0)); break;
+  __shared__ T s_a[8], s_l[8];
+  __shared__ int s_last;
+  const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
+  const int i = blockIdx.x * 8 + w;
+  const int B = p.B, R = p.R;
+  T term = 0, lpi = 0;
+  if (i < B) {
+    const T* x = p.phi + (size_t)i * R;
+    const T* y = p.psi + (size_t)i * R;
+    T sxy = 0, sxx = 0, syy = 0, sdd = 0, sad = 0;
+    for (int c = lane; c < R; c += kWarp) {
+      const T a = x[c], b = y[c], d = a - b;
+      sxy += a * b;
+      sxx += a * a;
+      syy += b * b;
+      sdd += d * d;
+      sad += fabs(d);
     }
-    dphi[(size_t)i * R + c] = ib * it * g;
+    sxy = warp_sum(sxy);
+    sxx = warp_sum(sxx);
+    syy = warp_sum(syy);
+    sdd = warp_sum(sdd);
+    sad = warp_sum(sad);
+    const T it = T(1.0 / p.tau), ib = T(-1.0 / B);
+    T f;
+    switch (p.energy) {
+      case CRL_ENERGY_DOT: f = sxy; break;
+      case CRL_ENERGY_COS: f = sxy / (dev_sqrt(sxx) * dev_sqrt(syy)); break;
+      case CRL_ENERGY_L2: f = -dev_sqrt(sdd); break;
+      case CRL_ENERGY_L2SQ: f = -sdd; break;
+      default: f = -sad; break;
+    }
+    f *= it;
+    if (lane == 0) p.fdiag[i] = f;
+    lpi = p.logpi[i];
+    term = T(p.alpha) * lpi - f;
+    const T nx = dev_sqrt(sxx), ny = dev_sqrt(syy), dist = dev_sqrt(sdd);
+    for (int c = lane; c < R; c += kWarp) {
+      const T a = x[c], b = y[c], d = a - b;
+      T g;
+      switch (p.energy) {
+        case CRL_ENERGY_DOT: g = b; break;
+        case CRL_ENERGY_COS: {
+          const T xh = a / nx, yh = b / ny;
+          g = (yh - xh * (sxy / (nx * ny))) / nx;
+          break;
+        }
+        case CRL_ENERGY_L2: g = (dist >= T(1e-12)) ? -d / dist : T(0); break;
+        case CRL_ENERGY_L2SQ: g = T(-2) * d; break;
+        default: g = (d > T(0)) ? T(-1) : ((d < T(0)) ? T(1) : T(0)); break;
+      }
+      const T dv = ib * it * g;
+      if (p.dz) p.dz[(size_t)i * p.ldz + c] = __float2bfloat16_rn((float)dv);
+      else p.dphi[(size_t)i * R + c] = dv;
+    }
   }
-}
-
-// loss2 = {mean(alpha log pi - f), mean log pi}.  One block.
-template <typename T>
-__global__ void __launch_bounds__(1024) actor_loss_kernel(int B, double alpha, const T* __restrict__ logpi,
-                                                         const T* __restrict__ fdiag, T* __restrict__ loss2,
-                                                         unsigned* status, int* t_bump) {
-  pdl_enter();
+  if (lane == 0) {
+    s_a[w] = term;
+    s_l[w] = lpi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T a = 0, l = 0;
+    for (int k = 0; k < 8; ++k) {
+      a += s_a[k];
+      l += s_l[k];
+    }
+    p.partial[2 * blockIdx.x] = a;
+    p.partial[2 * blockIdx.x + 1] = l;
+    __threadfence();
+    s_last = (atomicAdd(p.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
   __shared__ T sm[32];
   T a = 0, l = 0;
-  for (int i = threadIdx.x; i < B; i += blockDim.x) {
-    a += T(alpha) * logpi[i] - fdiag[i];
-    l += logpi[i];
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+    a += *((volatile T*)p.partial + 2 * k);
+    l += *((volatile T*)p.partial + 2 * k + 1);
   }
   a = block_sum(a, sm);
   l = block_sum(l, sm);
   if (threadIdx.x == 0) {
-    loss2[0] = a / T(B);
-    loss2[1] = l / T(B);
-    if (status && !finite_val(a)) atomicOr(status, CRL_STATUS_NONFINITE);
-    if (t_bump) *t_bump += 1;
+    p.loss2[0] = a / T(B);
+    p.loss2[1] = l / T(B);
+    if (p.status && !finite_val(a)) atomicOr(p.status, CRL_STATUS_NONFINITE);
+    if (p.t_bump) *p.t_bump += 1;
+    // next relabel step: the one this step's relabel used, plus one
+    if (p.step_bump) *p.step_bump = *p.last_step + 1ull;
+    *p.ticket = 0u;
   }
 }
 
+// dz != null: the gradient is written as BF16 dz [B][ldz] and dz^T [2A][ldt]
+// (the policy network's output gradient) instead of dout.
 template <typename T>
 __global__ void __launch_bounds__(256) head_backward_kernel(int B, int A, double alpha, const T* __restrict__ out,
                                                            const T* __restrict__ eps_used,
-                                                           const T* __restrict__ da, T* __restrict__ dout) {
+                                                           const T* __restrict__ da, T* __restrict__ dout,
+                                                           __nv_bfloat16* __restrict__ dz, int ldz,
+                                                           __nv_bfloat16* __restrict__ dzT, int ldt) {
   pdl_enter();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
@@ -171,8 +215,17 @@ __global__ void __launch_bounds__(256) head_backward_kernel(int B, int A, double
     const T du = da[(size_t)b * A + d] * (T(1) - a * a) + ab * T(2) * a;
     const T dl = du * sigma * e - ab;
     const bool inside = lraw > T(kLogStdMin) && lraw < T(kLogStdMax);
-    dout[(size_t)b * 2 * A + d] = du;
-    dout[(size_t)b * 2 * A + A + d] = inside ? dl : T(0);
+    const T dlv = inside ? dl : T(0);
+    if (dz) {
+      const __nv_bfloat16 hu = __float2bfloat16_rn((float)du), hl = __float2bfloat16_rn((float)dlv);
+      dz[(size_t)b * ldz + d] = hu;
+      dz[(size_t)b * ldz + A + d] = hl;
+      dzT[(size_t)d * ldt + b] = hu;
+      dzT[(size_t)(A + d) * ldt + b] = hl;
+    } else {
+      dout[(size_t)b * 2 * A + d] = du;
+      dout[(size_t)b * 2 * A + A + d] = dlv;
+    }
   }
 }
 
@@ -180,36 +233,44 @@ __global__ void __launch_bounds__(256) head_backward_kernel(int B, int A, double
 
 template <typename T>
 void actor_head_forward(const ActorSpec& as, const T* pi_out, const float* eps, const unsigned long long* step_dev,
-                        uint64_t seed, uint64_t agent, int B, T* a_new, T* logpi, T* eps_used, cudaStream_t st) {
+                        uint64_t seed, uint64_t agent, int B, T* a_new, T* logpi, T* eps_used, cudaStream_t st,
+                        __nv_bfloat16* x0, int x0_ld, int x0_col) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 5);
-  launch_k(head_forward_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, B, as.A, pi_out, eps, step_dev, seed, agent, a_new,
-                                                           logpi, eps_used);
+  launch_k(head_forward_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, B, as.A, pi_out, eps, step_dev, seed,
+           agent, a_new, logpi, eps_used, x0, x0_ld, x0_col);
 }
+
+size_t actor_loss_ws_bytes(int B, size_t elem) { return (size_t)ceil_div(B, 8) * 2 * elem + 256; }
 
 template <typename T>
 void actor_energy_and_loss(const ActorSpec& as, const T* phi, const T* psi, const T* logpi, int B, int R, T* dphi,
-                           T* fdiag, T* loss2, unsigned* status, int* t_bump, cudaStream_t st) {
-  {
-    TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * R);
-    launch_k(diag_energy_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, B, R, as.energy, as.tau, phi, psi, fdiag, dphi);
-  }
-  TraceLaunch tr(CRL_TRACE_AUX, st, 2.0 * B * sizeof(T));
-  launch_k(actor_loss_kernel<T>, dim3(1), dim3(1024), 0, st, B, as.alpha, logpi, fdiag, loss2, status, t_bump);
+                           T* fdiag, T* loss2, void* ws, unsigned* ticket, unsigned* status, int* t_bump,
+                           unsigned long long* step_bump, const unsigned long long* last_step, cudaStream_t st,
+                           __nv_bfloat16* dz, int ldz) {
+  ActorLossArgs<T> p{B,    R,     as.energy, as.tau, as.alpha, phi,    psi,       logpi,     fdiag,
+                     dphi, dz,    ldz,       static_cast<T*>(ws), ticket, loss2, status, t_bump, step_bump,
+                     last_step};
+  TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * R);
+  launch_k(diag_energy_loss_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, p);
 }
 
 template <typename T>
 void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used, const T* da, int B, T* dout,
-                         cudaStream_t st) {
+                         cudaStream_t st, __nv_bfloat16* dz, int ldz, __nv_bfloat16* dzT, int ldt) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 6);
-  launch_k(head_backward_kernel<T>, dim3(ceil_div(B, 256)), dim3(256), 0, st, B, as.A, as.alpha, pi_out, eps_used, da, dout);
+  launch_k(head_backward_kernel<T>, dim3(ceil_div(B, 256)), dim3(256), 0, st, B, as.A, as.alpha, pi_out, eps_used,
+           da, dout, dz, ldz, dzT, ldt);
 }
 
 #define CRL_INST_ACTOR(T)                                                                                        \
   template void actor_head_forward<T>(const ActorSpec&, const T*, const float*, const unsigned long long*,       \
-                                      uint64_t, uint64_t, int, T*, T*, T*, cudaStream_t);                        \
+                                      uint64_t, uint64_t, int, T*, T*, T*, cudaStream_t, __nv_bfloat16*, int,    \
+                                      int);                                                                      \
   template void actor_energy_and_loss<T>(const ActorSpec&, const T*, const T*, const T*, int, int, T*, T*, T*,   \
-                                         unsigned*, int*, cudaStream_t);                                         \
-  template void actor_head_backward<T>(const ActorSpec&, const T*, const T*, const T*, int, T*, cudaStream_t);
+                                         void*, unsigned*, unsigned*, int*, unsigned long long*,                 \
+                                         const unsigned long long*, cudaStream_t, __nv_bfloat16*, int);          \
+  template void actor_head_backward<T>(const ActorSpec&, const T*, const T*, const T*, int, T*, cudaStream_t,    \
+                                       __nv_bfloat16*, int, __nv_bfloat16*, int);
 CRL_INST_ACTOR(float)
 CRL_INST_ACTOR(double)
 

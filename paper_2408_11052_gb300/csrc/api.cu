@@ -33,7 +33,7 @@ struct Counters {
   int t_critic;                  // Adam step counters (incremented by the loss kernels)
   int t_actor;
   unsigned status;               // CRL_STATUS_* bits
-  int pad;
+  unsigned ticket_actor;         // last-block ticket of the actor loss kernel (zero between launches)
 };
 
 class Failure {
@@ -155,6 +155,7 @@ struct crl_ctx {
   size_t ws_bytes = 0;
   void *pi_out = nullptr, *a_new = nullptr, *logpi = nullptr, *eps_used = nullptr, *fdiag = nullptr;
   void *da = nullptr, *dout = nullptr;
+  void* actor_ws = nullptr;  // per-block partial sums of the actor loss
   float* loss_f = nullptr;  // 8 floats: float copy of the loss parts
   float *bs = nullptr, *ba = nullptr, *bg = nullptr;  // batch of crl_update_step
   // host-input staging for crl_buffer_insert
@@ -296,8 +297,10 @@ void critic_impl(crl_ctx* c, const float* s, const float* a, const float* g, int
   check_launch("critic step");
 }
 
+// bump_step: the loss kernel also advances the relabel step counter (update step).
 template <typename T>
-void actor_impl(crl_ctx* c, const float* s, const float* g, const float* eps, int B, int apply, cudaStream_t st) {
+void actor_impl(crl_ctx* c, const float* s, const float* g, const float* eps, int B, int apply, cudaStream_t st,
+                bool bump_step = false) {
   const crl_config& cf = c->cfg;
   const T* ppi = static_cast<const T*>(c->nets[CRL_NET_PI].params);
   const T* pphi = static_cast<const T*>(c->nets[CRL_NET_PHI].params);
@@ -317,8 +320,9 @@ void actor_impl(crl_ctx* c, const float* s, const float* g, const float* eps, in
   actor_head_forward<T>(as, pi_out, eps, &c->ctr->last_step, cf.seed, cf.agent, B, a_new, logpi, eps_used, st);
   mlp_forward<T, T>(c->shapes[CRL_NET_PHI], pphi, s, a_new, B, phi, c->saved[CRL_NET_PHI], st);
   mlp_forward<T, float>(c->shapes[CRL_NET_PSI], ppsi, g, nullptr, B, psi, c->saved[CRL_NET_PSI], st);
-  actor_energy_and_loss<T>(as, phi, psi, logpi, B, cf.repr, dphi, static_cast<T*>(c->fdiag), loss, &c->ctr->status,
-                           apply ? &c->ctr->t_actor : nullptr, st);
+  actor_energy_and_loss<T>(as, phi, psi, logpi, B, cf.repr, dphi, static_cast<T*>(c->fdiag), loss, c->actor_ws,
+                           &c->ctr->ticket_actor, &c->ctr->status, apply ? &c->ctr->t_actor : nullptr,
+                           bump_step ? &c->ctr->step : nullptr, &c->ctr->last_step, st);
   mlp_backward<T, T>(c->shapes[CRL_NET_PHI], pphi, s, a_new, B, c->saved[CRL_NET_PHI], dphi, nullptr, nullptr, da,
                      st);
   actor_head_backward<T>(as, pi_out, eps_used, da, B, dout, st);
@@ -373,8 +377,11 @@ AdamShadowNet adam_net_of(crl_ctx* c, int net, const int* t, float lr) {
 // rebuild the BF16 weight shadows first (the caller may have changed the
 // weights).  packed: the relabel kernel already wrote the split network inputs.
 // phi and psi run side by side as grouped launches (one per layer).
+// with_pi: the policy's forward (its parameters do not change before the
+// actor step) joins the encoders' grouped launches; the actor step then
+// reuses its output (update step only, where relabel packed its input).
 void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g, int B, int apply, cudaStream_t st,
-                      bool refresh = true, bool packed = false) {
+                      bool refresh = true, bool packed = false, bool with_pi = false) {
   const crl_config& cf = c->cfg;
   unsigned* status = &c->ctr->status;
   BfNet& P = c->bf[CRL_NET_PHI];
@@ -389,9 +396,15 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     bf_net_pack_input(P, s, a, B, st);
     bf_net_pack_input(Q, g, nullptr, B, st);
   }
-  const BfPass pass[2] = {{&P, pphi, static_cast<float*>(c->nets[CRL_NET_PHI].grads), nullptr},
-                          {&Q, ppsi, static_cast<float*>(c->nets[CRL_NET_PSI].grads), nullptr}};
-  bf_check(bf_forward(c->groups, pass, 2, B, status, st));
+  const BfPass pass[3] = {{&P, pphi, static_cast<float*>(c->nets[CRL_NET_PHI].grads), nullptr},
+                          {&Q, ppsi, static_cast<float*>(c->nets[CRL_NET_PSI].grads), nullptr},
+                          {&c->bf[CRL_NET_PI], static_cast<const float*>(c->nets[CRL_NET_PI].params), nullptr,
+                           nullptr}};
+  if (with_pi) {
+    bf_maps(c, CRL_NET_PI, B);
+    bf_refresh(c, CRL_NET_PI, refresh, st);
+  }
+  bf_check(bf_forward(c->groups, pass, with_pi ? 3 : 2, B, status, st));
   float* rl = static_cast<float*>(c->row_lse);
   float* cl = static_cast<float*>(c->col_lse);
   float* loss = static_cast<float*>(c->loss);
@@ -423,11 +436,13 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
   check_launch("critic step (bf16)");
 }
 
-// Actor step with BF16 tensor-core networks.  pi(s, g) and psi(g) run side by
-// side (psi does not depend on the policy), then the head, phi(s, a'), the
-// diagonal energy and the backward through phi (input gradient only) and pi.
+// Actor step with BF16 tensor-core networks: pi(s, g) (unless pi_ready), the
+// head, phi(s, a') and psi(g) side by side, the diagonal energy with the loss,
+// and the backward through phi (input gradient only) and pi.  packed: the
+// relabel kernel wrote the split network inputs, so the head writes a' into
+// phi's input directly.  bump_step: the loss kernel advances the relabel step.
 void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* eps, int B, int apply, cudaStream_t st,
-                     bool refresh = true, bool packed = false) {
+                     bool refresh = true, bool packed = false, bool pi_ready = false, bool bump_step = false) {
   const crl_config& cf = c->cfg;
   unsigned* status = &c->ctr->status;
   BfNet& PI = c->bf[CRL_NET_PI];
@@ -443,27 +458,30 @@ void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* ep
   float* a_new = static_cast<float*>(c->a_new);
   float* logpi = static_cast<float*>(c->logpi);
   float* eps_used = static_cast<float*>(c->eps_used);
-  float* dphi = static_cast<float*>(c->dphi);
   float* da = static_cast<float*>(c->da);
-  float* dout = static_cast<float*>(c->dout);
   float* loss = static_cast<float*>(c->loss) + 4;
   ActorSpec as{cf.A, cf.energy, (double)cf.temperature, (double)cf.alpha};
   if (!packed) {
     bf_net_pack_input(PI, s, g, B, st);
     bf_net_pack_input(Q, g, nullptr, B, st);
   }
-  const BfPass fwd1[2] = {{&PI, ppi, nullptr, nullptr}, {&Q, ppsi, nullptr, nullptr}};
-  bf_check(bf_forward(c->groups, fwd1, 2, B, status, st));
-  actor_head_forward<float>(as, PI.y, eps, &c->ctr->last_step, cf.seed, cf.agent, B, a_new, logpi, eps_used, st);
-  bf_net_pack_input(P, s, a_new, B, st);
-  const BfPass phi_pass[1] = {{&P, pphi, nullptr, da}};
-  bf_check(bf_forward(c->groups, phi_pass, 1, B, status, st));
-  actor_energy_and_loss<float>(as, P.y, Q.y, logpi, B, cf.repr, dphi, static_cast<float*>(c->fdiag), loss, status,
-                               apply ? &c->ctr->t_actor : nullptr, st);
-  bf_net_load_dy(P, dphi, B, st);
-  bf_check(bf_backward(c->groups, phi_pass, 1, B, status, st));
-  actor_head_backward<float>(as, PI.y, eps_used, da, B, dout, st);
-  bf_net_load_dy(PI, dout, B, st);
+  if (!pi_ready) {
+    const BfPass pi_fwd[1] = {{&PI, ppi, nullptr, nullptr}};
+    bf_check(bf_forward(c->groups, pi_fwd, 1, B, status, st));
+  }
+  actor_head_forward<float>(as, PI.y, eps, &c->ctr->last_step, cf.seed, cf.agent, B, a_new, logpi, eps_used, st,
+                            packed ? P.x0 : nullptr, bf_net_x0_ld(P), P.s.in0);
+  if (!packed) bf_net_pack_input(P, s, a_new, B, st);
+  // phi(s, a') and psi(g) with the critic's updated weights
+  const BfPass fwd[2] = {{&P, pphi, nullptr, da}, {&Q, ppsi, nullptr, nullptr}};
+  bf_check(bf_forward(c->groups, fwd, 2, B, status, st));
+  actor_energy_and_loss<float>(as, P.y, Q.y, logpi, B, cf.repr, nullptr, static_cast<float*>(c->fdiag), loss,
+                               c->actor_ws, &c->ctr->ticket_actor, status, apply ? &c->ctr->t_actor : nullptr,
+                               bump_step ? &c->ctr->step : nullptr, &c->ctr->last_step, st, P.dz[P.layers],
+                               P.L[P.layers].out_pad);
+  bf_check(bf_backward(c->groups, fwd, 1, B, status, st));
+  actor_head_backward<float>(as, PI.y, eps_used, da, B, nullptr, st, PI.dz[PI.layers], PI.L[PI.layers].out_pad,
+                             PI.dzT[PI.layers], PI.Mmax);
   const BfPass pi_pass[1] = {{&PI, ppi, static_cast<float*>(c->nets[CRL_NET_PI].grads), nullptr}};
   bf_check(bf_backward(c->groups, pi_pass, 1, B, status, st));
   if (apply) {
@@ -516,11 +534,16 @@ void insert_impl(crl_ctx* c, const float* obs, const float* act, const uint8_t* 
   c->size_host = (int32_t)(c->total_host < cf.T ? c->total_host : cf.T);
 }
 
+// bump: advance the step counter after a CRL_STEP_AUTO draw (the update step
+// leaves that to its actor-loss kernel, which runs once per step anyway).
 void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g, int32_t* idx, cudaStream_t st,
-                  bool pack_bf16 = false) {
+                  bool pack_bf16 = false, bool bump = true) {
   const crl_config& cf = c->cfg;
   CRL_REQUIRE(s && a && g, CRL_E_INVALID_ARG, "s, a and g must be non-null");
-  CRL_REQUIRE(B >= 1 && B <= cf.B, CRL_E_SHAPE, "B must lie in [1, cfg.B]");
+  CRL_REQUIRE(B >= 1, CRL_E_SHAPE, "B must be >= 1");
+  CRL_REQUIRE(!pack_bf16 || B <= cf.B, CRL_E_SHAPE, "B must lie in [1, cfg.B]");
+  CRL_REQUIRE((int64_t)B * cf.D < ((int64_t)1 << 31) && (int64_t)B * 3 < ((int64_t)1 << 31), CRL_E_SHAPE,
+              "B x D must stay below 2^31");
   CRL_REQUIRE(c->size_host > 0, CRL_E_BUFFER_EMPTY, "the replay buffer is empty");
   RelabelArgs ra{};
   ra.seed = cf.seed;
@@ -544,7 +567,7 @@ void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g
     }
   }
   launch_relabel(c->bd, ra, st);
-  if (step == CRL_STEP_AUTO) launch_bump_u64(&c->ctr->step, st);
+  if (step == CRL_STEP_AUTO && bump) launch_bump_u64(&c->ctr->step, st);
   check_launch("sample relabel");
 }
 
@@ -686,6 +709,7 @@ int crl_create(const crl_config* cfg, crl_ctx** out) {
     c->fdiag = c->dalloc((size_t)B * e);
     c->da = c->dalloc((size_t)B * A * e);
     c->dout = c->dalloc((size_t)B * 2 * A * e);
+    c->actor_ws = c->dalloc(actor_loss_ws_bytes(B, e));
     // FP32 / BF16: the loss parts are already float and land in the ABI's float buffer directly
     c->loss_f = (e == sizeof(float)) ? static_cast<float*>(c->loss) : static_cast<float*>(c->dalloc(8 * sizeof(float)));
     c->bs = static_cast<float*>(c->dalloc((size_t)B * cf.D * sizeof(float)));
@@ -816,18 +840,19 @@ namespace {
 // relabel (device step counter) -> critic + Adam -> actor + Adam on the batch workspaces
 void update_body(crl_ctx* ctx, cudaStream_t st) {
   const int B = ctx->cfg.B;
-  // the BF16 path has the relabel kernel pack the network inputs directly
-  relabel_impl(ctx, CRL_STEP_AUTO, B, ctx->bs, ctx->ba, ctx->bg, nullptr, st, ctx->bf16);
+  // the BF16 path has the relabel kernel pack the network inputs directly; the
+  // actor-loss kernel advances the step counter
+  relabel_impl(ctx, CRL_STEP_AUTO, B, ctx->bs, ctx->ba, ctx->bg, nullptr, st, ctx->bf16, false);
   if (ctx->cfg.precision == CRL_PREC_FP64) {
     critic_impl<double>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
-    actor_impl<double>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st);
+    actor_impl<double>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st, true);
   } else if (ctx->bf16) {
     // the shadows follow the weights through the fused Adam; only the first call refreshes
-    critic_impl_bf16(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st, false, true);
-    actor_impl_bf16(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st, false, true);
+    critic_impl_bf16(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st, false, true, true);
+    actor_impl_bf16(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st, false, true, true, true);
   } else {
     critic_impl<float>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
-    actor_impl<float>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st);
+    actor_impl<float>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st, true);
   }
 }
 }  // namespace

@@ -18,37 +18,17 @@
 namespace crl {
 
 // ---------------------------------------------------------------------------
-// Insert: copy the newest min(n, T) slices into their ring slots with the
-// episode marked open (-1).  One warp per (slice, env) row.
-__global__ void __launch_bounds__(128) insert_rows_kernel(BufferDev bd, const float* __restrict__ obs,
-                                                         const float* __restrict__ act, int n, int i0,
-                                                         long long total_before) {
-  pdl_enter();
-  const int lane = threadIdx.x % kWarp;
-  const long long row = (long long)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
-  const long long nrows = (long long)(n - i0) * bd.E;
-  if (row >= nrows) return;
-  const int i = i0 + (int)(row / bd.E);
-  const int e = (int)(row % bd.E);
-  const long long abs_i = total_before + i;
-  float* dst = bd.rows + ((size_t)e * bd.T + (size_t)(abs_i % bd.T)) * bd.W;
-  const float* so = obs + ((size_t)i * bd.E + e) * bd.D;
-  const float* sa = act + ((size_t)i * bd.E + e) * bd.A;
-  for (int c = lane; c < bd.W; c += kWarp) {
-    float v;
-    if (c < bd.D) v = so[c];
-    else if (c < bd.D + bd.A) v = sa[c - bd.D];
-    else if (c == bd.D + bd.A) v = __int_as_float(-1);
-    else v = 0.f;
-    dst[c] = v;
-  }
-}
-
-// Close episodes: for every done flag, stamp the episode's stored steps with
-// the absolute index of its last step.  One warp per environment walks its n
-// flags in order; the stamping of one episode is spread over the lanes.
-__global__ void __launch_bounds__(128) close_episodes_kernel(BufferDev bd, const uint8_t* __restrict__ done,
-                                                            int n, long long total_before) {
+// Insert n time slices in one launch, one warp per environment:
+//  1. copy the environment's newest min(n, T) slices into their ring slots,
+//     with the episode marked open (-1);
+//  2. walk its n done flags in order and stamp every episode they close with
+//     the absolute index of its last step (one episode's stamping is spread
+//     over the lanes).
+// The warp's own copies precede its stamps (__syncwarp orders them).  Block 0
+// records the new fill.
+__global__ void __launch_bounds__(128) insert_kernel(BufferDev bd, const float* __restrict__ obs,
+                                                    const float* __restrict__ act, const uint8_t* __restrict__ done,
+                                                    int n, int i0, long long total_before) {
   pdl_enter();
   const int lane = threadIdx.x % kWarp;
   const int e = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
@@ -59,6 +39,21 @@ __global__ void __launch_bounds__(128) close_episodes_kernel(BufferDev bd, const
     bd.state[1] = (int32_t)total_after;
   }
   if (e >= bd.E) return;
+  for (int i = i0; i < n; ++i) {
+    const long long abs_i = total_before + i;
+    float* dst = bd.rows + ((size_t)e * bd.T + (size_t)(abs_i % bd.T)) * bd.W;
+    const float* so = obs + ((size_t)i * bd.E + e) * bd.D;
+    const float* sa = act + ((size_t)i * bd.E + e) * bd.A;
+    for (int c = lane; c < bd.W; c += kWarp) {
+      float v;
+      if (c < bd.D) v = so[c];
+      else if (c < bd.D + bd.A) v = sa[c - bd.D];
+      else if (c == bd.D + bd.A) v = __int_as_float(-1);
+      else v = 0.f;
+      dst[c] = v;
+    }
+  }
+  __syncwarp();
   const long long win_lo = total_after - size_after;
   long long start = bd.ep_start[e];
   for (int i = 0; i < n; ++i) {
@@ -77,13 +72,10 @@ void launch_buffer_insert(const BufferDev& bd, const float* obs, const float* ac
                           int n, int64_t total_before, cudaStream_t st) {
   const int i0 = n > bd.T ? n - bd.T : 0;
   const long long rows = (long long)(n - i0) * bd.E;
-  {
-    // algorithmic bytes: read obs and act, write the rows (obs, act, episode end)
-    TraceLaunch tr(CRL_TRACE_INSERT, st, (double)rows * ((bd.D + bd.A) * 4.0 + (bd.D + bd.A + 1) * 4.0));
-    launch_k(insert_rows_kernel, dim3(ceil_div(rows, 4)), dim3(128), 0, st, bd, obs, act, n, i0, total_before);
-  }
-  TraceLaunch tr(CRL_TRACE_INSERT, st, (double)n * bd.E);  // read the done flags
-  launch_k(close_episodes_kernel, dim3(ceil_div(bd.E, 4)), dim3(128), 0, st, bd, done, n, total_before);
+  // algorithmic bytes: read obs, act and the done flags, write the rows (obs, act, episode end)
+  TraceLaunch tr(CRL_TRACE_INSERT, st,
+                 (double)rows * ((bd.D + bd.A) * 4.0 + (bd.D + bd.A + 1) * 4.0) + (double)n * bd.E);
+  launch_k(insert_kernel, dim3(ceil_div(bd.E, 4)), dim3(128), 0, st, bd, obs, act, done, n, i0, total_before);
 }
 
 // ---------------------------------------------------------------------------
@@ -119,74 +111,108 @@ __device__ __forceinline__ int geometric_offset(unsigned long long v, int L, int
   return lo;
 }
 
-// One warp per sample: lane 0 draws the Philox block and the offset, the warp
-// copies the state-action row and the goal dims.
+// Indices of sample b from Philox4x64-10 block (step, b, 0, 0): the
+// transition (e, t), t counted from the oldest stored step, uniform over the
+// E x size stored steps (word 0), and the offset k from the geometric
+// distribution truncated to the episode (top half of word 1).
+__device__ __forceinline__ void sample_indices(const BufferDev& bd, const RelabelArgs& ra, unsigned long long step,
+                                               int b, int size, long long total, int& e, int& t, int& k) {
+  const Philox4 r = philox4x64_10(step, (unsigned long long)b, 0ull, 0ull, ra.seed, ra.agent);
+  const unsigned long long nstored = (unsigned long long)size * (unsigned long long)bd.E;
+  const unsigned long long idx = __umul64hi(r.w[0], nstored);
+  e = (int)(idx / (unsigned long long)size);
+  t = (int)(idx % (unsigned long long)size);
+  const long long abs_t = total - size + t;
+  const float* row = bd.rows + ((size_t)e * bd.T + (size_t)(abs_t % bd.T)) * bd.W;
+  const int ep_end = __float_as_int(row[bd.D + bd.A]);
+  int L = (ep_end < 0) ? (size - 1 - t) : (int)(ep_end - abs_t);
+  if (L < 0 || L > size - 1 - t) {
+    atomicOr(ra.status, CRL_STATUS_BAD_INDEX);
+    L = L < 0 ? 0 : size - 1 - t;
+  }
+  k = geometric_offset(r.w[1] >> 32, L, ra.offset_min, bd.gq);
+}
+
+// One warp per ra.spw consecutive samples (1..32).  Phase 1: lane j < spw
+// draws the indices of sample b0 + j (independent Philox / episode-end /
+// inverse-CDF chains side by side).  Phase 2: the warp copies each sample's
+// state-action row with 16-byte loads (ring rows start on 16-byte boundaries)
+// and gathers its goal dims.  Small batches take spw = 1 (a warp per sample,
+// the most parallel copy); large ones up to 32 (index chains 32 wide).
 __global__ void __launch_bounds__(256) relabel_kernel(BufferDev bd, RelabelArgs ra) {
   pdl_enter();
   const int lane = threadIdx.x % kWarp;
-  const int b = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const int spw = ra.spw;
+  const int b0 = (blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp) * spw;
   const unsigned long long step = (ra.step == CRL_STEP_AUTO) ? *ra.step_dev : ra.step;
   if (blockIdx.x == 0 && threadIdx.x == 0 && ra.last_step_dev != nullptr) *ra.last_step_dev = step;
-  if (b >= ra.B) return;
+  if (b0 >= ra.B) return;
   const int size = bd.state[0];
   const long long total = bd.state[1];
   if (size <= 0) {
     if (lane == 0) atomicOr(ra.status, CRL_STATUS_BAD_INDEX);
     return;
   }
+  const int b = b0 + lane;
   int e = 0, t = 0, k = 0;
-  if (lane == 0) {
-    const Philox4 r = philox4x64_10(step, (unsigned long long)b, 0ull, 0ull, ra.seed, ra.agent);
-    const unsigned long long nstored = (unsigned long long)size * (unsigned long long)bd.E;
-    const unsigned long long idx = __umul64hi(r.w[0], nstored);
-    e = (int)(idx / (unsigned long long)size);
-    t = (int)(idx % (unsigned long long)size);
-    const long long abs_t = total - size + t;
-    const float* row = bd.rows + ((size_t)e * bd.T + (size_t)(abs_t % bd.T)) * bd.W;
-    const int ep_end = __float_as_int(row[bd.D + bd.A]);
-    int L = (ep_end < 0) ? (size - 1 - t) : (int)(ep_end - abs_t);
-    if (L < 0 || L > size - 1 - t) {
-      atomicOr(ra.status, CRL_STATUS_BAD_INDEX);
-      L = L < 0 ? 0 : size - 1 - t;
-    }
-    k = geometric_offset(r.w[1] >> 32, L, ra.offset_min, bd.gq);
-  }
-  e = __shfl_sync(0xffffffffu, e, 0);
-  t = __shfl_sync(0xffffffffu, t, 0);
-  k = __shfl_sync(0xffffffffu, k, 0);
-  const long long abs_t = total - size + t;
-  const float* row = bd.rows + ((size_t)e * bd.T + (size_t)(abs_t % bd.T)) * bd.W;
-  const float* grow = bd.rows + ((size_t)e * bd.T + (size_t)((abs_t + k) % bd.T)) * bd.W;
-  for (int c = lane; c < bd.D + bd.A; c += kWarp) {
-    const float v = row[c];
-    if (c < bd.D) ra.s[(size_t)b * bd.D + c] = v;
-    else ra.a[(size_t)b * bd.A + (c - bd.D)] = v;
-  }
-  if (lane < ra.G) ra.g[(size_t)b * ra.G + lane] = grow[ra.goal_idx[lane]];
-  // BF16 split packs of the network inputs (hi, lo interleaved; transposed copy)
-  for (int k = 0; k < 3; ++k) {
-    const RelabelPack& pk = ra.pack[k];
-    if (pk.x0 == nullptr) continue;
-    const int ncol = (k == 0) ? bd.D + bd.A : (k == 1 ? ra.G : bd.D + ra.G);
-    __nv_bfloat16* x0 = static_cast<__nv_bfloat16*>(pk.x0);
-    __nv_bfloat16* xT = static_cast<__nv_bfloat16*>(pk.x0T);
-    for (int c = lane; c < ncol; c += kWarp) {
-      float v;
-      if (k == 0) v = row[c];
-      else if (k == 1) v = grow[ra.goal_idx[c]];
-      else v = c < bd.D ? row[c] : grow[ra.goal_idx[c - bd.D]];
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-      x0[(size_t)b * pk.ld + 2 * c] = hi;
-      x0[(size_t)b * pk.ld + 2 * c + 1] = lo;
-      xT[(size_t)(2 * c) * pk.ldt + b] = hi;
-      xT[(size_t)(2 * c + 1) * pk.ldt + b] = lo;
+  if (lane < spw && b < ra.B) {
+    sample_indices(bd, ra, step, b, size, total, e, t, k);
+    if (ra.idx != nullptr) {
+      ra.idx[3 * (size_t)b + 0] = e;
+      ra.idx[3 * (size_t)b + 1] = t;
+      ra.idx[3 * (size_t)b + 2] = k;
     }
   }
-  if (ra.idx != nullptr && lane == 0) {
-    ra.idx[3 * (size_t)b + 0] = e;
-    ra.idx[3 * (size_t)b + 1] = t;
-    ra.idx[3 * (size_t)b + 2] = k;
+  const int nb = min(spw, ra.B - b0);
+  const int D = bd.D, DA = bd.D + bd.A;
+  const int nv = (DA + 3) / 4;          // float4 chunks over obs + act (the tail chunk may hold ep_end / pad)
+  const bool s_vec = (D % 4) == 0;      // s rows 16-byte aligned
+  for (int j = 0; j < nb; ++j) {
+    const int ej = __shfl_sync(0xffffffffu, e, j);
+    const int tj = __shfl_sync(0xffffffffu, t, j);
+    const int kj = __shfl_sync(0xffffffffu, k, j);
+    const int bj = b0 + j;
+    const long long abs_t = total - size + tj;
+    const float* row = bd.rows + ((size_t)ej * bd.T + (size_t)(abs_t % bd.T)) * bd.W;
+    const float* grow = bd.rows + ((size_t)ej * bd.T + (size_t)((abs_t + kj) % bd.T)) * bd.W;
+    float* srow = ra.s + (size_t)bj * D;
+    float* arow = ra.a + (size_t)bj * bd.A;
+    for (int q = lane; q < nv; q += kWarp) {
+      const float4 v = *reinterpret_cast<const float4*>(row + 4 * q);
+      const int c = 4 * q;
+      if (s_vec && c + 3 < D) {
+        *reinterpret_cast<float4*>(srow + c) = v;
+      } else {
+        const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int ci = c + i;
+          if (ci < D) srow[ci] = x[i];
+          else if (ci < DA) arow[ci - D] = x[i];
+        }
+      }
+    }
+    if (lane < ra.G) ra.g[(size_t)bj * ra.G + lane] = grow[ra.goal_idx[lane]];
+    // BF16 split packs of the network inputs (hi, lo interleaved; transposed copy)
+    for (int kk = 0; kk < 3; ++kk) {
+      const RelabelPack& pk = ra.pack[kk];
+      if (pk.x0 == nullptr) continue;
+      const int ncol = (kk == 0) ? DA : (kk == 1 ? ra.G : D + ra.G);
+      __nv_bfloat16* x0 = static_cast<__nv_bfloat16*>(pk.x0);
+      __nv_bfloat16* xT = static_cast<__nv_bfloat16*>(pk.x0T);
+      for (int c = lane; c < ncol; c += kWarp) {
+        float v;
+        if (kk == 0) v = row[c];
+        else if (kk == 1) v = grow[ra.goal_idx[c]];
+        else v = c < D ? row[c] : grow[ra.goal_idx[c - D]];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        x0[(size_t)bj * pk.ld + 2 * c] = hi;
+        x0[(size_t)bj * pk.ld + 2 * c + 1] = lo;
+        xT[(size_t)(2 * c) * pk.ldt + bj] = hi;
+        xT[(size_t)(2 * c + 1) * pk.ldt + bj] = lo;
+      }
+    }
   }
 }
 
@@ -194,7 +220,10 @@ void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st)
   // algorithmic bytes per sample: read obs + act + episode end + goal dims, write s, a, g (+ idx)
   const double per = (bd.D + bd.A + 1 + ra.G) * 4.0 + (bd.D + bd.A + ra.G) * 4.0 + (ra.idx ? 12.0 : 0.0);
   TraceLaunch tr(CRL_TRACE_RELABEL, st, per * ra.B);
-  launch_k(relabel_kernel, dim3(ceil_div(ra.B, 8)), dim3(256), 0, st, bd, ra);
+  // samples per warp: as many warps as fill the GPU (152 SMs x 48 resident warps), at most 32
+  RelabelArgs r = ra;
+  r.spw = (int)std::min<long long>(32, std::max<long long>(1, (long long)ra.B / (152 * 48)));
+  launch_k(relabel_kernel, dim3(ceil_div(ra.B, 8 * r.spw)), dim3(256), 0, st, bd, r);
 }
 
 __global__ void bump_u64_kernel(unsigned long long* c) {

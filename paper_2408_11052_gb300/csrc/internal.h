@@ -1,6 +1,7 @@
 // Internal interfaces between the translation units of libcrl (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -46,6 +47,7 @@ struct RelabelArgs {
   int32_t* idx;                     // [B][3] or null
   unsigned* status;                 // device status word
   RelabelPack pack[3];              // phi (s, a), psi (g), pi (s, g); x0 == null: not written
+  int spw;                          // samples per warp (set by launch_relabel)
 };
 
 void launch_buffer_insert(const BufferDev& bd, const float* obs, const float* act, const uint8_t* done,
@@ -95,16 +97,47 @@ struct ActorSpec {
   double tau, alpha;
 };
 // eps: explicit [B][A] (may be float for a T = double path) or null -> Philox noise.
+// x0 != null: a' is also written, split into BF16 (hi, lo), into columns
+// [x0_col, x0_col + A) of the BF16 network input x0 (row stride x0_ld).
 template <typename T>
 void actor_head_forward(const ActorSpec& as, const T* pi_out, const float* eps,
                         const unsigned long long* step_dev, uint64_t seed, uint64_t agent, int B,
-                        T* a_new, T* logpi, T* eps_used, cudaStream_t st);
+                        T* a_new, T* logpi, T* eps_used, cudaStream_t st, __nv_bfloat16* x0 = nullptr,
+                        int x0_ld = 0, int x0_col = 0);
+template <typename T>
+struct ActorLossArgs {
+  int B, R, energy;
+  double tau, alpha;
+  const T* phi;
+  const T* psi;
+  const T* logpi;
+  T* fdiag;
+  T* dphi;
+  __nv_bfloat16* dz;
+  int ldz;
+  T* partial;                 // [ceil(B / 8)][2]
+  unsigned* ticket;           // zero between launches
+  T* loss2;
+  unsigned* status;
+  int* t_bump;
+  unsigned long long* step_bump;
+  const unsigned long long* last_step;
+};
+size_t actor_loss_ws_bytes(int B, size_t elem);
+// Diagonal energy, dphi (T, or BF16 into dz [B][ldz] when dz != null) and the
+// actor loss in one launch.  ws: actor_loss_ws_bytes(B, sizeof(T)); ticket: a
+// zero-initialised device word.  t_bump: ++*t_bump; step_bump: *step_bump =
+// *last_step + 1 (both optional).
 template <typename T>
 void actor_energy_and_loss(const ActorSpec& as, const T* phi, const T* psi, const T* logpi, int B, int R,
-                           T* dphi, T* fdiag, T* loss2, unsigned* status, int* t_bump, cudaStream_t st);
+                           T* dphi, T* fdiag, T* loss2, void* ws, unsigned* ticket, unsigned* status,
+                           int* t_bump, unsigned long long* step_bump, const unsigned long long* last_step,
+                           cudaStream_t st, __nv_bfloat16* dz = nullptr, int ldz = 0);
+// dz != null: the output gradient is written as BF16 dz [B][ldz] and dz^T [2A][ldt] instead of dout.
 template <typename T>
 void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used, const T* da, int B,
-                         T* dout, cudaStream_t st);
+                         T* dout, cudaStream_t st, __nv_bfloat16* dz = nullptr, int ldz = 0,
+                         __nv_bfloat16* dzT = nullptr, int ldt = 0);
 
 // ---------------------------------------------------------------- Adam
 template <typename T>

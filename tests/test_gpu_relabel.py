@@ -84,8 +84,9 @@ def test_relabel_errors():
         ctx.sample(step=0, B=32)
     assert e.value.code == api.E_BUFFER_EMPTY
     ctx, _, _ = setup(w, n=10)
+    one = [torch.empty(1, n, dtype=torch.float32, device=ctx.device) for n in (w.D, w.A, w.G)]
     with pytest.raises(api.CRLError) as e:
-        ctx.sample(step=0, B=33)
+        ctx.sample(step=0, B=0, out=(*one, None))
     assert e.value.code == api.E_SHAPE
 
 
@@ -103,3 +104,23 @@ def test_relabel_full_size_large_batch_sampled_rows():
     ctx, _, buf = setup(w, perturb=False, mean_len=None)
     rows = list(range(0, w.B, 8))
     compare(ctx, buf, w, 3, w.B, sample_rows=rows)
+
+
+def test_relabel_batch_larger_than_config():
+    """A standalone sample may exceed the configured batch (the outputs are the
+    caller's): 5000 samples on a context built for 32, every row checked."""
+    w = small(B=32)
+    ctx, _, buf = setup(w, n=90, mean_len=6.0)
+    compare(ctx, buf, w, 77, 5000)
+    assert ctx.sync_status() == (0, 0)
+
+
+def test_relabel_throughput_shapes_sampled():
+    """The relabel throughput measurement's launch: Humanoid-shaped rows (obs 268,
+    action 17, goal 3), 1024 envs x 1000 steps, 2^20 samples; 2000 rows checked."""
+    w = workload.Workload("relabel", E=1024, T=1000, D=268, A=17, G=3, B=256, hidden=64, layers=1, repr=64,
+                          seed=5)
+    ctx, _, buf = setup(w, perturb=False, mean_len=None)
+    rows = np.random.default_rng(3).choice(1 << 20, 2000, replace=False)
+    compare(ctx, buf, w, 4242, 1 << 20, sample_rows=rows)
+    assert ctx.sync_status() == (0, 0)
