@@ -266,13 +266,19 @@ def run_arm(args, w, precision, path, dev, world, rank, flush, full):
     assert rc == api.OK, f"warm-up status {status}"
     out = {}
     if full:
-        # kernels per step: count every traced class over one untimed step
-        launches = 0
+        # kernels per step and the time of each kernel class: every class traced
+        # over 20 eager steps (CUDA events around each of its launches)
+        launches, breakdown = 0, {}
         for cls in api.TRACE:
             ctx.trace_start(cls, 4096)
-            step_device()
-            launches += ctx.trace_stop()[0]
+            for _ in range(20):
+                step_device()
+            n, cls_ms, _ = ctx.trace_stop()
+            launches += n // 20
+            breakdown[cls] = {"launches_per_step": n // 20, "us_per_step": 1e3 * cls_ms / 20,
+                              "us_per_launch": 1e3 * cls_ms / max(n, 1)}
         out["launches_per_step"] = launches
+        out["breakdown"] = breakdown
 
     # timed region: graph-replayed steps, no tracing (tracing forces eager launches)
     with ClockSampler(dev.index) as clk:
@@ -363,7 +369,7 @@ def main():
     torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     if args.only_relabel:
-        rw, res = relabel_throughput(dev, flush, sizes=(1 << 20,), K=3, W=1)
+        rw, res = relabel_throughput(dev, flush)
         print(json.dumps({"relabel": {"workload": rw.name, "results": res}}), flush=True)
         return
 
@@ -432,6 +438,8 @@ def main():
             "e2e": {"value": world * args.steps / (main_arm["e2e_ms"] / 1e3), "unit": "update steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
             "gpu_launches": main_arm["launches_per_step"] * args.steps,
+            "breakdown": {"timing": "eager, events around every launch (no launch overlap): sums exceed ms_per_step",
+                          **main_arm["breakdown"]},
             "roofline": roof,
             "clocks": main_arm["clocks"]}
     if comparator is not None:

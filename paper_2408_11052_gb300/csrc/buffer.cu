@@ -133,6 +133,11 @@ __device__ __forceinline__ void sample_indices(const BufferDev& bd, const Relabe
   k = geometric_offset(r.w[1] >> 32, L, ra.offset_min, bd.gq);
 }
 
+#ifndef CRL_RELABEL_UNROLL
+#define CRL_RELABEL_UNROLL 2
+#endif
+constexpr int kRelabelUnroll = CRL_RELABEL_UNROLL;  // samples whose loads are in flight together
+
 // One warp per ra.spw consecutive samples (1..32).  Phase 1: lane j < spw
 // draws the indices of sample b0 + j (independent Philox / episode-end /
 // inverse-CDF chains side by side).  Phase 2: the warp copies each sample's
@@ -167,6 +172,58 @@ __global__ void __launch_bounds__(256) relabel_kernel(BufferDev bd, RelabelArgs 
   const int D = bd.D, DA = bd.D + bd.A;
   const int nv = (DA + 3) / 4;          // float4 chunks over obs + act (the tail chunk may hold ep_end / pad)
   const bool s_vec = (D % 4) == 0;      // s rows 16-byte aligned
+  const bool packs = ra.pack[0].x0 || ra.pack[1].x0 || ra.pack[2].x0;
+  if (!packs && nv <= 4 * kWarp) {
+    // kRelabelUnroll samples at a time: every load of the group issues before any store
+    constexpr int U = kRelabelUnroll;
+    for (int j0 = 0; j0 < nb; j0 += U) {
+      float4 v[U][4];
+      float gv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = min(j0 + u, nb - 1);
+        const int ej = __shfl_sync(0xffffffffu, e, j);
+        const int tj = __shfl_sync(0xffffffffu, t, j);
+        const int kj = __shfl_sync(0xffffffffu, k, j);
+        const long long abs_t = total - size + tj;
+        const float* row = bd.rows + ((size_t)ej * bd.T + (size_t)(abs_t % bd.T)) * bd.W;
+        const float* grow = bd.rows + ((size_t)ej * bd.T + (size_t)((abs_t + kj) % bd.T)) * bd.W;
+        const bool live = j0 + u < nb;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int q = lane + kWarp * r;
+          if (live && q < nv) v[u][r] = __ldcs(reinterpret_cast<const float4*>(row) + q);
+        }
+        gv[u] = (live && lane < ra.G) ? grow[ra.goal_idx[lane]] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (j0 + u >= nb) break;
+        const int bj = b0 + j0 + u;
+        float* srow = ra.s + (size_t)bj * D;
+        float* arow = ra.a + (size_t)bj * bd.A;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int q = lane + kWarp * r;
+          if (q >= nv) break;
+          const int c = 4 * q;
+          if (s_vec && c + 3 < D) {
+            __stcs(reinterpret_cast<float4*>(srow + c), v[u][r]);
+          } else {
+            const float x[4] = {v[u][r].x, v[u][r].y, v[u][r].z, v[u][r].w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int ci = c + i;
+              if (ci < D) __stcs(srow + ci, x[i]);
+              else if (ci < DA) __stcs(arow + ci - D, x[i]);
+            }
+          }
+        }
+        if (lane < ra.G) __stcs(ra.g + (size_t)bj * ra.G + lane, gv[u]);
+      }
+    }
+    return;
+  }
   for (int j = 0; j < nb; ++j) {
     const int ej = __shfl_sync(0xffffffffu, e, j);
     const int tj = __shfl_sync(0xffffffffu, t, j);
