@@ -267,6 +267,41 @@ const char* crl_last_error(const crl_ctx* ctx);
 int crl_trace_start(crl_ctx* ctx, int32_t kernel_class, int32_t max_launches);
 int crl_trace_stop(crl_ctx* ctx, int32_t* launches, double* total_ms, double* work);
 
+/* ---- batched sweep (library extension: the paper trains one agent per run;
+ * its multi-seed experiments, §5, become one GPU program) -------------------
+ * A sweep owns n independent agents (1 <= n <= 64), each a full context built
+ * from cfgs[i] (its own replay buffer, networks and Philox key (seed, agent)).
+ * The agents share precision, path, hidden width, depth and LayerNorm; batch,
+ * obs / action / goal dims, buffer size, repr and hyperparameters may differ.
+ * grouped = 1 (BF16 fused only): every kernel of the update step is one launch
+ * over all agents (grouped tcgen05 GEMMs over every agent's networks of a
+ * layer; block-offset tables for the other kernels).  grouped = 0 (any
+ * precision): the agents' update steps one after another.  Each agent's
+ * results are those of crl_update_step on that agent alone.
+ * CRL_E_INVALID_ARG / CRL_E_UNSUPPORTED on mismatched or unsupported configs. */
+typedef struct crl_sweep crl_sweep;
+int crl_sweep_create(const crl_config* cfgs, int32_t n, int32_t grouped, crl_sweep** out);
+int crl_sweep_destroy(crl_sweep* sw);     /* destroys the agents' contexts too */
+/* Agent i's context, owned by the sweep (do not crl_destroy it): bind its
+ * parameters, fill its buffer, read its state with the single-agent calls.
+ * Re-binding an agent's parameters makes the next sweep step rebuild its
+ * launch tables and graph. */
+int crl_sweep_agent(crl_sweep* sw, int32_t i, crl_ctx** ctx);
+/* One update step of every agent (crl_update_step per agent): insert n_insert
+ * time slices into each agent's buffer (obs[i] [n][E_i][D_i], act[i], done[i]
+ * as crl_buffer_insert; device pointers go into one launch, host pointers are
+ * staged per agent; arrays may be NULL when n_insert = 0), then relabel,
+ * critic + Adam, actor + Adam.  The step after the first is captured once as a
+ * CUDA graph on `stream` (not the legacy default stream) and replayed.
+ * loss_out: [n][6] floats (the crl_update_step layout per agent), host or
+ * device, or NULL. */
+int crl_sweep_update_step(crl_sweep* sw, const float* const* obs, const float* const* act,
+                          const uint8_t* const* done, int32_t n_insert, float* loss_out, void* stream);
+/* OR of the status words of the sweep's shared launches and of every agent
+ * (read and cleared); the return code as crl_sync_status. */
+int crl_sweep_sync_status(crl_sweep* sw, void* stream, uint32_t* status);
+const char* crl_sweep_last_error(const crl_sweep* sw);
+
 /* ---- launch overlap (library extension; the paper has no counterpart) -----
  * Process-wide.  enable = 1 (the default): every kernel of the library is
  * launched with programmatic stream serialisation, so it is scheduled while

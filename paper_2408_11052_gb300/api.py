@@ -85,6 +85,13 @@ _SIGNATURES = {
     "crl_trace_start": (c_int32, [c_void_p, c_int32, c_int32]),
     "crl_trace_stop": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_double), POINTER(c_double)]),
     "crl_set_launch_overlap": (c_int32, [c_int32]),
+    "crl_sweep_create": (c_int32, [POINTER(CrlConfig), c_int32, c_int32, POINTER(c_void_p)]),
+    "crl_sweep_destroy": (c_int32, [c_void_p]),
+    "crl_sweep_agent": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
+    "crl_sweep_update_step": (c_int32, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p), c_int32,
+                                        c_void_p, c_void_p]),
+    "crl_sweep_sync_status": (c_int32, [c_void_p, c_void_p, POINTER(c_uint32)]),
+    "crl_sweep_last_error": (ctypes.c_char_p, [c_void_p]),
     "crl_mlp_saved_bytes": (c_int32, [POINTER(CrlMlpDesc), c_int32, POINTER(c_size_t)]),
     "crl_mlp_forward": (c_int32, [POINTER(CrlMlpDesc), c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
                                   c_void_p]),
@@ -201,14 +208,19 @@ class CRLContext:
     for the FP64 check path.
     """
 
-    def __init__(self, workload, precision="fp32", path="plain", device="cuda", agent=0, offset_min=1, **over):
+    def __init__(self, workload, precision="fp32", path="plain", device="cuda", agent=0, offset_min=1,
+                 _handle=None, **over):
         import torch
         self.w = workload
         self.cfg = make_config(workload, precision, path, agent, offset_min, **over)
         self.device = torch.device(device)
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
-        h = c_void_p()
-        check(lib().crl_create(byref(self.cfg), byref(h)))
+        self.owned = _handle is None
+        if _handle is None:
+            h = c_void_p()
+            check(lib().crl_create(byref(self.cfg), byref(h)))
+        else:
+            h = _handle                      # an agent of a sweep: the sweep owns it
         self.handle = h
         self.layout = {}
         self.store = {}
@@ -317,7 +329,73 @@ class CRLContext:
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
-            lib().crl_destroy(self.handle)
+            if getattr(self, "owned", True):
+                lib().crl_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CRLSweep:
+    """Independent agents advanced together by ``crl_sweep_update_step``.
+
+    ``workloads``: one Workload per agent (shared hidden width, depth and
+    LayerNorm).  ``grouped``: one launch per kernel over all agents (BF16
+    fused); otherwise the agents' steps run one after another.  ``agents[i]``
+    is a CRLContext view of agent i (parameters as torch tensors, buffer,
+    single-agent calls); the sweep owns the contexts.
+    """
+
+    def __init__(self, workloads, precision="bf16", path="fused", grouped=True, device="cuda", offset_min=1):
+        import torch
+        self.device = torch.device(device)
+        cfgs = (CrlConfig * len(workloads))()
+        for i, w in enumerate(workloads):
+            cfgs[i] = make_config(w, precision, path, agent=i, offset_min=offset_min)
+        h = c_void_p()
+        rc = lib().crl_sweep_create(cfgs, len(workloads), 1 if grouped else 0, byref(h))
+        if rc != OK:
+            raise CRLError(rc, lib().crl_sweep_last_error(None).decode())
+        self.handle = h
+        self.n = len(workloads)
+        self.agents = []
+        for i, w in enumerate(workloads):
+            a = c_void_p()
+            self._check(lib().crl_sweep_agent(self.handle, i, byref(a)))
+            self.agents.append(CRLContext(w, precision, path, device, agent=i, offset_min=offset_min, _handle=a))
+
+    def _check(self, rc):
+        if rc != OK:
+            raise CRLError(rc, lib().crl_sweep_last_error(self.handle).decode())
+
+    def update_step(self, obs=None, act=None, done=None, loss_out=None, stream=None):
+        """obs / act / done: per-agent lists of [n][E_i][...] tensors (same n), or None."""
+        n = 0 if obs is None else obs[0].shape[0]
+        arrays = []
+        for xs in (obs, act, done):
+            arr = (c_void_p * self.n)()
+            if xs is not None:
+                for i, x in enumerate(xs):
+                    arr[i] = ptr(x)
+            arrays.append(arr)
+        self._check(lib().crl_sweep_update_step(self.handle, arrays[0], arrays[1], arrays[2], n, ptr(loss_out),
+                                                stream_handle(stream)))
+        return loss_out
+
+    def sync_status(self, stream=None):
+        s = c_uint32()
+        rc = lib().crl_sweep_sync_status(self.handle, stream_handle(stream), byref(s))
+        return rc, s.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            for a in self.agents:
+                a.handle = c_void_p()
+            lib().crl_sweep_destroy(self.handle)
             self.handle = c_void_p()
 
     def __del__(self):

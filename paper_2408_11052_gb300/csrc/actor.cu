@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tables.h"
 #include "philox.cuh"
 #include "trace.h"
 
@@ -55,18 +56,19 @@ __device__ T philox_normal(unsigned long long step, int b, int d, unsigned long 
 // x0 != null: a' also goes into columns [x0_col, x0_col + A) of the split BF16
 // network input x0 (hi, lo interleaved: element c at 2c, 2c + 1).
 template <typename T>
-__global__ void __launch_bounds__(256) head_forward_kernel(int B, int A, const T* __restrict__ out,
-                                                          const float* __restrict__ eps,
-                                                          const unsigned long long* __restrict__ step_dev,
-                                                          unsigned long long seed, unsigned long long agent,
-                                                          T* __restrict__ a_new, T* __restrict__ logpi,
-                                                          T* __restrict__ eps_used, __nv_bfloat16* __restrict__ x0,
-                                                          int x0_ld, int x0_col) {
-  pdl_enter();
+__device__ __forceinline__ void head_forward_body(const HeadFwdArgs<T>& p, int lb) {
+  const int B = p.B, A = p.A;
+  const T* __restrict__ out = p.out;
+  const float* __restrict__ eps = p.eps;
+  T* __restrict__ a_new = p.a_new;
+  T* __restrict__ eps_used = p.eps_used;
+  __nv_bfloat16* __restrict__ x0 = p.x0;
+  const int x0_ld = p.x0_ld, x0_col = p.x0_col;
+  const unsigned long long seed = p.seed, agent = p.agent;
   const int lane = threadIdx.x % kWarp;
-  const int b = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const int b = lb * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   if (b >= B) return;
-  const unsigned long long step = eps ? 0ull : *step_dev;
+  const unsigned long long step = eps ? 0ull : *p.step_dev;
   T lp = 0;
   for (int d = lane; d < A; d += kWarp) {
     const T mu = out[(size_t)b * 2 * A + d];
@@ -87,7 +89,13 @@ __global__ void __launch_bounds__(256) head_forward_kernel(int B, int A, const T
     lp += -T(0.5) * e * e - T(kHalfLog2Pi) - l - T(2) * (T(kLog2) - u - softplus(T(-2) * u));
   }
   lp = warp_sum(lp);
-  if (lane == 0) logpi[b] = lp;
+  if (lane == 0) p.logpi[b] = lp;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) head_forward_kernel(const __grid_constant__ HeadFwdArgs<T> p) {
+  pdl_enter();
+  head_forward_body(p, blockIdx.x);
 }
 
 // f_i = f(phi_i, psi_i) / tau and dphi_i = -(1/B) df_i/dphi_i, one warp per
@@ -97,12 +105,11 @@ __global__ void __launch_bounds__(256) head_forward_kernel(int B, int A, const T
 // depend on which block finishes last.  dz != null: dphi is written as BF16
 // [B][ldz] (the phi network's output gradient) instead of T.
 template <typename T>
-__global__ void __launch_bounds__(256) diag_energy_loss_kernel(ActorLossArgs<T> p) {
-  pdl_enter();
+__device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p, int lb, int nb) {
   __shared__ T s_a[8], s_l[8];
   __shared__ int s_last;
   const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
-  const int i = blockIdx.x * 8 + w;
+  const int i = lb * 8 + w;
   const int B = p.B, R = p.R;
   T term = 0, lpi = 0;
   if (i < B) {
@@ -166,17 +173,17 @@ __global__ void __launch_bounds__(256) diag_energy_loss_kernel(ActorLossArgs<T> 
       a += s_a[k];
       l += s_l[k];
     }
-    p.partial[2 * blockIdx.x] = a;
-    p.partial[2 * blockIdx.x + 1] = l;
+    p.partial[2 * lb] = a;
+    p.partial[2 * lb + 1] = l;
     __threadfence();
-    s_last = (atomicAdd(p.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+    s_last = (atomicAdd(p.ticket, 1u) == (unsigned)nb - 1u) ? 1 : 0;
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   __shared__ T sm[32];
   T a = 0, l = 0;
-  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
     a += *((volatile T*)p.partial + 2 * k);
     l += *((volatile T*)p.partial + 2 * k + 1);
   }
@@ -193,16 +200,26 @@ __global__ void __launch_bounds__(256) diag_energy_loss_kernel(ActorLossArgs<T> 
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) diag_energy_loss_kernel(const __grid_constant__ ActorLossArgs<T> p) {
+  pdl_enter();
+  diag_energy_loss_body(p, blockIdx.x, gridDim.x);
+}
+
 // dz != null: the gradient is written as BF16 dz [B][ldz] and dz^T [2A][ldt]
 // (the policy network's output gradient) instead of dout.
 template <typename T>
-__global__ void __launch_bounds__(256) head_backward_kernel(int B, int A, double alpha, const T* __restrict__ out,
-                                                           const T* __restrict__ eps_used,
-                                                           const T* __restrict__ da, T* __restrict__ dout,
-                                                           __nv_bfloat16* __restrict__ dz, int ldz,
-                                                           __nv_bfloat16* __restrict__ dzT, int ldt) {
-  pdl_enter();
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void head_backward_body(const HeadBwdArgs<T>& p, int lb) {
+  const int B = p.B, A = p.A;
+  const double alpha = p.alpha;
+  const T* __restrict__ out = p.out;
+  const T* __restrict__ eps_used = p.eps_used;
+  const T* __restrict__ da = p.da;
+  T* __restrict__ dout = p.dout;
+  __nv_bfloat16* __restrict__ dz = p.dz;
+  __nv_bfloat16* __restrict__ dzT = p.dzT;
+  const int ldz = p.ldz, ldt = p.ldt;
+  const int b = lb * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const T ab = T(alpha / B);
   for (int d = 0; d < A; ++d) {
@@ -229,6 +246,48 @@ __global__ void __launch_bounds__(256) head_backward_kernel(int B, int A, double
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) head_backward_kernel(const __grid_constant__ HeadBwdArgs<T> p) {
+  pdl_enter();
+  head_backward_body(p, blockIdx.x);
+}
+
+// ---- several agents in one launch (BF16 path: float) ----------------------------
+__global__ void __launch_bounds__(256) head_forward_multi_kernel(const HeadFwdArgs<float>* __restrict__ tasks,
+                                                                const int* __restrict__ begin, int n) {
+  pdl_enter();
+  int lb, nb;
+  const int s = segment_of(begin, n, blockIdx.x, lb, nb);
+  head_forward_body(tasks[s], lb);
+}
+__global__ void __launch_bounds__(256) diag_energy_loss_multi_kernel(const ActorLossArgs<float>* __restrict__ tasks,
+                                                                    const int* __restrict__ begin, int n) {
+  pdl_enter();
+  int lb, nb;
+  const int s = segment_of(begin, n, blockIdx.x, lb, nb);
+  diag_energy_loss_body(tasks[s], lb, nb);
+}
+__global__ void __launch_bounds__(256) head_backward_multi_kernel(const HeadBwdArgs<float>* __restrict__ tasks,
+                                                                 const int* __restrict__ begin, int n) {
+  pdl_enter();
+  int lb, nb;
+  const int s = segment_of(begin, n, blockIdx.x, lb, nb);
+  head_backward_body(tasks[s], lb);
+}
+
+// Device tables of `tasks` and their block offsets (rows_per_block rows per block).
+template <class Task>
+const char* multi_tables(BlobCache& cache, const std::vector<Task>& tasks, int rows_per_block, cudaStream_t st,
+                         const Task** dt, const int** db, int* blocks) {
+  std::vector<int> begin(tasks.size() + 1, 0);
+  for (size_t i = 0; i < tasks.size(); ++i) begin[i + 1] = begin[i] + ceil_div(tasks[i].B, rows_per_block);
+  *blocks = begin.back();
+  const char* err = nullptr;
+  if (!(*dt = cache.get(tasks, st, &err))) return err;
+  if (!(*db = cache.get(begin, st, &err))) return err;
+  return nullptr;
+}
+
 }  // namespace
 
 template <typename T>
@@ -236,8 +295,49 @@ void actor_head_forward(const ActorSpec& as, const T* pi_out, const float* eps, 
                         uint64_t seed, uint64_t agent, int B, T* a_new, T* logpi, T* eps_used, cudaStream_t st,
                         __nv_bfloat16* x0, int x0_ld, int x0_col) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 5);
-  launch_k(head_forward_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, B, as.A, pi_out, eps, step_dev, seed,
-           agent, a_new, logpi, eps_used, x0, x0_ld, x0_col);
+  const HeadFwdArgs<T> p{B, as.A, pi_out, eps, step_dev, seed, agent, a_new, logpi, eps_used, x0, x0_ld, x0_col};
+  launch_k(head_forward_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, p);
+}
+
+const char* actor_head_forward_multi(BlobCache& cache, const std::vector<HeadFwdArgs<float>>& tasks,
+                                     cudaStream_t st) {
+  if (tasks.empty()) return nullptr;
+  const HeadFwdArgs<float>* dt;
+  const int* db;
+  int blocks;
+  if (const char* err = multi_tables(cache, tasks, 8, st, &dt, &db, &blocks)) return err;
+  double bytes = 0.0;
+  for (const auto& t : tasks) bytes += (double)t.B * t.A * 4.0 * 5;
+  TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
+  launch_k(head_forward_multi_kernel, dim3(blocks), dim3(256), 0, st, dt, db, (int)tasks.size());
+  return nullptr;
+}
+
+const char* actor_loss_multi(BlobCache& cache, const std::vector<ActorLossArgs<float>>& tasks, cudaStream_t st) {
+  if (tasks.empty()) return nullptr;
+  const ActorLossArgs<float>* dt;
+  const int* db;
+  int blocks;
+  if (const char* err = multi_tables(cache, tasks, 8, st, &dt, &db, &blocks)) return err;
+  double work = 0.0;
+  for (const auto& t : tasks) work += 2.0 * t.B * t.R;
+  TraceLaunch tr(CRL_TRACE_ENERGY, st, work);
+  launch_k(diag_energy_loss_multi_kernel, dim3(blocks), dim3(256), 0, st, dt, db, (int)tasks.size());
+  return nullptr;
+}
+
+const char* actor_head_backward_multi(BlobCache& cache, const std::vector<HeadBwdArgs<float>>& tasks,
+                                      cudaStream_t st) {
+  if (tasks.empty()) return nullptr;
+  const HeadBwdArgs<float>* dt;
+  const int* db;
+  int blocks;
+  if (const char* err = multi_tables(cache, tasks, 256, st, &dt, &db, &blocks)) return err;
+  double bytes = 0.0;
+  for (const auto& t : tasks) bytes += (double)t.B * t.A * 4.0 * 6;
+  TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
+  launch_k(head_backward_multi_kernel, dim3(blocks), dim3(256), 0, st, dt, db, (int)tasks.size());
+  return nullptr;
 }
 
 size_t actor_loss_ws_bytes(int B, size_t elem) { return (size_t)ceil_div(B, 8) * 2 * elem + 256; }
@@ -258,8 +358,8 @@ template <typename T>
 void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used, const T* da, int B, T* dout,
                          cudaStream_t st, __nv_bfloat16* dz, int ldz, __nv_bfloat16* dzT, int ldt) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 6);
-  launch_k(head_backward_kernel<T>, dim3(ceil_div(B, 256)), dim3(256), 0, st, B, as.A, as.alpha, pi_out, eps_used,
-           da, dout, dz, ldz, dzT, ldt);
+  const HeadBwdArgs<T> p{B, as.A, as.alpha, pi_out, eps_used, da, dout, dz, ldz, dzT, ldt};
+  launch_k(head_backward_kernel<T>, dim3(ceil_div(B, 256)), dim3(256), 0, st, p);
 }
 
 #define CRL_INST_ACTOR(T)                                                                                        \

@@ -14,6 +14,7 @@
 #include "energy_tc.cuh"
 #include "internal.h"
 #include "mlp_bf16.cuh"
+#include "ctx.h"
 #include "trace.h"
 
 using namespace crl;
@@ -23,40 +24,9 @@ thread_local Tracer* g_tracer = nullptr;
 int g_launch_overlap = 1;
 }
 
-namespace {
+namespace crl {
 
 thread_local std::string g_thread_error;
-
-struct Counters {
-  unsigned long long step;       // next Philox step for CRL_STEP_AUTO
-  unsigned long long last_step;  // step of the last sample (actor noise)
-  int t_critic;                  // Adam step counters (incremented by the loss kernels)
-  int t_actor;
-  unsigned status;               // CRL_STATUS_* bits
-  unsigned ticket_actor;         // last-block ticket of the actor loss kernel (zero between launches)
-};
-
-class Failure {
- public:
-  int code;
-  std::string msg;
-  Failure(int c, std::string m) : code(c), msg(std::move(m)) {}
-};
-
-#define CRL_CHECK_CUDA(expr)                                                                     \
-  do {                                                                                           \
-    cudaError_t e_ = (expr);                                                                     \
-    if (e_ != cudaSuccess) throw Failure(CRL_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
-#define CRL_REQUIRE(cond, code, msg) \
-  do {                               \
-    if (!(cond)) throw Failure((code), (msg)); \
-  } while (0)
-
-inline void check_launch(const char* what) {
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) throw Failure(CRL_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
 
 bool is_host_pointer(const void* p) {
   cudaPointerAttributes at;
@@ -129,110 +99,19 @@ void validate_config(const crl_config& c) {
   CRL_REQUIRE((int64_t)c.E * c.T * W < ((int64_t)1 << 40), CRL_E_INVALID_ARG, "replay buffer too large");
 }
 
-}  // namespace
+}  // namespace crl
 
-struct crl_ctx {
-  crl_config cfg{};
-  int device = 0;
-  size_t esz = 4;
-  BufferDev bd{};
-  float* rows = nullptr;
-  int32_t* ep_start = nullptr;
-  int32_t* bstate = nullptr;
-  unsigned long long* gq = nullptr;
-  int32_t size_host = 0;
-  int64_t total_host = 0;
-  Counters* ctr = nullptr;
-  bool bound = false;
-  crl_net_ptrs nets[3]{};
-  MlpShape shapes[3]{};
-  int64_t counts[3]{};
-  // workspaces
-  std::vector<void*> allocs;
-  void* saved[3]{};
-  void *phi = nullptr, *psi = nullptr, *dphi = nullptr, *dpsi = nullptr;
-  void *row_lse = nullptr, *col_lse = nullptr, *loss = nullptr, *ws = nullptr;
-  size_t ws_bytes = 0;
-  void *pi_out = nullptr, *a_new = nullptr, *logpi = nullptr, *eps_used = nullptr, *fdiag = nullptr;
-  void *da = nullptr, *dout = nullptr;
-  void* actor_ws = nullptr;  // per-block partial sums of the actor loss
-  float* loss_f = nullptr;  // 8 floats: float copy of the loss parts
-  float *bs = nullptr, *ba = nullptr, *bg = nullptr;  // batch of crl_update_step
-  // host-input staging for crl_buffer_insert
-  void* stage = nullptr;
-  size_t stage_bytes = 0;
-  Tracer tracer;
-  // BF16 tensor-core networks (precision CRL_PREC_BF16)
-  bool bf16 = false;
-  BfNet bf[3];
-  bool shadow_ok[3] = {false, false, false};  // BF16 shadows match the FP32 master weights
-  bool fused = false;
-  EnergyTc etc;
-  void* etc_ws = nullptr;
-  // device problem tables of the grouped tensor-core GEMMs
-  GemmGroups groups;
-  // CUDA graph of relabel -> critic -> actor, replayed by crl_update_step
-  cudaGraphExec_t graph = nullptr;
-  cudaStream_t graph_stream = nullptr;
-  int update_calls = 0;
-  std::string err;
-
-  void* dalloc(size_t bytes) {
-    void* p = nullptr;
-    CRL_CHECK_CUDA(cudaMalloc(&p, bytes > 0 ? bytes : 16));
-    allocs.push_back(p);
-    return p;
-  }
-  void drop_trace_events() {
-    if (tracer.ev) {
-      for (int i = 0; i < 2 * tracer.cap; ++i) cudaEventDestroy(tracer.ev[i]);
-      delete[] tracer.ev;
-    }
-    tracer = Tracer();
-  }
-  void drop_graph() {
-    if (graph) cudaGraphExecDestroy(graph);
-    graph = nullptr;
-    graph_stream = nullptr;
-  }
-  ~crl_ctx() {
-    drop_graph();
-    drop_trace_events();
-    for (void* p : allocs) cudaFree(p);
-    if (stage) cudaFree(stage);
-  }
-};
 
 namespace crl {
 void set_thread_error(const std::string& msg) { g_thread_error = msg; }
 }  // namespace crl
 
-namespace {
+namespace crl {
 
 int fail(crl_ctx* ctx, const Failure& f) {
   if (ctx) ctx->err = f.msg;
   g_thread_error = f.msg;
   return f.code;
-}
-
-// Runs one entry point: maps internal failures to status codes and makes the
-// context's tracer visible to the launch sites for the duration of the call.
-template <typename F>
-int guarded(crl_ctx* ctx, F&& body) {
-  struct TracerScope {
-    explicit TracerScope(crl_ctx* c) { g_tracer = (c && c->tracer.cls) ? &c->tracer : nullptr; }
-    ~TracerScope() { g_tracer = nullptr; }
-  } scope(ctx);
-  try {
-    body();
-    return CRL_OK;
-  } catch (const Failure& f) {
-    return fail(ctx, f);
-  } catch (const std::bad_alloc&) {
-    return fail(ctx, Failure(CRL_E_INVALID_ARG, "host allocation failed"));
-  } catch (...) {
-    return fail(ctx, Failure(CRL_E_INVALID_ARG, "unexpected internal error"));
-  }
 }
 
 LossSpec loss_spec(const crl_config& c) {
@@ -368,8 +247,17 @@ void bf_refresh(crl_ctx* c, int net, bool refresh, cudaStream_t st) {
 
 AdamShadowNet adam_net_of(crl_ctx* c, int net, const int* t, float lr) {
   const crl_net_ptrs& np = c->nets[net];
-  return AdamShadowNet{static_cast<float*>(np.params), static_cast<const float*>(np.grads),
-                       static_cast<float*>(np.adam_m), static_cast<float*>(np.adam_v), c->counts[net], t, lr,
+  const crl_config& cf = c->cfg;
+  return AdamShadowNet{static_cast<float*>(np.params),
+                       static_cast<const float*>(np.grads),
+                       static_cast<float*>(np.adam_m),
+                       static_cast<float*>(np.adam_v),
+                       c->counts[net],
+                       t,
+                       lr,
+                       cf.adam_beta1,
+                       cf.adam_beta2,
+                       cf.adam_eps,
                        &c->bf[net]};
 }
 
@@ -396,15 +284,15 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     bf_net_pack_input(P, s, a, B, st);
     bf_net_pack_input(Q, g, nullptr, B, st);
   }
-  const BfPass pass[3] = {{&P, pphi, static_cast<float*>(c->nets[CRL_NET_PHI].grads), nullptr},
-                          {&Q, ppsi, static_cast<float*>(c->nets[CRL_NET_PSI].grads), nullptr},
+  const BfPass pass[3] = {{&P, pphi, static_cast<float*>(c->nets[CRL_NET_PHI].grads), nullptr, B},
+                          {&Q, ppsi, static_cast<float*>(c->nets[CRL_NET_PSI].grads), nullptr, B},
                           {&c->bf[CRL_NET_PI], static_cast<const float*>(c->nets[CRL_NET_PI].params), nullptr,
-                           nullptr}};
+                           nullptr, B}};
   if (with_pi) {
     bf_maps(c, CRL_NET_PI, B);
     bf_refresh(c, CRL_NET_PI, refresh, st);
   }
-  bf_check(bf_forward(c->groups, pass, with_pi ? 3 : 2, B, status, st));
+  bf_check(bf_forward(c->groups, pass, with_pi ? 3 : 2, status, st));
   float* rl = static_cast<float*>(c->row_lse);
   float* cl = static_cast<float*>(c->col_lse);
   float* loss = static_cast<float*>(c->loss);
@@ -426,12 +314,12 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     bf_net_load_dy(P, dphi, B, st);
     bf_net_load_dy(Q, dpsi, B, st);
   }
-  bf_check(bf_backward(c->groups, pass, 2, B, status, st));
+  bf_check(bf_backward(c->groups, pass, 2, status, st));
   if (apply) {
     // Adam for phi and psi in one launch, refreshing their BF16 shadows
     const AdamShadowNet an[2] = {adam_net_of(c, CRL_NET_PHI, &c->ctr->t_critic, cf.lr_critic),
                                  adam_net_of(c, CRL_NET_PSI, &c->ctr->t_critic, cf.lr_critic)};
-    adam_shadow_update(an, 2, cf.adam_beta1, cf.adam_beta2, cf.adam_eps, st);
+    bf_check(adam_shadow_update(c->tables, an, 2, st));
   }
   check_launch("critic step (bf16)");
 }
@@ -466,27 +354,27 @@ void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* ep
     bf_net_pack_input(Q, g, nullptr, B, st);
   }
   if (!pi_ready) {
-    const BfPass pi_fwd[1] = {{&PI, ppi, nullptr, nullptr}};
-    bf_check(bf_forward(c->groups, pi_fwd, 1, B, status, st));
+    const BfPass pi_fwd[1] = {{&PI, ppi, nullptr, nullptr, B}};
+    bf_check(bf_forward(c->groups, pi_fwd, 1, status, st));
   }
   actor_head_forward<float>(as, PI.y, eps, &c->ctr->last_step, cf.seed, cf.agent, B, a_new, logpi, eps_used, st,
                             packed ? P.x0 : nullptr, bf_net_x0_ld(P), P.s.in0);
   if (!packed) bf_net_pack_input(P, s, a_new, B, st);
   // phi(s, a') and psi(g) with the critic's updated weights
-  const BfPass fwd[2] = {{&P, pphi, nullptr, da}, {&Q, ppsi, nullptr, nullptr}};
-  bf_check(bf_forward(c->groups, fwd, 2, B, status, st));
+  const BfPass fwd[2] = {{&P, pphi, nullptr, da, B}, {&Q, ppsi, nullptr, nullptr, B}};
+  bf_check(bf_forward(c->groups, fwd, 2, status, st));
   actor_energy_and_loss<float>(as, P.y, Q.y, logpi, B, cf.repr, nullptr, static_cast<float*>(c->fdiag), loss,
                                c->actor_ws, &c->ctr->ticket_actor, status, apply ? &c->ctr->t_actor : nullptr,
                                bump_step ? &c->ctr->step : nullptr, &c->ctr->last_step, st, P.dz[P.layers],
                                P.L[P.layers].out_pad);
-  bf_check(bf_backward(c->groups, fwd, 1, B, status, st));
+  bf_check(bf_backward(c->groups, fwd, 1, status, st));
   actor_head_backward<float>(as, PI.y, eps_used, da, B, nullptr, st, PI.dz[PI.layers], PI.L[PI.layers].out_pad,
                              PI.dzT[PI.layers], PI.Mmax);
-  const BfPass pi_pass[1] = {{&PI, ppi, static_cast<float*>(c->nets[CRL_NET_PI].grads), nullptr}};
-  bf_check(bf_backward(c->groups, pi_pass, 1, B, status, st));
+  const BfPass pi_pass[1] = {{&PI, ppi, static_cast<float*>(c->nets[CRL_NET_PI].grads), nullptr, B}};
+  bf_check(bf_backward(c->groups, pi_pass, 1, status, st));
   if (apply) {
     const AdamShadowNet an = adam_net_of(c, CRL_NET_PI, &c->ctr->t_actor, cf.lr_actor);
-    adam_shadow_update(&an, 1, cf.adam_beta1, cf.adam_beta2, cf.adam_eps, st);
+    bf_check(adam_shadow_update(c->tables, &an, 1, st));
   }
   check_launch("actor step (bf16)");
 }
@@ -536,8 +424,9 @@ void insert_impl(crl_ctx* c, const float* obs, const float* act, const uint8_t* 
 
 // bump: advance the step counter after a CRL_STEP_AUTO draw (the update step
 // leaves that to its actor-loss kernel, which runs once per step anyway).
-void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g, int32_t* idx, cudaStream_t st,
-                  bool pack_bf16 = false, bool bump = true) {
+// Checked relabel arguments (spw set for the batch).
+RelabelArgs relabel_args(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g, int32_t* idx,
+                         bool pack_bf16) {
   const crl_config& cf = c->cfg;
   CRL_REQUIRE(s && a && g, CRL_E_INVALID_ARG, "s, a and g must be non-null");
   CRL_REQUIRE(B >= 1, CRL_E_SHAPE, "B must be >= 1");
@@ -566,12 +455,19 @@ void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g
       ra.pack[k] = RelabelPack{n.x0, bf_net_x0_ld(n), n.x0T, n.Mmax};
     }
   }
+  ra.spw = relabel_spw(B);
+  return ra;
+}
+
+void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g, int32_t* idx, cudaStream_t st,
+                  bool pack_bf16, bool bump) {
+  const RelabelArgs ra = relabel_args(c, step, B, s, a, g, idx, pack_bf16);
   launch_relabel(c->bd, ra, st);
   if (step == CRL_STEP_AUTO && bump) launch_bump_u64(&c->ctr->step, st);
   check_launch("sample relabel");
 }
 
-}  // namespace
+}  // namespace crl
 
 // =============================================================================
 extern "C" {
@@ -700,7 +596,8 @@ int crl_create(const crl_config* cfg, crl_ctx** out) {
     c->row_lse = c->dalloc((size_t)B * e);
     c->col_lse = c->dalloc((size_t)B * e);
     c->loss = c->dalloc(8 * e);
-    c->ws_bytes = infonce_ws_bytes(loss_spec(cf), B, R, e, cf.path);
+    // the fused path keeps no B x B buffer (its energy stage has its own small workspace)
+    c->ws_bytes = (cf.path == CRL_PATH_FUSED) ? 0 : infonce_ws_bytes(loss_spec(cf), B, R, e, cf.path);
     c->ws = c->dalloc(c->ws_bytes);
     c->pi_out = c->dalloc((size_t)B * 2 * A * e);
     c->a_new = c->dalloc((size_t)B * A * e);
@@ -777,9 +674,11 @@ int crl_bind_params(crl_ctx* ctx, const crl_net_ptrs nets[3]) {
     CRL_CHECK_CUDA(cudaDeviceSynchronize());
     ctx->drop_graph();
     ctx->groups.reset();   // tables hold parameter pointers
+    ctx->tables.reset();
     ctx->update_calls = 0;
     for (int i = 0; i < 3; ++i) ctx->shadow_ok[i] = false;
     ctx->bound = true;
+    ctx->bind_generation += 1;
   });
 }
 
@@ -836,7 +735,9 @@ int crl_actor_step(crl_ctx* ctx, const float* s, const float* g, const float* ep
   });
 }
 
-namespace {
+}  // extern "C"
+
+namespace crl {
 // relabel (device step counter) -> critic + Adam -> actor + Adam on the batch workspaces
 void update_body(crl_ctx* ctx, cudaStream_t st) {
   const int B = ctx->cfg.B;
@@ -855,7 +756,9 @@ void update_body(crl_ctx* ctx, cudaStream_t st) {
     actor_impl<float>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st, true);
   }
 }
-}  // namespace
+}  // namespace crl
+
+extern "C" {
 
 int crl_update_step(crl_ctx* ctx, const float* obs, const float* act, const uint8_t* done, int32_t n_insert,
                     float* loss_out, void* stream) {

@@ -26,15 +26,19 @@ namespace crl {
 //     over the lanes).
 // The warp's own copies precede its stamps (__syncwarp orders them).  Block 0
 // records the new fill.
-__global__ void __launch_bounds__(128) insert_kernel(BufferDev bd, const float* __restrict__ obs,
-                                                    const float* __restrict__ act, const uint8_t* __restrict__ done,
-                                                    int n, int i0, long long total_before) {
-  pdl_enter();
+// lb: block index within this buffer's share of the grid (4 environments per block).
+__device__ __forceinline__ void insert_body(const InsertArgs& ia, int lb) {
+  const BufferDev& bd = ia.bd;
+  const float* __restrict__ obs = ia.obs;
+  const float* __restrict__ act = ia.act;
+  const uint8_t* __restrict__ done = ia.done;
+  const int n = ia.n, i0 = ia.i0;
+  const long long total_before = ia.total_before;
   const int lane = threadIdx.x % kWarp;
-  const int e = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const int e = lb * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   const long long total_after = total_before + n;
   const long long size_after = total_after < bd.T ? total_after : bd.T;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lb == 0 && threadIdx.x == 0) {
     bd.state[0] = (int32_t)size_after;
     bd.state[1] = (int32_t)total_after;
   }
@@ -68,6 +72,32 @@ __global__ void __launch_bounds__(128) insert_kernel(BufferDev bd, const float* 
   if (lane == 0) bd.ep_start[e] = (int32_t)start;
 }
 
+__global__ void __launch_bounds__(128) insert_kernel(const __grid_constant__ InsertArgs ia) {
+  pdl_enter();
+  insert_body(ia, blockIdx.x);
+}
+
+// Several buffers (agents) in one launch; arguments by value (they change every step).
+__global__ void __launch_bounds__(128) insert_multi_kernel(const __grid_constant__ InsertMulti m) {
+  pdl_enter();
+  int lb, nb;
+  const int s = segment_of(m.begin, m.n, blockIdx.x, lb, nb);
+  insert_body(m.a[s], lb);
+}
+
+int insert_blocks(const BufferDev& bd) { return ceil_div(bd.E, 4); }
+
+void launch_buffer_insert_multi(const InsertMulti& m, cudaStream_t st) {
+  double bytes = 0.0;
+  for (int s = 0; s < m.n; ++s) {
+    const InsertArgs& a = m.a[s];
+    bytes += (double)(a.n - a.i0) * a.bd.E * ((a.bd.D + a.bd.A) * 4.0 + (a.bd.D + a.bd.A + 1) * 4.0) +
+             (double)a.n * a.bd.E;
+  }
+  TraceLaunch tr(CRL_TRACE_INSERT, st, bytes);
+  launch_k(insert_multi_kernel, dim3(m.begin[m.n]), dim3(128), 0, st, m);
+}
+
 void launch_buffer_insert(const BufferDev& bd, const float* obs, const float* act, const uint8_t* done,
                           int n, int64_t total_before, cudaStream_t st) {
   const int i0 = n > bd.T ? n - bd.T : 0;
@@ -75,7 +105,8 @@ void launch_buffer_insert(const BufferDev& bd, const float* obs, const float* ac
   // algorithmic bytes: read obs, act and the done flags, write the rows (obs, act, episode end)
   TraceLaunch tr(CRL_TRACE_INSERT, st,
                  (double)rows * ((bd.D + bd.A) * 4.0 + (bd.D + bd.A + 1) * 4.0) + (double)n * bd.E);
-  launch_k(insert_kernel, dim3(ceil_div(bd.E, 4)), dim3(128), 0, st, bd, obs, act, done, n, i0, total_before);
+  const InsertArgs ia{bd, obs, act, done, n, i0, total_before};
+  launch_k(insert_kernel, dim3(insert_blocks(bd)), dim3(128), 0, st, ia);
 }
 
 // ---------------------------------------------------------------------------
@@ -144,13 +175,13 @@ constexpr int kRelabelUnroll = CRL_RELABEL_UNROLL;  // samples whose loads are i
 // state-action row with 16-byte loads (ring rows start on 16-byte boundaries)
 // and gathers its goal dims.  Small batches take spw = 1 (a warp per sample,
 // the most parallel copy); large ones up to 32 (index chains 32 wide).
-__global__ void __launch_bounds__(256) relabel_kernel(BufferDev bd, RelabelArgs ra) {
-  pdl_enter();
+// lb: block index within this sample batch's share of the grid (8 warps per block).
+__device__ __forceinline__ void relabel_body(const BufferDev& bd, const RelabelArgs& ra, int lb) {
   const int lane = threadIdx.x % kWarp;
   const int spw = ra.spw;
-  const int b0 = (blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp) * spw;
+  const int b0 = (lb * (blockDim.x / kWarp) + threadIdx.x / kWarp) * spw;
   const unsigned long long step = (ra.step == CRL_STEP_AUTO) ? *ra.step_dev : ra.step;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && ra.last_step_dev != nullptr) *ra.last_step_dev = step;
+  if (lb == 0 && threadIdx.x == 0 && ra.last_step_dev != nullptr) *ra.last_step_dev = step;
   if (b0 >= ra.B) return;
   const int size = bd.state[0];
   const long long total = bd.state[1];
@@ -273,14 +304,38 @@ __global__ void __launch_bounds__(256) relabel_kernel(BufferDev bd, RelabelArgs 
   }
 }
 
+__global__ void __launch_bounds__(256) relabel_kernel(const __grid_constant__ BufferDev bd,
+                                                     const __grid_constant__ RelabelArgs ra) {
+  pdl_enter();
+  relabel_body(bd, ra, blockIdx.x);
+}
+
+// Several agents' batches in one launch (per-agent arguments in an immutable device table).
+__global__ void __launch_bounds__(256) relabel_multi_kernel(const RelabelTask* __restrict__ tasks,
+                                                           const int* __restrict__ begin, int n) {
+  pdl_enter();
+  int lb, nb;
+  const int s = segment_of(begin, n, blockIdx.x, lb, nb);
+  relabel_body(tasks[s].bd, tasks[s].ra, lb);
+}
+
+int relabel_spw(int B) { return (int)std::min<long long>(32, std::max<long long>(1, (long long)B / (152 * 48))); }
+int relabel_blocks(const RelabelArgs& ra) { return ceil_div(ra.B, 8 * ra.spw); }
+
+void launch_relabel_multi(const RelabelTask* tasks, const int* begin, int n, int blocks, double bytes,
+                          cudaStream_t st) {
+  TraceLaunch tr(CRL_TRACE_RELABEL, st, bytes);
+  launch_k(relabel_multi_kernel, dim3(blocks), dim3(256), 0, st, tasks, begin, n);
+}
+
 void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st) {
   // algorithmic bytes per sample: read obs + act + episode end + goal dims, write s, a, g (+ idx)
   const double per = (bd.D + bd.A + 1 + ra.G) * 4.0 + (bd.D + bd.A + ra.G) * 4.0 + (ra.idx ? 12.0 : 0.0);
   TraceLaunch tr(CRL_TRACE_RELABEL, st, per * ra.B);
   // samples per warp: as many warps as fill the GPU (152 SMs x 48 resident warps), at most 32
   RelabelArgs r = ra;
-  r.spw = (int)std::min<long long>(32, std::max<long long>(1, (long long)ra.B / (152 * 48)));
-  launch_k(relabel_kernel, dim3(ceil_div(ra.B, 8 * r.spw)), dim3(256), 0, st, bd, r);
+  r.spw = relabel_spw(ra.B);
+  launch_k(relabel_kernel, dim3(relabel_blocks(r)), dim3(256), 0, st, bd, r);
 }
 
 __global__ void bump_u64_kernel(unsigned long long* c) {

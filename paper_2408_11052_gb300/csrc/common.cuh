@@ -66,6 +66,22 @@ __device__ __forceinline__ T softplus(T x) {
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// ---- multi-agent launches -------------------------------------------------------
+// A launch over several independent problems (agents, networks) gives problem s
+// the blocks [begin[s], begin[s + 1]) of a 1-D grid (begin: n + 1 entries).
+// Returns s; lb = block index within the problem, nb = its block count.
+__device__ __forceinline__ int segment_of(const int* __restrict__ begin, int n, int b, int& lb, int& nb) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  lb = b - begin[lo];
+  nb = begin[lo + 1] - begin[lo];
+  return lo;
+}
+
 // ---- programmatic dependent launch ---------------------------------------------
 // Every libcrl kernel is launched with programmatic stream serialisation
 // allowed (launch_k), so it may start while its predecessor on the stream is

@@ -25,6 +25,7 @@
 //           exchanged.  Both write their result as BF16 dy [B][R] and dy^T
 //           [R][B], the layout the encoder backward consumes.
 #include <cuda_bf16.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -75,17 +76,15 @@ struct PrepSide {
   bf16* XT;
   float* aux;
 };
-// blockIdx.y = 0: phi -> X, 1: psi -> Y.
-__global__ void __launch_bounds__(1024) prep_kernel(int B, int R, int energy, int ldt, PrepSide s0, PrepSide s1) {
-  pdl_enter();
-  const PrepSide p = blockIdx.y ? s1 : s0;
+// lb: block of 32 rows.
+__device__ __forceinline__ void prep_body(int B, int R, int energy, int ldt, const PrepSide& p, int lb) {
   const float* __restrict__ y = p.y;
   bf16* __restrict__ X = p.X;
   bf16* __restrict__ XT = p.XT;
   float* __restrict__ aux = p.aux;
   __shared__ float tile[32][33];
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int row = blockIdx.x * 32 + w;
+  const int row = lb * 32 + w;
   float scale = 1.f;
   if (row < B) {
     const float* yr = y + (size_t)row * R;
@@ -112,10 +111,16 @@ __global__ void __launch_bounds__(1024) prep_kernel(int B, int R, int energy, in
     }
     tile[w][lane] = v;
     __syncthreads();
-    const int cc = c0 + w, rr = blockIdx.x * 32 + lane;
+    const int cc = c0 + w, rr = lb * 32 + lane;
     if (cc < R && rr < B) XT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
     __syncthreads();
   }
+}
+
+// blockIdx.y = 0: phi -> X, 1: psi -> Y.
+__global__ void __launch_bounds__(1024) prep_kernel(int B, int R, int energy, int ldt, PrepSide s0, PrepSide s1) {
+  pdl_enter();
+  prep_body(B, R, energy, ldt, blockIdx.y ? s1 : s0, blockIdx.x);
 }
 
 // ---- forward ----------------------------------------------------------------------
@@ -199,8 +204,10 @@ __device__ void finalize_block(const FwdArgs& a, int nI, int nJ) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                          const __grid_constant__ CUtensorMap tmY, FwdArgs a) {
+// One 128 x 128 tile (row tile I, column tile J) of an n x n tile grid.
+// global_maps: the tensor maps live in a device table (acquire them first).
+__device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const FwdArgs& a, int I,
+                                         int J, int n, bool global_maps) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   const int nk = a.R / 64;
@@ -216,10 +223,14 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant_
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int lg = warp % 4, q = warp / 4;
-  const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
+  const int i0 = I * kTile, j0 = J * kTile;
   if (tid == 0) {
-    tc::prefetch_tmap(&tmX);
-    tc::prefetch_tmap(&tmY);
+    if (global_maps) {
+      tc::tmap_acquire(tmX);
+      tc::tmap_acquire(tmY);
+    }
+    tc::prefetch_tmap(tmX);
+    tc::prefetch_tmap(tmY);
     tc::mbar_init(load_bar, 1);
     tc::mbar_init(mma_bar, 1);
     tc::fence_mbar_init();
@@ -239,8 +250,8 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant_
     tc::mbar_arrive_expect_tx(load_bar, (uint32_t)(2 * nk * 16384));
     for (int kb = 0; kb < nk; ++kb)
       for (int r = 0; r < 2; ++r) {
-        tc::tma_load_2d(Xs + kb * 16384 + r * 8192, &tmX, load_bar, kb * 64, i0 + 64 * r);
-        tc::tma_load_2d(Ys + kb * 16384 + r * 8192, &tmY, load_bar, kb * 64, j0 + 64 * r);
+        tc::tma_load_2d(Xs + kb * 16384 + r * 8192, tmX, load_bar, kb * 64, i0 + 64 * r);
+        tc::tma_load_2d(Ys + kb * 16384 + r * 8192, tmY, load_bar, kb * 64, j0 + 64 * r);
       }
   } else if (tid == 32) {
     if (tc::mbar_wait(load_bar, 0)) {
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant_
       float m = part[tid], s = part[4 * kTile + tid];
       for (int g = 1; g < 4; ++g) lse_merge(m, s, part[g * kTile + tid], part[(4 + g) * kTile + tid]);
       if (i < a.B) {
-        float* rp = a.rowpart + ((size_t)blockIdx.x * a.B + i) * 2;
+        float* rp = a.rowpart + ((size_t)J * a.B + i) * 2;
         rp[0] = m;
         rp[1] = s;
       }
@@ -323,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant_
     float m = part[tid], s = part[4 * kTile + tid];
     for (int g = 1; g < 4; ++g) lse_merge(m, s, part[g * kTile + tid], part[(4 + g) * kTile + tid]);
     if (j < a.B) {
-      float* cp = a.colpart + ((size_t)blockIdx.y * a.B + j) * 2;
+      float* cp = a.colpart + ((size_t)I * a.B + j) * 2;
       cp[0] = m;
       cp[1] = s;
     }
@@ -335,13 +346,19 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant_
   __shared__ int s_last;
   __threadfence();
   __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y - 1) ? 1 : 0;
+  if (tid == 0) s_last = (atomicAdd(a.ticket, 1u) == (unsigned)(n * n) - 1u) ? 1 : 0;
   __syncthreads();
   if (s_last) {
     __threadfence();
-    finalize_block(a, gridDim.y, gridDim.x);
+    finalize_block(a, n, n);
     if (tid == 0) *a.ticket = 0u;
   }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmY,
+                                                          const __grid_constant__ FwdArgs a) {
+  fwd_body(&tmX, &tmY, a, blockIdx.y, blockIdx.x, gridDim.x, false);
 }
 
 // ---- backward ---------------------------------------------------------------------
@@ -372,16 +389,15 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int chunk) {
 // rows 32 (w % 4) .., columns 32 (w / 4) ..), and the MMA adds H other into
 // the TMEM accumulator.
 // CTAs [0, nrow) run the row pass (own = phi), CTAs [nrow, 2 nrow) the column pass (own = psi).
-__global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                          const __grid_constant__ CUtensorMap tmY,
-                                                          const __grid_constant__ CUtensorMap tmXT,
-                                                          const __grid_constant__ CUtensorMap tmYT, BwdArgs row,
-                                                          BwdArgs col, int nrow) {
-  const bool colpass = (int)blockIdx.x >= nrow;
+// lb in [0, 2 nrow): the row pass for lb < nrow, else the column pass.
+__device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const CUtensorMap* tmXT,
+                                         const CUtensorMap* tmYT, const BwdArgs& row, const BwdArgs& col, int nrow,
+                                         int lb, bool global_maps) {
+  const bool colpass = lb >= nrow;
   const BwdArgs a = colpass ? col : row;
-  const CUtensorMap* tmOwn = colpass ? &tmY : &tmX;
-  const CUtensorMap* tmOther = colpass ? &tmX : &tmY;
-  const CUtensorMap* tmOtherT = colpass ? &tmXT : &tmYT;
+  const CUtensorMap* tmOwn = colpass ? tmY : tmX;
+  const CUtensorMap* tmOther = colpass ? tmX : tmY;
+  const CUtensorMap* tmOtherT = colpass ? tmXT : tmYT;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   const int nk = a.R / 64;
@@ -404,9 +420,14 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant_
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int lg = warp % 4, q = warp / 4;
   const int r = lg * 32 + lane;  // row of this thread within the tile
-  const int u0 = ((int)blockIdx.x - (colpass ? nrow : 0)) * kTile;
+  const int u0 = (lb - (colpass ? nrow : 0)) * kTile;
   const int nV = (a.B + kTile - 1) / kTile;
   if (tid == 0) {
+    if (global_maps) {
+      tc::tmap_acquire(tmOwn);
+      tc::tmap_acquire(tmOther);
+      tc::tmap_acquire(tmOtherT);
+    }
     tc::prefetch_tmap(tmOwn);
     tc::prefetch_tmap(tmOther);
     tc::prefetch_tmap(tmOtherT);
@@ -605,6 +626,50 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant_
   if (warp == 0) tc::tmem_dealloc(tmem, tcols);
 }
 
+__global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmY,
+                                                          const __grid_constant__ CUtensorMap tmXT,
+                                                          const __grid_constant__ CUtensorMap tmYT,
+                                                          const __grid_constant__ BwdArgs row,
+                                                          const __grid_constant__ BwdArgs col, int nrow) {
+  bwd_body(&tmX, &tmY, &tmXT, &tmYT, row, col, nrow, blockIdx.x, false);
+}
+
+// ---- several agents in one launch ------------------------------------------------
+// Per-agent arguments and tensor maps in an immutable device table; agent s
+// owns the blocks [begin[s], begin[s+1]) of each launch: 2 ceil(B / 32) prep
+// blocks (phi then psi), n^2 forward tiles, 2 n backward CTAs.
+struct alignas(64) EnergyTask {
+  CUtensorMap tmX, tmY, tmXT, tmYT;
+  FwdArgs f;
+  BwdArgs row, col;
+  PrepSide s0, s1;
+  int B, R, energy, ldt, n;
+};
+
+__global__ void __launch_bounds__(1024) prep_multi_kernel(const EnergyTask* __restrict__ tasks,
+                                                         const int* __restrict__ begin, int n) {
+  pdl_enter();
+  int lb, nb;
+  const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];
+  const int half = nb / 2;
+  prep_body(t.B, t.R, t.energy, t.ldt, lb < half ? t.s0 : t.s1, lb < half ? lb : lb - half);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) fwd_multi_kernel(const EnergyTask* __restrict__ tasks,
+                                                               const int* __restrict__ begin, int n) {
+  int lb, nb;
+  const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];
+  fwd_body(&t.tmX, &t.tmY, t.f, lb / t.n, lb % t.n, t.n, true);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) bwd_multi_kernel(const EnergyTask* __restrict__ tasks,
+                                                               const int* __restrict__ begin, int n) {
+  int lb, nb;
+  const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];
+  bwd_body(&t.tmX, &t.tmY, &t.tmXT, &t.tmYT, t.row, t.col, t.n, lb, true);
+}
+
 size_t fwd_smem(int R) {
   const size_t opnd = (size_t)2 * (R / 64) * 16384, ftile = (size_t)kTile * 129 * 4;
   return (opnd > ftile ? opnd : ftile) + 2 * 4 * kTile * 4 + 1024 + 64;
@@ -705,6 +770,78 @@ void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi
   b.d_outT = dpsiT;
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 8.0 * B * B * e.R);
   launch_k(bwd_kernel, dim3(2 * n), dim3(kThreads), sm, st, e.tmX, e.tmY, e.tmXT, e.tmYT, a, b, n);
+}
+
+const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& agents, int stage, cudaStream_t st) {
+  const int na = (int)agents.size();
+  if (na == 0) return nullptr;
+  std::vector<EnergyTask> tasks(na);
+  std::vector<int> begin(na + 1, 0);
+  int Rmax = 64;
+  double work = 0.0;
+  for (int i = 0; i < na; ++i) {
+    const EnergyAgent& g = agents[i];
+    EnergyTask& t = tasks[i];
+    memset(&t, 0, sizeof(t));
+    const EnergyTc& e = *g.e;
+    t.tmX = e.tmX;
+    t.tmY = e.tmY;
+    t.tmXT = e.tmXT;
+    t.tmYT = e.tmYT;
+    t.B = g.B;
+    t.R = e.R;
+    t.energy = g.ls.energy;
+    t.ldt = e.ldt;
+    t.n = (g.B + kTile - 1) / kTile;
+    t.s0 = PrepSide{g.phi, e.X, e.XT, e.auxX};
+    t.s1 = PrepSide{g.psi, e.Y, e.YT, e.auxY};
+    unsigned* ticket = static_cast<unsigned*>(g.ws);
+    float* rowpart = reinterpret_cast<float*>(static_cast<char*>(g.ws) + 256);
+    float* colpart = rowpart + (size_t)2 * t.n * g.B;
+    float* diag = colpart + (size_t)2 * t.n * g.B;
+    t.f = FwdArgs{g.B,     e.R,     g.ls.energy, (float)(1.0 / g.ls.tau), e.auxX, e.auxY, rowpart, colpart, diag,
+                  g.status, loss_weights(g.ls), (float)g.ls.beta, g.r, g.c, g.loss4, g.t_bump, ticket};
+    t.row = BwdArgs{g.B,    e.R,     g.ls.energy, 0,       (float)(1.0 / g.ls.tau), (float)g.ls.beta,
+                    (float)(1.0 / g.B), loss_weights(g.ls), e.auxX, e.auxY, g.r, g.c, g.phi, g.dphi, g.dphiT,
+                    g.ldt,  g.status};
+    t.col = t.row;
+    t.col.transposed = 1;
+    t.col.aux_own = e.auxY;
+    t.col.aux_other = e.auxX;
+    t.col.lse_own = g.c;
+    t.col.lse_other = g.r;
+    t.col.own_f32 = g.psi;
+    t.col.d_out = g.dpsi;
+    t.col.d_outT = g.dpsiT;
+    const int nb = stage == 0 ? 2 * ceil_div(g.B, 32) : (stage == 1 ? t.n * t.n : 2 * t.n);
+    begin[i + 1] = begin[i] + nb;
+    Rmax = std::max(Rmax, e.R);
+    work += (stage == 1 ? 2.0 : 8.0) * g.B * g.B * e.R * (stage == 0 ? 0.0 : 1.0);
+  }
+  const char* err = nullptr;
+  const EnergyTask* dt = cache.get(tasks, st, &err);
+  if (!dt) return err;
+  const int* db = cache.get(begin, st, &err);
+  if (!db) return err;
+  TraceLaunch tr(CRL_TRACE_ENERGY, st, work);
+  if (stage == 0) {
+    launch_k(prep_multi_kernel, dim3(begin[na]), dim3(1024), 0, st, dt, db, na);
+  } else if (stage == 1) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(fwd_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
+      attr = true;
+    }
+    launch_k(fwd_multi_kernel, dim3(begin[na]), dim3(kThreads), fwd_smem(Rmax), st, dt, db, na);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(bwd_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(256));
+      attr = true;
+    }
+    launch_k(bwd_multi_kernel, dim3(begin[na]), dim3(kThreads), bwd_smem(Rmax), st, dt, db, na);
+  }
+  return nullptr;
 }
 
 }  // namespace crl

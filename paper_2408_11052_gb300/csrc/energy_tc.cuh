@@ -4,7 +4,10 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "internal.h"
+#include "tables.h"
 
 namespace crl {
 
@@ -29,5 +32,28 @@ void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, flo
 void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
                         const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dphiT,
                         __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, unsigned* status, cudaStream_t st);
+
+// One agent of a multi-agent launch of the fused energy stage (its maps built
+// by energy_tc_maps for batch B).
+struct EnergyAgent {
+  EnergyTc* e;
+  LossSpec ls;
+  int B;
+  const float* phi;   // [B][R] FP32 encoder outputs
+  const float* psi;
+  float* loss4;
+  float* r;
+  float* c;
+  void* ws;           // energy_tc_ws_bytes(B), zeroed at creation
+  int* t_bump;
+  __nv_bfloat16* dphi;
+  __nv_bfloat16* dphiT;
+  __nv_bfloat16* dpsi;
+  __nv_bfloat16* dpsiT;
+  int ldt;
+  unsigned* status;
+};
+// stage 0: prepare, 1: forward (+ loss), 2: backward -- one launch over all agents.
+const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& agents, int stage, cudaStream_t st);
 
 }  // namespace crl

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/crl.h"
 
@@ -53,6 +54,34 @@ struct RelabelArgs {
 void launch_buffer_insert(const BufferDev& bd, const float* obs, const float* act, const uint8_t* done,
                           int n, int64_t total_before, cudaStream_t st);
 void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st);
+
+// ---------------------------------------------------------------- multi-agent launches
+constexpr int kMaxAgents = 64;
+struct InsertArgs {
+  BufferDev bd;
+  const float* obs;
+  const float* act;
+  const uint8_t* done;
+  int n, i0;                        // slices given, first slice written (n - T when n > T)
+  long long total_before;
+};
+// Insert into several buffers in one launch: buffer s owns blocks [begin[s], begin[s+1]).
+struct InsertMulti {
+  InsertArgs a[kMaxAgents];
+  int begin[kMaxAgents + 1];
+  int n;
+};
+int insert_blocks(const BufferDev& bd);
+void launch_buffer_insert_multi(const InsertMulti& m, cudaStream_t st);
+struct RelabelTask {
+  BufferDev bd;
+  RelabelArgs ra;                   // ra.spw set (relabel_spw)
+};
+int relabel_spw(int B);
+int relabel_blocks(const RelabelArgs& ra);
+// tasks / begin: device tables (n tasks, n + 1 block offsets).
+void launch_relabel_multi(const RelabelTask* tasks, const int* begin, int n, int blocks, double bytes,
+                          cudaStream_t st);
 void build_discount_table(float gamma, int n, unsigned long long* out);  // host
 
 // ---------------------------------------------------------------- MLPs
@@ -124,6 +153,32 @@ struct ActorLossArgs {
   const unsigned long long* last_step;
 };
 size_t actor_loss_ws_bytes(int B, size_t elem);
+template <typename T>
+struct HeadFwdArgs {
+  int B, A;
+  const T* out;                     // [B][2A] policy output (mu, log-std)
+  const float* eps;                 // [B][A] or null (Philox noise at *step_dev)
+  const unsigned long long* step_dev;
+  unsigned long long seed, agent;
+  T* a_new;
+  T* logpi;
+  T* eps_used;
+  __nv_bfloat16* x0;                // optional split BF16 copy of a' (see actor_head_forward)
+  int x0_ld, x0_col;
+};
+template <typename T>
+struct HeadBwdArgs {
+  int B, A;
+  double alpha;
+  const T* out;
+  const T* eps_used;
+  const T* da;
+  T* dout;
+  __nv_bfloat16* dz;                // optional BF16 output gradient (see actor_head_backward)
+  int ldz;
+  __nv_bfloat16* dzT;
+  int ldt;
+};
 // Diagonal energy, dphi (T, or BF16 into dz [B][ldz] when dz != null) and the
 // actor loss in one launch.  ws: actor_loss_ws_bytes(B, sizeof(T)); ticket: a
 // zero-initialised device word.  t_bump: ++*t_bump; step_bump: *step_bump =
@@ -138,6 +193,14 @@ template <typename T>
 void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used, const T* da, int B,
                          T* dout, cudaStream_t st, __nv_bfloat16* dz = nullptr, int ldz = 0,
                          __nv_bfloat16* dzT = nullptr, int ldt = 0);
+
+class BlobCache;
+// Several agents in one launch each (float tasks of the BF16 path; tables cached in `cache`).
+const char* actor_head_forward_multi(BlobCache& cache, const std::vector<HeadFwdArgs<float>>& tasks,
+                                     cudaStream_t st);
+const char* actor_loss_multi(BlobCache& cache, const std::vector<ActorLossArgs<float>>& tasks, cudaStream_t st);
+const char* actor_head_backward_multi(BlobCache& cache, const std::vector<HeadBwdArgs<float>>& tasks,
+                                      cudaStream_t st);
 
 // ---------------------------------------------------------------- Adam
 template <typename T>

@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "mlp_bf16.cuh"
@@ -133,6 +134,7 @@ void pack(int rows, const float* s0, int ld0, int n0, const float* s1, int ld1, 
 
 // ---- LayerNorm (grouped over the networks of a pass: blockIdx.y = network) ----------
 struct LnFwdNet {
+  int M, ldt;
   float* z;
   float* rstd;
   const float* g;
@@ -147,9 +149,10 @@ struct LnFwdGroup {
 // LayerNorm forward over rows of z [M][H] (FP32, replaced by zhat), rstd [M],
 // h = ReLU(zhat * g + beta) written as BF16 [M][H] and, through a shared tile,
 // transposed [H][ldt].  Block = 32 rows (one warp each).
-__global__ void __launch_bounds__(1024) ln_fwd_kernel(int M, int H, int ldt, LnFwdGroup grp) {
+__global__ void __launch_bounds__(1024) ln_fwd_kernel(int H, const __grid_constant__ LnFwdGroup grp) {
   pdl_enter();
   const LnFwdNet& a = grp.n[blockIdx.y];
+  const int M = a.M, ldt = a.ldt;
   float* __restrict__ z = a.z;
   __shared__ float tile[32][33];
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
@@ -188,6 +191,7 @@ __global__ void __launch_bounds__(1024) ln_fwd_kernel(int M, int H, int ldt, LnF
 }
 
 struct LnBwdNet {
+  int M, ldt;
   const float* du;
   const float* zhat;
   const float* rstd;
@@ -203,9 +207,10 @@ struct LnBwdGroup {
 
 // LayerNorm backward: du (ReLU-masked, FP32) -> dz = rstd (g du - mean(g du) - zhat mean(g du zhat)),
 // written BF16 [M][H] and transposed.  Block = 32 rows.
-__global__ void __launch_bounds__(1024) ln_bwd_kernel(int M, int H, int ldt, LnBwdGroup grp) {
+__global__ void __launch_bounds__(1024) ln_bwd_kernel(int H, const __grid_constant__ LnBwdGroup grp) {
   pdl_enter();
   const LnBwdNet& a = grp.n[blockIdx.y];
+  const int M = a.M, ldt = a.ldt;
   const float* __restrict__ du = a.du;
   const float* __restrict__ zhat = a.zhat;
   const float* __restrict__ g = a.g;
@@ -241,9 +246,10 @@ __global__ void __launch_bounds__(1024) ln_bwd_kernel(int M, int H, int ldt, LnB
 }
 
 // dgain[n] = sum_m du * zhat, dbeta[n] = sum_m du.  Block = 32 columns x 8 row groups.
-__global__ void __launch_bounds__(256) ln_param_grad_kernel(int M, int H, LnBwdGroup grp) {
+__global__ void __launch_bounds__(256) ln_param_grad_kernel(int H, const __grid_constant__ LnBwdGroup grp) {
   pdl_enter();
   const LnBwdNet& p = grp.n[blockIdx.y];
+  const int M = p.M;
   const float* __restrict__ du = p.du;
   const float* __restrict__ zhat = p.zhat;
   __shared__ float sa[8][33], sb[8][33];
@@ -500,18 +506,22 @@ void bf_net_load_dy(BfNet& n, const float* dy, int M, cudaStream_t st) {
   pack(M, dy, out, out, nullptr, 0, 0, n.dz[n.layers], pad8(out), n.dzT[n.layers], n.Mmax, st);
 }
 
-const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, int M, unsigned* status, cudaStream_t st) {
-  if (M <= 0 || count <= 0) return nullptr;
-  if (count > kMaxGroupNets) return "too many networks in one grouped pass";
+const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st) {
+  if (count <= 0) return nullptr;
   const BfNet& n0 = *nets[0].net;
   const int H = n0.s.hidden, layers = n0.layers;
   const bool ln = n0.s.layernorm != 0;
+  for (int k = 1; k < count; ++k)
+    if (nets[k].net->layers != layers || nets[k].net->s.hidden != H || (nets[k].net->s.layernorm != 0) != ln)
+      return "the networks of a grouped pass differ in depth, hidden width or LayerNorm";
   std::vector<tc::GemmProblem> probs;
   for (int l = 0; l <= layers; ++l) {
     probs.clear();
     double flops = 0.0;
     for (int k = 0; k < count; ++k) {
       BfNet& n = *nets[k].net;
+      const int M = nets[k].M;
+      if (M <= 0) continue;
       const BfLayer& L = n.L[l];
       const float* params = nets[k].params;
       const CUtensorMap& A = (l == 0) ? n.tm_x0A : n.tm_hA[l - 1];
@@ -536,27 +546,37 @@ const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, int M, uns
       flops += 2.0 * M * L.out * L.in;
     }
     if (const char* err = launch_group(gg, probs, flops, status, st)) return err;
-    if (l < layers && ln) {
+    for (int k0 = 0; l < layers && ln && k0 < count; k0 += kMaxGroupNets) {
+      const int kc = std::min(kMaxGroupNets, count - k0);
       LnFwdGroup grp;
       memset(&grp, 0, sizeof(grp));
-      for (int k = 0; k < count; ++k) {
-        BfNet& n = *nets[k].net;
+      int Mx = 0;
+      double bytes = 0.0;
+      for (int k = 0; k < kc; ++k) {
+        BfNet& n = *nets[k0 + k].net;
         const BfLayer& L = n.L[l];
-        grp.n[k] = LnFwdNet{n.z[l], n.rstd[l], nets[k].params + L.og, nets[k].params + L.obeta, n.h[l], n.hT[l]};
+        const float* pr = nets[k0 + k].params;
+        const int M = std::max(nets[k0 + k].M, 0);
+        grp.n[k] = LnFwdNet{M, n.Mmax, n.z[l], n.rstd[l], pr + L.og, pr + L.obeta, n.h[l], n.hT[l]};
+        Mx = std::max(Mx, M);
+        bytes += (double)M * H * 12.0;
       }
-      TraceLaunch tr(CRL_TRACE_AUX, st, (double)count * M * H * 12.0);
-      launch_k(ln_fwd_kernel, dim3(ceil_div(M, 32), count), dim3(1024), 0, st, M, H, n0.Mmax, grp);
+      if (Mx == 0) continue;
+      TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
+      launch_k(ln_fwd_kernel, dim3(ceil_div(Mx, 32), kc), dim3(1024), 0, st, H, grp);
     }
   }
   return nullptr;
 }
 
-const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, int M, unsigned* status, cudaStream_t st) {
-  if (M <= 0 || count <= 0) return nullptr;
-  if (count > kMaxGroupNets) return "too many networks in one grouped pass";
+const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st) {
+  if (count <= 0) return nullptr;
   const BfNet& n0 = *nets[0].net;
   const int H = n0.s.hidden, layers = n0.layers;
   const bool ln = n0.s.layernorm != 0;
+  for (int k = 1; k < count; ++k)
+    if (nets[k].net->layers != layers || nets[k].net->s.hidden != H || (nets[k].net->s.layernorm != 0) != ln)
+      return "the networks of a grouped pass differ in depth, hidden width or LayerNorm";
   std::vector<tc::GemmProblem> probs;
   // input-gradient chain: dz[l] -> dz[l - 1]
   for (int l = layers; l >= 1; --l) {
@@ -564,6 +584,8 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, int M, un
     double flops = 0.0;
     for (int k = 0; k < count; ++k) {
       BfNet& n = *nets[k].net;
+      const int M = nets[k].M;
+      if (M <= 0) continue;
       const BfLayer& L = n.L[l];
       tc::EpiDesc e = epi_of(ln ? tc::kEpiBwdDXLN : tc::kEpiBwdDX);
       e.mask = n.h[l - 1];
@@ -580,27 +602,36 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, int M, un
       flops += 2.0 * M * H * L.out;
     }
     if (const char* err = launch_group(gg, probs, flops, status, st)) return err;
-    if (ln) {
+    for (int k0 = 0; ln && k0 < count; k0 += kMaxGroupNets) {
+      const int kc = std::min(kMaxGroupNets, count - k0);
       LnBwdGroup grp, pg;
       memset(&grp, 0, sizeof(grp));
       memset(&pg, 0, sizeof(pg));
-      int np = 0;
-      for (int k = 0; k < count; ++k) {
-        BfNet& n = *nets[k].net;
+      int np = 0, Mx = 0;
+      double bytes = 0.0, pbytes = 0.0;
+      for (int k = 0; k < kc; ++k) {
+        const BfPass& bp = nets[k0 + k];
+        BfNet& n = *bp.net;
         const BfLayer& P = n.L[l - 1];
-        const LnBwdNet b{n.du, n.z[l - 1], n.rstd[l - 1], nets[k].params + P.og, n.dz[l - 1], n.dzT[l - 1],
-                         nets[k].grads ? nets[k].grads + P.og : nullptr,
-                         nets[k].grads ? nets[k].grads + P.obeta : nullptr};
+        const int M = std::max(bp.M, 0);
+        const LnBwdNet b{M, n.Mmax, n.du, n.z[l - 1], n.rstd[l - 1], bp.params + P.og, n.dz[l - 1], n.dzT[l - 1],
+                         bp.grads ? bp.grads + P.og : nullptr, bp.grads ? bp.grads + P.obeta : nullptr};
         grp.n[k] = b;
-        if (nets[k].grads) pg.n[np++] = b;
+        Mx = std::max(Mx, M);
+        bytes += (double)M * H * 16.0;
+        if (bp.grads) {
+          pg.n[np++] = b;
+          pbytes += (double)M * H * 8.0;
+        }
       }
+      if (Mx == 0) continue;
       // the parameter gradients read du before the next layer's launch overwrites it
       if (np > 0) {
-        TraceLaunch tr(CRL_TRACE_AUX, st, (double)np * M * H * 8.0);
-        launch_k(ln_param_grad_kernel, dim3(ceil_div(H, 32), np), dim3(256), 0, st, M, H, pg);
+        TraceLaunch tr(CRL_TRACE_AUX, st, pbytes);
+        launch_k(ln_param_grad_kernel, dim3(ceil_div(H, 32), np), dim3(256), 0, st, H, pg);
       }
-      TraceLaunch tr(CRL_TRACE_AUX, st, (double)count * M * H * 16.0);
-      launch_k(ln_bwd_kernel, dim3(ceil_div(M, 32), count), dim3(1024), 0, st, M, H, n0.Mmax, grp);
+      TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
+      launch_k(ln_bwd_kernel, dim3(ceil_div(Mx, 32), kc), dim3(1024), 0, st, H, grp);
     }
   }
   // every weight gradient, and the first-layer input gradients, in one launch
@@ -608,6 +639,8 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, int M, un
   double flops = 0.0;
   for (int k = 0; k < count; ++k) {
     BfNet& n = *nets[k].net;
+    const int M = nets[k].M;
+    if (M <= 0) continue;
     if (float* grads = nets[k].grads) {
       for (int l = 0; l <= layers; ++l) {
         const BfLayer& L = n.L[l];
@@ -648,38 +681,30 @@ struct AdamNetDev {
   float* v;
   long long n;
   const int* t;
-  float lr;
+  float lr, b1, b2, eps;
   int nl;
   ShadowLayer L[CRL_MAX_LAYERS + 1];
 };
-struct AdamPair {
-  AdamNetDev a[2];
-  int count;
-  float b1, b2, eps;
-};
 
-__global__ void __launch_bounds__(256) adam_shadow_kernel(AdamPair ap) {
-  pdl_enter();
-  __shared__ float s_corr[2][2];
-  if (threadIdx.x < ap.count) {
-    const AdamNetDev& a = ap.a[threadIdx.x];
+// Adam on one network's FP32 master parameters (grid-stride over its blocks
+// lb of nb) and the refresh of its BF16 shadows.  Bias corrections in double
+// (1 - b^t loses most of its digits in float for small t).
+__device__ __forceinline__ void adam_shadow_body(const AdamNetDev& a, int lb, int nb) {
+  const float b1 = a.b1, b2 = a.b2, eps = a.eps;
+  __shared__ float s_corr[2];
+  if (threadIdx.x == 0) {
     const double t = (double)*a.t;
-    s_corr[threadIdx.x][0] = (float)((double)a.lr / (1.0 - pow((double)ap.b1, t)));
-    s_corr[threadIdx.x][1] = (float)(1.0 / (1.0 - pow((double)ap.b2, t)));
+    s_corr[0] = (float)((double)a.lr / (1.0 - pow((double)b1, t)));
+    s_corr[1] = (float)(1.0 / (1.0 - pow((double)b2, t)));
   }
   __syncthreads();
-  const long long n0 = ap.a[0].n, ntot = n0 + (ap.count > 1 ? ap.a[1].n : 0);
-  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < ntot;
-       gi += (long long)gridDim.x * blockDim.x) {
-    const int w = gi < n0 ? 0 : 1;
-    const AdamNetDev& a = ap.a[w];
-    const long long i = gi - (w ? n0 : 0);
+  for (long long i = (long long)lb * blockDim.x + threadIdx.x; i < a.n; i += (long long)nb * blockDim.x) {
     const float g = a.g[i];
-    const float mi = ap.b1 * a.m[i] + (1.f - ap.b1) * g;
-    const float vi = ap.b2 * a.v[i] + (1.f - ap.b2) * g * g;
+    const float mi = b1 * a.m[i] + (1.f - b1) * g;
+    const float vi = b2 * a.v[i] + (1.f - b2) * g * g;
     a.m[i] = mi;
     a.v[i] = vi;
-    const float p = a.p[i] - s_corr[w][0] * mi / (sqrtf(vi * s_corr[w][1]) + ap.eps);
+    const float p = a.p[i] - s_corr[0] * mi / (sqrtf(vi * s_corr[1]) + eps);
     a.p[i] = p;
     for (int l = 0; l < a.nl; ++l) {
       const ShadowLayer& L = a.L[l];
@@ -700,17 +725,26 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(AdamPair ap) {
   }
 }
 
+// Network s owns blocks [begin[s], begin[s+1]).
+__global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __restrict__ nets,
+                                                          const int* __restrict__ begin, int n) {
+  pdl_enter();
+  int lb, nb;
+  const int s = segment_of(begin, n, blockIdx.x, lb, nb);
+  adam_shadow_body(nets[s], lb, nb);
+}
+
 }  // namespace
 
-void adam_shadow_update(const AdamShadowNet* nets, int count, float b1, float b2, float eps, cudaStream_t st) {
-  AdamPair ap{};
-  ap.count = count;
-  ap.b1 = b1;
-  ap.b2 = b2;
-  ap.eps = eps;
+const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int count, cudaStream_t st) {
+  if (count <= 0) return nullptr;
+  std::vector<AdamNetDev> devs(count);
+  std::vector<int> begin(count + 1, 0);
   long long ntot = 0;
+  for (int k = 0; k < count; ++k) ntot += nets[k].n;
   for (int k = 0; k < count; ++k) {
-    AdamNetDev& a = ap.a[k];
+    AdamNetDev& a = devs[k];
+    memset(&a, 0, sizeof(a));
     const AdamShadowNet& s = nets[k];
     a.p = s.p;
     a.g = s.g;
@@ -719,16 +753,26 @@ void adam_shadow_update(const AdamShadowNet* nets, int count, float b1, float b2
     a.n = s.n;
     a.t = s.t_dev;
     a.lr = s.lr;
+    a.b1 = s.b1;
+    a.b2 = s.b2;
+    a.eps = s.eps;
     a.nl = s.net->layers + 1;
     for (int l = 0; l <= s.net->layers; ++l) {
       const BfLayer& L = s.net->L[l];
       a.L[l] = ShadowLayer{L.oW, L.out, L.in, l == 0 ? 2 : 1, L.kp, L.out_pad, L.W, L.Wt};
     }
-    ntot += s.n;
+    // about 8 blocks per SM in total, shared in proportion to the parameter counts
+    const long long share = (long long)(152 * 8) * s.n / std::max<long long>(ntot, 1) + 1;
+    begin[k + 1] = begin[k] + (int)std::max<long long>(1, std::min<long long>((s.n + 255) / 256, share));
   }
+  const char* err = nullptr;
+  const AdamNetDev* dt = cache.get(devs, st, &err);
+  if (!dt) return err;
+  const int* db = cache.get(begin, st, &err);
+  if (!db) return err;
   TraceLaunch tr(CRL_TRACE_ADAM, st, 28.0 * ntot);
-  const int blocks = (int)std::min<long long>((ntot + 255) / 256, 152 * 8);
-  launch_k(adam_shadow_kernel, dim3(blocks), dim3(256), 0, st, ap);
+  launch_k(adam_shadow_kernel, dim3(begin[count]), dim3(256), 0, st, dt, db, count);
+  return nullptr;
 }
 
 }  // namespace crl

@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tables.h"
 #include "tc_gemm.cuh"
 
 namespace crl {
@@ -133,15 +134,16 @@ struct BfPass {
   const float* params;
   float* grads;   // backward: FP32 gradients in the flat layout, or null (no weight gradients)
   float* dx1;     // backward: FP32 gradient of input columns [in0, in0 + in1) as [M][in1], or null
+  int M;          // batch rows of this network (its tensor maps built for M)
 };
 // Forward of `count` networks (one grouped launch per layer): y [M][out] FP32 in net->y.
-const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, int M, unsigned* status, cudaStream_t st);
+const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st);
 // Backward of `count` networks from their dz[layers] / dzT[layers]: one grouped
 // input-gradient launch per hidden layer, then one launch with every weight
 // gradient and first-layer input gradient.
-const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, int M, unsigned* status, cudaStream_t st);
+const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st);
 
-// Adam on the FP32 master parameters of up to two networks in one launch, also
+// Adam on the FP32 master parameters of several networks in one launch, also
 // refreshing each network's BF16 shadows (W_hi / W_lo and Wt) from the updated
 // weights.  grads / m / v share the flat layout of params.
 struct AdamShadowNet {
@@ -151,9 +153,10 @@ struct AdamShadowNet {
   float* v;
   int64_t n;
   const int* t_dev;   // Adam step counter (already incremented for this step)
-  float lr;
+  float lr, b1, b2, eps;
   BfNet* net;
 };
-void adam_shadow_update(const AdamShadowNet* nets, int count, float b1, float b2, float eps, cudaStream_t st);
+// One launch for `count` networks (any number); its launch tables live in `cache`.
+const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int count, cudaStream_t st);
 
 }  // namespace crl

@@ -73,11 +73,6 @@ struct GemmSmem {
   static_assert(BN % 64 == 0 && BN <= 256, "BN must be 64, 128 or 256");
 };
 
-__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
-  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
-               : "memory");
-}
-
 // 32 BF16 values -> four 16-byte stores (dst 16-byte aligned)
 __device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float (&x)[32]) {
   uint32_t w[16];
