@@ -338,13 +338,144 @@ def relabel_throughput(dev, flush, sizes=(1 << 20, 1 << 22), K=10, W=3):
     return w, res
 
 
+def run_sweep_arm(args, ws, precision, path, grouped, dev, flush, steps, full):
+    """A batched sweep of independent agents: sweep steps/s (and, with full,
+    the traced roofline pass, host-input pass and launch count)."""
+    import torch
+    from paper_2408_11052_gb300 import api
+
+    stream = torch.cuda.current_stream()
+    sw = api.CRLSweep(ws, precision, path, grouped=grouped)
+    n_all = 64                      # insert slices cycled through (the values do not change the work)
+    ins = []
+    for i, w in enumerate(ws):
+        for k, v in workload.init_agent(w).items():
+            sw.agents[i].load_network(k, v)
+        obs, act, done = workload.buffer_contents_device(w, device=dev)
+        sw.agents[i].insert(obs, act, done)
+        del obs, act, done
+        ins.append(workload.buffer_contents_device(w, n=n_all, seed_offset=100, device=dev))
+    host = None
+    if full:
+        host = [tuple(x.cpu().pin_memory() for x in a) for a in ins]
+    loss_dev = torch.zeros(len(ws), 6, dtype=torch.float32, device=dev)
+    loss_host = torch.zeros(len(ws), 6, dtype=torch.float32).pin_memory()
+    cursor = [0]
+
+    def step(src, loss):
+        i = cursor[0] % n_all
+        cursor[0] += 1
+        sw.update_step([a[0][i:i + 1] for a in src], [a[1][i:i + 1] for a in src], [a[2][i:i + 1] for a in src],
+                       loss_out=loss)
+
+    def timed(fn, K, trace=None):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        torch.cuda.synchronize()
+        if trace:
+            sw.agents[0].trace_start(trace, 4096 * K)
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            fn()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        tr = sw.agents[0].trace_stop() if trace else None
+        return sum(s.elapsed_time(e) for s, e in zip(starts, ends)), tr
+
+    for _ in range(args.warmup):
+        step(ins, loss_dev)
+    torch.cuda.synchronize()
+    rc, status = sw.sync_status()
+    assert rc == api.OK, f"sweep warm-up status {status}"
+    out = {}
+    with ClockSampler(dev.index) as clk:
+        out["ms"], _ = timed(lambda: step(ins, loss_dev), steps)
+    out["clocks"] = clk.summary()
+    if full:
+        launches = 0
+        for cls in api.TRACE:
+            sw.agents[0].trace_start(cls, 1 << 16)
+            step(ins, loss_dev)
+            launches += sw.agents[0].trace_stop()[0]
+        out["launches_per_step"] = launches
+        _, out["trace"] = timed(lambda: step(ins, loss_dev), min(steps, 20), trace=args.trace)
+        for _ in range(3):
+            step(host, loss_host)
+        out["e2e_ms"], _ = timed(lambda: step(host, loss_host), steps)
+    rc, status = sw.sync_status()
+    assert rc == api.OK, f"sweep status {status}"
+    sw.close()
+    return out
+
+
+def run_sweep(args, dev, flush):
+    """The batched-sweep workload: 32 independent agents (batch 256..2048, obs
+    29 / 64 / 268, repr 64 / 128, 512 envs x 1000 steps each) per update step;
+    the grouped BF16 sweep, with the same agents stepped one after another in
+    BF16 and in FP32 as comparators."""
+    ws = workload.sweep_agents(32)
+    B_total = sum(w.B for w in ws)
+    main_arm = run_sweep_arm(args, ws, "bf16", "fused", True, dev, flush, args.steps, full=True)
+    comps = []
+    if not args.no_comparator:
+        from paper_2408_11052_gb300 import api
+        prev = api.set_autotune(False)
+        k = min(args.steps, 50)
+        c = run_sweep_arm(args, ws, "bf16", "fused", True, dev, flush, k, full=False)
+        api.set_autotune(prev)
+        comps.append({"precision": "bf16", "path": "fused", "grouped": True, "autotune": False,
+                      "value": len(ws) * k / (c["ms"] / 1e3), "unit": "agent update steps/s",
+                      "ms_per_step": c["ms"] / k, "clocks": c["clocks"],
+                      "note": "grouped, tile widths from the fixed rule instead of the autotuner"})
+        for prec, path in (("bf16", "fused"), ("fp32", "plain")):
+            k = min(args.steps, 20)
+            c = run_sweep_arm(args, ws, prec, path, False, dev, flush, k, full=False)
+            comps.append({"precision": prec, "path": path, "grouped": False,
+                          "value": len(ws) * k / (c["ms"] / 1e3), "unit": "agent update steps/s",
+                          "ms_per_step": c["ms"] / k, "clocks": c["clocks"],
+                          "note": "the same agents' update steps one after another in one CUDA graph"})
+    ms = main_arm["ms"]
+    sweeps_per_s = args.steps / (ms / 1e3)
+    value = len(ws) * sweeps_per_s
+    for c in comps:
+        c["speedup"] = value / c["value"]
+    peaks, peak_src = load_peaks()
+    n_tr, tr_ms, tr_work = main_arm["trace"]
+    achieved = tr_work / (tr_ms / 1e3) / 1e12
+    peak = peaks["bf16_tflops_sustained"]
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "kernel_class": args.trace, "launches": n_tr, "avg_launch_us": 1e3 * tr_ms / max(n_tr, 1),
+            "timing": "eager traced pass (CUDA events around every launch of the class)", "traffic": None,
+            "peak_source": f"{peak_src} bf16_tflops_sustained (kernel timed inside a long step)"}
+    h2d = sum(w.E * (w.D + w.A) * 4 + w.E for w in ws)
+    line = {"metric": METRIC, "value": value, "unit": "agent update steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded random-walk buffers, random-init nets)",
+            "samples_per_s": B_total * sweeps_per_s,
+            "config": {"workload": "sweep_32_agents_E512xT1000_B256-2048_D29-64-268_R64-128_2x256",
+                       "agents": len(ws), "batch_total": B_total, "batches": [w.B for w in ws],
+                       "obs": [w.D for w in ws], "repr": [w.repr for w in ws], "hidden": [256, 256],
+                       "precision": "bf16", "path": "fused", "grouped": True,
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "step": "per agent: insert 1 slice + relabel + critic + Adam + actor + Adam",
+                       "parallelism": "32 independent agents on one GPU"},
+            "e2e": {"value": len(ws) * args.steps / (main_arm["e2e_ms"] / 1e3), "unit": "agent update steps/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24 * len(ws)},
+            "gpu_launches": main_arm["launches_per_step"] * args.steps,
+            "roofline": roof, "clocks": main_arm["clocks"]}
+    if comps:
+        line["comparator"] = comps
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ant", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ant", choices=sorted(WORKLOADS) + ["sweep"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--path", default="fused", choices=["plain", "fused"])
     ap.add_argument("--trace", default="gemm", choices=["gemm", "energy", "relabel", "adam", "aux", "insert"])
@@ -355,7 +486,7 @@ def main():
                     help="run only the standalone relabel throughput (a short command for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    w = WORKLOADS[args.workload]
+    w = WORKLOADS.get(args.workload, workload.ANT_AUTOGRAD)
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -368,6 +499,9 @@ def main():
     # as a CUDA graph there (the legacy default stream cannot be captured)
     torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if args.workload == "sweep":
+        run_sweep(args, dev, flush)
+        return
     if args.only_relabel:
         rw, res = relabel_throughput(dev, flush)
         print(json.dumps({"relabel": {"workload": rw.name, "results": res}}), flush=True)

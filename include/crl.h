@@ -297,6 +297,8 @@ int crl_sweep_agent(crl_sweep* sw, int32_t i, crl_ctx** ctx);
  * device, or NULL. */
 int crl_sweep_update_step(crl_sweep* sw, const float* const* obs, const float* const* act,
                           const uint8_t* const* done, int32_t n_insert, float* loss_out, void* stream);
+/* Tracing a sweep: crl_trace_start / crl_trace_stop on agent 0's context
+ * record every launch of the sweep step (the step then runs eagerly). */
 /* OR of the status words of the sweep's shared launches and of every agent
  * (read and cleared); the return code as crl_sync_status. */
 int crl_sweep_sync_status(crl_sweep* sw, void* stream, uint32_t* status);
@@ -311,6 +313,17 @@ const char* crl_sweep_last_error(const crl_sweep* sw);
  * graphs captured) after the call; a context whose update-step graph was
  * captured before keeps replaying it.  Returns the previous setting. */
 int32_t crl_set_launch_overlap(int32_t enable);
+
+/* ---- tile autotuning (library extension; the paper has no counterpart) ----
+ * Process-wide.  enable = 1 (the default): the first eager launch of each
+ * distinct grouped tensor-core GEMM (a problem list: sizes, operands,
+ * epilogue) times the tile widths 64, 128 and 256 on the launch itself
+ * (repeating it is harmless: its outputs are a pure function of inputs it
+ * does not modify) and keeps the fastest for that context or sweep; outputs
+ * do not depend on the tile width.  enable = 0: a fixed rule (128-wide tiles
+ * when they fill the GPU, else 64).  Never tunes during graph capture or
+ * tracing.  Returns the previous setting. */
+int32_t crl_set_autotune(int32_t enable);
 
 /* ---- op-level entry points (stateless; used by torch.autograd.Function) ---
  * Same kernels as the step calls.  dtype: CRL_PREC_FP32 (float) or

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "crl_trace_start": (c_int32, [c_void_p, c_int32, c_int32]),
     "crl_trace_stop": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_double), POINTER(c_double)]),
     "crl_set_launch_overlap": (c_int32, [c_int32]),
+    "crl_set_autotune": (c_int32, [c_int32]),
     "crl_sweep_create": (c_int32, [POINTER(CrlConfig), c_int32, c_int32, POINTER(c_void_p)]),
     "crl_sweep_destroy": (c_int32, [c_void_p]),
     "crl_sweep_agent": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
@@ -156,6 +157,12 @@ def set_launch_overlap(enable):
     """Process-wide: launch every kernel with programmatic stream serialisation
     (True, the default) or in plain stream order.  Returns the previous setting."""
     return bool(lib().crl_set_launch_overlap(1 if enable else 0))
+
+
+def set_autotune(enable):
+    """Process-wide: time the grouped GEMMs' tile widths on first use (True, the
+    default) or use the fixed rule.  Returns the previous setting."""
+    return bool(lib().crl_set_autotune(1 if enable else 0))
 
 
 def stream_handle(stream=None):

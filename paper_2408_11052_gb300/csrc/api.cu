@@ -22,6 +22,7 @@ using namespace crl;
 namespace crl {
 thread_local Tracer* g_tracer = nullptr;
 int g_launch_overlap = 1;
+int g_autotune = 1;
 }
 
 namespace crl {
@@ -841,6 +842,12 @@ const char* crl_last_error(const crl_ctx* ctx) { return ctx ? ctx->err.c_str() :
 int32_t crl_set_launch_overlap(int32_t enable) {
   const int32_t prev = g_launch_overlap;
   g_launch_overlap = enable ? 1 : 0;
+  return prev;
+}
+
+int32_t crl_set_autotune(int32_t enable) {
+  const int32_t prev = g_autotune;
+  g_autotune = enable ? 1 : 0;
   return prev;
 }
 

@@ -99,8 +99,10 @@ __device__ __forceinline__ void pdl_enter() {
   pdl_trigger();
 }
 
-// Process-wide switch (crl_set_launch_overlap); 1 = launch with the attribute.
+// Process-wide switches: crl_set_launch_overlap (1 = launch with the attribute)
+// and crl_set_autotune (1 = grouped GEMMs time their tile widths on first use).
 extern int g_launch_overlap;
+extern int g_autotune;
 
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

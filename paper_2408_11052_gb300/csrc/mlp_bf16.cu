@@ -331,23 +331,78 @@ void launch_gemm_bn(const tc::GemmProblem* table, int nprob, int tiles, unsigned
   launch_k(tc::tc_gemm_kernel<BN>, dim3(tiles), dim3(128), S::kBytes, st, table, nprob, status);
 }
 
-// One grouped launch of `probs`: 128 x 64 tiles unless 128 x 128 tiles already
-// fill the 152 SMs.  `flops` is the algorithmic work (2 M N K of the unsplit
-// products) for tracing.
+void launch_bn(int BN, const tc::GemmProblem* t, int nprob, int tiles, unsigned* status, cudaStream_t st) {
+  if (BN == 256) launch_gemm_bn<256>(t, nprob, tiles, status, st);
+  else if (BN == 128) launch_gemm_bn<128>(t, nprob, tiles, status, st);
+  else launch_gemm_bn<64>(t, nprob, tiles, status, st);
+}
+
+// Tile width without measurement: 128 x 64 tiles unless 128 x 128 tiles already fill the 152 SMs.
+int heuristic_bn(const std::vector<tc::GemmProblem>& probs) {
+  long long ctas128 = 0;
+  for (const auto& p : probs) ctas128 += (long long)ceil_div(p.M, 128) * ceil_div(p.N, 128);
+  return ctas128 >= 148 ? 128 : 64;
+}
+
+// Autotuner: time each candidate tile width on the launch itself (every GEMM
+// epilogue writes a pure function of inputs the launch does not modify, so
+// repeating it is harmless and the tile width does not change any output
+// value), keep the fastest.  Runs once per distinct problem list, outside
+// graph capture; returns 0 when it cannot measure (the caller falls back).
+int tune_bn(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, unsigned* status, cudaStream_t st) {
+  static const int kCand[3] = {64, 128, 256};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return 0;
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  for (int BN : kCand) {
+    int tiles = 0;
+    const char* err = nullptr;
+    const tc::GemmProblem* t = gg.table(probs, BN, &tiles, st, &err);
+    if (!t || tiles == 0) continue;
+    launch_bn(BN, t, (int)probs.size(), tiles, status, st);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) launch_bn(BN, t, (int)probs.size(), tiles, status, st);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+    if (best == 0 || ms < best_ms) {
+      best = BN;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+// One grouped launch of `probs` with the tuned (or heuristic) tile width.
+// `flops` is the algorithmic work (2 M N K of the unsplit products) for tracing.
 const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, double flops, unsigned* status,
                          cudaStream_t st) {
   if (probs.empty()) return nullptr;
-  long long ctas128 = 0;
-  for (const auto& p : probs) ctas128 += (long long)ceil_div(p.M, 128) * ceil_div(p.N, 128);
-  const int BN = ctas128 >= 148 ? 128 : 64;
+  const uint64_t key = fnv1a(probs.data(), probs.size() * sizeof(tc::GemmProblem));
+  int BN = gg.tuned_bn(key);
+  if (BN == 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+    if (g_autotune && !capturing && g_tracer == nullptr) {
+      BN = tune_bn(gg, probs, status, st);
+      if (BN) gg.set_tuned_bn(key, BN);
+    }
+    if (BN == 0) BN = heuristic_bn(probs);
+  }
   int tiles = 0;
   const char* err = nullptr;
   const tc::GemmProblem* t = gg.table(probs, BN, &tiles, st, &err);
   if (!t) return err;
   if (tiles == 0) return nullptr;
   TraceLaunch tr(CRL_TRACE_GEMM, st, flops);
-  if (BN == 128) launch_gemm_bn<128>(t, (int)probs.size(), tiles, status, st);
-  else launch_gemm_bn<64>(t, (int)probs.size(), tiles, status, st);
+  launch_bn(BN, t, (int)probs.size(), tiles, status, st);
   return nullptr;
 }
 
@@ -401,6 +456,7 @@ void GemmGroups::reset() {
   for (void* p : chunks_) cudaFree(p);
   chunks_.clear();
   map_.clear();
+  tuned_.clear();
   cur_ = nullptr;
   used_ = cap_ = 0;
 }
@@ -731,7 +787,14 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __re
   pdl_enter();
   int lb, nb;
   const int s = segment_of(begin, n, blockIdx.x, lb, nb);
-  adam_shadow_body(nets[s], lb, nb);
+  // the network's descriptor (read for every element's layer lookup) into shared memory
+  __shared__ AdamNetDev sa;
+  static_assert(sizeof(AdamNetDev) % 4 == 0, "word copy");
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(nets + s);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+  for (int i = threadIdx.x; i < (int)(sizeof(AdamNetDev) / 4); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  adam_shadow_body(sa, lb, nb);
 }
 
 }  // namespace

@@ -97,10 +97,22 @@ class GemmGroups {
   // device table; nullptr (and *err) on failure.
   const tc::GemmProblem* table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles, cudaStream_t st,
                                const char** err);
-  // Frees every table (synchronises the device).
+  // Frees every table (synchronises the device) and forgets the tuned tile widths.
   void reset();
+  // Autotuned tile width of a problem list (keyed by its untiled content), 0 if none.
+  int tuned_bn(uint64_t key) const {
+    auto it = tuned_.find(key);
+    return it == tuned_.end() ? 0 : it->second;
+  }
+  void set_tuned_bn(uint64_t key, int bn) { tuned_[key] = bn; }
+  // Tile widths chosen so far: counts of 64, 128 and 256.
+  void tuned_counts(int* c64, int* c128, int* c256) const {
+    *c64 = *c128 = *c256 = 0;
+    for (const auto& kv : tuned_) (kv.second == 256 ? *c256 : kv.second == 128 ? *c128 : *c64) += 1;
+  }
 
  private:
+  std::unordered_map<uint64_t, int> tuned_;
   struct Entry {
     const tc::GemmProblem* dev;
     int tiles;

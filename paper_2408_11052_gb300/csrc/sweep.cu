@@ -53,8 +53,16 @@ int sweep_fail(crl_sweep* sw, const Failure& f) {
   return fail(nullptr, f);
 }
 
+// Runs one sweep entry point; launches are traced by agent 0's tracer when it is on.
 template <typename F>
 int sweep_guarded(crl_sweep* sw, F&& body) {
+  struct TracerScope {
+    explicit TracerScope(crl_sweep* s) {
+      crl_ctx* c = (s && !s->agents.empty()) ? s->agents[0] : nullptr;
+      g_tracer = (c && c->tracer.cls) ? &c->tracer : nullptr;
+    }
+    ~TracerScope() { g_tracer = nullptr; }
+  } scope(sw);
   try {
     body();
     return CRL_OK;

@@ -137,6 +137,28 @@ def buffer_contents(w, n=None, mean_len=None, seed_offset=0):
     return obs, act, done
 
 
+def buffer_contents_device(w, n=None, seed_offset=0, device="cuda"):
+    """The recipe of ``buffer_contents`` with fixed-length episodes, drawn on the
+    device with a seeded torch generator (a different random stream from the
+    numpy one; used to fill large buffers quickly, e.g. the 32-agent sweep).
+    Returns device tensors obs [n][E][D], act [n][E][A], done [n][E] (uint8)."""
+    import torch
+    n = w.T if n is None else n
+    g = torch.Generator(device=device)
+    g.manual_seed(w.seed * 7919 + 29 + seed_offset)
+    t = torch.arange(n, device=device)
+    done = ((t + 1) % w.episode_len == 0).to(torch.uint8)[:, None].expand(n, w.E).contiguous()
+    act = torch.rand((n, w.E, w.A), generator=g, device=device) * 2.0 - 1.0
+    obs = torch.empty((n, w.E, w.D), device=device)
+    for e0 in range(0, n, w.episode_len):
+        e1 = min(n, e0 + w.episode_len)
+        start = torch.randn((1, w.E, w.D), generator=g, device=device)
+        steps = 0.1 * torch.randn((e1 - e0, w.E, w.D), generator=g, device=device)
+        steps[0] = 0.0
+        obs[e0:e1] = start + torch.cumsum(steps, dim=0)
+    return obs, act, done
+
+
 def network_shapes(w, net):
     """(in_dim, [hidden]*layers, out_dim) of phi, psi or pi."""
     ins = {"phi": w.D + w.A, "psi": w.G, "pi": w.D + w.G}[net]
