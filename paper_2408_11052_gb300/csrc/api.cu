@@ -293,7 +293,15 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     bf_maps(c, CRL_NET_PI, B);
     bf_refresh(c, CRL_NET_PI, refresh, st);
   }
-  bf_check(bf_forward(c->groups, pass, with_pi ? 3 : 2, status, st));
+  // fused path: the encoders' output layers also write the energy's BF16 operands
+  const EnergyOut eo[2] = {{c->etc.X, c->etc.XT, c->etc.ldt, c->etc.auxX, cf.energy},
+                           {c->etc.Y, c->etc.YT, c->etc.ldt, c->etc.auxY, cf.energy}};
+  BfPass fpass[3] = {pass[0], pass[1], pass[2]};
+  if (c->fused) {
+    fpass[0].energy_out = &eo[0];
+    fpass[1].energy_out = &eo[1];
+  }
+  bf_check(bf_forward(c->groups, fpass, with_pi ? 3 : 2, status, st));
   float* rl = static_cast<float*>(c->row_lse);
   float* cl = static_cast<float*>(c->col_lse);
   float* loss = static_cast<float*>(c->loss);
@@ -304,7 +312,6 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     // fused tcgen05 energy stage: no B x B matrix; the gradients land in the encoders' dy buffers
     const char* e = energy_tc_maps(c->etc, B);
     if (e) throw Failure(CRL_E_CUDA, std::string("tensor map: ") + e);
-    energy_tc_prepare(c->etc, ls, P.y, Q.y, B, st);
     energy_tc_forward(c->etc, ls, B, loss, rl, cl, c->etc_ws, status, apply ? &c->ctr->t_critic : nullptr, st);
     energy_tc_backward(c->etc, ls, B, P.y, Q.y, rl, cl, 1.0, P.dz[P.layers], P.dzT[P.layers], Q.dz[Q.layers],
                        Q.dzT[Q.layers], P.Mmax, status, st);

@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
@@ -133,6 +134,34 @@ void pack(int rows, const float* s0, int ld0, int n0, const float* s1, int ld1, 
 }
 
 // ---- LayerNorm (grouped over the networks of a pass: blockIdx.y = network) ----------
+// Block = 8 warps x 2 rows = 16 rows.  Each warp reduces its row with float4
+// loads (three passes over the row: mean, variance, output; the row stays in
+// L1), writes the row-major outputs and stages the BF16 row in shared memory;
+// the block then writes the transposed copy as 16-byte pieces of 8 rows.
+constexpr int kLnRows = 16;
+inline size_t ln_smem_bytes(int H) { return (size_t)kLnRows * (H + 4) * 2; }
+constexpr int kLnMaxSmem = 200 * 1024;   // hidden widths up to 6396
+
+// Transposed store of the staged [16][H] BF16 tile (row stride H + 4) into
+// dst [H][ldt] at rows row0 .. row0 + 15 (clipped to M).
+__device__ __forceinline__ void ln_store_transposed(const bf16* tile, int H, bf16* dst, int ldt, int row0, int M) {
+  const int S = H + 4;
+  for (int idx = threadIdx.x; idx < 2 * H; idx += blockDim.x) {
+    const int c = idx >> 1, half = idx & 1;
+    const int r0 = row0 + 8 * half;
+    if (r0 >= M) continue;
+    alignas(16) bf16 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = tile[(8 * half + k) * S + c];
+    bf16* d = dst + (size_t)c * ldt + r0;
+    if (r0 + 8 <= M) {
+      *reinterpret_cast<uint4*>(d) = *reinterpret_cast<const uint4*>(v);
+    } else {
+      for (int k = 0; k < M - r0; ++k) d[k] = v[k];
+    }
+  }
+}
+
 struct LnFwdNet {
   int M, ldt;
   float* z;
@@ -147,47 +176,56 @@ struct LnFwdGroup {
 };
 
 // LayerNorm forward over rows of z [M][H] (FP32, replaced by zhat), rstd [M],
-// h = ReLU(zhat * g + beta) written as BF16 [M][H] and, through a shared tile,
-// transposed [H][ldt].  Block = 32 rows (one warp each).
-__global__ void __launch_bounds__(1024) ln_fwd_kernel(int H, const __grid_constant__ LnFwdGroup grp) {
+// h = ReLU(zhat * g + beta) written as BF16 [M][H] and transposed [H][ldt].
+__global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constant__ LnFwdGroup grp) {
   pdl_enter();
+  extern __shared__ __align__(16) unsigned char ln_smem[];
+  bf16* tile = reinterpret_cast<bf16*>(ln_smem);
   const LnFwdNet& a = grp.n[blockIdx.y];
-  const int M = a.M, ldt = a.ldt;
-  float* __restrict__ z = a.z;
-  __shared__ float tile[32][33];
+  const int M = a.M, ldt = a.ldt, S = H + 4;
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int row = blockIdx.x * 32 + w;
-  float mean = 0.f, rs = 0.f;
-  if (row < M) {
-    const float* zr = z + (size_t)row * H;
+  const int row0 = blockIdx.x * kLnRows;
+  if (row0 >= M) return;
+  const int nv = H / 4;
+  for (int rr = w; rr < kLnRows; rr += 8) {
+    const int row = row0 + rr;
+    if (row >= M) break;
+    float4* zr = reinterpret_cast<float4*>(a.z + (size_t)row * H);
     float s = 0.f;
-    for (int c = lane; c < H; c += 32) s += zr[c];
-    mean = warp_sum(s) / H;
-    float q = 0.f;
-    for (int c = lane; c < H; c += 32) {
-      const float d = zr[c] - mean;
-      q += d * d;
+    for (int q = lane; q < nv; q += 32) {
+      const float4 x = zr[q];
+      s += (x.x + x.y) + (x.z + x.w);
     }
-    rs = rsqrtf(warp_sum(q) / H + kLnEpsF);
+    const float mean = warp_sum(s) / H;
+    float sq = 0.f;
+    for (int q = lane; q < nv; q += 32) {
+      const float4 x = zr[q];
+      const float d0 = x.x - mean, d1 = x.y - mean, d2 = x.z - mean, d3 = x.w - mean;
+      sq += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
+    }
+    const float rs = rsqrtf(warp_sum(sq) / H + kLnEpsF);
     if (lane == 0) a.rstd[row] = rs;
-  }
-  for (int c0 = 0; c0 < H; c0 += 32) {
-    const int c = c0 + lane;
-    float hv = 0.f;
-    if (row < M && c < H) {
-      const size_t o = (size_t)row * H + c;
-      const float zh = (z[o] - mean) * rs;
-      z[o] = zh;
-      hv = fmaxf(zh * a.g[c] + a.beta[c], 0.f);
-      a.h[o] = __float2bfloat16_rn(hv);
+    const float4* g4 = reinterpret_cast<const float4*>(a.g);
+    const float4* b4 = reinterpret_cast<const float4*>(a.beta);
+    uint2* hr = reinterpret_cast<uint2*>(a.h + (size_t)row * H);
+    uint2* tr = reinterpret_cast<uint2*>(tile + rr * S);
+    for (int q = lane; q < nv; q += 32) {
+      float4 x = zr[q];
+      const float4 gg = g4[q], bb = b4[q];
+      x.x = (x.x - mean) * rs;
+      x.y = (x.y - mean) * rs;
+      x.z = (x.z - mean) * rs;
+      x.w = (x.w - mean) * rs;
+      zr[q] = x;
+      const __nv_bfloat162 p0 = __floats2bfloat162_rn(fmaxf(x.x * gg.x + bb.x, 0.f), fmaxf(x.y * gg.y + bb.y, 0.f));
+      const __nv_bfloat162 p1 = __floats2bfloat162_rn(fmaxf(x.z * gg.z + bb.z, 0.f), fmaxf(x.w * gg.w + bb.w, 0.f));
+      const uint2 v = make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+      hr[q] = v;
+      tr[q] = v;
     }
-    tile[w][lane] = hv;
-    __syncthreads();
-    // warp w writes column c0 + w for the block's 32 rows
-    const int cc = c0 + w, rr = blockIdx.x * 32 + lane;
-    if (cc < H && rr < M) a.hT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
-    __syncthreads();
   }
+  __syncthreads();
+  ln_store_transposed(tile, H, a.hT, ldt, row0, M);
 }
 
 struct LnBwdNet {
@@ -198,82 +236,92 @@ struct LnBwdNet {
   const float* g;
   bf16* dz;
   bf16* dzT;
-  float* dg;   // ln_param_grad_kernel only
+  float* dg;          // null: no LayerNorm parameter gradients
   float* db;
+  float* partial;     // [ceil(M / 16)][2][H] per-block column sums (dg, db)
+  unsigned* ticket;   // zero between launches
 };
 struct LnBwdGroup {
   LnBwdNet n[kMaxGroupNets];
 };
 
-// LayerNorm backward: du (ReLU-masked, FP32) -> dz = rstd (g du - mean(g du) - zhat mean(g du zhat)),
-// written BF16 [M][H] and transposed.  Block = 32 rows.
-__global__ void __launch_bounds__(1024) ln_bwd_kernel(int H, const __grid_constant__ LnBwdGroup grp) {
+// LayerNorm backward: du (ReLU-masked, FP32) -> dz = rstd (g du - mean(g du) -
+// zhat mean(g du zhat)), written BF16 [M][H] and transposed; with dg / db the
+// gain and shift gradients dg = sum_m du zhat, db = sum_m du: every block
+// writes its 16 rows' column sums, and the last block to finish (ticket) adds
+// them in block order.
+__global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constant__ LnBwdGroup grp) {
   pdl_enter();
+  extern __shared__ __align__(16) unsigned char ln_smem[];
+  bf16* tile = reinterpret_cast<bf16*>(ln_smem);
+  __shared__ int s_last;
   const LnBwdNet& a = grp.n[blockIdx.y];
-  const int M = a.M, ldt = a.ldt;
-  const float* __restrict__ du = a.du;
-  const float* __restrict__ zhat = a.zhat;
-  const float* __restrict__ g = a.g;
-  __shared__ float tile[32][33];
+  const int M = a.M, ldt = a.ldt, S = H + 4;
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int row = blockIdx.x * 32 + w;
-  float s1 = 0.f, s2 = 0.f, rs = 0.f;
-  if (row < M) {
-    for (int c = lane; c < H; c += 32) {
-      const size_t o = (size_t)row * H + c;
-      const float d = du[o] * g[c];
-      s1 += d;
-      s2 += d * zhat[o];
+  const int row0 = blockIdx.x * kLnRows;
+  const int nblk = (M + kLnRows - 1) / kLnRows;
+  if (row0 >= M) return;
+  const int nv = H / 4;
+  const float4* g4 = reinterpret_cast<const float4*>(a.g);
+  for (int rr = w; rr < kLnRows; rr += 8) {
+    const int row = row0 + rr;
+    if (row >= M) break;
+    const float4* dr = reinterpret_cast<const float4*>(a.du + (size_t)row * H);
+    const float4* zr = reinterpret_cast<const float4*>(a.zhat + (size_t)row * H);
+    float s1 = 0.f, s2 = 0.f;
+    for (int q = lane; q < nv; q += 32) {
+      const float4 d = dr[q], z = zr[q], gg = g4[q];
+      const float e0 = d.x * gg.x, e1 = d.y * gg.y, e2 = d.z * gg.z, e3 = d.w * gg.w;
+      s1 += (e0 + e1) + (e2 + e3);
+      s2 += (e0 * z.x + e1 * z.y) + (e2 * z.z + e3 * z.w);
     }
     s1 = warp_sum(s1) / H;
     s2 = warp_sum(s2) / H;
-    rs = a.rstd[row];
-  }
-  for (int c0 = 0; c0 < H; c0 += 32) {
-    const int c = c0 + lane;
-    float v = 0.f;
-    if (row < M && c < H) {
-      const size_t o = (size_t)row * H + c;
-      v = rs * (du[o] * g[c] - s1 - zhat[o] * s2);
-      a.dz[o] = __float2bfloat16_rn(v);
-    }
-    tile[w][lane] = v;
-    __syncthreads();
-    const int cc = c0 + w, rr = blockIdx.x * 32 + lane;
-    if (cc < H && rr < M) a.dzT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
-    __syncthreads();
-  }
-}
-
-// dgain[n] = sum_m du * zhat, dbeta[n] = sum_m du.  Block = 32 columns x 8 row groups.
-__global__ void __launch_bounds__(256) ln_param_grad_kernel(int H, const __grid_constant__ LnBwdGroup grp) {
-  pdl_enter();
-  const LnBwdNet& p = grp.n[blockIdx.y];
-  const int M = p.M;
-  const float* __restrict__ du = p.du;
-  const float* __restrict__ zhat = p.zhat;
-  __shared__ float sa[8][33], sb[8][33];
-  const int cx = threadIdx.x % 32, ry = threadIdx.x / 32;
-  const int n = blockIdx.x * 32 + cx;
-  float a = 0.f, b = 0.f;
-  if (n < H) {
-    for (int m = ry; m < M; m += 8) {
-      const size_t o = (size_t)m * H + n;
-      a += du[o] * zhat[o];
-      b += du[o];
+    const float rs = a.rstd[row];
+    uint2* out = reinterpret_cast<uint2*>(a.dz + (size_t)row * H);
+    uint2* tr = reinterpret_cast<uint2*>(tile + rr * S);
+    for (int q = lane; q < nv; q += 32) {
+      const float4 d = dr[q], z = zr[q], gg = g4[q];
+      const __nv_bfloat162 p0 = __floats2bfloat162_rn(rs * (d.x * gg.x - s1 - z.x * s2),
+                                                      rs * (d.y * gg.y - s1 - z.y * s2));
+      const __nv_bfloat162 p1 = __floats2bfloat162_rn(rs * (d.z * gg.z - s1 - z.z * s2),
+                                                      rs * (d.w * gg.w - s1 - z.w * s2));
+      const uint2 v = make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+      out[q] = v;
+      tr[q] = v;
     }
   }
-  sa[ry][cx] = a;
-  sb[ry][cx] = b;
   __syncthreads();
-  if (ry == 0 && n < H) {
-    for (int r = 1; r < 8; ++r) {
-      a += sa[r][cx];
-      b += sb[r][cx];
+  ln_store_transposed(tile, H, a.dzT, ldt, row0, M);
+  if (a.dg == nullptr) return;
+  // column sums of this block's rows
+  const int rmax = min(kLnRows, M - row0);
+  for (int c = threadIdx.x; c < H; c += blockDim.x) {
+    float sg = 0.f, sb = 0.f;
+    for (int r = 0; r < rmax; ++r) {
+      const size_t o = (size_t)(row0 + r) * H + c;
+      sg += a.du[o] * a.zhat[o];
+      sb += a.du[o];
     }
-    p.dg[n] = a;
-    p.db[n] = b;
+    a.partial[((size_t)blockIdx.x * 2 + 0) * H + c] = sg;
+    a.partial[((size_t)blockIdx.x * 2 + 1) * H + c] = sb;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(a.ticket, 1u) == (unsigned)nblk - 1u) ? 1 : 0;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int c = threadIdx.x; c < H; c += blockDim.x) {
+    float sg = 0.f, sb = 0.f;
+    for (int k = 0; k < nblk; ++k) {
+      sg += __ldcg(a.partial + ((size_t)k * 2 + 0) * H + c);
+      sb += __ldcg(a.partial + ((size_t)k * 2 + 1) * H + c);
+    }
+    a.dg[c] = sg;
+    a.db[c] = sb;
+  }
+  if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
 __global__ void fill_bf16_kernel(bf16* p, size_t n, float v) {
@@ -320,37 +368,49 @@ tc::GemmProblem problem(const CUtensorMap& a, const CUtensorMap& b, int M, int N
   return p;
 }
 
-template <int BN>
-void launch_gemm_bn(const tc::GemmProblem* table, int nprob, int tiles, unsigned* status, cudaStream_t st) {
-  using S = tc::GemmSmem<BN>;
+template <int BN, int STAGES>
+void launch_gemm_cfg(const tc::GemmProblem* table, int nprob, int tiles, unsigned* status, cudaStream_t st) {
+  using S = tc::GemmSmem<BN, STAGES>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tc::tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+    cudaFuncSetAttribute(tc::tc_gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
     attr = true;
   }
-  launch_k(tc::tc_gemm_kernel<BN>, dim3(tiles), dim3(128), S::kBytes, st, table, nprob, status);
+  launch_k(tc::tc_gemm_kernel<BN, STAGES>, dim3(tiles), dim3(128), S::kBytes, st, table, nprob, status);
 }
 
-void launch_bn(int BN, const tc::GemmProblem* t, int nprob, int tiles, unsigned* status, cudaStream_t st) {
-  if (BN == 256) launch_gemm_bn<256>(t, nprob, tiles, status, st);
-  else if (BN == 128) launch_gemm_bn<128>(t, nprob, tiles, status, st);
-  else launch_gemm_bn<64>(t, nprob, tiles, status, st);
+// A GEMM configuration: tile width and ring depth, coded as 16 * BN + stages.
+constexpr int gemm_cfg(int bn, int stages) { return 16 * bn + stages; }
+constexpr int kGemmCfgs[5] = {gemm_cfg(64, 4), gemm_cfg(64, 8), gemm_cfg(128, 3), gemm_cfg(128, 6),
+                              gemm_cfg(256, 4)};
+
+void launch_cfg(int cfg, const tc::GemmProblem* t, int nprob, int tiles, unsigned* status, cudaStream_t st) {
+  switch (cfg) {
+    case gemm_cfg(64, 8): launch_gemm_cfg<64, 8>(t, nprob, tiles, status, st); break;
+    case gemm_cfg(128, 3): launch_gemm_cfg<128, 3>(t, nprob, tiles, status, st); break;
+    case gemm_cfg(128, 4): launch_gemm_cfg<128, 4>(t, nprob, tiles, status, st); break;
+    case gemm_cfg(128, 6): launch_gemm_cfg<128, 6>(t, nprob, tiles, status, st); break;
+    case gemm_cfg(256, 4): launch_gemm_cfg<256, 4>(t, nprob, tiles, status, st); break;
+    default: launch_gemm_cfg<64, 4>(t, nprob, tiles, status, st); break;
+  }
 }
 
-// Tile width without measurement: 128 x 64 tiles unless 128 x 128 tiles already fill the 152 SMs.
-int heuristic_bn(const std::vector<tc::GemmProblem>& probs) {
+// Configuration without measurement: 128 x 64 tiles unless 128 x 128 tiles
+// already fill the 152 SMs; 4-deep rings.
+int heuristic_cfg(const std::vector<tc::GemmProblem>& probs, int min_bn) {
   long long ctas128 = 0;
   for (const auto& p : probs) ctas128 += (long long)ceil_div(p.M, 128) * ceil_div(p.N, 128);
-  return ctas128 >= 148 ? 128 : 64;
+  const int bn = std::max(ctas128 >= 148 ? 128 : 64, min_bn <= 64 ? 64 : (min_bn <= 128 ? 128 : 256));
+  return bn == 256 ? gemm_cfg(256, 4) : (bn == 128 ? gemm_cfg(128, 4) : gemm_cfg(64, 4));
 }
 
-// Autotuner: time each candidate tile width on the launch itself (every GEMM
-// epilogue writes a pure function of inputs the launch does not modify, so
-// repeating it is harmless and the tile width does not change any output
-// value), keep the fastest.  Runs once per distinct problem list, outside
-// graph capture; returns 0 when it cannot measure (the caller falls back).
-int tune_bn(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, unsigned* status, cudaStream_t st) {
-  static const int kCand[3] = {64, 128, 256};
+// Autotuner: time each candidate configuration (tile width, ring depth) on
+// the launch itself (every GEMM epilogue writes a pure function of inputs the
+// launch does not modify, so repeating it is harmless, and neither choice
+// changes any output value), keep the fastest.  Runs once per distinct problem
+// list, outside graph capture; returns 0 when it cannot measure (the caller
+// falls back to the fixed rule).
+int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, unsigned* status, cudaStream_t st) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return 0;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -359,19 +419,20 @@ int tune_bn(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, unsigned* statu
   }
   int best = 0;
   float best_ms = 0.f;
-  for (int BN : kCand) {
+  for (int cfg : kGemmCfgs) {
+    if (cfg / 16 < min_bn) continue;
     int tiles = 0;
     const char* err = nullptr;
-    const tc::GemmProblem* t = gg.table(probs, BN, &tiles, st, &err);
+    const tc::GemmProblem* t = gg.table(probs, cfg / 16, &tiles, st, &err);
     if (!t || tiles == 0) continue;
-    launch_bn(BN, t, (int)probs.size(), tiles, status, st);  // warm-up
+    launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);  // warm-up
     cudaEventRecord(e0, st);
-    for (int r = 0; r < 3; ++r) launch_bn(BN, t, (int)probs.size(), tiles, status, st);
+    for (int r = 0; r < 3; ++r) launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);
     cudaEventRecord(e1, st);
     float ms = 0.f;
     if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
     if (best == 0 || ms < best_ms) {
-      best = BN;
+      best = cfg;
       best_ms = ms;
     }
   }
@@ -386,23 +447,28 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
                          cudaStream_t st) {
   if (probs.empty()) return nullptr;
   const uint64_t key = fnv1a(probs.data(), probs.size() * sizeof(tc::GemmProblem));
-  int BN = gg.tuned_bn(key);
-  if (BN == 0) {
+  // an energy-operand epilogue needs the whole row in one tile
+  int min_bn = 0;
+  for (const auto& p : probs)
+    if (p.epi.kind == tc::kEpiFwdOutEnergy) min_bn = std::max(min_bn, p.N);
+  if (min_bn > 256) return "an energy-operand output layer wider than 256 columns";
+  int cfg = g_autotune ? gg.tuned_bn(key) : 0;
+  if (cfg == 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
     if (g_autotune && !capturing && g_tracer == nullptr) {
-      BN = tune_bn(gg, probs, status, st);
-      if (BN) gg.set_tuned_bn(key, BN);
+      cfg = tune_cfg(gg, probs, min_bn, status, st);
+      if (cfg) gg.set_tuned_bn(key, cfg);
     }
-    if (BN == 0) BN = heuristic_bn(probs);
+    if (cfg == 0) cfg = heuristic_cfg(probs, min_bn);
   }
   int tiles = 0;
   const char* err = nullptr;
-  const tc::GemmProblem* t = gg.table(probs, BN, &tiles, st, &err);
+  const tc::GemmProblem* t = gg.table(probs, cfg / 16, &tiles, st, &err);
   if (!t) return err;
   if (tiles == 0) return nullptr;
   TraceLaunch tr(CRL_TRACE_GEMM, st, flops);
-  launch_bn(BN, t, (int)probs.size(), tiles, status, st);
+  launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);
   return nullptr;
 }
 
@@ -462,6 +528,7 @@ void GemmGroups::reset() {
 }
 
 const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner) {
+  if (s.layernorm && ln_smem_bytes(s.hidden) > (size_t)kLnMaxSmem) return "LayerNorm hidden width above 6396";
   n.s = s;
   n.Mmax = Mmax;
   n.layers = s.layers;
@@ -509,7 +576,13 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
     n.dzT[l] = static_cast<bf16*>(A(w * Mmax * 2));
     if (cudaMemset(n.dz[l], 0, (size_t)Mmax * w * 2) != cudaSuccess) return "cudaMemset failed";
   }
-  if (s.layernorm) n.du = static_cast<float*>(A((size_t)Mmax * H * 4));
+  if (s.layernorm) {
+    n.du = static_cast<float*>(A((size_t)Mmax * H * 4));
+    n.ln_partial = static_cast<float*>(A((size_t)ceil_div(Mmax, kLnRows) * 2 * H * 4));
+    n.ln_ticket = static_cast<unsigned*>(A(256));
+    if (!n.du || !n.ln_partial || !n.ln_ticket || cudaMemset(n.ln_ticket, 0, 256) != cudaSuccess)
+      return "LayerNorm workspace set-up failed";
+  }
   if (cudaMemset(n.x0, 0, (size_t)Mmax * pad8(2 * in) * 2) != cudaSuccess) return "cudaMemset failed";
   // the ones rows of the transposed activations (never overwritten)
   fill_bf16_kernel<<<ceil_div(Mmax, 256), 256>>>(n.x0T + (size_t)(2 * in) * Mmax, Mmax, 1.f);
@@ -582,7 +655,17 @@ const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* 
       const float* params = nets[k].params;
       const CUtensorMap& A = (l == 0) ? n.tm_x0A : n.tm_hA[l - 1];
       tc::EpiDesc e;
-      if (l == layers) {
+      if (l == layers && nets[k].energy_out) {
+        const EnergyOut& eo = *nets[k].energy_out;
+        e = epi_of(tc::kEpiFwdOutEnergy);
+        e.ld0 = L.out;
+        e.out0 = n.y;
+        e.out1 = eo.X;
+        e.out2 = eo.XT;
+        e.ld1 = eo.ldt;
+        e.aux = eo.aux;
+        e.energy = eo.energy;
+      } else if (l == layers) {
         e = epi_of(tc::kEpiFwdOut);
         e.ld0 = L.out;
         e.out0 = n.y;
@@ -618,8 +701,13 @@ const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* 
         bytes += (double)M * H * 12.0;
       }
       if (Mx == 0) continue;
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(ln_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLnMaxSmem);
+        attr = true;
+      }
       TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
-      launch_k(ln_fwd_kernel, dim3(ceil_div(Mx, 32), kc), dim3(1024), 0, st, H, grp);
+      launch_k(ln_fwd_kernel, dim3(ceil_div(Mx, kLnRows), kc), dim3(256), ln_smem_bytes(H), st, H, grp);
     }
   }
   return nullptr;
@@ -660,34 +748,38 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
     if (const char* err = launch_group(gg, probs, flops, status, st)) return err;
     for (int k0 = 0; ln && k0 < count; k0 += kMaxGroupNets) {
       const int kc = std::min(kMaxGroupNets, count - k0);
-      LnBwdGroup grp, pg;
+      LnBwdGroup grp;
       memset(&grp, 0, sizeof(grp));
-      memset(&pg, 0, sizeof(pg));
-      int np = 0, Mx = 0;
-      double bytes = 0.0, pbytes = 0.0;
+      int Mx = 0;
+      double bytes = 0.0;
       for (int k = 0; k < kc; ++k) {
         const BfPass& bp = nets[k0 + k];
         BfNet& n = *bp.net;
         const BfLayer& P = n.L[l - 1];
         const int M = std::max(bp.M, 0);
-        const LnBwdNet b{M, n.Mmax, n.du, n.z[l - 1], n.rstd[l - 1], bp.params + P.og, n.dz[l - 1], n.dzT[l - 1],
-                         bp.grads ? bp.grads + P.og : nullptr, bp.grads ? bp.grads + P.obeta : nullptr};
-        grp.n[k] = b;
+        grp.n[k] = LnBwdNet{M,
+                            n.Mmax,
+                            n.du,
+                            n.z[l - 1],
+                            n.rstd[l - 1],
+                            bp.params + P.og,
+                            n.dz[l - 1],
+                            n.dzT[l - 1],
+                            bp.grads ? bp.grads + P.og : nullptr,
+                            bp.grads ? bp.grads + P.obeta : nullptr,
+                            n.ln_partial,
+                            n.ln_ticket};
         Mx = std::max(Mx, M);
-        bytes += (double)M * H * 16.0;
-        if (bp.grads) {
-          pg.n[np++] = b;
-          pbytes += (double)M * H * 8.0;
-        }
+        bytes += (double)M * H * (bp.grads ? 24.0 : 16.0);
       }
       if (Mx == 0) continue;
-      // the parameter gradients read du before the next layer's launch overwrites it
-      if (np > 0) {
-        TraceLaunch tr(CRL_TRACE_AUX, st, pbytes);
-        launch_k(ln_param_grad_kernel, dim3(ceil_div(H, 32), np), dim3(256), 0, st, H, pg);
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(ln_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLnMaxSmem);
+        attr = true;
       }
       TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
-      launch_k(ln_bwd_kernel, dim3(ceil_div(Mx, 32), kc), dim3(1024), 0, st, H, grp);
+      launch_k(ln_bwd_kernel, dim3(ceil_div(Mx, kLnRows), kc), dim3(256), ln_smem_bytes(H), st, H, grp);
     }
   }
   // every weight gradient, and the first-layer input gradients, in one launch
@@ -738,63 +830,79 @@ struct AdamNetDev {
   long long n;
   const int* t;
   float lr, b1, b2, eps;
+  float log_b1, log_b2;   // ln(b1), ln(b2) (computed in double on the host)
   int nl;
   ShadowLayer L[CRL_MAX_LAYERS + 1];
 };
 
-// Adam on one network's FP32 master parameters (grid-stride over its blocks
-// lb of nb) and the refresh of its BF16 shadows.  Bias corrections in double
-// (1 - b^t loses most of its digits in float for small t).
-__device__ __forceinline__ void adam_shadow_body(const AdamNetDev& a, int lb, int nb) {
+// One block of work for the Adam + shadow kernel: a 32 x 32 tile of a weight
+// matrix (layer >= 0: rows [r0, r0 + 32) of the output units, columns
+// [c0, c0 + 32) of the inputs), or a flat range of the parameter array
+// (layer < 0: [r0, r0 + c0) -- biases, LayerNorm gains and shifts and the
+// zero padding between tensors, whose update is zero).
+struct AdamUnit {
+  int net, layer, r0, c0;
+};
+
+// Adam on the FP32 master parameters and the refresh of the BF16 shadows:
+// W2 = [W_hi | W_lo] row-major (coalesced along the tile's columns) and Wt
+// (the transposed single BF16, written through a shared-memory transpose).
+// Bias corrections 1 - b^t = -expm1(t ln b): accurate to a few float ulps
+// where 1 - b^t is small (early steps), unlike 1 - powf(b, t).
+__global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __restrict__ nets,
+                                                          const AdamUnit* __restrict__ units) {
+  pdl_enter();
+  const AdamUnit u = units[blockIdx.x];
+  const AdamNetDev& a = nets[u.net];
+  // the descriptor's fields in registers: the stores below cannot change them
+  const float* __restrict__ g = a.g;
+  float* __restrict__ m = a.m;
+  float* __restrict__ v = a.v;
+  float* __restrict__ p = a.p;
   const float b1 = a.b1, b2 = a.b2, eps = a.eps;
-  __shared__ float s_corr[2];
-  if (threadIdx.x == 0) {
-    const double t = (double)*a.t;
-    s_corr[0] = (float)((double)a.lr / (1.0 - pow((double)b1, t)));
-    s_corr[1] = (float)(1.0 / (1.0 - pow((double)b2, t)));
+  const float t = (float)*a.t;
+  const float c1 = a.lr / -expm1f(t * a.log_b1);
+  const float c2 = 1.f / -expm1f(t * a.log_b2);
+  auto step = [&](long long i) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - c1 * mi / (sqrtf(vi * c2) + eps);
+    p[i] = pi;
+    return pi;
+  };
+  if (u.layer < 0) {
+    for (int k = threadIdx.x; k < u.c0; k += blockDim.x) step((long long)u.r0 + k);
+    return;
   }
-  __syncthreads();
-  for (long long i = (long long)lb * blockDim.x + threadIdx.x; i < a.n; i += (long long)nb * blockDim.x) {
-    const float g = a.g[i];
-    const float mi = b1 * a.m[i] + (1.f - b1) * g;
-    const float vi = b2 * a.v[i] + (1.f - b2) * g * g;
-    a.m[i] = mi;
-    a.v[i] = vi;
-    const float p = a.p[i] - s_corr[0] * mi / (sqrtf(vi * s_corr[1]) + eps);
-    a.p[i] = p;
-    for (int l = 0; l < a.nl; ++l) {
-      const ShadowLayer& L = a.L[l];
-      const long long off = i - L.oW;
-      if (off >= 0 && off < (long long)L.out * L.in) {
-        const int o = (int)(off / L.in), c = (int)(off % L.in);
-        const bf16 hi = __float2bfloat16_rn(p);
-        const bf16 lo = __float2bfloat16_rn(p - __bfloat162float(hi));
-        bf16* d = L.W2 + (size_t)o * 2 * L.kp;
-        for (int q = 0; q < L.rep; ++q) {
-          d[L.rep * c + q] = hi;
-          d[L.kp + L.rep * c + q] = lo;
-        }
-        L.Wt[(size_t)c * L.ldt + o] = hi;
-        break;
+  __shared__ bf16 tile[32][34];
+  const ShadowLayer L = a.L[u.layer];
+  bf16* __restrict__ W2 = L.W2;
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    const int rr = e / 32, cc = e % 32;
+    const int o = u.r0 + rr, c = u.c0 + cc;
+    bf16 hi = __float2bfloat16_rn(0.f);
+    if (o < L.out && c < L.in) {
+      const float pv = step(L.oW + (long long)o * L.in + c);
+      hi = __float2bfloat16_rn(pv);
+      const bf16 lo = __float2bfloat16_rn(pv - __bfloat162float(hi));
+      bf16* d = W2 + (size_t)o * 2 * L.kp;
+      for (int q = 0; q < L.rep; ++q) {
+        d[L.rep * c + q] = hi;
+        d[L.kp + L.rep * c + q] = lo;
       }
     }
+    tile[cc][rr] = hi;
   }
-}
-
-// Network s owns blocks [begin[s], begin[s+1]).
-__global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __restrict__ nets,
-                                                          const int* __restrict__ begin, int n) {
-  pdl_enter();
-  int lb, nb;
-  const int s = segment_of(begin, n, blockIdx.x, lb, nb);
-  // the network's descriptor (read for every element's layer lookup) into shared memory
-  __shared__ AdamNetDev sa;
-  static_assert(sizeof(AdamNetDev) % 4 == 0, "word copy");
-  const uint32_t* src = reinterpret_cast<const uint32_t*>(nets + s);
-  uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
-  for (int i = threadIdx.x; i < (int)(sizeof(AdamNetDev) / 4); i += blockDim.x) dst[i] = src[i];
   __syncthreads();
-  adam_shadow_body(sa, lb, nb);
+  bf16* __restrict__ Wt = L.Wt;
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    const int cc = e / 32, rr = e % 32;
+    const int o = u.r0 + rr, c = u.c0 + cc;
+    if (o < L.out && c < L.in) Wt[(size_t)c * L.ldt + o] = tile[cc][rr];
+  }
 }
 
 }  // namespace
@@ -802,9 +910,8 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __re
 const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int count, cudaStream_t st) {
   if (count <= 0) return nullptr;
   std::vector<AdamNetDev> devs(count);
-  std::vector<int> begin(count + 1, 0);
+  std::vector<AdamUnit> units;
   long long ntot = 0;
-  for (int k = 0; k < count; ++k) ntot += nets[k].n;
   for (int k = 0; k < count; ++k) {
     AdamNetDev& a = devs[k];
     memset(&a, 0, sizeof(a));
@@ -819,22 +926,28 @@ const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int 
     a.b1 = s.b1;
     a.b2 = s.b2;
     a.eps = s.eps;
+    a.log_b1 = (float)std::log((double)s.b1);
+    a.log_b2 = (float)std::log((double)s.b2);
     a.nl = s.net->layers + 1;
+    ntot += s.n;
     for (int l = 0; l <= s.net->layers; ++l) {
       const BfLayer& L = s.net->L[l];
       a.L[l] = ShadowLayer{L.oW, L.out, L.in, l == 0 ? 2 : 1, L.kp, L.out_pad, L.W, L.Wt};
+      for (int r0 = 0; r0 < L.out; r0 += 32)
+        for (int c0 = 0; c0 < L.in; c0 += 32) units.push_back(AdamUnit{k, l, r0, c0});
+      // the layer's vectors (bias, LayerNorm gain and shift) and padding up to the next tensor
+      const long long v0 = L.oW + (long long)round_up((int64_t)L.out * L.in, 64);
+      const long long v1 = (l < s.net->layers) ? s.net->L[l + 1].oW : s.n;
+      for (long long o = v0; o < v1; o += 1024) units.push_back(AdamUnit{k, -1, (int)o, (int)std::min<long long>(1024, v1 - o)});
     }
-    // about 8 blocks per SM in total, shared in proportion to the parameter counts
-    const long long share = (long long)(152 * 8) * s.n / std::max<long long>(ntot, 1) + 1;
-    begin[k + 1] = begin[k] + (int)std::max<long long>(1, std::min<long long>((s.n + 255) / 256, share));
   }
   const char* err = nullptr;
   const AdamNetDev* dt = cache.get(devs, st, &err);
   if (!dt) return err;
-  const int* db = cache.get(begin, st, &err);
-  if (!db) return err;
+  const AdamUnit* du = cache.get(units, st, &err);
+  if (!du) return err;
   TraceLaunch tr(CRL_TRACE_ADAM, st, 28.0 * ntot);
-  launch_k(adam_shadow_kernel, dim3(begin[count]), dim3(256), 0, st, dt, db, count);
+  launch_k(adam_shadow_kernel, dim3((unsigned)units.size()), dim3(256), 0, st, dt, du);
   return nullptr;
 }
 

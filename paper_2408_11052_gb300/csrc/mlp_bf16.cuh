@@ -75,6 +75,8 @@ struct BfNet {
   __nv_bfloat16* dz[CRL_MAX_LAYERS + 1] = {};
   __nv_bfloat16* dzT[CRL_MAX_LAYERS + 1] = {};
   float* du = nullptr;                     // LayerNorm backward input [Mmax][H]
+  float* ln_partial = nullptr;             // LayerNorm gain / shift gradient partials [Mmax/16][2][H]
+  unsigned* ln_ticket = nullptr;           // their last-block ticket (zero between launches)
   // tensor maps, built for the batch size M of the last call
   int tm_M = -1;
   CUtensorMap tm_x0A, tm_x0TB;
@@ -99,17 +101,13 @@ class GemmGroups {
                                const char** err);
   // Frees every table (synchronises the device) and forgets the tuned tile widths.
   void reset();
-  // Autotuned tile width of a problem list (keyed by its untiled content), 0 if none.
+  // Autotuned configuration (16 x tile width + ring depth) of a problem list,
+  // keyed by its untiled content; 0 if none.
   int tuned_bn(uint64_t key) const {
     auto it = tuned_.find(key);
     return it == tuned_.end() ? 0 : it->second;
   }
-  void set_tuned_bn(uint64_t key, int bn) { tuned_[key] = bn; }
-  // Tile widths chosen so far: counts of 64, 128 and 256.
-  void tuned_counts(int* c64, int* c128, int* c256) const {
-    *c64 = *c128 = *c256 = 0;
-    for (const auto& kv : tuned_) (kv.second == 256 ? *c256 : kv.second == 128 ? *c128 : *c64) += 1;
-  }
+  void set_tuned_bn(uint64_t key, int cfg) { tuned_[key] = cfg; }
 
  private:
   std::unordered_map<uint64_t, int> tuned_;
@@ -139,6 +137,16 @@ void bf_net_pack_input(BfNet& n, const float* x0, const float* x1, int M, cudaSt
 // Store an FP32 gradient dy [M][out] into dz[layers] / dzT[layers] (BF16, both layouts).
 void bf_net_load_dy(BfNet& n, const float* dy, int M, cudaStream_t st);
 
+// The fused energy's BF16 operand written by an encoder's output layer (see
+// kEpiFwdOutEnergy): x [M][out], x^T [out][ldt], aux [M].
+struct EnergyOut {
+  __nv_bfloat16* X;
+  __nv_bfloat16* XT;
+  int ldt;
+  float* aux;
+  int energy;
+};
+
 // One network of a grouped pass.  All networks of a group have the same
 // number of layers and the same hidden width and LayerNorm setting.
 struct BfPass {
@@ -147,6 +155,7 @@ struct BfPass {
   float* grads;   // backward: FP32 gradients in the flat layout, or null (no weight gradients)
   float* dx1;     // backward: FP32 gradient of input columns [in0, in0 + in1) as [M][in1], or null
   int M;          // batch rows of this network (its tensor maps built for M)
+  const EnergyOut* energy_out = nullptr;   // forward: also write the fused energy's operand
 };
 // Forward of `count` networks (one grouped launch per layer): y [M][out] FP32 in net->y.
 const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st);

@@ -113,7 +113,14 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
   }
   // ---- critic: phi, psi and pi forward (pi's parameters do not change before the actor step)
   std::vector<BfPass> fwd, bwd;
-  for (crl_ctx* c : sw->agents) {
+  std::vector<EnergyOut> eo(2 * na);
+  for (int i = 0; i < na; ++i) {
+    crl_ctx* c = sw->agents[i];
+    eo[2 * i] = EnergyOut{c->etc.X, c->etc.XT, c->etc.ldt, c->etc.auxX, c->cfg.energy};
+    eo[2 * i + 1] = EnergyOut{c->etc.Y, c->etc.YT, c->etc.ldt, c->etc.auxY, c->cfg.energy};
+  }
+  for (int i = 0; i < na; ++i) {
+    crl_ctx* c = sw->agents[i];
     const int B = c->cfg.B;
     for (int net = 0; net < 3; ++net) {
       bf_maps(c, net, B);
@@ -121,11 +128,13 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     }
     const crl_net_ptrs* np = c->nets;
     fwd.push_back({&c->bf[CRL_NET_PHI], static_cast<const float*>(np[CRL_NET_PHI].params),
-                   static_cast<float*>(np[CRL_NET_PHI].grads), nullptr, B});
+                   static_cast<float*>(np[CRL_NET_PHI].grads), nullptr, B, &eo[2 * i]});
     fwd.push_back({&c->bf[CRL_NET_PSI], static_cast<const float*>(np[CRL_NET_PSI].params),
-                   static_cast<float*>(np[CRL_NET_PSI].grads), nullptr, B});
+                   static_cast<float*>(np[CRL_NET_PSI].grads), nullptr, B, &eo[2 * i + 1]});
     bwd.push_back(fwd[fwd.size() - 2]);
     bwd.push_back(fwd.back());
+    bwd[bwd.size() - 2].energy_out = nullptr;
+    bwd.back().energy_out = nullptr;
     fwd.push_back({&c->bf[CRL_NET_PI], static_cast<const float*>(np[CRL_NET_PI].params), nullptr, nullptr, B});
   }
   sweep_check(bf_forward(sw->groups, fwd.data(), (int)fwd.size(), status, st));
@@ -141,7 +150,8 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
                              &c->ctr->t_critic, P.dz[P.layers], P.dzT[P.layers], Q.dz[Q.layers], Q.dzT[Q.layers],
                              P.Mmax, &c->ctr->status});
   }
-  for (int stage = 0; stage < 3; ++stage) sweep_check(energy_tc_multi(sw->tables, ea, stage, st));
+  // (the operands were written by the encoders' output layers: no prepare stage)
+  for (int stage = 1; stage < 3; ++stage) sweep_check(energy_tc_multi(sw->tables, ea, stage, st));
   sweep_check(bf_backward(sw->groups, bwd.data(), (int)bwd.size(), status, st));
   {
     std::vector<AdamShadowNet> an;

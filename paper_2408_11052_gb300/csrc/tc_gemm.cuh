@@ -9,10 +9,10 @@
 // sizes, epilogue descriptor) lives in device memory and is never written
 // while kernels run.
 //
-// One CTA computes one 128 x BN tile (BN in {64, 128}); 128 threads:
+// One CTA computes one 128 x BN tile (BN in {64, 128, 256}); 128 threads:
 //   warp 0 / lane 0 -- TMA producer: 64-wide K slices of A and B (as 64-row
 //                      boxes: every tensor map has box {64, 64}) into a
-//                      4-stage shared-memory ring (128-byte swizzle);
+//                      STAGES-deep shared-memory ring (128-byte swizzle);
 //   warp 1 / lane 0 -- MMA issuer: 4 x tcgen05.mma (K = 16 each) per slice
 //                      into the FP32 accumulator in TMEM (128 lanes x BN cols);
 //   all 4 warps     -- epilogue: warp w reads TMEM lanes 32w..32w+31 (rows)
@@ -33,7 +33,6 @@ namespace tc {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kStages = 4;
 
 // What the FP32 accumulator tile of a problem becomes.
 enum EpiKind : int {
@@ -45,14 +44,20 @@ enum EpiKind : int {
   kEpiBwdDW = 5,      // dW [M][kin] (columns < kin), db [M] (column kin: the ones row)
   kEpiBwdDW0 = 6,     // split first layer: dW[m][c] = acc[2c] + acc[2c+1], db[m] = acc[2 kin]
   kEpiDX0 = 7,        // dx [M][nc] = acc columns [c0, c0 + nc)
+  kEpiFwdOutEnergy = 8,  // output layer feeding the fused energy: y = acc + b FP32 [M][ld0], the BF16
+                         // energy operand x = y * s [M][N] (out1) and x^T [N][ld1] (out2), aux [M];
+                         // s = 1 / |y| and aux = s for the cosine energy, else s = 1 and aux = |bf16(y)|^2.
+                         // The tile must span the whole row (the launch picks BN >= N).
 };
 
 struct EpiDesc {
-  int kind, ld0, ld1, kin, c0, nc, ldm, pad;
+  int kind, ld0, ld1, kin, c0, nc, ldm, energy;
   const float* bias;
   const __nv_bfloat16* mask;  // [M][ldm], BF16 post-ReLU activation (> 0 where the unit is active)
   void* out0;
   void* out1;
+  void* out2;
+  float* aux;
 };
 
 struct alignas(64) GemmProblem {
@@ -62,15 +67,20 @@ struct alignas(64) GemmProblem {
   EpiDesc epi;
 };
 
-template <int BN>
+// Ring depth STAGES: deep rings keep a whole 512-deep product in flight at
+// once (latency-bound small problems); shallow ones leave room for two CTAs
+// per SM, one's epilogue overlapping the other's main loop (large problems).
+template <int BN, int STAGES>
 struct GemmSmem {
   static constexpr uint32_t kABytes = kBM * kBK * 2;   // 16 KiB
   static constexpr uint32_t kBBytes = BN * kBK * 2;    // BN * 128 B
   static constexpr uint32_t kStageBytes = kABytes + kBBytes;
+  static constexpr int kStages = STAGES;
   // operand ring + barriers (full[S], empty[S], done) + TMEM slot, plus 1 KiB for alignment
   static constexpr uint32_t kBytes = kStages * kStageBytes + 1024 + 256;
   static constexpr uint32_t kTmemCols = BN;
   static_assert(BN % 64 == 0 && BN <= 256, "BN must be 64, 128 or 256");
+  static_assert(kBytes <= 227 * 1024, "shared memory per CTA");
 };
 
 // 32 BF16 values -> four 16-byte stores (dst 16-byte aligned)
@@ -235,19 +245,61 @@ __device__ __forceinline__ void epilogue_chunk(const EpiDesc& e, int row, int co
   }
 }
 
+// The output layer feeding the fused energy (kEpiFwdOutEnergy): two passes over
+// this thread's row in TMEM (the tile holds all N columns): FP32 output and the
+// squared norm, then the scaled BF16 operand, row-major and transposed.
+__device__ __forceinline__ void epilogue_energy(const EpiDesc& e, int row, uint32_t lane_base, int N, int M) {
+  using bf16 = __nv_bfloat16;
+  const bool live = row < M;
+  const bool cosine = e.energy == CRL_ENERGY_COS;
+  float q = 0.f;
+#pragma unroll 1
+  for (int c = 0; c < N; c += 32) {
+    float v[32];
+    tmem_ld32(lane_base + c, v);   // warp-collective: every lane, live or not
+    if (!live) continue;
+    float b[32];
+    load_bias32(e.bias + c, b);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      v[i] += b[i];
+      const float r = cosine ? v[i] : __bfloat162float(__float2bfloat16_rn(v[i]));
+      q += r * r;
+    }
+    store_f32x32(static_cast<float*>(e.out0) + (size_t)row * e.ld0 + c, v);
+  }
+  const float scale = cosine ? rsqrtf(q) : 1.f;
+  if (live) e.aux[row] = cosine ? scale : q;
+  bf16* X = static_cast<bf16*>(e.out1);
+  bf16* XT = static_cast<bf16*>(e.out2);
+#pragma unroll 1
+  for (int c = 0; c < N; c += 32) {
+    float v[32];
+    tmem_ld32(lane_base + c, v);
+    if (!live) continue;
+    float b[32];
+    load_bias32(e.bias + c, b);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = (v[i] + b[i]) * scale;
+    store_bf16x32(X + (size_t)row * N + c, v);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) XT[(size_t)(c + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
+  }
+}
+
 // nkA > 0: A has only nkA K-slices and slice kb of B multiplies slice kb % nkA of
 // A -- B holds [W_hi | W_lo] along K and each A tile is used against both halves.
-template <int BN>
+template <int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const GemmProblem* __restrict__ probs, int nprob, unsigned* status) {
-  using S = GemmSmem<BN>;
+  using S = GemmSmem<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
   uint8_t* sA = smem;
-  uint8_t* sB = smem + kStages * S::kABytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * S::kStageBytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* done = empty + kStages;
+  uint8_t* sB = smem + S::kStages * S::kABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::kStages * S::kStageBytes);
+  uint64_t* empty = full + S::kStages;
+  uint64_t* done = empty + S::kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
   // problem of this CTA: the last p with tile_begin <= blockIdx.x (the table is immutable)
@@ -273,7 +325,7 @@ __global__ void __launch_bounds__(128, 1)
     tmap_acquire(tmB);
     prefetch_tmap(tmA);
     prefetch_tmap(tmB);
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < S::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -295,8 +347,8 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0 && lane == 0) {
     // TMA producer
     for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) & 1) ^ 1)) {
+      const int s = kb % S::kStages;
+      if (kb >= S::kStages && !mbar_wait(&empty[s], ((kb / S::kStages) & 1) ^ 1)) {
         atomicOr(status, CRL_STATUS_TIMEOUT);
         break;
       }
@@ -316,8 +368,8 @@ __global__ void __launch_bounds__(128, 1)
     constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
     bool ok = true;
     for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      if (!mbar_wait(&full[s], (kb / kStages) & 1)) {
+      const int s = kb % S::kStages;
+      if (!mbar_wait(&full[s], (kb / S::kStages) & 1)) {
         atomicOr(status, CRL_STATUS_TIMEOUT);
         ok = false;
         break;
@@ -344,11 +396,15 @@ __global__ void __launch_bounds__(128, 1)
     const int row = m0 + warp * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     const int ncol = (N - n0 < BN) ? N - n0 : BN;
+    if (e.kind == kEpiFwdOutEnergy) {
+      epilogue_energy(e, row, lane_base, ncol, M);
+    } else {
 #pragma unroll 1
-    for (int c = 0; c < ncol; c += 32) {
-      float v[32];
-      tmem_ld32(lane_base + c, v);
-      epilogue_chunk(e, row, n0 + c, v, M, N);
+      for (int c = 0; c < ncol; c += 32) {
+        float v[32];
+        tmem_ld32(lane_base + c, v);
+        epilogue_chunk(e, row, n0 + c, v, M, N);
+      }
     }
   } else if (threadIdx.x == 0) {
     atomicOr(status, CRL_STATUS_TIMEOUT);
