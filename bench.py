@@ -482,6 +482,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the FP32 plain arm")
     ap.add_argument("--no-relabel", action="store_true", help="skip the standalone relabel throughput")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed GEMM tile rule (deterministic launch sequence for profiler captures)")
     ap.add_argument("--only-relabel", action="store_true",
                     help="run only the standalone relabel throughput (a short command for ncu captures)")
     args = ap.parse_args()
@@ -493,6 +495,9 @@ def main():
 
     import torch
 
+    if args.no_autotune:
+        from paper_2408_11052_gb300 import api as _api
+        _api.set_autotune(False)
     rank, world, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local if world > 1 else 0)
     # one non-default stream for everything: the library replays the update step

@@ -442,7 +442,8 @@ RelabelArgs relabel_args(crl_ctx* c, uint64_t step, int B, float* s, float* a, f
   CRL_REQUIRE((int64_t)B * cf.D < ((int64_t)1 << 31) && (int64_t)B * 3 < ((int64_t)1 << 31), CRL_E_SHAPE,
               "B x D must stay below 2^31");
   CRL_REQUIRE(c->size_host > 0, CRL_E_BUFFER_EMPTY, "the replay buffer is empty");
-  RelabelArgs ra{};
+  RelabelArgs ra;
+  std::memset(&ra, 0, sizeof(ra));   // zero padding: these arguments also key device tables
   ra.seed = cf.seed;
   ra.agent = cf.agent;
   ra.step = step;

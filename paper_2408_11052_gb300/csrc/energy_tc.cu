@@ -144,7 +144,8 @@ struct FwdArgs {
   float* c_out;
   float* loss4;
   int* t_bump;
-  unsigned* ticket;  // zero between launches
+  unsigned* tickets;  // [2 n + 1]: per row tile, per column tile, final (zero between launches)
+  float* tile_part;   // [2][n][2]: per row / column tile (sum of (lse - diag), sum of lse^2)
 };
 
 __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2) {
@@ -159,49 +160,65 @@ __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2
   m = M;
 }
 
-// Merge the partials into r, c and the loss parts (one block of any size).
-__device__ void finalize_block(const FwdArgs& a, int nI, int nJ) {
-  __shared__ float sm[32];
+// Merge the nJ partials of the 128 rows (col = false) or columns (col = true)
+// of tile T into the logsumexps and this tile's loss partials.  One block.
+__device__ void merge_tile(const FwdArgs& a, int T, int n, bool col) {
+  __shared__ float s_red[2][32];
   const int B = a.B;
-  float af = 0.f, ab = 0.f, ar2 = 0.f, ac2 = 0.f;
-  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+  const float* part = col ? a.colpart : a.rowpart;
+  float sd = 0.f, s2 = 0.f;
+  for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
+    const int i = T * kTile + k;
+    if (i >= B) continue;
     float m = -INFINITY, s = 0.f;
-    for (int J = 0; J < nJ; ++J) {
-      const float* p = a.rowpart + ((size_t)J * B + i) * 2;
+    for (int P = 0; P < n; ++P) {
+      const float* p = part + ((size_t)P * B + i) * 2;
       lse_merge(m, s, __ldcg(p), __ldcg(p + 1));
     }
-    const float r = m + __logf(s);
-    m = -INFINITY;
-    s = 0.f;
-    for (int I = 0; I < nI; ++I) {
-      const float* p = a.colpart + ((size_t)I * B + i) * 2;
-      lse_merge(m, s, __ldcg(p), __ldcg(p + 1));
-    }
-    const float c = m + __logf(s);
-    const float d = __ldcg(a.diag + i);
-    a.r_out[i] = r;
-    a.c_out[i] = c;
-    af += r - d;
-    ab += c - d;
-    ar2 += r * r;
-    ac2 += c * c;
+    const float l = m + __logf(s);
+    (col ? a.c_out : a.r_out)[i] = l;
+    sd += l - __ldcg(a.diag + i);
+    s2 += l * l;
   }
-  af = block_sum(af, sm);
-  ab = block_sum(ab, sm);
-  ar2 = block_sum(ar2, sm);
-  ac2 = block_sum(ac2, sm);
+  sd = warp_sum(sd);
+  s2 = warp_sum(s2);
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  if (lane == 0) {
+    s_red[0][w] = sd;
+    s_red[1][w] = s2;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const float inv = 1.f / B;
-    const float lf = af * inv, lb = ab * inv;
-    const float pen = a.beta * (a.w.pr * ar2 * inv + a.w.pc * ac2 * inv);
-    const float total = a.w.wf * lf + a.w.wb * lb + pen;
-    a.loss4[0] = total;
-    a.loss4[1] = lf;
-    a.loss4[2] = lb;
-    a.loss4[3] = pen;
-    if (a.status && !isfinite(total)) atomicOr(a.status, CRL_STATUS_NONFINITE);
-    if (a.t_bump) *a.t_bump += 1;
+    float a0 = 0.f, a1 = 0.f;
+    for (int k = 0; k < (int)(blockDim.x / 32); ++k) {
+      a0 += s_red[0][k];
+      a1 += s_red[1][k];
+    }
+    float* tp = a.tile_part + ((size_t)(col ? 1 : 0) * n + T) * 2;
+    tp[0] = a0;
+    tp[1] = a1;
   }
+}
+
+// The loss parts from the 2 n tile partials, added in tile order.  One thread.
+__device__ void finalize_loss(const FwdArgs& a, int n) {
+  float af = 0.f, ar2 = 0.f, ab = 0.f, ac2 = 0.f;
+  for (int T = 0; T < n; ++T) {
+    af += __ldcg(a.tile_part + 2 * T);
+    ar2 += __ldcg(a.tile_part + 2 * T + 1);
+    ab += __ldcg(a.tile_part + 2 * (n + T));
+    ac2 += __ldcg(a.tile_part + 2 * (n + T) + 1);
+  }
+  const float inv = 1.f / a.B;
+  const float lf = af * inv, lb = ab * inv;
+  const float pen = a.beta * (a.w.pr * ar2 * inv + a.w.pc * ac2 * inv);
+  const float total = a.w.wf * lf + a.w.wb * lb + pen;
+  a.loss4[0] = total;
+  a.loss4[1] = lf;
+  a.loss4[2] = lb;
+  a.loss4[3] = pen;
+  if (a.status && !isfinite(total)) atomicOr(a.status, CRL_STATUS_NONFINITE);
+  if (a.t_bump) *a.t_bump += 1;
 }
 
 // One 128 x 128 tile (row tile I, column tile J) of an n x n tile grid.
@@ -342,16 +359,35 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
-  // the last CTA to finish merges every CTA's partials (no CTA waits for another)
-  __shared__ int s_last;
+  // Finalize without any CTA waiting for another: the last CTA of row tile I
+  // merges its rows' partials, the last of column tile J its columns', and the
+  // CTA completing the last of the 2 n merges adds the tiles' loss partials.
+  __shared__ int s_row, s_col, s_fin;
   __threadfence();
   __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(a.ticket, 1u) == (unsigned)(n * n) - 1u) ? 1 : 0;
+  if (tid == 0) {
+    s_row = (atomicAdd(a.tickets + I, 1u) == (unsigned)n - 1u) ? 1 : 0;
+    s_col = (atomicAdd(a.tickets + n + J, 1u) == (unsigned)n - 1u) ? 1 : 0;
+  }
   __syncthreads();
-  if (s_last) {
+  if (!s_row && !s_col) return;
+  __threadfence();
+  if (s_row) merge_tile(a, I, n, false);
+  __syncthreads();
+  if (s_col) merge_tile(a, J, n, true);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    if (s_row) a.tickets[I] = 0u;
+    if (s_col) a.tickets[n + J] = 0u;
+    const unsigned add = (unsigned)(s_row + s_col);
+    s_fin = (atomicAdd(a.tickets + 2 * n, add) + add == (unsigned)(2 * n)) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_fin && tid == 0) {
     __threadfence();
-    finalize_block(a, n, n);
-    if (tid == 0) *a.ticket = 0u;
+    finalize_loss(a, n);
+    a.tickets[2 * n] = 0u;
   }
 }
 
@@ -389,6 +425,70 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int chunk) {
 // rows 32 (w % 4) .., columns 32 (w / 4) ..), and the MMA adds H other into
 // the TMEM accumulator.
 // CTAs [0, nrow) run the row pass (own = phi), CTAs [nrow, 2 nrow) the column pass (own = psi).
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Per-row constants of the coefficient tile (own side = this thread's row).
+struct HCoef {
+  float a_own;    // own auxiliary (|x|^2 for the L2 energies)
+  float l_own2;   // own logsumexp x log2(e)
+  float k_own;    // scale (w_own + 2 beta p_own l_own)
+  float k_diag;   // scale (w_f + w_b): the positive pair's -1 terms
+  float inv_tau;
+  float k1;       // log2(e) / tau
+};
+
+// dL/dF x (chain factor of the energy) for this thread's 32 columns 32 q ..:
+// with P_own = e^(F - l_own) and P_oth = e^(F - l_oth),
+//   g = P_own k_own + P_oth k_oth - [u == v] k_diag,
+// which is scale (w_f (P - d) + w_b (Q - d) + 2 beta (p_r r P + p_c c Q)) with
+// P = e^(F - r), Q = e^(F - c) whichever side is own.  EK 0: L2 (F = -d / tau,
+// factor 1 / (tau d), zero where d < 1e-12), 1: L2^2 (F = -d^2 / tau, factor
+// 2 / tau), 2: dot / cos (F = s / tau, factor 1 / tau).  The BF16-rounded
+// coefficients are packed in pairs and summed into rowsum.
+template <int EK>
+__device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, const float* s_aux,
+                                        const float* s_lse2, const float* s_koth, int q, int u, int v0, int B,
+                                        float& rowsum, uint32_t (&packed)[16]) {
+#pragma unroll
+  for (int k = 0; k < 32; k += 2) {
+    float h2[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int cl = q * 32 + k + e;
+      const int v = v0 + cl;
+      const float sval = sv[k + e];
+      float f2, fac;
+      if (EK == 0) {
+        const float t = fmaxf(hc.a_own + s_aux[cl] - 2.f * sval, 0.f);
+        const float rs = t >= 1e-24f ? rsqrtf(t) : 0.f;
+        f2 = -(t * rs) * hc.k1;
+        fac = hc.inv_tau * rs;
+      } else if (EK == 1) {
+        const float t = fmaxf(hc.a_own + s_aux[cl] - 2.f * sval, 0.f);
+        f2 = -t * hc.k1;
+        fac = 2.f * hc.inv_tau;
+      } else {
+        f2 = sval * hc.k1;
+        fac = hc.inv_tau;
+      }
+      float g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - s_lse2[cl]) * s_koth[cl]);
+      if (u == v) g -= hc.k_diag;
+      h2[e] = (u < B && v < B) ? g * fac : 0.f;
+    }
+    const __nv_bfloat162 p2 = __floats2bfloat162_rn(h2[0], h2[1]);
+    // the row sum takes the BF16-rounded coefficients the MMA multiplies, so
+    // acc - rowsum * own stays a sum of H (other - own) terms
+    rowsum += __low2float(p2) + __high2float(p2);
+    packed[k / 2] = *reinterpret_cast<const uint32_t*>(&p2);
+  }
+}
+
 // lb in [0, 2 nrow): the row pass for lb < nrow, else the column pass.
 __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const CUtensorMap* tmXT,
                                          const CUtensorMap* tmYT, const BwdArgs& row, const BwdArgs& col, int nrow,
@@ -408,7 +508,9 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   float* s_lse = reinterpret_cast<float*>(Hs + 2 * 16384);  // [128] column logsumexp of the other side
   float* s_aux = s_lse + kTile;                             // [128]
   float* s_red = s_aux + kTile;                             // [4][128] partial sums
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_red + 4 * kTile);
+  float* s_lse2 = s_red + 4 * kTile;                        // [128] other side's logsumexp x log2(e)
+  float* s_koth = s_lse2 + kTile;                           // [128] other side's coefficient (see HCoef)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_koth + kTile);
   uint64_t* xload = bars;
   uint64_t* yload = bars + 1;
   uint64_t* ytload = bars + 2;
@@ -461,6 +563,17 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   const int u = u0 + r;
   const float a_own = (u < a.B) ? a.aux_own[u] : 0.f;
   const float l_own = (u < a.B) ? a.lse_own[u] : 0.f;
+  // loss weights of this side (row pass: forward direction and row penalty;
+  // column pass: backward direction and column penalty) and of the other
+  const float w_own = a.transposed ? a.w.wb : a.w.wf, p_own = a.transposed ? a.w.pc : a.w.pr;
+  const float w_oth = a.transposed ? a.w.wf : a.w.wb, p_oth = a.transposed ? a.w.pr : a.w.pc;
+  HCoef hc;
+  hc.a_own = a_own;
+  hc.l_own2 = l_own * kLog2e;
+  hc.k_own = a.scale * (w_own + 2.f * a.beta * p_own * l_own);
+  hc.k_diag = a.scale * (a.w.wf + a.w.wb);
+  hc.inv_tau = a.inv_tau;
+  hc.k1 = a.inv_tau * kLog2e;
   float rowsum = 0.f;
   bool ok = true;
   for (int vt = 0; vt < nV && ok; ++vt) {
@@ -471,8 +584,11 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     if (!ok) break;
     if (tid < kTile) {
       const int v = v0 + tid;
-      s_lse[tid] = (v < a.B) ? a.lse_other[v] : 0.f;
+      const float lo = (v < a.B) ? a.lse_other[v] : 0.f;
+      s_lse[tid] = lo;
       s_aux[tid] = (v < a.B) ? a.aux_other[v] : 0.f;
+      s_lse2[tid] = lo * kLog2e;
+      s_koth[tid] = a.scale * (w_oth + 2.f * a.beta * p_oth * lo);
     }
     if (tid == 0) {
       tc::mbar_arrive_expect_tx(yload, (uint32_t)(nk * 16384));
@@ -513,39 +629,10 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
       float sv[32];
       tc::tmem_ld32(tS + lane_off + q * 32, sv);
       uint32_t packed[16];
-#pragma unroll
-      for (int k = 0; k < 32; k += 2) {
-        float h2[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int cl = q * 32 + k + e;
-          const int v = v0 + cl;
-          float h = 0.f;
-          if (u < a.B && v < a.B) {
-            const float ao = s_aux[cl];
-            const float f = energy_of(a.energy, sv[k + e], a_own, ao, a.inv_tau);
-            const float lr = a.transposed ? s_lse[cl] : l_own;   // row logsumexp r_i
-            const float lc = a.transposed ? l_own : s_lse[cl];   // column logsumexp c_j
-            const float P = __expf(f - lr), Q = __expf(f - lc);
-            const float dl = (u == v) ? 1.f : 0.f;
-            float g = a.w.wf * (P - dl) + a.w.wb * (Q - dl) + 2.f * a.beta * (a.w.pr * lr * P + a.w.pc * lc * Q);
-            g *= a.scale;
-            if (a.energy == CRL_ENERGY_L2) {
-              const float d = sqrtf(fmaxf(a_own + ao - 2.f * sv[k + e], 0.f));
-              h = (d >= 1e-12f) ? g * a.inv_tau / d : 0.f;
-            } else if (a.energy == CRL_ENERGY_L2SQ) {
-              h = 2.f * g * a.inv_tau;
-            } else {
-              h = g * a.inv_tau;
-            }
-          }
-          h2[e] = h;
-        }
-        const __nv_bfloat162 p2 = __floats2bfloat162_rn(h2[0], h2[1]);
-        // the row sum takes the BF16-rounded coefficients the MMA multiplies, so
-        // acc - rowsum * own stays a sum of H (other - own) terms
-        rowsum += __low2float(p2) + __high2float(p2);
-        packed[k / 2] = *reinterpret_cast<const uint32_t*>(&p2);
+      switch (a.energy) {
+        case CRL_ENERGY_L2: build_h<0>(sv, hc, s_aux, s_lse2, s_koth, q, u, v0, a.B, rowsum, packed); break;
+        case CRL_ENERGY_L2SQ: build_h<1>(sv, hc, s_aux, s_lse2, s_koth, q, u, v0, a.B, rowsum, packed); break;
+        default: build_h<2>(sv, hc, s_aux, s_lse2, s_koth, q, u, v0, a.B, rowsum, packed); break;
       }
       // columns 32 q .. +31 = K-block q / 2, 16-byte chunks (q % 2) * 4 .. +3
       uint8_t* hb = Hs + (q / 2) * 16384;
@@ -676,7 +763,65 @@ size_t fwd_smem(int R) {
 }
 size_t bwd_smem(int R) {
   const size_t ybytes = std::max<size_t>((size_t)(R / 64) * 16384, (size_t)2 * R * 128);
-  return (size_t)(R / 64) * 16384 + ybytes + 2 * 16384 + (2 + 4) * kTile * 4 + 1024 + 64;
+  return (size_t)(R / 64) * 16384 + ybytes + 2 * 16384 + (2 + 4 + 2) * kTile * 4 + 1024 + 64;
+}
+
+FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* loss4, float* r, float* c,
+                 int* t_bump, unsigned* status) {
+  const int n = (B + kTile - 1) / kTile;
+  char* base = static_cast<char*>(ws);
+  unsigned* tickets = reinterpret_cast<unsigned*>(base);
+  float* tile_part = reinterpret_cast<float*>(base + round_up((2 * n + 1) * 4, 256));
+  float* rowpart = reinterpret_cast<float*>(base + round_up((2 * n + 1) * 4, 256) + round_up(4 * n * 4, 256));
+  float* colpart = rowpart + (size_t)2 * n * B;
+  float* diag = colpart + (size_t)2 * n * B;
+  // member by member into zeroed storage: the arguments also key device tables
+  FwdArgs f;
+  memset(&f, 0, sizeof(f));
+  f.B = B;
+  f.R = e.R;
+  f.energy = ls.energy;
+  f.inv_tau = (float)(1.0 / ls.tau);
+  f.auxX = e.auxX;
+  f.auxY = e.auxY;
+  f.rowpart = rowpart;
+  f.colpart = colpart;
+  f.diag = diag;
+  f.status = status;
+  f.w = loss_weights(ls);
+  f.beta = (float)ls.beta;
+  f.r_out = r;
+  f.c_out = c;
+  f.loss4 = loss4;
+  f.t_bump = t_bump;
+  f.tickets = tickets;
+  f.tile_part = tile_part;
+  return f;
+}
+
+// Backward arguments of the row pass (own = phi), member by member into zeroed storage.
+BwdArgs bwd_args(const EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* r, const float* c,
+                 double dtotal, bf16* dphi, bf16* dphiT, int ldt, unsigned* status) {
+  BwdArgs a;
+  memset(&a, 0, sizeof(a));
+  a.B = B;
+  a.R = e.R;
+  a.energy = ls.energy;
+  a.transposed = 0;
+  a.inv_tau = (float)(1.0 / ls.tau);
+  a.beta = (float)ls.beta;
+  a.scale = (float)(dtotal / B);
+  a.w = loss_weights(ls);
+  a.aux_own = e.auxX;
+  a.aux_other = e.auxY;
+  a.lse_own = r;
+  a.lse_other = c;
+  a.own_f32 = phi;
+  a.d_out = dphi;
+  a.d_outT = dphiT;
+  a.ldt = ldt;
+  a.status = status;
+  return a;
 }
 
 const char* mk(CUtensorMap* m, const void* base, int inner, int rows, int stride) {
@@ -687,12 +832,13 @@ const char* mk(CUtensorMap* m, const void* base, int inner, int rows, int stride
 
 }  // namespace
 
-// The finalize ticket (first 256 bytes; zeroed when the workspace is created,
-// reset by each launch's last CTA), then rowpart [nJ][B][2], colpart
-// [nI][B][2] and diag [B].
+// Workspace of the forward: tickets [2 n + 1] (zeroed when the workspace is
+// created, reset by the CTAs that use them), tile loss partials [2][n][2],
+// rowpart [nJ][B][2], colpart [nI][B][2], diag [B].
 size_t energy_tc_ws_bytes(int B) {
   const int n = (B + kTile - 1) / kTile;
-  return ((size_t)2 * n * B * 2 + B) * sizeof(float) + 256;
+  return (size_t)round_up((2 * n + 1) * 4, 256) + (size_t)round_up(4 * n * 4, 256) +
+         ((size_t)2 * n * B * 2 + B) * sizeof(float);
 }
 
 bool energy_tc_supported(const LossSpec& ls, int B, int R, const char** why) {
@@ -731,12 +877,7 @@ void energy_tc_prepare(EnergyTc& e, const LossSpec& ls, const float* phi, const 
 void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, float* r, float* c, void* ws,
                        unsigned* status, int* t_bump, cudaStream_t st) {
   const int n = (B + kTile - 1) / kTile;
-  unsigned* ticket = static_cast<unsigned*>(ws);
-  float* rowpart = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
-  float* colpart = rowpart + (size_t)2 * n * B;
-  float* diag = colpart + (size_t)2 * n * B;
-  FwdArgs a{B,     e.R,  ls.energy, (float)(1.0 / ls.tau), e.auxX, e.auxY, rowpart, colpart, diag, status,
-            loss_weights(ls), (float)ls.beta, r, c, loss4, t_bump, ticket};
+  FwdArgs a = fwd_args(e, ls, B, ws, loss4, r, c, t_bump, status);
   const size_t sm = fwd_smem(e.R);
   static bool attr = false;
   if (!attr) {
@@ -757,8 +898,7 @@ void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi
     attr = true;
   }
   const size_t sm = bwd_smem(e.R);
-  BwdArgs a{B, e.R, ls.energy, 0, (float)(1.0 / ls.tau), (float)ls.beta, (float)(dtotal / B), loss_weights(ls),
-            e.auxX, e.auxY, r, c, phi, dphi, dphiT, ldt, status};
+  const BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, dphi, dphiT, ldt, status);
   BwdArgs b = a;
   b.transposed = 1;
   b.aux_own = e.auxY;
@@ -795,15 +935,8 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     t.n = (g.B + kTile - 1) / kTile;
     t.s0 = PrepSide{g.phi, e.X, e.XT, e.auxX};
     t.s1 = PrepSide{g.psi, e.Y, e.YT, e.auxY};
-    unsigned* ticket = static_cast<unsigned*>(g.ws);
-    float* rowpart = reinterpret_cast<float*>(static_cast<char*>(g.ws) + 256);
-    float* colpart = rowpart + (size_t)2 * t.n * g.B;
-    float* diag = colpart + (size_t)2 * t.n * g.B;
-    t.f = FwdArgs{g.B,     e.R,     g.ls.energy, (float)(1.0 / g.ls.tau), e.auxX, e.auxY, rowpart, colpart, diag,
-                  g.status, loss_weights(g.ls), (float)g.ls.beta, g.r, g.c, g.loss4, g.t_bump, ticket};
-    t.row = BwdArgs{g.B,    e.R,     g.ls.energy, 0,       (float)(1.0 / g.ls.tau), (float)g.ls.beta,
-                    (float)(1.0 / g.B), loss_weights(g.ls), e.auxX, e.auxY, g.r, g.c, g.phi, g.dphi, g.dphiT,
-                    g.ldt,  g.status};
+    t.f = fwd_args(e, g.ls, g.B, g.ws, g.loss4, g.r, g.c, g.t_bump, g.status);
+    t.row = bwd_args(e, g.ls, g.B, g.phi, g.r, g.c, 1.0, g.dphi, g.dphiT, g.ldt, g.status);
     t.col = t.row;
     t.col.transposed = 1;
     t.col.aux_own = e.auxY;

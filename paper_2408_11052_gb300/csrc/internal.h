@@ -24,6 +24,7 @@ struct BufferDev {
   int32_t* state;                   // [2] device copy of {size, total}
   const unsigned long long* gq;     // [T + 2] fixed-point discount table (see relabel)
   int E, T, D, A, W;
+  int pad_;                         // explicit (zero): no implicit padding (descriptors key device tables)
 };
 
 // Optional BF16 packing of a network input by the relabel kernel: the split

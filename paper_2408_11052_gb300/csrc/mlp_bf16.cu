@@ -932,7 +932,15 @@ const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int 
     ntot += s.n;
     for (int l = 0; l <= s.net->layers; ++l) {
       const BfLayer& L = s.net->L[l];
-      a.L[l] = ShadowLayer{L.oW, L.out, L.in, l == 0 ? 2 : 1, L.kp, L.out_pad, L.W, L.Wt};
+      ShadowLayer& sl = a.L[l];   // member by member: the zeroed padding keys the device table
+      sl.oW = L.oW;
+      sl.out = L.out;
+      sl.in = L.in;
+      sl.rep = l == 0 ? 2 : 1;
+      sl.kp = L.kp;
+      sl.ldt = L.out_pad;
+      sl.W2 = L.W;
+      sl.Wt = L.Wt;
       for (int r0 = 0; r0 < L.out; r0 += 32)
         for (int c0 = 0; c0 < L.in; c0 += 32) units.push_back(AdamUnit{k, l, r0, c0});
       // the layer's vectors (bias, LayerNorm gain and shift) and padding up to the next tensor

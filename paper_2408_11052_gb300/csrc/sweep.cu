@@ -168,9 +168,22 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     for (crl_ctx* c : sw->agents) {
       const crl_config& cf = c->cfg;
       BfNet& P = c->bf[CRL_NET_PHI];
-      hf.push_back(HeadFwdArgs<float>{cf.B, cf.A, c->bf[CRL_NET_PI].y, nullptr, &c->ctr->last_step, cf.seed, cf.agent,
-                                      static_cast<float*>(c->a_new), static_cast<float*>(c->logpi),
-                                      static_cast<float*>(c->eps_used), P.x0, bf_net_x0_ld(P), P.s.in0});
+      HeadFwdArgs<float> h;
+      memset(&h, 0, sizeof(h));   // member by member: zeroed padding keys the device table
+      h.B = cf.B;
+      h.A = cf.A;
+      h.out = c->bf[CRL_NET_PI].y;
+      h.eps = nullptr;
+      h.step_dev = &c->ctr->last_step;
+      h.seed = cf.seed;
+      h.agent = cf.agent;
+      h.a_new = static_cast<float*>(c->a_new);
+      h.logpi = static_cast<float*>(c->logpi);
+      h.eps_used = static_cast<float*>(c->eps_used);
+      h.x0 = P.x0;
+      h.x0_ld = bf_net_x0_ld(P);
+      h.x0_col = P.s.in0;
+      hf.push_back(h);
     }
     sweep_check(actor_head_forward_multi(sw->tables, hf, st));
   }
@@ -192,25 +205,28 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
       const crl_config& cf = c->cfg;
       BfNet& P = c->bf[CRL_NET_PHI];
       BfNet& Q = c->bf[CRL_NET_PSI];
-      al.push_back(ActorLossArgs<float>{cf.B,
-                                        cf.repr,
-                                        cf.energy,
-                                        (double)cf.temperature,
-                                        (double)cf.alpha,
-                                        P.y,
-                                        Q.y,
-                                        static_cast<const float*>(c->logpi),
-                                        static_cast<float*>(c->fdiag),
-                                        nullptr,
-                                        P.dz[P.layers],
-                                        P.L[P.layers].out_pad,
-                                        static_cast<float*>(c->actor_ws),
-                                        &c->ctr->ticket_actor,
-                                        static_cast<float*>(c->loss) + 4,
-                                        &c->ctr->status,
-                                        &c->ctr->t_actor,
-                                        &c->ctr->step,
-                                        &c->ctr->last_step});
+      ActorLossArgs<float> t;
+      memset(&t, 0, sizeof(t));
+      t.B = cf.B;
+      t.R = cf.repr;
+      t.energy = cf.energy;
+      t.tau = (double)cf.temperature;
+      t.alpha = (double)cf.alpha;
+      t.phi = P.y;
+      t.psi = Q.y;
+      t.logpi = static_cast<const float*>(c->logpi);
+      t.fdiag = static_cast<float*>(c->fdiag);
+      t.dphi = nullptr;
+      t.dz = P.dz[P.layers];
+      t.ldz = P.L[P.layers].out_pad;
+      t.partial = static_cast<float*>(c->actor_ws);
+      t.ticket = &c->ctr->ticket_actor;
+      t.loss2 = static_cast<float*>(c->loss) + 4;
+      t.status = &c->ctr->status;
+      t.t_bump = &c->ctr->t_actor;
+      t.step_bump = &c->ctr->step;
+      t.last_step = &c->ctr->last_step;
+      al.push_back(t);
     }
     sweep_check(actor_loss_multi(sw->tables, al, st));
   }
@@ -220,9 +236,20 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     for (crl_ctx* c : sw->agents) {
       const crl_config& cf = c->cfg;
       BfNet& PI = c->bf[CRL_NET_PI];
-      hb.push_back(HeadBwdArgs<float>{cf.B, cf.A, (double)cf.alpha, PI.y, static_cast<const float*>(c->eps_used),
-                                      static_cast<const float*>(c->da), nullptr, PI.dz[PI.layers],
-                                      PI.L[PI.layers].out_pad, PI.dzT[PI.layers], PI.Mmax});
+      HeadBwdArgs<float> h;
+      memset(&h, 0, sizeof(h));
+      h.B = cf.B;
+      h.A = cf.A;
+      h.alpha = (double)cf.alpha;
+      h.out = PI.y;
+      h.eps_used = static_cast<const float*>(c->eps_used);
+      h.da = static_cast<const float*>(c->da);
+      h.dout = nullptr;
+      h.dz = PI.dz[PI.layers];
+      h.ldz = PI.L[PI.layers].out_pad;
+      h.dzT = PI.dzT[PI.layers];
+      h.ldt = PI.Mmax;
+      hb.push_back(h);
     }
     sweep_check(actor_head_backward_multi(sw->tables, hb, st));
   }
