@@ -124,11 +124,13 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The maximum of x over all ranks (NCCL on the GPU, gloo on the host)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

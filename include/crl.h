@@ -86,6 +86,8 @@ extern "C" {
 /* kernel organisation */
 #define CRL_PATH_PLAIN 0  /* one kernel per op; the B x B energy matrix in HBM */
 #define CRL_PATH_FUSED 1  /* fused kernels; the B x B matrix is never written   */
+                          /* (BF16 only; repr 64 / 128 / 192 / 256, B a multiple
+                           * of 8; every energy but L1, which the plain path has) */
 /* networks */
 #define CRL_NET_PHI 0     /* phi(s, a): input concat(s, a), output repr        */
 #define CRL_NET_PSI 1     /* psi(g):    input g, output repr                   */

@@ -92,7 +92,6 @@ void validate_config(const crl_config& c) {
     CRL_REQUIRE(c.B % 8 == 0 && c.hidden % 8 == 0, CRL_E_UNSUPPORTED,
                 "the BF16 path needs B and hidden to be multiples of 8 (16-byte TMA rows)");
   }
-  CRL_REQUIRE(c.energy != CRL_ENERGY_L1, CRL_E_UNSUPPORTED, "the L1 energy backward is not implemented");
   CRL_REQUIRE(c.lr_critic >= 0.f && c.lr_actor >= 0.f && c.adam_eps > 0.f && c.adam_beta1 >= 0.f &&
                   c.adam_beta1 < 1.f && c.adam_beta2 >= 0.f && c.adam_beta2 < 1.f,
               CRL_E_INVALID_ARG, "bad Adam hyperparameters");
@@ -1015,7 +1014,6 @@ int crl_infonce_backward(const crl_loss_desc* d, const void* phi, const void* ps
                          size_t ws_bytes, void* stream) {
   return guarded(nullptr, [&] {
     const LossSpec ls = checked_loss(d);
-    CRL_REQUIRE(ls.energy != CRL_ENERGY_L1, CRL_E_UNSUPPORTED, "the L1 energy backward is not implemented");
     CRL_REQUIRE(phi && psi && row_lse && col_lse && dphi && dpsi && ws && B >= 1 && R >= 1, CRL_E_INVALID_ARG,
                 "bad argument");
     CRL_REQUIRE(ws_bytes >= infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path), CRL_E_SHAPE,

@@ -17,6 +17,8 @@
 //                           dpsi_j = (H^T phi)_j - (sum_i H_ij) psi_j   (H = 0 where d = 0)
 //   L2^2: the same with H = 2 G / tau
 //   cos:  the dot form on x = phi/|phi|, then dphi = (dx - x <x, dx>) / |phi|.
+//   L1:   H = G / tau,  dphi_ik = -sum_j H_ij sign(phi_ik - psi_jk),
+//                       dpsi_jk = -sum_i H_ij sign(psi_jk - phi_ik)   (sign(0) = 0)
 #include <algorithm>
 
 #include "common.cuh"
@@ -266,6 +268,59 @@ __global__ void __launch_bounds__(256) project_rows_kernel(int B, int R, const T
 
 }  // namespace
 
+namespace {
+
+// L1 energy gradient: out[a][k] = -sum_b Ht(a, b) sign(own[a][k] - oth[b][k]),
+// Ht(a, b) = H[a][b] (transposed = 0: own = phi) or H[b][a] (transposed = 1:
+// own = psi).  Block = 32 a x 32 k outputs (4 per thread), b in chunks of 32
+// through shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) l1_grad_kernel(int B, int R, const T* __restrict__ H, int transposed,
+                                                     const T* __restrict__ own, const T* __restrict__ oth,
+                                                     T* __restrict__ out) {
+  pdl_enter();
+  __shared__ T Hs[32][33];
+  __shared__ T Os[32][33];
+  const int a0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // k = k0 + tx, a = a0 + ty + 8 m
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  T mine[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int a = a0 + ty + 8 * m, k = k0 + tx;
+    mine[m] = (a < B && k < R) ? own[(size_t)a * R + k] : T(0);
+  }
+  for (int b0 = 0; b0 < B; b0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int a = a0 + r, b = b0 + tx;
+      T h = T(0);
+      if (a < B && b < B) h = transposed ? H[(size_t)b * B + a] : H[(size_t)a * B + b];
+      Hs[r][tx] = h;
+      const int bb = b0 + r, k = k0 + tx;
+      Os[r][tx] = (bb < B && k < R) ? oth[(size_t)bb * R + k] : T(0);
+    }
+    __syncthreads();
+    const int nb = min(32, B - b0);
+    for (int j = 0; j < nb; ++j) {
+      const T o = Os[j][tx];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const T d = mine[m] - o;
+        const T sg = (d > T(0)) ? T(1) : ((d < T(0)) ? T(-1) : T(0));
+        acc[m] += Hs[ty + 8 * m][j] * sg;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int a = a0 + ty + 8 * m, k = k0 + tx;
+    if (a < B && k < R) out[(size_t)a * R + k] = -acc[m];
+  }
+}
+
+}  // namespace
+
 size_t infonce_ws_bytes(const LossSpec& ls, int B, int R, size_t elem, int path) {
   (void)ls;
   (void)path;
@@ -314,6 +369,7 @@ void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int
     switch (ls.energy) {
       case CRL_ENERGY_L2:
       case CRL_ENERGY_L2SQ: gemm<T, InnerOp::kSqDiff>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
+      case CRL_ENERGY_L1: gemm<T, InnerOp::kAbsDiff>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
       default: gemm<T, InnerOp::kMul>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
     }
   }
@@ -333,6 +389,14 @@ void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int
     gemm<T>(B, R, B, LoadTrans<T>{H, B}, LoadKN<T>{w.xh, R}, EpiScale<T>{dpsi, R, T(1)}, st, CRL_TRACE_ENERGY);
     { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(project_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, R, w.xh, w.inx, dphi); }
     { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(project_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, R, w.yh, w.iny, dpsi); }
+  } else if (ls.energy == CRL_ENERGY_L1) {
+    const dim3 grid(ceil_div(R, 32), ceil_div(B, 32));
+    {
+      TraceLaunch tr_(CRL_TRACE_ENERGY, st, 2.0 * B * B * R);
+      launch_k(l1_grad_kernel<T>, grid, dim3(256), 0, st, B, R, H, 0, phi, psi, dphi);
+    }
+    TraceLaunch tr_(CRL_TRACE_ENERGY, st, 2.0 * B * B * R);
+    launch_k(l1_grad_kernel<T>, grid, dim3(256), 0, st, B, R, H, 1, psi, phi, dpsi);
   } else {  // dot
     gemm<T>(B, R, B, LoadMK<T>{H, B}, LoadKN<T>{psi, R}, EpiScale<T>{dphi, R, T(1)}, st, CRL_TRACE_ENERGY);
     gemm<T>(B, R, B, LoadTrans<T>{H, B}, LoadKN<T>{phi, R}, EpiScale<T>{dpsi, R, T(1)}, st, CRL_TRACE_ENERGY);

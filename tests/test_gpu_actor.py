@@ -34,7 +34,7 @@ def run_actor(w, precision, start=5, eps_seed=3, nets=None, n=70, mean_len=9.0):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq"])
+@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq", "l1"])
 @pytest.mark.parametrize("layernorm", [False, True])
 def test_actor_step_matches_oracle(precision, energy, layernorm):
     w = small(energy=energy, layernorm=layernorm, tau=0.8)

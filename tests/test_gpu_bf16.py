@@ -55,7 +55,7 @@ def run_critic(w, nets=None, n=70, mean_len=9.0):
     return ctx, loss, ref
 
 
-@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq"])
+@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq", "l1"])
 @pytest.mark.parametrize("layernorm", [False, True])
 def test_bf16_critic_matches_oracle(energy, layernorm):
     w = bf16_small(energy=energy, layernorm=layernorm, tau=0.7 if energy == "cos" else 1.0)

@@ -40,7 +40,7 @@ def check(ctx, got, ref, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq"])
+@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq", "l1"])
 @pytest.mark.parametrize("loss", ["fwd", "bwd", "sym"])
 @pytest.mark.parametrize("layernorm", [False, True])
 def test_critic_step_matches_oracle(precision, energy, loss, layernorm):

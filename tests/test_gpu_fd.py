@@ -26,7 +26,7 @@ def fd_loss_fn(ctx, w, s, a, g, penalty_axis="row"):
     return loss
 
 
-@pytest.mark.parametrize("energy", ["dot", "l2"])
+@pytest.mark.parametrize("energy", ["dot", "l2", "l1"])
 @pytest.mark.parametrize("loss", ["fwd", "bwd", "sym"])
 def test_fp64_gradient_against_central_differences(energy, loss):
     w = workload.ANT_AUTOGRAD.with_(energy=energy, loss=loss)

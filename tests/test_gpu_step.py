@@ -151,3 +151,15 @@ def test_graph_replay_matches_eager(precision, path):
     np.testing.assert_array_equal(runs[0][0], runs[1][0])
     for n in ("phi", "psi", "pi"):
         np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
+
+
+def test_l1_energy_runs_on_the_plain_path_only():
+    """-L1 (App. A.2) has a plain-path backward; the fused BF16 path rejects it."""
+    w = small(B=64, energy="l1")
+    h = ctypes.c_void_p()
+    cfg = api.make_config(w, precision="bf16", path="fused", repr=64)
+    assert api.lib().crl_create(ctypes.byref(cfg), ctypes.byref(h)) == api.E_UNSUPPORTED
+    for precision in ("fp32", "bf16"):
+        cfg = api.make_config(w, precision=precision, path="plain")
+        assert api.lib().crl_create(ctypes.byref(cfg), ctypes.byref(h)) == api.OK
+        api.lib().crl_destroy(h)
