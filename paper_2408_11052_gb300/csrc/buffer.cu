@@ -304,6 +304,111 @@ __device__ __forceinline__ void relabel_body(const BufferDev& bd, const RelabelA
   }
 }
 
+// Columns of pack k of a relabelled sample: phi (s, a), psi (g), pi (s, g).
+__device__ __host__ __forceinline__ int pack_cols(int k, int D, int A, int G) {
+  return k == 0 ? D + A : (k == 1 ? G : D + G);
+}
+size_t relabel_pack_smem(const BufferDev& bd, const RelabelArgs& ra) {
+  size_t bytes = 0;
+  for (int k = 0; k < 3; ++k)
+    if (ra.pack[k].x0) bytes += (size_t)2 * pack_cols(k, bd.D, bd.A, ra.G) * 33 * 2;
+  return bytes;
+}
+
+// Relabel with the BF16 network-input packs (the update step): a block of 32
+// warps takes 32 consecutive samples, one per warp (lane 0 draws the indices,
+// the warp copies the row).  Each warp writes its sample's split inputs
+// row-major and stages them in shared memory ([2 c][33] per pack, padded
+// against bank conflicts); the block then writes the transposed copies with
+// each column's 32 samples contiguous.
+__device__ __forceinline__ void relabel_pack_body(const BufferDev& bd, const RelabelArgs& ra, int lb) {
+  extern __shared__ __align__(16) unsigned char relabel_smem[];
+  __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(relabel_smem);
+  const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
+  const int b0 = lb * kWarp;
+  const int b = b0 + w;
+  const unsigned long long step = (ra.step == CRL_STEP_AUTO) ? *ra.step_dev : ra.step;
+  if (lb == 0 && threadIdx.x == 0 && ra.last_step_dev != nullptr) *ra.last_step_dev = step;
+  const int size = bd.state[0];
+  const long long total = bd.state[1];
+  if (size <= 0) {
+    if (threadIdx.x == 0) atomicOr(ra.status, CRL_STATUS_BAD_INDEX);
+    return;
+  }
+  const int D = bd.D, DA = bd.D + bd.A;
+  if (b < ra.B) {
+    int e = 0, t = 0, k = 0;
+    if (lane == 0) {
+      sample_indices(bd, ra, step, b, size, total, e, t, k);
+      if (ra.idx != nullptr) {
+        ra.idx[3 * (size_t)b + 0] = e;
+        ra.idx[3 * (size_t)b + 1] = t;
+        ra.idx[3 * (size_t)b + 2] = k;
+      }
+    }
+    e = __shfl_sync(0xffffffffu, e, 0);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    const long long abs_t = total - size + t;
+    const float* row = bd.rows + ((size_t)e * bd.T + (size_t)(abs_t % bd.T)) * bd.W;
+    const float* grow = bd.rows + ((size_t)e * bd.T + (size_t)((abs_t + k) % bd.T)) * bd.W;
+    for (int c = lane; c < DA; c += kWarp) {
+      const float v = row[c];
+      if (c < D) ra.s[(size_t)b * D + c] = v;
+      else ra.a[(size_t)b * bd.A + (c - D)] = v;
+    }
+    if (lane < ra.G) ra.g[(size_t)b * ra.G + lane] = grow[ra.goal_idx[lane]];
+    __nv_bfloat16* sk = stage;
+    for (int kk = 0; kk < 3; ++kk) {
+      const RelabelPack& pk = ra.pack[kk];
+      if (pk.x0 == nullptr) continue;
+      const int ncol = pack_cols(kk, D, bd.A, ra.G);
+      __nv_bfloat16* x0 = static_cast<__nv_bfloat16*>(pk.x0);
+      for (int c = lane; c < ncol; c += kWarp) {
+        float v;
+        if (kk == 0) v = row[c];
+        else if (kk == 1) v = grow[ra.goal_idx[c]];
+        else v = c < D ? row[c] : grow[ra.goal_idx[c - D]];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        x0[(size_t)b * pk.ld + 2 * c] = hi;
+        x0[(size_t)b * pk.ld + 2 * c + 1] = lo;
+        sk[(2 * c) * 33 + w] = hi;
+        sk[(2 * c + 1) * 33 + w] = lo;
+      }
+      sk += 2 * ncol * 33;
+    }
+  }
+  __syncthreads();
+  const int nb = min(kWarp, ra.B - b0);
+  const __nv_bfloat16* sk = stage;
+  for (int kk = 0; kk < 3; ++kk) {
+    const RelabelPack& pk = ra.pack[kk];
+    if (pk.x0 == nullptr) continue;
+    const int rows = 2 * pack_cols(kk, D, bd.A, ra.G);
+    __nv_bfloat16* xT = static_cast<__nv_bfloat16*>(pk.x0T);
+    for (int idx = threadIdx.x; idx < rows * kWarp; idx += blockDim.x) {
+      const int col = idx / kWarp, j = idx % kWarp;
+      if (j < nb) xT[(size_t)col * pk.ldt + b0 + j] = sk[col * 33 + j];
+    }
+    sk += rows * 33;
+  }
+}
+
+__global__ void __launch_bounds__(1024) relabel_pack_kernel(const __grid_constant__ BufferDev bd,
+                                                           const __grid_constant__ RelabelArgs ra) {
+  pdl_enter();
+  relabel_pack_body(bd, ra, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) relabel_pack_multi_kernel(const RelabelTask* __restrict__ tasks,
+                                                                 const int* __restrict__ begin, int n) {
+  pdl_enter();
+  int lb, nb;
+  const int s = segment_of(begin, n, blockIdx.x, lb, nb);
+  relabel_pack_body(tasks[s].bd, tasks[s].ra, lb);
+}
+
 __global__ void __launch_bounds__(256) relabel_kernel(const __grid_constant__ BufferDev bd,
                                                      const __grid_constant__ RelabelArgs ra) {
   pdl_enter();
@@ -320,12 +425,24 @@ __global__ void __launch_bounds__(256) relabel_multi_kernel(const RelabelTask* _
 }
 
 int relabel_spw(int B) { return (int)std::min<long long>(32, std::max<long long>(1, (long long)B / (152 * 48))); }
-int relabel_blocks(const RelabelArgs& ra) { return ceil_div(ra.B, 8 * ra.spw); }
+bool relabel_packs(const RelabelArgs& ra) { return ra.pack[0].x0 || ra.pack[1].x0 || ra.pack[2].x0; }
+int relabel_blocks(const RelabelArgs& ra) {
+  return relabel_packs(ra) ? ceil_div(ra.B, kWarp) : ceil_div(ra.B, 8 * ra.spw);
+}
 
-void launch_relabel_multi(const RelabelTask* tasks, const int* begin, int n, int blocks, double bytes,
-                          cudaStream_t st) {
+void launch_relabel_multi(const RelabelTask* tasks, const int* begin, int n, int blocks, double bytes, bool packs,
+                          size_t smem, cudaStream_t st) {
   TraceLaunch tr(CRL_TRACE_RELABEL, st, bytes);
-  launch_k(relabel_multi_kernel, dim3(blocks), dim3(256), 0, st, tasks, begin, n);
+  if (packs) {
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+      cudaFuncSetAttribute(relabel_pack_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = smem;
+    }
+    launch_k(relabel_pack_multi_kernel, dim3(blocks), dim3(1024), smem, st, tasks, begin, n);
+  } else {
+    launch_k(relabel_multi_kernel, dim3(blocks), dim3(256), 0, st, tasks, begin, n);
+  }
 }
 
 void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st) {
@@ -335,7 +452,17 @@ void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st)
   // samples per warp: as many warps as fill the GPU (152 SMs x 48 resident warps), at most 32
   RelabelArgs r = ra;
   r.spw = relabel_spw(ra.B);
-  launch_k(relabel_kernel, dim3(relabel_blocks(r)), dim3(256), 0, st, bd, r);
+  if (relabel_packs(r)) {
+    const size_t smem = relabel_pack_smem(bd, r);
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+      cudaFuncSetAttribute(relabel_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = smem;
+    }
+    launch_k(relabel_pack_kernel, dim3(relabel_blocks(r)), dim3(1024), smem, st, bd, r);
+  } else {
+    launch_k(relabel_kernel, dim3(relabel_blocks(r)), dim3(256), 0, st, bd, r);
+  }
 }
 
 __global__ void bump_u64_kernel(unsigned long long* c) {

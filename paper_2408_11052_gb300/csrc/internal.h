@@ -79,10 +79,13 @@ struct RelabelTask {
   RelabelArgs ra;                   // ra.spw set (relabel_spw)
 };
 int relabel_spw(int B);
+bool relabel_packs(const RelabelArgs& ra);
 int relabel_blocks(const RelabelArgs& ra);
-// tasks / begin: device tables (n tasks, n + 1 block offsets).
-void launch_relabel_multi(const RelabelTask* tasks, const int* begin, int n, int blocks, double bytes,
-                          cudaStream_t st);
+size_t relabel_pack_smem(const BufferDev& bd, const RelabelArgs& ra);  // shared memory of the pack kernels
+// tasks / begin: device tables (n tasks, n + 1 block offsets).  packs: every
+// task writes the BF16 input packs (smem: the largest task's relabel_pack_smem).
+void launch_relabel_multi(const RelabelTask* tasks, const int* begin, int n, int blocks, double bytes, bool packs,
+                          size_t smem, cudaStream_t st);
 void build_discount_table(float gamma, int n, unsigned long long* out);  // host
 
 // ---------------------------------------------------------------- MLPs

@@ -94,6 +94,7 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     std::vector<RelabelTask> tasks(na);
     std::vector<int> begin(na + 1, 0);
     double bytes = 0.0;
+    size_t smem = 0;
     for (int i = 0; i < na; ++i) {
       crl_ctx* c = sw->agents[i];
       const crl_config& cf = c->cfg;
@@ -102,6 +103,7 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
       tasks[i].bd = c->bd;
       tasks[i].ra = relabel_args(c, CRL_STEP_AUTO, cf.B, c->bs, c->ba, c->bg, nullptr, true);
       begin[i + 1] = begin[i] + relabel_blocks(tasks[i].ra);
+      smem = std::max(smem, relabel_pack_smem(c->bd, tasks[i].ra));
       bytes += cf.B * ((cf.D + cf.A + 1 + cf.G) * 4.0 + (cf.D + cf.A + cf.G) * 4.0);
     }
     const char* err = nullptr;
@@ -109,7 +111,7 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     sweep_check(dt ? nullptr : err);
     const int* db = sw->tables.get(begin, st, &err);
     sweep_check(db ? nullptr : err);
-    launch_relabel_multi(dt, db, na, begin[na], bytes, st);
+    launch_relabel_multi(dt, db, na, begin[na], bytes, true, smem, st);
   }
   // ---- critic: phi, psi and pi forward (pi's parameters do not change before the actor step)
   std::vector<BfPass> fwd, bwd;
