@@ -24,6 +24,12 @@ P2  log pi(a'|s, g) = sum_d [ -eps_d^2 / 2 - log(2 pi) / 2 - l_d
 P3  L_actor = mean_i [ alpha * log pi_i - F_ii ], F_ii = f(phi(s_i, a'_i), psi(g_i)) / tau
     with the critic's energy and temperature; alpha is given.
 P4  The clip passes the gradient only strictly inside (-5, 2).
+P5  Entropy-coefficient auto-tuning (§5.1, "a tuneable entropy coefficient";
+    the paper gives no rule): alpha = exp(log_alpha), log_alpha learned by
+    Adam on  L(log_alpha) = -log_alpha * (mean_i log pi_i + H_target)  with
+    log pi held fixed and H_target = -A (the action dimension).  The actor
+    loss of a step uses alpha before that step's update; the configured alpha
+    is the initial value.
 """
 
 import numpy as np
@@ -103,3 +109,8 @@ def actor_loss_and_grad(pi_net, phi_net, psi_net, s, g, eps, energy="l2", tau=1.
     grads, _ = mlp.backward(pi_net, pi_cache, np.concatenate([dmu, dl_raw], axis=1))
     return {"loss": loss, "logpi_mean": float(np.mean(logpi)), "f_mean": float(np.mean(f)),
             "grads": grads, "a_new": a_new, "logpi": logpi}
+
+
+def alpha_loss_grad(logpi_mean, target_entropy):
+    """dL/d(log alpha) of  L = -log_alpha * (logpi_mean + target_entropy)  (reading P5)."""
+    return -(float(logpi_mean) + float(target_entropy))

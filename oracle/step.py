@@ -59,6 +59,11 @@ class AgentState:
         self.v = {k: zeros_like_net(n) for k, n in self.nets.items()}
         self.t_critic = 0
         self.t_actor = 0
+        # entropy-coefficient auto-tuning (reading P5): log alpha and its Adam moments,
+        # initialised from cfg["alpha"] on the first tuned step
+        self.log_alpha = None
+        self.m_alpha = 0.0
+        self.v_alpha = 0.0
 
 
 def update_step(state, buf, cfg, step, eps):
@@ -66,7 +71,9 @@ def update_step(state, buf, cfg, step, eps):
 
     cfg keys: seed, agent, B, goal_idx, gamma, offset_min, energy, tau, loss,
     sym_reduction, beta, penalty_axis, alpha, lr_critic, lr_actor, and optionally
-    adam_beta1, adam_beta2, adam_eps (textbook defaults).
+    adam_beta1, adam_beta2, adam_eps (textbook defaults) and alpha_autotune,
+    target_entropy, lr_alpha (reading P5 of the actor module; the returned dict
+    then carries the alpha used and the updated one).
     eps [B][A]: the actor's Gaussian noise, drawn by the caller.
     """
     s, a, g, idx = relabel.sample_relabel(buf, cfg["seed"], cfg.get("agent", 0), step, cfg["B"],
@@ -79,9 +86,20 @@ def update_step(state, buf, cfg, step, eps):
     for name, grads in (("phi", gphi), ("psi", gpsi)):
         state.nets[name], state.m[name], state.v[name] = adam_net(
             state.nets[name], grads, state.m[name], state.v[name], state.t_critic, cfg["lr_critic"], *betas)
+    tune = bool(cfg.get("alpha_autotune", False))
+    if tune and state.log_alpha is None:
+        state.log_alpha = float(np.log(cfg["alpha"]))
+    alpha = float(np.exp(state.log_alpha)) if tune else cfg["alpha"]
     act = actor.actor_loss_and_grad(state.nets["pi"], state.nets["phi"], state.nets["psi"], s, g, eps,
-                                    cfg["energy"], cfg["tau"], cfg["alpha"])
+                                    cfg["energy"], cfg["tau"], alpha)
     state.t_actor += 1
     state.nets["pi"], state.m["pi"], state.v["pi"] = adam_net(
         state.nets["pi"], act["grads"], state.m["pi"], state.v["pi"], state.t_actor, cfg["lr_actor"], *betas)
-    return {"critic": parts, "actor_loss": act["loss"], "logpi_mean": act["logpi_mean"], "idx": idx}
+    out = {"critic": parts, "actor_loss": act["loss"], "logpi_mean": act["logpi_mean"], "idx": idx, "alpha": alpha}
+    if tune:
+        ga = actor.alpha_loss_grad(act["logpi_mean"], cfg["target_entropy"])
+        la, state.m_alpha, state.v_alpha = adam.adam_update(state.log_alpha, ga, state.m_alpha, state.v_alpha,
+                                                        state.t_actor, cfg["lr_alpha"], *betas)
+        state.log_alpha = float(la)
+        out["alpha_next"] = float(np.exp(state.log_alpha))
+    return out

@@ -240,3 +240,79 @@ def test_gaussian_noise_is_standard_normal():
     again = actor.gaussian_noise(3, 0, 5, 4, 7)
     np.testing.assert_array_equal(again, eps.reshape(600, 7)[:4])
     assert (actor.gaussian_noise(3, 0, 6, 4, 7) != again).all()
+
+
+# ---- entropy-coefficient auto-tuning (reading P5) -------------------------------
+
+def test_alpha_first_adam_step_moves_log_alpha_by_lr_against_the_entropy_gap():
+    """First Adam step: m_hat = g, v_hat = g^2, so log alpha moves by -lr sign(g)
+    (up to eps): up when the policy's entropy -mean(log pi) is below the target
+    H_target = -A, down when above."""
+    from oracle.actor import alpha_loss_grad
+    from oracle.adam import adam_update
+    lr, A = 6e-4, 8
+    for logpi_mean, expect_up in ((-2.0, False), (12.0, True)):   # entropy 2 > -8: down; entropy -12 < -8: up
+        g = alpha_loss_grad(logpi_mean, -A)
+        la, m, v = adam_update(np.log(0.1), g, 0.0, 0.0, 1, lr)
+        step = float(la) - np.log(0.1)
+        assert np.isclose(abs(step), lr, rtol=1e-6)
+        assert (step > 0) == expect_up
+
+
+def test_alpha_update_matches_torch_adam_on_the_scalar_loss():
+    """Three steps of the oracle's log-alpha update against torch.optim.Adam minimising
+    -log_alpha * (mean log pi + H_target) (log pi held fixed)."""
+    import torch
+    from oracle.actor import alpha_loss_grad
+    from oracle.adam import adam_update
+    H = -17.0
+    logpis = [-3.0, -25.0, -10.5]
+    la, m, v = np.log(0.1), 0.0, 0.0
+    p = torch.tensor(np.log(0.1), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([p], lr=3e-3, betas=(0.9, 0.999), eps=1e-8)
+    for t, lp in enumerate(logpis, start=1):
+        la, m, v = adam_update(la, alpha_loss_grad(lp, H), m, v, t, 3e-3)
+        opt.zero_grad()
+        loss = -p * (lp + H)
+        loss.backward()
+        opt.step()
+        assert np.isclose(float(la), p.item(), rtol=0, atol=1e-12)
+
+
+def test_update_step_uses_alpha_before_its_update():
+    """With auto-tuning the step's actor loss equals the actor loss at the pre-update
+    alpha, and the returned next alpha is one Adam step on log alpha from it."""
+    from paper_2408_11052_gb300 import workload
+    from oracle.actor import actor_loss_and_grad, alpha_loss_grad, gaussian_noise
+    from oracle.adam import adam_update
+    from oracle.relabel import ReplayBuffer, sample_relabel
+    from oracle.step import AgentState, update_step
+    w = workload.SMALL_FP32.with_(E=4, T=30, B=8, hidden=16, repr=8)
+    nets = {k: [{kk: vv.astype(np.float64) for kk, vv in l.items()} for l in v]
+            for k, v in workload.init_agent(w).items()}
+    obs, act, done = workload.buffer_contents(w, n=30, mean_len=6.0)
+    buf = ReplayBuffer(w.E, w.T, w.D, w.A)
+    buf.insert(obs, act, done)
+    cfg = dict(seed=w.seed, agent=0, B=w.B, goal_idx=w.goals(), gamma=w.gamma, energy=w.energy, tau=w.tau,
+               loss=w.loss, sym_reduction=w.sym_reduction, beta=w.beta, penalty_axis=w.penalty_axis, alpha=0.1,
+               lr_critic=w.lr_critic, lr_actor=w.lr_actor, alpha_autotune=True, target_entropy=-float(w.A),
+               lr_alpha=6e-4)
+    state = AgentState(nets["phi"], nets["psi"], nets["pi"])
+    alphas = []
+    for step in range(2):
+        eps = gaussian_noise(w.seed, 0, step, w.B, w.A)
+        before = AgentState(state.nets["phi"], state.nets["psi"], state.nets["pi"])   # a deep copy
+        out = update_step(state, buf, cfg, step, eps)
+        alphas.append((out["alpha"], out["alpha_next"]))
+        if step == 0:
+            # the step's actor loss is the one at the initial alpha
+            s, _, g, _ = sample_relabel(buf, w.seed, 0, step, w.B, w.goals(), w.gamma)
+            ref = actor_loss_and_grad(before.nets["pi"], state.nets["phi"], state.nets["psi"], s, g, eps,
+                                      w.energy, w.tau, 0.1)
+            assert np.isclose(out["actor_loss"], ref["loss"], rtol=0, atol=1e-12)
+            la_next, _, _ = adam_update(np.log(0.1), alpha_loss_grad(out["logpi_mean"], cfg["target_entropy"]),
+                                        0.0, 0.0, 1, 6e-4)
+            assert np.isclose(out["alpha"], 0.1)
+            assert np.isclose(np.log(out["alpha_next"]), float(la_next), rtol=0, atol=1e-12)
+    assert np.isclose(alphas[1][0], alphas[0][1])          # step 2 uses the alpha step 1 produced
+    assert alphas[0][1] != alphas[0][0]
