@@ -128,11 +128,22 @@ typedef struct crl_config {
   float adam_beta1, adam_beta2, adam_eps;
   uint64_t seed;        /* Philox key word 0                                        */
   uint64_t agent;       /* Philox key word 1 (independent agents)                   */
+  /* entropy-coefficient auto-tuning (§5.1 "a tuneable entropy coefficient";
+   * the rule is a reading): with alpha_autotune = 1, log(alpha) starts at
+   * log(alpha) and after every actor update takes one Adam step (lr_alpha,
+   * adam_beta1/2, adam_eps) on  -log(alpha) * (mean log pi + target_entropy)
+   * with log pi held fixed; the actor loss of a step uses alpha before that
+   * step's update.  crl_get_alpha reads the current value. */
+  int32_t alpha_autotune;
+  float target_entropy; /* -A by convention (crl_config_default: -8)               */
+  float lr_alpha;       /* crl_config_default: 6e-4 (the actor's rate)             */
+  int32_t reserved;     /* zero                                                     */
 } crl_config;
 
 /* Fill *cfg with the paper's defaults (App. B.3: batch 256, gamma 0.99,
  * 2 x 256 hidden, repr 64, L2 energy, symmetric InfoNCE, penalty 0.1,
- * lr 3e-4 / 6e-4) and Ant-like sizes (E 1024, T 1000, D 29, A 8, G 2). */
+ * lr 3e-4 / 6e-4) and Ant-like sizes (E 1024, T 1000, D 29, A 8, G 2);
+ * fixed alpha 0.1 (alpha_autotune 0). */
 void crl_config_default(crl_config* cfg);
 
 /* ---- parameter layout ---------------------------------------------------- */
@@ -248,6 +259,9 @@ int crl_set_step(crl_ctx* ctx, uint64_t step);
  * bits) and clear it.  Returns CRL_E_NONFINITE / CRL_E_TIMEOUT when those bits
  * are set, CRL_OK otherwise. */
 int crl_sync_status(crl_ctx* ctx, void* stream, uint32_t* status);
+/* The entropy coefficient the next actor step will use: exp(log alpha) with
+ * auto-tuning, else cfg.alpha.  Synchronous read. */
+int crl_get_alpha(crl_ctx* ctx, float* alpha);
 
 /* Message of the last failing call on ctx (ctx == NULL: on this thread). */
 const char* crl_last_error(const crl_ctx* ctx);

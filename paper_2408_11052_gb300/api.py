@@ -42,7 +42,9 @@ class CrlConfig(ctypes.Structure):
                 ("layernorm", c_int32), ("precision", c_int32), ("path", c_int32), ("offset_min", c_int32),
                 ("lr_critic", c_float), ("lr_actor", c_float),
                 ("adam_beta1", c_float), ("adam_beta2", c_float), ("adam_eps", c_float),
-                ("seed", c_uint64), ("agent", c_uint64)]
+                ("seed", c_uint64), ("agent", c_uint64),
+                ("alpha_autotune", c_int32), ("target_entropy", c_float), ("lr_alpha", c_float),
+                ("reserved", c_int32)]
 
 
 class CrlTensorInfo(ctypes.Structure):
@@ -81,6 +83,7 @@ _SIGNATURES = {
     "crl_get_step": (c_int32, [c_void_p, POINTER(c_uint64)]),
     "crl_set_step": (c_int32, [c_void_p, c_uint64]),
     "crl_sync_status": (c_int32, [c_void_p, c_void_p, POINTER(c_uint32)]),
+    "crl_get_alpha": (c_int32, [c_void_p, POINTER(c_float)]),
     "crl_last_error": (ctypes.c_char_p, [c_void_p]),
     "crl_trace_start": (c_int32, [c_void_p, c_int32, c_int32]),
     "crl_trace_stop": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_double), POINTER(c_double)]),
@@ -186,6 +189,9 @@ def make_config(w, precision="fp32", path="plain", agent=0, offset_min=1, penalt
     c.precision, c.path, c.offset_min = PREC[precision], PATH[path], offset_min
     c.lr_critic, c.lr_actor = w.lr_critic, w.lr_actor
     c.seed, c.agent = w.seed, agent
+    c.alpha_autotune = 1 if w.alpha_autotune else 0
+    c.target_entropy = -float(w.A) if w.target_entropy is None else w.target_entropy
+    c.lr_alpha = w.lr_actor if w.lr_alpha is None else w.lr_alpha
     for k, v in over.items():
         setattr(c, k, v)
     return c
@@ -238,7 +244,13 @@ class CRLContext:
             self.store[net] = {k: torch.zeros(n, dtype=self.dtype, device=self.device)
                                for k in ("params", "grads", "adam_m", "adam_v")}
             ptrs[i] = CrlNetPtrs(*(self.store[net][k].data_ptr() for k in ("params", "grads", "adam_m", "adam_v")))
-        check(lib().crl_bind_params(self.handle, ptrs), self.handle)
+        self._ptrs = ptrs
+        self.rebind()
+
+    def rebind(self):
+        """Bind the parameter arrays again: gradients, the Adam step counters and the
+        tuned entropy coefficient start afresh (parameters and moments are kept)."""
+        check(lib().crl_bind_params(self.handle, self._ptrs), self.handle)
 
     # -- parameters -----------------------------------------------------------
     def views(self, net, which="params"):
@@ -307,6 +319,12 @@ class CRLContext:
         check(lib().crl_update_step(self.handle, ptr(obs), ptr(act), ptr(done), n, ptr(loss_out),
                                     stream_handle(stream)), self.handle)
         return loss_out
+
+    def get_alpha(self):
+        """The entropy coefficient the next actor step uses."""
+        v = c_float()
+        check(lib().crl_get_alpha(self.handle, byref(v)), self.handle)
+        return v.value
 
     def get_step(self):
         v = c_uint64()

@@ -141,7 +141,9 @@ __device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p,
     f *= it;
     if (lane == 0) p.fdiag[i] = f;
     lpi = p.logpi[i];
-    term = T(p.alpha) * lpi - f;
+    // every block reads log alpha before its ticket; the last block updates it after all tickets
+    const double alpha = p.tune.state ? exp(p.tune.state[0]) : p.alpha;
+    term = T(alpha) * lpi - f;
     const T nx = dev_sqrt(sxx), ny = dev_sqrt(syy), dist = dev_sqrt(sdd);
     for (int c = lane; c < R; c += kWarp) {
       const T a = x[c], b = y[c], d = a - b;
@@ -194,6 +196,22 @@ __device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p,
     p.loss2[1] = l / T(B);
     if (p.status && !finite_val(a)) atomicOr(p.status, CRL_STATUS_NONFINITE);
     if (p.t_bump) *p.t_bump += 1;
+    if (p.tune.state) {
+      double* s = p.tune.state;
+      s[3] = exp(s[0]);
+      if (p.t_bump) {
+        // Adam on log alpha: gradient of -log alpha * (mean log pi + target entropy)
+        const int t = *p.t_bump;
+        const double g = -((double)l / B + p.tune.target_entropy);
+        const double b1 = p.tune.b1, b2 = p.tune.b2;
+        const double m = b1 * s[1] + (1.0 - b1) * g;
+        const double v = b2 * s[2] + (1.0 - b2) * g * g;
+        const double mh = m / (1.0 - pow(b1, (double)t)), vh = v / (1.0 - pow(b2, (double)t));
+        s[0] -= p.tune.lr * mh / (sqrt(vh) + p.tune.eps);
+        s[1] = m;
+        s[2] = v;
+      }
+    }
     // next relabel step: the one this step's relabel used, plus one
     if (p.step_bump) *p.step_bump = *p.last_step + 1ull;
     *p.ticket = 0u;
@@ -221,7 +239,7 @@ __device__ __forceinline__ void head_backward_body(const HeadBwdArgs<T>& p, int 
   const int ldz = p.ldz, ldt = p.ldt;
   const int b = lb * blockDim.x + threadIdx.x;
   if (b >= B) return;
-  const T ab = T(alpha / B);
+  const T ab = T((p.alpha_used ? *p.alpha_used : alpha) / B);
   for (int d = 0; d < A; ++d) {
     const T mu = out[(size_t)b * 2 * A + d];
     const T lraw = out[(size_t)b * 2 * A + A + d];
@@ -349,7 +367,7 @@ void actor_energy_and_loss(const ActorSpec& as, const T* phi, const T* psi, cons
                            __nv_bfloat16* dz, int ldz) {
   ActorLossArgs<T> p{B,    R,     as.energy, as.tau, as.alpha, phi,    psi,       logpi,     fdiag,
                      dphi, dz,    ldz,       static_cast<T*>(ws), ticket, loss2, status, t_bump, step_bump,
-                     last_step};
+                     last_step, as.tune};
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * R);
   launch_k(diag_energy_loss_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, p);
 }
@@ -358,7 +376,8 @@ template <typename T>
 void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used, const T* da, int B, T* dout,
                          cudaStream_t st, __nv_bfloat16* dz, int ldz, __nv_bfloat16* dzT, int ldt) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 6);
-  const HeadBwdArgs<T> p{B, as.A, as.alpha, pi_out, eps_used, da, dout, dz, ldz, dzT, ldt};
+  const HeadBwdArgs<T> p{B,  as.A, as.alpha, pi_out, eps_used, da,
+                         dout, dz, ldz,     dzT,    ldt,      as.tune.state ? as.tune.state + 3 : nullptr};
   launch_k(head_backward_kernel<T>, dim3(ceil_div(B, 256)), dim3(256), 0, st, p);
 }
 

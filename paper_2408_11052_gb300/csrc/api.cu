@@ -73,6 +73,9 @@ void validate_config(const crl_config& c) {
   CRL_REQUIRE(c.gamma >= 0.f && c.gamma < 1.f, CRL_E_INVALID_ARG, "gamma must lie in [0, 1)");
   CRL_REQUIRE(c.temperature > 0.f && std::isfinite(c.temperature), CRL_E_INVALID_ARG, "temperature must be > 0");
   CRL_REQUIRE(c.beta_lse >= 0.f && c.alpha >= 0.f, CRL_E_INVALID_ARG, "beta_lse and alpha must be >= 0");
+  CRL_REQUIRE(c.alpha_autotune == 0 || c.alpha_autotune == 1, CRL_E_INVALID_ARG, "alpha_autotune must be 0 or 1");
+  CRL_REQUIRE(!c.alpha_autotune || (c.alpha > 0.f && std::isfinite(c.target_entropy) && c.lr_alpha >= 0.f),
+              CRL_E_INVALID_ARG, "alpha_autotune needs alpha > 0, a finite target_entropy and lr_alpha >= 0");
   CRL_REQUIRE(c.energy >= CRL_ENERGY_L2 && c.energy <= CRL_ENERGY_L2SQ, CRL_E_INVALID_ARG, "unknown energy");
   CRL_REQUIRE(c.loss >= CRL_LOSS_FWD && c.loss <= CRL_LOSS_SYM, CRL_E_INVALID_ARG, "unknown loss");
   CRL_REQUIRE(c.sym_reduction == CRL_SYM_MEAN || c.sym_reduction == CRL_SYM_SUM, CRL_E_INVALID_ARG,
@@ -194,7 +197,7 @@ void actor_impl(crl_ctx* c, const float* s, const float* g, const float* eps, in
   T* da = static_cast<T*>(c->da);
   T* dout = static_cast<T*>(c->dout);
   T* loss = static_cast<T*>(c->loss) + 4;
-  ActorSpec as{cf.A, cf.energy, (double)cf.temperature, (double)cf.alpha};
+  const ActorSpec as = actor_spec_of(c);
   mlp_forward<T, float>(c->shapes[CRL_NET_PI], ppi, s, g, B, pi_out, c->saved[CRL_NET_PI], st);
   actor_head_forward<T>(as, pi_out, eps, &c->ctr->last_step, cf.seed, cf.agent, B, a_new, logpi, eps_used, st);
   mlp_forward<T, T>(c->shapes[CRL_NET_PHI], pphi, s, a_new, B, phi, c->saved[CRL_NET_PHI], st);
@@ -243,6 +246,31 @@ void bf_refresh(crl_ctx* c, int net, bool refresh, cudaStream_t st) {
     bf_net_shadow(c->bf[net], static_cast<const float*>(c->nets[net].params), st);
     c->shadow_ok[net] = true;
   }
+}
+
+ActorSpec actor_spec_of(crl_ctx* c) {
+  const crl_config& cf = c->cfg;
+  ActorSpec as;
+  std::memset(&as, 0, sizeof(as));   // member by member: zeroed padding keys the device tables
+  as.A = cf.A;
+  as.energy = cf.energy;
+  as.tau = (double)cf.temperature;
+  as.alpha = (double)cf.alpha;
+  if (cf.alpha_autotune) {
+    as.tune.state = c->ctr->alpha;
+    as.tune.target_entropy = (double)cf.target_entropy;
+    as.tune.lr = (double)cf.lr_alpha;
+    as.tune.b1 = (double)cf.adam_beta1;
+    as.tune.b2 = (double)cf.adam_beta2;
+    as.tune.eps = (double)cf.adam_eps;
+  }
+  return as;
+}
+
+void reset_alpha(crl_ctx* c) {
+  const double a = (double)c->cfg.alpha;
+  const double init[4] = {std::log(a), 0.0, 0.0, a};
+  CRL_CHECK_CUDA(cudaMemcpy(c->ctr->alpha, init, sizeof(init), cudaMemcpyHostToDevice));
 }
 
 AdamShadowNet adam_net_of(crl_ctx* c, int net, const int* t, float lr) {
@@ -355,7 +383,7 @@ void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* ep
   float* eps_used = static_cast<float*>(c->eps_used);
   float* da = static_cast<float*>(c->da);
   float* loss = static_cast<float*>(c->loss) + 4;
-  ActorSpec as{cf.A, cf.energy, (double)cf.temperature, (double)cf.alpha};
+  const ActorSpec as = actor_spec_of(c);
   if (!packed) {
     bf_net_pack_input(PI, s, g, B, st);
     bf_net_pack_input(Q, g, nullptr, B, st);
@@ -512,6 +540,9 @@ void crl_config_default(crl_config* c) {
   c->adam_eps = 1e-8f;
   c->seed = 0;
   c->agent = 0;
+  c->alpha_autotune = 0;
+  c->target_entropy = -(float)c->A;
+  c->lr_alpha = c->lr_actor;
 }
 
 int crl_param_count(const crl_config* cfg, int32_t net, int64_t* count) {
@@ -583,6 +614,7 @@ int crl_create(const crl_config* cfg, crl_ctx** out) {
     CRL_CHECK_CUDA(cudaMemset(c->ep_start, 0, (size_t)cf.E * sizeof(int32_t)));
     CRL_CHECK_CUDA(cudaMemset(c->bstate, 0, 2 * sizeof(int32_t)));
     CRL_CHECK_CUDA(cudaMemset(c->ctr, 0, sizeof(Counters)));
+    reset_alpha(c);
     CRL_CHECK_CUDA(cudaMemset(c->rows, 0, (size_t)cf.E * cf.T * W * sizeof(float)));
     std::vector<unsigned long long> table(cf.T + 2);
     build_discount_table(cf.gamma, cf.T + 2, table.data());
@@ -679,6 +711,7 @@ int crl_bind_params(crl_ctx* ctx, const crl_net_ptrs nets[3]) {
       CRL_CHECK_CUDA(cudaMemset(nets[i].grads, 0, (size_t)ctx->counts[i] * ctx->esz));
     }
     CRL_CHECK_CUDA(cudaMemset(&ctx->ctr->t_critic, 0, 2 * sizeof(int)));
+    reset_alpha(ctx);
     CRL_CHECK_CUDA(cudaDeviceSynchronize());
     ctx->drop_graph();
     ctx->groups.reset();   // tables hold parameter pointers
@@ -825,6 +858,20 @@ int crl_set_step(crl_ctx* ctx, uint64_t step) {
     CRL_REQUIRE(step != CRL_STEP_AUTO, CRL_E_INVALID_ARG, "CRL_STEP_AUTO is not a step value");
     unsigned long long v = step;
     CRL_CHECK_CUDA(cudaMemcpy(&ctx->ctr->step, &v, sizeof(v), cudaMemcpyHostToDevice));
+  });
+}
+
+int crl_get_alpha(crl_ctx* ctx, float* alpha) {
+  return guarded(ctx, [&] {
+    CRL_REQUIRE(ctx && alpha, CRL_E_INVALID_ARG, "null argument");
+    if (!ctx->cfg.alpha_autotune) {
+      *alpha = ctx->cfg.alpha;
+      return;
+    }
+    double v[4];
+    CRL_CHECK_CUDA(cudaDeviceSynchronize());
+    CRL_CHECK_CUDA(cudaMemcpy(v, ctx->ctr->alpha, sizeof(v), cudaMemcpyDeviceToHost));
+    *alpha = (float)std::exp(v[0]);
   });
 }
 

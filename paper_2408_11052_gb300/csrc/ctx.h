@@ -24,6 +24,7 @@ struct Counters {
   int t_actor;
   unsigned status;               // CRL_STATUS_* bits
   unsigned ticket_actor;         // last-block ticket of the actor loss kernel (zero between launches)
+  double alpha[4];               // entropy-coefficient auto-tuning: log alpha, Adam m, v, alpha last used
 };
 
 class Failure {
@@ -141,6 +142,11 @@ void bf_maps(crl_ctx* c, int net, int B);
 void bf_check(const char* err);
 void bf_refresh(crl_ctx* c, int net, bool refresh, cudaStream_t st);
 AdamShadowNet adam_net_of(crl_ctx* c, int net, const int* t, float lr);
+// The actor's sizes, energy, temperature, fixed alpha and (with alpha_autotune)
+// the device state of the tuned alpha.
+ActorSpec actor_spec_of(crl_ctx* c);
+// Resets the tuned alpha to log(cfg.alpha) with zero Adam moments (synchronous).
+void reset_alpha(crl_ctx* c);
 void insert_impl(crl_ctx* c, const float* obs, const float* act, const uint8_t* done, int n, cudaStream_t st);
 void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g, int32_t* idx, cudaStream_t st,
                   bool pack_bf16 = false, bool bump = true);

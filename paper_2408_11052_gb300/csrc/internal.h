@@ -125,9 +125,19 @@ void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int
                       cudaStream_t st);
 
 // ---------------------------------------------------------------- actor head
+// Entropy-coefficient auto-tuning (the rule is a reading; the paper only says the
+// coefficient is tuneable): state == null keeps the fixed alpha.  state[4] =
+// {log alpha, Adam m, Adam v, alpha used by the last actor loss}, in FP64 for every
+// precision.  After the actor loss of an applied step, log alpha takes one Adam step
+// on  -log alpha * (mean log pi + target_entropy)  at the actor's step number.
+struct AlphaTune {
+  double* state;
+  double target_entropy, lr, b1, b2, eps;
+};
 struct ActorSpec {
   int A, energy;
   double tau, alpha;
+  AlphaTune tune;
 };
 // eps: explicit [B][A] (may be float for a T = double path) or null -> Philox noise.
 // x0 != null: a' is also written, split into BF16 (hi, lo), into columns
@@ -155,6 +165,7 @@ struct ActorLossArgs {
   int* t_bump;
   unsigned long long* step_bump;
   const unsigned long long* last_step;
+  AlphaTune tune;             // tune.state != null: alpha = exp(state[0]), updated at the end
 };
 size_t actor_loss_ws_bytes(int B, size_t elem);
 template <typename T>
@@ -182,11 +193,13 @@ struct HeadBwdArgs {
   int ldz;
   __nv_bfloat16* dzT;
   int ldt;
+  const double* alpha_used;         // non-null: the alpha the actor loss used (overrides alpha)
 };
 // Diagonal energy, dphi (T, or BF16 into dz [B][ldz] when dz != null) and the
 // actor loss in one launch.  ws: actor_loss_ws_bytes(B, sizeof(T)); ticket: a
 // zero-initialised device word.  t_bump: ++*t_bump; step_bump: *step_bump =
-// *last_step + 1 (both optional).
+// *last_step + 1 (both optional).  as.tune.state: alpha is read from it and, when
+// t_bump is set, updated (see AlphaTune).
 template <typename T>
 void actor_energy_and_loss(const ActorSpec& as, const T* phi, const T* psi, const T* logpi, int B, int R,
                            T* dphi, T* fdiag, T* loss2, void* ws, unsigned* ticket, unsigned* status,

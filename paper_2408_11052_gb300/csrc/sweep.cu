@@ -228,6 +228,7 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
       t.t_bump = &c->ctr->t_actor;
       t.step_bump = &c->ctr->step;
       t.last_step = &c->ctr->last_step;
+      t.tune = actor_spec_of(c).tune;
       al.push_back(t);
     }
     sweep_check(actor_loss_multi(sw->tables, al, st));
@@ -251,6 +252,7 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
       h.ldz = PI.L[PI.layers].out_pad;
       h.dzT = PI.dzT[PI.layers];
       h.ldt = PI.Mmax;
+      h.alpha_used = cf.alpha_autotune ? c->ctr->alpha + 3 : nullptr;
       hb.push_back(h);
     }
     sweep_check(actor_head_backward_multi(sw->tables, hb, st));

@@ -55,6 +55,9 @@ class Workload:
     episode_len: int = 1000
     seed: int = 0
     goal_idx: tuple = field(default=None)
+    alpha_autotune: bool = False     # learn log(alpha) (reading P5); target entropy -A, lr = lr_actor
+    target_entropy: float = None
+    lr_alpha: float = None
 
     def goals(self):
         return tuple(range(self.G)) if self.goal_idx is None else tuple(self.goal_idx)

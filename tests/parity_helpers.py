@@ -39,7 +39,9 @@ def hp(w):
     """Hyperparameters exactly as the library holds them (float32)."""
     return {"tau": f32(w.tau), "beta": f32(w.beta), "alpha": f32(w.alpha), "gamma": f32(w.gamma),
             "lr_critic": f32(w.lr_critic), "lr_actor": f32(w.lr_actor),
-            "adam_beta1": f32(0.9), "adam_beta2": f32(0.999), "adam_eps": f32(1e-8)}
+            "adam_beta1": f32(0.9), "adam_beta2": f32(0.999), "adam_eps": f32(1e-8),
+            "target_entropy": f32(-w.A if w.target_entropy is None else w.target_entropy),
+            "lr_alpha": f32(w.lr_actor if w.lr_alpha is None else w.lr_alpha)}
 
 
 def small(**kw):

@@ -47,7 +47,29 @@ def test_config_default_layout_matches_binding(lib):
     assert c.lr_critic == pytest.approx(3e-4) and c.lr_actor == pytest.approx(6e-4)
     assert c.adam_eps == pytest.approx(1e-8) and c.offset_min == 1
     assert c.seed == 0 and c.agent == 0
-    assert ctypes.sizeof(api.CrlConfig) == 184
+    assert c.alpha_autotune == 0 and c.target_entropy == pytest.approx(-8.0) and c.lr_alpha == pytest.approx(6e-4)
+
+
+def test_config_struct_layout_matches_the_header(tmp_path):
+    """sizeof and every field offset of crl_config as the C compiler lays out the
+    header, against the ctypes mirror."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in api.CrlConfig._fields_]
+    src = tmp_path / "layout.c"
+    lines = ["#include <stddef.h>", "#include <stdio.h>", f'#include "{ROOT}/include/crl.h"', "int main(void) {",
+             '  printf("%zu\\n", sizeof(crl_config));']
+    lines += [f'  printf("%zu\\n", offsetof(crl_config, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(api.CrlConfig)
+    assert out[1:] == [getattr(api.CrlConfig, f).offset for f in fields]
 
 
 @pytest.mark.parametrize("w", [workload.ANT_AUTOGRAD, workload.HUMANOID_BF16, workload.LARGE_BATCH])

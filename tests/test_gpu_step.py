@@ -22,7 +22,8 @@ def oracle_steps(w, nets, buf, n_steps, start_step, inserts, check_kinks=False):
     cfg = dict(seed=w.seed, agent=0, B=w.B, goal_idx=w.goals(), gamma=w.gamma, energy=w.energy, tau=h["tau"],
                loss=w.loss, sym_reduction=w.sym_reduction, beta=h["beta"], penalty_axis=w.penalty_axis,
                alpha=h["alpha"], lr_critic=h["lr_critic"], lr_actor=h["lr_actor"], adam_beta1=h["adam_beta1"],
-               adam_beta2=h["adam_beta2"], adam_eps=h["adam_eps"])
+               adam_beta2=h["adam_beta2"], adam_eps=h["adam_eps"], alpha_autotune=w.alpha_autotune,
+               target_entropy=h["target_entropy"], lr_alpha=h["lr_alpha"])
     outs = []
     for i in range(n_steps):
         buf.insert(*inserts[i])
@@ -87,6 +88,64 @@ def test_update_steps_match_oracle(precision, host_inputs):
     assert ctx.get_step() == start + 3
 
 
+@pytest.mark.parametrize("precision,path", [("fp64", "plain"), ("fp32", "plain"), ("bf16", "plain"),
+                                            ("bf16", "fused")])
+def test_alpha_autotune_matches_oracle(precision, path):
+    """Entropy-coefficient auto-tuning: the alpha each actor loss uses, the alpha after
+    each step, the losses and the policy after four steps against the oracle's step.
+    lr_alpha 0.05 moves alpha by about 5 % a step, so a wrong alpha shows in the loss."""
+    w = small(B=64, repr=64, alpha_autotune=True, target_entropy=-3.0, lr_alpha=0.05)
+    ctx, nets, buf = setup(w, precision=precision, path=path, n=60)
+    n_steps = 4
+    extra = workload.buffer_contents(w, n=n_steps, mean_len=9.0, seed_offset=99)
+    inserts = [tuple(x[i:i + 1] for x in extra) for i in range(n_steps)]
+    start = 0
+    if precision != "bf16":
+        start = None
+        for cand in range(0, 48):
+            trial = oracle.relabel.ReplayBuffer(w.E, w.T, w.D, w.A)
+            trial.obs, trial.act, trial.done = buf.obs.copy(), buf.act.copy(), buf.done.copy()
+            if oracle_steps(w, nets, trial, n_steps, cand, inserts, check_kinks=True) is not None:
+                start = cand
+                break
+        assert start is not None
+    ctx.set_step(start)
+    assert ctx.get_alpha() == pytest.approx(w.alpha, rel=1e-7)
+    loss_out = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+    losses, alphas = [], []
+    for obs, act, done in inserts:
+        ctx.update_step(*(torch.from_numpy(x).to(ctx.device) for x in (obs, act, done)), loss_out=loss_out)
+        torch.cuda.synchronize()
+        losses.append(loss_out.cpu().numpy().astype(np.float64).copy())
+        alphas.append(ctx.get_alpha())
+    state, outs = oracle_steps(w, nets, buf, n_steps, start, inserts)
+    assert len({round(o["alpha"], 6) for o in outs}) == n_steps          # alpha really moves
+    rtol = {"fp64": 1e-7, "fp32": 2e-4, "bf16": 2e-2}[precision]
+    arel = {"fp64": 1e-7, "fp32": 1e-5, "bf16": 1e-3}[precision]
+    for got, ref, a in zip(losses, outs, alphas):
+        np.testing.assert_allclose(got[4:6], [ref["actor_loss"], ref["logpi_mean"]], rtol=rtol, atol=1e-6 + rtol * 1e-2)
+        assert a == pytest.approx(ref["alpha_next"], rel=arel)
+    if precision != "bf16":
+        for gl, rl in zip(ctx.network("pi"), state.nets["pi"]):
+            for k in rl:
+                if precision == "fp64":
+                    np.testing.assert_allclose(gl[k], rl[k], rtol=1e-9, atol=1e-12)
+                else:
+                    err = np.abs(gl[k] - rl[k])
+                    assert np.mean(err <= 1e-3 * w.lr_actor + 1e-7) > 0.98, k
+    assert ctx.sync_status() == (0, 0)
+    ctx.rebind()                 # binding the parameters again resets the tuned coefficient
+    assert ctx.get_alpha() == pytest.approx(w.alpha, rel=1e-7)
+
+
+def test_alpha_is_fixed_without_autotune():
+    w = small(B=32)
+    ctx, _, _ = setup(w, n=40)
+    for _ in range(2):
+        ctx.update_step(*(torch.from_numpy(x).to(ctx.device) for x in workload.buffer_contents(w, n=1, seed_offset=3)))
+    assert ctx.get_alpha() == np.float32(w.alpha)
+
+
 def test_nonfinite_loss_sets_status():
     w = small(B=32)
     ctx, _, _ = setup(w, n=40)
@@ -107,7 +166,10 @@ def test_bad_sizes_and_configs_are_rejected():
     assert e.value.code == api.E_SHAPE
     h = ctypes.c_void_p()
     for bad in (api.make_config(w, gamma=1.0), api.make_config(w, temperature=0.0),
-                api.make_config(w, layers=0), api.make_config(w, offset_min=2)):
+                api.make_config(w, layers=0), api.make_config(w, offset_min=2),
+                api.make_config(w, alpha_autotune=1, alpha=0.0),
+                api.make_config(w, alpha_autotune=1, target_entropy=float("nan")),
+                api.make_config(w, alpha_autotune=2)):
         assert api.lib().crl_create(ctypes.byref(bad), ctypes.byref(h)) == api.E_INVALID_ARG
         assert h.value is None
     cfg = api.make_config(w)

@@ -66,6 +66,7 @@ def run_and_compare(ws, precision, path, grouped, steps=4, check=None):
                 b = ctx.store[net][which].cpu().numpy()
                 np.testing.assert_array_equal(a, b, err_msg=f"agent {i} {net} {which}")
         assert sw.agents[i].get_step() == ctx.get_step() == steps
+        assert sw.agents[i].get_alpha() == ctx.get_alpha()
     sw.close()
 
 
@@ -79,6 +80,12 @@ def test_sequential_sweep_matches_single_agents_fp32():
 
 def test_sequential_bf16_sweep_matches_single_agents():
     run_and_compare(uneven_agents()[:2], "bf16", "fused", grouped=False, steps=3)
+
+
+def test_grouped_sweep_with_alpha_autotune():
+    """Agents that tune their entropy coefficient (one of them with a fixed one)."""
+    ws = [w.with_(alpha_autotune=(i != 2), lr_alpha=0.05, target_entropy=-2.0 - i) for i, w in enumerate(uneven_agents())]
+    run_and_compare(ws, "bf16", "fused", grouped=True, steps=3)
 
 
 def test_grouped_sweep_of_32_agents_sampled():
