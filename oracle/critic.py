@@ -31,12 +31,43 @@ C6  The logsumexp penalty is not defined in the paper.  Reading: the mean
     ("row"); "col" uses c_j = LSE_i F_ij; "both" averages the two.
 C7  The L2 gradient is undefined where phi_i = psi_j; the subgradient 0 is
     taken there (distances below 1e-12).
+
+The other objectives of App. A.2 and §5.2 (``critic_loss``, ``critic_grad_F``)
+------------------------------------------------------------------------------
+C8  FlatNCE (App. A.2): S_i = sum_j exp(F_ij - F_ii) over the whole batch
+    (j = i included, as printed); the forward direction anchors on (s_i, a_i)
+    and sums over goals j, the backward direction anchors on g_i and sums over
+    state-actions j.  The printed loss -sum_i log(S_i / detach S_i) has the
+    value 0 (it is reported as 0), and the printed leading minus would make
+    its gradient the negated InfoNCE gradient, i.e. training would ascend
+    InfoNCE, at odds with §5.2's report that FlatNCE trains about as well as
+    the InfoNCE objectives.  Reading: the gradient is that of +mean_i log S_i
+    (the minus is a sign slip); because the j = i term of S_i is the constant
+    1, this gradient equals InfoNCE's of the same direction.
+C9  Forward-backward (App. A.2, Monte Carlo form): the second sum of the
+    printed formula runs inside the sum over i, so
+    L_FB = mean_i [ -exp(F_ii) + 1/(2(B - 1)) sum_{j != i} exp(F_ij)^2 ],
+    defined for B >= 2.
+C10 DPO, IPO, SPPO (App. A.2): the double sums over (i, j) run over all B^2
+    pairs, j = i included as printed, and are averaged over the pairs (the
+    mean of reading C4 applied to both sums).  For SPPO the (F_ii - 1)^2 term
+    sits inside the sum over j, so it enters with weight 1 / B per anchor.
+C11 NCE-binary (§5.2 names it as the objective originally proposed for CRL;
+    App. A.2 does not define it).  Reading: binary cross-entropy of sigma(F_ij)
+    against the label [i = j] (the positive on the diagonal, every other pair
+    a negative), averaged over the B^2 pairs.
+C12 The logsumexp penalty (reading C6) is added to every objective (§5.2
+    applies the 0.1 regulariser to each objective).  The reported parts keep
+    InfoNCE's forward and backward values as diagnostics for every objective;
+    "contrastive" is the chosen objective's value and total = contrastive +
+    penalty.
 """
 
 import numpy as np
 
 ENERGIES = ("l2", "dot", "cos", "l1", "l2sq")
 LOSSES = ("fwd", "bwd", "sym")
+OBJECTIVES = LOSSES + ("flatnce_fwd", "flatnce_bwd", "fb", "dpo", "ipo", "sppo", "nce_binary")
 
 
 def energy_matrix(phi, psi, energy="l2", tau=1.0):
@@ -145,6 +176,114 @@ def infonce_grad_F(F, loss="sym", sym_reduction="mean", beta=0.1, penalty_axis="
     G = wf * (P - eye) + wb * (Q - eye)
     G = G + 2.0 * beta * (pr * r[:, None] * P + pc * c[None, :] * Q)
     return G / B
+
+
+def sigmoid(x):
+    """sigma(x) = 1 / (1 + exp(-x)), as exp(-log(1 + exp(-x))) without overflow."""
+    return np.exp(-np.logaddexp(0.0, -np.asarray(x, dtype=np.float64)))
+
+
+def neg_log_sigmoid(x):
+    """-log sigma(x) = log(1 + exp(-x)), without overflow."""
+    return np.logaddexp(0.0, -np.asarray(x, dtype=np.float64))
+
+
+def objective_value(F, loss):
+    """The value of an objective outside the InfoNCE family (App. A.2; C8-C11)."""
+    F = np.asarray(F, dtype=np.float64)
+    B = F.shape[0]
+    d = np.diagonal(F)
+    if loss in ("flatnce_fwd", "flatnce_bwd"):
+        # S_i over goals j (fwd) or over state-actions j (bwd); log(S_i / detach S_i)
+        E = F - d[:, None] if loss == "flatnce_fwd" else F.T - d[:, None]
+        S = np.exp(E).sum(axis=1)
+        S_detached = S.copy()
+        return float(-np.mean(np.log(S / S_detached)))
+    if loss == "fb":
+        if B < 2:
+            raise ValueError("the forward-backward objective needs B >= 2")
+        off = ~np.eye(B, dtype=bool)
+        neg = np.where(off, np.exp(F) ** 2, 0.0).sum(axis=1) / (2.0 * (B - 1))
+        return float(np.mean(-np.exp(d) + neg))
+    if loss == "dpo":
+        delta = d[:, None] - F                               # F(s_i, a_i, g_i) - F(s_i, a_i, g_j)
+        return float(np.mean(neg_log_sigmoid(delta)))
+    if loss == "ipo":
+        delta = d[:, None] - F
+        return float(np.mean((delta - 1.0) ** 2))
+    if loss == "sppo":
+        pos = np.broadcast_to(d[:, None], F.shape)
+        return float(np.mean((pos - 1.0) ** 2 + (F + 1.0) ** 2))
+    if loss == "nce_binary":
+        y = np.eye(B)
+        # -log sigma(F) for the positives, -log(1 - sigma(F)) = -log sigma(-F) for the negatives
+        return float(np.mean(y * neg_log_sigmoid(F) + (1.0 - y) * neg_log_sigmoid(-F)))
+    raise ValueError(loss)
+
+
+def objective_grad_F(F, loss):
+    """dL/dF [B][B] of ``objective_value`` (the gradient of reading C8 for FlatNCE)."""
+    F = np.asarray(F, dtype=np.float64)
+    B = F.shape[0]
+    d = np.diagonal(F)
+    eye = np.eye(B)
+    if loss in ("flatnce_fwd", "flatnce_bwd"):
+        # mean_i log S_i with S_i = sum_j exp(E_ij), E_ij = F_ij - F_ii (fwd): dS_i/dF_ij = exp(E_ij)
+        # for j != i, dS_i/dF_ii = -sum_{j != i} exp(E_ij) (the j = i term is constant).
+        E = F - d[:, None] if loss == "flatnce_fwd" else F.T - d[:, None]
+        W = np.exp(E) / np.exp(E).sum(axis=1, keepdims=True)
+        Woff = W * (1.0 - eye)
+        G = (Woff - np.diag(Woff.sum(axis=1))) / B
+        return G if loss == "flatnce_fwd" else G.T
+    if loss == "fb":
+        G = np.exp(2.0 * F) * (1.0 - eye) / (B * (B - 1.0))
+        return G - np.diag(np.exp(d)) / B
+    if loss in ("dpo", "ipo"):
+        delta = d[:, None] - F
+        # dL/d(delta_ij) / B^2; delta_ij rises with F_ii and falls with F_ij
+        h = -sigmoid(-delta) if loss == "dpo" else 2.0 * (delta - 1.0)
+        h = h / B ** 2
+        return -h + np.diag(h.sum(axis=1))
+    if loss == "sppo":
+        return 2.0 * (F + 1.0) / B ** 2 + np.diag(2.0 * (d - 1.0)) / B
+    if loss == "nce_binary":
+        return (sigmoid(F) - eye) / B ** 2
+    raise ValueError(loss)
+
+
+def critic_loss(F, loss="sym", sym_reduction="mean", beta=0.1, penalty_axis="row"):
+    """Loss parts of any objective of App. A.2 / §5.2 plus the penalty (C4-C12).
+
+    Same keys as ``infonce_loss``; for the objectives outside the InfoNCE family
+    "fwd" / "bwd" stay InfoNCE's values (diagnostics) and "contrastive" is the
+    objective's value.
+    """
+    if loss in LOSSES:
+        return infonce_loss(F, loss, sym_reduction, beta, penalty_axis)
+    parts = infonce_loss(F, "fwd", sym_reduction, beta, penalty_axis)
+    value = objective_value(F, loss)
+    parts["contrastive"] = value
+    parts["total"] = value + parts["penalty"]
+    return parts
+
+
+def penalty_grad_F(F, beta, penalty_axis):
+    """dL/dF of beta * (pr mean r^2 + pc mean c^2) (reading C6)."""
+    F = np.asarray(F, dtype=np.float64)
+    B = F.shape[0]
+    r = logsumexp(F, axis=1)
+    c = logsumexp(F, axis=0)
+    pr, pc = penalty_weights(penalty_axis)
+    P = np.exp(F - r[:, None])
+    Q = np.exp(F - c[None, :])
+    return 2.0 * beta * (pr * r[:, None] * P + pc * c[None, :] * Q) / B
+
+
+def critic_grad_F(F, loss="sym", sym_reduction="mean", beta=0.1, penalty_axis="row"):
+    """dL/dF of ``critic_loss``'s total."""
+    if loss in LOSSES:
+        return infonce_grad_F(F, loss, sym_reduction, beta, penalty_axis)
+    return objective_grad_F(F, loss) + penalty_grad_F(F, beta, penalty_axis)
 
 
 def energy_backward(phi, psi, G, energy="l2", tau=1.0):

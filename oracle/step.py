@@ -24,8 +24,8 @@ def critic_loss_and_grad(phi_net, psi_net, s, a, g, energy="l2", tau=1.0, loss="
     phi, cphi = mlp.forward(phi_net, x)
     psi, cpsi = mlp.forward(psi_net, np.asarray(g, dtype=np.float64))
     F = critic.energy_matrix(phi, psi, energy, tau)
-    parts = critic.infonce_loss(F, loss, sym_reduction, beta, penalty_axis)
-    G = critic.infonce_grad_F(F, loss, sym_reduction, beta, penalty_axis)
+    parts = critic.critic_loss(F, loss, sym_reduction, beta, penalty_axis)
+    G = critic.critic_grad_F(F, loss, sym_reduction, beta, penalty_axis)
     dphi, dpsi = critic.energy_backward(phi, psi, G, energy, tau)
     gphi, _ = mlp.backward(phi_net, cphi, dphi)
     gpsi, _ = mlp.backward(psi_net, cpsi, dpsi)
