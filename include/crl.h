@@ -70,6 +70,31 @@ extern "C" {
 #define CRL_LOSS_FWD 0
 #define CRL_LOSS_BWD 1
 #define CRL_LOSS_SYM 2
+/* The other contrastive objectives of App. A.2 / §5.2, over F_ij = f(s_i, a_i,
+ * g_j) / temperature with the positives on the diagonal; each also takes the
+ * logsumexp penalty (§5.2 adds it to every objective).
+ *   FLATNCE_FWD / _BWD: S_i = sum_j exp(F_ij - F_ii) over goals j (FWD) or
+ *     S_i = sum_j exp(F_ji - F_ii) over state-actions j (BWD), j = i included;
+ *     the loss log(S_i / detach S_i) has the value 0 and (reading: the printed
+ *     leading minus is a sign slip) the gradient of mean_i log S_i, which equals
+ *     InfoNCE's of the same direction.
+ *   FB: Monte Carlo forward-backward, mean_i [-exp(F_ii) + sum_{j != i}
+ *     exp(F_ij)^2 / (2 (B - 1))]; needs B >= 2 (CRL_E_SHAPE otherwise).
+ *   DPO: mean over all B^2 pairs of -log sigma(F_ii - F_ij).
+ *   IPO: mean over all pairs of (F_ii - F_ij - 1)^2.
+ *   SPPO: mean over all pairs of (F_ii - 1)^2 + (F_ij + 1)^2.
+ *   NCE_BINARY (named in §5.2, not defined there; reading: binary
+ *     cross-entropy of sigma(F_ij) against the label [i = j], mean over pairs).
+ * For these, loss4 = {objective + penalty, InfoNCE forward value, InfoNCE
+ * backward value, penalty}: the InfoNCE values are diagnostics.  The fused
+ * path (CRL_PATH_FUSED) takes the InfoNCE directions only. */
+#define CRL_LOSS_FLATNCE_FWD 3
+#define CRL_LOSS_FLATNCE_BWD 4
+#define CRL_LOSS_FB 5
+#define CRL_LOSS_DPO 6
+#define CRL_LOSS_IPO 7
+#define CRL_LOSS_SPPO 8
+#define CRL_LOSS_NCE_BINARY 9
 /* symmetric reduction: mean of the two directions, or their sum (App. A.2) */
 #define CRL_SYM_MEAN 0
 #define CRL_SYM_SUM 1

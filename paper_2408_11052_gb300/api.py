@@ -21,7 +21,8 @@ E_INVALID_ARG, E_SHAPE, E_BUFFER_EMPTY, E_CUDA, E_NONFINITE, E_TIMEOUT, E_NOT_BO
     -1, -2, -3, -4, -5, -6, -7, -8
 STATUS_NONFINITE, STATUS_BAD_INDEX, STATUS_TIMEOUT = 1, 2, 4
 ENERGY = {"l2": 0, "dot": 1, "cos": 2, "l1": 3, "l2sq": 4}
-LOSS = {"fwd": 0, "bwd": 1, "sym": 2}
+LOSS = {"fwd": 0, "bwd": 1, "sym": 2, "flatnce_fwd": 3, "flatnce_bwd": 4, "fb": 5, "dpo": 6, "ipo": 7, "sppo": 8,
+        "nce_binary": 9}
 SYM = {"mean": 0, "sum": 1}
 PENALTY = {"row": 0, "col": 1, "both": 2}
 PREC = {"fp32": 0, "bf16": 1, "fp64": 2}

@@ -77,7 +77,8 @@ void validate_config(const crl_config& c) {
   CRL_REQUIRE(!c.alpha_autotune || (c.alpha > 0.f && std::isfinite(c.target_entropy) && c.lr_alpha >= 0.f),
               CRL_E_INVALID_ARG, "alpha_autotune needs alpha > 0, a finite target_entropy and lr_alpha >= 0");
   CRL_REQUIRE(c.energy >= CRL_ENERGY_L2 && c.energy <= CRL_ENERGY_L2SQ, CRL_E_INVALID_ARG, "unknown energy");
-  CRL_REQUIRE(c.loss >= CRL_LOSS_FWD && c.loss <= CRL_LOSS_SYM, CRL_E_INVALID_ARG, "unknown loss");
+  CRL_REQUIRE(c.loss >= CRL_LOSS_FWD && c.loss <= CRL_LOSS_NCE_BINARY, CRL_E_INVALID_ARG, "unknown loss");
+  CRL_REQUIRE(c.loss != CRL_LOSS_FB || c.B >= 2, CRL_E_INVALID_ARG, "the forward-backward objective needs B >= 2");
   CRL_REQUIRE(c.sym_reduction == CRL_SYM_MEAN || c.sym_reduction == CRL_SYM_SUM, CRL_E_INVALID_ARG,
               "unknown sym_reduction");
   CRL_REQUIRE(c.penalty_axis >= CRL_PENALTY_ROW && c.penalty_axis <= CRL_PENALTY_BOTH, CRL_E_INVALID_ARG,
@@ -753,6 +754,7 @@ int crl_critic_step(crl_ctx* ctx, const float* s, const float* a, const float* g
     CRL_REQUIRE(ctx->bound, CRL_E_NOT_BOUND, "crl_bind_params has not been called");
     CRL_REQUIRE(s && a && g, CRL_E_INVALID_ARG, "s, a and g must be non-null");
     CRL_REQUIRE(B >= 1 && B <= ctx->cfg.B, CRL_E_SHAPE, "B must lie in [1, cfg.B]");
+    CRL_REQUIRE(ctx->cfg.loss != CRL_LOSS_FB || B >= 2, CRL_E_SHAPE, "the forward-backward objective needs B >= 2");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (ctx->cfg.precision == CRL_PREC_FP64) critic_impl<double>(ctx, s, a, g, B, apply_update, st);
     else if (ctx->bf16) critic_impl_bf16(ctx, s, a, g, B, apply_update, st);
@@ -1007,7 +1009,7 @@ namespace {
 LossSpec checked_loss(const crl_loss_desc* d) {
   CRL_REQUIRE(d, CRL_E_INVALID_ARG, "null descriptor");
   CRL_REQUIRE(d->energy >= CRL_ENERGY_L2 && d->energy <= CRL_ENERGY_L2SQ, CRL_E_INVALID_ARG, "unknown energy");
-  CRL_REQUIRE(d->loss >= CRL_LOSS_FWD && d->loss <= CRL_LOSS_SYM, CRL_E_INVALID_ARG, "unknown loss");
+  CRL_REQUIRE(d->loss >= CRL_LOSS_FWD && d->loss <= CRL_LOSS_NCE_BINARY, CRL_E_INVALID_ARG, "unknown loss");
   CRL_REQUIRE(d->sym_reduction == CRL_SYM_MEAN || d->sym_reduction == CRL_SYM_SUM, CRL_E_INVALID_ARG,
               "unknown sym_reduction");
   CRL_REQUIRE(d->penalty_axis >= CRL_PENALTY_ROW && d->penalty_axis <= CRL_PENALTY_BOTH, CRL_E_INVALID_ARG,
@@ -1043,6 +1045,7 @@ int crl_infonce_forward(const crl_loss_desc* d, const void* phi, const void* psi
                 "bad argument");
     CRL_REQUIRE(ws_bytes >= infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path), CRL_E_SHAPE,
                 "workspace too small");
+    CRL_REQUIRE(ls.loss != CRL_LOSS_FB || B >= 2, CRL_E_SHAPE, "the forward-backward objective needs B >= 2");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (d->dtype == CRL_PREC_FP64)
       infonce_forward<double>(ls, static_cast<const double*>(phi), static_cast<const double*>(psi), B, R,
@@ -1065,6 +1068,7 @@ int crl_infonce_backward(const crl_loss_desc* d, const void* phi, const void* ps
                 "bad argument");
     CRL_REQUIRE(ws_bytes >= infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path), CRL_E_SHAPE,
                 "workspace too small");
+    CRL_REQUIRE(ls.loss != CRL_LOSS_FB || B >= 2, CRL_E_SHAPE, "the forward-backward objective needs B >= 2");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (d->dtype == CRL_PREC_FP64)
       infonce_backward<double>(ls, static_cast<const double*>(phi), static_cast<const double*>(psi), B, R,

@@ -19,6 +19,19 @@
 //   cos:  the dot form on x = phi/|phi|, then dphi = (dx - x <x, dx>) / |phi|.
 //   L1:   H = G / tau,  dphi_ik = -sum_j H_ij sign(phi_ik - psi_jk),
 //                       dpsi_jk = -sum_i H_ij sign(psi_jk - phi_ik)   (sign(0) = 0)
+//
+// The other objectives of App. A.2 / §5.2 (d_i = F_ii, s = sigma, sp = softplus,
+// all pair sums over j = 1..B):
+//   FlatNCE fwd / bwd: value 0, dL/dF as InfoNCE fwd / bwd (wf or wb = 1).
+//   FB:   value mean_i [-e^{d_i} + sum_{j != i} e^{2 F_ij} / (2 (B - 1))];
+//         dL/dF_ij = e^{2 F_ij} / (B (B - 1)) (j != i), -e^{d_i} / B (j = i).
+//   DPO:  value sum_ij sp(F_ij - d_i) / B^2;  e_ij = s(F_ij - d_i) / B^2.
+//   IPO:  value sum_ij (d_i - F_ij - 1)^2 / B^2;  e_ij = -2 (d_i - F_ij - 1) / B^2.
+//         For both, dL/dF_ij = e_ij - [i = j] k_i with k_i = sum_j e_ij.
+//   SPPO: value sum_i (d_i - 1)^2 / B + sum_ij (F_ij + 1)^2 / B^2;
+//         dL/dF_ij = 2 (F_ij + 1) / B^2 + [i = j] 2 (d_i - 1) / B.
+//   NCE-binary: value sum_ij (sp(F_ij) - [i = j] F_ij) / B^2;  dL/dF_ij = (s(F_ij) - [i = j]) / B^2.
+// One warp per row gives d_i, the row's share of the value and k_i.
 #include <algorithm>
 
 #include "common.cuh"
@@ -37,6 +50,9 @@ struct PlainWs {
   T* csum;    // [B]
   T* inx;     // [B] 1/|phi_i|
   T* iny;     // [B] 1/|psi_j|
+  T* dg;      // [B] F_ii (objectives outside InfoNCE)
+  T* ov;      // [B] row i's share of the objective's value
+  T* kd;      // [B] k_i of DPO / IPO
   T* xh;      // [B][R] phi / |phi|
   T* yh;      // [B][R] psi / |psi|
 };
@@ -54,6 +70,12 @@ PlainWs<T> carve_plain(int B, int R, void* ws) {
   w.inx = p;
   p += B;
   w.iny = p;
+  p += B;
+  w.dg = p;
+  p += B;
+  w.ov = p;
+  p += B;
+  w.kd = p;
   p += B;
   w.xh = p;
   p += (size_t)B * R;
@@ -171,44 +193,117 @@ __global__ void __launch_bounds__(256) col_sum_kernel(int B, const T* __restrict
   out[j] = s;
 }
 
+// wf, wb: weights of the InfoNCE directions in the loss and its gradient (FlatNCE
+// takes InfoNCE's gradient); obj: the loss code.
 struct DirWeights {
   double wf, wb, pr, pc;
+  int obj;
 };
 inline DirWeights weights(const LossSpec& ls) {
-  DirWeights w{0, 0, 0, 0};
-  if (ls.loss == CRL_LOSS_FWD) w.wf = 1;
-  else if (ls.loss == CRL_LOSS_BWD) w.wb = 1;
-  else w.wf = w.wb = (ls.sym_reduction == CRL_SYM_SUM) ? 1.0 : 0.5;
+  DirWeights w{0, 0, 0, 0, ls.loss};
+  if (ls.loss == CRL_LOSS_FWD || ls.loss == CRL_LOSS_FLATNCE_FWD) w.wf = 1;
+  else if (ls.loss == CRL_LOSS_BWD || ls.loss == CRL_LOSS_FLATNCE_BWD) w.wb = 1;
+  else if (ls.loss == CRL_LOSS_SYM) w.wf = w.wb = (ls.sym_reduction == CRL_SYM_SUM) ? 1.0 : 0.5;
   if (ls.penalty_axis == CRL_PENALTY_ROW) w.pr = 1;
   else if (ls.penalty_axis == CRL_PENALTY_COL) w.pc = 1;
   else w.pr = w.pc = 0.5;
   return w;
 }
 
+template <typename T>
+__device__ __forceinline__ T sigmoid(T x) {
+  // 1 / (1 + e^{-x}) without overflow: e^{x} / (1 + e^{x}) for x < 0
+  const T e = dev_exp(-fabs(x));
+  return x >= T(0) ? T(1) / (T(1) + e) : e / (T(1) + e);
+}
+
+// Objectives outside InfoNCE: d_i, row i's share of the value and k_i (see the
+// header comment).  One warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) objective_rows_kernel(int B, const T* __restrict__ F, int obj,
+                                                            T* __restrict__ dg, T* __restrict__ ov,
+                                                            T* __restrict__ kd) {
+  pdl_enter();
+  const int lane = threadIdx.x % kWarp;
+  const int row = blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  if (row >= B) return;
+  const T* f = F + (size_t)row * B;
+  const T d = f[row];
+  T v = 0, k = 0;
+  for (int j = lane; j < B; j += kWarp) {
+    const T x = f[j];
+    switch (obj) {
+      case CRL_LOSS_FB:
+        if (j != row) v += dev_exp(T(2) * x);
+        break;
+      case CRL_LOSS_DPO:
+        v += softplus(x - d);
+        k += sigmoid(x - d);
+        break;
+      case CRL_LOSS_IPO: {
+        const T u = d - x - T(1);
+        v += u * u;
+        k -= T(2) * u;
+        break;
+      }
+      case CRL_LOSS_SPPO:
+        v += (x + T(1)) * (x + T(1));
+        break;
+      case CRL_LOSS_NCE_BINARY:
+        v += softplus(x);
+        break;
+      default: break;
+    }
+  }
+  v = warp_sum(v);
+  k = warp_sum(k);
+  if (lane != 0) return;
+  const T bb = T(B) * T(B);
+  T val = 0;
+  switch (obj) {
+    case CRL_LOSS_FB: val = (-dev_exp(d) + v / (T(2) * T(B - 1))) / T(B); break;
+    case CRL_LOSS_DPO:
+    case CRL_LOSS_IPO: val = v / bb; break;
+    case CRL_LOSS_SPPO: val = (T(B) * (d - T(1)) * (d - T(1)) + v) / bb; break;
+    case CRL_LOSS_NCE_BINARY: val = (v - d) / bb; break;
+    default: break;
+  }
+  dg[row] = d;
+  ov[row] = val;
+  kd[row] = k / bb;
+}
+
+inline bool has_rows_pass(int obj) { return obj >= CRL_LOSS_FB; }
+
 // Loss parts from the diagonal of F and the row / column logsumexp.  One block.
+// ov: per-row objective values (objectives outside InfoNCE; FlatNCE: null, value 0).
 template <typename T>
 __global__ void __launch_bounds__(1024) loss_kernel(int B, const T* __restrict__ F, int ldf, const T* __restrict__ r,
-                                                   const T* __restrict__ c, DirWeights w, double beta,
-                                                   T* __restrict__ loss4, unsigned* status, int* t_bump) {
+                                                   const T* __restrict__ c, const T* __restrict__ ov, DirWeights w,
+                                                   double beta, T* __restrict__ loss4, unsigned* status,
+                                                   int* t_bump) {
   pdl_enter();
   __shared__ T sm[32];
-  T a_f = 0, a_b = 0, a_r2 = 0, a_c2 = 0;
+  T a_f = 0, a_b = 0, a_r2 = 0, a_c2 = 0, a_o = 0;
   for (int i = threadIdx.x; i < B; i += blockDim.x) {
     const T d = F[(size_t)i * ldf + i];
     a_f += r[i] - d;
     a_b += c[i] - d;
     a_r2 += r[i] * r[i];
     a_c2 += c[i] * c[i];
+    if (ov) a_o += ov[i];
   }
   a_f = block_sum(a_f, sm);
   a_b = block_sum(a_b, sm);
   a_r2 = block_sum(a_r2, sm);
   a_c2 = block_sum(a_c2, sm);
+  a_o = block_sum(a_o, sm);
   if (threadIdx.x == 0) {
     const T inv = T(1) / T(B);
     const T lf = a_f * inv, lb = a_b * inv;
     const T pen = T(beta) * (T(w.pr) * a_r2 * inv + T(w.pc) * a_c2 * inv);
-    const T total = T(w.wf) * lf + T(w.wb) * lb + pen;
+    const bool info = w.obj <= CRL_LOSS_SYM;
+    const T total = (info ? T(w.wf) * lf + T(w.wb) * lb : a_o) + pen;
     loss4[0] = total;
     loss4[1] = lf;
     loss4[2] = lb;
@@ -219,13 +314,16 @@ __global__ void __launch_bounds__(1024) loss_kernel(int B, const T* __restrict__
 }
 
 // F -> H in place (see the header comment).
+// dg, kd: F_ii and k_i from objective_rows_kernel (objectives outside InfoNCE).
 template <typename T>
 __global__ void __launch_bounds__(256) grad_coeff_kernel(int B, T* __restrict__ F, const T* __restrict__ r,
-                                                        const T* __restrict__ c, DirWeights w, double beta,
+                                                        const T* __restrict__ c, const T* __restrict__ dg,
+                                                        const T* __restrict__ kd, DirWeights w, double beta,
                                                         double dtotal, int energy, double tau) {
   pdl_enter();
   const size_t n = (size_t)B * B;
   const T scale = T(dtotal / B);
+  const T bb = T(B) * T(B);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / B), j = (int)(e % B);
     const T f = F[e];
@@ -234,6 +332,17 @@ __global__ void __launch_bounds__(256) grad_coeff_kernel(int B, T* __restrict__ 
     const T dlt = (i == j) ? T(1) : T(0);
     T g = T(w.wf) * (P - dlt) + T(w.wb) * (Q - dlt) + T(2.0 * beta) * (T(w.pr) * r[i] * P + T(w.pc) * c[j] * Q);
     g *= scale;
+    if (w.obj >= CRL_LOSS_FB) {
+      T o = 0;
+      switch (w.obj) {
+        case CRL_LOSS_FB: o = (i == j) ? -dev_exp(f) / T(B) : dev_exp(T(2) * f) / (T(B) * T(B - 1)); break;
+        case CRL_LOSS_DPO: o = sigmoid(f - dg[i]) / bb - dlt * kd[i]; break;
+        case CRL_LOSS_IPO: o = T(-2) * (dg[i] - f - T(1)) / bb - dlt * kd[i]; break;
+        case CRL_LOSS_SPPO: o = T(2) * (f + T(1)) / bb + dlt * T(2) * (f - T(1)) / T(B); break;
+        default: o = (sigmoid(f) - dlt) / bb; break;  // NCE-binary
+      }
+      g += T(dtotal) * o;
+    }
     T h;
     switch (energy) {
       case CRL_ENERGY_L2: {
@@ -324,7 +433,7 @@ __global__ void __launch_bounds__(256) l1_grad_kernel(int B, int R, const T* __r
 size_t infonce_ws_bytes(const LossSpec& ls, int B, int R, size_t elem, int path) {
   (void)ls;
   (void)path;
-  return ((size_t)B * B + 4 * (size_t)B + 2 * (size_t)B * R) * elem;
+  return ((size_t)B * B + 7 * (size_t)B + 2 * (size_t)B * R) * elem;
 }
 
 template <typename T>
@@ -348,7 +457,16 @@ void infonce_forward(const LossSpec& ls, const T* phi, const T* psi, int B, int 
   }
   { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(row_lse_kernel<T>, dim3(nb), dim3(256), 0, st, B, w.F, row_lse); }
   { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(col_lse_kernel<T>, dim3(ceil_div(B, 32)), dim3(256), 0, st, B, w.F, col_lse); }
-  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(loss_kernel<T>, dim3(1), dim3(1024), 0, st, B, w.F, B, row_lse, col_lse, weights(ls), ls.beta, loss4, status, t_bump); }
+  const bool rows = has_rows_pass(ls.loss);
+  if (rows) {
+    TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0);
+    launch_k(objective_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, (const T*)w.F, ls.loss, w.dg, w.ov, w.kd);
+  }
+  {
+    TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0);
+    launch_k(loss_kernel<T>, dim3(1), dim3(1024), 0, st, B, (const T*)w.F, B, (const T*)row_lse, (const T*)col_lse,
+             rows ? (const T*)w.ov : nullptr, weights(ls), ls.beta, loss4, status, t_bump);
+  }
 }
 
 template <typename T>
@@ -373,9 +491,16 @@ void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int
       default: gemm<T, InnerOp::kMul>(B, B, R, la, lb, ep, st, CRL_TRACE_ENERGY); break;
     }
   }
+  if (has_rows_pass(ls.loss)) {
+    TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0);
+    launch_k(objective_rows_kernel<T>, dim3(nb), dim3(256), 0, st, B, (const T*)w.F, ls.loss, w.dg, w.ov, w.kd);
+  }
   const int ge = (int)std::min<int64_t>(ceil_div((int64_t)B * B, 256), 152 * 16);
-  { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(grad_coeff_kernel<T>, dim3(ge), dim3(256), 0, st, B, w.F, row_lse, col_lse, weights(ls), ls.beta, dtotal, ls.energy,
-                                           ls.tau); }
+  {
+    TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0);
+    launch_k(grad_coeff_kernel<T>, dim3(ge), dim3(256), 0, st, B, w.F, row_lse, col_lse, (const T*)w.dg,
+             (const T*)w.kd, weights(ls), ls.beta, dtotal, ls.energy, ls.tau);
+  }
   const T* H = w.F;
   if (ls.energy == CRL_ENERGY_L2 || ls.energy == CRL_ENERGY_L2SQ) {
     { TraceLaunch tr_(CRL_TRACE_ENERGY, st, 0.0); launch_k(row_sum_kernel<T>, dim3(nb), dim3(256), 0, st, B, H, w.rsum); }

@@ -846,6 +846,10 @@ bool energy_tc_supported(const LossSpec& ls, int B, int R, const char** why) {
     *why = "the fused path has no L1 energy";
     return false;
   }
+  if (ls.loss > CRL_LOSS_SYM) {
+    *why = "the fused path takes the InfoNCE objectives (forward, backward, symmetric) only";
+    return false;
+  }
   if (R % 64 != 0 || R > 256) {
     *why = "the fused path needs repr to be 64, 128, 192 or 256";
     return false;

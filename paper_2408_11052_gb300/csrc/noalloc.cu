@@ -72,7 +72,7 @@ extern "C" int crl_infonce_forward_noalloc(const crl_loss_desc* d, const void* p
     return CRL_E_INVALID_ARG;
   }
   if (d->energy < CRL_ENERGY_L2 || d->energy > CRL_ENERGY_L2SQ || d->loss < CRL_LOSS_FWD ||
-      d->loss > CRL_LOSS_SYM || (d->sym_reduction != CRL_SYM_MEAN && d->sym_reduction != CRL_SYM_SUM) ||
+      d->loss > CRL_LOSS_NCE_BINARY || (d->loss == CRL_LOSS_FB && B < 2) || (d->sym_reduction != CRL_SYM_MEAN && d->sym_reduction != CRL_SYM_SUM) ||
       d->penalty_axis < CRL_PENALTY_ROW || d->penalty_axis > CRL_PENALTY_BOTH || !(d->temperature > 0.f) ||
       d->beta_lse < 0.f) {
     crl::set_thread_error("crl_infonce_forward_noalloc: bad loss descriptor");

@@ -66,6 +66,17 @@ def test_bf16_critic_matches_oracle(energy, layernorm):
     assert ctx.sync_status() == (0, 0)
 
 
+@pytest.mark.parametrize("loss", ["flatnce_fwd", "fb", "dpo", "ipo", "sppo", "nce_binary"])
+def test_bf16_plain_critic_objectives(loss):
+    """The objectives outside InfoNCE on the BF16 plain path (the fused path takes InfoNCE only)."""
+    w = bf16_small(loss=loss)
+    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w)
+    assert abs(got[0] - parts["total"]) <= BF16_LOSS_RTOL * abs(parts["total"])
+    assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
+    assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
+    assert ctx.sync_status() == (0, 0)
+
+
 @pytest.mark.parametrize("B", [8, 64, 136, 256])
 def test_bf16_critic_batch_sizes(B):
     w = bf16_small(B=B, hidden=64, repr=16)

@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2408_11052_gb300 import workload
+from paper_2408_11052_gb300 import api, workload
 
 from parity_helpers import (FP32_GRAD_RTOL, FP32_LOSS_RTOL, FP64_GRAD_RTOL, FP64_LOSS_RTOL, assert_grads_close,
                             assert_scalar_close, hp, pick_step, setup, small)
@@ -64,6 +64,53 @@ def test_critic_ragged_and_degenerate_batches(B):
     if B == 1:
         assert ref[0]["contrastive"] == 0.0       # one sample: the softmax over one entry is 1
     check(ctx, got, ref, "fp32")
+
+
+OBJECTIVES = ["flatnce_fwd", "flatnce_bwd", "fb", "dpo", "ipo", "sppo", "nce_binary"]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("energy", ["l2", "dot"])
+@pytest.mark.parametrize("loss", OBJECTIVES)
+def test_critic_objectives_match_oracle(precision, energy, loss):
+    """The other objectives of App. A.2 / §5.2 with the logsumexp penalty."""
+    w = small(energy=energy, loss=loss)
+    ctx, _, _, got, ref = run_critic(w, precision)
+    check(ctx, got, ref, precision)
+    assert ctx.sync_status() == (0, 0)
+
+
+@pytest.mark.parametrize("B,loss", [(2, "fb"), (65, "dpo"), (129, "ipo"), (63, "sppo"), (1, "nce_binary"),
+                                    (1, "dpo"), (3, "flatnce_bwd")])
+def test_critic_objectives_ragged_and_degenerate_batches(B, loss):
+    w = small(B=B, hidden=33, repr=5, loss=loss)
+    ctx, _, _, got, ref = run_critic(w, "fp32")
+    check(ctx, got, ref, "fp32")
+
+
+def test_forward_backward_objective_needs_two_samples():
+    w = small(B=4, loss="fb")
+    ctx, _, _ = setup(w, n=40)
+    s, a, g, _ = ctx.sample(step=0)
+    with pytest.raises(api.CRLError) as e:
+        ctx.critic_step(s[:1], a[:1], g[:1])
+    assert e.value.code == api.E_SHAPE
+
+
+@pytest.mark.parametrize("direction", ["fwd", "bwd"])
+def test_flatnce_gradient_is_infonce_gradient_on_gpu(direction):
+    """Reading C8: FlatNCE's gradient is InfoNCE's of the same direction (the same
+    coefficients, so bit for bit), and its value is 0: total = penalty."""
+    out = {}
+    for loss in (direction, "flatnce_" + direction):
+        w = small(loss=loss)
+        ctx, _, _, got, _ = run_critic(w, "fp32")
+        out[loss] = (got, {n: ctx.store[n]["grads"].cpu().numpy() for n in ("phi", "psi")})
+    a, b = out[direction], out["flatnce_" + direction]
+    for n in ("phi", "psi"):
+        np.testing.assert_array_equal(a[1][n], b[1][n])
+    assert b[0][0] == b[0][3] and b[0][3] == a[0][3]
+    np.testing.assert_array_equal(a[0][1:], b[0][1:])
 
 
 def test_equal_representations_give_log_B_on_gpu():

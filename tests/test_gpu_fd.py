@@ -26,8 +26,8 @@ def fd_loss_fn(ctx, w, s, a, g, penalty_axis="row"):
     return loss
 
 
-@pytest.mark.parametrize("energy", ["dot", "l2", "l1"])
-@pytest.mark.parametrize("loss", ["fwd", "bwd", "sym"])
+@pytest.mark.parametrize("energy,loss", [(e, l) for e in ("dot", "l2", "l1") for l in ("fwd", "bwd", "sym")] +
+                         [("l2", l) for l in ("fb", "dpo", "ipo", "sppo", "nce_binary")] + [("dot", "dpo")])
 def test_fp64_gradient_against_central_differences(energy, loss):
     w = workload.ANT_AUTOGRAD.with_(energy=energy, loss=loss)
     ctx, _, _ = setup(w, precision="fp64", n=60)
@@ -84,6 +84,11 @@ def test_autograd_functions_gradcheck_fp64():
         for loss in ("fwd", "bwd", "sym"):
             fl = lambda a, b: functional.infonce_loss(a, b, energy, loss, "mean", "both", 0.9, 0.1)[0]
             assert torch.autograd.gradcheck(fl, (phi, psi), eps=1e-6, atol=1e-8, rtol=1e-6)
+    # the other objectives (FlatNCE has the constant value 0, so finite differences do not see its gradient)
+    for energy in ("l2", "dot"):
+        for loss in ("fb", "dpo", "ipo", "sppo", "nce_binary"):
+            fl = lambda a, b: functional.infonce_loss(a, b, energy, loss, "mean", "row", 0.9, 0.1)[0]
+            assert torch.autograd.gradcheck(fl, (phi, psi), eps=1e-6, atol=1e-8, rtol=1e-6), (energy, loss)
 
 
 def test_autograd_functions_fp32_match_oracle():

@@ -88,6 +88,39 @@ def test_update_steps_match_oracle(precision, host_inputs):
     assert ctx.get_step() == start + 3
 
 
+@pytest.mark.parametrize("loss", ["dpo", "fb", "flatnce_bwd"])
+def test_update_steps_with_other_objectives_match_oracle(loss):
+    """Three full FP64 update steps with an objective outside InfoNCE."""
+    w = small(B=48, loss=loss)
+    ctx, nets, buf = setup(w, precision="fp64", n=60)
+    extra = workload.buffer_contents(w, n=3, mean_len=9.0, seed_offset=5)
+    inserts = [tuple(x[i:i + 1] for x in extra) for i in range(3)]
+    start = None
+    for cand in range(0, 48):
+        trial = oracle.relabel.ReplayBuffer(w.E, w.T, w.D, w.A)
+        trial.obs, trial.act, trial.done = buf.obs.copy(), buf.act.copy(), buf.done.copy()
+        if oracle_steps(w, nets, trial, 3, cand, inserts, check_kinks=True) is not None:
+            start = cand
+            break
+    assert start is not None
+    ctx.set_step(start)
+    loss_out = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+    got = []
+    for ins in inserts:
+        ctx.update_step(*(torch.from_numpy(x).to(ctx.device) for x in ins), loss_out=loss_out)
+        got.append(loss_out.cpu().numpy().astype(np.float64).copy())
+    state, outs = oracle_steps(w, nets, buf, 3, start, inserts)
+    for g, ref in zip(got, outs):
+        c = ref["critic"]
+        np.testing.assert_allclose(g[:4], [c["total"], c["fwd"], c["bwd"], c["penalty"]], rtol=1.2e-7, atol=1e-7)
+        np.testing.assert_allclose(g[4:6], [ref["actor_loss"], ref["logpi_mean"]], rtol=1.2e-7, atol=1e-6)
+    for net in ("phi", "psi", "pi"):
+        for gl, rl in zip(ctx.network(net), state.nets[net]):
+            for k in rl:
+                np.testing.assert_allclose(gl[k], rl[k], rtol=1e-9, atol=1e-12)
+    assert ctx.sync_status() == (0, 0)
+
+
 @pytest.mark.parametrize("precision,path", [("fp64", "plain"), ("fp32", "plain"), ("bf16", "plain"),
                                             ("bf16", "fused")])
 def test_alpha_autotune_matches_oracle(precision, path):
