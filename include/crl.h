@@ -86,8 +86,8 @@ extern "C" {
  *   NCE_BINARY (named in §5.2, not defined there; reading: binary
  *     cross-entropy of sigma(F_ij) against the label [i = j], mean over pairs).
  * For these, loss4 = {objective + penalty, InfoNCE forward value, InfoNCE
- * backward value, penalty}: the InfoNCE values are diagnostics.  The fused
- * path (CRL_PATH_FUSED) takes the InfoNCE directions only. */
+ * backward value, penalty}: the InfoNCE values are diagnostics.  Every path
+ * takes every objective. */
 #define CRL_LOSS_FLATNCE_FWD 3
 #define CRL_LOSS_FLATNCE_BWD 4
 #define CRL_LOSS_FB 5

@@ -342,7 +342,7 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     if (e) throw Failure(CRL_E_CUDA, std::string("tensor map: ") + e);
     energy_tc_forward(c->etc, ls, B, loss, rl, cl, c->etc_ws, status, apply ? &c->ctr->t_critic : nullptr, st);
     energy_tc_backward(c->etc, ls, B, P.y, Q.y, rl, cl, 1.0, P.dz[P.layers], P.dzT[P.layers], Q.dz[Q.layers],
-                       Q.dzT[Q.layers], P.Mmax, status, st);
+                       Q.dzT[Q.layers], P.Mmax, c->etc_ws, status, st);
   } else {
     infonce_forward<float>(ls, P.y, Q.y, B, cf.repr, loss, rl, cl, c->ws, CRL_PATH_PLAIN, status,
                            apply ? &c->ctr->t_critic : nullptr, st);

@@ -24,6 +24,16 @@
 //           is the same kernel with the roles of phi and psi (and of r and c)
 //           exchanged.  Both write their result as BF16 dy [B][R] and dy^T
 //           [R][B], the layout the encoder backward consumes.
+//
+// The other objectives of App. A.2 / §5.2 (FlatNCE, forward-backward, DPO, IPO,
+// SPPO, NCE-binary; definitions and readings as in the plain path) ride on the
+// same tiles.  FlatNCE is InfoNCE's gradient with the value 0.  For the rest the
+// forward tile also sums each row's objective terms over its 128 columns
+// (partials merged per row like the logsumexps), and the backward adds the
+// objective's dL/dF_ij to the coefficient tile.  DPO and IPO need the anchor
+// F_ii inside every tile: each forward CTA computes it for its rows from the
+// BF16 operand rows (the same products the MMA sums), and the forward leaves it
+// and k_i (the diagonal coefficient sum_j e_ij) for the backward.
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -47,11 +57,13 @@ struct Weights {
   float wf, wb, pr, pc;
 };
 
+// Weights of the InfoNCE directions (FlatNCE takes InfoNCE's gradient; the
+// other objectives none) and of the penalty axes.
 Weights loss_weights(const LossSpec& ls) {
   Weights w{0, 0, 0, 0};
-  if (ls.loss == CRL_LOSS_FWD) w.wf = 1;
-  else if (ls.loss == CRL_LOSS_BWD) w.wb = 1;
-  else w.wf = w.wb = (ls.sym_reduction == CRL_SYM_SUM) ? 1.f : 0.5f;
+  if (ls.loss == CRL_LOSS_FWD || ls.loss == CRL_LOSS_FLATNCE_FWD) w.wf = 1;
+  else if (ls.loss == CRL_LOSS_BWD || ls.loss == CRL_LOSS_FLATNCE_BWD) w.wb = 1;
+  else if (ls.loss == CRL_LOSS_SYM) w.wf = w.wb = (ls.sym_reduction == CRL_SYM_SUM) ? 1.f : 0.5f;
   if (ls.penalty_axis == CRL_PENALTY_ROW) w.pr = 1;
   else if (ls.penalty_axis == CRL_PENALTY_COL) w.pc = 1;
   else w.pr = w.pc = 0.5f;
@@ -129,10 +141,15 @@ __global__ void __launch_bounds__(1024) prep_kernel(int B, int R, int energy, in
 constexpr int kThreads = 512;
 
 struct FwdArgs {
-  int B, R, energy;
+  int B, R, energy, obj;  // obj: the loss code
   float inv_tau;
   const float* auxX;
   const float* auxY;
+  const bf16* X;   // [B][R] operand rows (the DPO / IPO anchor F_ii)
+  const bf16* Y;
+  float* objpart;  // [nJ][B][2] per-row objective partials over each column tile
+  float* dpre;     // [B] the anchor F_ii of DPO / IPO (written by the J = 0 tiles)
+  float* kd;       // [B] k_i of DPO / IPO (written by the row merges)
   float* rowpart;  // [nJ][B][2]
   float* colpart;  // [nI][B][2]
   float* diag;     // [B]
@@ -145,8 +162,23 @@ struct FwdArgs {
   float* loss4;
   int* t_bump;
   unsigned* tickets;  // [2 n + 1]: per row tile, per column tile, final (zero between launches)
-  float* tile_part;   // [2][n][2]: per row / column tile (sum of (lse - diag), sum of lse^2)
+  float* tile_part;   // [2][n][3]: per row / column tile (sum of (lse - diag), sum of lse^2, objective value)
 };
+
+__device__ __forceinline__ float sigmoidf_fast(float x) { return __frcp_rn(1.f + __expf(-x)); }
+__device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.f) + log1pf(__expf(-fabsf(x))); }
+
+// Row u's share of the objective's value from its merged partials (vp: the sum
+// over j of the objective's pair terms; d: F_uu; see the plain path).
+__device__ __forceinline__ float objective_share(int obj, int B, float vp, float d) {
+  const float bb = (float)B * (float)B;
+  switch (obj) {
+    case CRL_LOSS_FB: return (-__expf(d) + vp / (2.f * (float)(B - 1))) / (float)B;
+    case CRL_LOSS_SPPO: return ((float)B * (d - 1.f) * (d - 1.f) + vp) / bb;
+    case CRL_LOSS_NCE_BINARY: return (vp - d) / bb;
+    default: return vp / bb;  // DPO, IPO
+  }
+}
 
 __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2) {
   if (s2 <= 0.f) return;
@@ -165,8 +197,10 @@ __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2
 __device__ void merge_tile(const FwdArgs& a, int T, int n, bool col) {
   __shared__ float s_red[2][32];
   const int B = a.B;
+  __shared__ float s_obj[32];
   const float* part = col ? a.colpart : a.rowpart;
-  float sd = 0.f, s2 = 0.f;
+  const bool objrows = !col && a.obj >= CRL_LOSS_FB;
+  float sd = 0.f, s2 = 0.f, so = 0.f;
   for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
     const int i = T * kTile + k;
     if (i >= B) continue;
@@ -177,42 +211,60 @@ __device__ void merge_tile(const FwdArgs& a, int T, int n, bool col) {
     }
     const float l = m + __logf(s);
     (col ? a.c_out : a.r_out)[i] = l;
-    sd += l - __ldcg(a.diag + i);
+    const float d = __ldcg(a.diag + i);
+    sd += l - d;
     s2 += l * l;
+    if (objrows) {
+      float vp = 0.f, kp = 0.f;
+      for (int P = 0; P < n; ++P) {
+        const float* p = a.objpart + ((size_t)P * B + i) * 2;
+        vp += __ldcg(p);
+        kp += __ldcg(p + 1);
+      }
+      so += objective_share(a.obj, B, vp, d);
+      if (a.obj == CRL_LOSS_DPO || a.obj == CRL_LOSS_IPO) a.kd[i] = kp / ((float)B * (float)B);
+    }
   }
   sd = warp_sum(sd);
   s2 = warp_sum(s2);
+  so = warp_sum(so);
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   if (lane == 0) {
     s_red[0][w] = sd;
     s_red[1][w] = s2;
+    s_obj[w] = so;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float a0 = 0.f, a1 = 0.f;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
     for (int k = 0; k < (int)(blockDim.x / 32); ++k) {
       a0 += s_red[0][k];
       a1 += s_red[1][k];
+      a2 += s_obj[k];
     }
-    float* tp = a.tile_part + ((size_t)(col ? 1 : 0) * n + T) * 2;
+    float* tp = a.tile_part + ((size_t)(col ? 1 : 0) * n + T) * 3;
     tp[0] = a0;
     tp[1] = a1;
+    tp[2] = a2;
   }
 }
 
 // The loss parts from the 2 n tile partials, added in tile order.  One thread.
 __device__ void finalize_loss(const FwdArgs& a, int n) {
-  float af = 0.f, ar2 = 0.f, ab = 0.f, ac2 = 0.f;
+  float af = 0.f, ar2 = 0.f, ab = 0.f, ac2 = 0.f, ao = 0.f;
   for (int T = 0; T < n; ++T) {
-    af += __ldcg(a.tile_part + 2 * T);
-    ar2 += __ldcg(a.tile_part + 2 * T + 1);
-    ab += __ldcg(a.tile_part + 2 * (n + T));
-    ac2 += __ldcg(a.tile_part + 2 * (n + T) + 1);
+    af += __ldcg(a.tile_part + 3 * T);
+    ar2 += __ldcg(a.tile_part + 3 * T + 1);
+    ao += __ldcg(a.tile_part + 3 * T + 2);
+    ab += __ldcg(a.tile_part + 3 * (n + T));
+    ac2 += __ldcg(a.tile_part + 3 * (n + T) + 1);
   }
   const float inv = 1.f / a.B;
   const float lf = af * inv, lb = ab * inv;
   const float pen = a.beta * (a.w.pr * ar2 * inv + a.w.pc * ac2 * inv);
-  const float total = a.w.wf * lf + a.w.wb * lb + pen;
+  // FlatNCE: value 0; the objectives outside InfoNCE: the merged row shares
+  const float contrastive = a.obj <= CRL_LOSS_SYM ? a.w.wf * lf + a.w.wb * lb : (a.obj >= CRL_LOSS_FB ? ao : 0.f);
+  const float total = contrastive + pen;
   a.loss4[0] = total;
   a.loss4[1] = lf;
   a.loss4[2] = lb;
@@ -233,7 +285,9 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   float* Ft = reinterpret_cast<float*>(smem);  // reused after the MMA: [128][129]
   const size_t opnd = (size_t)2 * nk * 16384, ftile = (size_t)kTile * 129 * 4;
   float* part = reinterpret_cast<float*>(smem + (opnd > ftile ? opnd : ftile));  // [2][4][128] (m, s)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(part + 2 * 4 * kTile);
+  float* opart = part + 2 * 4 * kTile;                                            // [2][4][128] objective
+  float* s_d = opart + 2 * 4 * kTile;                                             // [128] anchor F_ii
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_d + kTile);
   uint64_t* load_bar = bars;
   uint64_t* mma_bar = bars + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
@@ -286,6 +340,32 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
     }
   }
   __syncwarp();
+  const bool anchored = a.obj == CRL_LOSS_DPO || a.obj == CRL_LOSS_IPO;
+  if (anchored) {
+    // the anchor F_ii of this tile's rows while the MMA runs: 4 threads per row,
+    // each R / 4 columns of the BF16 operand rows (8 per 16-byte load)
+    const int rr = tid / 4, part4 = tid % 4, i = i0 + rr;
+    float sxy = 0.f;
+    if (i < a.B) {
+      const int per = a.R / 4;
+      const uint4* xr = reinterpret_cast<const uint4*>(a.X + (size_t)i * a.R + part4 * per);
+      const uint4* yr = reinterpret_cast<const uint4*>(a.Y + (size_t)i * a.R + part4 * per);
+      for (int c = 0; c < per / 8; ++c) {
+        const uint4 xv = xr[c], yv = yr[c];
+        const bf16* xb = reinterpret_cast<const bf16*>(&xv);
+        const bf16* yb = reinterpret_cast<const bf16*>(&yv);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sxy = fmaf(__bfloat162float(xb[e]), __bfloat162float(yb[e]), sxy);
+      }
+    }
+    sxy += __shfl_xor_sync(0xffffffffu, sxy, 1);
+    sxy += __shfl_xor_sync(0xffffffffu, sxy, 2);
+    if (part4 == 0) {
+      const float d = (i < a.B) ? energy_of(a.energy, sxy, a.auxX[i], a.auxY[i], a.inv_tau) : 0.f;
+      s_d[rr] = d;
+      if (J == 0 && i < a.B) a.dpre[i] = d;
+    }
+  }
   const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(mma_bar, 0) ? 1 : 0) != 0;
   tc::fence_after_sync();
   // every warp must agree before the operand smem is reused for the F tile
@@ -316,6 +396,50 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
     }
     part[(0 * 4 + q) * kTile + r] = m;
     part[(1 * 4 + q) * kTile + r] = sum;
+    if (a.obj >= CRL_LOSS_FB) {
+      // this row's objective terms over the thread's 32 columns (v[k] = -inf off the batch)
+      // (one fully unrolled loop per objective keeps v[] in registers)
+      float vp = 0.f, kp = 0.f;
+      const float d = anchored ? s_d[r] : 0.f;
+      const int jn = (i < a.B) ? min(32, a.B - (j0 + q * 32)) : 0;  // valid columns of the 32
+      const int jd = i - (j0 + q * 32);                              // the diagonal's column, if here
+      switch (a.obj) {
+        case CRL_LOSS_FB:
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            if (k < jn && k != jd) vp += __expf(2.f * v[k]);
+          break;
+        case CRL_LOSS_DPO:
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            if (k < jn) {
+              vp += softplusf(v[k] - d);
+              kp += sigmoidf_fast(v[k] - d);
+            }
+          break;
+        case CRL_LOSS_IPO:
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            if (k < jn) {
+              const float t = d - v[k] - 1.f;
+              vp += t * t;
+              kp -= 2.f * t;
+            }
+          break;
+        case CRL_LOSS_SPPO:
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            if (k < jn) vp += (v[k] + 1.f) * (v[k] + 1.f);
+          break;
+        default:  // NCE-binary
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            if (k < jn) vp += softplusf(v[k]);
+          break;
+      }
+      opart[(0 * 4 + q) * kTile + r] = vp;
+      opart[(1 * 4 + q) * kTile + r] = kp;
+    }
   } else if (tid == 0) {
     atomicOr(a.status, CRL_STATUS_TIMEOUT);
   }
@@ -330,6 +454,12 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
         float* rp = a.rowpart + ((size_t)J * a.B + i) * 2;
         rp[0] = m;
         rp[1] = s;
+        if (a.obj >= CRL_LOSS_FB) {
+          // the four column groups in order
+          float* op = a.objpart + ((size_t)J * a.B + i) * 2;
+          op[0] = opart[tid] + opart[kTile + tid] + opart[2 * kTile + tid] + opart[3 * kTile + tid];
+          op[1] = opart[4 * kTile + tid] + opart[5 * kTile + tid] + opart[6 * kTile + tid] + opart[7 * kTile + tid];
+        }
       }
     }
   }
@@ -400,7 +530,11 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant_
 // ---- backward ---------------------------------------------------------------------
 struct BwdArgs {
   int B, R, energy, transposed;  // transposed: own = psi (the column pass)
+  int obj;                       // the loss code
   float inv_tau, beta, scale;    // scale = dtotal / B
+  float dtotal;
+  const float* dpre;             // [B] anchor F_ii of DPO / IPO (from the forward)
+  const float* kd;               // [B] k_i of DPO / IPO (from the forward)
   Weights w;
   const float* aux_own;
   const float* aux_other;
@@ -441,7 +575,47 @@ struct HCoef {
   float k_diag;   // scale (w_f + w_b): the positive pair's -1 terms
   float inv_tau;
   float k1;       // log2(e) / tau
+  // objectives outside InfoNCE (OBJ > 0)
+  float d_own, kd_own;  // row pass: this row's anchor F_uu and k_u
+  float c_bb, c_b, c_fb;  // dtotal / B^2, dtotal / B, dtotal / (B (B - 1))
+  float dtotal;
+  int transposed;
 };
+
+// Objective kinds of the coefficient tile: 0 the InfoNCE family (FlatNCE
+// included), then forward-backward, DPO, IPO, SPPO, NCE-binary.
+enum : int { kObjInfo = 0, kObjFB, kObjDPO, kObjIPO, kObjSPPO, kObjNCE };
+inline int obj_kind(int loss) {
+  switch (loss) {
+    case CRL_LOSS_FB: return kObjFB;
+    case CRL_LOSS_DPO: return kObjDPO;
+    case CRL_LOSS_IPO: return kObjIPO;
+    case CRL_LOSS_SPPO: return kObjSPPO;
+    case CRL_LOSS_NCE_BINARY: return kObjNCE;
+    default: return kObjInfo;
+  }
+}
+
+// dtotal x (the objective's dL/dF_ij) for F = f2 / log2(e); the row of the pair
+// is u in the row pass and v in the column pass (d_row, k_row: its anchor F_ii
+// and k_i, the latter already divided by B^2).
+template <int OBJ>
+__device__ __forceinline__ float objective_coef(float f2, bool diag, float d_row, float k_row, const HCoef& hc) {
+  if (OBJ == kObjFB) return diag ? -ex2(f2) * hc.c_b : ex2(2.f * f2) * hc.c_fb;
+  const float F = f2 * (1.f / kLog2e);
+  float o;
+  if (OBJ == kObjDPO) {
+    o = __frcp_rn(1.f + ex2((d_row - F) * kLog2e)) * hc.c_bb;  // sigma(F - d)
+  } else if (OBJ == kObjIPO) {
+    o = -2.f * (d_row - F - 1.f) * hc.c_bb;
+  } else if (OBJ == kObjSPPO) {
+    o = 2.f * (F + 1.f) * hc.c_bb + (diag ? 2.f * (F - 1.f) * hc.c_b : 0.f);
+  } else {  // NCE-binary: sigma(F) - [i = j]
+    o = (__frcp_rn(1.f + ex2(-f2)) - (diag ? 1.f : 0.f)) * hc.c_bb;
+  }
+  if ((OBJ == kObjDPO || OBJ == kObjIPO) && diag) o -= k_row * hc.dtotal;
+  return o;
+}
 
 // dL/dF x (chain factor of the energy) for this thread's 32 columns 32 q ..:
 // with P_own = e^(F - l_own) and P_oth = e^(F - l_oth),
@@ -451,10 +625,11 @@ struct HCoef {
 // factor 1 / (tau d), zero where d < 1e-12), 1: L2^2 (F = -d^2 / tau, factor
 // 2 / tau), 2: dot / cos (F = s / tau, factor 1 / tau).  The BF16-rounded
 // coefficients are packed in pairs and summed into rowsum.
-template <int EK>
+template <int EK, int OBJ>
 __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, const float* s_aux,
-                                        const float* s_lse2, const float* s_koth, int q, int u, int v0, int B,
-                                        float& rowsum, uint32_t (&packed)[16]) {
+                                        const float* s_lse2, const float* s_koth, const float* s_dv,
+                                        const float* s_kv, int q, int u, int v0, int B, float& rowsum,
+                                        uint32_t (&packed)[16]) {
 #pragma unroll
   for (int k = 0; k < 32; k += 2) {
     float h2[2];
@@ -479,6 +654,11 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
       }
       float g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - s_lse2[cl]) * s_koth[cl]);
       if (u == v) g -= hc.k_diag;
+      if (OBJ != kObjInfo) {
+        const float d_row = hc.transposed ? s_dv[cl] : hc.d_own;
+        const float k_row = hc.transposed ? s_kv[cl] : hc.kd_own;
+        g += objective_coef<OBJ>(f2, u == v, d_row, k_row, hc);
+      }
       h2[e] = (u < B && v < B) ? g * fac : 0.f;
     }
     const __nv_bfloat162 p2 = __floats2bfloat162_rn(h2[0], h2[1]);
@@ -490,6 +670,7 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
 }
 
 // lb in [0, 2 nrow): the row pass for lb < nrow, else the column pass.
+template <int OBJ>
 __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const CUtensorMap* tmXT,
                                          const CUtensorMap* tmYT, const BwdArgs& row, const BwdArgs& col, int nrow,
                                          int lb, bool global_maps) {
@@ -510,7 +691,9 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   float* s_red = s_aux + kTile;                             // [4][128] partial sums
   float* s_lse2 = s_red + 4 * kTile;                        // [128] other side's logsumexp x log2(e)
   float* s_koth = s_lse2 + kTile;                           // [128] other side's coefficient (see HCoef)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_koth + kTile);
+  float* s_dv = s_koth + kTile;                             // [128] column pass: the rows' anchor F_vv
+  float* s_kv = s_dv + kTile;                               // [128] column pass: the rows' k_v
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_kv + kTile);
   uint64_t* xload = bars;
   uint64_t* yload = bars + 1;
   uint64_t* ytload = bars + 2;
@@ -574,6 +757,14 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   hc.k_diag = a.scale * (a.w.wf + a.w.wb);
   hc.inv_tau = a.inv_tau;
   hc.k1 = a.inv_tau * kLog2e;
+  constexpr bool kAnchored = OBJ == kObjDPO || OBJ == kObjIPO;
+  hc.d_own = (kAnchored && u < a.B) ? a.dpre[u] : 0.f;
+  hc.kd_own = (kAnchored && u < a.B) ? a.kd[u] : 0.f;
+  hc.dtotal = a.dtotal;
+  hc.c_bb = a.dtotal / ((float)a.B * (float)a.B);
+  hc.c_b = a.dtotal / (float)a.B;
+  hc.c_fb = a.B > 1 ? a.dtotal / ((float)a.B * (float)(a.B - 1)) : 0.f;
+  hc.transposed = a.transposed;
   float rowsum = 0.f;
   bool ok = true;
   for (int vt = 0; vt < nV && ok; ++vt) {
@@ -589,6 +780,10 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
       s_aux[tid] = (v < a.B) ? a.aux_other[v] : 0.f;
       s_lse2[tid] = lo * kLog2e;
       s_koth[tid] = a.scale * (w_oth + 2.f * a.beta * p_oth * lo);
+      if (kAnchored && a.transposed) {
+        s_dv[tid] = (v < a.B) ? a.dpre[v] : 0.f;
+        s_kv[tid] = (v < a.B) ? a.kd[v] : 0.f;
+      }
     }
     if (tid == 0) {
       tc::mbar_arrive_expect_tx(yload, (uint32_t)(nk * 16384));
@@ -630,9 +825,13 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
       tc::tmem_ld32(tS + lane_off + q * 32, sv);
       uint32_t packed[16];
       switch (a.energy) {
-        case CRL_ENERGY_L2: build_h<0>(sv, hc, s_aux, s_lse2, s_koth, q, u, v0, a.B, rowsum, packed); break;
-        case CRL_ENERGY_L2SQ: build_h<1>(sv, hc, s_aux, s_lse2, s_koth, q, u, v0, a.B, rowsum, packed); break;
-        default: build_h<2>(sv, hc, s_aux, s_lse2, s_koth, q, u, v0, a.B, rowsum, packed); break;
+        case CRL_ENERGY_L2:
+          build_h<0, OBJ>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, rowsum, packed);
+          break;
+        case CRL_ENERGY_L2SQ:
+          build_h<1, OBJ>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, rowsum, packed);
+          break;
+        default: build_h<2, OBJ>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, rowsum, packed); break;
       }
       // columns 32 q .. +31 = K-block q / 2, 16-byte chunks (q % 2) * 4 .. +3
       uint8_t* hb = Hs + (q / 2) * 16384;
@@ -713,13 +912,14 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   if (warp == 0) tc::tmem_dealloc(tmem, tcols);
 }
 
+template <int OBJ>
 __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant__ CUtensorMap tmX,
                                                           const __grid_constant__ CUtensorMap tmY,
                                                           const __grid_constant__ CUtensorMap tmXT,
                                                           const __grid_constant__ CUtensorMap tmYT,
                                                           const __grid_constant__ BwdArgs row,
                                                           const __grid_constant__ BwdArgs col, int nrow) {
-  bwd_body(&tmX, &tmY, &tmXT, &tmYT, row, col, nrow, blockIdx.x, false);
+  bwd_body<OBJ>(&tmX, &tmY, &tmXT, &tmYT, row, col, nrow, blockIdx.x, false);
 }
 
 // ---- several agents in one launch ------------------------------------------------
@@ -750,20 +950,21 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_multi_kernel(const EnergyTask
   fwd_body(&t.tmX, &t.tmY, t.f, lb / t.n, lb % t.n, t.n, true);
 }
 
+template <int OBJ>
 __global__ void __launch_bounds__(kThreads, 1) bwd_multi_kernel(const EnergyTask* __restrict__ tasks,
                                                                const int* __restrict__ begin, int n) {
   int lb, nb;
   const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];
-  bwd_body(&t.tmX, &t.tmY, &t.tmXT, &t.tmYT, t.row, t.col, t.n, lb, true);
+  bwd_body<OBJ>(&t.tmX, &t.tmY, &t.tmXT, &t.tmYT, t.row, t.col, t.n, lb, true);
 }
 
 size_t fwd_smem(int R) {
   const size_t opnd = (size_t)2 * (R / 64) * 16384, ftile = (size_t)kTile * 129 * 4;
-  return (opnd > ftile ? opnd : ftile) + 2 * 4 * kTile * 4 + 1024 + 64;
+  return (opnd > ftile ? opnd : ftile) + (2 * 2 * 4 + 1) * kTile * 4 + 1024 + 64;
 }
 size_t bwd_smem(int R) {
   const size_t ybytes = std::max<size_t>((size_t)(R / 64) * 16384, (size_t)2 * R * 128);
-  return (size_t)(R / 64) * 16384 + ybytes + 2 * 16384 + (2 + 4 + 2) * kTile * 4 + 1024 + 64;
+  return (size_t)(R / 64) * 16384 + ybytes + 2 * 16384 + (2 + 4 + 2 + 2) * kTile * 4 + 1024 + 64;
 }
 
 FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* loss4, float* r, float* c,
@@ -772,18 +973,27 @@ FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* 
   char* base = static_cast<char*>(ws);
   unsigned* tickets = reinterpret_cast<unsigned*>(base);
   float* tile_part = reinterpret_cast<float*>(base + round_up((2 * n + 1) * 4, 256));
-  float* rowpart = reinterpret_cast<float*>(base + round_up((2 * n + 1) * 4, 256) + round_up(4 * n * 4, 256));
+  float* rowpart = reinterpret_cast<float*>(base + round_up((2 * n + 1) * 4, 256) + round_up(6 * n * 4, 256));
   float* colpart = rowpart + (size_t)2 * n * B;
   float* diag = colpart + (size_t)2 * n * B;
+  float* objpart = diag + B;
+  float* dpre = objpart + (size_t)2 * n * B;
+  float* kd = dpre + B;
   // member by member into zeroed storage: the arguments also key device tables
   FwdArgs f;
   memset(&f, 0, sizeof(f));
   f.B = B;
   f.R = e.R;
   f.energy = ls.energy;
+  f.obj = ls.loss;
   f.inv_tau = (float)(1.0 / ls.tau);
   f.auxX = e.auxX;
   f.auxY = e.auxY;
+  f.X = e.X;
+  f.Y = e.Y;
+  f.objpart = objpart;
+  f.dpre = dpre;
+  f.kd = kd;
   f.rowpart = rowpart;
   f.colpart = colpart;
   f.diag = diag;
@@ -801,16 +1011,20 @@ FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* 
 
 // Backward arguments of the row pass (own = phi), member by member into zeroed storage.
 BwdArgs bwd_args(const EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* r, const float* c,
-                 double dtotal, bf16* dphi, bf16* dphiT, int ldt, unsigned* status) {
+                 double dtotal, bf16* dphi, bf16* dphiT, int ldt, unsigned* status, const FwdArgs& f) {
   BwdArgs a;
   memset(&a, 0, sizeof(a));
   a.B = B;
   a.R = e.R;
   a.energy = ls.energy;
   a.transposed = 0;
+  a.obj = ls.loss;
   a.inv_tau = (float)(1.0 / ls.tau);
   a.beta = (float)ls.beta;
   a.scale = (float)(dtotal / B);
+  a.dtotal = (float)dtotal;
+  a.dpre = f.dpre;
+  a.kd = f.kd;
   a.w = loss_weights(ls);
   a.aux_own = e.auxX;
   a.aux_other = e.auxY;
@@ -833,21 +1047,18 @@ const char* mk(CUtensorMap* m, const void* base, int inner, int rows, int stride
 }  // namespace
 
 // Workspace of the forward: tickets [2 n + 1] (zeroed when the workspace is
-// created, reset by the CTAs that use them), tile loss partials [2][n][2],
-// rowpart [nJ][B][2], colpart [nI][B][2], diag [B].
+// created, reset by the CTAs that use them), tile loss partials [2][n][3],
+// rowpart [nJ][B][2], colpart [nI][B][2], diag [B], objpart [nJ][B][2],
+// dpre [B], kd [B].
 size_t energy_tc_ws_bytes(int B) {
   const int n = (B + kTile - 1) / kTile;
-  return (size_t)round_up((2 * n + 1) * 4, 256) + (size_t)round_up(4 * n * 4, 256) +
-         ((size_t)2 * n * B * 2 + B) * sizeof(float);
+  return (size_t)round_up((2 * n + 1) * 4, 256) + (size_t)round_up(6 * n * 4, 256) +
+         ((size_t)2 * n * B * 3 + 3 * (size_t)B) * sizeof(float);
 }
 
 bool energy_tc_supported(const LossSpec& ls, int B, int R, const char** why) {
   if (ls.energy == CRL_ENERGY_L1) {
     *why = "the fused path has no L1 energy";
-    return false;
-  }
-  if (ls.loss > CRL_LOSS_SYM) {
-    *why = "the fused path takes the InfoNCE objectives (forward, backward, symmetric) only";
     return false;
   }
   if (R % 64 != 0 || R > 256) {
@@ -892,17 +1103,48 @@ void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, flo
   launch_k(fwd_kernel, dim3(n, n), dim3(kThreads), sm, st, e.tmX, e.tmY, a);
 }
 
-void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
-                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dphiT,
-                        __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, unsigned* status, cudaStream_t st) {
-  const int n = (B + kTile - 1) / kTile;
+namespace {
+template <int OBJ>
+void launch_bwd_t(const EnergyTc& e, const BwdArgs& a, const BwdArgs& b, int n, size_t sm, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(256));
+    cudaFuncSetAttribute(bwd_kernel<OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(256));
     attr = true;
   }
+  launch_k(bwd_kernel<OBJ>, dim3(2 * n), dim3(kThreads), sm, st, e.tmX, e.tmY, e.tmXT, e.tmYT, a, b, n);
+}
+
+template <int OBJ>
+void launch_bwd_multi_t(const EnergyTask* dt, const int* db, int na, int blocks, size_t sm, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(bwd_multi_kernel<OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(256));
+    attr = true;
+  }
+  launch_k(bwd_multi_kernel<OBJ>, dim3(blocks), dim3(kThreads), sm, st, dt, db, na);
+}
+
+void launch_bwd_multi(int kind, const EnergyTask* dt, const int* db, int na, int blocks, size_t sm,
+                      cudaStream_t st) {
+  switch (kind) {
+    case kObjFB: launch_bwd_multi_t<kObjFB>(dt, db, na, blocks, sm, st); break;
+    case kObjDPO: launch_bwd_multi_t<kObjDPO>(dt, db, na, blocks, sm, st); break;
+    case kObjIPO: launch_bwd_multi_t<kObjIPO>(dt, db, na, blocks, sm, st); break;
+    case kObjSPPO: launch_bwd_multi_t<kObjSPPO>(dt, db, na, blocks, sm, st); break;
+    case kObjNCE: launch_bwd_multi_t<kObjNCE>(dt, db, na, blocks, sm, st); break;
+    default: launch_bwd_multi_t<kObjInfo>(dt, db, na, blocks, sm, st); break;
+  }
+}
+}  // namespace
+
+void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
+                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dphiT,
+                        __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, void* ws, unsigned* status,
+                        cudaStream_t st) {
+  const int n = (B + kTile - 1) / kTile;
   const size_t sm = bwd_smem(e.R);
-  const BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, dphi, dphiT, ldt, status);
+  const FwdArgs f = fwd_args(e, ls, B, ws, nullptr, nullptr, nullptr, nullptr, status);
+  const BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, dphi, dphiT, ldt, status, f);
   BwdArgs b = a;
   b.transposed = 1;
   b.aux_own = e.auxY;
@@ -913,7 +1155,14 @@ void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi
   b.d_out = dpsi;
   b.d_outT = dpsiT;
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 8.0 * B * B * e.R);
-  launch_k(bwd_kernel, dim3(2 * n), dim3(kThreads), sm, st, e.tmX, e.tmY, e.tmXT, e.tmYT, a, b, n);
+  switch (obj_kind(ls.loss)) {
+    case kObjFB: launch_bwd_t<kObjFB>(e, a, b, n, sm, st); break;
+    case kObjDPO: launch_bwd_t<kObjDPO>(e, a, b, n, sm, st); break;
+    case kObjIPO: launch_bwd_t<kObjIPO>(e, a, b, n, sm, st); break;
+    case kObjSPPO: launch_bwd_t<kObjSPPO>(e, a, b, n, sm, st); break;
+    case kObjNCE: launch_bwd_t<kObjNCE>(e, a, b, n, sm, st); break;
+    default: launch_bwd_t<kObjInfo>(e, a, b, n, sm, st); break;
+  }
 }
 
 const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& agents, int stage, cudaStream_t st) {
@@ -940,7 +1189,7 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     t.s0 = PrepSide{g.phi, e.X, e.XT, e.auxX};
     t.s1 = PrepSide{g.psi, e.Y, e.YT, e.auxY};
     t.f = fwd_args(e, g.ls, g.B, g.ws, g.loss4, g.r, g.c, g.t_bump, g.status);
-    t.row = bwd_args(e, g.ls, g.B, g.phi, g.r, g.c, 1.0, g.dphi, g.dphiT, g.ldt, g.status);
+    t.row = bwd_args(e, g.ls, g.B, g.phi, g.r, g.c, 1.0, g.dphi, g.dphiT, g.ldt, g.status, t.f);
     t.col = t.row;
     t.col.transposed = 1;
     t.col.aux_own = e.auxY;
@@ -971,12 +1220,28 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     }
     launch_k(fwd_multi_kernel, dim3(begin[na]), dim3(kThreads), fwd_smem(Rmax), st, dt, db, na);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(bwd_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(256));
-      attr = true;
+    // one launch per objective kind present (the agents of one kind in a table of their own)
+    int kinds = 0;
+    for (const EnergyAgent& g : agents) kinds |= 1 << obj_kind(g.ls.loss);
+    if (kinds == 1 << kObjInfo) {
+      launch_bwd_multi(kObjInfo, dt, db, na, begin[na], bwd_smem(Rmax), st);
+      return nullptr;
     }
-    launch_k(bwd_multi_kernel, dim3(begin[na]), dim3(kThreads), bwd_smem(Rmax), st, dt, db, na);
+    for (int kind = 0; kind <= kObjNCE; ++kind) {
+      if (!(kinds & (1 << kind))) continue;
+      std::vector<EnergyTask> sub;
+      std::vector<int> sb(1, 0);
+      for (int i = 0; i < na; ++i)
+        if (obj_kind(agents[i].ls.loss) == kind) {
+          sub.push_back(tasks[i]);
+          sb.push_back(sb.back() + begin[i + 1] - begin[i]);
+        }
+      const EnergyTask* st_t = cache.get(sub, st, &err);
+      if (!st_t) return err;
+      const int* st_b = cache.get(sb, st, &err);
+      if (!st_b) return err;
+      launch_bwd_multi(kind, st_t, st_b, (int)sub.size(), sb.back(), bwd_smem(Rmax), st);
+    }
   }
   return nullptr;
 }

@@ -29,9 +29,11 @@ void energy_tc_prepare(EnergyTc& e, const LossSpec& ls, const float* phi, const 
 void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, float* r, float* c, void* ws,
                        unsigned* status, int* t_bump, cudaStream_t st);
 // dphi / dpsi as BF16 [B][R] and transposed [R][ldt] (the encoders' dy layout), scaled by dtotal.
+// ws: the forward's workspace (its anchors and diagonal coefficients for DPO / IPO).
 void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
                         const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dphiT,
-                        __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, unsigned* status, cudaStream_t st);
+                        __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, void* ws, unsigned* status,
+                        cudaStream_t st);
 
 // One agent of a multi-agent launch of the fused energy stage (its maps built
 // by energy_tc_maps for batch B).

@@ -103,13 +103,11 @@ def test_host_side_errors_without_gpu(lib):
 
 
 def test_config_validation_of_objectives_without_gpu(lib):
-    """Rejected before any device work: unknown objective, forward-backward with
-    B = 1, and objectives outside InfoNCE on the fused path."""
+    """Rejected before any device work: unknown objective and forward-backward
+    with B = 1."""
     h = ctypes.c_void_p()
     w = workload.SMALL_FP32
     for cfg, code in ((api.make_config(w, loss=10), api.E_INVALID_ARG),
-                      (api.make_config(w.with_(B=1, loss="fb")), api.E_INVALID_ARG),
-                      (api.make_config(w.with_(loss="dpo", repr=64, B=64), precision="bf16", path="fused"),
-                       api.E_UNSUPPORTED)):
+                      (api.make_config(w.with_(B=1, loss="fb")), api.E_INVALID_ARG)):
         assert lib.crl_create(ctypes.byref(cfg), ctypes.byref(h)) == code
         assert h.value is None

@@ -184,6 +184,45 @@ def test_fused_critic_ragged_tiles(B, penalty):
     check_fused(ctx, got, ref)
 
 
+OBJECTIVES = ["flatnce_fwd", "flatnce_bwd", "fb", "dpo", "ipo", "sppo", "nce_binary"]
+
+
+@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq"])
+@pytest.mark.parametrize("loss", OBJECTIVES)
+def test_fused_critic_objectives_match_oracle(energy, loss):
+    """The objectives outside InfoNCE on the fused tcgen05 path (App. A.2 / §5.2).
+    Forward-backward with the unbounded dot energy sums exp(2 F): BF16's absolute
+    error in F becomes relative error in the loss, so that case takes tau = 4
+    (|F| of a few units instead of about 10)."""
+    tau = 0.7 if energy == "cos" else (4.0 if (energy, loss) == ("dot", "fb") else 1.0)
+    w = bf16_small(energy=energy, loss=loss, repr=64, tau=tau)
+    ctx, got, ref = run_critic_fused(w)
+    check_fused(ctx, got, ref)
+
+
+@pytest.mark.parametrize("B,loss", [(136, "dpo"), (264, "ipo"), (264, "fb"), (392, "sppo"), (136, "nce_binary"),
+                                    (8, "dpo"), (520, "dpo")])
+def test_fused_critic_objectives_ragged_tiles(B, loss):
+    """Several 128-row tiles and a ragged last one: the anchors F_ii and the row
+    partials cross tiles."""
+    w = bf16_small(B=B, repr=128, loss=loss)
+    ctx, got, ref = run_critic_fused(w)
+    check_fused(ctx, got, ref)
+
+
+@pytest.mark.parametrize("direction", ["fwd", "bwd"])
+def test_fused_flatnce_gradient_is_infonce_gradient(direction):
+    out = {}
+    for loss in (direction, "flatnce_" + direction):
+        w = bf16_small(loss=loss, repr=64, B=136)
+        ctx, got, _ = run_critic_fused(w)
+        out[loss] = (got, {n: ctx.store[n]["grads"].cpu().numpy() for n in ("phi", "psi")})
+    a, b = out[direction], out["flatnce_" + direction]
+    for n in ("phi", "psi"):
+        np.testing.assert_array_equal(a[1][n], b[1][n])
+    assert b[0][0] == b[0][3] == a[0][3]
+
+
 def test_fused_critic_full_size_ant():
     ctx, got, ref = run_critic_fused(workload.ANT_AUTOGRAD, mean_len=None)
     check_fused(ctx, got, ref)

@@ -88,6 +88,13 @@ def test_grouped_sweep_with_alpha_autotune():
     run_and_compare(ws, "bf16", "fused", grouped=True, steps=3)
 
 
+def test_grouped_sweep_with_mixed_objectives():
+    """An objective sweep (§5.2) in one grouped sweep: the backward runs one launch
+    per objective kind over its agents."""
+    ws = [w.with_(loss=l) for w, l in zip(uneven_agents(), ("dpo", "sym", "fb", "ipo"))]
+    run_and_compare(ws, "bf16", "fused", grouped=True, steps=3)
+
+
 def test_grouped_sweep_of_32_agents_sampled():
     """The 32-agent sweep workload's shapes (batch 256..2048, obs 29 / 64 / 268,
     repr 64 / 128, 512 envs), short buffers; agents 0, 13 and 31 checked."""
