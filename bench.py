@@ -147,7 +147,9 @@ def cpu_oracle_rate(w, n_steps, budget_s=20.0):
     state = oracle.step.AgentState(nets["phi"], nets["psi"], nets["pi"])
     cfg = dict(seed=w.seed, agent=0, B=w.B, goal_idx=w.goals(), gamma=w.gamma, energy=w.energy, tau=w.tau,
                loss=w.loss, sym_reduction=w.sym_reduction, beta=w.beta, penalty_axis=w.penalty_axis, alpha=w.alpha,
-               lr_critic=w.lr_critic, lr_actor=w.lr_actor)
+               lr_critic=w.lr_critic, lr_actor=w.lr_actor, alpha_autotune=w.alpha_autotune,
+               target_entropy=-w.A if w.target_entropy is None else w.target_entropy,
+               lr_alpha=w.lr_actor if w.lr_alpha is None else w.lr_alpha)
     done_steps = 0
     t0 = time.perf_counter()
     for i in range(n_steps):
@@ -471,6 +473,11 @@ def run_sweep(args, dev, flush):
     print(json.dumps(line), flush=True)
 
 
+def api_losses():
+    from paper_2408_11052_gb300 import api as _api
+    return _api.LOSS
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,9 +495,19 @@ def main():
                     help="fixed GEMM tile rule (deterministic launch sequence for profiler captures)")
     ap.add_argument("--only-relabel", action="store_true",
                     help="run only the standalone relabel throughput (a short command for ncu captures)")
+    ap.add_argument("--loss", default=None, choices=sorted(api_losses()),
+                    help="contrastive objective instead of the workload's (App. A.2 / §5.2)")
+    ap.add_argument("--energy", default=None, choices=["l2", "dot", "cos", "l2sq", "l1"],
+                    help="energy function instead of the workload's")
+    ap.add_argument("--alpha-autotune", action="store_true", help="learn the entropy coefficient")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS.get(args.workload, workload.ANT_AUTOGRAD)
+    over = {k: v for k, v in (("loss", args.loss), ("energy", args.energy)) if v is not None}
+    if args.alpha_autotune:
+        over["alpha_autotune"] = True
+    if over:
+        w = w.with_(**over)
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -572,7 +589,8 @@ def main():
             "samples_per_s": value * w.B,
             "config": {"workload": w.name, "batch": w.B, "envs": w.E, "steps_per_env": w.T, "obs": w.D,
                        "action": w.A, "goal": w.G, "hidden": [w.hidden] * w.layers, "repr": w.repr,
-                       "energy": w.energy, "loss": w.loss, "precision": args.precision, "path": args.path,
+                       "energy": w.energy, "loss": w.loss, "alpha_autotune": bool(w.alpha_autotune),
+                       "precision": args.precision, "path": args.path,
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "step": "insert 1 slice + relabel + critic fwd/bwd + Adam + actor fwd/bwd + Adam",
                        "parallelism": f"{world} independent agents"},

@@ -366,6 +366,19 @@ int32_t crl_set_launch_overlap(int32_t enable);
  * tracing.  Returns the previous setting. */
 int32_t crl_set_autotune(int32_t enable);
 
+/* Which tensor-core GEMM kernels the grouped launches may use (process-wide;
+ * library extension): CRL_GEMM_ANY (the default; the autotuner picks among
+ * both), CRL_GEMM_ONE_TILE (one CTA per output tile), CRL_GEMM_PERSISTENT (one
+ * CTA per SM walking the tiles, its epilogue overlapping the next tile's
+ * main loop through a double-buffered TMEM accumulator).  Both kernels give
+ * identical outputs.  Without autotuning the fixed rule picks the tile width
+ * and this setting the kernel (ANY: one tile per CTA).  Returns the previous
+ * setting, or CRL_E_INVALID_ARG for an unknown mode. */
+#define CRL_GEMM_ANY 0
+#define CRL_GEMM_ONE_TILE 1
+#define CRL_GEMM_PERSISTENT 2
+int32_t crl_set_gemm_kernel(int32_t mode);
+
 /* ---- op-level entry points (stateless; used by torch.autograd.Function) ---
  * Same kernels as the step calls.  dtype: CRL_PREC_FP32 (float) or
  * CRL_PREC_FP64 (double) for every floating pointer of the call; inputs x0/x1

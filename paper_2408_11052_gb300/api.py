@@ -90,6 +90,7 @@ _SIGNATURES = {
     "crl_trace_stop": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_double), POINTER(c_double)]),
     "crl_set_launch_overlap": (c_int32, [c_int32]),
     "crl_set_autotune": (c_int32, [c_int32]),
+    "crl_set_gemm_kernel": (c_int32, [c_int32]),
     "crl_sweep_create": (c_int32, [POINTER(CrlConfig), c_int32, c_int32, POINTER(c_void_p)]),
     "crl_sweep_destroy": (c_int32, [c_void_p]),
     "crl_sweep_agent": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
@@ -167,6 +168,16 @@ def set_autotune(enable):
     """Process-wide: time the grouped GEMMs' tile widths on first use (True, the
     default) or use the fixed rule.  Returns the previous setting."""
     return bool(lib().crl_set_autotune(1 if enable else 0))
+
+
+GEMM_KERNEL = {"any": 0, "one_tile": 1, "persistent": 2}
+
+
+def set_gemm_kernel(mode):
+    """Process-wide: which tensor-core GEMM kernels the grouped launches may use
+    ("any", "one_tile" or "persistent").  Returns the previous mode's name."""
+    prev = lib().crl_set_gemm_kernel(GEMM_KERNEL[mode])
+    return {v: k for k, v in GEMM_KERNEL.items()}[prev]
 
 
 def stream_handle(stream=None):

@@ -23,6 +23,7 @@ namespace crl {
 thread_local Tracer* g_tracer = nullptr;
 int g_launch_overlap = 1;
 int g_autotune = 1;
+int g_gemm_kernel = CRL_GEMM_ANY;
 }
 
 namespace crl {
@@ -904,6 +905,13 @@ int32_t crl_set_launch_overlap(int32_t enable) {
 int32_t crl_set_autotune(int32_t enable) {
   const int32_t prev = g_autotune;
   g_autotune = enable ? 1 : 0;
+  return prev;
+}
+
+int32_t crl_set_gemm_kernel(int32_t mode) {
+  if (mode < CRL_GEMM_ANY || mode > CRL_GEMM_PERSISTENT) return CRL_E_INVALID_ARG;
+  const int32_t prev = g_gemm_kernel;
+  g_gemm_kernel = mode;
   return prev;
 }
 

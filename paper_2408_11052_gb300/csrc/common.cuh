@@ -103,6 +103,7 @@ __device__ __forceinline__ void pdl_enter() {
 // and crl_set_autotune (1 = grouped GEMMs time their tile widths on first use).
 extern int g_launch_overlap;
 extern int g_autotune;
+extern int g_gemm_kernel;  // CRL_GEMM_*
 
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -379,13 +379,49 @@ void launch_gemm_cfg(const tc::GemmProblem* table, int nprob, int tiles, unsigne
   launch_k(tc::tc_gemm_kernel<BN, STAGES>, dim3(tiles), dim3(128), S::kBytes, st, table, nprob, status);
 }
 
-// A GEMM configuration: tile width and ring depth, coded as 16 * BN + stages.
-constexpr int gemm_cfg(int bn, int stages) { return 16 * bn + stages; }
-constexpr int kGemmCfgs[5] = {gemm_cfg(64, 4), gemm_cfg(64, 8), gemm_cfg(128, 3), gemm_cfg(128, 6),
-                              gemm_cfg(256, 4)};
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || n <= 0)
+      n = 148;
+  }
+  return n;
+}
+
+template <int BN, int STAGES>
+void launch_gemm_persistent(const tc::GemmProblem* table, int nprob, int tiles, unsigned* status, cudaStream_t st) {
+  using S = tc::GemmSmem<BN, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc::tc_gemm_persistent_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         S::kBytes);
+    attr = true;
+  }
+  const int grid = std::min(tiles, sm_count());
+  launch_k(tc::tc_gemm_persistent_kernel<BN, STAGES>, dim3(grid), dim3(192), S::kBytes, st, table, nprob, tiles,
+           status);
+}
+
+// A GEMM configuration: tile width, ring depth and kernel (one tile per CTA, or
+// the persistent kernel), coded as 8192 * persistent + 16 * BN + stages.
+constexpr int gemm_cfg(int bn, int stages, int persistent = 0) { return 8192 * persistent + 16 * bn + stages; }
+constexpr int cfg_bn(int cfg) { return (cfg % 8192) / 16; }
+bool cfg_allowed(int cfg) {
+  if (g_gemm_kernel == CRL_GEMM_ONE_TILE) return cfg < 8192;
+  if (g_gemm_kernel == CRL_GEMM_PERSISTENT) return cfg >= 8192;
+  return true;
+}
+constexpr int kGemmCfgs[8] = {gemm_cfg(64, 4),       gemm_cfg(64, 8),       gemm_cfg(128, 3),
+                              gemm_cfg(128, 6),      gemm_cfg(256, 4),      gemm_cfg(64, 8, 1),
+                              gemm_cfg(128, 6, 1),   gemm_cfg(256, 4, 1)};
 
 void launch_cfg(int cfg, const tc::GemmProblem* t, int nprob, int tiles, unsigned* status, cudaStream_t st) {
   switch (cfg) {
+    case gemm_cfg(64, 8, 1): launch_gemm_persistent<64, 8>(t, nprob, tiles, status, st); break;
+    case gemm_cfg(128, 6, 1): launch_gemm_persistent<128, 6>(t, nprob, tiles, status, st); break;
+    case gemm_cfg(256, 4, 1): launch_gemm_persistent<256, 4>(t, nprob, tiles, status, st); break;
     case gemm_cfg(64, 8): launch_gemm_cfg<64, 8>(t, nprob, tiles, status, st); break;
     case gemm_cfg(128, 3): launch_gemm_cfg<128, 3>(t, nprob, tiles, status, st); break;
     case gemm_cfg(128, 4): launch_gemm_cfg<128, 4>(t, nprob, tiles, status, st); break;
@@ -401,6 +437,8 @@ int heuristic_cfg(const std::vector<tc::GemmProblem>& probs, int min_bn) {
   long long ctas128 = 0;
   for (const auto& p : probs) ctas128 += (long long)ceil_div(p.M, 128) * ceil_div(p.N, 128);
   const int bn = std::max(ctas128 >= 148 ? 128 : 64, min_bn <= 64 ? 64 : (min_bn <= 128 ? 128 : 256));
+  if (g_gemm_kernel == CRL_GEMM_PERSISTENT)
+    return bn == 256 ? gemm_cfg(256, 4, 1) : (bn == 128 ? gemm_cfg(128, 6, 1) : gemm_cfg(64, 8, 1));
   return bn == 256 ? gemm_cfg(256, 4) : (bn == 128 ? gemm_cfg(128, 4) : gemm_cfg(64, 4));
 }
 
@@ -420,10 +458,11 @@ int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, un
   int best = 0;
   float best_ms = 0.f;
   for (int cfg : kGemmCfgs) {
-    if (cfg / 16 < min_bn) continue;
+    if (cfg_bn(cfg) < min_bn) continue;
+    if (!cfg_allowed(cfg)) continue;
     int tiles = 0;
     const char* err = nullptr;
-    const tc::GemmProblem* t = gg.table(probs, cfg / 16, &tiles, st, &err);
+    const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err);
     if (!t || tiles == 0) continue;
     launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);  // warm-up
     cudaEventRecord(e0, st);
@@ -453,6 +492,7 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
     if (p.epi.kind == tc::kEpiFwdOutEnergy) min_bn = std::max(min_bn, p.N);
   if (min_bn > 256) return "an energy-operand output layer wider than 256 columns";
   int cfg = g_autotune ? gg.tuned_bn(key) : 0;
+  if (cfg != 0 && !cfg_allowed(cfg)) cfg = 0;   // tuned under another kernel setting
   if (cfg == 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
@@ -464,7 +504,7 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
   }
   int tiles = 0;
   const char* err = nullptr;
-  const tc::GemmProblem* t = gg.table(probs, cfg / 16, &tiles, st, &err);
+  const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err);
   if (!t) return err;
   if (tiles == 0) return nullptr;
   TraceLaunch tr(CRL_TRACE_GEMM, st, flops);

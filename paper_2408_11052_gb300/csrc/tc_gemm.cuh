@@ -414,5 +414,172 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) tmem_dealloc(tmem, S::kTmemCols);
 }
 
+// The problem of tile t: the last p with tile_begin <= t (the table is immutable).
+__device__ __forceinline__ const GemmProblem* find_problem(const GemmProblem* __restrict__ probs, int nprob, int t) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (probs[mid].tile_begin <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return probs + lo;
+}
+
+// Persistent variant: gridDim.x CTAs (one per SM at most) walk the tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... of the whole problem list.
+// 192 threads:
+//   warp 0 / lane 0 -- TMA producer over all of the CTA's tiles: the operand
+//                      ring runs on across tile boundaries;
+//   warp 1 / lane 0 -- MMA issuer: tile i accumulates into TMEM buffer i % 2
+//                      (2 x BN columns), once the epilogue has released it;
+//   warps 2..5      -- epilogue of tile i from buffer i % 2 while the MMAs of
+//                      tile i + 1 fill the other one (warp w reads TMEM lanes
+//                      32 (w % 4) ..).
+// The epilogue is the same as the one-tile kernel's, so both give identical
+// outputs.
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_persistent_kernel(const GemmProblem* __restrict__ probs, int nprob, int total, unsigned* status) {
+  using S = GemmSmem<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + S::kStages * S::kABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::kStages * S::kStageBytes);
+  uint64_t* empty = full + S::kStages;
+  uint64_t* accf = empty + S::kStages;  // [2] accumulator buffer ready (MMA -> epilogue)
+  uint64_t* acce = accf + 2;            // [2] accumulator buffer free (epilogue -> MMA), 4 arrivals
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 2 * BN);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  pdl_wait();
+  pdl_trigger();
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer; `it` counts K-slices over all tiles of this CTA
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const GemmProblem* P = find_problem(probs, nprob, t);
+        const int lt = t - P->tile_begin;
+        const int m0 = (lt / P->tiles_n) * kBM, n0 = (lt % P->tiles_n) * BN;
+        const int nk = (P->K + kBK - 1) / kBK, nkA = P->nkA;
+        const CUtensorMap* tmA = &P->a;
+        const CUtensorMap* tmB = &P->b;
+        tmap_acquire(tmA);
+        tmap_acquire(tmB);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % S::kStages;
+          if (it >= S::kStages && !mbar_wait(&empty[s], ((it / S::kStages) & 1) ^ 1)) {
+            atomicOr(status, CRL_STATUS_TIMEOUT);
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[s], S::kStageBytes);
+          const int ka = nkA > 0 ? kb % nkA : kb;
+#pragma unroll
+          for (int r = 0; r < kBM / 64; ++r)
+            tma_load_2d(sA + s * S::kABytes + r * 8192, tmA, &full[s], ka * kBK, m0 + 64 * r);
+#pragma unroll
+          for (int r = 0; r < BN / 64; ++r)
+            tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kb * kBK, n0 + 64 * r);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
+      int it = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+        const GemmProblem* P = find_problem(probs, nprob, t);
+        const int nk = (P->K + kBK - 1) / kBK;
+        const int buf = i & 1, use = i >> 1;
+        // the epilogue of tile i - 2 must have read this buffer out
+        if (use > 0 && !mbar_wait(&acce[buf], (use - 1) & 1)) {
+          atomicOr(status, CRL_STATUS_TIMEOUT);
+          break;
+        }
+        fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % S::kStages;
+          if (!mbar_wait(&full[s], (it / S::kStages) & 1)) {
+            atomicOr(status, CRL_STATUS_TIMEOUT);
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint64_t da = sdesc_kmajor_sw128(sA + s * S::kABytes);
+          const uint64_t db = sdesc_kmajor_sw128(sB + s * S::kBBytes);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&accf[buf]);
+      }
+    }
+  } else {
+    // epilogue warps (tcgen05.ld is warp-collective: decisions stay warp-uniform)
+    const int eg = warp & 3;
+    int i = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      const int buf = i & 1, use = i >> 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[buf], use & 1) ? 1 : 0) != 0;
+      if (!ok) {
+        if (lane == 0) atomicOr(status, CRL_STATUS_TIMEOUT);
+        break;
+      }
+      fence_after_sync();
+      const GemmProblem* P = find_problem(probs, nprob, t);
+      const int lt = t - P->tile_begin;
+      const int m0 = (lt / P->tiles_n) * kBM, n0 = (lt % P->tiles_n) * BN;
+      const int M = P->M, N = P->N;
+      const EpiDesc e = P->epi;
+      const int row = m0 + eg * 32 + lane;
+      const uint32_t lane_base = tmem + (uint32_t)(buf * BN) + ((uint32_t)(eg * 32) << 16);
+      const int ncol = (N - n0 < BN) ? N - n0 : BN;
+      if (e.kind == kEpiFwdOutEnergy) {
+        epilogue_energy(e, row, lane_base, ncol, M);
+      } else {
+#pragma unroll 1
+        for (int c = 0; c < ncol; c += 32) {
+          float v[32];
+          tmem_ld32(lane_base + c, v);
+          epilogue_chunk(e, row, n0 + c, v, M, N);
+        }
+      }
+      // release the buffer to the MMA issuer
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 2 * BN);
+}
+
 }  // namespace tc
 }  // namespace crl

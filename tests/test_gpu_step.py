@@ -248,6 +248,42 @@ def test_graph_replay_matches_eager(precision, path):
         np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
 
 
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_persistent_gemm_matches_one_tile_gemm(path):
+    """The persistent tensor-core GEMM (double-buffered TMEM, several tiles per CTA:
+    batch 2048 gives more tiles than SMs) and the one-tile kernel give bit-identical
+    update steps (fixed tile rule, so both run the same tile widths)."""
+    w = small(B=2048, hidden=512, repr=64, E=8, T=400)
+    prev_tune = api.set_autotune(False)
+    runs = []
+    try:
+        for mode in ("one_tile", "persistent"):
+            prev = api.set_gemm_kernel(mode)
+            try:
+                ctx, _, _ = setup(w, precision="bf16", path=path, n=300, mean_len=40.0)
+                extra = workload.buffer_contents(w, n=3, mean_len=9.0, seed_offset=7)
+                loss = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+                hist = []
+                for i in range(3):
+                    ctx.update_step(*(torch.from_numpy(x[i:i + 1]).to(ctx.device) for x in extra), loss_out=loss)
+                    hist.append(loss.cpu().numpy().copy())
+                torch.cuda.synchronize()
+                assert ctx.sync_status() == (0, 0)
+                runs.append((np.array(hist), {n: ctx.store[n]["params"].cpu().numpy() for n in ("phi", "psi", "pi")}))
+            finally:
+                api.set_gemm_kernel(prev)
+    finally:
+        api.set_autotune(prev_tune)
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    for n in ("phi", "psi", "pi"):
+        np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
+
+
+def test_gemm_kernel_mode_is_validated():
+    assert api.lib().crl_set_gemm_kernel(3) == api.E_INVALID_ARG
+    assert api.set_gemm_kernel("any") == "any"
+
+
 def test_l1_energy_runs_on_the_plain_path_only():
     """-L1 (App. A.2) has a plain-path backward; the fused BF16 path rejects it."""
     w = small(B=64, energy="l1")
