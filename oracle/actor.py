@@ -30,6 +30,16 @@ P5  Entropy-coefficient auto-tuning (§5.1, "a tuneable entropy coefficient";
     log pi held fixed and H_target = -A (the action dimension).  The actor
     loss of a step uses alpha before that step's update; the configured alpha
     is the initial value.
+P6  Random-goal actor mix (App. D, weight alpha_rg; the paper recommends and
+    uses 0): sample b's actor goal is, with probability alpha_rg, the
+    relabelled goal of sample (b + 1) mod B of the same batch (another,
+    independently drawn transition, so a draw from the buffer's goal
+    marginal), else its own relabelled goal.  The choice uses the top 32 bits
+    of word 2 of sample b's relabel Philox block (step, b, 0, 0): a random goal
+    iff (w2 >> 32) < floor(alpha_rg * 2^32) (alpha_rg a float32, so the
+    threshold is exact).  The per-sample mixture is an unbiased estimate of
+    App. D's weighted sum of the two expectations.  See
+    ``relabel.actor_goal_mix``.
 """
 
 import numpy as np

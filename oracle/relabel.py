@@ -135,6 +135,25 @@ def draw_indices(seed, agent, step, b, E, size):
     return e, t, v
 
 
+def actor_goal_mix(seed, agent, step, g, alpha_rg):
+    """Actor goals of the random-goal mix (App. D; reading P6 of the actor module).
+
+    g [B][G]: the relabelled goals of the batch drawn at ``step``.  Returns
+    (g_actor [B][G], random [B] bool).
+    """
+    g = np.asarray(g, dtype=np.float64)
+    B = g.shape[0]
+    thr = min(int(np.floor(float(np.float32(alpha_rg)) * TWO32)), TWO32)
+    out = g.copy()
+    rnd = np.zeros(B, dtype=bool)
+    for b in range(B):
+        w = philox4x64_10((step, b, 0, 0), (seed, agent))
+        if (w[2] >> 32) < thr:
+            rnd[b] = True
+            out[b] = g[(b + 1) % B]
+    return out, rnd
+
+
 def sample_relabel(buf, seed, agent, step, B, goal_idx, gamma, offset_min=1):
     """Sample a relabelled batch (Algorithm 1, "sample with discount").
 

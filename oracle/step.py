@@ -73,7 +73,8 @@ def update_step(state, buf, cfg, step, eps):
     sym_reduction, beta, penalty_axis, alpha, lr_critic, lr_actor, and optionally
     adam_beta1, adam_beta2, adam_eps (textbook defaults) and alpha_autotune,
     target_entropy, lr_alpha (reading P5 of the actor module; the returned dict
-    then carries the alpha used and the updated one).
+    then carries the alpha used and the updated one) and alpha_rg (the
+    random-goal actor mix, reading P6; 0 by default).
     eps [B][A]: the actor's Gaussian noise, drawn by the caller.
     """
     s, a, g, idx = relabel.sample_relabel(buf, cfg["seed"], cfg.get("agent", 0), step, cfg["B"],
@@ -86,11 +87,14 @@ def update_step(state, buf, cfg, step, eps):
     for name, grads in (("phi", gphi), ("psi", gpsi)):
         state.nets[name], state.m[name], state.v[name] = adam_net(
             state.nets[name], grads, state.m[name], state.v[name], state.t_critic, cfg["lr_critic"], *betas)
+    g_actor = g
+    if cfg.get("alpha_rg", 0.0) > 0.0:
+        g_actor, _ = relabel.actor_goal_mix(cfg["seed"], cfg.get("agent", 0), step, g, cfg["alpha_rg"])
     tune = bool(cfg.get("alpha_autotune", False))
     if tune and state.log_alpha is None:
         state.log_alpha = float(np.log(cfg["alpha"]))
     alpha = float(np.exp(state.log_alpha)) if tune else cfg["alpha"]
-    act = actor.actor_loss_and_grad(state.nets["pi"], state.nets["phi"], state.nets["psi"], s, g, eps,
+    act = actor.actor_loss_and_grad(state.nets["pi"], state.nets["phi"], state.nets["psi"], s, g_actor, eps,
                                     cfg["energy"], cfg["tau"], alpha)
     state.t_actor += 1
     state.nets["pi"], state.m["pi"], state.v["pi"] = adam_net(
