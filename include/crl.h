@@ -162,7 +162,13 @@ typedef struct crl_config {
   int32_t alpha_autotune;
   float target_entropy; /* -A by convention (crl_config_default: -8)               */
   float lr_alpha;       /* crl_config_default: 6e-4 (the actor's rate)             */
-  int32_t reserved;     /* zero                                                     */
+  /* random-goal actor mix (App. D; 0, the paper's choice, by default): in
+   * crl_update_step each sample's actor goal is, with probability alpha_rg,
+   * the relabelled goal of sample (b + 1) mod B (a goal of another, independently
+   * drawn transition), else its own; the choice is (word 2 of the sample's
+   * relabel Philox block) >> 32 < floor(alpha_rg 2^32).  The critic always
+   * takes the relabelled goals.  Grouped sweeps take alpha_rg = 0 only. */
+  float alpha_rg;
 } crl_config;
 
 /* Fill *cfg with the paper's defaults (App. B.3: batch 256, gamma 0.99,

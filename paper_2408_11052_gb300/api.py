@@ -45,7 +45,7 @@ class CrlConfig(ctypes.Structure):
                 ("adam_beta1", c_float), ("adam_beta2", c_float), ("adam_eps", c_float),
                 ("seed", c_uint64), ("agent", c_uint64),
                 ("alpha_autotune", c_int32), ("target_entropy", c_float), ("lr_alpha", c_float),
-                ("reserved", c_int32)]
+                ("alpha_rg", c_float)]
 
 
 class CrlTensorInfo(ctypes.Structure):
@@ -204,6 +204,7 @@ def make_config(w, precision="fp32", path="plain", agent=0, offset_min=1, penalt
     c.alpha_autotune = 1 if w.alpha_autotune else 0
     c.target_entropy = -float(w.A) if w.target_entropy is None else w.target_entropy
     c.lr_alpha = w.lr_actor if w.lr_alpha is None else w.lr_alpha
+    c.alpha_rg = w.alpha_rg
     for k, v in over.items():
         setattr(c, k, v)
     return c

@@ -75,6 +75,7 @@ void validate_config(const crl_config& c) {
   CRL_REQUIRE(c.temperature > 0.f && std::isfinite(c.temperature), CRL_E_INVALID_ARG, "temperature must be > 0");
   CRL_REQUIRE(c.beta_lse >= 0.f && c.alpha >= 0.f, CRL_E_INVALID_ARG, "beta_lse and alpha must be >= 0");
   CRL_REQUIRE(c.alpha_autotune == 0 || c.alpha_autotune == 1, CRL_E_INVALID_ARG, "alpha_autotune must be 0 or 1");
+  CRL_REQUIRE(c.alpha_rg >= 0.f && c.alpha_rg <= 1.f, CRL_E_INVALID_ARG, "alpha_rg must lie in [0, 1]");
   CRL_REQUIRE(!c.alpha_autotune || (c.alpha > 0.f && std::isfinite(c.target_entropy) && c.lr_alpha >= 0.f),
               CRL_E_INVALID_ARG, "alpha_autotune needs alpha > 0, a finite target_entropy and lr_alpha >= 0");
   CRL_REQUIRE(c.energy >= CRL_ENERGY_L2 && c.energy <= CRL_ENERGY_L2SQ, CRL_E_INVALID_ARG, "unknown energy");
@@ -654,6 +655,7 @@ int crl_create(const crl_config* cfg, crl_ctx** out) {
     c->bs = static_cast<float*>(c->dalloc((size_t)B * cf.D * sizeof(float)));
     c->ba = static_cast<float*>(c->dalloc((size_t)B * cf.A * sizeof(float)));
     c->bg = static_cast<float*>(c->dalloc((size_t)B * cf.G * sizeof(float)));
+    c->bg_act = static_cast<float*>(c->dalloc((size_t)B * cf.G * sizeof(float)));
     CRL_CHECK_CUDA(cudaMemset(c->loss, 0, 8 * e));
     CRL_CHECK_CUDA(cudaMemset(c->loss_f, 0, 8 * sizeof(float)));
     if (cf.precision == CRL_PREC_BF16) {
@@ -788,16 +790,24 @@ void update_body(crl_ctx* ctx, cudaStream_t st) {
   // the BF16 path has the relabel kernel pack the network inputs directly; the
   // actor-loss kernel advances the step counter
   relabel_impl(ctx, CRL_STEP_AUTO, B, ctx->bs, ctx->ba, ctx->bg, nullptr, st, ctx->bf16, false);
+  // random-goal actor mix: the actor takes its own goals (and its own input packs)
+  const bool mix = ctx->cfg.alpha_rg > 0.f;
+  const float* g_actor = ctx->bg;
+  if (mix) {
+    launch_actor_goals(B, ctx->cfg.G, ctx->bg, ctx->bg_act, ctx->cfg.seed, ctx->cfg.agent, &ctx->ctr->last_step,
+                       ctx->cfg.alpha_rg, st);
+    g_actor = ctx->bg_act;
+  }
   if (ctx->cfg.precision == CRL_PREC_FP64) {
     critic_impl<double>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
-    actor_impl<double>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st, true);
+    actor_impl<double>(ctx, ctx->bs, g_actor, nullptr, B, 1, st, true);
   } else if (ctx->bf16) {
     // the shadows follow the weights through the fused Adam; only the first call refreshes
-    critic_impl_bf16(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st, false, true, true);
-    actor_impl_bf16(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st, false, true, true, true);
+    critic_impl_bf16(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st, false, true, !mix);
+    actor_impl_bf16(ctx, ctx->bs, g_actor, nullptr, B, 1, st, false, !mix, !mix, true);
   } else {
     critic_impl<float>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
-    actor_impl<float>(ctx, ctx->bs, ctx->bg, nullptr, B, 1, st, true);
+    actor_impl<float>(ctx, ctx->bs, g_actor, nullptr, B, 1, st, true);
   }
 }
 }  // namespace crl

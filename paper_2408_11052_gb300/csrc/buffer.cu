@@ -7,6 +7,7 @@
 // observation, action and the absolute index of the last step of its episode
 // (see BufferDev in internal.h).  All environments insert in lockstep.
 #include <algorithm>
+#include <cmath>
 
 #include <cuda_bf16.h>
 
@@ -468,6 +469,30 @@ void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st)
 __global__ void bump_u64_kernel(unsigned long long* c) {
   pdl_enter();
   *c += 1ull;
+}
+
+// Random-goal actor mix (App. D): sample b takes the goal of sample (b + 1) mod B
+// when the top half of word 2 of its relabel Philox block falls below thr.
+__global__ void __launch_bounds__(256) actor_goals_kernel(int B, int G, const float* __restrict__ g,
+                                                         float* __restrict__ g_act, unsigned long long seed,
+                                                         unsigned long long agent,
+                                                         const unsigned long long* __restrict__ step_dev,
+                                                         unsigned long long thr) {
+  pdl_enter();
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const Philox4 r = philox4x64_10(*step_dev, (unsigned long long)b, 0ull, 0ull, seed, agent);
+  const int src = ((r.w[2] >> 32) < thr) ? (b + 1 == B ? 0 : b + 1) : b;
+  for (int c = 0; c < G; ++c) g_act[(size_t)b * G + c] = g[(size_t)src * G + c];
+}
+
+void launch_actor_goals(int B, int G, const float* g, float* g_act, uint64_t seed, uint64_t agent,
+                        const unsigned long long* step_dev, float alpha_rg, cudaStream_t st) {
+  // floor(alpha_rg 2^32), exact for a float alpha_rg in [0, 1]
+  const unsigned long long thr = (unsigned long long)std::floor((double)alpha_rg * 4294967296.0);
+  TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * G * 8.0);
+  launch_k(actor_goals_kernel, dim3(ceil_div(B, 256)), dim3(256), 0, st, B, G, g, g_act,
+           (unsigned long long)seed, (unsigned long long)agent, step_dev, thr);
 }
 
 void launch_bump_u64(unsigned long long* ctr, cudaStream_t st) {

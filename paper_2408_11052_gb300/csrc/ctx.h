@@ -86,6 +86,7 @@ struct crl_ctx {
   void* actor_ws = nullptr;  // per-block partial sums of the actor loss
   float* loss_f = nullptr;  // 8 floats: float copy of the loss parts
   float *bs = nullptr, *ba = nullptr, *bg = nullptr;  // batch of crl_update_step
+  float* bg_act = nullptr;                             // the actor's goals (random-goal mix)
   // host-input staging for crl_buffer_insert
   void* stage = nullptr;
   size_t stage_bytes = 0;

@@ -226,6 +226,11 @@ void adam_update(T* p, const T* g, T* m, T* v, int64_t n, const int* t_dev, int 
 
 // Small device utilities.
 void launch_bump_u64(unsigned long long* ctr, cudaStream_t st);
+// Random-goal actor mix (App. D): g_act[b] = g[(b + 1) mod B] when (word 2 of the
+// Philox block (*step_dev, b, 0, 0) keyed (seed, agent)) >> 32 < floor(alpha_rg 2^32),
+// else g[b].  step_dev: the step the relabel of g used.
+void launch_actor_goals(int B, int G, const float* g, float* g_act, uint64_t seed, uint64_t agent,
+                        const unsigned long long* step_dev, float alpha_rg, cudaStream_t st);
 
 // Sets the message crl_last_error(NULL) returns on the calling thread.
 void set_thread_error(const std::string& msg);

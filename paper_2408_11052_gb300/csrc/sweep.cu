@@ -304,9 +304,12 @@ int crl_sweep_create(const crl_config* cfgs, int32_t n, int32_t grouped, crl_swe
                       c.layers == c0.layers && (c.layernorm != 0) == (c0.layernorm != 0),
                   CRL_E_INVALID_ARG, "the agents of a sweep share precision, path, hidden width, depth and LayerNorm");
     }
-    if (grouped)
+    if (grouped) {
       CRL_REQUIRE(c0.precision == CRL_PREC_BF16 && c0.path == CRL_PATH_FUSED, CRL_E_UNSUPPORTED,
                   "the grouped sweep runs the BF16 fused path");
+      for (int i = 0; i < n; ++i)
+        CRL_REQUIRE(cfgs[i].alpha_rg == 0.f, CRL_E_UNSUPPORTED, "the grouped sweep takes alpha_rg = 0 only");
+    }
     sw = new crl_sweep();
     sw->grouped = grouped ? 1 : 0;
     for (int i = 0; i < n; ++i) {

@@ -58,6 +58,7 @@ class Workload:
     alpha_autotune: bool = False     # learn log(alpha) (reading P5); target entropy -A, lr = lr_actor
     target_entropy: float = None
     lr_alpha: float = None
+    alpha_rg: float = 0.0            # random-goal actor mix (reading P6)
 
     def goals(self):
         return tuple(range(self.G)) if self.goal_idx is None else tuple(self.goal_idx)

@@ -23,7 +23,7 @@ def oracle_steps(w, nets, buf, n_steps, start_step, inserts, check_kinks=False):
                loss=w.loss, sym_reduction=w.sym_reduction, beta=h["beta"], penalty_axis=w.penalty_axis,
                alpha=h["alpha"], lr_critic=h["lr_critic"], lr_actor=h["lr_actor"], adam_beta1=h["adam_beta1"],
                adam_beta2=h["adam_beta2"], adam_eps=h["adam_eps"], alpha_autotune=w.alpha_autotune,
-               target_entropy=h["target_entropy"], lr_alpha=h["lr_alpha"])
+               target_entropy=h["target_entropy"], lr_alpha=h["lr_alpha"], alpha_rg=float(np.float32(w.alpha_rg)))
     outs = []
     for i in range(n_steps):
         buf.insert(*inserts[i])
@@ -119,6 +119,54 @@ def test_update_steps_with_other_objectives_match_oracle(loss):
             for k in rl:
                 np.testing.assert_allclose(gl[k], rl[k], rtol=1e-9, atol=1e-12)
     assert ctx.sync_status() == (0, 0)
+
+
+@pytest.mark.parametrize("precision,path", [("fp64", "plain"), ("fp32", "plain"), ("bf16", "plain"),
+                                            ("bf16", "fused")])
+@pytest.mark.parametrize("alpha_rg", [0.5, 1.0])
+def test_random_goal_mix_matches_oracle(precision, path, alpha_rg):
+    """Random-goal actor mix (App. D): three update steps against the oracle's; the
+    critic parts keep the relabelled goals, the actor takes the mixed ones."""
+    w = small(B=64, repr=64, alpha_rg=alpha_rg)
+    ctx, nets, buf = setup(w, precision=precision, path=path, n=60)
+    extra = workload.buffer_contents(w, n=3, mean_len=9.0, seed_offset=11)
+    inserts = [tuple(x[i:i + 1] for x in extra) for i in range(3)]
+    start = 0
+    if precision != "bf16":
+        start = None
+        for cand in range(0, 48):
+            trial = oracle.relabel.ReplayBuffer(w.E, w.T, w.D, w.A)
+            trial.obs, trial.act, trial.done = buf.obs.copy(), buf.act.copy(), buf.done.copy()
+            if oracle_steps(w, nets, trial, 3, cand, inserts, check_kinks=True) is not None:
+                start = cand
+                break
+        assert start is not None
+    ctx.set_step(start)
+    loss_out = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+    got = []
+    for ins in inserts:
+        ctx.update_step(*(torch.from_numpy(x).to(ctx.device) for x in ins), loss_out=loss_out)
+        got.append(loss_out.cpu().numpy().astype(np.float64).copy())
+    _, outs = oracle_steps(w, nets, buf, 3, start, inserts)
+    rtol = {"fp64": 1.2e-7, "fp32": 2e-4, "bf16": 2e-2}[precision]
+    for g, ref in zip(got, outs):
+        np.testing.assert_allclose(g[0], ref["critic"]["total"], rtol=rtol)
+        np.testing.assert_allclose(g[4:6], [ref["actor_loss"], ref["logpi_mean"]], rtol=rtol, atol=1e-6)
+    assert ctx.sync_status() == (0, 0)
+
+
+def test_random_goal_mix_changes_only_the_actor():
+    """Same seeds with and without the mix: identical critic losses, different actor loss."""
+    out = {}
+    for a_rg in (0.0, 0.7):
+        w = small(B=64, alpha_rg=a_rg)
+        ctx, _, _ = setup(w, n=60)
+        loss_out = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+        ctx.update_step(*(torch.from_numpy(x).to(ctx.device) for x in workload.buffer_contents(w, n=1, seed_offset=3)),
+                        loss_out=loss_out)
+        out[a_rg] = loss_out.cpu().numpy()
+    np.testing.assert_array_equal(out[0.0][:4], out[0.7][:4])
+    assert out[0.0][4] != out[0.7][4]
 
 
 @pytest.mark.parametrize("precision,path", [("fp64", "plain"), ("fp32", "plain"), ("bf16", "plain"),

@@ -111,3 +111,6 @@ def test_sweep_rejects_mismatched_agents():
     with pytest.raises(api.CRLError) as e:
         api.CRLSweep(ws, "fp32", "plain", grouped=True)
     assert e.value.code == api.E_UNSUPPORTED
+    with pytest.raises(api.CRLError) as e:
+        api.CRLSweep([ws[0], ws[1].with_(alpha_rg=0.5)], "bf16", "fused", grouped=True)
+    assert e.value.code == api.E_UNSUPPORTED
