@@ -294,6 +294,24 @@ int crl_sync_status(crl_ctx* ctx, void* stream, uint32_t* status);
  * auto-tuning, else cfg.alpha.  Synchronous read. */
 int crl_get_alpha(crl_ctx* ctx, float* alpha);
 
+/* ---- collection stub (Algorithm 1's loop over environments) -------------
+ * The simulator is outside this library; this call stands in for it with
+ * synthetic dynamics so that the update-to-data loop (§5.6) runs end to end
+ * on the device.  n_steps environment steps for all E environments, each:
+ * a = tanh(mu + sigma eps) from the policy pi(s, g) (the actor's head, noise
+ * from its own Philox stream), the slice (s, a, done) appended to the replay
+ * buffer (done on an episode's last step, t = episode_length - 1), then
+ * s' = s + 0.1 xi + 0.05 a[d mod A] (xi ~ N(0, I)), or after an episode's last
+ * step a fresh s' ~ N(0, I) with a fresh commanded goal g' ~ N(0, I) [G].
+ * The first call draws every environment's first state and goal.  All draws:
+ * Box-Muller on Philox4x64-10 blocks (step, env, word, d / 4) keyed (seed,
+ * agent), words 2 (action), 3 (dynamics), 4 (reset state), 5 (reset goal); the
+ * collection counter starts at 0, the first states use 2^64 - 1.
+ * obs_out [n_steps][E][D], act_out [n_steps][E][A], done_out [n_steps][E]
+ * (device, optional): the slices inserted.  Async on `stream`. */
+int crl_collect(crl_ctx* ctx, int32_t n_steps, int32_t episode_length, float* obs_out, float* act_out,
+                uint8_t* done_out, void* stream);
+
 /* Message of the last failing call on ctx (ctx == NULL: on this thread). */
 const char* crl_last_error(const crl_ctx* ctx);
 

@@ -27,4 +27,4 @@ adam     Adam update (optimiser of the learning rates in App. B.3).
 step     one full CRL update step (Algorithm 1, inner loop body).
 """
 
-from . import philox, relabel, mlp, critic, actor, adam, step  # noqa: F401
+from . import philox, relabel, mlp, critic, actor, adam, step, collect  # noqa: F401

@@ -50,11 +50,12 @@ LOG_STD_MIN = -5.0
 LOG_STD_MAX = 2.0
 
 
-def gaussian_noise(seed, agent, step, B, A):
+def gaussian_noise(seed, agent, step, B, A, word=1):
     """eps [B][A] ~ N(0, 1) drawn from Philox4x64-10 by the Box-Muller transform.
 
-    Used when the update step draws its own actor noise (reading P1).  For row b
-    and element d: block (step, b, 1, d // 4) under key (seed, agent); words
+    Used when the update step draws its own actor noise (reading P1; ``word`` 1,
+    the collection stub's draws use 2 to 5).  For row b
+    and element d: block (step, b, word, d // 4) under key (seed, agent); words
     2q and 2q+1 (q = (d % 4) // 2) give u1, u2 = (top 53 bits + 1/2) / 2^53,
     and the element is sqrt(-2 ln u1) * (cos 2 pi u2 if d is even else sin 2 pi u2)
     (Box & Muller, 1958).
@@ -63,7 +64,7 @@ def gaussian_noise(seed, agent, step, B, A):
     eps = np.zeros((B, A))
     for b in range(B):
         for d in range(A):
-            w = philox4x64_10((step, b, 1, d // 4), (seed, agent))
+            w = philox4x64_10((step, b, word, d // 4), (seed, agent))
             q = (d % 4) // 2
             u1 = ((w[2 * q] >> 11) + 0.5) / 2.0 ** 53
             u2 = ((w[2 * q + 1] >> 11) + 0.5) / 2.0 ** 53

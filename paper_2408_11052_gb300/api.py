@@ -85,6 +85,7 @@ _SIGNATURES = {
     "crl_set_step": (c_int32, [c_void_p, c_uint64]),
     "crl_sync_status": (c_int32, [c_void_p, c_void_p, POINTER(c_uint32)]),
     "crl_get_alpha": (c_int32, [c_void_p, POINTER(c_float)]),
+    "crl_collect": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "crl_last_error": (ctypes.c_char_p, [c_void_p]),
     "crl_trace_start": (c_int32, [c_void_p, c_int32, c_int32]),
     "crl_trace_stop": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_double), POINTER(c_double)]),
@@ -332,6 +333,14 @@ class CRLContext:
         check(lib().crl_update_step(self.handle, ptr(obs), ptr(act), ptr(done), n, ptr(loss_out),
                                     stream_handle(stream)), self.handle)
         return loss_out
+
+    def collect(self, n_steps, episode_length=1000, out=None, stream=None):
+        """n_steps synthetic environment steps for all E environments, appended to the
+        replay buffer; out = (obs [n][E][D], act [n][E][A], done [n][E] uint8) device
+        tensors receive the slices (optional)."""
+        o = (None, None, None) if out is None else out
+        check(lib().crl_collect(self.handle, n_steps, episode_length, ptr(o[0]), ptr(o[1]), ptr(o[2]),
+                                stream_handle(stream)), self.handle)
 
     def get_alpha(self):
         """The entropy coefficient the next actor step uses."""

@@ -24,33 +24,8 @@ constexpr double kLogStdMin = -5.0;
 constexpr double kLogStdMax = 2.0;
 constexpr double kLog2 = 0.69314718055994530942;
 constexpr double kHalfLog2Pi = 0.91893853320467274178;
-constexpr double kTwoPi = 6.28318530717958647693;
 
 namespace {
-
-// N(0, 1) noise for element d of row b: Box-Muller on Philox4x64-10 block
-// (step, b, 1, d / 4); words (0, 1) feed elements 4q, 4q+1 and words (2, 3)
-// feed 4q+2, 4q+3 (cos / sin branch).
-// The FP64 path draws the noise in double; the FP32 path in float (same
-// Philox words, so the two agree to float rounding).
-template <typename T>
-__device__ T philox_normal(unsigned long long step, int b, int d, unsigned long long seed, unsigned long long agent) {
-  const Philox4 r = philox4x64_10(step, (unsigned long long)b, 1ull, (unsigned long long)(d / 4), seed, agent);
-  const int pair = (d % 4) / 2;
-  const double u1 = u64_to_unit_open(r.w[2 * pair]);
-  const double u2 = u64_to_unit_open(r.w[2 * pair + 1]);
-  if constexpr (sizeof(T) == 8) {
-    const double rad = sqrt(-2.0 * log(u1));
-    double s, c;
-    sincos(kTwoPi * u2, &s, &c);
-    return (d % 2 == 0) ? rad * c : rad * s;
-  } else {
-    const float rad = sqrtf(-2.0f * logf((float)u1));
-    float s, c;
-    sincosf((float)(kTwoPi * u2), &s, &c);
-    return (d % 2 == 0) ? rad * c : rad * s;
-  }
-}
 
 // One warp per row b, lanes over the action dims.
 // x0 != null: a' also goes into columns [x0_col, x0_col + A) of the split BF16
@@ -74,7 +49,7 @@ __device__ __forceinline__ void head_forward_body(const HeadFwdArgs<T>& p, int l
     const T mu = out[(size_t)b * 2 * A + d];
     const T lraw = out[(size_t)b * 2 * A + A + d];
     const T l = fmin(fmax(lraw, T(kLogStdMin)), T(kLogStdMax));
-    const T e = eps ? T(eps[(size_t)b * A + d]) : philox_normal<T>(step, b, d, seed, agent);
+    const T e = eps ? T(eps[(size_t)b * A + d]) : philox_normal<T>(step, b, 1ull + p.noise_extra, d, seed, agent);
     const T u = mu + dev_exp(l) * e;
     const T act = dev_tanh(u);
     a_new[(size_t)b * A + d] = act;
@@ -311,9 +286,10 @@ const char* multi_tables(BlobCache& cache, const std::vector<Task>& tasks, int r
 template <typename T>
 void actor_head_forward(const ActorSpec& as, const T* pi_out, const float* eps, const unsigned long long* step_dev,
                         uint64_t seed, uint64_t agent, int B, T* a_new, T* logpi, T* eps_used, cudaStream_t st,
-                        __nv_bfloat16* x0, int x0_ld, int x0_col) {
+                        __nv_bfloat16* x0, int x0_ld, int x0_col, int noise_extra) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 5);
-  const HeadFwdArgs<T> p{B, as.A, pi_out, eps, step_dev, seed, agent, a_new, logpi, eps_used, x0, x0_ld, x0_col};
+  const HeadFwdArgs<T> p{B,        as.A, pi_out, eps,   step_dev, seed,  agent,      a_new,
+                         logpi,    eps_used, x0, x0_ld, x0_col,   noise_extra};
   launch_k(head_forward_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, p);
 }
 
@@ -384,7 +360,7 @@ void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used
 #define CRL_INST_ACTOR(T)                                                                                        \
   template void actor_head_forward<T>(const ActorSpec&, const T*, const float*, const unsigned long long*,       \
                                       uint64_t, uint64_t, int, T*, T*, T*, cudaStream_t, __nv_bfloat16*, int,    \
-                                      int);                                                                      \
+                                      int, int);                                                                 \
   template void actor_energy_and_loss<T>(const ActorSpec&, const T*, const T*, const T*, int, int, T*, T*, T*,   \
                                          void*, unsigned*, unsigned*, int*, unsigned long long*,                 \
                                          const unsigned long long*, cudaStream_t, __nv_bfloat16*, int);          \

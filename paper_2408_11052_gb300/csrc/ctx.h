@@ -87,6 +87,17 @@ struct crl_ctx {
   float* loss_f = nullptr;  // 8 floats: float copy of the loss parts
   float *bs = nullptr, *ba = nullptr, *bg = nullptr;  // batch of crl_update_step
   float* bg_act = nullptr;                             // the actor's goals (random-goal mix)
+  // collection stub (crl_collect): environment state and staging, allocated on first use
+  struct Envs {
+    bool ready = false;
+    float* s = nullptr;                   // [E][D] current states
+    float* g = nullptr;                   // [E][G] current commanded goals
+    int32_t* t = nullptr;                 // [E] step within the episode
+    unsigned long long* step = nullptr;   // next collection step (Philox counter)
+    void *pi_out = nullptr, *a = nullptr, *logpi = nullptr, *eps = nullptr, *saved = nullptr;
+    float *obs = nullptr, *act = nullptr;  // one time slice for the insert
+    uint8_t* done = nullptr;
+  } env;
   // host-input staging for crl_buffer_insert
   void* stage = nullptr;
   size_t stage_bytes = 0;

@@ -146,7 +146,7 @@ template <typename T>
 void actor_head_forward(const ActorSpec& as, const T* pi_out, const float* eps,
                         const unsigned long long* step_dev, uint64_t seed, uint64_t agent, int B,
                         T* a_new, T* logpi, T* eps_used, cudaStream_t st, __nv_bfloat16* x0 = nullptr,
-                        int x0_ld = 0, int x0_col = 0);
+                        int x0_ld = 0, int x0_col = 0, int noise_extra = 0);
 template <typename T>
 struct ActorLossArgs {
   int B, R, energy;
@@ -180,6 +180,7 @@ struct HeadFwdArgs {
   T* eps_used;
   __nv_bfloat16* x0;                // optional split BF16 copy of a' (see actor_head_forward)
   int x0_ld, x0_col;
+  int noise_extra;                  // Philox stream word 1 + noise_extra (0: the actor; 1: the collection stub)
 };
 template <typename T>
 struct HeadBwdArgs {

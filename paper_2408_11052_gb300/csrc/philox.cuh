@@ -48,4 +48,30 @@ __device__ __forceinline__ double u64_to_unit_open(unsigned long long x) {
   return ((double)(x >> 11) + 0.5) * (1.0 / 9007199254740992.0);
 }
 
+// N(0, 1) draw for element d of row b: Box-Muller on the block (step, b, word, d / 4);
+// words (0, 1) feed elements 4q, 4q+1 and words (2, 3) feed 4q+2, 4q+3 (cos /
+// sin branch).  `word` separates the streams (1: the actor's noise; the
+// collection stub takes 2 to 5).  T = double draws in double, float in float
+// (the same Philox words, so the two agree to float rounding).
+template <typename T>
+__device__ T philox_normal(unsigned long long step, int b, unsigned long long word, int d, unsigned long long seed,
+                           unsigned long long agent) {
+  constexpr double kTwoPi = 6.28318530717958647693;
+  const Philox4 r = philox4x64_10(step, (unsigned long long)b, word, (unsigned long long)(d / 4), seed, agent);
+  const int pair = (d % 4) / 2;
+  const double u1 = u64_to_unit_open(r.w[2 * pair]);
+  const double u2 = u64_to_unit_open(r.w[2 * pair + 1]);
+  if constexpr (sizeof(T) == 8) {
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincos(kTwoPi * u2, &s, &c);
+    return (d % 2 == 0) ? rad * c : rad * s;
+  } else {
+    const float rad = sqrtf(-2.0f * logf((float)u1));
+    float s, c;
+    sincosf((float)(kTwoPi * u2), &s, &c);
+    return (d % 2 == 0) ? rad * c : rad * s;
+  }
+}
+
 }  // namespace crl
