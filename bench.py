@@ -303,6 +303,44 @@ def run_arm(args, w, precision, path, dev, world, rank, flush, full):
     return out
 
 
+def collect_loop(w, precision, path, dev, unroll=62, utd=16, rounds=1):
+    """Algorithm 1's outer loop with the collection stub: each round collects
+    `unroll` synthetic environment steps for all E environments (crl_collect),
+    then runs E * unroll / utd update steps (App. B.3: 1024 environments, unroll
+    62; §4.1 and §5.6: update-to-data ratio 1:16).  One warm-up round, then
+    `rounds` timed rounds (CUDA events on the stream)."""
+    import torch
+    from paper_2408_11052_gb300 import api
+
+    stream = torch.cuda.current_stream()
+    ctx = api.CRLContext(w, precision=precision, path=path)
+    for k, v in workload.init_agent(w).items():
+        ctx.load_network(k, v)
+    updates = w.E * unroll // utd
+    loss = torch.zeros(6, dtype=torch.float32, device=dev)
+    ctx.collect(max(unroll, 64), w.T)            # prefill before the first update
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * (rounds + 1))]
+    for r in range(rounds + 1):
+        ev[3 * r].record(stream)
+        ctx.collect(unroll, w.T)
+        ev[3 * r + 1].record(stream)
+        for _ in range(updates):
+            ctx.update_step(loss_out=loss)
+        ev[3 * r + 2].record(stream)
+    torch.cuda.synchronize()
+    rc, status = ctx.sync_status()
+    assert rc == api.OK, f"collect loop status {status}"
+    col = sum(ev[3 * r].elapsed_time(ev[3 * r + 1]) for r in range(1, rounds + 1)) / rounds
+    upd = sum(ev[3 * r + 1].elapsed_time(ev[3 * r + 2]) for r in range(1, rounds + 1)) / rounds
+    env_steps = w.E * unroll
+    return {"env_steps_per_s": env_steps / ((col + upd) / 1e3), "update_steps_per_s": updates / ((col + upd) / 1e3),
+            "envs": w.E, "unroll": unroll, "utd": f"1:{utd}", "updates_per_round": updates,
+            "collect_ms_per_round": col, "update_ms_per_round": upd, "rounds_timed": rounds,
+            "episode_length": w.T, "precision": precision, "path": path,
+            "note": "collection = crl_collect (synthetic dynamics standing in for the simulator, policy forward "
+                    "on all envs, insert); updates = crl_update_step graph replays"}
+
+
 def relabel_throughput(dev, flush, sizes=(1 << 20, 1 << 22), K=10, W=3):
     """Standalone sample + relabel launches on Humanoid-shaped rows (HBM-bound):
     samples/s and achieved GB/s per batch size."""
@@ -491,6 +529,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the FP32 plain arm")
     ap.add_argument("--no-relabel", action="store_true", help="skip the standalone relabel throughput")
+    ap.add_argument("--no-loop", action="store_true", help="skip the collection + update loop (UTD 1:16)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed GEMM tile rule (deterministic launch sequence for profiler captures)")
     ap.add_argument("--only-relabel", action="store_true",
@@ -566,6 +605,10 @@ def main():
         roof["traffic"] = traffic
         roof["traffic_source"] = "profiles/roofline_traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
 
+    loop = None
+    if rank == 0 and world == 1 and not args.no_loop:
+        loop = collect_loop(w, args.precision, args.path, dev)
+
     relabel = None
     if rank == 0 and world == 1 and not args.no_relabel:
         rw, res = relabel_throughput(dev, flush)
@@ -605,6 +648,8 @@ def main():
         line["comparator"] = comparator
     if relabel is not None:
         line["relabel"] = relabel
+    if loop is not None:
+        line["collect_loop"] = loop
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
