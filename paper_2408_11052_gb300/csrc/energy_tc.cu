@@ -70,6 +70,51 @@ Weights loss_weights(const LossSpec& ls) {
   return w;
 }
 
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.69314718055994531f;
+
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// F log2(e) of one pair from S = <x, y> and the row / column auxiliaries, with
+// k1 = log2(e) / tau.  EK 0: L2, 1: L2^2, 2: dot / cos (normalised operands).
+template <int EK>
+__device__ __forceinline__ float energy2(float s, float ax, float ay, float k1) {
+  if (EK == 0) return -sqrt_approx(fmaxf(ax + ay - 2.f * s, 0.f)) * k1;
+  if (EK == 1) return -fmaxf(ax + ay - 2.f * s, 0.f) * k1;
+  return s * k1;
+}
+
+// One thread's 32 columns of its row: S -> F log2(e) in place (-inf outside
+// the batch: columns >= jn of an edge tile), returning their maximum.
+template <int EK>
+__device__ __forceinline__ float tile_row(float (&v)[32], float ax, const float* __restrict__ ay, float k1, bool full,
+                                          int jn) {
+  float m = -INFINITY;
+  if (full) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      v[k] = energy2<EK>(v[k], ax, ay[k], k1);
+      m = fmaxf(m, v[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      v[k] = (k < jn) ? energy2<EK>(v[k], ax, ay[k], k1) : -INFINITY;
+      m = fmaxf(m, v[k]);
+    }
+  }
+  return m;
+}
+
 __device__ __forceinline__ float energy_of(int energy, float s, float ax, float ay, float inv_tau) {
   switch (energy) {
     case CRL_ENERGY_L2: return -sqrtf(fmaxf(ax + ay - 2.f * s, 0.f)) * inv_tau;
@@ -275,6 +320,9 @@ __device__ void finalize_loss(const FwdArgs& a, int n) {
 
 // One 128 x 128 tile (row tile I, column tile J) of an n x n tile grid.
 // global_maps: the tensor maps live in a device table (acquire them first).
+// OBJ: the body also handles the objectives outside InfoNCE (a separate
+// instantiation keeps the InfoNCE one within 64 registers, two CTAs per SM).
+template <bool OBJ>
 __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const FwdArgs& a, int I,
                                          int J, int n, bool global_maps) {
   extern __shared__ uint8_t smem_raw[];
@@ -287,7 +335,8 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   float* part = reinterpret_cast<float*>(smem + (opnd > ftile ? opnd : ftile));  // [2][4][128] (m, s)
   float* opart = part + 2 * 4 * kTile;                                            // [2][4][128] objective
   float* s_d = opart + 2 * 4 * kTile;                                             // [128] anchor F_ii
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_d + kTile);
+  float* s_ay = s_d + kTile;                                                       // [128] column auxiliaries
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_ay + kTile);
   uint64_t* load_bar = bars;
   uint64_t* mma_bar = bars + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
@@ -340,7 +389,8 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
     }
   }
   __syncwarp();
-  const bool anchored = a.obj == CRL_LOSS_DPO || a.obj == CRL_LOSS_IPO;
+  if (tid < kTile) s_ay[tid] = (j0 + tid < a.B) ? a.auxY[j0 + tid] : 0.f;
+  const bool anchored = OBJ && (a.obj == CRL_LOSS_DPO || a.obj == CRL_LOSS_IPO);
   if (anchored) {
     // the anchor F_ii of this tile's rows while the MMA runs: 4 threads per row,
     // each R / 4 columns of the BF16 operand rows (8 per 16-byte load)
@@ -372,36 +422,37 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
   const int r = lg * 32 + lane;  // row of this thread within the tile
   if (all_ok) {
+    // F log2(e) of this thread's row r and columns 32 q .. 32 q + 31 (interior
+    // tiles skip the bounds tests), the row's maximum and sum of 2^(F log2 e - max)
     const int i = i0 + r;
     const float ax = (i < a.B) ? a.auxX[i] : 0.f;
+    const float k1 = a.inv_tau * kLog2e;
+    const bool full = i0 + kTile <= a.B && j0 + kTile <= a.B;
+    const int jn = (i < a.B) ? min(32, a.B - (j0 + q * 32)) : 0;  // valid columns of the 32
     float v[32];
     tc::tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + q * 32, v);
-    float m = -INFINITY;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const int j = j0 + q * 32 + k;
-      float f = -INFINITY;
-      if (i < a.B && j < a.B) {
-        f = energy_of(a.energy, v[k], ax, a.auxY[j], a.inv_tau);
-        if (i == j) a.diag[i] = f;
-      }
-      v[k] = f;
-      Ft[r * 129 + q * 32 + k] = f;
-      m = fmaxf(m, f);
+    float m2;
+    switch (a.energy) {
+      case CRL_ENERGY_L2: m2 = tile_row<0>(v, ax, s_ay + q * 32, k1, full, jn); break;
+      case CRL_ENERGY_L2SQ: m2 = tile_row<1>(v, ax, s_ay + q * 32, k1, full, jn); break;
+      default: m2 = tile_row<2>(v, ax, s_ay + q * 32, k1, full, jn); break;
     }
     float sum = 0.f;
-    if (m > -INFINITY) {
 #pragma unroll
-      for (int k = 0; k < 32; ++k) sum += __expf(v[k] - m);
+    for (int k = 0; k < 32; ++k) {
+      Ft[r * 129 + q * 32 + k] = v[k];
+      sum += ex2(v[k] - m2);
     }
-    part[(0 * 4 + q) * kTile + r] = m;
+    if (m2 == -INFINITY) sum = 0.f;
+    part[(0 * 4 + q) * kTile + r] = m2 * kLn2;
     part[(1 * 4 + q) * kTile + r] = sum;
-    if (a.obj >= CRL_LOSS_FB) {
-      // this row's objective terms over the thread's 32 columns (v[k] = -inf off the batch)
+    if (OBJ && a.obj >= CRL_LOSS_FB) {
+      // this row's objective terms over the thread's 32 columns, F = v[k] ln 2
       // (one fully unrolled loop per objective keeps v[] in registers)
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] *= kLn2;
       float vp = 0.f, kp = 0.f;
       const float d = anchored ? s_d[r] : 0.f;
-      const int jn = (i < a.B) ? min(32, a.B - (j0 + q * 32)) : 0;  // valid columns of the 32
       const int jd = i - (j0 + q * 32);                              // the diagonal's column, if here
       switch (a.obj) {
         case CRL_LOSS_FB:
@@ -446,15 +497,16 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   __syncthreads();
   if (all_ok) {
     if (tid < kTile) {
-      // merge the four column-group partials of row tid
+      // merge the four column-group partials of row tid; a diagonal tile leaves F_ii
       const int i = i0 + tid;
+      if (I == J && i < a.B) a.diag[i] = Ft[tid * 129 + tid] * kLn2;
       float m = part[tid], s = part[4 * kTile + tid];
       for (int g = 1; g < 4; ++g) lse_merge(m, s, part[g * kTile + tid], part[(4 + g) * kTile + tid]);
       if (i < a.B) {
         float* rp = a.rowpart + ((size_t)J * a.B + i) * 2;
         rp[0] = m;
         rp[1] = s;
-        if (a.obj >= CRL_LOSS_FB) {
+        if (OBJ && a.obj >= CRL_LOSS_FB) {
           // the four column groups in order
           float* op = a.objpart + ((size_t)J * a.B + i) * 2;
           op[0] = opart[tid] + opart[kTile + tid] + opart[2 * kTile + tid] + opart[3 * kTile + tid];
@@ -466,13 +518,17 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   __syncthreads();
   if (all_ok) {
     // column partials: thread (column c, row group g) over rows 32 g .. 32 g + 31
+    // (F log2 e in the tile; the partials in natural units like the rows')
     const int c = tid % kTile, g = tid / kTile;
-    float m = -INFINITY;
-    for (int rr = 0; rr < 32; ++rr) m = fmaxf(m, Ft[(32 * g + rr) * 129 + c]);
+    const float* col = Ft + (32 * g) * 129 + c;
+    float m2 = -INFINITY;
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) m2 = fmaxf(m2, col[rr * 129]);
     float sum = 0.f;
-    if (m > -INFINITY)
-      for (int rr = 0; rr < 32; ++rr) sum += __expf(Ft[(32 * g + rr) * 129 + c] - m);
-    part[g * kTile + c] = m;
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) sum += ex2(col[rr * 129] - m2);
+    if (m2 == -INFINITY) sum = 0.f;
+    part[g * kTile + c] = m2 * kLn2;
     part[(4 + g) * kTile + c] = sum;
   }
   __syncthreads();
@@ -521,10 +577,11 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                          const __grid_constant__ CUtensorMap tmY,
-                                                          const __grid_constant__ FwdArgs a) {
-  fwd_body(&tmX, &tmY, a, blockIdx.y, blockIdx.x, gridDim.x, false);
+template <bool OBJ>
+__global__ void __launch_bounds__(kThreads, OBJ ? 1 : 2) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                                   const __grid_constant__ CUtensorMap tmY,
+                                                                   const __grid_constant__ FwdArgs a) {
+  fwd_body<OBJ>(&tmX, &tmY, a, blockIdx.y, blockIdx.x, gridDim.x, false);
 }
 
 // ---- backward ---------------------------------------------------------------------
@@ -559,14 +616,6 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int chunk) {
 // rows 32 (w % 4) .., columns 32 (w / 4) ..), and the MMA adds H other into
 // the TMEM accumulator.
 // CTAs [0, nrow) run the row pass (own = phi), CTAs [nrow, 2 nrow) the column pass (own = psi).
-constexpr float kLog2e = 1.4426950408889634f;
-
-__device__ __forceinline__ float ex2(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // Per-row constants of the coefficient tile (own side = this thread's row).
 struct HCoef {
   float a_own;    // own auxiliary (|x|^2 for the L2 energies)
@@ -625,7 +674,10 @@ __device__ __forceinline__ float objective_coef(float f2, bool diag, float d_row
 // factor 1 / (tau d), zero where d < 1e-12), 1: L2^2 (F = -d^2 / tau, factor
 // 2 / tau), 2: dot / cos (F = s / tau, factor 1 / tau).  The BF16-rounded
 // coefficients are packed in pairs and summed into rowsum.
-template <int EK, int OBJ>
+// LIVE: which softmax terms carry weight in this pass (0: both, 1: own only,
+// 2: other only); a term whose coefficient is zero for the whole pass (one
+// InfoNCE direction, a one-axis penalty) costs no exp2.
+template <int EK, int OBJ, int LIVE>
 __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, const float* s_aux,
                                         const float* s_lse2, const float* s_koth, const float* s_dv,
                                         const float* s_kv, int q, int u, int v0, int B, float& rowsum,
@@ -652,7 +704,10 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
         f2 = sval * hc.k1;
         fac = hc.inv_tau;
       }
-      float g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - s_lse2[cl]) * s_koth[cl]);
+      float g;
+      if (LIVE == 1) g = ex2(f2 - hc.l_own2) * hc.k_own;
+      else if (LIVE == 2) g = ex2(f2 - s_lse2[cl]) * s_koth[cl];
+      else g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - s_lse2[cl]) * s_koth[cl]);
       if (u == v) g -= hc.k_diag;
       if (OBJ != kObjInfo) {
         const float d_row = hc.transposed ? s_dv[cl] : hc.d_own;
@@ -755,6 +810,9 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   hc.l_own2 = l_own * kLog2e;
   hc.k_own = a.scale * (w_own + 2.f * a.beta * p_own * l_own);
   hc.k_diag = a.scale * (a.w.wf + a.w.wb);
+  const bool own_live = w_own != 0.f || (a.beta != 0.f && p_own != 0.f);
+  const bool oth_live = w_oth != 0.f || (a.beta != 0.f && p_oth != 0.f);
+  const int live = (own_live && oth_live) ? 0 : (oth_live ? 2 : 1);
   hc.inv_tau = a.inv_tau;
   hc.k1 = a.inv_tau * kLog2e;
   constexpr bool kAnchored = OBJ == kObjDPO || OBJ == kObjIPO;
@@ -824,15 +882,20 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
       float sv[32];
       tc::tmem_ld32(tS + lane_off + q * 32, sv);
       uint32_t packed[16];
-      switch (a.energy) {
-        case CRL_ENERGY_L2:
-          build_h<0, OBJ>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, rowsum, packed);
-          break;
-        case CRL_ENERGY_L2SQ:
-          build_h<1, OBJ>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, rowsum, packed);
-          break;
-        default: build_h<2, OBJ>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, rowsum, packed); break;
+#define CRL_BUILD_H(EK, LV) build_h<EK, OBJ, LV>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, rowsum, packed)
+      const int ek = a.energy == CRL_ENERGY_L2 ? 0 : (a.energy == CRL_ENERGY_L2SQ ? 1 : 2);
+      switch (3 * ek + live) {
+        case 0: CRL_BUILD_H(0, 0); break;
+        case 1: CRL_BUILD_H(0, 1); break;
+        case 2: CRL_BUILD_H(0, 2); break;
+        case 3: CRL_BUILD_H(1, 0); break;
+        case 4: CRL_BUILD_H(1, 1); break;
+        case 5: CRL_BUILD_H(1, 2); break;
+        case 6: CRL_BUILD_H(2, 0); break;
+        case 7: CRL_BUILD_H(2, 1); break;
+        default: CRL_BUILD_H(2, 2); break;
       }
+#undef CRL_BUILD_H
       // columns 32 q .. +31 = K-block q / 2, 16-byte chunks (q % 2) * 4 .. +3
       uint8_t* hb = Hs + (q / 2) * 16384;
 #pragma unroll
@@ -943,11 +1006,12 @@ __global__ void __launch_bounds__(1024) prep_multi_kernel(const EnergyTask* __re
   prep_body(t.B, t.R, t.energy, t.ldt, lb < half ? t.s0 : t.s1, lb < half ? lb : lb - half);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) fwd_multi_kernel(const EnergyTask* __restrict__ tasks,
-                                                               const int* __restrict__ begin, int n) {
+template <bool OBJ>
+__global__ void __launch_bounds__(kThreads, OBJ ? 1 : 2) fwd_multi_kernel(const EnergyTask* __restrict__ tasks,
+                                                                         const int* __restrict__ begin, int n) {
   int lb, nb;
   const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];
-  fwd_body(&t.tmX, &t.tmY, t.f, lb / t.n, lb % t.n, t.n, true);
+  fwd_body<OBJ>(&t.tmX, &t.tmY, t.f, lb / t.n, lb % t.n, t.n, true);
 }
 
 template <int OBJ>
@@ -960,7 +1024,7 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_multi_kernel(const EnergyTask
 
 size_t fwd_smem(int R) {
   const size_t opnd = (size_t)2 * (R / 64) * 16384, ftile = (size_t)kTile * 129 * 4;
-  return (opnd > ftile ? opnd : ftile) + (2 * 2 * 4 + 1) * kTile * 4 + 1024 + 64;
+  return (opnd > ftile ? opnd : ftile) + (2 * 2 * 4 + 2) * kTile * 4 + 1024 + 64;
 }
 size_t bwd_smem(int R) {
   const size_t ybytes = std::max<size_t>((size_t)(R / 64) * 16384, (size_t)2 * R * 128);
@@ -1096,11 +1160,13 @@ void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, flo
   const size_t sm = fwd_smem(e.R);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
+    cudaFuncSetAttribute(fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
+    cudaFuncSetAttribute(fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
     attr = true;
   }
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * B * e.R);
-  launch_k(fwd_kernel, dim3(n, n), dim3(kThreads), sm, st, e.tmX, e.tmY, a);
+  if (ls.loss >= CRL_LOSS_FB) launch_k(fwd_kernel<true>, dim3(n, n), dim3(kThreads), sm, st, e.tmX, e.tmY, a);
+  else launch_k(fwd_kernel<false>, dim3(n, n), dim3(kThreads), sm, st, e.tmX, e.tmY, a);
 }
 
 namespace {
@@ -1215,10 +1281,14 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
   } else if (stage == 1) {
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(fwd_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
+      cudaFuncSetAttribute(fwd_multi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
+      cudaFuncSetAttribute(fwd_multi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
       attr = true;
     }
-    launch_k(fwd_multi_kernel, dim3(begin[na]), dim3(kThreads), fwd_smem(Rmax), st, dt, db, na);
+    bool obj = false;
+    for (const EnergyAgent& g : agents) obj = obj || g.ls.loss >= CRL_LOSS_FB;
+    if (obj) launch_k(fwd_multi_kernel<true>, dim3(begin[na]), dim3(kThreads), fwd_smem(Rmax), st, dt, db, na);
+    else launch_k(fwd_multi_kernel<false>, dim3(begin[na]), dim3(kThreads), fwd_smem(Rmax), st, dt, db, na);
   } else {
     // one launch per objective kind present (the agents of one kind in a table of their own)
     int kinds = 0;
