@@ -673,8 +673,6 @@ int crl_create(const crl_config* cfg, crl_ctx** out) {
       e.ldt = B;
       e.X = static_cast<__nv_bfloat16*>(c->dalloc((size_t)B * R * 2));
       e.Y = static_cast<__nv_bfloat16*>(c->dalloc((size_t)B * R * 2));
-      e.XT = static_cast<__nv_bfloat16*>(c->dalloc((size_t)B * R * 2));
-      e.YT = static_cast<__nv_bfloat16*>(c->dalloc((size_t)B * R * 2));
       e.auxX = static_cast<float*>(c->dalloc((size_t)B * 4));
       e.auxY = static_cast<float*>(c->dalloc((size_t)B * 4));
       c->etc_ws = c->dalloc(energy_tc_ws_bytes(B));

@@ -169,7 +169,7 @@ __device__ __forceinline__ void prep_body(int B, int R, int energy, int ldt, con
     tile[w][lane] = v;
     __syncthreads();
     const int cc = c0 + w, rr = lb * 32 + lane;
-    if (cc < R && rr < B) XT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
+    if (XT && cc < R && rr < B) XT[(size_t)cc * ldt + rr] = __float2bfloat16_rn(tile[lane][w]);
     __syncthreads();
   }
 }
@@ -726,23 +726,19 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
 
 // lb in [0, 2 nrow): the row pass for lb < nrow, else the column pass.
 template <int OBJ>
-__device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const CUtensorMap* tmXT,
-                                         const CUtensorMap* tmYT, const BwdArgs& row, const BwdArgs& col, int nrow,
-                                         int lb, bool global_maps) {
+__device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const BwdArgs& row,
+                                         const BwdArgs& col, int nrow, int lb, bool global_maps) {
   const bool colpass = lb >= nrow;
   const BwdArgs a = colpass ? col : row;
   const CUtensorMap* tmOwn = colpass ? tmY : tmX;
   const CUtensorMap* tmOther = colpass ? tmX : tmY;
-  const CUtensorMap* tmOtherT = colpass ? tmXT : tmYT;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   const int nk = a.R / 64;
   uint8_t* Xs = smem;                                  // own tile                 nk x 16 KiB
-  uint8_t* Ys = Xs + nk * 16384;                       // other tile, then other^T  max(nk x 16 KiB, 2 R 128 B)
-  const int ybytes = (nk * 16384 > 2 * a.R * 128) ? nk * 16384 : 2 * a.R * 128;
-  uint8_t* Hs = Ys + ybytes;                           // H tile                   2 x 16 KiB
-  float* s_lse = reinterpret_cast<float*>(Hs + 2 * 16384);  // [128] column logsumexp of the other side
-  float* s_aux = s_lse + kTile;                             // [128]
+  uint8_t* Ys = Xs + nk * 16384;                       // other tile               nk x 16 KiB
+  uint8_t* Hs = Ys + nk * 16384;                       // H tile                   2 x 16 KiB
+  float* s_aux = reinterpret_cast<float*>(Hs + 2 * 16384);  // [128]
   float* s_red = s_aux + kTile;                             // [4][128] partial sums
   float* s_lse2 = s_red + 4 * kTile;                        // [128] other side's logsumexp x log2(e)
   float* s_koth = s_lse2 + kTile;                           // [128] other side's coefficient (see HCoef)
@@ -751,10 +747,9 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   uint64_t* bars = reinterpret_cast<uint64_t*>(s_kv + kTile);
   uint64_t* xload = bars;
   uint64_t* yload = bars + 1;
-  uint64_t* ytload = bars + 2;
-  uint64_t* s_done = bars + 3;
-  uint64_t* h_done = bars + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
+  uint64_t* s_done = bars + 2;
+  uint64_t* h_done = bars + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
   const uint32_t tcols = (128 + a.R <= 256) ? 256u : 512u;
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -766,14 +761,11 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     if (global_maps) {
       tc::tmap_acquire(tmOwn);
       tc::tmap_acquire(tmOther);
-      tc::tmap_acquire(tmOtherT);
     }
     tc::prefetch_tmap(tmOwn);
     tc::prefetch_tmap(tmOther);
-    tc::prefetch_tmap(tmOtherT);
     tc::mbar_init(xload, 1);
     tc::mbar_init(yload, 1);
-    tc::mbar_init(ytload, 1);
     tc::mbar_init(s_done, 1);
     tc::mbar_init(h_done, 1);
     tc::fence_mbar_init();
@@ -834,7 +826,6 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     if (tid < kTile) {
       const int v = v0 + tid;
       const float lo = (v < a.B) ? a.lse_other[v] : 0.f;
-      s_lse[tid] = lo;
       s_aux[tid] = (v < a.B) ? a.aux_other[v] : 0.f;
       s_lse2[tid] = lo * kLog2e;
       s_koth[tid] = a.scale * (w_oth + 2.f * a.beta * p_oth * lo);
@@ -870,13 +861,6 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     ok = __syncthreads_and(ok ? 1 : 0) != 0;
     if (!ok) break;
     tc::fence_after_sync();
-    if (tid == 0) {
-      // S is done with the other tile: bring in other^T (2 K-blocks over v, R rows) in its place
-      tc::mbar_arrive_expect_tx(ytload, (uint32_t)(2 * a.R * 128));
-      for (int kb = 0; kb < 2; ++kb)
-        for (int qq = 0; qq < a.R / 64; ++qq)
-          tc::tma_load_2d(Ys + kb * a.R * 128 + qq * 8192, tmOtherT, ytload, v0 + 64 * kb, 64 * qq);
-    }
     // coefficient tile H: this thread's row r, columns 32 q .. 32 q + 31
     {
       float sv[32];
@@ -909,19 +893,19 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 32) {
+      // the other tile itself is the MN-major B operand (K = its 128 rows, N = R):
+      // K steps of 16 rows are 2048 bytes, R chunks of 64 columns 16 KiB apart
       tc::fence_after_sync();
-      if (tc::mbar_wait(ytload, vt & 1)) {
-        const uint32_t idesc = tc::idesc_bf16_f32(128, a.R);
-        for (int kb = 0; kb < 2; ++kb) {
-          const uint64_t dh = tc::sdesc_kmajor_sw128(Hs + kb * 16384);
-          const uint64_t dt = tc::sdesc_kmajor_sw128(Ys + kb * a.R * 128);
+      const uint32_t idesc = tc::idesc_bf16_f32_bmn(128, a.R);
+      for (int kb = 0; kb < 2; ++kb) {
+        const uint64_t dh = tc::sdesc_kmajor_sw128(Hs + kb * 16384);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) tc::mma_bf16(tAcc, dh + 2 * k, dt + 2 * k, idesc, (vt | kb | k) ? 1u : 0u);
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t dt = tc::sdesc_mnmajor_sw128(Ys + kb * 8192 + k * 2048, 16384);
+          tc::mma_bf16(tAcc, dh + 2 * k, dt, idesc, (vt | kb | k) ? 1u : 0u);
         }
-        tc::mma_commit(h_done);
-      } else {
-        atomicOr(a.status, CRL_STATUS_TIMEOUT);
       }
+      tc::mma_commit(h_done);
     }
     __syncwarp();
   }
@@ -978,11 +962,9 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
 template <int OBJ>
 __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant__ CUtensorMap tmX,
                                                           const __grid_constant__ CUtensorMap tmY,
-                                                          const __grid_constant__ CUtensorMap tmXT,
-                                                          const __grid_constant__ CUtensorMap tmYT,
                                                           const __grid_constant__ BwdArgs row,
                                                           const __grid_constant__ BwdArgs col, int nrow) {
-  bwd_body<OBJ>(&tmX, &tmY, &tmXT, &tmYT, row, col, nrow, blockIdx.x, false);
+  bwd_body<OBJ>(&tmX, &tmY, row, col, nrow, blockIdx.x, false);
 }
 
 // ---- several agents in one launch ------------------------------------------------
@@ -990,7 +972,7 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant_
 // owns the blocks [begin[s], begin[s+1]) of each launch: 2 ceil(B / 32) prep
 // blocks (phi then psi), n^2 forward tiles, 2 n backward CTAs.
 struct alignas(64) EnergyTask {
-  CUtensorMap tmX, tmY, tmXT, tmYT;
+  CUtensorMap tmX, tmY;
   FwdArgs f;
   BwdArgs row, col;
   PrepSide s0, s1;
@@ -1019,7 +1001,7 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_multi_kernel(const EnergyTask
                                                                const int* __restrict__ begin, int n) {
   int lb, nb;
   const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];
-  bwd_body<OBJ>(&t.tmX, &t.tmY, &t.tmXT, &t.tmYT, t.row, t.col, t.n, lb, true);
+  bwd_body<OBJ>(&t.tmX, &t.tmY, t.row, t.col, t.n, lb, true);
 }
 
 size_t fwd_smem(int R) {
@@ -1027,8 +1009,7 @@ size_t fwd_smem(int R) {
   return (opnd > ftile ? opnd : ftile) + (2 * 2 * 4 + 2) * kTile * 4 + 1024 + 64;
 }
 size_t bwd_smem(int R) {
-  const size_t ybytes = std::max<size_t>((size_t)(R / 64) * 16384, (size_t)2 * R * 128);
-  return (size_t)(R / 64) * 16384 + ybytes + 2 * 16384 + (2 + 4 + 2 + 2) * kTile * 4 + 1024 + 64;
+  return (size_t)2 * (R / 64) * 16384 + 2 * 16384 + (1 + 4 + 1 + 1 + 2) * kTile * 4 + 1024 + 64;
 }
 
 FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* loss4, float* r, float* c,
@@ -1141,8 +1122,6 @@ const char* energy_tc_maps(EnergyTc& e, int B) {
   const char* err;
   if ((err = mk(&e.tmX, e.X, e.R, B, e.R))) return err;
   if ((err = mk(&e.tmY, e.Y, e.R, B, e.R))) return err;
-  if ((err = mk(&e.tmXT, e.XT, B, e.R, e.ldt))) return err;
-  if ((err = mk(&e.tmYT, e.YT, B, e.R, e.ldt))) return err;
   e.tm_B = B;
   return nullptr;
 }
@@ -1177,7 +1156,7 @@ void launch_bwd_t(const EnergyTc& e, const BwdArgs& a, const BwdArgs& b, int n, 
     cudaFuncSetAttribute(bwd_kernel<OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(256));
     attr = true;
   }
-  launch_k(bwd_kernel<OBJ>, dim3(2 * n), dim3(kThreads), sm, st, e.tmX, e.tmY, e.tmXT, e.tmYT, a, b, n);
+  launch_k(bwd_kernel<OBJ>, dim3(2 * n), dim3(kThreads), sm, st, e.tmX, e.tmY, a, b, n);
 }
 
 template <int OBJ>
@@ -1245,8 +1224,6 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     const EnergyTc& e = *g.e;
     t.tmX = e.tmX;
     t.tmY = e.tmY;
-    t.tmXT = e.tmXT;
-    t.tmYT = e.tmYT;
     t.B = g.B;
     t.R = e.R;
     t.energy = g.ls.energy;

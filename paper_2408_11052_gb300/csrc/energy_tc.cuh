@@ -14,9 +14,10 @@ namespace crl {
 // BF16 operands and per-row auxiliaries of the fused energy stage for batches up to Bmax.
 struct EnergyTc {
   int R = 0, Bmax = 0, ldt = 0;
-  __nv_bfloat16 *X = nullptr, *XT = nullptr, *Y = nullptr, *YT = nullptr;  // [Bmax][R], [R][Bmax]
-  float *auxX = nullptr, *auxY = nullptr;                                    // [Bmax]
-  CUtensorMap tmX, tmY, tmXT, tmYT;
+  __nv_bfloat16 *X = nullptr, *Y = nullptr;   // [Bmax][R]
+  __nv_bfloat16 *XT = nullptr, *YT = nullptr; // optional transposed copies [R][ldt] (null: not written)
+  float *auxX = nullptr, *auxY = nullptr;     // [Bmax]
+  CUtensorMap tmX, tmY;
   int tm_B = -1;
 };
 

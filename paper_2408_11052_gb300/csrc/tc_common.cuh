@@ -119,6 +119,22 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(const void* tile) {
   return d;
 }
 
+// Shared-memory matrix descriptor of an MN-major operand tile with the
+// 128-byte swizzle: rows of 128 bytes (64 BF16 along MN) for one K index,
+// 8-K-row groups 1024 bytes apart (stride byte offset), and the next 64
+// MN elements `lbo` bytes further (leading byte offset).  A K-major tile
+// written by TMA with the 128-byte swizzle, [MN-chunk][rows][64], read with
+// K = its rows and MN = its columns, is this layout with lbo = the chunk size.
+__device__ __forceinline__ uint64_t sdesc_mnmajor_sw128(const void* tile, uint32_t lbo) {
+  const uint64_t addr = smem_u32(tile);
+  uint64_t d = (addr >> 4) & 0x3FFFull;      // bits  0-13: start address >> 4
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;  // bits 16-29: leading byte offset >> 4
+  d |= (uint64_t)(1024 >> 4) << 32;          // bits 32-45: stride byte offset = 1024 B
+  d |= 1ull << 46;                           // bits 46-47: descriptor version 1
+  d |= 2ull << 61;                           // bits 61-63: 128-byte swizzle
+  return d;
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: BF16 A and B, FP32
 // accumulator, both operands K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
@@ -129,6 +145,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | ((uint32_t)(N >> 3) << 17)          // N / 8
          | ((uint32_t)(M >> 4) << 24);         // M / 16
 }
+// The same with B MN-major (bit 16).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_bmn(int M, int N) { return idesc_bf16_f32(M, N) | (1u << 16); }
 
 // D[tmem] (+)= A[smem] * B[smem]^T for one K = 16 slice.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,

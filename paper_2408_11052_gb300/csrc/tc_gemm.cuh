@@ -45,7 +45,7 @@ enum EpiKind : int {
   kEpiBwdDW0 = 6,     // split first layer: dW[m][c] = acc[2c] + acc[2c+1], db[m] = acc[2 kin]
   kEpiDX0 = 7,        // dx [M][nc] = acc columns [c0, c0 + nc)
   kEpiFwdOutEnergy = 8,  // output layer feeding the fused energy: y = acc + b FP32 [M][ld0], the BF16
-                         // energy operand x = y * s [M][N] (out1) and x^T [N][ld1] (out2), aux [M];
+                         // energy operand x = y * s [M][N] (out1), optionally x^T [N][ld1] (out2), aux [M];
                          // s = 1 / |y| and aux = s for the cosine energy, else s = 1 and aux = |bf16(y)|^2.
                          // The tile must span the whole row (the launch picks BN >= N).
 };
@@ -283,7 +283,8 @@ __device__ __forceinline__ void epilogue_energy(const EpiDesc& e, int row, uint3
     for (int i = 0; i < 32; ++i) v[i] = (v[i] + b[i]) * scale;
     store_bf16x32(X + (size_t)row * N + c, v);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) XT[(size_t)(c + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
+    for (int i = 0; i < 32; ++i)
+      if (XT) XT[(size_t)(c + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
   }
 }
 
