@@ -328,18 +328,20 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   const int nk = a.R / 64;
-  uint8_t* Xs = smem;
-  uint8_t* Ys = smem + nk * 16384;
+  // operands: a two-stage ring of 64-wide K chunks (X chunk, then Y chunk, 16 KiB
+  // each), so that two CTAs fit on an SM at every repr; the F tile reuses it
+  const int nst = nk < 2 ? nk : 2;
   float* Ft = reinterpret_cast<float*>(smem);  // reused after the MMA: [128][129]
-  const size_t opnd = (size_t)2 * nk * 16384, ftile = (size_t)kTile * 129 * 4;
+  const size_t opnd = (size_t)nst * 32768, ftile = (size_t)kTile * 129 * 4;
   float* part = reinterpret_cast<float*>(smem + (opnd > ftile ? opnd : ftile));  // [2][4][128] (m, s)
   float* opart = part + 2 * 4 * kTile;                                            // [2][4][128] objective
   float* s_d = opart + 2 * 4 * kTile;                                             // [128] anchor F_ii
   float* s_ay = s_d + kTile;                                                       // [128] column auxiliaries
   uint64_t* bars = reinterpret_cast<uint64_t*>(s_ay + kTile);
-  uint64_t* load_bar = bars;
-  uint64_t* mma_bar = bars + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  uint64_t* full = bars;        // [2]
+  uint64_t* empty = bars + 2;   // [2]
+  uint64_t* mma_bar = bars + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int lg = warp % 4, q = warp / 4;
@@ -351,7 +353,10 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
     }
     tc::prefetch_tmap(tmX);
     tc::prefetch_tmap(tmY);
-    tc::mbar_init(load_bar, 1);
+    for (int st = 0; st < 2; ++st) {
+      tc::mbar_init(&full[st], 1);
+      tc::mbar_init(&empty[st], 1);
+    }
     tc::mbar_init(mma_bar, 1);
     tc::fence_mbar_init();
   }
@@ -367,26 +372,39 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   pdl_trigger();
 
   if (tid == 0) {
-    tc::mbar_arrive_expect_tx(load_bar, (uint32_t)(2 * nk * 16384));
-    for (int kb = 0; kb < nk; ++kb)
+    // producer: chunk kb into stage kb % 2 once the MMAs of chunk kb - 2 are done with it
+    for (int kb = 0; kb < nk; ++kb) {
+      const int st = kb & 1;
+      if (kb >= 2 && !tc::mbar_wait(&empty[st], ((kb >> 1) - 1) & 1)) {
+        atomicOr(a.status, CRL_STATUS_TIMEOUT);
+        break;
+      }
+      uint8_t* xs = smem + st * 32768;
+      tc::mbar_arrive_expect_tx(&full[st], 32768u);
       for (int r = 0; r < 2; ++r) {
-        tc::tma_load_2d(Xs + kb * 16384 + r * 8192, tmX, load_bar, kb * 64, i0 + 64 * r);
-        tc::tma_load_2d(Ys + kb * 16384 + r * 8192, tmY, load_bar, kb * 64, j0 + 64 * r);
+        tc::tma_load_2d(xs + r * 8192, tmX, &full[st], kb * 64, i0 + 64 * r);
+        tc::tma_load_2d(xs + 16384 + r * 8192, tmY, &full[st], kb * 64, j0 + 64 * r);
       }
-  } else if (tid == 32) {
-    if (tc::mbar_wait(load_bar, 0)) {
-      tc::fence_after_sync();
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
-      for (int kb = 0; kb < nk; ++kb) {
-        const uint64_t dx = tc::sdesc_kmajor_sw128(Xs + kb * 16384);
-        const uint64_t dy = tc::sdesc_kmajor_sw128(Ys + kb * 16384);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
-      }
-      tc::mma_commit(mma_bar);
-    } else {
-      atomicOr(a.status, CRL_STATUS_TIMEOUT);
     }
+  } else if (tid == 32) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+    bool good = true;
+    for (int kb = 0; kb < nk && good; ++kb) {
+      const int st = kb & 1;
+      if (!tc::mbar_wait(&full[st], (kb >> 1) & 1)) {
+        atomicOr(a.status, CRL_STATUS_TIMEOUT);
+        good = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint8_t* xs = smem + st * 32768;
+      const uint64_t dx = tc::sdesc_kmajor_sw128(xs);
+      const uint64_t dy = tc::sdesc_kmajor_sw128(xs + 16384);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
+      if (kb + 2 < nk) tc::mma_commit(&empty[st]);
+    }
+    if (good) tc::mma_commit(mma_bar);
   }
   __syncwarp();
   if (tid < kTile) s_ay[tid] = (j0 + tid < a.B) ? a.auxY[j0 + tid] : 0.f;
@@ -1005,7 +1023,8 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_multi_kernel(const EnergyTask
 }
 
 size_t fwd_smem(int R) {
-  const size_t opnd = (size_t)2 * (R / 64) * 16384, ftile = (size_t)kTile * 129 * 4;
+  const int nk = R / 64;
+  const size_t opnd = (size_t)(nk < 2 ? nk : 2) * 32768, ftile = (size_t)kTile * 129 * 4;
   return (opnd > ftile ? opnd : ftile) + (2 * 2 * 4 + 2) * kTile * 4 + 1024 + 64;
 }
 size_t bwd_smem(int R) {
