@@ -695,7 +695,9 @@ __device__ __forceinline__ float objective_coef(float f2, bool diag, float d_row
 // LIVE: which softmax terms carry weight in this pass (0: both, 1: own only,
 // 2: other only); a term whose coefficient is zero for the whole pass (one
 // InfoNCE direction, a one-axis penalty) costs no exp2.
-template <int EK, int OBJ, int LIVE>
+// EDGE: the tile holds the diagonal or reaches past the batch (the per-pair
+// tests run); interior tiles skip them.
+template <int EK, int OBJ, int LIVE, bool EDGE>
 __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, const float* s_aux,
                                         const float* s_lse2, const float* s_koth, const float* s_dv,
                                         const float* s_kv, int q, int u, int v0, int B, float& rowsum,
@@ -726,13 +728,13 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
       if (LIVE == 1) g = ex2(f2 - hc.l_own2) * hc.k_own;
       else if (LIVE == 2) g = ex2(f2 - s_lse2[cl]) * s_koth[cl];
       else g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - s_lse2[cl]) * s_koth[cl]);
-      if (u == v) g -= hc.k_diag;
+      if (EDGE && u == v) g -= hc.k_diag;
       if (OBJ != kObjInfo) {
         const float d_row = hc.transposed ? s_dv[cl] : hc.d_own;
         const float k_row = hc.transposed ? s_kv[cl] : hc.kd_own;
-        g += objective_coef<OBJ>(f2, u == v, d_row, k_row, hc);
+        g += objective_coef<OBJ>(f2, EDGE && u == v, d_row, k_row, hc);
       }
-      h2[e] = (u < B && v < B) ? g * fac : 0.f;
+      h2[e] = (!EDGE || (u < B && v < B)) ? g * fac : 0.f;
     }
     const __nv_bfloat162 p2 = __floats2bfloat162_rn(h2[0], h2[1]);
     // the row sum takes the BF16-rounded coefficients the MMA multiplies, so
@@ -884,18 +886,31 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
       float sv[32];
       tc::tmem_ld32(tS + lane_off + q * 32, sv);
       uint32_t packed[16];
-#define CRL_BUILD_H(EK, LV) build_h<EK, OBJ, LV>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, rowsum, packed)
+#define CRL_BUILD_H(EK, LV, ED)                                                                     \
+  build_h<EK, OBJ, LV, (ED) || OBJ != kObjInfo>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, \
+                                                rowsum, packed)
       const int ek = a.energy == CRL_ENERGY_L2 ? 0 : (a.energy == CRL_ENERGY_L2SQ ? 1 : 2);
-      switch (3 * ek + live) {
-        case 0: CRL_BUILD_H(0, 0); break;
-        case 1: CRL_BUILD_H(0, 1); break;
-        case 2: CRL_BUILD_H(0, 2); break;
-        case 3: CRL_BUILD_H(1, 0); break;
-        case 4: CRL_BUILD_H(1, 1); break;
-        case 5: CRL_BUILD_H(1, 2); break;
-        case 6: CRL_BUILD_H(2, 0); break;
-        case 7: CRL_BUILD_H(2, 1); break;
-        default: CRL_BUILD_H(2, 2); break;
+      // (the objectives outside InfoNCE always take the tested form: fewer instantiations)
+      const bool edge = OBJ != kObjInfo || u0 == v0 || u0 + kTile > a.B || v0 + kTile > a.B;
+      switch (2 * (3 * ek + live) + (edge ? 1 : 0)) {
+        case 0: CRL_BUILD_H(0, 0, false); break;
+        case 1: CRL_BUILD_H(0, 0, true); break;
+        case 2: CRL_BUILD_H(0, 1, false); break;
+        case 3: CRL_BUILD_H(0, 1, true); break;
+        case 4: CRL_BUILD_H(0, 2, false); break;
+        case 5: CRL_BUILD_H(0, 2, true); break;
+        case 6: CRL_BUILD_H(1, 0, false); break;
+        case 7: CRL_BUILD_H(1, 0, true); break;
+        case 8: CRL_BUILD_H(1, 1, false); break;
+        case 9: CRL_BUILD_H(1, 1, true); break;
+        case 10: CRL_BUILD_H(1, 2, false); break;
+        case 11: CRL_BUILD_H(1, 2, true); break;
+        case 12: CRL_BUILD_H(2, 0, false); break;
+        case 13: CRL_BUILD_H(2, 0, true); break;
+        case 14: CRL_BUILD_H(2, 1, false); break;
+        case 15: CRL_BUILD_H(2, 1, true); break;
+        case 16: CRL_BUILD_H(2, 2, false); break;
+        default: CRL_BUILD_H(2, 2, true); break;
       }
 #undef CRL_BUILD_H
       // columns 32 q .. +31 = K-block q / 2, 16-byte chunks (q % 2) * 4 .. +3
