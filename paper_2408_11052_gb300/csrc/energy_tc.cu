@@ -644,6 +644,8 @@ struct HCoef {
   float k1;       // log2(e) / tau
   // objectives outside InfoNCE (OBJ > 0)
   float d_own, kd_own;  // row pass: this row's anchor F_uu and k_u
+  const float* dpre;    // column pass: the rows' anchors and k (read per pair)
+  const float* kd;
   float c_bb, c_b, c_fb;  // dtotal / B^2, dtotal / B, dtotal / (B (B - 1))
   float dtotal;
   int transposed;
@@ -699,9 +701,8 @@ __device__ __forceinline__ float objective_coef(float f2, bool diag, float d_row
 // tests run); interior tiles skip them.
 template <int EK, int OBJ, int LIVE, bool EDGE>
 __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, const float* s_aux,
-                                        const float* s_lse2, const float* s_koth, const float* s_dv,
-                                        const float* s_kv, int q, int u, int v0, int B, float& rowsum,
-                                        uint32_t (&packed)[16]) {
+                                        const float* s_lse2, const float* s_koth, int q, int u, int v0, int B,
+                                        float& rowsum, uint32_t (&packed)[16]) {
 #pragma unroll
   for (int k = 0; k < 32; k += 2) {
     float h2[2];
@@ -730,8 +731,8 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
       else g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - s_lse2[cl]) * s_koth[cl]);
       if (EDGE && u == v) g -= hc.k_diag;
       if (OBJ != kObjInfo) {
-        const float d_row = hc.transposed ? s_dv[cl] : hc.d_own;
-        const float k_row = hc.transposed ? s_kv[cl] : hc.kd_own;
+        const float d_row = hc.transposed ? (v < B ? __ldg(hc.dpre + v) : 0.f) : hc.d_own;
+        const float k_row = hc.transposed ? (v < B ? __ldg(hc.kd + v) : 0.f) : hc.kd_own;
         g += objective_coef<OBJ>(f2, EDGE && u == v, d_row, k_row, hc);
       }
       h2[e] = (!EDGE || (u < B && v < B)) ? g * fac : 0.f;
@@ -745,6 +746,12 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
 }
 
 // lb in [0, 2 nrow): the row pass for lb < nrow, else the column pass.
+//
+// Pipeline over the other side's tiles v (buffer b = v % 2 for the tile and its
+// S accumulator): while the 16 warps turn S(v) into the coefficient tile, the
+// tensor core may still run acc(v - 1); as soon as acc(v - 1) is done, thread 0
+// loads tile v + 1 into the buffer it freed, and after acc(v) is issued thread
+// 32 issues S(v + 1) into the other TMEM accumulator.
 template <int OBJ>
 __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const BwdArgs& row,
                                          const BwdArgs& col, int nrow, int lb, bool global_maps) {
@@ -755,22 +762,21 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
   const int nk = a.R / 64;
-  uint8_t* Xs = smem;                                  // own tile                 nk x 16 KiB
-  uint8_t* Ys = Xs + nk * 16384;                       // other tile               nk x 16 KiB
-  uint8_t* Hs = Ys + nk * 16384;                       // H tile                   2 x 16 KiB
+  const uint32_t tbytes = (uint32_t)nk * 16384;          // one operand tile
+  uint8_t* Xs = smem;                                     // own tile                  nk x 16 KiB
+  uint8_t* Ys = Xs + tbytes;                              // other tiles, 2 buffers    2 x nk x 16 KiB
+  uint8_t* Hs = Ys + 2 * tbytes;                          // H tile                    2 x 16 KiB
   float* s_aux = reinterpret_cast<float*>(Hs + 2 * 16384);  // [128]
-  float* s_red = s_aux + kTile;                             // [4][128] partial sums
-  float* s_lse2 = s_red + 4 * kTile;                        // [128] other side's logsumexp x log2(e)
+  float* s_lse2 = s_aux + kTile;                            // [128] other side's logsumexp x log2(e)
   float* s_koth = s_lse2 + kTile;                           // [128] other side's coefficient (see HCoef)
-  float* s_dv = s_koth + kTile;                             // [128] column pass: the rows' anchor F_vv
-  float* s_kv = s_dv + kTile;                               // [128] column pass: the rows' k_v
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_kv + kTile);
+  float* s_red = reinterpret_cast<float*>(Hs);              // [4][128] partial sums (H is free by then)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_koth + kTile);
   uint64_t* xload = bars;
-  uint64_t* yload = bars + 1;
-  uint64_t* s_done = bars + 2;
-  uint64_t* h_done = bars + 3;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
-  const uint32_t tcols = (128 + a.R <= 256) ? 256u : 512u;
+  uint64_t* yfull = bars + 1;  // [2]
+  uint64_t* sfull = bars + 3;  // [2]
+  uint64_t* hfree = bars + 5;  // acc(v) done: H and the tile's buffer are free
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6);
+  constexpr uint32_t tcols = 512;  // S, S, acc (R <= 256)
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int lg = warp % 4, q = warp / 4;
@@ -785,9 +791,11 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     tc::prefetch_tmap(tmOwn);
     tc::prefetch_tmap(tmOther);
     tc::mbar_init(xload, 1);
-    tc::mbar_init(yload, 1);
-    tc::mbar_init(s_done, 1);
-    tc::mbar_init(h_done, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&yfull[b], 1);
+      tc::mbar_init(&sfull[b], 1);
+    }
+    tc::mbar_init(hfree, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -798,17 +806,44 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tS = tmem, tAcc = tmem + 128;
+  const uint32_t tAcc = tmem + 256;
   const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
   pdl_wait();
   pdl_trigger();
 
+  auto load_other = [&](int v) {  // thread 0
+    uint8_t* dst = Ys + (v & 1) * tbytes;
+    tc::mbar_arrive_expect_tx(&yfull[v & 1], tbytes);
+    for (int kb = 0; kb < nk; ++kb)
+      for (int rr = 0; rr < 2; ++rr)
+        tc::tma_load_2d(dst + kb * 16384 + rr * 8192, tmOther, &yfull[v & 1], kb * 64, v * kTile + 64 * rr);
+  };
+  auto issue_s = [&](int v) -> bool {  // thread 32: S(v) = own . other(v)^T into accumulator v % 2
+    if (!tc::mbar_wait(&yfull[v & 1], (v >> 1) & 1)) return false;
+    tc::fence_after_sync();
+    const uint8_t* ys = Ys + (v & 1) * tbytes;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+    for (int kb = 0; kb < nk; ++kb) {
+      const uint64_t dx = tc::sdesc_kmajor_sw128(Xs + kb * 16384);
+      const uint64_t dy = tc::sdesc_kmajor_sw128(ys + kb * 16384);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        tc::mma_bf16(tmem + (uint32_t)((v & 1) * 128), dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
+    }
+    tc::mma_commit(&sfull[v & 1]);
+    return true;
+  };
   if (tid == 0) {
-    tc::mbar_arrive_expect_tx(xload, (uint32_t)(nk * 16384));
+    tc::mbar_arrive_expect_tx(xload, tbytes);
     for (int kb = 0; kb < nk; ++kb)
       for (int rr = 0; rr < 2; ++rr)
         tc::tma_load_2d(Xs + kb * 16384 + rr * 8192, tmOwn, xload, kb * 64, u0 + 64 * rr);
+    load_other(0);
+    if (nV > 1) load_other(1);
+  } else if (tid == 32) {
+    if (!tc::mbar_wait(xload, 0) || !issue_s(0)) atomicOr(a.status, CRL_STATUS_TIMEOUT);
   }
+  __syncwarp();
 
   const int u = u0 + r;
   const float a_own = (u < a.B) ? a.aux_own[u] : 0.f;
@@ -830,6 +865,8 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   constexpr bool kAnchored = OBJ == kObjDPO || OBJ == kObjIPO;
   hc.d_own = (kAnchored && u < a.B) ? a.dpre[u] : 0.f;
   hc.kd_own = (kAnchored && u < a.B) ? a.kd[u] : 0.f;
+  hc.dpre = a.dpre;
+  hc.kd = a.kd;
   hc.dtotal = a.dtotal;
   hc.c_bb = a.dtotal / ((float)a.B * (float)a.B);
   hc.c_b = a.dtotal / (float)a.B;
@@ -838,57 +875,34 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   float rowsum = 0.f;
   bool ok = true;
   for (int vt = 0; vt < nV && ok; ++vt) {
-    const int v0 = vt * kTile;
-    // the previous iteration's MMAs must be done with Ys (other^T) and Hs
-    if (vt > 0) ok = tc::mbar_wait(h_done, (vt - 1) & 1);
-    ok = __syncthreads_and(ok ? 1 : 0) != 0;
-    if (!ok) break;
+    const int v0 = vt * kTile, b = vt & 1;
     if (tid < kTile) {
       const int v = v0 + tid;
       const float lo = (v < a.B) ? a.lse_other[v] : 0.f;
       s_aux[tid] = (v < a.B) ? a.aux_other[v] : 0.f;
       s_lse2[tid] = lo * kLog2e;
       s_koth[tid] = a.scale * (w_oth + 2.f * a.beta * p_oth * lo);
-      if (kAnchored && a.transposed) {
-        s_dv[tid] = (v < a.B) ? a.dpre[v] : 0.f;
-        s_kv[tid] = (v < a.B) ? a.kd[v] : 0.f;
-      }
     }
-    if (tid == 0) {
-      tc::mbar_arrive_expect_tx(yload, (uint32_t)(nk * 16384));
-      for (int kb = 0; kb < nk; ++kb)
-        for (int rr = 0; rr < 2; ++rr)
-          tc::tma_load_2d(Ys + kb * 16384 + rr * 8192, tmOther, yload, kb * 64, v0 + 64 * rr);
-    } else if (tid == 32) {
-      bool good = (vt > 0) || tc::mbar_wait(xload, 0);
-      good = good && tc::mbar_wait(yload, vt & 1);
-      if (good) {
-        tc::fence_after_sync();
-        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
-        for (int kb = 0; kb < nk; ++kb) {
-          const uint64_t dx = tc::sdesc_kmajor_sw128(Xs + kb * 16384);
-          const uint64_t dy = tc::sdesc_kmajor_sw128(Ys + kb * 16384);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) tc::mma_bf16(tS, dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
-        }
-        tc::mma_commit(s_done);
-      } else {
-        atomicOr(a.status, CRL_STATUS_TIMEOUT);
-      }
+    bool good = true;
+    if (tid == 0 && vt >= 1) {
+      // acc(vt - 1) done: H and the buffer of tile vt - 1 are free; tile vt + 1 goes there
+      good = tc::mbar_wait(hfree, (vt - 1) & 1);
+      if (good && vt + 1 < nV) load_other(vt + 1);
     }
-    __syncwarp();
-    ok = __all_sync(0xffffffffu, tc::mbar_wait(s_done, vt & 1) ? 1 : 0) != 0;
+    ok = __syncthreads_and(good ? 1 : 0) != 0;
+    if (!ok) break;
+    // coefficient tile H from S(vt): this thread's row r, columns 32 q .. 32 q + 31
+    // (every warp reaches every barrier: the decision to stop is block-wide)
+    ok = __all_sync(0xffffffffu, tc::mbar_wait(&sfull[b], (vt >> 1) & 1) ? 1 : 0) != 0;
     ok = __syncthreads_and(ok ? 1 : 0) != 0;
     if (!ok) break;
     tc::fence_after_sync();
-    // coefficient tile H: this thread's row r, columns 32 q .. 32 q + 31
     {
       float sv[32];
-      tc::tmem_ld32(tS + lane_off + q * 32, sv);
+      tc::tmem_ld32(tmem + (uint32_t)(b * 128) + lane_off + q * 32, sv);
       uint32_t packed[16];
 #define CRL_BUILD_H(EK, LV, ED)                                                                     \
-  build_h<EK, OBJ, LV, (ED) || OBJ != kObjInfo>(sv, hc, s_aux, s_lse2, s_koth, s_dv, s_kv, q, u, v0, a.B, \
-                                                rowsum, packed)
+  build_h<EK, OBJ, LV, (ED) || OBJ != kObjInfo>(sv, hc, s_aux, s_lse2, s_koth, q, u, v0, a.B, rowsum, packed)
       const int ek = a.energy == CRL_ENERGY_L2 ? 0 : (a.energy == CRL_ENERGY_L2SQ ? 1 : 2);
       // (the objectives outside InfoNCE always take the tested form: fewer instantiations)
       const bool edge = OBJ != kObjInfo || u0 == v0 || u0 + kTile > a.B || v0 + kTile > a.B;
@@ -921,28 +935,32 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
         *reinterpret_cast<uint4*>(hb + sw128_offset(r, (q % 2) * 4 + c4)) = val;
       }
     }
-    // make the generic-proxy H writes visible to the tensor core, then acc += H other
+    // make the generic-proxy H writes visible to the tensor core (and the S reads
+    // ordered before the next MMAs into this accumulator), then acc += H other(vt)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 32) {
-      // the other tile itself is the MN-major B operand (K = its 128 rows, N = R):
+      // the tile in buffer b is the MN-major B operand (K = its 128 rows, N = R):
       // K steps of 16 rows are 2048 bytes, R chunks of 64 columns 16 KiB apart
       tc::fence_after_sync();
+      const uint8_t* ys = Ys + b * tbytes;
       const uint32_t idesc = tc::idesc_bf16_f32_bmn(128, a.R);
       for (int kb = 0; kb < 2; ++kb) {
         const uint64_t dh = tc::sdesc_kmajor_sw128(Hs + kb * 16384);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const uint64_t dt = tc::sdesc_mnmajor_sw128(Ys + kb * 8192 + k * 2048, 16384);
+          const uint64_t dt = tc::sdesc_mnmajor_sw128(ys + kb * 8192 + k * 2048, 16384);
           tc::mma_bf16(tAcc, dh + 2 * k, dt, idesc, (vt | kb | k) ? 1u : 0u);
         }
       }
-      tc::mma_commit(h_done);
+      tc::mma_commit(hfree);
+      // S(vt + 1) into the other accumulator (read out in the previous iteration)
+      if (vt + 1 < nV && !issue_s(vt + 1)) atomicOr(a.status, CRL_STATUS_TIMEOUT);
     }
     __syncwarp();
   }
-  if (ok) ok = __all_sync(0xffffffffu, tc::mbar_wait(h_done, (nV - 1) & 1) ? 1 : 0) != 0;
+  if (ok) ok = __all_sync(0xffffffffu, tc::mbar_wait(hfree, (nV - 1) & 1) ? 1 : 0) != 0;
   // row sums of the four column groups
   s_red[q * kTile + r] = rowsum;
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
@@ -1043,7 +1061,8 @@ size_t fwd_smem(int R) {
   return (opnd > ftile ? opnd : ftile) + (2 * 2 * 4 + 2) * kTile * 4 + 1024 + 64;
 }
 size_t bwd_smem(int R) {
-  return (size_t)2 * (R / 64) * 16384 + 2 * 16384 + (1 + 4 + 1 + 1 + 2) * kTile * 4 + 1024 + 64;
+  // own tile, two other tiles, H (then the row-sum partials), three per-tile arrays, barriers, alignment
+  return (size_t)3 * (R / 64) * 16384 + 2 * 16384 + 3 * kTile * 4 + 64 + 1024;
 }
 
 FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* loss4, float* r, float* c,
