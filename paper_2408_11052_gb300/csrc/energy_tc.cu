@@ -703,22 +703,33 @@ template <int EK, int OBJ, int LIVE, bool EDGE>
 __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, const float* s_aux,
                                         const float* s_lse2, const float* s_koth, int q, int u, int v0, int B,
                                         float& rowsum, uint32_t (&packed)[16]) {
+  // per-column constants of the other side, four columns per shared-memory load
+  float cax[4], clse[4], ckoth[4];
 #pragma unroll
   for (int k = 0; k < 32; k += 2) {
+    if ((k & 3) == 0) {
+      const int c4 = q * 32 + k;
+      if (EK != 2) *reinterpret_cast<float4*>(cax) = *reinterpret_cast<const float4*>(s_aux + c4);
+      if (LIVE != 1) {
+        *reinterpret_cast<float4*>(clse) = *reinterpret_cast<const float4*>(s_lse2 + c4);
+        *reinterpret_cast<float4*>(ckoth) = *reinterpret_cast<const float4*>(s_koth + c4);
+      }
+    }
     float h2[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int cl = q * 32 + k + e;
       const int v = v0 + cl;
+      const int c = (k & 3) + e;
       const float sval = sv[k + e];
       float f2, fac;
       if (EK == 0) {
-        const float t = fmaxf(hc.a_own + s_aux[cl] - 2.f * sval, 0.f);
+        const float t = fmaxf(hc.a_own + cax[c] - 2.f * sval, 0.f);
         const float rs = t >= 1e-24f ? rsqrtf(t) : 0.f;
         f2 = -(t * rs) * hc.k1;
         fac = hc.inv_tau * rs;
       } else if (EK == 1) {
-        const float t = fmaxf(hc.a_own + s_aux[cl] - 2.f * sval, 0.f);
+        const float t = fmaxf(hc.a_own + cax[c] - 2.f * sval, 0.f);
         f2 = -t * hc.k1;
         fac = 2.f * hc.inv_tau;
       } else {
@@ -727,8 +738,8 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
       }
       float g;
       if (LIVE == 1) g = ex2(f2 - hc.l_own2) * hc.k_own;
-      else if (LIVE == 2) g = ex2(f2 - s_lse2[cl]) * s_koth[cl];
-      else g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - s_lse2[cl]) * s_koth[cl]);
+      else if (LIVE == 2) g = ex2(f2 - clse[c]) * ckoth[c];
+      else g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - clse[c]) * ckoth[c]);
       if (EDGE && u == v) g -= hc.k_diag;
       if (OBJ != kObjInfo) {
         const float d_row = hc.transposed ? (v < B ? __ldg(hc.dpre + v) : 0.f) : hc.d_own;
@@ -889,12 +900,11 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
       good = tc::mbar_wait(hfree, (vt - 1) & 1);
       if (good && vt + 1 < nV) load_other(vt + 1);
     }
+    // coefficient tile H from S(vt): this thread's row r, columns 32 q .. 32 q + 31.
+    // One barrier publishes the per-tile arrays and thread 0's wait; every warp
+    // reaches every barrier (the decision to stop is block-wide).
+    good = (__all_sync(0xffffffffu, tc::mbar_wait(&sfull[b], (vt >> 1) & 1) ? 1 : 0) != 0) && good;
     ok = __syncthreads_and(good ? 1 : 0) != 0;
-    if (!ok) break;
-    // coefficient tile H from S(vt): this thread's row r, columns 32 q .. 32 q + 31
-    // (every warp reaches every barrier: the decision to stop is block-wide)
-    ok = __all_sync(0xffffffffu, tc::mbar_wait(&sfull[b], (vt >> 1) & 1) ? 1 : 0) != 0;
-    ok = __syncthreads_and(ok ? 1 : 0) != 0;
     if (!ok) break;
     tc::fence_after_sync();
     {
