@@ -133,31 +133,45 @@ void pack(int rows, const float* s0, int ld0, int n0, const float* s1, int ld1, 
   launch_k(pack_kernel, grid, dim3(256), 0, st, rows, s0, ld0, n0, s1, ld1, n1, dst, ld, dstT, ldt);
 }
 
-// ---- LayerNorm (grouped over the networks of a pass: blockIdx.y = network) ----------
-// Block = 8 warps x 2 rows = 16 rows.  Each warp reduces its row with float4
-// loads (three passes over the row: mean, variance, output; the row stays in
-// L1), writes the row-major outputs and stages the BF16 row in shared memory;
-// the block then writes the transposed copy as 16-byte pieces of 8 rows.
-constexpr int kLnRows = 16;
+// LayerNorm kernels: one warp per row, 8 rows per 256-thread block.  Rows of
+// up to 1024 values stay in registers (float4 pieces, lane-strided), so the
+// statistics and the output take one pass over global memory; wider rows loop
+// over global memory.  The block stages its BF16 output rows in shared memory
+// ([8][H + 4], padded against bank conflicts) and writes the transposed copy as
+// 16-byte pieces of 8 rows.
+constexpr int kLnRows = 8;
+constexpr int kLnRegVec = 8;   // float4 pieces per lane held in registers (H <= 1024)
 inline size_t ln_smem_bytes(int H) { return (size_t)kLnRows * (H + 4) * 2; }
-constexpr int kLnMaxSmem = 200 * 1024;   // hidden widths up to 6396
+constexpr int kLnMaxSmem = 200 * 1024;
+inline int ln_vec(int H) { return (H + 127) / 128 <= kLnRegVec ? (H + 127) / 128 : 0; }
+// The backward's register path also stages the rows' du zhat and du ([2][8][H] FP32)
+// for the column sums.
+inline size_t ln_bwd_smem_bytes(int H) {
+  return ((ln_smem_bytes(H) + 15) & ~(size_t)15) + (ln_vec(H) > 0 ? (size_t)2 * kLnRows * H * 4 : 0);
+}
+// Deterministic two-level reduction of the LayerNorm parameter gradients: the
+// blocks' column sums go in groups of ln_group(nblk) (at most 63 groups: one
+// ticket word each, plus one for the final level).
+__host__ __device__ inline int ln_group(int nblk) { return nblk <= 63 * 16 ? 16 : (nblk + 62) / 63; }
+inline size_t ln_partial_floats(int Mmax, int H) {
+  const int nblk = (Mmax + kLnRows - 1) / kLnRows;
+  const int ng = (nblk + ln_group(nblk) - 1) / ln_group(nblk);
+  return (size_t)(nblk + ng) * 2 * H;
+}
 
-// Transposed store of the staged [16][H] BF16 tile (row stride H + 4) into
-// dst [H][ldt] at rows row0 .. row0 + 15 (clipped to M).
+// Transposed store of the staged [8][H] BF16 tile (row stride H + 4) into
+// dst [H][ldt] at rows row0 .. row0 + 7 (clipped to M).
 __device__ __forceinline__ void ln_store_transposed(const bf16* tile, int H, bf16* dst, int ldt, int row0, int M) {
   const int S = H + 4;
-  for (int idx = threadIdx.x; idx < 2 * H; idx += blockDim.x) {
-    const int c = idx >> 1, half = idx & 1;
-    const int r0 = row0 + 8 * half;
-    if (r0 >= M) continue;
+  for (int c = threadIdx.x; c < H; c += blockDim.x) {
     alignas(16) bf16 v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = tile[(8 * half + k) * S + c];
-    bf16* d = dst + (size_t)c * ldt + r0;
-    if (r0 + 8 <= M) {
+    for (int k = 0; k < 8; ++k) v[k] = tile[k * S + c];
+    bf16* d = dst + (size_t)c * ldt + row0;
+    if (row0 + 8 <= M) {
       *reinterpret_cast<uint4*>(d) = *reinterpret_cast<const uint4*>(v);
     } else {
-      for (int k = 0; k < M - r0; ++k) d[k] = v[k];
+      for (int k = 0; k < M - row0; ++k) d[k] = v[k];
     }
   }
 }
@@ -175,57 +189,96 @@ struct LnFwdGroup {
   LnFwdNet n[kMaxGroupNets];
 };
 
+__device__ __forceinline__ uint2 ln_relu_pack(float4 x, float4 gg, float4 bb) {
+  const __nv_bfloat162 p0 = __floats2bfloat162_rn(fmaxf(x.x * gg.x + bb.x, 0.f), fmaxf(x.y * gg.y + bb.y, 0.f));
+  const __nv_bfloat162 p1 = __floats2bfloat162_rn(fmaxf(x.z * gg.z + bb.z, 0.f), fmaxf(x.w * gg.w + bb.w, 0.f));
+  return make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+}
+
 // LayerNorm forward over rows of z [M][H] (FP32, replaced by zhat), rstd [M],
 // h = ReLU(zhat * g + beta) written as BF16 [M][H] and transposed [H][ldt].
+// NV > 0: the row in registers (NV float4 per lane); NV = 0: three passes.
+template <int NV>
 __global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constant__ LnFwdGroup grp) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char ln_smem[];
   bf16* tile = reinterpret_cast<bf16*>(ln_smem);
   const LnFwdNet& a = grp.n[blockIdx.y];
-  const int M = a.M, ldt = a.ldt, S = H + 4;
+  const int M = a.M, S = H + 4;
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   const int row0 = blockIdx.x * kLnRows;
   if (row0 >= M) return;
   const int nv = H / 4;
-  for (int rr = w; rr < kLnRows; rr += 8) {
-    const int row = row0 + rr;
-    if (row >= M) break;
+  const int row = row0 + w;
+  if (row < M) {
     float4* zr = reinterpret_cast<float4*>(a.z + (size_t)row * H);
-    float s = 0.f;
-    for (int q = lane; q < nv; q += 32) {
-      const float4 x = zr[q];
-      s += (x.x + x.y) + (x.z + x.w);
-    }
-    const float mean = warp_sum(s) / H;
-    float sq = 0.f;
-    for (int q = lane; q < nv; q += 32) {
-      const float4 x = zr[q];
-      const float d0 = x.x - mean, d1 = x.y - mean, d2 = x.z - mean, d3 = x.w - mean;
-      sq += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
-    }
-    const float rs = rsqrtf(warp_sum(sq) / H + kLnEpsF);
-    if (lane == 0) a.rstd[row] = rs;
     const float4* g4 = reinterpret_cast<const float4*>(a.g);
     const float4* b4 = reinterpret_cast<const float4*>(a.beta);
     uint2* hr = reinterpret_cast<uint2*>(a.h + (size_t)row * H);
-    uint2* tr = reinterpret_cast<uint2*>(tile + rr * S);
-    for (int q = lane; q < nv; q += 32) {
-      float4 x = zr[q];
-      const float4 gg = g4[q], bb = b4[q];
-      x.x = (x.x - mean) * rs;
-      x.y = (x.y - mean) * rs;
-      x.z = (x.z - mean) * rs;
-      x.w = (x.w - mean) * rs;
-      zr[q] = x;
-      const __nv_bfloat162 p0 = __floats2bfloat162_rn(fmaxf(x.x * gg.x + bb.x, 0.f), fmaxf(x.y * gg.y + bb.y, 0.f));
-      const __nv_bfloat162 p1 = __floats2bfloat162_rn(fmaxf(x.z * gg.z + bb.z, 0.f), fmaxf(x.w * gg.w + bb.w, 0.f));
-      const uint2 v = make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
-      hr[q] = v;
-      tr[q] = v;
+    uint2* tr = reinterpret_cast<uint2*>(tile + w * S);
+    if constexpr (NV > 0) {
+      float4 x[NV];
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const int q = lane + 32 * j;
+        x[j] = q < nv ? zr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        s += (x[j].x + x[j].y) + (x[j].z + x[j].w);
+      }
+      const float mean = warp_sum(s) / H;
+      float sq = 0.f;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        if (lane + 32 * j >= nv) continue;
+        const float d0 = x[j].x - mean, d1 = x[j].y - mean, d2 = x[j].z - mean, d3 = x[j].w - mean;
+        sq += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
+      }
+      const float rs = rsqrtf(warp_sum(sq) / H + kLnEpsF);
+      if (lane == 0) a.rstd[row] = rs;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const int q = lane + 32 * j;
+        if (q >= nv) continue;
+        float4 xn;
+        xn.x = (x[j].x - mean) * rs;
+        xn.y = (x[j].y - mean) * rs;
+        xn.z = (x[j].z - mean) * rs;
+        xn.w = (x[j].w - mean) * rs;
+        zr[q] = xn;
+        const uint2 v = ln_relu_pack(xn, g4[q], b4[q]);
+        hr[q] = v;
+        tr[q] = v;
+      }
+    } else {
+      float s = 0.f;
+      for (int q = lane; q < nv; q += 32) {
+        const float4 x = zr[q];
+        s += (x.x + x.y) + (x.z + x.w);
+      }
+      const float mean = warp_sum(s) / H;
+      float sq = 0.f;
+      for (int q = lane; q < nv; q += 32) {
+        const float4 x = zr[q];
+        const float d0 = x.x - mean, d1 = x.y - mean, d2 = x.z - mean, d3 = x.w - mean;
+        sq += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
+      }
+      const float rs = rsqrtf(warp_sum(sq) / H + kLnEpsF);
+      if (lane == 0) a.rstd[row] = rs;
+      for (int q = lane; q < nv; q += 32) {
+        float4 x = zr[q];
+        x.x = (x.x - mean) * rs;
+        x.y = (x.y - mean) * rs;
+        x.z = (x.z - mean) * rs;
+        x.w = (x.w - mean) * rs;
+        zr[q] = x;
+        const uint2 v = ln_relu_pack(x, g4[q], b4[q]);
+        hr[q] = v;
+        tr[q] = v;
+      }
     }
   }
   __syncthreads();
-  ln_store_transposed(tile, H, a.hT, ldt, row0, M);
+  ln_store_transposed(tile, H, a.hT, a.ldt, row0, M);
 }
 
 struct LnBwdNet {
@@ -238,91 +291,200 @@ struct LnBwdNet {
   bf16* dzT;
   float* dg;          // null: no LayerNorm parameter gradients
   float* db;
-  float* partial;     // [ceil(M / 16)][2][H] per-block column sums (dg, db)
-  unsigned* ticket;   // zero between launches
+  float* partial;     // [nblk][2][H] per-block column sums (dg, db), then [ngroups][2][H] group sums
+  unsigned* ticket;   // [64], zero between launches: one per group, the last for the final level
 };
 struct LnBwdGroup {
   LnBwdNet n[kMaxGroupNets];
 };
 
+__device__ __forceinline__ uint2 ln_bwd_pack(float4 d, float4 z, float4 gg, float s1, float s2, float rs) {
+  const __nv_bfloat162 p0 =
+      __floats2bfloat162_rn(rs * (d.x * gg.x - s1 - z.x * s2), rs * (d.y * gg.y - s1 - z.y * s2));
+  const __nv_bfloat162 p1 =
+      __floats2bfloat162_rn(rs * (d.z * gg.z - s1 - z.z * s2), rs * (d.w * gg.w - s1 - z.w * s2));
+  return make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+}
+
 // LayerNorm backward: du (ReLU-masked, FP32) -> dz = rstd (g du - mean(g du) -
 // zhat mean(g du zhat)), written BF16 [M][H] and transposed; with dg / db the
 // gain and shift gradients dg = sum_m du zhat, db = sum_m du: every block
-// writes its 16 rows' column sums, and the last block to finish (ticket) adds
-// them in block order.
+// writes its 8 rows' column sums; the last block of each group of blocks
+// (ticket) adds its group's sums in block order, and the last group to finish
+// adds the group sums in group order.  NV as in the forward.
+template <int NV>
 __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constant__ LnBwdGroup grp) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char ln_smem[];
   bf16* tile = reinterpret_cast<bf16*>(ln_smem);
+  // register path: [2][8][H] FP32 (du zhat, du) of the block's rows, after the tile
+  float* colbuf = reinterpret_cast<float*>(ln_smem + (((size_t)kLnRows * (H + 4) * 2 + 15) & ~(size_t)15));
   __shared__ int s_last;
   const LnBwdNet& a = grp.n[blockIdx.y];
-  const int M = a.M, ldt = a.ldt, S = H + 4;
+  const int M = a.M, S = H + 4;
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   const int row0 = blockIdx.x * kLnRows;
   const int nblk = (M + kLnRows - 1) / kLnRows;
   if (row0 >= M) return;
   const int nv = H / 4;
   const float4* g4 = reinterpret_cast<const float4*>(a.g);
-  for (int rr = w; rr < kLnRows; rr += 8) {
-    const int row = row0 + rr;
-    if (row >= M) break;
+  const int row = row0 + w;
+  if (row < M) {
     const float4* dr = reinterpret_cast<const float4*>(a.du + (size_t)row * H);
     const float4* zr = reinterpret_cast<const float4*>(a.zhat + (size_t)row * H);
-    float s1 = 0.f, s2 = 0.f;
-    for (int q = lane; q < nv; q += 32) {
-      const float4 d = dr[q], z = zr[q], gg = g4[q];
-      const float e0 = d.x * gg.x, e1 = d.y * gg.y, e2 = d.z * gg.z, e3 = d.w * gg.w;
-      s1 += (e0 + e1) + (e2 + e3);
-      s2 += (e0 * z.x + e1 * z.y) + (e2 * z.z + e3 * z.w);
-    }
-    s1 = warp_sum(s1) / H;
-    s2 = warp_sum(s2) / H;
     const float rs = a.rstd[row];
     uint2* out = reinterpret_cast<uint2*>(a.dz + (size_t)row * H);
-    uint2* tr = reinterpret_cast<uint2*>(tile + rr * S);
-    for (int q = lane; q < nv; q += 32) {
-      const float4 d = dr[q], z = zr[q], gg = g4[q];
-      const __nv_bfloat162 p0 = __floats2bfloat162_rn(rs * (d.x * gg.x - s1 - z.x * s2),
-                                                      rs * (d.y * gg.y - s1 - z.y * s2));
-      const __nv_bfloat162 p1 = __floats2bfloat162_rn(rs * (d.z * gg.z - s1 - z.z * s2),
-                                                      rs * (d.w * gg.w - s1 - z.w * s2));
-      const uint2 v = make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
-      out[q] = v;
-      tr[q] = v;
+    uint2* tr = reinterpret_cast<uint2*>(tile + w * S);
+    if constexpr (NV > 0) {
+      float4 d[NV], z[NV];
+      float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const int q = lane + 32 * j;
+        if (q < nv) {
+          d[j] = dr[q];
+          z[j] = zr[q];
+          const float4 gg = g4[q];
+          const float e0 = d[j].x * gg.x, e1 = d[j].y * gg.y, e2 = d[j].z * gg.z, e3 = d[j].w * gg.w;
+          s1 += (e0 + e1) + (e2 + e3);
+          s2 += (e0 * z[j].x + e1 * z[j].y) + (e2 * z[j].z + e3 * z[j].w);
+        }
+      }
+      s1 = warp_sum(s1) / H;
+      s2 = warp_sum(s2) / H;
+      float4* cz = reinterpret_cast<float4*>(colbuf + (size_t)w * H);
+      float4* cd = reinterpret_cast<float4*>(colbuf + (size_t)(kLnRows + w) * H);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const int q = lane + 32 * j;
+        if (q >= nv) continue;
+        const uint2 v = ln_bwd_pack(d[j], z[j], g4[q], s1, s2, rs);
+        out[q] = v;
+        tr[q] = v;
+        if (a.dg != nullptr) {
+          cz[q] = make_float4(d[j].x * z[j].x, d[j].y * z[j].y, d[j].z * z[j].z, d[j].w * z[j].w);
+          cd[q] = d[j];
+        }
+      }
+    } else {
+      float s1 = 0.f, s2 = 0.f;
+      for (int q = lane; q < nv; q += 32) {
+        const float4 dd = dr[q], zz = zr[q], gg = g4[q];
+        const float e0 = dd.x * gg.x, e1 = dd.y * gg.y, e2 = dd.z * gg.z, e3 = dd.w * gg.w;
+        s1 += (e0 + e1) + (e2 + e3);
+        s2 += (e0 * zz.x + e1 * zz.y) + (e2 * zz.z + e3 * zz.w);
+      }
+      s1 = warp_sum(s1) / H;
+      s2 = warp_sum(s2) / H;
+      for (int q = lane; q < nv; q += 32) {
+        const uint2 v = ln_bwd_pack(dr[q], zr[q], g4[q], s1, s2, rs);
+        out[q] = v;
+        tr[q] = v;
+      }
     }
   }
   __syncthreads();
-  ln_store_transposed(tile, H, a.dzT, ldt, row0, M);
+  ln_store_transposed(tile, H, a.dzT, a.ldt, row0, M);
   if (a.dg == nullptr) return;
-  // column sums of this block's rows
+  // column sums of this block's rows (rows in order)
   const int rmax = min(kLnRows, M - row0);
   for (int c = threadIdx.x; c < H; c += blockDim.x) {
     float sg = 0.f, sb = 0.f;
-    for (int r = 0; r < rmax; ++r) {
-      const size_t o = (size_t)(row0 + r) * H + c;
-      sg += a.du[o] * a.zhat[o];
-      sb += a.du[o];
+    if constexpr (NV > 0) {
+#pragma unroll
+      for (int r = 0; r < kLnRows; ++r) {
+        if (r >= rmax) break;
+        sg += colbuf[(size_t)r * H + c];
+        sb += colbuf[(size_t)(kLnRows + r) * H + c];
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < kLnRows; ++r) {
+        if (r >= rmax) break;
+        const size_t o = (size_t)(row0 + r) * H + c;
+        const float dv = a.du[o];
+        sg += dv * a.zhat[o];
+        sb += dv;
+      }
     }
     a.partial[((size_t)blockIdx.x * 2 + 0) * H + c] = sg;
     a.partial[((size_t)blockIdx.x * 2 + 1) * H + c] = sb;
   }
+  const int G = ln_group(nblk), ng = (nblk + G - 1) / G, grp_id = blockIdx.x / G;
+  const int k0 = grp_id * G, k1 = min(nblk, k0 + G);
+  float* gpart = a.partial + (size_t)nblk * 2 * H;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(a.ticket, 1u) == (unsigned)nblk - 1u) ? 1 : 0;
+  if (threadIdx.x == 0) s_last = (atomicAdd(a.ticket + grp_id, 1u) == (unsigned)(k1 - k0) - 1u) ? 1 : 0;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   for (int c = threadIdx.x; c < H; c += blockDim.x) {
     float sg = 0.f, sb = 0.f;
-    for (int k = 0; k < nblk; ++k) {
+#pragma unroll 16
+    for (int k = k0; k < k1; ++k) {
       sg += __ldcg(a.partial + ((size_t)k * 2 + 0) * H + c);
       sb += __ldcg(a.partial + ((size_t)k * 2 + 1) * H + c);
+    }
+    gpart[((size_t)grp_id * 2 + 0) * H + c] = sg;
+    gpart[((size_t)grp_id * 2 + 1) * H + c] = sb;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.ticket[grp_id] = 0u;
+    s_last = (atomicAdd(a.ticket + 63, 1u) == (unsigned)ng - 1u) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int c = threadIdx.x; c < H; c += blockDim.x) {
+    float sg = 0.f, sb = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < ng; ++k) {
+      sg += __ldcg(gpart + ((size_t)k * 2 + 0) * H + c);
+      sb += __ldcg(gpart + ((size_t)k * 2 + 1) * H + c);
     }
     a.dg[c] = sg;
     a.db[c] = sb;
   }
-  if (threadIdx.x == 0) *a.ticket = 0u;
+  if (threadIdx.x == 0) a.ticket[63] = 0u;
 }
+
+// LayerNorm launches with the register width chosen from H.
+template <int NV>
+void launch_ln_fwd_t(int H, dim3 grid, cudaStream_t st, const LnFwdGroup& grp) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(ln_fwd_kernel<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLnMaxSmem);
+    attr = true;
+  }
+  launch_k(ln_fwd_kernel<NV>, grid, dim3(256), ln_smem_bytes(H), st, H, grp);
+}
+template <int NV>
+void launch_ln_bwd_t(int H, dim3 grid, cudaStream_t st, const LnBwdGroup& grp) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(ln_bwd_kernel<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLnMaxSmem);
+    attr = true;
+  }
+  launch_k(ln_bwd_kernel<NV>, grid, dim3(256), ln_bwd_smem_bytes(H), st, H, grp);
+}
+#define CRL_LN_DISPATCH(FN)                    \
+  switch (ln_vec(H)) {                         \
+    case 1: FN<1>(H, grid, st, grp); break;    \
+    case 2: FN<2>(H, grid, st, grp); break;    \
+    case 3: FN<3>(H, grid, st, grp); break;    \
+    case 4: FN<4>(H, grid, st, grp); break;    \
+    case 5: FN<5>(H, grid, st, grp); break;    \
+    case 6: FN<6>(H, grid, st, grp); break;    \
+    case 7: FN<7>(H, grid, st, grp); break;    \
+    case 8: FN<8>(H, grid, st, grp); break;    \
+    default: FN<0>(H, grid, st, grp); break;   \
+  }
+void launch_ln_fwd(int H, dim3 grid, cudaStream_t st, const LnFwdGroup& grp) { CRL_LN_DISPATCH(launch_ln_fwd_t) }
+void launch_ln_bwd(int H, dim3 grid, cudaStream_t st, const LnBwdGroup& grp) { CRL_LN_DISPATCH(launch_ln_bwd_t) }
+#undef CRL_LN_DISPATCH
 
 __global__ void fill_bf16_kernel(bf16* p, size_t n, float v) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -640,7 +802,7 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
   }
   if (s.layernorm) {
     n.du = static_cast<float*>(A((size_t)Mmax * H * 4));
-    n.ln_partial = static_cast<float*>(A((size_t)ceil_div(Mmax, kLnRows) * 2 * H * 4));
+    n.ln_partial = static_cast<float*>(A(ln_partial_floats(Mmax, H) * 4));
     n.ln_ticket = static_cast<unsigned*>(A(256));
     if (!n.du || !n.ln_partial || !n.ln_ticket || cudaMemset(n.ln_ticket, 0, 256) != cudaSuccess)
       return "LayerNorm workspace set-up failed";
@@ -763,13 +925,8 @@ const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* 
         bytes += (double)M * H * 12.0;
       }
       if (Mx == 0) continue;
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(ln_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLnMaxSmem);
-        attr = true;
-      }
       TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
-      launch_k(ln_fwd_kernel, dim3(ceil_div(Mx, kLnRows), kc), dim3(256), ln_smem_bytes(H), st, H, grp);
+      launch_ln_fwd(H, dim3(ceil_div(Mx, kLnRows), kc), st, grp);
     }
   }
   return nullptr;
@@ -835,13 +992,8 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
         bytes += (double)M * H * (bp.grads ? 24.0 : 16.0);
       }
       if (Mx == 0) continue;
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(ln_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLnMaxSmem);
-        attr = true;
-      }
       TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
-      launch_k(ln_bwd_kernel, dim3(ceil_div(Mx, kLnRows), kc), dim3(256), ln_smem_bytes(H), st, H, grp);
+      launch_ln_bwd(H, dim3(ceil_div(Mx, kLnRows), kc), st, grp);
     }
   }
   // every weight gradient, and the first-layer input gradients, in one launch
