@@ -596,7 +596,7 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
 }
 
 template <bool OBJ>
-__global__ void __launch_bounds__(kThreads, OBJ ? 1 : 2) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
+__global__ void __launch_bounds__(kThreads, 2) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
                                                                    const __grid_constant__ CUtensorMap tmY,
                                                                    const __grid_constant__ FwdArgs a) {
   fwd_body<OBJ>(&tmX, &tmY, a, blockIdx.y, blockIdx.x, gridDim.x, false);
@@ -1050,7 +1050,7 @@ __global__ void __launch_bounds__(1024) prep_multi_kernel(const EnergyTask* __re
 }
 
 template <bool OBJ>
-__global__ void __launch_bounds__(kThreads, OBJ ? 1 : 2) fwd_multi_kernel(const EnergyTask* __restrict__ tasks,
+__global__ void __launch_bounds__(kThreads, 2) fwd_multi_kernel(const EnergyTask* __restrict__ tasks,
                                                                          const int* __restrict__ begin, int n) {
   int lb, nb;
   const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];

@@ -184,6 +184,32 @@ def test_fused_critic_ragged_tiles(B, penalty):
     check_fused(ctx, got, ref)
 
 
+@pytest.mark.parametrize("R,B", [(192, 264), (256, 136), (64, 392)])
+def test_fused_critic_every_repr_width(R, B):
+    """The fused energy at each repr its kernels take (64 to 256: one to four K
+    chunks in the forward ring, the backward's two other-side buffers at 232 KB
+    of shared memory for 256) with several ragged tiles."""
+    w = bf16_small(B=B, repr=R)
+    ctx, got, ref = run_critic_fused(w)
+    check_fused(ctx, got, ref)
+
+
+@pytest.mark.parametrize("hidden", [1088, 1536])
+def test_bf16_layernorm_rows_wider_than_registers(hidden):
+    """LayerNorm rows wider than 1024 take the kernels' multi-pass form (narrower
+    rows stay in registers); forward, backward and the gain / shift gradients."""
+    w = bf16_small(B=48, hidden=hidden, layers=2, repr=24, layernorm=True)
+    # (LayerNorm shifts raised by 4 keep every unit far from its kink, as in the Humanoid tests)
+    nets = workload.init_agent(w, perturb=True)
+    for net in ("phi", "psi"):
+        for layer in nets[net][:-1]:
+            layer["ln_b"] = layer["ln_b"] + np.float32(4.0)
+    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w, nets=nets)
+    assert abs(got[0] - parts["total"]) <= BF16_LOSS_RTOL * abs(parts["total"])
+    assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
+    assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
+
+
 OBJECTIVES = ["flatnce_fwd", "flatnce_bwd", "fb", "dpo", "ipo", "sppo", "nce_binary"]
 
 
