@@ -24,6 +24,7 @@ thread_local Tracer* g_tracer = nullptr;
 int g_launch_overlap = 1;
 int g_autotune = 1;
 int g_gemm_kernel = CRL_GEMM_ANY;
+int g_mlp_fusion = CRL_MLP_AUTO;
 }
 
 namespace crl {
@@ -913,6 +914,13 @@ int32_t crl_set_launch_overlap(int32_t enable) {
 int32_t crl_set_autotune(int32_t enable) {
   const int32_t prev = g_autotune;
   g_autotune = enable ? 1 : 0;
+  return prev;
+}
+
+int32_t crl_set_mlp_fusion(int32_t mode) {
+  if (mode < CRL_MLP_AUTO || mode > CRL_MLP_WHOLE) return CRL_E_INVALID_ARG;
+  const int32_t prev = g_mlp_fusion;
+  g_mlp_fusion = mode;
   return prev;
 }
 

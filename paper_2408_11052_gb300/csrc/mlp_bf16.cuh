@@ -98,6 +98,7 @@ class GemmGroups {
   // Fills tiles_n / tile_begin of `probs` for tile width BN and returns the
   // device table; nullptr (and *err) on failure.
   // pairs: each problem's m-tiles padded to an even count (cluster-pair kernel).
+  // BN = 0: the problems are uploaded as given (tiles_n / tile_begin untouched).
   const tc::GemmProblem* table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles, cudaStream_t st,
                                const char** err, bool pairs = false);
   // Frees every table (synchronises the device) and forgets the tuned tile widths.

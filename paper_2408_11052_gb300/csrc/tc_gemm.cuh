@@ -711,5 +711,214 @@ __global__ void __launch_bounds__(128, 1)
   cluster_sync();
 }
 
+// ---- whole-network forward for narrow networks ------------------------------------
+// One CTA per (network, 128-row block) runs every layer of the network's forward:
+// the layer's activations stay in shared memory as the next layer's A operand
+// (K-major, 128-byte swizzle, up to 256 columns), so a pass over L + 1 layers is
+// one launch instead of L + 1.  Layer l is problem l of the network's slice of
+// the problem table (the same problems the per-layer launches run: B = the
+// split weights, nkA A slices, the layer's epilogue); layer 0's A is loaded
+// from its tensor map once.  192 threads: warp 4 lane 0 streams the weights of
+// every layer through a STAGES-deep ring, warp 5 lane 0 issues the MMAs (layer
+// l waits until the epilogue of layer l - 1 has written its activations and
+// read the accumulator), warps 0..3 run the epilogues (hidden layers: bias +
+// ReLU to h, h^T and the shared-memory A; the output layer: its own
+// epilogue).  Same products in the same order and the same epilogue arithmetic
+// as the per-layer kernels, so the outputs are identical.  Requirements
+// (checked by the host): hidden widths multiples of 32 up to 256, every layer's
+// K at most 256 (4 slices), no LayerNorm.
+constexpr int kMlpMaxSlices = 4;
+
+template <int STAGES>
+struct MlpSmem {
+  static constexpr uint32_t kABytes = kMlpMaxSlices * kBM * kBK * 2;   // 64 KiB
+  static constexpr uint32_t kBStage = 256 * kBK * 2;                    // 32 KiB (N <= 256)
+  static constexpr uint32_t kBytes = kABytes + STAGES * kBStage + 1024 + 256;
+  static_assert(kBytes <= 227 * 1024, "shared memory per CTA");
+};
+
+__device__ __forceinline__ uint32_t mlp_sw128_offset(int row, int chunk) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+// The table holds nnet x nlayer problems, network-major; the first problem of
+// network k carries in tile_begin the index of its first CTA.
+template <int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    tc_mlp_forward_kernel(const GemmProblem* __restrict__ probs, int nlayer, int nnet, unsigned* status) {
+  using S = MlpSmem<STAGES>;
+  using bf16 = __nv_bfloat16;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + S::kABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * S::kBStage);
+  uint64_t* empty = full + STAGES;
+  uint64_t* xfull = empty + STAGES;   // layer 0's A loaded
+  uint64_t* accf = xfull + 1;         // layer l's accumulator ready (phase l)
+  uint64_t* abuf = accf + 1;          // layer l's epilogue done (phase l; four warps)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(abuf + 1);
+
+  int lo = 0, hi = nnet - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (probs[(size_t)mid * nlayer].tile_begin <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmProblem* P = probs + (size_t)lo * nlayer;
+  const int m0 = ((int)blockIdx.x - P[0].tile_begin) * kBM;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(xfull, 1);
+    mbar_init(accf, 1);
+    mbar_init(abuf, 4);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 256);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  pdl_wait();
+  pdl_trigger();
+
+  if (warp == 4) {
+    if (lane == 0) {
+      // layer 0's A (nkA slices of 128 x 64), then every layer's weight slices
+      const int nkA0 = P[0].nkA;
+      const CUtensorMap* tmA = &P[0].a;
+      tmap_acquire(tmA);
+      mbar_arrive_expect_tx(xfull, (uint32_t)nkA0 * 16384u);
+      for (int ka = 0; ka < nkA0; ++ka)
+        for (int r = 0; r < 2; ++r) tma_load_2d(sA + ka * 16384 + r * 8192, tmA, xfull, ka * kBK, m0 + 64 * r);
+      int it = 0;
+      bool ok = true;
+      for (int l = 0; l < nlayer && ok; ++l) {
+        const CUtensorMap* tmB = &P[l].b;
+        tmap_acquire(tmB);
+        const int nk = (P[l].K + kBK - 1) / kBK;
+        const int nbox = (P[l].N + 63) / 64;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1)) {
+            atomicOr(status, CRL_STATUS_TIMEOUT);
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[s], (uint32_t)nbox * 8192u);
+          for (int r = 0; r < nbox; ++r) tma_load_2d(sB + s * S::kBStage + r * 8192, tmB, &full[s], kb * kBK, 64 * r);
+        }
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      bool ok = mbar_wait(xfull, 0);
+      if (!ok) atomicOr(status, CRL_STATUS_TIMEOUT);
+      int it = 0;
+      for (int l = 0; l < nlayer && ok; ++l) {
+        // the epilogue of layer l - 1 has written its activations and read the accumulator
+        if (l > 0 && !mbar_wait(abuf, (l - 1) & 1)) {
+          atomicOr(status, CRL_STATUS_TIMEOUT);
+          break;
+        }
+        fence_after_sync();
+        const int nk = (P[l].K + kBK - 1) / kBK, nkA = P[l].nkA;
+        const int nmma = ((P[l].N + 63) / 64) * 64;
+        const uint32_t idesc = idesc_bf16_f32(kBM, nmma);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
+            atomicOr(status, CRL_STATUS_TIMEOUT);
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint64_t da = sdesc_kmajor_sw128(sA + (kb % nkA) * 16384);
+          const uint64_t db = sdesc_kmajor_sw128(sB + s * S::kBStage);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(accf);
+      }
+    }
+  } else {
+    // epilogue warps 0..3: TMEM lanes 32 w .. (rows of the block)
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int l = 0; l < nlayer; ++l) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(accf, l & 1) ? 1 : 0) != 0;
+      if (!ok) {
+        if (lane == 0) atomicOr(status, CRL_STATUS_TIMEOUT);
+        break;
+      }
+      fence_after_sync();
+      const EpiDesc e = P[l].epi;
+      const int M = P[l].M, N = P[l].N;
+      if (l == nlayer - 1) {
+        if (e.kind == kEpiFwdOutEnergy) {
+          epilogue_energy(e, row, lane_base, N, M);
+        } else {
+#pragma unroll 1
+          for (int c = 0; c < N; c += 32) {
+            float v[32];
+            tmem_ld32(lane_base + c, v);
+            epilogue_chunk(e, row, c, v, M, N);
+          }
+        }
+        break;
+      }
+      // hidden layer: bias + ReLU to h, h^T and the next layer's A in shared memory
+      bf16* h = static_cast<bf16*>(e.out0);
+      bf16* hT = static_cast<bf16*>(e.out1);
+#pragma unroll 1
+      for (int c = 0; c < N; c += 32) {
+        float v[32];
+        tmem_ld32(lane_base + c, v);
+        float b[32];
+        load_bias32(e.bias + c, b);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + b[i], 0.f);
+        uint32_t w[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          w[i] = *reinterpret_cast<const uint32_t*>(&p2);
+        }
+        // columns c .. c + 31: K slice c / 64, 16-byte chunks (c % 64) / 8 ..
+        uint8_t* as = sA + (c / 64) * 16384;
+        const int ch0 = (c % 64) / 8;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(as + mlp_sw128_offset(warp * 32 + lane, ch0 + q)) =
+              make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        if (row < M) {
+          uint4* hr = reinterpret_cast<uint4*>(h + (size_t)row * e.ld0 + c);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) hr[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) hT[(size_t)(c + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
+        }
+      }
+      // the generic-proxy writes of A visible to the tensor core, the accumulator reads done
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(abuf);
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
 }  // namespace tc
 }  // namespace crl
