@@ -539,6 +539,10 @@ def main():
     ap.add_argument("--energy", default=None, choices=["l2", "dot", "cos", "l2sq", "l1"],
                     help="energy function instead of the workload's")
     ap.add_argument("--alpha-autotune", action="store_true", help="learn the entropy coefficient")
+    ap.add_argument("--mlp-fusion", default="auto", choices=["auto", "layers", "whole"],
+                    help="BF16 network forward: grouped per-layer launches or one whole-network kernel")
+    ap.add_argument("--gemm-kernel", default="any", choices=["any", "one_tile", "persistent", "pair"],
+                    help="BF16 GEMM kernel family the autotuner may pick from")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS.get(args.workload, workload.ANT_AUTOGRAD)
@@ -553,9 +557,11 @@ def main():
 
     import torch
 
+    from paper_2408_11052_gb300 import api as _api
     if args.no_autotune:
-        from paper_2408_11052_gb300 import api as _api
         _api.set_autotune(False)
+    _api.set_mlp_fusion(args.mlp_fusion)
+    _api.set_gemm_kernel(args.gemm_kernel)
     rank, world, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local if world > 1 else 0)
     # one non-default stream for everything: the library replays the update step
@@ -634,6 +640,7 @@ def main():
                        "action": w.A, "goal": w.G, "hidden": [w.hidden] * w.layers, "repr": w.repr,
                        "energy": w.energy, "loss": w.loss, "alpha_autotune": bool(w.alpha_autotune),
                        "precision": args.precision, "path": args.path,
+                       "mlp_fusion": args.mlp_fusion, "gemm_kernel": args.gemm_kernel,
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "step": "insert 1 slice + relabel + critic fwd/bwd + Adam + actor fwd/bwd + Adam",
                        "parallelism": f"{world} independent agents"},

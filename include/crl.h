@@ -312,6 +312,32 @@ int crl_get_alpha(crl_ctx* ctx, float* alpha);
 int crl_collect(crl_ctx* ctx, int32_t n_steps, int32_t episode_length, float* obs_out, float* act_out,
                 uint8_t* done_out, void* stream);
 
+/* ---- checkpoint / resume --------------------------------------------------
+ * The library-owned training state of ctx as one host blob: the replay buffer
+ * (rows, episode starts, fill and insert count), the device counters (the
+ * CRL_STEP_AUTO step, the last sampled step, the Adam step counts of critic
+ * and actor, the tuned log alpha with its Adam moments) and, once crl_collect
+ * has run, the collection stub's environments (states, goals, episode steps,
+ * collection counter).  Parameters, gradients and Adam moments are the
+ * caller's memory and are saved by the caller.  Because every draw of the
+ * method (relabel offsets, actor noise, goal mix, collection) is a
+ * counter-based Philox block of (seed, agent, step), a context created with
+ * the same config, bound to the saved parameters and moments and given this
+ * blob continues bit-identically to the one that saved it.  (A library
+ * extension: the paper describes no checkpoint format.)
+ * crl_state_bytes: size of the blob now (it grows once crl_collect has run).
+ * crl_save_state: synchronises the device, writes the blob to `host` (host
+ *   memory, >= crl_state_bytes, else CRL_E_SHAPE).
+ * crl_load_state: synchronises the device, checks the blob's magic and sizes
+ *   (CRL_E_INVALID_ARG if it is not a blob of this library or is corrupt,
+ *   CRL_E_SHAPE if it comes from a context of other sizes or is truncated),
+ *   restores the state, drops the captured update graph and refreshes the
+ *   BF16 weight shadows at the next step.  A blob carrying environments needs
+ *   bound parameters (CRL_E_NOT_BOUND). */
+int crl_state_bytes(crl_ctx* ctx, size_t* bytes);
+int crl_save_state(crl_ctx* ctx, void* host, size_t bytes);
+int crl_load_state(crl_ctx* ctx, const void* host, size_t bytes);
+
 /* Message of the last failing call on ctx (ctx == NULL: on this thread). */
 const char* crl_last_error(const crl_ctx* ctx);
 

@@ -86,6 +86,9 @@ _SIGNATURES = {
     "crl_sync_status": (c_int32, [c_void_p, c_void_p, POINTER(c_uint32)]),
     "crl_get_alpha": (c_int32, [c_void_p, POINTER(c_float)]),
     "crl_collect": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "crl_state_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
+    "crl_save_state": (c_int32, [c_void_p, c_void_p, c_size_t]),
+    "crl_load_state": (c_int32, [c_void_p, c_void_p, c_size_t]),
     "crl_last_error": (ctypes.c_char_p, [c_void_p]),
     "crl_trace_start": (c_int32, [c_void_p, c_int32, c_int32]),
     "crl_trace_stop": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_double), POINTER(c_double)]),
@@ -352,6 +355,20 @@ class CRLContext:
         o = (None, None, None) if out is None else out
         check(lib().crl_collect(self.handle, n_steps, episode_length, ptr(o[0]), ptr(o[1]), ptr(o[2]),
                                 stream_handle(stream)), self.handle)
+
+    def save_state(self):
+        """The library-owned training state (replay buffer, counters, tuned alpha,
+        collection environments) as bytes; parameters and moments are the caller's."""
+        n = c_size_t()
+        check(lib().crl_state_bytes(self.handle, byref(n)), self.handle)
+        buf = ctypes.create_string_buffer(n.value)
+        check(lib().crl_save_state(self.handle, buf, n.value), self.handle)
+        return buf.raw
+
+    def load_state(self, blob):
+        """Restores a state written by save_state on a context of the same sizes."""
+        data = bytes(blob)
+        check(lib().crl_load_state(self.handle, data, len(data)), self.handle)
 
     def get_alpha(self):
         """The entropy coefficient the next actor step uses."""

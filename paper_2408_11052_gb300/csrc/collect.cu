@@ -122,6 +122,31 @@ void collect_steps(crl_ctx* c, int n, int episode_length, float* obs_out, float*
 
 }  // namespace
 
+// Allocates the collection stub's environments and staging and resets every
+// environment (episode starts drawn from the collection stream at step 0).
+void collect_alloc(crl_ctx* ctx, cudaStream_t st) {
+  const crl_config& cf = ctx->cfg;
+  crl_ctx::Envs& v = ctx->env;
+  const size_t es = ctx->esz;
+  const int E = cf.E;
+  v.s = static_cast<float*>(ctx->dalloc((size_t)E * cf.D * sizeof(float)));
+  v.g = static_cast<float*>(ctx->dalloc((size_t)E * cf.G * sizeof(float)));
+  v.t = static_cast<int32_t*>(ctx->dalloc((size_t)E * sizeof(int32_t)));
+  v.step = static_cast<unsigned long long*>(ctx->dalloc(sizeof(unsigned long long)));
+  v.pi_out = ctx->dalloc((size_t)E * 2 * cf.A * es);
+  v.a = ctx->dalloc((size_t)E * cf.A * es);
+  v.logpi = ctx->dalloc((size_t)E * es);
+  v.eps = ctx->dalloc((size_t)E * cf.A * es);
+  v.saved = ctx->dalloc(mlp_saved_bytes(ctx->shapes[CRL_NET_PI], E, es));
+  v.obs = static_cast<float*>(ctx->dalloc((size_t)E * cf.D * sizeof(float)));
+  v.act = static_cast<float*>(ctx->dalloc((size_t)E * cf.A * sizeof(float)));
+  v.done = static_cast<uint8_t*>(ctx->dalloc((size_t)E));
+  CRL_CHECK_CUDA(cudaMemsetAsync(v.step, 0, sizeof(unsigned long long), st));
+  launch_k(env_init_kernel, dim3(ceil_div(E, 8)), dim3(256), 0, st, E, cf.D, cf.G, v.s, v.g, v.t,
+           (unsigned long long)cf.seed, (unsigned long long)cf.agent);
+  v.ready = true;
+}
+
 }  // namespace crl
 
 extern "C" int crl_collect(crl_ctx* ctx, int32_t n_steps, int32_t episode_length, float* obs_out, float* act_out,
@@ -139,25 +164,7 @@ extern "C" int crl_collect(crl_ctx* ctx, int32_t n_steps, int32_t episode_length
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     crl_ctx::Envs& v = ctx->env;
     const size_t es = ctx->esz;
-    if (!v.ready) {
-      const int E = cf.E;
-      v.s = static_cast<float*>(ctx->dalloc((size_t)E * cf.D * sizeof(float)));
-      v.g = static_cast<float*>(ctx->dalloc((size_t)E * cf.G * sizeof(float)));
-      v.t = static_cast<int32_t*>(ctx->dalloc((size_t)E * sizeof(int32_t)));
-      v.step = static_cast<unsigned long long*>(ctx->dalloc(sizeof(unsigned long long)));
-      v.pi_out = ctx->dalloc((size_t)E * 2 * cf.A * es);
-      v.a = ctx->dalloc((size_t)E * cf.A * es);
-      v.logpi = ctx->dalloc((size_t)E * es);
-      v.eps = ctx->dalloc((size_t)E * cf.A * es);
-      v.saved = ctx->dalloc(mlp_saved_bytes(ctx->shapes[CRL_NET_PI], E, es));
-      v.obs = static_cast<float*>(ctx->dalloc((size_t)E * cf.D * sizeof(float)));
-      v.act = static_cast<float*>(ctx->dalloc((size_t)E * cf.A * sizeof(float)));
-      v.done = static_cast<uint8_t*>(ctx->dalloc((size_t)E));
-      CRL_CHECK_CUDA(cudaMemsetAsync(v.step, 0, sizeof(unsigned long long), st));
-      launch_k(env_init_kernel, dim3(ceil_div(E, 8)), dim3(256), 0, st, E, cf.D, cf.G, v.s, v.g, v.t,
-               (unsigned long long)cf.seed, (unsigned long long)cf.agent);
-      v.ready = true;
-    }
+    if (!v.ready) collect_alloc(ctx, st);
     if (cf.precision == CRL_PREC_FP64)
       collect_steps<double>(ctx, n_steps, episode_length, obs_out, act_out, done_out, st);
     else

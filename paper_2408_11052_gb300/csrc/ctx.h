@@ -165,6 +165,8 @@ void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g
 RelabelArgs relabel_args(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g, int32_t* idx,
                          bool pack_bf16);
 void update_body(crl_ctx* ctx, cudaStream_t st);
+// Allocates and resets the collection stub's environments (crl_collect's first call).
+void collect_alloc(crl_ctx* ctx, cudaStream_t st);
 
 // Runs one entry point: maps internal failures to status codes and makes the
 // context's tracer visible to the launch sites for the duration of the call.
