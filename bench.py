@@ -171,6 +171,27 @@ def cpu_oracle_rate(w, n_steps, budget_s=20.0):
     return done_steps / dt, done_steps, cores
 
 
+BLAS_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def cpu_oracle_rate_one_thread(args, budget_s=10.0):
+    """The same oracle rate in a child process whose BLAS runs one thread:
+    (steps/s, steps done), or None when the child fails."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-rate", str(budget_s), "--workload", args.workload]
+    for flag, v in (("--loss", args.loss), ("--energy", args.energy)):
+        if v is not None:
+            cmd += [flag, v]
+    if args.alpha_autotune:
+        cmd.append("--alpha-autotune")
+    env = dict(os.environ, **{k: "1" for k in BLAS_THREAD_VARS})
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=budget_s + 300)
+        r = json.loads(out.stdout.strip().splitlines()[-1])
+        return r["value"], r["steps"]
+    except (subprocess.SubprocessError, ValueError, KeyError, IndexError):
+        return None
+
+
 def run_reference(args, w):
     """--impl reference: the FP64 CPU oracle, as it stands, on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -543,6 +564,7 @@ def main():
                     help="BF16 network forward: grouped per-layer launches or one whole-network kernel")
     ap.add_argument("--gemm-kernel", default="any", choices=["any", "one_tile", "persistent", "pair"],
                     help="BF16 GEMM kernel family the autotuner may pick from")
+    ap.add_argument("--oracle-rate", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS.get(args.workload, workload.ANT_AUTOGRAD)
@@ -551,6 +573,10 @@ def main():
         over["alpha_autotune"] = True
     if over:
         w = w.with_(**over)
+    if args.oracle_rate is not None:
+        rate, steps, _ = cpu_oracle_rate(w, 200, budget_s=args.oracle_rate)
+        print(json.dumps({"value": rate, "steps": steps}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -629,6 +655,10 @@ def main():
         rate, steps, cores = cpu_oracle_rate(w, 200, budget_s=15.0)
         cpu = {"value": rate, "unit": "update steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{steps} full update steps of the same workload (FP64 numpy oracle)"}
+        one = cpu_oracle_rate_one_thread(args)
+        if one is not None:
+            cpu["one_thread"] = {"value": one[0], "unit": "update steps/s", "cores": 1,
+                                 "sample": f"{one[1]} update steps, BLAS limited to one thread"}
 
     h2d = w.E * (w.D + w.A) * 4 + w.E
     line = {"metric": METRIC, "value": value, "unit": "update steps/s", "n_gpus": world, "steps": args.steps,
