@@ -92,6 +92,10 @@ __device__ __forceinline__ int segment_of(const int* __restrict__ begin, int n, 
 // that allocate tensor memory trigger only after the allocation, so a waiting
 // successor never holds TMEM that its predecessor still needs.
 // Both instructions are no-ops for a kernel launched without the attribute.
+// L2 prefetch of the line holding p (a hint; nothing waits for it).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<uint64_t>(p)));
+}
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_enter() {

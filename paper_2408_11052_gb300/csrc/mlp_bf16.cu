@@ -1142,9 +1142,26 @@ struct AdamUnit {
 // where 1 - b^t is small (early steps), unlike 1 - powf(b, t).
 __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __restrict__ nets,
                                                           const AdamUnit* __restrict__ units) {
-  pdl_enter();
+  // the tables are immutable, and p, m, v are written by Adam alone: pull this
+  // block's lines into L2 while the predecessor (which writes g) drains
   const AdamUnit u = units[blockIdx.x];
   const AdamNetDev& a = nets[u.net];
+  if (threadIdx.x < 96) {
+    const float* arr = threadIdx.x < 32 ? a.p : (threadIdx.x < 64 ? a.m : a.v);
+    const int j = threadIdx.x % 32;
+    if (u.layer < 0) {
+      if (32 * j < u.c0) prefetch_l2(arr + u.r0 + 32 * j);
+    } else {
+      const ShadowLayer& L = a.L[u.layer];
+      const int o = u.r0 + j;
+      if (o < L.out) {
+        const float* row = arr + L.oW + (long long)o * L.in + u.c0;
+        prefetch_l2(row);
+        prefetch_l2(row + min(31, L.in - 1 - u.c0));
+      }
+    }
+  }
+  pdl_enter();
   // the descriptor's fields in registers: the stores below cannot change them
   const float* __restrict__ g = a.g;
   float* __restrict__ m = a.m;

@@ -108,6 +108,15 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
+// L2 prefetch of one box of a 2-D tensor map (a hint: it moves no data into
+// shared memory and completes nothing; L2 is the coherence point of global
+// memory, so a later load still sees every write made before it).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1)
+               : "memory");
+}
 
 // ---- TMEM ---------------------------------------------------------------------
 // Executed by one full warp; writes the TMEM base address to *slot.

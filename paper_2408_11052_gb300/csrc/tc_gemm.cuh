@@ -126,6 +126,19 @@ __device__ __forceinline__ void load_mask32(const __nv_bfloat16* m, bool (&on)[3
   }
 }
 
+// L2 prefetch of a tile's B operand (the weight side of every product here),
+// issued before pdl_wait so that its DRAM reads overlap the predecessor's
+// tail.  The predecessor never writes it: B holds weights (written by the
+// Adam step of an earlier launch) or activations of an earlier layer.
+template <int BN>
+__device__ __forceinline__ void prefetch_b_tile(const CUtensorMap* tmB, int K, int N, int n0) {
+  const int nk = (K + kBK - 1) / kBK;
+  for (int kb = 0; kb < nk && kb < 64; ++kb)
+#pragma unroll
+    for (int r = 0; r < BN / 64; ++r)
+      if (n0 + 64 * r < N) tma_prefetch_2d(tmB, kb * kBK, n0 + 64 * r);
+}
+
 // Epilogue of one 32-column chunk (columns col0 .. col0 + 31) of row `row`.
 // The full-chunk paths use 16-byte accesses; they need 16-byte aligned rows:
 // leading dimensions a multiple of 8 BF16 / 4 FP32 elements (hidden widths
@@ -326,6 +339,7 @@ __global__ void __launch_bounds__(128, 1)
     tmap_acquire(tmB);
     prefetch_tmap(tmA);
     prefetch_tmap(tmB);
+    prefetch_b_tile<BN>(tmB, K, N, n0);
     for (int s = 0; s < S::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
@@ -454,6 +468,11 @@ __global__ void __launch_bounds__(192, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
+    if ((int)blockIdx.x < total) {   // the first tile's B operand
+      const GemmProblem* P = find_problem(probs, nprob, blockIdx.x);
+      tmap_acquire(&P->b);
+      prefetch_b_tile<BN>(&P->b, P->K, P->N, (((int)blockIdx.x - P->tile_begin) % P->tiles_n) * BN);
+    }
     for (int s = 0; s < S::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
