@@ -15,57 +15,13 @@
 #include "common.cuh"
 #include "internal.h"
 #include "tables.h"
+#include "actor_head.cuh"
 #include "philox.cuh"
 #include "trace.h"
 
 namespace crl {
 
-constexpr double kLogStdMin = -5.0;
-constexpr double kLogStdMax = 2.0;
-constexpr double kLog2 = 0.69314718055994530942;
-constexpr double kHalfLog2Pi = 0.91893853320467274178;
-
 namespace {
-
-// One warp per row b, lanes over the action dims.
-// x0 != null: a' also goes into columns [x0_col, x0_col + A) of the split BF16
-// network input x0 (hi, lo interleaved: element c at 2c, 2c + 1).
-template <typename T>
-__device__ __forceinline__ void head_forward_body(const HeadFwdArgs<T>& p, int lb) {
-  const int B = p.B, A = p.A;
-  const T* __restrict__ out = p.out;
-  const float* __restrict__ eps = p.eps;
-  T* __restrict__ a_new = p.a_new;
-  T* __restrict__ eps_used = p.eps_used;
-  __nv_bfloat16* __restrict__ x0 = p.x0;
-  const int x0_ld = p.x0_ld, x0_col = p.x0_col;
-  const unsigned long long seed = p.seed, agent = p.agent;
-  const int lane = threadIdx.x % kWarp;
-  const int b = lb * (blockDim.x / kWarp) + threadIdx.x / kWarp;
-  if (b >= B) return;
-  const unsigned long long step = eps ? 0ull : *p.step_dev;
-  T lp = 0;
-  for (int d = lane; d < A; d += kWarp) {
-    const T mu = out[(size_t)b * 2 * A + d];
-    const T lraw = out[(size_t)b * 2 * A + A + d];
-    const T l = fmin(fmax(lraw, T(kLogStdMin)), T(kLogStdMax));
-    const T e = eps ? T(eps[(size_t)b * A + d]) : philox_normal<T>(step, b, 1ull + p.noise_extra, d, seed, agent);
-    const T u = mu + dev_exp(l) * e;
-    const T act = dev_tanh(u);
-    a_new[(size_t)b * A + d] = act;
-    if (x0) {
-      const float v = (float)act;
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      __nv_bfloat16* dst = x0 + (size_t)b * x0_ld + 2 * (x0_col + d);
-      dst[0] = hi;
-      dst[1] = __float2bfloat16_rn(v - __bfloat162float(hi));
-    }
-    eps_used[(size_t)b * A + d] = e;
-    lp += -T(0.5) * e * e - T(kHalfLog2Pi) - l - T(2) * (T(kLog2) - u - softplus(T(-2) * u));
-  }
-  lp = warp_sum(lp);
-  if (lane == 0) p.logpi[b] = lp;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) head_forward_kernel(const __grid_constant__ HeadFwdArgs<T> p) {
@@ -246,13 +202,6 @@ __global__ void __launch_bounds__(256) head_backward_kernel(const __grid_constan
 }
 
 // ---- several agents in one launch (BF16 path: float) ----------------------------
-__global__ void __launch_bounds__(256) head_forward_multi_kernel(const HeadFwdArgs<float>* __restrict__ tasks,
-                                                                const int* __restrict__ begin, int n) {
-  pdl_enter();
-  int lb, nb;
-  const int s = segment_of(begin, n, blockIdx.x, lb, nb);
-  head_forward_body(tasks[s], lb);
-}
 __global__ void __launch_bounds__(256) diag_energy_loss_multi_kernel(const ActorLossArgs<float>* __restrict__ tasks,
                                                                     const int* __restrict__ begin, int n) {
   pdl_enter();
@@ -291,20 +240,6 @@ void actor_head_forward(const ActorSpec& as, const T* pi_out, const float* eps, 
   const HeadFwdArgs<T> p{B,        as.A, pi_out, eps,   step_dev, seed,  agent,      a_new,
                          logpi,    eps_used, x0, x0_ld, x0_col,   noise_extra};
   launch_k(head_forward_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, p);
-}
-
-const char* actor_head_forward_multi(BlobCache& cache, const std::vector<HeadFwdArgs<float>>& tasks,
-                                     cudaStream_t st) {
-  if (tasks.empty()) return nullptr;
-  const HeadFwdArgs<float>* dt;
-  const int* db;
-  int blocks;
-  if (const char* err = multi_tables(cache, tasks, 8, st, &dt, &db, &blocks)) return err;
-  double bytes = 0.0;
-  for (const auto& t : tasks) bytes += (double)t.B * t.A * 4.0 * 5;
-  TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
-  launch_k(head_forward_multi_kernel, dim3(blocks), dim3(256), 0, st, dt, db, (int)tasks.size());
-  return nullptr;
 }
 
 const char* actor_loss_multi(BlobCache& cache, const std::vector<ActorLossArgs<float>>& tasks, cudaStream_t st) {

@@ -300,8 +300,11 @@ AdamShadowNet adam_net_of(crl_ctx* c, int net, const int* t, float lr) {
 // with_pi: the policy's forward (its parameters do not change before the
 // actor step) joins the encoders' grouped launches; the actor step then
 // reuses its output (update step only, where relabel packed its input).
+// head: the actor head's forward, run by extra blocks of the Adam launch (update
+// step only: it reads the policy output the with_pi forward wrote).
 void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g, int B, int apply, cudaStream_t st,
-                      bool refresh = true, bool packed = false, bool with_pi = false) {
+                      bool refresh = true, bool packed = false, bool with_pi = false,
+                      const HeadFwdArgs<float>* head = nullptr) {
   const crl_config& cf = c->cfg;
   unsigned* status = &c->ctr->status;
   BfNet& P = c->bf[CRL_NET_PHI];
@@ -358,7 +361,8 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     // Adam for phi and psi in one launch, refreshing their BF16 shadows
     const AdamShadowNet an[2] = {adam_net_of(c, CRL_NET_PHI, &c->ctr->t_critic, cf.lr_critic),
                                  adam_net_of(c, CRL_NET_PSI, &c->ctr->t_critic, cf.lr_critic)};
-    bf_check(adam_shadow_update(c->tables, an, 2, st));
+    const std::vector<HeadFwdArgs<float>> heads(head ? 1 : 0, head ? *head : HeadFwdArgs<float>{});
+    bf_check(adam_shadow_update(c->tables, an, 2, st, &heads));
   }
   check_launch("critic step (bf16)");
 }
@@ -368,8 +372,10 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
 // and the backward through phi (input gradient only) and pi.  packed: the
 // relabel kernel wrote the split network inputs, so the head writes a' into
 // phi's input directly.  bump_step: the loss kernel advances the relabel step.
+// head_done: the head's forward already ran in the critic's Adam launch.
 void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* eps, int B, int apply, cudaStream_t st,
-                     bool refresh = true, bool packed = false, bool pi_ready = false, bool bump_step = false) {
+                     bool refresh = true, bool packed = false, bool pi_ready = false, bool bump_step = false,
+                     bool head_done = false) {
   const crl_config& cf = c->cfg;
   unsigned* status = &c->ctr->status;
   BfNet& PI = c->bf[CRL_NET_PI];
@@ -396,8 +402,9 @@ void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* ep
     const BfPass pi_fwd[1] = {{&PI, ppi, nullptr, nullptr, B}};
     bf_check(bf_forward(c->groups, pi_fwd, 1, status, st));
   }
-  actor_head_forward<float>(as, PI.y, eps, &c->ctr->last_step, cf.seed, cf.agent, B, a_new, logpi, eps_used, st,
-                            packed ? P.x0 : nullptr, bf_net_x0_ld(P), P.s.in0);
+  if (!head_done)
+    actor_head_forward<float>(as, PI.y, eps, &c->ctr->last_step, cf.seed, cf.agent, B, a_new, logpi, eps_used, st,
+                              packed ? P.x0 : nullptr, bf_net_x0_ld(P), P.s.in0);
   if (!packed) bf_net_pack_input(P, s, a_new, B, st);
   // phi(s, a') and psi(g) with the critic's updated weights
   const BfPass fwd[2] = {{&P, pphi, nullptr, da, B}, {&Q, ppsi, nullptr, nullptr, B}};
@@ -801,9 +808,27 @@ void update_body(crl_ctx* ctx, cudaStream_t st) {
     critic_impl<double>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
     actor_impl<double>(ctx, ctx->bs, g_actor, nullptr, B, 1, st, true);
   } else if (ctx->bf16) {
-    // the shadows follow the weights through the fused Adam; only the first call refreshes
-    critic_impl_bf16(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st, false, true, !mix);
-    actor_impl_bf16(ctx, ctx->bs, g_actor, nullptr, B, 1, st, false, !mix, !mix, true);
+    // the shadows follow the weights through the fused Adam; only the first call refreshes.
+    // Without the goal mix the actor's head forward (Philox noise at the last
+    // sampled step, a' straight into phi's packed input) runs in the critic's Adam launch.
+    BfNet& P = ctx->bf[CRL_NET_PHI];
+    HeadFwdArgs<float> head;
+    memset(&head, 0, sizeof(head));   // member by member: zeroed padding keys the device table
+    head.B = B;
+    head.A = ctx->cfg.A;
+    head.out = ctx->bf[CRL_NET_PI].y;
+    head.eps = nullptr;
+    head.step_dev = &ctx->ctr->last_step;
+    head.seed = ctx->cfg.seed;
+    head.agent = ctx->cfg.agent;
+    head.a_new = static_cast<float*>(ctx->a_new);
+    head.logpi = static_cast<float*>(ctx->logpi);
+    head.eps_used = static_cast<float*>(ctx->eps_used);
+    head.x0 = P.x0;
+    head.x0_ld = bf_net_x0_ld(P);
+    head.x0_col = P.s.in0;
+    critic_impl_bf16(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st, false, true, !mix, mix ? nullptr : &head);
+    actor_impl_bf16(ctx, ctx->bs, g_actor, nullptr, B, 1, st, false, !mix, !mix, true, !mix);
   } else {
     critic_impl<float>(ctx, ctx->bs, ctx->ba, ctx->bg, B, 1, st);
     actor_impl<float>(ctx, ctx->bs, g_actor, nullptr, B, 1, st, true);

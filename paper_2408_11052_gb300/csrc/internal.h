@@ -214,8 +214,6 @@ void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used
 
 class BlobCache;
 // Several agents in one launch each (float tasks of the BF16 path; tables cached in `cache`).
-const char* actor_head_forward_multi(BlobCache& cache, const std::vector<HeadFwdArgs<float>>& tasks,
-                                     cudaStream_t st);
 const char* actor_loss_multi(BlobCache& cache, const std::vector<ActorLossArgs<float>>& tasks, cudaStream_t st);
 const char* actor_head_backward_multi(BlobCache& cache, const std::vector<HeadBwdArgs<float>>& tasks,
                                       cudaStream_t st);

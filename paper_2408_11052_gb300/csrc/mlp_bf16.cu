@@ -13,6 +13,7 @@
 #include <cmath>
 #include <vector>
 
+#include "actor_head.cuh"
 #include "common.cuh"
 #include "mlp_bf16.cuh"
 #include "tc_gemm.cuh"
@@ -1140,8 +1141,20 @@ struct AdamUnit {
 // (the transposed single BF16, written through a shared-memory transpose).
 // Bias corrections 1 - b^t = -expm1(t ln b): accurate to a few float ulps
 // where 1 - b^t is small (early steps), unlike 1 - powf(b, t).
+// Blocks [nunits, gridDim.x) run the actor head's forward (head_begin: each
+// task's first block, 8 rows per block) instead: it reads only the policy's
+// output, so it rides in the critic's Adam launch.
 __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __restrict__ nets,
-                                                          const AdamUnit* __restrict__ units) {
+                                                          const AdamUnit* __restrict__ units, int nunits,
+                                                          const HeadFwdArgs<float>* __restrict__ heads,
+                                                          const int* __restrict__ head_begin, int nheads) {
+  if ((int)blockIdx.x >= nunits) {
+    pdl_enter();
+    int lb, nb;
+    const int s = segment_of(head_begin, nheads, (int)blockIdx.x - nunits, lb, nb);
+    head_forward_body(heads[s], lb);
+    return;
+  }
   // the tables are immutable, and p, m, v are written by Adam alone: pull this
   // block's lines into L2 while the predecessor (which writes g) drains
   const AdamUnit u = units[blockIdx.x];
@@ -1215,7 +1228,8 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __re
 
 }  // namespace
 
-const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int count, cudaStream_t st) {
+const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int count, cudaStream_t st,
+                               const std::vector<HeadFwdArgs<float>>* heads) {
   if (count <= 0) return nullptr;
   std::vector<AdamNetDev> devs(count);
   std::vector<AdamUnit> units;
@@ -1262,8 +1276,24 @@ const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int 
   if (!dt) return err;
   const AdamUnit* du = cache.get(units, st, &err);
   if (!du) return err;
-  TraceLaunch tr(CRL_TRACE_ADAM, st, 28.0 * ntot);
-  launch_k(adam_shadow_kernel, dim3((unsigned)units.size()), dim3(256), 0, st, dt, du);
+  const HeadFwdArgs<float>* dh = nullptr;
+  const int* dhb = nullptr;
+  int nh = 0, head_blocks = 0;
+  double head_bytes = 0.0;
+  if (heads && !heads->empty()) {
+    std::vector<int> begin(heads->size() + 1, 0);
+    for (size_t i = 0; i < heads->size(); ++i) {
+      begin[i + 1] = begin[i] + ceil_div((*heads)[i].B, 8);
+      head_bytes += (double)(*heads)[i].B * (*heads)[i].A * 4.0 * 5;
+    }
+    head_blocks = begin.back();
+    nh = (int)heads->size();
+    if (!(dh = cache.get(*heads, st, &err))) return err;
+    if (!(dhb = cache.get(begin, st, &err))) return err;
+  }
+  TraceLaunch tr(CRL_TRACE_ADAM, st, 28.0 * ntot + head_bytes);
+  launch_k(adam_shadow_kernel, dim3((unsigned)(units.size() + head_blocks)), dim3(256), 0, st, dt, du,
+           (int)units.size(), dh, dhb, nh);
   return nullptr;
 }
 

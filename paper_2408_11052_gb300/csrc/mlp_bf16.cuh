@@ -180,6 +180,8 @@ struct AdamShadowNet {
   BfNet* net;
 };
 // One launch for `count` networks (any number); its launch tables live in `cache`.
-const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int count, cudaStream_t st);
+// heads: actor-head forwards run by extra blocks of the same launch (optional).
+const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int count, cudaStream_t st,
+                               const std::vector<HeadFwdArgs<float>>* heads = nullptr);
 
 }  // namespace crl

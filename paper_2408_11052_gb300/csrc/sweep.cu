@@ -155,16 +155,8 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
   // (the operands were written by the encoders' output layers: no prepare stage)
   for (int stage = 1; stage < 3; ++stage) sweep_check(energy_tc_multi(sw->tables, ea, stage, st));
   sweep_check(bf_backward(sw->groups, bwd.data(), (int)bwd.size(), status, st));
-  {
-    std::vector<AdamShadowNet> an;
-    for (crl_ctx* c : sw->agents) {
-      an.push_back(adam_net_of(c, CRL_NET_PHI, &c->ctr->t_critic, c->cfg.lr_critic));
-      an.push_back(adam_net_of(c, CRL_NET_PSI, &c->ctr->t_critic, c->cfg.lr_critic));
-    }
-    sweep_check(adam_shadow_update(sw->tables, an.data(), (int)an.size(), st));
-  }
-  // ---- actor: head (writes a' into phi's input), phi and psi forward with the
-  // updated critic, diagonal energy + loss, phi's input gradient, head backward, pi backward
+  // Adam for every phi and psi; the actors' head forwards (a' into phi's input:
+  // they read only the policies' outputs) run as extra blocks of the same launch
   {
     std::vector<HeadFwdArgs<float>> hf;
     for (crl_ctx* c : sw->agents) {
@@ -187,8 +179,15 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
       h.x0_col = P.s.in0;
       hf.push_back(h);
     }
-    sweep_check(actor_head_forward_multi(sw->tables, hf, st));
+    std::vector<AdamShadowNet> an;
+    for (crl_ctx* c : sw->agents) {
+      an.push_back(adam_net_of(c, CRL_NET_PHI, &c->ctr->t_critic, c->cfg.lr_critic));
+      an.push_back(adam_net_of(c, CRL_NET_PSI, &c->ctr->t_critic, c->cfg.lr_critic));
+    }
+    sweep_check(adam_shadow_update(sw->tables, an.data(), (int)an.size(), st, &hf));
   }
+  // ---- actor: phi and psi forward with the updated critic, diagonal energy +
+  // loss, phi's input gradient, head backward, pi backward
   std::vector<BfPass> afwd, phi_b, pi_b;
   for (crl_ctx* c : sw->agents) {
     const int B = c->cfg.B;
