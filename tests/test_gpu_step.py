@@ -296,6 +296,38 @@ def test_graph_replay_matches_eager(precision, path):
         np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
 
 
+@pytest.mark.parametrize("precision,path", [("fp32", "plain"), ("bf16", "plain"), ("bf16", "fused")])
+def test_update_step_matches_separate_calls(precision, path):
+    """crl_update_step (the relabel kernel packing the network inputs, the
+    policy's forward inside the critic's launches, the actor head inside the
+    critic's Adam launch, the step counter advanced on the device) equals insert
+    + sample + crl_critic_step + crl_actor_step called one by one, bit for bit."""
+    w = small(B=64, repr=64)
+    extra = workload.buffer_contents(w, n=3, mean_len=9.0, seed_offset=7)
+    runs = []
+    for fused in (True, False):
+        ctx, _, _ = setup(w, precision=precision, path=path, n=60)
+        hist = []
+        for i in range(3):
+            ins = [torch.from_numpy(x[i:i + 1]).to(ctx.device) for x in extra]
+            if fused:
+                loss = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+                ctx.update_step(*ins, loss_out=loss)
+                hist.append(loss.cpu().numpy().copy())
+            else:
+                ctx.insert(*ins)
+                s, a, g, _ = ctx.sample(step=i, B=w.B)
+                lc = ctx.critic_step(s, a, g, apply_update=True)
+                la = ctx.actor_step(s, g, apply_update=True)
+                hist.append(np.concatenate([lc.cpu().numpy(), la.cpu().numpy()]))
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == (0, 0)
+        runs.append((np.array(hist), {n: ctx.store[n]["params"].cpu().numpy() for n in ("phi", "psi", "pi")}))
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    for n in ("phi", "psi", "pi"):
+        np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n], err_msg=n)
+
+
 @pytest.mark.parametrize("kernel", ["persistent", "pair"])
 @pytest.mark.parametrize("path", ["plain", "fused"])
 def test_persistent_gemm_matches_one_tile_gemm(path, kernel):
