@@ -338,6 +338,20 @@ int crl_state_bytes(crl_ctx* ctx, size_t* bytes);
 int crl_save_state(crl_ctx* ctx, void* host, size_t bytes);
 int crl_load_state(crl_ctx* ctx, const void* host, size_t bytes);
 
+/* ---- logit statistics (library diagnostic) --------------------------------
+ * With on != 0 every critic step of ctx (crl_critic_step, crl_update_step, a
+ * sweep step) also computes, from the representations its energy was formed
+ * from, the mean positive-pair logit (1/B) sum_i F_ii and the mean negative
+ * logit (1/(B^2 - B)) sum_{i != j} F_ij (NaN for B = 1), F = f(phi_i, psi_j) /
+ * tau with the configured energy (§3.1, App. A.2).  The representations are the
+ * encoders' FP32 outputs (FP64 on the check path); on the fused BF16 path the
+ * energy itself is formed from their BF16 rounding.  Cost: one extra pass over
+ * the B x B pairs (two launches, deterministic FP64 sums); off by default.
+ * crl_get_logit_stats synchronises the device and copies the values of the
+ * last such step to out[2] (host memory; NaN before any). */
+int crl_set_logit_stats(crl_ctx* ctx, int32_t on);
+int crl_get_logit_stats(crl_ctx* ctx, float* out);
+
 /* Message of the last failing call on ctx (ctx == NULL: on this thread). */
 const char* crl_last_error(const crl_ctx* ctx);
 

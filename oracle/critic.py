@@ -94,6 +94,17 @@ def energy_matrix(phi, psi, energy="l2", tau=1.0):
     return f / tau
 
 
+def logit_stats(F):
+    """Diagnostic of an energy matrix (no counterpart in the paper): the mean
+    positive-pair logit (1/B) sum_i F_ii and the mean negative logit
+    (1/(B^2 - B)) sum_{i != j} F_ij (NaN when B = 1: there are no negatives)."""
+    F = np.asarray(F, dtype=np.float64)
+    B = F.shape[0]
+    diag = float(np.trace(F)) / B
+    off = float((F.sum() - np.trace(F)) / (B * (B - 1))) if B > 1 else float("nan")
+    return diag, off
+
+
 def energy_diagonal(phi, psi, energy="l2", tau=1.0):
     """f(phi_i, psi_i) / tau for each i (the positive pairs)."""
     phi = np.asarray(phi, dtype=np.float64)

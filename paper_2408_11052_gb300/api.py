@@ -89,6 +89,8 @@ _SIGNATURES = {
     "crl_state_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
     "crl_save_state": (c_int32, [c_void_p, c_void_p, c_size_t]),
     "crl_load_state": (c_int32, [c_void_p, c_void_p, c_size_t]),
+    "crl_set_logit_stats": (c_int32, [c_void_p, c_int32]),
+    "crl_get_logit_stats": (c_int32, [c_void_p, POINTER(c_float)]),
     "crl_last_error": (ctypes.c_char_p, [c_void_p]),
     "crl_trace_start": (c_int32, [c_void_p, c_int32, c_int32]),
     "crl_trace_stop": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_double), POINTER(c_double)]),
@@ -369,6 +371,16 @@ class CRLContext:
         """Restores a state written by save_state on a context of the same sizes."""
         data = bytes(blob)
         check(lib().crl_load_state(self.handle, data, len(data)), self.handle)
+
+    def set_logit_stats(self, on=True):
+        """Record the mean positive and negative logits of every critic step."""
+        check(lib().crl_set_logit_stats(self.handle, 1 if on else 0), self.handle)
+
+    def logit_stats(self):
+        """(mean F_ii, mean F_ij over i != j) of the last critic step with stats on."""
+        out = (c_float * 2)()
+        check(lib().crl_get_logit_stats(self.handle, out), self.handle)
+        return out[0], out[1]
 
     def get_alpha(self):
         """The entropy coefficient the next actor step uses."""

@@ -163,6 +163,7 @@ void critic_impl(crl_ctx* c, const float* s, const float* a, const float* g, int
   const LossSpec ls = loss_spec(cf);
   infonce_forward<T>(ls, phi, psi, B, cf.repr, loss, rl, cl, c->ws, cf.path, &c->ctr->status,
                      apply ? &c->ctr->t_critic : nullptr, st);
+  logit_stats_launch(c, phi, psi, B, sizeof(T) == 8, st);
   infonce_backward<T>(ls, phi, psi, B, cf.repr, rl, cl, 1.0, dphi, dpsi, c->ws, cf.path, st);
   mlp_backward<T, float>(c->shapes[CRL_NET_PHI], pphi, s, a, B, c->saved[CRL_NET_PHI], dphi,
                          static_cast<T*>(c->nets[CRL_NET_PHI].grads), nullptr, nullptr, st);
@@ -336,6 +337,7 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     fpass[1].energy_out = &eo[1];
   }
   bf_check(bf_forward(c->groups, fpass, with_pi ? 3 : 2, status, st));
+  logit_stats_launch(c, P.y, Q.y, B, false, st);
   float* rl = static_cast<float*>(c->row_lse);
   float* cl = static_cast<float*>(c->col_lse);
   float* loss = static_cast<float*>(c->loss);
@@ -735,6 +737,7 @@ int crl_bind_params(crl_ctx* ctx, const crl_net_ptrs nets[3]) {
 
 int crl_buffer_insert(crl_ctx* ctx, const float* obs, const float* act, const uint8_t* done, int32_t n,
                       void* stream) {
+  NvtxRange nvtx("crl_buffer_insert");
   return guarded(ctx, [&] {
     CRL_REQUIRE(ctx, CRL_E_INVALID_ARG, "null context");
     insert_impl(ctx, obs, act, done, n, static_cast<cudaStream_t>(stream));
@@ -750,6 +753,7 @@ int crl_buffer_size(const crl_ctx* ctx, int32_t* size, int64_t* total) {
 
 int crl_sample_relabel(crl_ctx* ctx, uint64_t step, int32_t B, float* s, float* a, float* g, int32_t* idx,
                        void* stream) {
+  NvtxRange nvtx("crl_sample_relabel");
   return guarded(ctx, [&] {
     CRL_REQUIRE(ctx, CRL_E_INVALID_ARG, "null context");
     relabel_impl(ctx, step, B, s, a, g, idx, static_cast<cudaStream_t>(stream));
@@ -758,6 +762,7 @@ int crl_sample_relabel(crl_ctx* ctx, uint64_t step, int32_t B, float* s, float* 
 
 int crl_critic_step(crl_ctx* ctx, const float* s, const float* a, const float* g, int32_t B, int32_t apply_update,
                     float* loss_out, void* stream) {
+  NvtxRange nvtx("crl_critic_step");
   return guarded(ctx, [&] {
     CRL_REQUIRE(ctx, CRL_E_INVALID_ARG, "null context");
     CRL_REQUIRE(ctx->bound, CRL_E_NOT_BOUND, "crl_bind_params has not been called");
@@ -774,6 +779,7 @@ int crl_critic_step(crl_ctx* ctx, const float* s, const float* a, const float* g
 
 int crl_actor_step(crl_ctx* ctx, const float* s, const float* g, const float* eps, int32_t B, int32_t apply_update,
                    float* loss_out, void* stream) {
+  NvtxRange nvtx("crl_actor_step");
   return guarded(ctx, [&] {
     CRL_REQUIRE(ctx, CRL_E_INVALID_ARG, "null context");
     CRL_REQUIRE(ctx->bound, CRL_E_NOT_BOUND, "crl_bind_params has not been called");
@@ -840,6 +846,7 @@ extern "C" {
 
 int crl_update_step(crl_ctx* ctx, const float* obs, const float* act, const uint8_t* done, int32_t n_insert,
                     float* loss_out, void* stream) {
+  NvtxRange nvtx("crl_update_step");
   return guarded(ctx, [&] {
     CRL_REQUIRE(ctx, CRL_E_INVALID_ARG, "null context");
     CRL_REQUIRE(ctx->bound, CRL_E_NOT_BOUND, "crl_bind_params has not been called");

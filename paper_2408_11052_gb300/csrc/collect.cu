@@ -152,6 +152,7 @@ void collect_alloc(crl_ctx* ctx, cudaStream_t st) {
 extern "C" int crl_collect(crl_ctx* ctx, int32_t n_steps, int32_t episode_length, float* obs_out, float* act_out,
                            uint8_t* done_out, void* stream) {
   using namespace crl;
+  NvtxRange nvtx("crl_collect");
   return guarded(ctx, [&] {
     CRL_REQUIRE(ctx, CRL_E_INVALID_ARG, "null context");
     CRL_REQUIRE(ctx->bound, CRL_E_NOT_BOUND, "crl_bind_params has not been called");

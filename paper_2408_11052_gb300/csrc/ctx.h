@@ -71,7 +71,7 @@ struct crl_ctx {
   int64_t total_host = 0;
   Counters* ctr = nullptr;
   bool bound = false;
-  int bind_generation = 0;  // incremented by every crl_bind_params (sweeps rebuild their tables)
+  int bind_generation = 0;  // incremented by crl_bind_params and crl_set_logit_stats (sweeps rebuild)
   crl_net_ptrs nets[3]{};
   MlpShape shapes[3]{};
   int64_t counts[3]{};
@@ -98,6 +98,10 @@ struct crl_ctx {
     float *obs = nullptr, *act = nullptr;  // one time slice for the insert
     uint8_t* done = nullptr;
   } env;
+  // logit statistics of the critic steps (crl_set_logit_stats): [2] floats and per-tile FP64 sums
+  bool stats_on = false;
+  float* stats = nullptr;
+  double* stats_part = nullptr;
   // host-input staging for crl_buffer_insert
   void* stage = nullptr;
   size_t stage_bytes = 0;
@@ -165,6 +169,10 @@ void relabel_impl(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g
 RelabelArgs relabel_args(crl_ctx* c, uint64_t step, int B, float* s, float* a, float* g, int32_t* idx,
                          bool pack_bf16);
 void update_body(crl_ctx* ctx, cudaStream_t st);
+// Logit statistics of a critic step's representations phi, psi [B][R] (float,
+// or double when fp64) into c->stats, when switched on (stats.cu).
+void logit_stats_alloc(crl_ctx* c);
+void logit_stats_launch(crl_ctx* c, const void* phi, const void* psi, int B, bool fp64, cudaStream_t st);
 // Allocates and resets the collection stub's environments (crl_collect's first call).
 void collect_alloc(crl_ctx* ctx, cudaStream_t st);
 

@@ -140,6 +140,8 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     fwd.push_back({&c->bf[CRL_NET_PI], static_cast<const float*>(np[CRL_NET_PI].params), nullptr, nullptr, B});
   }
   sweep_check(bf_forward(sw->groups, fwd.data(), (int)fwd.size(), status, st));
+  for (crl_ctx* c : sw->agents)
+    logit_stats_launch(c, c->bf[CRL_NET_PHI].y, c->bf[CRL_NET_PSI].y, c->cfg.B, false, st);
   // ---- fused energy + InfoNCE + penalty, forward and backward
   std::vector<EnergyAgent> ea;
   for (crl_ctx* c : sw->agents) {
@@ -347,6 +349,7 @@ int crl_sweep_agent(crl_sweep* sw, int32_t i, crl_ctx** ctx) {
 
 int crl_sweep_update_step(crl_sweep* sw, const float* const* obs, const float* const* act,
                           const uint8_t* const* done, int32_t n_insert, float* loss_out, void* stream) {
+  NvtxRange nvtx("crl_sweep_update_step");
   return sweep_guarded(sw, [&] {
     CRL_REQUIRE(sw, CRL_E_INVALID_ARG, "null sweep");
     CRL_REQUIRE(n_insert >= 0, CRL_E_INVALID_ARG, "n_insert must be >= 0");
