@@ -163,9 +163,7 @@ extern "C" int crl_collect(crl_ctx* ctx, int32_t n_steps, int32_t episode_length
     CRL_REQUIRE(!done_out || !is_host_pointer(done_out), CRL_E_INVALID_ARG, "done_out must be device memory");
     const crl_config& cf = ctx->cfg;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    crl_ctx::Envs& v = ctx->env;
-    const size_t es = ctx->esz;
-    if (!v.ready) collect_alloc(ctx, st);
+    if (!ctx->env.ready) collect_alloc(ctx, st);
     if (cf.precision == CRL_PREC_FP64)
       collect_steps<double>(ctx, n_steps, episode_length, obs_out, act_out, done_out, st);
     else

@@ -1032,7 +1032,7 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant_
 // Per-agent arguments and tensor maps in an immutable device table; agent s
 // owns the blocks [begin[s], begin[s+1]) of each launch: 2 ceil(B / 32) prep
 // blocks (phi then psi), n^2 forward tiles, 2 n backward CTAs.
-struct alignas(64) EnergyTask {
+struct EnergyTask {   // 128-byte aligned by its tensor maps
   CUtensorMap tmX, tmY;
   FwdArgs f;
   BwdArgs row, col;

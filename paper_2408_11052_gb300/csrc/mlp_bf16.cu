@@ -906,15 +906,17 @@ bool mlp_fusable(const BfPass* nets, int count) {
   for (int k = 0; k < count; ++k) {
     const BfNet& n = *nets[k].net;
     if (n.s.layernorm || n.s.hidden % 64 != 0 || n.s.hidden > 256) return false;
+    if (n.s.hidden != nets[0].net->s.hidden) return false;   // one cluster size per launch
     for (int l = 0; l <= n.layers; ++l)
       if (n.L[l].out > 256 || n.L[l].kp > 256) return false;
   }
   return true;
 }
 
-constexpr int kMlpStages = 4;
+constexpr int kMlpStages = 3;
 
-void launch_mlp_fused(const tc::GemmProblem* t, int nlayer, int nnet, int ctas, unsigned* status, cudaStream_t st) {
+void launch_mlp_fused(const tc::GemmProblem* t, int nlayer, int nnet, int ctas, int csize, unsigned* status,
+                      cudaStream_t st) {
   using S = tc::MlpSmem<kMlpStages>;
   static bool attr = false;
   if (!attr) {
@@ -922,7 +924,8 @@ void launch_mlp_fused(const tc::GemmProblem* t, int nlayer, int nnet, int ctas, 
                          S::kBytes);
     attr = true;
   }
-  launch_k(tc::tc_mlp_forward_kernel<kMlpStages>, dim3(ctas), dim3(192), S::kBytes, st, t, nlayer, nnet, status);
+  launch_k_cluster(tc::tc_mlp_forward_kernel<kMlpStages>, dim3(ctas), dim3(192), S::kBytes, st, (unsigned)csize, t,
+                   nlayer, nnet, csize, status);
 }
 
 }  // namespace
@@ -931,17 +934,16 @@ const char* bf_forward_layers(GemmGroups& gg, const BfPass* nets, int count, uns
 
 // One grouped pass over every layer: one grouped GEMM launch per layer, or,
 // when asked for (CRL_MLP_WHOLE) and the networks fit it, the whole-network
-// kernel in one launch (identical outputs).  The per-layer launches are the
-// default: at the widths the whole-network kernel takes, one SM per 128-row
-// block runs every layer's full width (twice the K of the split weights), and
-// the grouped per-layer launches, spread over four to eight times as many
-// SMs, measured faster on every workload here.
+// kernel in one launch (a cluster of H / 64 CTAs per 128-row block; identical
+// outputs).
 const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st) {
   if (count <= 0) return nullptr;
   if (g_mlp_fusion != CRL_MLP_WHOLE || !mlp_fusable(nets, count)) return bf_forward_layers(gg, nets, count, status, st);
   const int layers = nets[0].net->layers;
   for (int k = 1; k < count; ++k)
     if (nets[k].net->layers != layers) return bf_forward_layers(gg, nets, count, status, st);
+  // a cluster of H / 64 CTAs per 128-row block, one 64-column slice of every hidden layer each
+  const int csize = nets[0].net->s.hidden / 64;
   std::vector<tc::GemmProblem> probs;
   int ctas = 0, nnet = 0;
   double flops = 0.0;
@@ -953,7 +955,7 @@ const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* 
       probs.push_back(p);
       flops += 2.0 * nets[k].M * nets[k].net->L[l].out * nets[k].net->L[l].in;
     }
-    ctas += ceil_div(nets[k].M, tc::kBM);
+    ctas += ceil_div(nets[k].M, tc::kBM) * csize;
     ++nnet;
   }
   if (nnet == 0) return nullptr;
@@ -962,7 +964,7 @@ const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* 
   const tc::GemmProblem* t = gg.table(probs, 0, &tiles, st, &err);
   if (!t) return err;
   TraceLaunch tr(CRL_TRACE_GEMM, st, flops);
-  launch_mlp_fused(t, layers + 1, nnet, ctas, status, st);
+  launch_mlp_fused(t, layers + 1, nnet, ctas, csize, status, st);
   return nullptr;
 }
 

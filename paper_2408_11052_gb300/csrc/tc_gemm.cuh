@@ -60,12 +60,13 @@ struct EpiDesc {
   float* aux;
 };
 
-struct alignas(64) GemmProblem {
+struct GemmProblem {   // 128-byte aligned by its tensor maps
   CUtensorMap a, b;
   int M, N, K, nkA;   // nkA > 0: split-weight product (see tc_gemm_kernel)
   int tiles_n, tile_begin, pad0, pad1;
   EpiDesc epi;
 };
+static_assert(alignof(GemmProblem) >= 64 && sizeof(GemmProblem) % 64 == 0, "problem tables hold aligned tensor maps");
 
 // Ring depth STAGES: deep rings keep a whole 512-deep product in flight at
 // once (latency-bound small problems); shallow ones leave room for two CTAs
@@ -731,28 +732,34 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ---- whole-network forward for narrow networks ------------------------------------
-// One CTA per (network, 128-row block) runs every layer of the network's forward:
-// the layer's activations stay in shared memory as the next layer's A operand
-// (K-major, 128-byte swizzle, up to 256 columns), so a pass over L + 1 layers is
-// one launch instead of L + 1.  Layer l is problem l of the network's slice of
-// the problem table (the same problems the per-layer launches run: B = the
-// split weights, nkA A slices, the layer's epilogue); layer 0's A is loaded
-// from its tensor map once.  192 threads: warp 4 lane 0 streams the weights of
-// every layer through a STAGES-deep ring, warp 5 lane 0 issues the MMAs (layer
-// l waits until the epilogue of layer l - 1 has written its activations and
-// read the accumulator), warps 0..3 run the epilogues (hidden layers: bias +
-// ReLU to h, h^T and the shared-memory A; the output layer: its own
-// epilogue).  Same products in the same order and the same epilogue arithmetic
+// A cluster of C = H / 64 CTAs per (network, 128-row block) runs every layer of
+// the network's forward in one launch.  In a hidden layer, CTA rank r computes
+// the 64 output columns 64 r .. 64 r + 63 (its 64-row box of the layer's split
+// weights), writes them (bias + ReLU) to h and h^T, and as K slice r of the next
+// layer's A operand into its shared memory (K-major, 128-byte swizzle), which
+// it then copies into the same slice of every other CTA of the cluster (bulk
+// copies between the CTAs' shared memory, completing on the receiver's
+// barrier): after each hidden layer every CTA holds the whole next A.  The A
+// tile is double-buffered, so a slice for layer l + 1 never lands on the A a
+// slower CTA still multiplies in layer l.  The output layer (N <= 256, its
+// epilogue needs whole rows) runs on rank 0 alone, and the last hidden layer's
+// slices go to rank 0 only.  Layer l is problem l of the network's slice of the
+// problem table (the same problems the per-layer launches run: B = the split
+// weights, nkA A slices, the layer's epilogue); layer 0's A is loaded from its
+// tensor map by every CTA.  192 threads: warp 4 lane 0 streams the weights
+// through a STAGES-deep ring, warp 5 lane 0 issues the MMAs, warps 0..3 run the
+// epilogues.  Same products in the same order and the same epilogue arithmetic
 // as the per-layer kernels, so the outputs are identical.  Requirements
-// (checked by the host): hidden widths multiples of 32 up to 256, every layer's
-// K at most 256 (4 slices), no LayerNorm.
+// (checked by the host): hidden width H a multiple of 64 up to 256, every
+// layer's K at most 256 per weight half (4 slices), no LayerNorm.
 constexpr int kMlpMaxSlices = 4;
 
 template <int STAGES>
 struct MlpSmem {
-  static constexpr uint32_t kABytes = kMlpMaxSlices * kBM * kBK * 2;   // 64 KiB
+  static constexpr uint32_t kSlice = kBM * kBK * 2;                     // 16 KiB
+  static constexpr uint32_t kABytes = kMlpMaxSlices * kSlice;           // 64 KiB per A buffer
   static constexpr uint32_t kBStage = 256 * kBK * 2;                    // 32 KiB (N <= 256)
-  static constexpr uint32_t kBytes = kABytes + STAGES * kBStage + 1024 + 256;
+  static constexpr uint32_t kBytes = 2 * kABytes + STAGES * kBStage + 1024 + 256;
   static_assert(kBytes <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -761,23 +768,25 @@ __device__ __forceinline__ uint32_t mlp_sw128_offset(int row, int chunk) {
 }
 
 // The table holds nnet x nlayer problems, network-major; the first problem of
-// network k carries in tile_begin the index of its first CTA.
+// network k carries in tile_begin the index of its first CTA (a multiple of csize).
 template <int STAGES>
 __global__ void __launch_bounds__(192, 1)
-    tc_mlp_forward_kernel(const GemmProblem* __restrict__ probs, int nlayer, int nnet, unsigned* status) {
+    tc_mlp_forward_kernel(const GemmProblem* __restrict__ probs, int nlayer, int nnet, int csize, unsigned* status) {
   using S = MlpSmem<STAGES>;
   using bf16 = __nv_bfloat16;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + S::kABytes;
+  uint8_t* sA0 = smem;                    // A buffers: layer l reads buffer l % 2
+  uint8_t* sB = smem + 2 * S::kABytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * S::kBStage);
   uint64_t* empty = full + STAGES;
   uint64_t* xfull = empty + STAGES;   // layer 0's A loaded
   uint64_t* accf = xfull + 1;         // layer l's accumulator ready (phase l)
-  uint64_t* abuf = accf + 1;          // layer l's epilogue done (phase l; four warps)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(abuf + 1);
+  uint64_t* aready = accf + 1;        // [2] A buffer complete: the local slice + the peers' (tx)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(aready + 2);
+  auto abuf = [&](int l) { return sA0 + (l & 1) * S::kABytes; };
 
+  const uint32_t rank = csize > 1 ? cluster_ctarank() : 0u;
   int lo = 0, hi = nnet - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
@@ -785,8 +794,16 @@ __global__ void __launch_bounds__(192, 1)
     else hi = mid - 1;
   }
   const GemmProblem* P = probs + (size_t)lo * nlayer;
-  const int m0 = ((int)blockIdx.x - P[0].tile_begin) * kBM;
+  const int m0 = (((int)blockIdx.x - P[0].tile_begin) / csize) * kBM;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  // this CTA's share of layer l: hidden layers 64 columns at 64 rank; the output layer all N on rank 0
+  auto n_of = [&](int l) { return l < nlayer - 1 ? 64 : (rank == 0 ? P[l].N : 0); };
+  auto n0_of = [&](int l) { return l < nlayer - 1 ? 64 * (int)rank : 0; };
+  // bytes the peers deliver into this CTA's A buffer for layer l >= 1 (the
+  // output layer's input only to rank 0)
+  auto peer_bytes = [&](int l) {
+    return (l < nlayer - 1 || rank == 0) ? (uint32_t)(csize - 1) * S::kSlice : 0u;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -795,7 +812,8 @@ __global__ void __launch_bounds__(192, 1)
     }
     mbar_init(xfull, 1);
     mbar_init(accf, 1);
-    mbar_init(abuf, 4);
+    mbar_init(&aready[0], 1);
+    mbar_init(&aready[1], 1);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -803,7 +821,9 @@ __global__ void __launch_bounds__(192, 1)
     tmem_relinquish();
   }
   fence_before_sync();
-  __syncthreads();
+  // every CTA's barriers exist before any peer copies into it
+  if (csize > 1) cluster_sync();
+  else __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   pdl_wait();
@@ -811,20 +831,22 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 4) {
     if (lane == 0) {
-      // layer 0's A (nkA slices of 128 x 64), then every layer's weight slices
+      // layer 0's A (nkA slices of 128 x 64), then this CTA's weight boxes of every layer
       const int nkA0 = P[0].nkA;
       const CUtensorMap* tmA = &P[0].a;
       tmap_acquire(tmA);
       mbar_arrive_expect_tx(xfull, (uint32_t)nkA0 * 16384u);
       for (int ka = 0; ka < nkA0; ++ka)
-        for (int r = 0; r < 2; ++r) tma_load_2d(sA + ka * 16384 + r * 8192, tmA, xfull, ka * kBK, m0 + 64 * r);
+        for (int r = 0; r < 2; ++r) tma_load_2d(abuf(0) + ka * 16384 + r * 8192, tmA, xfull, ka * kBK, m0 + 64 * r);
       int it = 0;
       bool ok = true;
       for (int l = 0; l < nlayer && ok; ++l) {
+        const int nn = n_of(l);
+        if (nn == 0) continue;
         const CUtensorMap* tmB = &P[l].b;
         tmap_acquire(tmB);
         const int nk = (P[l].K + kBK - 1) / kBK;
-        const int nbox = (P[l].N + 63) / 64;
+        const int nbox = (nn + 63) / 64;
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
           if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1)) {
@@ -833,7 +855,8 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           mbar_arrive_expect_tx(&full[s], (uint32_t)nbox * 8192u);
-          for (int r = 0; r < nbox; ++r) tma_load_2d(sB + s * S::kBStage + r * 8192, tmB, &full[s], kb * kBK, 64 * r);
+          for (int r = 0; r < nbox; ++r)
+            tma_load_2d(sB + s * S::kBStage + r * 8192, tmB, &full[s], kb * kBK, n0_of(l) + 64 * r);
         }
       }
     }
@@ -843,15 +866,17 @@ __global__ void __launch_bounds__(192, 1)
       if (!ok) atomicOr(status, CRL_STATUS_TIMEOUT);
       int it = 0;
       for (int l = 0; l < nlayer && ok; ++l) {
-        // the epilogue of layer l - 1 has written its activations and read the accumulator
-        if (l > 0 && !mbar_wait(abuf, (l - 1) & 1)) {
+        const int nn = n_of(l);
+        if (nn == 0) break;
+        // layer l's A complete: this CTA's epilogue of layer l - 1 has written its
+        // slice (and read the accumulator), the peers' slices have landed
+        if (l > 0 && !mbar_wait(&aready[l & 1], ((l - 1) >> 1) & 1)) {
           atomicOr(status, CRL_STATUS_TIMEOUT);
           break;
         }
         fence_after_sync();
         const int nk = (P[l].K + kBK - 1) / kBK, nkA = P[l].nkA;
-        const int nmma = ((P[l].N + 63) / 64) * 64;
-        const uint32_t idesc = idesc_bf16_f32(kBM, nmma);
+        const uint32_t idesc = idesc_bf16_f32(kBM, ((nn + 63) / 64) * 64);
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
           if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
@@ -860,7 +885,7 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           fence_after_sync();
-          const uint64_t da = sdesc_kmajor_sw128(sA + (kb % nkA) * 16384);
+          const uint64_t da = sdesc_kmajor_sw128(abuf(l) + (kb % nkA) * 16384);
           const uint64_t db = sdesc_kmajor_sw128(sB + s * S::kBStage);
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k) mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
@@ -874,9 +899,12 @@ __global__ void __launch_bounds__(192, 1)
     const int row = m0 + warp * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     for (int l = 0; l < nlayer; ++l) {
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(accf, l & 1) ? 1 : 0) != 0;
+      const int nn = n_of(l);
+      if (nn == 0) break;
+      // one decision for the four epilogue warps (they meet at named barrier 1 below)
+      const bool ok = named_barrier_and(1, 128, mbar_wait(accf, l & 1));
       if (!ok) {
-        if (lane == 0) atomicOr(status, CRL_STATUS_TIMEOUT);
+        if (warp == 0 && lane == 0) atomicOr(status, CRL_STATUS_TIMEOUT);
         break;
       }
       fence_after_sync();
@@ -895,15 +923,17 @@ __global__ void __launch_bounds__(192, 1)
         }
         break;
       }
-      // hidden layer: bias + ReLU to h, h^T and the next layer's A in shared memory
+      // hidden layer: bias + ReLU of columns n0 .. n0 + 63 to h, h^T and slice `rank` of the next A
+      const int n0 = n0_of(l);
       bf16* h = static_cast<bf16*>(e.out0);
       bf16* hT = static_cast<bf16*>(e.out1);
+      uint8_t* as = abuf(l + 1) + rank * S::kSlice;
 #pragma unroll 1
-      for (int c = 0; c < N; c += 32) {
+      for (int c = 0; c < 64; c += 32) {
         float v[32];
         tmem_ld32(lane_base + c, v);
         float b[32];
-        load_bias32(e.bias + c, b);
+        load_bias32(e.bias + n0 + c, b);
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + b[i], 0.f);
         uint32_t w[16];
@@ -912,31 +942,41 @@ __global__ void __launch_bounds__(192, 1)
           const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
           w[i] = *reinterpret_cast<const uint32_t*>(&p2);
         }
-        // columns c .. c + 31: K slice c / 64, 16-byte chunks (c % 64) / 8 ..
-        uint8_t* as = sA + (c / 64) * 16384;
-        const int ch0 = (c % 64) / 8;
+        const int ch0 = c / 8;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           *reinterpret_cast<uint4*>(as + mlp_sw128_offset(warp * 32 + lane, ch0 + q)) =
               make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         if (row < M) {
-          uint4* hr = reinterpret_cast<uint4*>(h + (size_t)row * e.ld0 + c);
+          uint4* hr = reinterpret_cast<uint4*>(h + (size_t)row * e.ld0 + n0 + c);
 #pragma unroll
           for (int q = 0; q < 4; ++q) hr[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) hT[(size_t)(c + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
+          for (int i = 0; i < 32; ++i) hT[(size_t)(n0 + c + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
         }
       }
-      // the generic-proxy writes of A visible to the tensor core, the accumulator reads done
+      // the generic-proxy writes of the slice visible to the tensor core and to
+      // the bulk copies, the accumulator reads done; then one thread sends the
+      // slice to the peers (rank 0 only for the output layer's input) and arrives
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(abuf);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (warp == 0 && lane == 0) {
+        uint64_t* bar = &aready[(l + 1) & 1];
+        const bool last_hidden = l + 1 == nlayer - 1;
+        for (int p = 0; p < csize; ++p) {
+          if (p == (int)rank || (last_hidden && p != 0)) continue;
+          bulk_copy_to_peer(mapa_shared(as, (uint32_t)p), as, S::kSlice, mapa_shared(bar, (uint32_t)p));
+        }
+        mbar_arrive_expect_tx(bar, peer_bytes(l + 1));
+      }
     }
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 256);
+  // no CTA leaves while a peer's copy may still read from or write into it
+  if (csize > 1) cluster_sync();
 }
 
 }  // namespace tc

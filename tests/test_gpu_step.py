@@ -360,12 +360,17 @@ def test_persistent_gemm_matches_one_tile_gemm(path, kernel):
         np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
 
 
-@pytest.mark.parametrize("path,B", [("fused", 256), ("plain", 200), ("fused", 520)])
-def test_whole_network_forward_matches_per_layer_forward(path, B):
-    """The one-launch forward of narrow networks (activations on chip between
-    layers) and the per-layer launches give bit-identical update steps,
-    including the fused energy's operand epilogue and ragged row blocks."""
-    w = small(B=B, hidden=256, repr=64, E=8, T=200)
+@pytest.mark.parametrize("path,B,hidden,layers", [("fused", 256, 256, 2), ("plain", 200, 256, 2),
+                                                   ("fused", 520, 256, 2), ("fused", 136, 128, 2),
+                                                   ("fused", 96, 64, 2), ("fused", 200, 256, 3),
+                                                   ("plain", 72, 128, 4)])
+def test_whole_network_forward_matches_per_layer_forward(path, B, hidden, layers):
+    """The one-launch forward of narrow networks (a cluster of hidden / 64 CTAs
+    per row block exchanging each layer's activations through shared memory)
+    and the per-layer launches give bit-identical update steps, including the
+    fused energy's operand epilogue, ragged row blocks, clusters of 1, 2 and 4
+    CTAs and deeper networks (both activation buffers reused)."""
+    w = small(B=B, hidden=hidden, layers=layers, repr=64, E=8, T=200)
     runs = []
     for mode in ("layers", "whole"):
         prev = api.set_mlp_fusion(mode)
