@@ -1129,9 +1129,9 @@ struct AdamNetDev {
   ShadowLayer L[CRL_MAX_LAYERS + 1];
 };
 
-// One block of work for the Adam + shadow kernel: a 32 x 32 tile of a weight
+// One block of work for the Adam + shadow kernel: a 32 x 128 tile of a weight
 // matrix (layer >= 0: rows [r0, r0 + 32) of the output units, columns
-// [c0, c0 + 32) of the inputs), or a flat range of the parameter array
+// [c0, c0 + 128) of the inputs), or a flat range of the parameter array
 // (layer < 0: [r0, r0 + c0) -- biases, LayerNorm gains and shifts and the
 // zero padding between tensors, whose update is zero).
 struct AdamUnit {
@@ -1146,6 +1146,9 @@ struct AdamUnit {
 // Blocks [nunits, gridDim.x) run the actor head's forward (head_begin: each
 // task's first block, 8 rows per block) instead: it reads only the policy's
 // output, so it rides in the critic's Adam launch.
+// TW: the tile's columns (128 for large layers, 32 when the launch would
+// otherwise have too few blocks to hide memory latency).
+template <int TW>
 __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __restrict__ nets,
                                                           const AdamUnit* __restrict__ units, int nunits,
                                                           const HeadFwdArgs<float>* __restrict__ heads,
@@ -1161,19 +1164,21 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __re
   // block's lines into L2 while the predecessor (which writes g) drains
   const AdamUnit u = units[blockIdx.x];
   const AdamNetDev& a = nets[u.net];
-  if (threadIdx.x < 96) {
-    const float* arr = threadIdx.x < 32 ? a.p : (threadIdx.x < 64 ? a.m : a.v);
-    const int j = threadIdx.x % 32;
-    if (u.layer < 0) {
+  if (u.layer < 0) {
+    if (threadIdx.x < 96) {
+      const float* arr = threadIdx.x < 32 ? a.p : (threadIdx.x < 64 ? a.m : a.v);
+      const int j = threadIdx.x % 32;
       if (32 * j < u.c0) prefetch_l2(arr + u.r0 + 32 * j);
-    } else {
-      const ShadowLayer& L = a.L[u.layer];
-      const int o = u.r0 + j;
-      if (o < L.out) {
-        const float* row = arr + L.oW + (long long)o * L.in + u.c0;
-        prefetch_l2(row);
-        prefetch_l2(row + min(31, L.in - 1 - u.c0));
-      }
+    }
+  } else {
+    // 32 rows x TW columns: TW / 32 lines of 128 bytes per row and array
+    constexpr int kLines = TW / 32;
+    const ShadowLayer& L = a.L[u.layer];
+    for (int i = threadIdx.x; i < 3 * 32 * kLines; i += blockDim.x) {
+      const int arr_i = i / (32 * kLines), j = i % (32 * kLines);
+      const float* arr = arr_i == 0 ? a.p : (arr_i == 1 ? a.m : a.v);
+      const int o = u.r0 + j / kLines, c = u.c0 + 32 * (j % kLines);
+      if (o < L.out && c < L.in) prefetch_l2(arr + L.oW + (long long)o * L.in + c);
     }
   }
   pdl_enter();
@@ -1186,13 +1191,17 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __re
   const float t = (float)*a.t;
   const float c1 = a.lr / -expm1f(t * a.log_b1);
   const float c2 = 1.f / -expm1f(t * a.log_b2);
-  auto step = [&](long long i) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  // one element: moments and parameter from the gradient gi
+  auto upd = [=](float pi, float gi, float& mi, float& vi) {
+    mi = b1 * mi + (1.f - b1) * gi;
+    vi = b2 * vi + (1.f - b2) * gi * gi;
+    return pi - c1 * mi / (sqrtf(vi * c2) + eps);
+  };
+  auto step = [=](long long i) {
+    float mi = m[i], vi = v[i];
+    const float pi = upd(p[i], g[i], mi, vi);
     m[i] = mi;
     v[i] = vi;
-    const float pi = p[i] - c1 * mi / (sqrtf(vi * c2) + eps);
     p[i] = pi;
     return pi;
   };
@@ -1200,31 +1209,89 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __re
     for (int k = threadIdx.x; k < u.c0; k += blockDim.x) step((long long)u.r0 + k);
     return;
   }
-  __shared__ bf16 tile[32][34];
+  // weight tile rows [r0, r0 + 32) x columns [c0, c0 + TW): thread (rq, cq)
+  // takes columns 4 cq .. 4 cq + 3 of rows rq, rq + R, ... (R = 256 / (TW / 4)
+  // rows per pass; 16-byte accesses where the rows are 16-byte aligned); W_hi
+  // also goes to a transposed shared tile for the coalesced Wt rows
+  __shared__ bf16 tile[128][34];
   const ShadowLayer L = a.L[u.layer];
   bf16* __restrict__ W2 = L.W2;
-  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-    const int rr = e / 32, cc = e % 32;
-    const int o = u.r0 + rr, c = u.c0 + cc;
-    bf16 hi = __float2bfloat16_rn(0.f);
-    if (o < L.out && c < L.in) {
-      const float pv = step(L.oW + (long long)o * L.in + c);
-      hi = __float2bfloat16_rn(pv);
-      const bf16 lo = __float2bfloat16_rn(pv - __bfloat162float(hi));
-      bf16* d = W2 + (size_t)o * 2 * L.kp;
-      for (int q = 0; q < L.rep; ++q) {
-        d[L.rep * c + q] = hi;
-        d[L.kp + L.rep * c + q] = lo;
+  constexpr int kTpr = TW / 4, kRows = 256 / kTpr, kPasses = 32 / kRows;   // threads per row, rows per pass
+  const int cq = threadIdx.x % kTpr, rq = threadIdx.x / kTpr;
+  const int cc = 4 * cq, c = u.c0 + cc;
+  const bool vec = (L.in % 4) == 0 && c + 4 <= L.in;   // oW is a multiple of 64
+#pragma unroll
+  for (int k = 0; k < kPasses; ++k) {
+    const int rr = rq + kRows * k, o = u.r0 + rr;
+    float pv[4] = {0.f, 0.f, 0.f, 0.f};
+    bool live[4] = {false, false, false, false};
+    if (o < L.out) {
+      const long long i0 = L.oW + (long long)o * L.in + c;
+      if (vec) {
+        const float4 g4 = *reinterpret_cast<const float4*>(g + i0);
+        const float4 m4 = *reinterpret_cast<const float4*>(m + i0);
+        const float4 v4 = *reinterpret_cast<const float4*>(v + i0);
+        const float4 p4 = *reinterpret_cast<const float4*>(p + i0);
+        float mx = m4.x, my = m4.y, mz = m4.z, mw = m4.w, vx = v4.x, vy = v4.y, vz = v4.z, vw = v4.w;
+        pv[0] = upd(p4.x, g4.x, mx, vx);
+        pv[1] = upd(p4.y, g4.y, my, vy);
+        pv[2] = upd(p4.z, g4.z, mz, vz);
+        pv[3] = upd(p4.w, g4.w, mw, vw);
+        *reinterpret_cast<float4*>(m + i0) = make_float4(mx, my, mz, mw);
+        *reinterpret_cast<float4*>(v + i0) = make_float4(vx, vy, vz, vw);
+        *reinterpret_cast<float4*>(p + i0) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        live[0] = live[1] = live[2] = live[3] = true;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (c + j < L.in) {
+            pv[j] = step(i0 + j);
+            live[j] = true;
+          }
       }
     }
-    tile[cc][rr] = hi;
+    // W_hi / W_lo of the four columns (zero where the column lies outside the layer)
+    __nv_bfloat162 h01, h23, l01, l23;
+    {
+      const float x0 = live[0] ? pv[0] : 0.f, x1 = live[1] ? pv[1] : 0.f;
+      const float x2 = live[2] ? pv[2] : 0.f, x3 = live[3] ? pv[3] : 0.f;
+      h01 = __floats2bfloat162_rn(x0, x1);
+      h23 = __floats2bfloat162_rn(x2, x3);
+      l01 = __floats2bfloat162_rn(x0 - __low2float(h01), x1 - __high2float(h01));
+      l23 = __floats2bfloat162_rn(x2 - __low2float(h23), x3 - __high2float(h23));
+    }
+    tile[cc][rr] = __low2bfloat16(h01);
+    tile[cc + 1][rr] = __high2bfloat16(h01);
+    tile[cc + 2][rr] = __low2bfloat16(h23);
+    tile[cc + 3][rr] = __high2bfloat16(h23);
+    if (o < L.out) {
+      bf16* d = W2 + (size_t)o * 2 * L.kp;
+      if (vec && L.rep == 1) {
+        *reinterpret_cast<uint2*>(d + c) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+        *reinterpret_cast<uint2*>(d + L.kp + c) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (!live[j]) continue;
+          const __nv_bfloat162 hp = j < 2 ? h01 : h23, lp = j < 2 ? l01 : l23;
+          const bf16 hj = (j & 1) ? __high2bfloat16(hp) : __low2bfloat16(hp);
+          const bf16 lj = (j & 1) ? __high2bfloat16(lp) : __low2bfloat16(lp);
+          for (int q = 0; q < L.rep; ++q) {
+            d[L.rep * (c + j) + q] = hj;
+            d[L.kp + L.rep * (c + j) + q] = lj;
+          }
+        }
+      }
+    }
   }
   __syncthreads();
   bf16* __restrict__ Wt = L.Wt;
-  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-    const int cc = e / 32, rr = e % 32;
-    const int o = u.r0 + rr, c = u.c0 + cc;
-    if (o < L.out && c < L.in) Wt[(size_t)c * L.ldt + o] = tile[cc][rr];
+  for (int e = threadIdx.x; e < TW * 32; e += blockDim.x) {
+    const int ct = e / 32, rt = e % 32;
+    const int o = u.r0 + rt, col = u.c0 + ct;
+    if (o < L.out && col < L.in) Wt[(size_t)col * L.ldt + o] = tile[ct][rt];
   }
 }
 
@@ -1233,6 +1300,14 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __re
 const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int count, cudaStream_t st,
                                const std::vector<HeadFwdArgs<float>>* heads) {
   if (count <= 0) return nullptr;
+  // 32 x 128 weight tiles when there are at least two per SM, else 32 x 32
+  // (small networks: more blocks in flight hide the memory latency)
+  long long wide_tiles = 0;
+  for (int k = 0; k < count; ++k)
+    for (int l = 0; l <= nets[k].net->layers; ++l)
+      wide_tiles += (long long)ceil_div(nets[k].net->L[l].out, 32) * ceil_div(nets[k].net->L[l].in, 128);
+  const bool wide = wide_tiles >= 2LL * sm_count();
+  const int tw = wide ? 128 : 32;
   std::vector<AdamNetDev> devs(count);
   std::vector<AdamUnit> units;
   long long ntot = 0;
@@ -1266,7 +1341,7 @@ const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int 
       sl.W2 = L.W;
       sl.Wt = L.Wt;
       for (int r0 = 0; r0 < L.out; r0 += 32)
-        for (int c0 = 0; c0 < L.in; c0 += 32) units.push_back(AdamUnit{k, l, r0, c0});
+        for (int c0 = 0; c0 < L.in; c0 += tw) units.push_back(AdamUnit{k, l, r0, c0});
       // the layer's vectors (bias, LayerNorm gain and shift) and padding up to the next tensor
       const long long v0 = L.oW + (long long)round_up((int64_t)L.out * L.in, 64);
       const long long v1 = (l < s.net->layers) ? s.net->L[l + 1].oW : s.n;
@@ -1294,8 +1369,12 @@ const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int 
     if (!(dhb = cache.get(begin, st, &err))) return err;
   }
   TraceLaunch tr(CRL_TRACE_ADAM, st, 28.0 * ntot + head_bytes);
-  launch_k(adam_shadow_kernel, dim3((unsigned)(units.size() + head_blocks)), dim3(256), 0, st, dt, du,
-           (int)units.size(), dh, dhb, nh);
+  if (wide)
+    launch_k(adam_shadow_kernel<128>, dim3((unsigned)(units.size() + head_blocks)), dim3(256), 0, st, dt, du,
+             (int)units.size(), dh, dhb, nh);
+  else
+    launch_k(adam_shadow_kernel<32>, dim3((unsigned)(units.size() + head_blocks)), dim3(256), 0, st, dt, du,
+             (int)units.size(), dh, dhb, nh);
   return nullptr;
 }
 
