@@ -767,7 +767,7 @@ template <int OBJ>
 __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const BwdArgs& row,
                                          const BwdArgs& col, int nrow, int lb, bool global_maps) {
   const bool colpass = lb >= nrow;
-  const BwdArgs a = colpass ? col : row;
+  const BwdArgs& a = colpass ? col : row;   // fields read where used (no register copy)
   const CUtensorMap* tmOwn = colpass ? tmY : tmX;
   const CUtensorMap* tmOther = colpass ? tmX : tmY;
   extern __shared__ uint8_t smem_raw[];

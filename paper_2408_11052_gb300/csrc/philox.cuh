@@ -58,9 +58,9 @@ __device__ T philox_normal(unsigned long long step, int b, unsigned long long wo
                            unsigned long long agent) {
   constexpr double kTwoPi = 6.28318530717958647693;
   const Philox4 r = philox4x64_10(step, (unsigned long long)b, word, (unsigned long long)(d / 4), seed, agent);
-  const int pair = (d % 4) / 2;
-  const double u1 = u64_to_unit_open(r.w[2 * pair]);
-  const double u2 = u64_to_unit_open(r.w[2 * pair + 1]);
+  const bool pair = (d % 4) >= 2;   // words 0, 1 or 2, 3 (selected, not indexed: no local array)
+  const double u1 = u64_to_unit_open(pair ? r.w[2] : r.w[0]);
+  const double u2 = u64_to_unit_open(pair ? r.w[3] : r.w[1]);
   if constexpr (sizeof(T) == 8) {
     const double rad = sqrt(-2.0 * log(u1));
     double s, c;
