@@ -624,6 +624,14 @@ def main():
         peak = peaks["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": f"{peak_src} bf16_tflops_sustained (kernel timed inside a long step)", **common}
+        per_launch = tr_work / max(n_tr, 1)
+        # at the peak a launch's work takes per_launch / peak; when that is far
+        # below the launch's duration, the launch is latency-bound, not tensor-bound
+        roof["flop_per_launch"] = per_launch
+        roof["note"] = (f"{per_launch / 1e6:.1f} MFLOP per launch = {per_launch / (peak * 1e12) * 1e6:.2f} us at the "
+                        f"peak against {1e3 * tr_ms / max(n_tr, 1):.1f} us measured: "
+                        + ("latency-bound (pipeline fill, epilogue and launch latency dominate)"
+                           if per_launch / (peak * 1e12) < 0.2 * tr_ms / 1e3 / max(n_tr, 1) else "tensor-bound"))
     elif args.trace in ("gemm", "energy"):
         achieved = tr_work / (tr_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
