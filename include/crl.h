@@ -225,7 +225,11 @@ int crl_bind_params(crl_ctx* ctx, const crl_net_ptrs nets[3]);
 /* ---- replay buffer (Algorithm 1 "store trajectory"; App. B.3 capacity) -----
  * Append n time slices for all E environments at once:
  *   obs [n][E][D] float, act [n][E][A] float, done [n][E] uint8 (nonzero: that
- *   step's observation is the last of its episode).  Host or device pointers.
+ *   step's observation is the last of its episode).  Host or device pointers:
+ *   pinned (page-locked, mapped) host memory is read by the insert kernel in
+ *   place over the CPU-GPU link; pageable host memory is copied to a staging
+ *   buffer first.  Either way the call is asynchronous on `stream` and host
+ *   inputs must stay valid and unchanged until the stream has passed it.
  * The ring keeps the newest T steps per environment.  n >= 1. */
 int crl_buffer_insert(crl_ctx* ctx, const float* obs, const float* act, const uint8_t* done,
                       int32_t n, void* stream);

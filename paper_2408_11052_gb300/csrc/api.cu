@@ -31,6 +31,17 @@ namespace crl {
 
 thread_local std::string g_thread_error;
 
+// The device address of pinned, mapped host memory (a kernel may read it in
+// place), or nullptr for device, pageable or unknown memory.
+const void* host_device_alias(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 bool is_host_pointer(const void* p) {
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
@@ -436,7 +447,16 @@ void insert_impl(crl_ctx* c, const float* obs, const float* act, const uint8_t* 
   const size_t nobs = (size_t)n * cf.E * cf.D * sizeof(float);
   const size_t nact = (size_t)n * cf.E * cf.A * sizeof(float);
   const size_t ndone = (size_t)n * cf.E;
-  const bool h_obs = is_host_pointer(obs), h_act = is_host_pointer(act), h_done = is_host_pointer(done);
+  // pinned host inputs: the insert kernel reads them in place through their
+  // device alias (no copy); pageable host inputs: staged through device memory
+  const void* d_obs = is_host_pointer(obs) ? host_device_alias(obs) : nullptr;
+  const void* d_act = is_host_pointer(act) ? host_device_alias(act) : nullptr;
+  const void* d_done = is_host_pointer(done) ? host_device_alias(done) : nullptr;
+  const bool h_obs = is_host_pointer(obs) && !d_obs, h_act = is_host_pointer(act) && !d_act,
+             h_done = is_host_pointer(done) && !d_done;
+  if (d_obs) obs = static_cast<const float*>(d_obs);
+  if (d_act) act = static_cast<const float*>(d_act);
+  if (d_done) done = static_cast<const uint8_t*>(d_done);
   if (h_obs || h_act || h_done) {
     const size_t need = round_up(nobs, 256) + round_up(nact, 256) + round_up(ndone, 256);
     if (need > c->stage_bytes) {

@@ -369,10 +369,18 @@ int crl_sweep_update_step(crl_sweep* sw, const float* const* obs, const float* c
     }
     if (n_insert > 0) {
       CRL_REQUIRE(obs && act && done, CRL_E_INVALID_ARG, "obs, act and done must be non-null");
+      // device pointers, or the device aliases of pinned host inputs (read in place)
       bool device = true;
+      std::vector<const void*> in(3 * (size_t)na);
       for (int i = 0; i < na; ++i) {
         CRL_REQUIRE(obs[i] && act[i] && done[i], CRL_E_INVALID_ARG, "obs, act and done must be non-null");
-        device = device && !is_host_pointer(obs[i]) && !is_host_pointer(act[i]) && !is_host_pointer(done[i]);
+        const void* ptrs[3] = {obs[i], act[i], done[i]};
+        for (int j = 0; j < 3; ++j) {
+          const void* q = ptrs[j];
+          if (is_host_pointer(q)) q = host_device_alias(q);
+          device = device && q != nullptr;
+          in[3 * i + j] = q;
+        }
       }
       if (device && na <= kMaxAgents) {
         // one launch over every agent's buffer (arguments by value: they change every step)
@@ -384,7 +392,8 @@ int crl_sweep_update_step(crl_sweep* sw, const float* const* obs, const float* c
           CRL_REQUIRE(c->total_host + n_insert < ((int64_t)1 << 31) - 1, CRL_E_INVALID_ARG,
                       "more than 2^31 - 2 steps inserted per environment");
           const int i0 = n_insert > c->cfg.T ? n_insert - c->cfg.T : 0;
-          m.a[i] = InsertArgs{c->bd, obs[i], act[i], done[i], n_insert, i0, (long long)c->total_host};
+          m.a[i] = InsertArgs{c->bd, static_cast<const float*>(in[3 * i]), static_cast<const float*>(in[3 * i + 1]),
+                              static_cast<const uint8_t*>(in[3 * i + 2]), n_insert, i0, (long long)c->total_host};
           m.begin[i + 1] = m.begin[i] + insert_blocks(c->bd);
         }
         launch_buffer_insert_multi(m, st);

@@ -408,3 +408,32 @@ def test_l1_energy_runs_on_the_plain_path_only():
         cfg = api.make_config(w, precision=precision, path="plain")
         assert api.lib().crl_create(ctypes.byref(cfg), ctypes.byref(h)) == api.OK
         api.lib().crl_destroy(h)
+
+
+@pytest.mark.parametrize("precision,path", [("fp32", "plain"), ("bf16", "fused")])
+def test_pinned_host_inputs_equal_device_inputs(precision, path):
+    """Pinned host inputs (read in place by the insert kernel through their
+    device alias), pageable host inputs (staged) and device inputs give the same
+    losses and parameters."""
+    w = small(B=64, repr=64)
+    extra = workload.buffer_contents(w, n=3, mean_len=9.0, seed_offset=7)
+    runs = []
+    for kind in ("device", "pinned", "pageable"):
+        ctx, _, _ = setup(w, precision=precision, path=path, n=60)
+        loss = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+        hist = []
+        for i in range(3):
+            xs = [torch.from_numpy(np.ascontiguousarray(x[i:i + 1])) for x in extra]
+            if kind == "device":
+                xs = [x.to(ctx.device) for x in xs]
+            elif kind == "pinned":
+                xs = [x.pin_memory() for x in xs]
+            ctx.update_step(*xs, loss_out=loss)
+            torch.cuda.synchronize()
+            hist.append(loss.cpu().numpy().copy())
+        assert ctx.sync_status() == (0, 0)
+        runs.append((np.array(hist), {n: ctx.store[n]["params"].cpu().numpy() for n in ("phi", "psi", "pi")}))
+    for other in runs[1:]:
+        np.testing.assert_array_equal(runs[0][0], other[0])
+        for n in ("phi", "psi", "pi"):
+            np.testing.assert_array_equal(runs[0][1][n], other[1][n])

@@ -25,7 +25,7 @@ def fill(ctx, w, n, seed_offset):
     ctx.insert(*(torch.from_numpy(x).to(ctx.device) for x in (obs, act, done)))
 
 
-def run_and_compare(ws, precision, path, grouped, steps=4, check=None):
+def run_and_compare(ws, precision, path, grouped, steps=4, check=None, pinned=False):
     sw = api.CRLSweep(ws, precision, path, grouped=grouped)
     check = range(len(ws)) if check is None else check
     singles = {i: api.CRLContext(ws[i], precision, path, agent=i) for i in check}
@@ -46,7 +46,8 @@ def run_and_compare(ws, precision, path, grouped, steps=4, check=None):
     hist_sw, hist_1 = [], {i: [] for i in singles}
     with torch.cuda.stream(stream):
         for t in range(steps):
-            ins = [[torch.from_numpy(x[t:t + 1]).cuda() for x in extra[i]] for i in range(len(ws))]
+            ins = [[torch.from_numpy(np.ascontiguousarray(x[t:t + 1])).pin_memory() if pinned
+                    else torch.from_numpy(x[t:t + 1]).cuda() for x in extra[i]] for i in range(len(ws))]
             sw.update_step([a[0] for a in ins], [a[1] for a in ins], [a[2] for a in ins], loss_out=loss_sw)
             hist_sw.append(loss_sw.cpu().numpy().copy())
         for i, ctx in singles.items():
@@ -72,6 +73,11 @@ def run_and_compare(ws, precision, path, grouped, steps=4, check=None):
 
 def test_grouped_sweep_matches_single_agents():
     run_and_compare(uneven_agents(), "bf16", "fused", grouped=True)
+
+
+def test_grouped_sweep_with_pinned_host_inputs_matches_single_agents():
+    """Pinned host inputs of every agent, read in place by the grouped insert."""
+    run_and_compare(uneven_agents(), "bf16", "fused", grouped=True, steps=3, pinned=True)
 
 
 def test_sequential_sweep_matches_single_agents_fp32():
