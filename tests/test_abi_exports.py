@@ -111,3 +111,27 @@ def test_config_validation_of_objectives_without_gpu(lib):
                       (api.make_config(w.with_(B=1, loss="fb")), api.E_INVALID_ARG)):
         assert lib.crl_create(ctypes.byref(cfg), ctypes.byref(h)) == code
         assert h.value is None
+
+
+def header_defines():
+    text = open(HEADER).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(CRL_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text)}
+
+
+@pytest.mark.parametrize("table,prefix", [("ENERGY", "ENERGY"), ("LOSS", "LOSS"), ("PREC", "PREC"), ("PATH", "PATH"),
+                                          ("NET", "NET"), ("TRACE", "TRACE"), ("GEMM_KERNEL", "GEMM"),
+                                          ("MLP_FUSION", "MLP")])
+def test_binding_constants_match_the_header(table, prefix):
+    """Every name of the binding's table is the header's CRL_<prefix>_<NAME>, with its value."""
+    defines = header_defines()
+    for name, value in getattr(api, table).items():
+        key = f"CRL_{prefix}_{name.upper()}"
+        assert key in defines, key
+        assert defines[key] == value, (key, defines[key], value)
+
+
+def test_error_codes_match_the_header():
+    defines = header_defines()
+    for name in ("INVALID_ARG", "SHAPE", "BUFFER_EMPTY", "CUDA", "NONFINITE", "TIMEOUT", "NOT_BOUND", "UNSUPPORTED"):
+        assert defines[f"CRL_E_{name}"] == getattr(api, f"E_{name}"), name
+    assert defines["CRL_OK"] == api.OK
