@@ -562,7 +562,7 @@ def main():
     ap.add_argument("--alpha-autotune", action="store_true", help="learn the entropy coefficient")
     ap.add_argument("--mlp-fusion", default="auto", choices=["auto", "layers", "whole"],
                     help="BF16 network forward: grouped per-layer launches or one whole-network kernel")
-    ap.add_argument("--gemm-kernel", default="any", choices=["any", "one_tile", "persistent", "pair"],
+    ap.add_argument("--gemm-kernel", default="any", choices=["any", "one_tile", "persistent"],
                     help="BF16 GEMM kernel family the autotuner may pick from")
     ap.add_argument("--oracle-rate", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -438,16 +438,13 @@ int32_t crl_set_autotune(int32_t enable);
  * library extension): CRL_GEMM_ANY (the default; the autotuner picks among
  * the one-tile and persistent kernels), CRL_GEMM_ONE_TILE (one CTA per output tile), CRL_GEMM_PERSISTENT (one
  * CTA per SM walking the tiles, its epilogue overlapping the next tile's
- * main loop through a double-buffered TMEM accumulator), CRL_GEMM_PAIR
- * (clusters of two CTAs on vertically adjacent tiles, each loading half of
- * the shared weight-side tile and multicasting it to both).  All kernels give
+ * main loop through a double-buffered TMEM accumulator).  All kernels give
  * identical outputs.  Without autotuning the fixed rule picks the tile width
  * and this setting the kernel (ANY: one tile per CTA).  Returns the previous
  * setting, or CRL_E_INVALID_ARG for an unknown mode. */
 #define CRL_GEMM_ANY 0
 #define CRL_GEMM_ONE_TILE 1
 #define CRL_GEMM_PERSISTENT 2
-#define CRL_GEMM_PAIR 3
 int32_t crl_set_gemm_kernel(int32_t mode);
 
 /* How the BF16 path runs a network's forward pass (process-wide; library

@@ -177,7 +177,7 @@ def set_autotune(enable):
     return bool(lib().crl_set_autotune(1 if enable else 0))
 
 
-GEMM_KERNEL = {"any": 0, "one_tile": 1, "persistent": 2, "pair": 3}
+GEMM_KERNEL = {"any": 0, "one_tile": 1, "persistent": 2}
 
 
 def set_gemm_kernel(mode):

@@ -567,41 +567,22 @@ void launch_gemm_persistent(const tc::GemmProblem* table, int nprob, int tiles, 
            status);
 }
 
-template <int BN, int STAGES>
-void launch_gemm_pair(const tc::GemmProblem* table, int nprob, int tiles, unsigned* status, cudaStream_t st) {
-  using S = tc::GemmSmem<BN, STAGES>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc::tc_gemm_pair_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
-    attr = true;
-  }
-  launch_k_cluster(tc::tc_gemm_pair_kernel<BN, STAGES>, dim3(tiles), dim3(128), S::kBytes, st, 2u, table, nprob,
-                   status);
-}
-
 // A GEMM configuration: tile width, ring depth and kernel (0: one tile per CTA,
-// 1: persistent, 2: cluster pairs sharing B), coded as 8192 * kernel + 16 * BN + stages.
+// 1: persistent), coded as 8192 * kernel + 16 * BN + stages.
 constexpr int gemm_cfg(int bn, int stages, int kernel = 0) { return 8192 * kernel + 16 * bn + stages; }
 constexpr int cfg_bn(int cfg) { return (cfg % 8192) / 16; }
 constexpr int cfg_kernel(int cfg) { return cfg / 8192; }
-// ANY tunes over the one-tile and persistent kernels: the cluster pairs measured
-// slower on every workload here (their halved weight-side traffic is not what
-// bounds these GEMMs), so they run only when asked for.
+// ANY tunes over the one-tile and persistent kernels.
 bool cfg_allowed(int cfg) {
   if (g_gemm_kernel == CRL_GEMM_ONE_TILE) return cfg_kernel(cfg) == 0;
   if (g_gemm_kernel == CRL_GEMM_PERSISTENT) return cfg_kernel(cfg) == 1;
-  if (g_gemm_kernel == CRL_GEMM_PAIR) return cfg_kernel(cfg) == 2;
-  return cfg_kernel(cfg) != 2;
+  return true;
 }
-constexpr int kGemmCfgs[11] = {gemm_cfg(64, 4),     gemm_cfg(64, 8),     gemm_cfg(128, 3),    gemm_cfg(128, 6),
-                               gemm_cfg(256, 4),    gemm_cfg(64, 8, 1),  gemm_cfg(128, 6, 1), gemm_cfg(256, 4, 1),
-                               gemm_cfg(128, 4, 2), gemm_cfg(128, 6, 2), gemm_cfg(256, 4, 2)};
+constexpr int kGemmCfgs[8] = {gemm_cfg(64, 4),    gemm_cfg(64, 8),     gemm_cfg(128, 3),    gemm_cfg(128, 6),
+                              gemm_cfg(256, 4),   gemm_cfg(64, 8, 1),  gemm_cfg(128, 6, 1), gemm_cfg(256, 4, 1)};
 
 void launch_cfg(int cfg, const tc::GemmProblem* t, int nprob, int tiles, unsigned* status, cudaStream_t st) {
   switch (cfg) {
-    case gemm_cfg(128, 4, 2): launch_gemm_pair<128, 4>(t, nprob, tiles, status, st); break;
-    case gemm_cfg(128, 6, 2): launch_gemm_pair<128, 6>(t, nprob, tiles, status, st); break;
-    case gemm_cfg(256, 4, 2): launch_gemm_pair<256, 4>(t, nprob, tiles, status, st); break;
     case gemm_cfg(64, 8, 1): launch_gemm_persistent<64, 8>(t, nprob, tiles, status, st); break;
     case gemm_cfg(128, 6, 1): launch_gemm_persistent<128, 6>(t, nprob, tiles, status, st); break;
     case gemm_cfg(256, 4, 1): launch_gemm_persistent<256, 4>(t, nprob, tiles, status, st); break;
@@ -622,7 +603,6 @@ int heuristic_cfg(const std::vector<tc::GemmProblem>& probs, int min_bn) {
   const int bn = std::max(ctas128 >= 148 ? 128 : 64, min_bn <= 64 ? 64 : (min_bn <= 128 ? 128 : 256));
   if (g_gemm_kernel == CRL_GEMM_PERSISTENT)
     return bn == 256 ? gemm_cfg(256, 4, 1) : (bn == 128 ? gemm_cfg(128, 6, 1) : gemm_cfg(64, 8, 1));
-  if (g_gemm_kernel == CRL_GEMM_PAIR) return bn == 256 ? gemm_cfg(256, 4, 2) : gemm_cfg(128, 4, 2);
   return bn == 256 ? gemm_cfg(256, 4) : (bn == 128 ? gemm_cfg(128, 4) : gemm_cfg(64, 4));
 }
 
@@ -646,7 +626,7 @@ int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, un
     if (!cfg_allowed(cfg)) continue;
     int tiles = 0;
     const char* err = nullptr;
-    const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 2);
+    const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err);
     if (!t || tiles == 0) continue;
     launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);  // warm-up
     cudaEventRecord(e0, st);
@@ -688,7 +668,7 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
   }
   int tiles = 0;
   const char* err = nullptr;
-  const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 2);
+  const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err);
   if (!t) return err;
   if (tiles == 0) return nullptr;
   TraceLaunch tr(CRL_TRACE_GEMM, st, flops);
@@ -699,14 +679,13 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
 }  // namespace
 
 const tc::GemmProblem* GemmGroups::table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles,
-                                         cudaStream_t st, const char** err, bool pairs) {
+                                         cudaStream_t st, const char** err) {
   int tiles = 0;
   for (auto& p : probs) {
     if (BN == 0) break;
     p.tiles_n = ceil_div(p.N, BN);
     p.tile_begin = tiles;
-    const int tm = ceil_div(p.M, tc::kBM);
-    tiles += (pairs ? 2 * ceil_div(tm, 2) : tm) * p.tiles_n;
+    tiles += ceil_div(p.M, tc::kBM) * p.tiles_n;
   }
   *total_tiles = tiles;
   const size_t bytes = probs.size() * sizeof(tc::GemmProblem);

@@ -97,10 +97,9 @@ class GemmGroups {
   ~GemmGroups() { reset(); }
   // Fills tiles_n / tile_begin of `probs` for tile width BN and returns the
   // device table; nullptr (and *err) on failure.
-  // pairs: each problem's m-tiles padded to an even count (cluster-pair kernel).
   // BN = 0: the problems are uploaded as given (tiles_n / tile_begin untouched).
   const tc::GemmProblem* table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles, cudaStream_t st,
-                               const char** err, bool pairs = false);
+                               const char** err);
   // Frees every table (synchronises the device) and forgets the tuned tile widths.
   void reset();
   // Autotuned configuration (16 x tile width + ring depth) of a problem list,

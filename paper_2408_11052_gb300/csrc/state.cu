@@ -12,6 +12,7 @@
 // used) its states [E][D], goals [E][G], steps [E] and counter.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <cstring>
 
 #include "ctx.h"
@@ -100,13 +101,23 @@ int crl_load_state(crl_ctx* ctx, const void* host, size_t bytes) {
     CRL_REQUIRE(h.magic == kStateMagic && h.version == 1, CRL_E_INVALID_ARG, "not a state blob of this library");
     CRL_REQUIRE(h.E == cf.E && h.T == cf.T && h.W == ctx->bd.W && h.D == cf.D && h.A == cf.A && h.G == cf.G,
                 CRL_E_SHAPE, "the state blob was saved from a context of other sizes");
-    CRL_REQUIRE(h.size_host >= 0 && h.size_host <= cf.T && h.total_host >= h.size_host, CRL_E_INVALID_ARG,
-                "corrupt buffer fill in the state blob");
+    // the fill is min(total, T) and the device keeps total as int32 (the insert kernel's counter)
+    CRL_REQUIRE(h.total_host >= 0 && h.total_host <= INT32_MAX &&
+                    h.size_host == (h.total_host < cf.T ? h.total_host : (int64_t)cf.T),
+                CRL_E_INVALID_ARG, "corrupt buffer fill in the state blob");
     const bool env = h.env_ready != 0;
     const size_t E = (size_t)cf.E;
     size_t need = sizeof(StateHeader) + sizeof(Counters) + E * 4 + 8 + E * cf.T * (size_t)ctx->bd.W * 4;
     if (env) need += E * cf.D * 4 + E * cf.G * 4 + E * 4 + 8;
     CRL_REQUIRE(bytes >= need, CRL_E_SHAPE, "state blob truncated");
+    {
+      // the device copy of {size, total} must be the header's: the sampler turns
+      // it into ring-row addresses without further checks
+      int32_t dev_fill[2];
+      memcpy(dev_fill, static_cast<const char*>(host) + sizeof(h) + sizeof(Counters) + E * 4, sizeof(dev_fill));
+      CRL_REQUIRE(dev_fill[0] == (int32_t)h.size_host && dev_fill[1] == (int32_t)h.total_host, CRL_E_INVALID_ARG,
+                  "corrupt buffer fill in the state blob");
+    }
     if (env && !ctx->env.ready)  // the environments are allocated the way crl_collect's first call does
       CRL_REQUIRE(ctx->bound, CRL_E_NOT_BOUND, "bind the parameters before loading a state with environments");
     CRL_CHECK_CUDA(cudaDeviceSynchronize());

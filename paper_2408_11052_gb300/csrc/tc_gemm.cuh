@@ -602,135 +602,6 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) tmem_dealloc(tmem, 2 * BN);
 }
 
-// Cluster-pair variant: the two CTAs of a cluster compute the vertically
-// adjacent tiles (m-tiles 2i and 2i + 1, one n-tile) of one problem and share
-// the weight-side operand: each loads its own A tile and half of the BN rows
-// of B, multicast into both CTAs' rings, so each SM reads 128 + BN / 2 operand
-// rows per K slice instead of 128 + BN.  A stage is refilled only when both
-// CTAs' MMAs are done with it (empty barriers count two arrivals; every MMA
-// commit arrives on both CTAs).  The problem table pads each problem's m-tiles
-// to an even count (an out-of-range second tile loads zeros, still delivers
-// its half of B, and stores nothing).  Same epilogues and accumulation order as
-// the one-tile kernel, so the outputs are identical.  BN in {128, 256}.
-template <int BN, int STAGES>
-__global__ void __launch_bounds__(128, 1)
-    tc_gemm_pair_kernel(const GemmProblem* __restrict__ probs, int nprob, unsigned* status) {
-  static_assert(BN >= 128, "each CTA loads at least one 64-row box of B");
-  using S = GemmSmem<BN, STAGES>;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = align1024(smem_raw);
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + S::kStages * S::kABytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::kStages * S::kStageBytes);
-  uint64_t* empty = full + S::kStages;
-  uint64_t* done = empty + S::kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  constexpr uint16_t kPair = 0x3;
-
-  const int t = blockIdx.x;
-  const uint32_t rank = cluster_ctarank();
-  const GemmProblem* P = find_problem(probs, nprob, t);
-  const int pair = (t - P->tile_begin) >> 1;
-  const int M = P->M, N = P->N, K = P->K, nkA = P->nkA;
-  const int m0 = (2 * (pair / P->tiles_n) + (int)rank) * kBM, n0 = (pair % P->tiles_n) * BN;
-  const CUtensorMap* tmA = &P->a;
-  const CUtensorMap* tmB = &P->b;
-
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int nk = (K + kBK - 1) / kBK;
-
-  if (threadIdx.x == 0) {
-    tmap_acquire(tmA);
-    tmap_acquire(tmB);
-    prefetch_tmap(tmA);
-    prefetch_tmap(tmB);
-    for (int s = 0; s < S::kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 2);
-    }
-    mbar_init(done, 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) {
-    tmem_alloc(tmem_slot, S::kTmemCols);
-    tmem_relinquish();
-  }
-  fence_before_sync();
-  // both CTAs' barriers exist before either multicasts into the other
-  cluster_sync();
-  fence_after_sync();
-  const uint32_t tmem = *tmem_slot;
-  pdl_wait();
-  pdl_trigger();
-
-  if (warp == 0 && lane == 0) {
-    // TMA producer: own A tile, and this CTA's half of the B tile to both CTAs
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % S::kStages;
-      if (kb >= S::kStages && !mbar_wait(&empty[s], ((kb / S::kStages) & 1) ^ 1)) {
-        atomicOr(status, CRL_STATUS_TIMEOUT);
-        break;
-      }
-      mbar_arrive_expect_tx(&full[s], S::kStageBytes);
-      const int ka = nkA > 0 ? kb % nkA : kb;
-#pragma unroll
-      for (int r = 0; r < kBM / 64; ++r)
-        tma_load_2d(sA + s * S::kABytes + r * 8192, tmA, &full[s], ka * kBK, m0 + 64 * r);
-#pragma unroll
-      for (int r = 0; r < BN / 128; ++r) {
-        const int box = (int)rank * (BN / 128) + r;
-        tma_load_2d_mc(sB + s * S::kBBytes + box * 8192, tmB, &full[s], kb * kBK, n0 + 64 * box, kPair);
-      }
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer; each slice's completion frees the stage in both CTAs
-    constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
-    bool ok = true;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % S::kStages;
-      if (!mbar_wait(&full[s], (kb / S::kStages) & 1)) {
-        atomicOr(status, CRL_STATUS_TIMEOUT);
-        ok = false;
-        break;
-      }
-      fence_after_sync();
-      const uint64_t da = sdesc_kmajor_sw128(sA + s * S::kABytes);
-      const uint64_t db = sdesc_kmajor_sw128(sB + s * S::kBBytes);
-#pragma unroll
-      for (int k = 0; k < kBK / 16; ++k) mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-      mma_commit_mc(&empty[s], kPair);
-    }
-    if (ok) mma_commit(done);
-  }
-  __syncwarp();
-
-  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0) ? 1 : 0) != 0;
-  fence_after_sync();
-  if (ok) {
-    const EpiDesc e = P->epi;
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    const int ncol = (N - n0 < BN) ? N - n0 : BN;
-    if (e.kind == kEpiFwdOutEnergy) {
-      epilogue_energy(e, row, lane_base, ncol, M);
-    } else {
-#pragma unroll 1
-      for (int c = 0; c < ncol; c += 32) {
-        float v[32];
-        tmem_ld32(lane_base + c, v);
-        epilogue_chunk(e, row, n0 + c, v, M, N);
-      }
-    }
-  } else if (threadIdx.x == 0) {
-    atomicOr(status, CRL_STATUS_TIMEOUT);
-  }
-  fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, S::kTmemCols);
-  // neither CTA leaves while the other may still deliver into its shared memory
-  cluster_sync();
-}
-
 // ---- whole-network forward for narrow networks ------------------------------------
 // A cluster of C = H / 64 CTAs per (network, 128-row block) runs every layer of
 // the network's forward in one launch.  In a hidden layer, CTA rank r computes

@@ -116,3 +116,28 @@ def test_load_rejects_foreign_corrupt_and_truncated_blobs():
     with pytest.raises(api.CRLError) as e:
         ctx.load_state(bytes(corrupt))
     assert e.value.code == api.E_INVALID_ARG
+
+
+def test_load_rejects_a_device_fill_that_disagrees_with_the_header():
+    """The blob's copy of the device fill {size, total} feeds the sampler's ring-row
+    addresses unchecked, so a blob whose copy disagrees with its validated header
+    (here total < size, which would address rows before the ring) is refused, and
+    so is a header whose fill is not min(total, T)."""
+    w = small(E=4, T=20, B=16)
+    ctx = api.CRLContext(w)
+    blob = ctx.save_state()
+    # header: magic (8 B), 8 int32, size_host, total_host (int64) = 56 B; counters 64 B;
+    # episode starts E int32; then the device fill {size, total} (int32)
+    off = 56 + 64 + 4 * w.E
+    assert struct.unpack_from("<ii", blob, off) == (0, 0)
+    corrupt = bytearray(blob)
+    struct.pack_into("<ii", corrupt, off, w.T, 3)
+    with pytest.raises(api.CRLError) as e:
+        ctx.load_state(bytes(corrupt))
+    assert e.value.code == api.E_INVALID_ARG
+    corrupt = bytearray(blob)
+    struct.pack_into("<qq", corrupt, 8 + 8 * 4, w.T, w.T - 1)
+    with pytest.raises(api.CRLError) as e:
+        ctx.load_state(bytes(corrupt))
+    assert e.value.code == api.E_INVALID_ARG
+    ctx.load_state(blob)
