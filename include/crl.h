@@ -507,9 +507,10 @@ int crl_infonce_backward(const crl_loss_desc* d, const void* phi, const void* ps
 
 /* Allocation-free variant of crl_infonce_forward (the paper has no
  * counterpart; this is a library service).  For callers that must not
- * allocate device memory when they evaluate the loss -- e.g. code running
- * while another framework captures a CUDA graph, a host that fixes its device
- * memory at start-up, or a plugin inside a runtime that owns the allocator.
+ * allocate device memory when they evaluate the loss -- e.g. a host that
+ * fixes its device memory at start-up and forbids allocation afterwards
+ * (cudaMalloc can stall on a device-wide synchronisation and fragments
+ * memory), or a plugin inside a runtime that owns the device allocator.
  * Same arguments and results as crl_infonce_forward, minus the workspace: the
  * scratch is a fixed 4 MiB array inside the library, held on every GPU that
  * loads it until the process exits; sizes whose scratch would exceed it
@@ -518,8 +519,11 @@ int crl_infonce_backward(const crl_loss_desc* d, const void* phi, const void* ps
  * The first call on each device does a one-time set-up (looks up the array's
  * device address); make that first call before any stream capture.  Every
  * call shares the one array: calls whose work may overlap on the GPU (other
- * streams or threads without ordering) race and give wrong results.
- * dtype CRL_PREC_FP32 / CRL_PREC_FP64, path CRL_PATH_PLAIN. */
+ * streams or threads without ordering) race and give wrong results.  The
+ * array's device address is cached per device: do not call this on a device
+ * after cudaDeviceReset.  Descriptor checks and error codes are those of
+ * crl_infonce_forward; dtype CRL_PREC_FP32 / CRL_PREC_FP64, path
+ * CRL_PATH_PLAIN (else CRL_E_UNSUPPORTED). */
 int crl_infonce_forward_noalloc(const crl_loss_desc* d, const void* phi, const void* psi, int32_t B, int32_t R,
                                 void* loss4, void* row_lse, void* col_lse, void* stream);
 

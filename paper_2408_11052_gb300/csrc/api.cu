@@ -1081,7 +1081,9 @@ int crl_mlp_backward(const crl_mlp_desc* d, const void* params, const float* x0,
   });
 }
 
-namespace {
+}  // extern "C"
+
+namespace crl {
 LossSpec checked_loss(const crl_loss_desc* d) {
   CRL_REQUIRE(d, CRL_E_INVALID_ARG, "null descriptor");
   CRL_REQUIRE(d->energy >= CRL_ENERGY_L2 && d->energy <= CRL_ENERGY_L2SQ, CRL_E_INVALID_ARG, "unknown energy");
@@ -1103,7 +1105,9 @@ LossSpec checked_loss(const crl_loss_desc* d) {
   ls.beta = d->beta_lse;
   return ls;
 }
-}  // namespace
+}  // namespace crl
+
+extern "C" {
 
 int crl_infonce_workspace_bytes(const crl_loss_desc* d, int32_t B, int32_t R, size_t* bytes) {
   return guarded(nullptr, [&] {

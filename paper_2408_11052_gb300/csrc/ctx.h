@@ -178,6 +178,11 @@ void logit_stats_launch(crl_ctx* c, const void* phi, const void* psi, int B, boo
 // Allocates and resets the collection stub's environments (crl_collect's first call).
 void collect_alloc(crl_ctx* ctx, cudaStream_t st);
 
+// The loss of a crl_loss_desc after validation (throws Failure: CRL_E_INVALID_ARG
+// for an unknown energy, objective, reduction or penalty axis, or a bad
+// temperature / beta; CRL_E_UNSUPPORTED for a dtype / path this build lacks).
+LossSpec checked_loss(const crl_loss_desc* d);
+
 // Runs one entry point: maps internal failures to status codes and makes the
 // context's tracer visible to the launch sites for the duration of the call.
 template <typename F>

@@ -2,12 +2,13 @@
 // workspace and without any device allocation.
 //
 // Who needs this: code that must not allocate device memory at the moment it
-// evaluates the loss.  Examples are a call made while another framework is
-// capturing a CUDA graph (cudaMalloc cannot be captured and breaks the
-// capture), a host that fixes its device memory budget at start-up and
-// forbids allocation afterwards (long-running or real-time loops), and a
-// plugin running inside a runtime that owns the device allocator.  Those
-// callers still pass their inputs and outputs; the scratch lives here.
+// evaluates the loss.  Examples are a host that fixes its device memory
+// budget at start-up and forbids allocation afterwards (long-running or
+// real-time loops, where cudaMalloc can stall on a device-wide
+// synchronisation and fragments memory), and a plugin running inside a
+// runtime that owns the device allocator (its pools and accounting would not
+// see a cudaMalloc of ours).  Those callers still pass their inputs and
+// outputs; the scratch lives here.
 //
 // The scratch is one fixed array in the library's device memory,
 // kNoAllocScratchBytes long.  Every GPU that loads the library holds it until
@@ -18,12 +19,16 @@
 //
 // Host code cannot use the array's name as a device address (in host code it
 // is a host-side stand-in), so the address is looked up with
-// cudaGetSymbolAddress once per device, on that device's first call.
+// cudaGetSymbolAddress once per device, on that device's first call, and
+// cached.  cudaDeviceReset destroys the array with the context; the cached
+// address is then stale, so this entry point must not be used on a device
+// after it has been reset.
 #include <cuda_runtime.h>
 
 #include <mutex>
 #include <string>
 
+#include "ctx.h"
 #include "internal.h"
 
 namespace {
@@ -66,56 +71,32 @@ int scratch_address(void** out, std::string* err) {
 
 extern "C" int crl_infonce_forward_noalloc(const crl_loss_desc* d, const void* phi, const void* psi, int32_t B,
                                            int32_t R, void* loss4, void* row_lse, void* col_lse, void* stream) {
-  std::string err;
-  if (!d || !phi || !psi || !loss4 || !row_lse || !col_lse || B < 1 || R < 1) {
-    crl::set_thread_error("crl_infonce_forward_noalloc: null pointer or non-positive size");
-    return CRL_E_INVALID_ARG;
-  }
-  if (d->energy < CRL_ENERGY_L2 || d->energy > CRL_ENERGY_L2SQ || d->loss < CRL_LOSS_FWD ||
-      d->loss > CRL_LOSS_NCE_BINARY || (d->loss == CRL_LOSS_FB && B < 2) || (d->sym_reduction != CRL_SYM_MEAN && d->sym_reduction != CRL_SYM_SUM) ||
-      d->penalty_axis < CRL_PENALTY_ROW || d->penalty_axis > CRL_PENALTY_BOTH || !(d->temperature > 0.f) ||
-      d->beta_lse < 0.f) {
-    crl::set_thread_error("crl_infonce_forward_noalloc: bad loss descriptor");
-    return CRL_E_INVALID_ARG;
-  }
-  if ((d->dtype != CRL_PREC_FP32 && d->dtype != CRL_PREC_FP64) || d->path != CRL_PATH_PLAIN) {
-    crl::set_thread_error("crl_infonce_forward_noalloc: dtype must be FP32 or FP64 and path PLAIN");
-    return CRL_E_UNSUPPORTED;
-  }
-  crl::LossSpec ls;
-  ls.energy = d->energy;
-  ls.loss = d->loss;
-  ls.sym_reduction = d->sym_reduction;
-  ls.penalty_axis = d->penalty_axis;
-  ls.tau = d->temperature;
-  ls.beta = d->beta_lse;
-  const size_t elem = d->dtype == CRL_PREC_FP64 ? sizeof(double) : sizeof(float);
-  const size_t need = crl::infonce_ws_bytes(ls, B, R, elem, d->path);
-  if (need > kNoAllocScratchBytes) {
-    crl::set_thread_error("crl_infonce_forward_noalloc: batch " + std::to_string(B) + " x repr " +
-                          std::to_string(R) + " needs " + std::to_string(need) +
-                          " bytes of scratch, above the fixed 4 MiB (4194304 bytes) of this entry point");
-    return CRL_E_SHAPE;
-  }
-  void* ws = nullptr;
-  const int rc = scratch_address(&ws, &err);
-  if (rc != CRL_OK) {
-    crl::set_thread_error("crl_infonce_forward_noalloc: " + err);
-    return rc;
-  }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (d->dtype == CRL_PREC_FP64)
-    crl::infonce_forward<double>(ls, static_cast<const double*>(phi), static_cast<const double*>(psi), B, R,
-                                 static_cast<double*>(loss4), static_cast<double*>(row_lse),
-                                 static_cast<double*>(col_lse), ws, d->path, nullptr, nullptr, st);
-  else
-    crl::infonce_forward<float>(ls, static_cast<const float*>(phi), static_cast<const float*>(psi), B, R,
-                                static_cast<float*>(loss4), static_cast<float*>(row_lse), static_cast<float*>(col_lse),
-                                ws, d->path, nullptr, nullptr, st);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    crl::set_thread_error(std::string("crl_infonce_forward_noalloc: ") + cudaGetErrorString(e));
-    return CRL_E_CUDA;
-  }
-  return CRL_OK;
+  using namespace crl;
+  return guarded(nullptr, [&] {
+    // the same descriptor checks and error codes as crl_infonce_forward
+    const LossSpec ls = checked_loss(d);
+    CRL_REQUIRE(phi && psi && loss4 && row_lse && col_lse && B >= 1 && R >= 1, CRL_E_INVALID_ARG, "bad argument");
+    CRL_REQUIRE(ls.loss != CRL_LOSS_FB || B >= 2, CRL_E_SHAPE, "the forward-backward objective needs B >= 2");
+    CRL_REQUIRE((d->dtype == CRL_PREC_FP32 || d->dtype == CRL_PREC_FP64) && d->path == CRL_PATH_PLAIN,
+                CRL_E_UNSUPPORTED, "the allocation-free forward takes dtype FP32 or FP64 and path PLAIN");
+    const size_t elem = d->dtype == CRL_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const size_t need = infonce_ws_bytes(ls, B, R, elem, d->path);
+    CRL_REQUIRE(need <= kNoAllocScratchBytes, CRL_E_SHAPE,
+                "batch " + std::to_string(B) + " x repr " + std::to_string(R) + " needs " + std::to_string(need) +
+                    " bytes of scratch, above the fixed 4 MiB (4194304 bytes) of the allocation-free forward");
+    void* ws = nullptr;
+    std::string err;
+    const int rc = scratch_address(&ws, &err);
+    CRL_REQUIRE(rc == CRL_OK, rc, err);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (d->dtype == CRL_PREC_FP64)
+      infonce_forward<double>(ls, static_cast<const double*>(phi), static_cast<const double*>(psi), B, R,
+                              static_cast<double*>(loss4), static_cast<double*>(row_lse),
+                              static_cast<double*>(col_lse), ws, d->path, nullptr, nullptr, st);
+    else
+      infonce_forward<float>(ls, static_cast<const float*>(phi), static_cast<const float*>(psi), B, R,
+                             static_cast<float*>(loss4), static_cast<float*>(row_lse), static_cast<float*>(col_lse),
+                             ws, d->path, nullptr, nullptr, st);
+    check_launch("allocation-free infonce forward");
+  });
 }
