@@ -63,11 +63,41 @@ C12 The logsumexp penalty (reading C6) is added to every objective (§5.2
     penalty.
 """
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 ENERGIES = ("l2", "dot", "cos", "l1", "l2sq")
 LOSSES = ("fwd", "bwd", "sym")
 OBJECTIVES = LOSSES + ("flatnce_fwd", "flatnce_bwd", "fb", "dpo", "ipo", "sppo", "nce_binary")
+
+
+# The distance energies are computed one row i at a time from the differences
+# phi_i - psi_j (no expanded form).  Rows are grouped into fixed blocks of
+# ROW_BLOCK rows that run on a thread pool (numpy's element-wise kernels release
+# the interpreter lock); the block partition does not depend on the thread
+# count, so every result is the same on any machine.
+ROW_BLOCK = 256
+
+
+def _threads():
+    """Worker threads: OMP_NUM_THREADS when set, else every host core."""
+    try:
+        n = int(os.environ.get("OMP_NUM_THREADS", "") or (os.cpu_count() or 1))
+    except ValueError:
+        n = os.cpu_count() or 1
+    return max(1, n)
+
+
+def _over_row_blocks(n_rows, fn):
+    """[fn(i0, i1) for each block [i0, i1) of ROW_BLOCK rows], in block order."""
+    blocks = [(i0, min(i0 + ROW_BLOCK, n_rows)) for i0 in range(0, n_rows, ROW_BLOCK)]
+    n = min(_threads(), len(blocks))
+    if n <= 1:
+        return [fn(i0, i1) for i0, i1 in blocks]
+    with ThreadPoolExecutor(max_workers=n) as ex:
+        return list(ex.map(lambda b: fn(*b), blocks))
 
 
 def energy_matrix(phi, psi, energy="l2", tau=1.0):
@@ -77,14 +107,18 @@ def energy_matrix(phi, psi, energy="l2", tau=1.0):
     if energy in ("l2", "l2sq", "l1"):
         # one row i at a time: f(phi_i, psi_j) from the difference phi_i - psi_j
         f = np.empty((phi.shape[0], psi.shape[0]))
-        for i in range(phi.shape[0]):
-            d = phi[i][None, :] - psi
-            if energy == "l2":
-                f[i] = -np.sqrt((d ** 2).sum(axis=1))
-            elif energy == "l2sq":
-                f[i] = -(d ** 2).sum(axis=1)
-            else:
-                f[i] = -np.abs(d).sum(axis=1)
+
+        def rows(i0, i1):
+            for i in range(i0, i1):
+                d = phi[i][None, :] - psi
+                if energy == "l2":
+                    f[i] = -np.sqrt((d ** 2).sum(axis=1))
+                elif energy == "l2sq":
+                    f[i] = -(d ** 2).sum(axis=1)
+                else:
+                    f[i] = -np.abs(d).sum(axis=1)
+
+        _over_row_blocks(phi.shape[0], rows)
     elif energy == "dot":
         f = phi @ psi.T
     elif energy == "cos":
@@ -318,22 +352,30 @@ def energy_backward(phi, psi, G, energy="l2", tau=1.0):
     #   L2:   dF_ij/dphi_i = -(phi_i - psi_j) / (tau d_ij)   (0 where d_ij = 0, reading C7)
     #   L2^2: dF_ij/dphi_i = -2 (phi_i - psi_j) / tau
     #   L1:   dF_ij/dphi_i = -sign(phi_i - psi_j) / tau
-    # and dF_ij/dpsi_j is the negative of each.
+    # and dF_ij/dpsi_j is the negative of each.  dpsi sums the terms of every
+    # row: within a block of rows in row order, then the blocks in block order.
     dphi = np.zeros_like(phi)
+
+    def rows(i0, i1):
+        part = np.zeros_like(psi)
+        for i in range(i0, i1):
+            diff = phi[i][None, :] - psi                   # [j][r]
+            if energy == "l2":
+                d = np.sqrt((diff ** 2).sum(axis=1))
+                safe = d >= 1e-12
+                h = np.where(safe, G[i] / (tau * np.where(safe, d, 1.0)), 0.0)
+                term = h[:, None] * diff
+            elif energy == "l2sq":
+                term = (2.0 * G[i] / tau)[:, None] * diff
+            else:
+                term = (G[i] / tau)[:, None] * np.sign(diff)
+            dphi[i] = -term.sum(axis=0)
+            part += term
+        return part
+
     dpsi = np.zeros_like(psi)
-    for i in range(phi.shape[0]):
-        diff = phi[i][None, :] - psi                   # [j][r]
-        if energy == "l2":
-            d = np.sqrt((diff ** 2).sum(axis=1))
-            safe = d >= 1e-12
-            h = np.where(safe, G[i] / (tau * np.where(safe, d, 1.0)), 0.0)
-            term = h[:, None] * diff
-        elif energy == "l2sq":
-            term = (2.0 * G[i] / tau)[:, None] * diff
-        else:
-            term = (G[i] / tau)[:, None] * np.sign(diff)
-        dphi[i] = -term.sum(axis=0)
-        dpsi += term
+    for part in _over_row_blocks(phi.shape[0], rows):
+        dpsi += part
     return dphi, dpsi
 
 

@@ -163,3 +163,32 @@ def test_row_wise_energies_match_dense_broadcast():
     dphi, dpsi = critic.energy_backward(phi, psi, G, "l2", 1.0)
     np.testing.assert_allclose(dphi, -(H[:, :, None] * diff).sum(1), rtol=1e-12, atol=1e-13)
     np.testing.assert_allclose(dpsi, (H[:, :, None] * diff).sum(0), rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("energy", ["l2", "l2sq", "l1"])
+def test_row_blocks_give_the_same_bits_on_any_thread_count(energy, monkeypatch):
+    """Several row blocks (B > ROW_BLOCK, ragged last block): one thread and four
+    threads give identical bits (the block partition is fixed), and both equal
+    the dense [i][j][r] broadcast of the definition."""
+    B, R = critic.ROW_BLOCK * 2 + 37, 5
+    phi, psi = reps(B, R, 13)
+    G = np.random.default_rng(14).standard_normal((B, B))
+    out = {}
+    for n in ("1", "4"):
+        monkeypatch.setenv("OMP_NUM_THREADS", n)
+        out[n] = (critic.energy_matrix(phi, psi, energy), *critic.energy_backward(phi, psi, G, energy, 0.8))
+    for a, b in zip(out["1"], out["4"]):
+        np.testing.assert_array_equal(a, b)
+    diff = phi[:, None, :] - psi[None, :, :]
+    if energy == "l2":
+        dense = -np.sqrt((diff ** 2).sum(2))
+        term = (G / (0.8 * -dense))[:, :, None] * diff
+    elif energy == "l2sq":
+        dense = -(diff ** 2).sum(2)
+        term = (2.0 * G / 0.8)[:, :, None] * diff
+    else:
+        dense = -np.abs(diff).sum(2)
+        term = (G / 0.8)[:, :, None] * np.sign(diff)
+    np.testing.assert_allclose(out["1"][0], dense, rtol=1e-14)
+    np.testing.assert_allclose(out["1"][1], -term.sum(1), rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(out["1"][2], term.sum(0), rtol=1e-11, atol=1e-12)
