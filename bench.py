@@ -6,14 +6,19 @@ batch -> critic step (encoders, energy + InfoNCE + penalty, backward, Adam)
 public call crl_update_step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ant|small|humanoid|large] [--precision bf16|fp32|fp64]
-                  [--path fused|plain] [--trace gemm|energy|relabel|adam|aux|insert]
-                  [--no-comparator] [--no-relabel] [--no-cpu-baseline]
+                  [--workload large|humanoid|ant|small|sweep] [--precision bf16|fp32|fp64]
+                  [--path fused|plain] [--trace auto|gemm|energy|relabel|adam|aux|insert]
+                  [--no-comparator] [--no-relabel] [--no-cpu-baseline] [--no-extra] [--no-error]
 
-The headline is the BF16 fused path; the FP32 plain path runs on the same
-workload in the same process as "comparator".  "relabel" reports the
-standalone sample + relabel kernel at 2^20 and 2^22 samples per launch on
-Humanoid-shaped rows (its HBM roofline).
+The headline is the BF16 fused path on the large-batch workload (batch 8192,
+repr 256, 2 x 512 encoders); the FP32 plain path runs on the same workload in
+the same process as "comparator".  "error" states the loss and per-tensor
+gradient error of both arms against the FP64 oracle on one batch of the timed
+workload.  "workloads" repeats the measurement on the Humanoid (batch 1024,
+4 x 1024 LayerNorm encoders, critic + actor) and Ant (batch 256) workloads and
+on the 32-agent sweep.  "relabel" reports the standalone sample + relabel
+kernel at 2^20 and 2^22 samples per launch on Humanoid-shaped rows (its HBM
+roofline).
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs its own
 independent agent (its own Philox key and buffer): weak scaling, no data-path
@@ -141,9 +146,10 @@ def cpu_oracle_rate(w, n_steps, budget_s=20.0):
     nets = workload.init_agent(w)
     nets = {k: [{kk: vv.astype(np.float64) for kk, vv in l.items()} for l in v] for k, v in nets.items()}
     buf = oracle.relabel.ReplayBuffer(w.E, w.T, w.D, w.A)
-    obs, act, done = workload.buffer_contents(w, mean_len=None)
+    obs, act, done = buffer_contents_cached(w)
     buf.insert(obs, act, done)
-    extra = workload.buffer_contents(w, n=n_steps, mean_len=None, seed_offset=1)
+    n_steps = min(n_steps, 64)
+    extra = buffer_contents_cached(w, n=n_steps, seed_offset=1)
     state = oracle.step.AgentState(nets["phi"], nets["psi"], nets["pi"])
     cfg = dict(seed=w.seed, agent=0, B=w.B, goal_idx=w.goals(), gamma=w.gamma, energy=w.energy, tau=w.tau,
                loss=w.loss, sym_reduction=w.sym_reduction, beta=w.beta, penalty_axis=w.penalty_axis, alpha=w.alpha,
@@ -169,6 +175,79 @@ def cpu_oracle_rate(w, n_steps, budget_s=20.0):
     except ImportError:
         pass
     return done_steps / dt, done_steps, cores
+
+
+# The benchmark spec's error bars (FP32 path: relative errors; BF16 path: loss
+# relative error and per-tensor gradient cosine), each against the FP64 oracle.
+ERROR_BARS = {"fp32": {"loss_rel": 1e-5, "grad_rel": 1e-4}, "bf16": {"loss_rel": 2e-2, "grad_cos": 0.999}}
+
+
+def oracle_error(w, dev, arms, step=0):
+    """Oracle leg: the error of each arm's critic and actor step against the FP64
+    oracle on one batch of the timed workload (its networks and buffer, relabel
+    step `step`, actor noise given).  Per arm: the relabel indices (bit-exact or
+    not), the loss parts' relative errors, and per parameter tensor the
+    gradient's relative L2 error and cosine.  Runs outside every timed region."""
+    import torch
+    import oracle
+    from paper_2408_11052_gb300 import api
+
+    f32 = lambda x: float(np.float32(x))  # noqa: E731  (hyperparameters as the library holds them)
+    tau, beta, alpha = f32(w.tau), f32(w.beta), f32(w.alpha)
+    nets = workload.init_agent(w)
+    n64 = {k: [{kk: vv.astype(np.float64) for kk, vv in l.items()} for l in v] for k, v in nets.items()}
+    obs, act, done = buffer_contents_cached(w)
+    buf = oracle.relabel.ReplayBuffer(w.E, w.T, w.D, w.A)
+    buf.insert(obs, act, done)
+    t0 = time.perf_counter()
+    s, a, g, idx = oracle.relabel.sample_relabel(buf, w.seed, 0, step, w.B, w.goals(), w.gamma)
+    parts, gphi, gpsi, _, _ = oracle.step.critic_loss_and_grad(n64["phi"], n64["psi"], s, a, g, w.energy, tau,
+                                                               w.loss, w.sym_reduction, beta, w.penalty_axis)
+    eps = workload.actor_noise(w.B, w.A, 3)
+    ref_a = oracle.actor.actor_loss_and_grad(n64["pi"], n64["phi"], n64["psi"], s, g, eps.astype(np.float64),
+                                             w.energy, tau, alpha)
+    oracle_s = time.perf_counter() - t0
+
+    def tensors(got, ref, net):
+        rows = []
+        for li, (gl, rl) in enumerate(zip(got, ref)):
+            for k in rl:
+                x, y = np.asarray(gl[k], np.float64).ravel(), np.asarray(rl[k], np.float64).ravel()
+                nx, ny = np.linalg.norm(x), np.linalg.norm(y)
+                rows.append({"tensor": f"{net}.{li}.{k}", "rel_err": float(np.linalg.norm(x - y) / (ny or 1.0)),
+                             "cos": float(x @ y / (nx * ny)) if nx > 0 and ny > 0 else float(nx == ny)})
+        return rows
+
+    out = {"workload": w.name, "batch": f"relabel step {step} of the timed workload's buffer and networks",
+           "oracle": "FP64 numpy, materialised B x B", "oracle_s": oracle_s, "bars": ERROR_BARS}
+    for precision, path in arms:
+        ctx = api.CRLContext(w, precision=precision, path=path)
+        for k, v in nets.items():
+            ctx.load_network(k, v)
+        ctx.insert(torch.from_numpy(obs).to(dev), torch.from_numpy(act).to(dev), torch.from_numpy(done).to(dev))
+        sd, ad, gd, idd = ctx.sample(step=step)
+        lc = ctx.critic_step(sd, ad, gd, apply_update=False).cpu().numpy()
+        la = ctx.actor_step(sd, gd, torch.from_numpy(eps).to(dev), apply_update=False).cpu().numpy()
+        torch.cuda.synchronize()
+        rc, status = ctx.sync_status()
+        rel = lambda x, y: abs(float(x) - float(y)) / (abs(float(y)) or 1.0)  # noqa: E731
+        grads = tensors(ctx.network("phi", "grads"), gphi, "phi") + tensors(ctx.network("psi", "grads"), gpsi, "psi") \
+            + tensors(ctx.network("pi", "grads"), ref_a["grads"], "pi")
+        key = "bf16" if precision == "bf16" else "fp32"
+        r = {"precision": precision, "path": path, "status": status,
+             "relabel_indices_exact": bool(np.array_equal(idd.cpu().numpy().astype(np.int64), idx)),
+             "loss_rel_err": {"critic_total": rel(lc[0], parts["total"]), "critic_fwd": rel(lc[1], parts["fwd"]),
+                              "critic_bwd": rel(lc[2], parts["bwd"]), "penalty": rel(lc[3], parts["penalty"]),
+                              "actor": rel(la[0], ref_a["loss"])},
+             "grad_worst_rel_err": max(t["rel_err"] for t in grads),
+             "grad_worst_cos": min(t["cos"] for t in grads), "grads": grads}
+        bar = ERROR_BARS[key]
+        loss_ok = max(r["loss_rel_err"].values()) <= bar["loss_rel"]
+        grad_ok = r["grad_worst_cos"] >= bar["grad_cos"] if key == "bf16" else r["grad_worst_rel_err"] <= bar["grad_rel"]
+        r["within_bars"] = bool(loss_ok and grad_ok and r["relabel_indices_exact"] and rc == api.OK)
+        out[f"{precision}_{path}"] = r
+        ctx.close()
+    return out
 
 
 BLAS_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
@@ -234,6 +313,76 @@ def traffic_record(kernel_class, workload_name, precision, path):
     return rec["bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
 
 
+_BUFFERS = {}
+
+
+def buffer_contents_cached(w, n=None, seed_offset=0):
+    """workload.buffer_contents (fixed-length episodes), generated once per
+    (workload, n, seed offset) and reused by every arm of this run."""
+    key = (w.name, w.E, w.T, w.D, w.A, n, seed_offset)
+    if key not in _BUFFERS:
+        _BUFFERS[key] = workload.buffer_contents(w, n=n, mean_len=None, seed_offset=seed_offset)
+    return _BUFFERS[key]
+
+
+def roofline_of(arm, w, precision, path):
+    """The roofline object of an arm's traced kernel class: algorithmic work per
+    launch over the launches' CUDA-event time, against the measured peak."""
+    peaks, peak_src = load_peaks()
+    cls = arm["trace_class"]
+    n_tr, tr_ms, tr_work = arm["trace"]
+    traffic = traffic_record(cls, w.name, precision, path)
+    common = {"kernel_class": cls, "launches": n_tr, "avg_launch_us": 1e3 * tr_ms / max(n_tr, 1),
+              "work_per_launch": tr_work / max(n_tr, 1),
+              "timing": "eager traced pass of the same K steps (CUDA events around every launch of the class)",
+              "traffic": traffic}
+    if cls in ("gemm", "energy") and precision == "bf16":
+        achieved = tr_work / (tr_ms / 1e3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{peak_src} bf16_tflops_sustained (kernel timed inside a long step)", **common}
+        per_launch = tr_work / max(n_tr, 1)
+        # at the peak a launch's work takes per_launch / peak; when that is far
+        # below the launch's duration, the launch is latency-bound, not tensor-bound
+        roof["note"] = (f"{per_launch / 1e6:.1f} MFLOP per launch = {per_launch / (peak * 1e12) * 1e6:.2f} us at the "
+                        f"peak against {1e3 * tr_ms / max(n_tr, 1):.1f} us measured")
+    elif cls in ("gemm", "energy"):
+        achieved = tr_work / (tr_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_ALU_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz", **common}
+    else:
+        achieved = tr_work / (tr_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} hbm_gbs", **common}
+    if traffic is not None:
+        roof["traffic_source"] = "profiles/roofline_traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+    return roof
+
+
+def secondary(args, w, dev, flush, steps, error):
+    """One more workload on one GPU: the BF16 fused arm (breakdown, dominant
+    class roofline, host-input e2e) next to the FP32 plain arm, and (error) the
+    oracle leg's error table for both."""
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.trace = steps, "auto"
+    a = run_arm(sub, w, "bf16", "fused", dev, 1, 0, flush, full=True)
+    c = run_arm(sub, w, "fp32", "plain", dev, 1, 0, flush, full=False)
+    v, cv = steps / (a["ms"] / 1e3), steps / (c["ms"] / 1e3)
+    out = {"workload": w.name, "value": v, "unit": "update steps/s", "ms_per_step": a["ms"] / steps, "steps": steps,
+           "samples_per_s": v * w.B, "precision": "bf16", "path": "fused",
+           "e2e": {"value": steps / (a["e2e_ms"] / 1e3), "unit": "update steps/s",
+                   "h2d_bytes_per_step": w.E * (w.D + w.A) * 4 + w.E, "d2h_bytes_per_step": 24},
+           "comparator": {"precision": "fp32", "path": "plain", "value": cv, "unit": "update steps/s",
+                          "ms_per_step": c["ms"] / steps, "speedup": v / cv},
+           "launches_per_step": a["launches_per_step"],
+           "breakdown": {"timing": "eager, events around every launch", **a["breakdown"]},
+           "roofline": roofline_of(a, w, "bf16", "fused"), "clocks": a["clocks"]}
+    if error:
+        out["error"] = oracle_error(w, dev, (("bf16", "fused"), ("fp32", "plain")))
+    return out
+
+
 def run_arm(args, w, precision, path, dev, world, rank, flush, full):
     """Prefill, warm up and time one configuration of the update step.  full:
     also the traced roofline pass, the end-to-end (host-buffer) pass and the
@@ -245,11 +394,11 @@ def run_arm(args, w, precision, path, dev, world, rank, flush, full):
     ctx = api.CRLContext(w, precision=precision, path=path, agent=rank)
     for k, v in workload.init_agent(w).items():
         ctx.load_network(k, v)
-    obs, act, done = workload.buffer_contents(w, mean_len=None, seed_offset=rank)
+    obs, act, done = buffer_contents_cached(w, seed_offset=rank)
     ctx.insert(torch.from_numpy(obs).to(dev), torch.from_numpy(act).to(dev), torch.from_numpy(done).to(dev))
     del obs, act, done
     n_all = args.warmup + 2 * args.steps + 8
-    ins = workload.buffer_contents(w, n=n_all, mean_len=None, seed_offset=100 + rank)
+    ins = buffer_contents_cached(w, n=n_all, seed_offset=100 + rank)
     d_obs, d_act, d_done = (torch.from_numpy(x).to(dev) for x in ins)
     h_obs, h_act, h_done = (torch.from_numpy(x).pin_memory() for x in ins)
     loss_dev = torch.zeros(6, dtype=torch.float32, device=dev)
@@ -284,6 +433,20 @@ def run_arm(args, w, precision, path, dev, world, rank, flush, full):
         ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
         return ms, tr
 
+    def timed_e2e(K):
+        """Host wall clock around each step with host inputs and a host read of
+        its loss (the step's result): the host waits for every step."""
+        total = 0.0
+        for k in range(K):
+            flush.fill_(k & 0xFF)                 # evict L2 between steps (not timed)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            stream.synchronize()
+            _ = float(loss_host[0])
+            total += time.perf_counter() - t0
+        return 1e3 * total
+
     for _ in range(args.warmup):
         step_device()
     torch.cuda.synchronize()
@@ -304,6 +467,9 @@ def run_arm(args, w, precision, path, dev, world, rank, flush, full):
                               "us_per_launch": 1e3 * cls_ms / max(n, 1)}
         out["launches_per_step"] = launches
         out["breakdown"] = breakdown
+        # the roofline's kernel class: the one that takes the most time per step
+        out["trace_class"] = args.trace if args.trace != "auto" else \
+            max(breakdown, key=lambda c: breakdown[c]["us_per_step"])
 
     # timed region: graph-replayed steps, no tracing (tracing forces eager launches)
     with ClockSampler(dev.index) as clk:
@@ -313,10 +479,12 @@ def run_arm(args, w, precision, path, dev, world, rank, flush, full):
     if full:
         # roofline pass: the same K steps again, eager, with CUDA events around
         # every launch of the traced kernel class
-        _, out["trace"] = timed(step_device, args.steps, trace=args.trace)
+        _, out["trace"] = timed(step_device, args.steps, trace=out["trace_class"])
         for _ in range(3):
             step_host()
-        e2e_ms, _ = timed(step_host, args.steps)
+        barrier(world)
+        e2e_ms = timed_e2e(args.steps)
+        barrier(world)
         out["e2e_ms"] = max_over_ranks(e2e_ms, world)
     rc, status = ctx.sync_status()
     assert rc == api.OK, f"status {status}"
@@ -529,7 +697,7 @@ def run_sweep(args, dev, flush):
             "roofline": roof, "clocks": main_arm["clocks"]}
     if comps:
         line["comparator"] = comps
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def api_losses():
@@ -537,16 +705,20 @@ def api_losses():
     return _api.LOSS
 
 
-def main():
+def build_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ant", choices=sorted(WORKLOADS) + ["sweep"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + ["sweep"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--path", default="fused", choices=["plain", "fused"])
-    ap.add_argument("--trace", default="gemm", choices=["gemm", "energy", "relabel", "adam", "aux", "insert"])
+    ap.add_argument("--trace", default="auto", choices=["auto", "gemm", "energy", "relabel", "adam", "aux", "insert"],
+                    help="kernel class of the roofline object (auto: the one that takes the most time per step)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the Humanoid, Ant and sweep measurements of the default large-batch run")
+    ap.add_argument("--no-error", action="store_true", help="skip the error against the FP64 oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the FP32 plain arm")
     ap.add_argument("--no-relabel", action="store_true", help="skip the standalone relabel throughput")
@@ -565,9 +737,13 @@ def main():
     ap.add_argument("--gemm-kernel", default="any", choices=["any", "one_tile", "persistent"],
                     help="BF16 GEMM kernel family the autotuner may pick from")
     ap.add_argument("--oracle-rate", type=float, default=None, help=argparse.SUPPRESS)
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     args.warmup = max(args.warmup, 3)
-    w = WORKLOADS.get(args.workload, workload.ANT_AUTOGRAD)
+    w = WORKLOADS.get(args.workload, workload.LARGE_BATCH)
     over = {k: v for k, v in (("loss", args.loss), ("energy", args.energy)) if v is not None}
     if args.alpha_autotune:
         over["alpha_autotune"] = True
@@ -595,7 +771,7 @@ def main():
     torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     if args.workload == "sweep":
-        run_sweep(args, dev, flush)
+        print(json.dumps(run_sweep(args, dev, flush)), flush=True)
         return
     if args.only_relabel:
         rw, res = relabel_throughput(dev, flush)
@@ -613,41 +789,26 @@ def main():
                       "ms_per_step": comp["ms"] / args.steps, "speedup": value / cv, "clocks": comp["clocks"],
                       "note": "same workload, timing and launch mode; plain SIMT FP32 kernels, B x B materialised"}
 
-    peaks, peak_src = load_peaks()
-    n_tr, tr_ms, tr_work = main_arm["trace"]
-    traffic = traffic_record(args.trace, w.name, args.precision, args.path)
-    common = {"kernel_class": args.trace, "launches": n_tr, "avg_launch_us": 1e3 * tr_ms / max(n_tr, 1),
-              "timing": "eager traced pass of the same K steps (CUDA events around every launch of the class)",
-              "traffic": traffic}
-    if args.trace == "gemm" and args.precision == "bf16":
-        achieved = tr_work / (tr_ms / 1e3) / 1e12
-        peak = peaks["bf16_tflops_sustained"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"{peak_src} bf16_tflops_sustained (kernel timed inside a long step)", **common}
-        per_launch = tr_work / max(n_tr, 1)
-        # at the peak a launch's work takes per_launch / peak; when that is far
-        # below the launch's duration, the launch is latency-bound, not tensor-bound
-        roof["flop_per_launch"] = per_launch
-        roof["note"] = (f"{per_launch / 1e6:.1f} MFLOP per launch = {per_launch / (peak * 1e12) * 1e6:.2f} us at the "
-                        f"peak against {1e3 * tr_ms / max(n_tr, 1):.1f} us measured: "
-                        + ("latency-bound (pipeline fill, epilogue and launch latency dominate)"
-                           if per_launch / (peak * 1e12) < 0.2 * tr_ms / 1e3 / max(n_tr, 1) else "tensor-bound"))
-    elif args.trace in ("gemm", "energy"):
-        achieved = tr_work / (tr_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_ALU_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz", **common}
-    else:
-        achieved = tr_work / (tr_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} hbm_gbs", **common}
-    if traffic is not None:
-        roof["traffic"] = traffic
-        roof["traffic_source"] = "profiles/roofline_traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+    roof = roofline_of(main_arm, w, args.precision, args.path)
 
+    error = None
+    if rank == 0 and world == 1 and not args.no_error:
+        arms = [(args.precision, args.path)] + ([("fp32", "plain")] if comparator is not None else [])
+        error = oracle_error(w, dev, arms)
+
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra and args.workload == "large" and not over:
+        extra = {"humanoid": secondary(args, workload.HUMANOID_BF16, dev, flush, min(args.steps, 100),
+                                       error=not args.no_error),
+                 "ant": secondary(args, workload.ANT_AUTOGRAD, dev, flush, args.steps, error=not args.no_error)}
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.no_comparator, sub.trace = min(args.steps, 50), True, "gemm"
+        extra["sweep"] = run_sweep(sub, dev, flush)
+
+    loop_w = workload.ANT_AUTOGRAD if args.workload == "large" else w
     loop = None
     if rank == 0 and world == 1 and not args.no_loop:
-        loop = collect_loop(w, args.precision, args.path, dev)
+        loop = collect_loop(loop_w, args.precision, args.path, dev)
 
     relabel = None
     if rank == 0 and world == 1 and not args.no_relabel:
@@ -662,11 +823,15 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, steps, cores = cpu_oracle_rate(w, 200, budget_s=15.0)
         cpu = {"value": rate, "unit": "update steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{steps} full update steps of the same workload (FP64 numpy oracle)"}
-        one = cpu_oracle_rate_one_thread(args)
-        if one is not None:
-            cpu["one_thread"] = {"value": one[0], "unit": "update steps/s", "cores": 1,
-                                 "sample": f"{one[1]} update steps, BLAS limited to one thread"}
+               "sample": f"{steps} full update steps of the same workload (FP64 numpy oracle; its BLAS and its "
+                         f"distance-energy row blocks on every host core)"}
+        if rate > 0.5:        # one thread: only where a step takes well under a second on all cores
+            one = cpu_oracle_rate_one_thread(args)
+            if one is not None:
+                cpu["one_thread"] = {"value": one[0], "unit": "update steps/s", "cores": 1,
+                                     "sample": f"{one[1]} update steps, BLAS and row blocks on one thread"}
+        else:
+            cpu["one_thread"] = {"value": None, "note": f"skipped: one step takes {1 / rate:.0f} s on all cores"}
 
     h2d = w.E * (w.D + w.A) * 4 + w.E
     line = {"metric": METRIC, "value": value, "unit": "update steps/s", "n_gpus": world, "steps": args.steps,
@@ -683,7 +848,9 @@ def main():
                        "step": "insert 1 slice + relabel + critic fwd/bwd + Adam + actor fwd/bwd + Adam",
                        "parallelism": f"{world} independent agents"},
             "e2e": {"value": world * args.steps / (main_arm["e2e_ms"] / 1e3), "unit": "update steps/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24,
+                    "timing": "host wall clock per step: pinned host inputs read by the insert kernel, the "
+                              "loss copied to pinned host memory, the host waits for it every step"},
             "gpu_launches": main_arm["launches_per_step"] * args.steps,
             "breakdown": {"timing": "eager, events around every launch (no launch overlap): sums exceed ms_per_step",
                           **main_arm["breakdown"]},
@@ -691,6 +858,10 @@ def main():
             "clocks": main_arm["clocks"]}
     if comparator is not None:
         line["comparator"] = comparator
+    if error is not None:
+        line["error"] = error
+    if extra is not None:
+        line["workloads"] = extra
     if relabel is not None:
         line["relabel"] = relabel
     if loop is not None:

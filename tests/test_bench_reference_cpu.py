@@ -18,7 +18,7 @@ def run(extra_env=None, *args):
 
 
 def test_reference_line_keeps_the_contract():
-    r = run(None, "--steps", "1", "--warmup", "1")
+    r = run(None, "--steps", "1", "--warmup", "1", "--workload", "ant")
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -44,8 +44,21 @@ def test_reference_arm_runs_on_rank_zero_only():
 
 
 def test_oracle_rate_child_line():
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-rate", "0.5"], cwd=ROOT,
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-rate", "0.5", "--workload", "ant"],
+                       cwd=ROOT,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     d = json.loads(r.stdout.strip().splitlines()[-1])
     assert d["value"] > 0 and d["steps"] >= 1
+
+
+def test_default_workload_is_the_large_batch_headline():
+    """With no flags the benchmark times the large-batch workload (batch 8192,
+    repr 256), reports the roofline of its most expensive kernel class, and adds
+    the error against the oracle and the other workloads."""
+    sys.path.insert(0, ROOT)
+    import bench
+    args = bench.build_parser().parse_args([])
+    assert args.workload == "large" and bench.WORKLOADS["large"].B == 8192 and bench.WORKLOADS["large"].repr == 256
+    assert args.trace == "auto" and not args.no_error and not args.no_extra
+    assert args.gpus == 1 and args.warmup >= 3

@@ -1,6 +1,17 @@
 """GPU parity of the BF16 tensor-core path (tcgen05 GEMMs, FP32 accumulation) against
 the FP64 oracle: loss relative error <= 2e-2 and gradient cosine >= 0.999 per tensor
-(the BF16 tolerances of the parity contract)."""
+(the BF16 tolerances of the parity contract).
+
+The full-size cases (Humanoid: 4 x 1024 LayerNorm encoders, batch 1024; large
+batch: 2 x 512 encoders, batch 8192) run on the networks as initialised, with
+no batch selection: at the cosine bar a handful of ReLU units whose
+pre-activation lies within BF16 rounding of zero cannot move a tensor's
+cosine, so the masked backward and the LayerNorm backward with dead units are
+compared as they are.
+
+The actor objective mean_i[alpha log pi_i - F_ii] is a difference of two
+terms that may nearly cancel; its bar is 2e-2 relative to the sum of their
+magnitudes |alpha mean log pi| + |mean F_ii| (the size of what is computed)."""
 
 import numpy as np
 import pytest
@@ -42,9 +53,14 @@ def bf16_small(**kw):
     return workload.Workload("bf16", **base)
 
 
-def run_critic(w, nets=None, n=70, mean_len=9.0):
+def actor_loss_bar(ref, alpha):
+    """2e-2 of |alpha mean log pi| + |mean F_ii| (the actor loss is their difference)."""
+    return BF16_LOSS_RTOL * (abs(alpha * ref["logpi_mean"]) + abs(ref["f_mean"]))
+
+
+def run_critic(w, nets=None, n=70, mean_len=9.0, kink_free=True, start=4):
     ctx, nets, buf = setup(w, precision="bf16", n=n, mean_len=mean_len, nets=nets)
-    step = pick_step(w, nets, buf, 4)
+    step = pick_step(w, nets, buf, start) if kink_free else start
     s, a, g, _ = ctx.sample(step=step)
     loss = ctx.critic_step(s, a, g, apply_update=False).cpu().numpy()
     torch.cuda.synchronize()
@@ -96,11 +112,7 @@ def test_bf16_critic_full_size_ant():
 
 def test_bf16_critic_full_size_humanoid():
     w = workload.HUMANOID_BF16
-    nets = workload.init_agent(w, perturb=True)
-    for net in ("phi", "psi"):
-        for layer in nets[net][:-1]:
-            layer["ln_b"] = layer["ln_b"] + np.float32(4.0)
-    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w, nets=nets, mean_len=None)
+    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w, mean_len=None, kink_free=False)
     assert abs(got[0] - parts["total"]) <= BF16_LOSS_RTOL * abs(parts["total"])
     assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
     assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
@@ -120,7 +132,7 @@ def test_bf16_actor_matches_oracle(energy, layernorm):
     h = hp(w)
     ref = oracle.actor.actor_loss_and_grad(nets["pi"], nets["phi"], nets["psi"], s_o, g_o, eps.astype(np.float64),
                                            w.energy, h["tau"], h["alpha"])
-    assert abs(out[0] - ref["loss"]) <= BF16_LOSS_RTOL * abs(ref["loss"]) + 1e-3
+    assert abs(out[0] - ref["loss"]) <= actor_loss_bar(ref, h["alpha"])
     assert_grads_cosine(ctx.network("pi", "grads"), ref["grads"], "pi")
 
 
@@ -141,13 +153,16 @@ def test_bf16_update_steps_track_oracle():
         buf.insert(*ins)
         ref = oracle.step.update_step(state, buf, cfg, i, oracle.actor.gaussian_noise(w.seed, 0, i, w.B, w.A))
         assert abs(got[0] - ref["critic"]["total"]) <= BF16_LOSS_RTOL * abs(ref["critic"]["total"])
-        assert abs(got[4] - ref["actor_loss"]) <= BF16_LOSS_RTOL * abs(ref["actor_loss"]) + 1e-2
+        # actor loss = alpha mean log pi - mean F_ii: the bar is relative to |both terms|
+        alpha_logpi = ref["alpha"] * ref["logpi_mean"]
+        bar = BF16_LOSS_RTOL * (abs(alpha_logpi) + abs(alpha_logpi - ref["actor_loss"]))
+        assert abs(got[4] - ref["actor_loss"]) <= bar
     assert ctx.sync_status() == (0, 0)
 
 
 # ---- fused tensor-core energy stage (path "fused": the B x B matrix is never written) ----
 
-def run_critic_fused(w, nets=None, n=70, mean_len=9.0, start=4, kink_free=True):
+def run_critic_fused(w, nets=None, n=70, mean_len=9.0, start=4, kink_free=True, tau=None):
     ctx, nets, buf = setup(w, precision="bf16", path="fused", n=n, mean_len=mean_len, nets=nets)
     step = pick_step(w, nets, buf, start) if kink_free else start
     s, a, g, _ = ctx.sample(step=step)
@@ -163,7 +178,7 @@ def run_critic_fused(w, nets=None, n=70, mean_len=9.0, start=4, kink_free=True):
 def check_fused(ctx, got, ref):
     parts, gphi, gpsi, _, _ = ref
     for i, k in enumerate(("total", "fwd", "bwd", "penalty")):
-        assert abs(got[i] - parts[k]) <= BF16_LOSS_RTOL * abs(parts[k]) + 1e-4, (k, got[i], parts[k])
+        assert abs(got[i] - parts[k]) <= BF16_LOSS_RTOL * abs(parts[k]), (k, got[i], parts[k])
     assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
     assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
     assert ctx.sync_status() == (0, 0)
@@ -199,12 +214,7 @@ def test_bf16_layernorm_rows_wider_than_registers(hidden):
     """LayerNorm rows wider than 1024 take the kernels' multi-pass form (narrower
     rows stay in registers); forward, backward and the gain / shift gradients."""
     w = bf16_small(B=48, hidden=hidden, layers=2, repr=24, layernorm=True)
-    # (LayerNorm shifts raised by 4 keep every unit far from its kink, as in the Humanoid tests)
-    nets = workload.init_agent(w, perturb=True)
-    for net in ("phi", "psi"):
-        for layer in nets[net][:-1]:
-            layer["ln_b"] = layer["ln_b"] + np.float32(4.0)
-    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w, nets=nets)
+    ctx, got, (parts, gphi, gpsi, _, _) = run_critic(w, kink_free=False)
     assert abs(got[0] - parts["total"]) <= BF16_LOSS_RTOL * abs(parts["total"])
     assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
     assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")
@@ -255,24 +265,31 @@ def test_fused_critic_full_size_ant():
 
 
 def test_fused_critic_full_size_humanoid():
-    w = workload.HUMANOID_BF16
-    nets = workload.init_agent(w, perturb=True)
-    for net in ("phi", "psi"):
-        for layer in nets[net][:-1]:
-            layer["ln_b"] = layer["ln_b"] + np.float32(4.0)
-    ctx, got, ref = run_critic_fused(w, nets=nets, mean_len=None)
+    ctx, got, ref = run_critic_fused(workload.HUMANOID_BF16, mean_len=None, kink_free=False)
     check_fused(ctx, got, ref)
+
+
+def test_fused_actor_full_size_humanoid():
+    """The policy gradient on the BF16 fused path at Humanoid size (4 x 1024
+    LayerNorm policy and encoders, batch 1024, action 17, cos energy): the actor
+    loss and every pi gradient tensor against the oracle."""
+    w = workload.HUMANOID_BF16
+    ctx, nets, buf = setup(w, precision="bf16", path="fused", mean_len=None)
+    eps = workload.actor_noise(w.B, w.A, 3)
+    step = 4
+    s, a, g, _ = ctx.sample(step=step)
+    out = ctx.actor_step(s, g, torch.from_numpy(eps).to(ctx.device), apply_update=False).cpu().numpy()
+    s_o, _, g_o, _ = oracle.relabel.sample_relabel(buf, w.seed, 0, step, w.B, w.goals(), w.gamma)
+    h = hp(w)
+    ref = oracle.actor.actor_loss_and_grad(nets["pi"], nets["phi"], nets["psi"], s_o, g_o, eps.astype(np.float64),
+                                           w.energy, h["tau"], h["alpha"])
+    assert abs(out[0] - ref["loss"]) <= actor_loss_bar(ref, h["alpha"])
+    assert_grads_cosine(ctx.network("pi", "grads"), ref["grads"], "pi")
+    assert ctx.sync_status() == (0, 0)
 
 
 def test_fused_critic_full_size_large_batch():
     """Batch 8192, repr 256, 2 x 512 MLPs, L2 energy, forward InfoNCE (the B x B matrix
     would be 268 MB in FP32; the fused path never writes it)."""
-    w = workload.LARGE_BATCH
-    # 16.8M hidden units: no batch is kink-free, so the hidden biases are raised by
-    # 4 (every unit ~4 sigma from its kink), as in the Humanoid tests
-    nets = workload.init_agent(w, perturb=True)
-    for net in ("phi", "psi"):
-        for layer in nets[net][:-1]:
-            layer["b"] = layer["b"] + np.float32(4.0)
-    ctx, got, ref = run_critic_fused(w, nets=nets, n=40, mean_len=None, kink_free=False)
+    ctx, got, ref = run_critic_fused(workload.LARGE_BATCH, n=40, mean_len=None, kink_free=False)
     check_fused(ctx, got, ref)
