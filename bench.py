@@ -732,8 +732,6 @@ def build_parser():
     ap.add_argument("--energy", default=None, choices=["l2", "dot", "cos", "l2sq", "l1"],
                     help="energy function instead of the workload's")
     ap.add_argument("--alpha-autotune", action="store_true", help="learn the entropy coefficient")
-    ap.add_argument("--mlp-fusion", default="auto", choices=["auto", "layers", "whole"],
-                    help="BF16 network forward: grouped per-layer launches or one whole-network kernel")
     ap.add_argument("--gemm-kernel", default="any", choices=["any", "one_tile", "persistent"],
                     help="BF16 GEMM kernel family the autotuner may pick from")
     ap.add_argument("--oracle-rate", type=float, default=None, help=argparse.SUPPRESS)
@@ -762,7 +760,6 @@ def main():
     from paper_2408_11052_gb300 import api as _api
     if args.no_autotune:
         _api.set_autotune(False)
-    _api.set_mlp_fusion(args.mlp_fusion)
     _api.set_gemm_kernel(args.gemm_kernel)
     rank, world, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local if world > 1 else 0)
@@ -810,6 +807,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_loop:
         loop = collect_loop(loop_w, args.precision, args.path, dev)
 
+    peaks, peak_src = load_peaks()
     relabel = None
     if rank == 0 and world == 1 and not args.no_relabel:
         rw, res = relabel_throughput(dev, flush)
@@ -843,7 +841,7 @@ def main():
                        "action": w.A, "goal": w.G, "hidden": [w.hidden] * w.layers, "repr": w.repr,
                        "energy": w.energy, "loss": w.loss, "alpha_autotune": bool(w.alpha_autotune),
                        "precision": args.precision, "path": args.path,
-                       "mlp_fusion": args.mlp_fusion, "gemm_kernel": args.gemm_kernel,
+                       "gemm_kernel": args.gemm_kernel,
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "step": "insert 1 slice + relabel + critic fwd/bwd + Adam + actor fwd/bwd + Adam",
                        "parallelism": f"{world} independent agents"},

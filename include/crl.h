@@ -447,19 +447,6 @@ int32_t crl_set_autotune(int32_t enable);
 #define CRL_GEMM_PERSISTENT 2
 int32_t crl_set_gemm_kernel(int32_t mode);
 
-/* How the BF16 path runs a network's forward pass (process-wide; library
- * extension).  Narrow networks without LayerNorm (hidden width H a multiple of
- * 64 up to 256, every layer's input and output within 256) may run every layer
- * in one launch: a cluster of H / 64 CTAs per 128-row block, each computing 64
- * columns of a hidden layer and copying them into the other CTAs' shared
- * memory as the next layer's input (CRL_MLP_WHOLE).  CRL_MLP_AUTO (the
- * default) and CRL_MLP_LAYERS run one grouped launch per layer, which
- * measured faster here.  The outputs are identical.  Returns the previous
- * setting, or CRL_E_INVALID_ARG for an unknown mode. */
-#define CRL_MLP_AUTO 0
-#define CRL_MLP_LAYERS 1
-#define CRL_MLP_WHOLE 2
-int32_t crl_set_mlp_fusion(int32_t mode);
 
 /* ---- op-level entry points (stateless; used by torch.autograd.Function) ---
  * Same kernels as the step calls.  dtype: CRL_PREC_FP32 (float) or

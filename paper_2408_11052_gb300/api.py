@@ -97,7 +97,6 @@ _SIGNATURES = {
     "crl_set_launch_overlap": (c_int32, [c_int32]),
     "crl_set_autotune": (c_int32, [c_int32]),
     "crl_set_gemm_kernel": (c_int32, [c_int32]),
-    "crl_set_mlp_fusion": (c_int32, [c_int32]),
     "crl_sweep_create": (c_int32, [POINTER(CrlConfig), c_int32, c_int32, POINTER(c_void_p)]),
     "crl_sweep_destroy": (c_int32, [c_void_p]),
     "crl_sweep_agent": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
@@ -185,16 +184,6 @@ def set_gemm_kernel(mode):
     ("any", "one_tile" or "persistent").  Returns the previous mode's name."""
     prev = lib().crl_set_gemm_kernel(GEMM_KERNEL[mode])
     return {v: k for k, v in GEMM_KERNEL.items()}[prev]
-
-
-MLP_FUSION = {"auto": 0, "layers": 1, "whole": 2}
-
-
-def set_mlp_fusion(mode):
-    """Process-wide: run narrow BF16 forward passes in one launch per layer ("auto",
-    "layers") or in one launch for all layers ("whole").  Returns the previous mode."""
-    prev = lib().crl_set_mlp_fusion(MLP_FUSION[mode])
-    return {v: k for k, v in MLP_FUSION.items()}[prev]
 
 
 def stream_handle(stream=None):

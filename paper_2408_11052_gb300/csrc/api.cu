@@ -24,7 +24,6 @@ thread_local Tracer* g_tracer = nullptr;
 int g_launch_overlap = 1;
 int g_autotune = 1;
 int g_gemm_kernel = CRL_GEMM_ANY;
-int g_mlp_fusion = CRL_MLP_AUTO;
 }
 
 namespace crl {
@@ -969,13 +968,6 @@ int32_t crl_set_autotune(int32_t enable) {
   return prev;
 }
 
-int32_t crl_set_mlp_fusion(int32_t mode) {
-  if (mode < CRL_MLP_AUTO || mode > CRL_MLP_WHOLE) return CRL_E_INVALID_ARG;
-  const int32_t prev = g_mlp_fusion;
-  g_mlp_fusion = mode;
-  return prev;
-}
-
 int32_t crl_set_gemm_kernel(int32_t mode) {
   if (mode < CRL_GEMM_ANY || mode > CRL_GEMM_PERSISTENT) return CRL_E_INVALID_ARG;
   const int32_t prev = g_gemm_kernel;
@@ -1030,10 +1022,15 @@ int crl_trace_stop(crl_ctx* ctx, int32_t* launches, double* total_ms, double* wo
 int crl_mlp_saved_bytes(const crl_mlp_desc* d, int32_t M, size_t* bytes) {
   return guarded(nullptr, [&] {
     CRL_REQUIRE(d && bytes && M >= 1, CRL_E_INVALID_ARG, "bad argument");
-    CRL_REQUIRE(d->dtype == CRL_PREC_FP32 || d->dtype == CRL_PREC_FP64, CRL_E_UNSUPPORTED,
-                "dtype must be CRL_PREC_FP32 or CRL_PREC_FP64");
+    CRL_REQUIRE(d->dtype == CRL_PREC_FP32 || d->dtype == CRL_PREC_FP64 || d->dtype == CRL_PREC_BF16,
+                CRL_E_UNSUPPORTED, "dtype must be CRL_PREC_FP32, CRL_PREC_FP64 or CRL_PREC_BF16");
     MlpShape s{d->in0, d->in1, d->hidden, d->layers, d->out, d->layernorm ? 1 : 0};
-    *bytes = mlp_saved_bytes(s, M, dtype_size(d->dtype));
+    if (d->dtype == CRL_PREC_BF16) {
+      *bytes = mlp_bf16_saved_bytes(s, M);
+      CRL_REQUIRE(*bytes > 0, CRL_E_UNSUPPORTED, "LayerNorm hidden width above 6396 on the BF16 path");
+    } else {
+      *bytes = mlp_saved_bytes(s, M, dtype_size(d->dtype));
+    }
   });
 }
 
@@ -1042,8 +1039,8 @@ MlpShape checked_shape(const crl_mlp_desc* d) {
   CRL_REQUIRE(d, CRL_E_INVALID_ARG, "null descriptor");
   CRL_REQUIRE(d->in0 >= 1 && d->in1 >= 0 && d->hidden >= 1 && d->out >= 1, CRL_E_INVALID_ARG, "bad MLP sizes");
   CRL_REQUIRE(d->layers >= 1 && d->layers <= CRL_MAX_LAYERS, CRL_E_INVALID_ARG, "layers must lie in [1, 8]");
-  CRL_REQUIRE(d->dtype == CRL_PREC_FP32 || d->dtype == CRL_PREC_FP64, CRL_E_UNSUPPORTED,
-              "dtype must be CRL_PREC_FP32 or CRL_PREC_FP64");
+  CRL_REQUIRE(d->dtype == CRL_PREC_FP32 || d->dtype == CRL_PREC_FP64 || d->dtype == CRL_PREC_BF16,
+              CRL_E_UNSUPPORTED, "dtype must be CRL_PREC_FP32, CRL_PREC_FP64 or CRL_PREC_BF16");
   return MlpShape{d->in0, d->in1, d->hidden, d->layers, d->out, d->layernorm ? 1 : 0};
 }
 }  // namespace
@@ -1055,7 +1052,9 @@ int crl_mlp_forward(const crl_mlp_desc* d, const void* params, const float* x0, 
     CRL_REQUIRE(params && x0 && y && saved && M >= 1, CRL_E_INVALID_ARG, "bad argument");
     CRL_REQUIRE(s.in1 == 0 || x1, CRL_E_INVALID_ARG, "x1 is required when in1 > 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (d->dtype == CRL_PREC_FP64)
+    if (d->dtype == CRL_PREC_BF16)
+      mlp_bf16_forward(s, static_cast<const float*>(params), x0, x1, M, static_cast<float*>(y), saved, st);
+    else if (d->dtype == CRL_PREC_FP64)
       mlp_forward<double, float>(s, static_cast<const double*>(params), x0, x1, M, static_cast<double*>(y), saved, st);
     else
       mlp_forward<float, float>(s, static_cast<const float*>(params), x0, x1, M, static_cast<float*>(y), saved, st);
@@ -1070,7 +1069,10 @@ int crl_mlp_backward(const crl_mlp_desc* d, const void* params, const float* x0,
     CRL_REQUIRE(params && x0 && saved && dy && M >= 1, CRL_E_INVALID_ARG, "bad argument");
     CRL_REQUIRE(s.in1 == 0 || x1, CRL_E_INVALID_ARG, "x1 is required when in1 > 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (d->dtype == CRL_PREC_FP64)
+    if (d->dtype == CRL_PREC_BF16)
+      mlp_bf16_backward(s, static_cast<const float*>(params), M, saved, static_cast<const float*>(dy),
+                        static_cast<float*>(dparams), static_cast<float*>(dx0), static_cast<float*>(dx1), st);
+    else if (d->dtype == CRL_PREC_FP64)
       mlp_backward<double, float>(s, static_cast<const double*>(params), x0, x1, M, saved,
                                   static_cast<const double*>(dy), static_cast<double*>(dparams),
                                   static_cast<double*>(dx0), static_cast<double*>(dx1), st);
@@ -1093,9 +1095,9 @@ LossSpec checked_loss(const crl_loss_desc* d) {
   CRL_REQUIRE(d->penalty_axis >= CRL_PENALTY_ROW && d->penalty_axis <= CRL_PENALTY_BOTH, CRL_E_INVALID_ARG,
               "unknown penalty_axis");
   CRL_REQUIRE(d->temperature > 0.f && d->beta_lse >= 0.f, CRL_E_INVALID_ARG, "bad temperature or beta");
-  CRL_REQUIRE(d->dtype == CRL_PREC_FP32 || d->dtype == CRL_PREC_FP64, CRL_E_UNSUPPORTED,
-              "dtype must be CRL_PREC_FP32 or CRL_PREC_FP64");
-  CRL_REQUIRE(d->path == CRL_PATH_PLAIN, CRL_E_UNSUPPORTED, "only the plain path is available in this build");
+  CRL_REQUIRE(((d->dtype == CRL_PREC_FP32 || d->dtype == CRL_PREC_FP64) && d->path == CRL_PATH_PLAIN) ||
+                  (d->dtype == CRL_PREC_BF16 && d->path == CRL_PATH_FUSED),
+              CRL_E_UNSUPPORTED, "dtype / path must be FP32 or FP64 on the plain path, or BF16 on the fused path");
   LossSpec ls;
   ls.energy = d->energy;
   ls.loss = d->loss;
@@ -1113,7 +1115,8 @@ int crl_infonce_workspace_bytes(const crl_loss_desc* d, int32_t B, int32_t R, si
   return guarded(nullptr, [&] {
     const LossSpec ls = checked_loss(d);
     CRL_REQUIRE(bytes && B >= 1 && R >= 1, CRL_E_INVALID_ARG, "bad argument");
-    *bytes = infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path);
+    *bytes = d->dtype == CRL_PREC_BF16 ? infonce_bf16_ws_bytes(B, R)
+                                       : infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path);
   });
 }
 
@@ -1123,11 +1126,16 @@ int crl_infonce_forward(const crl_loss_desc* d, const void* phi, const void* psi
     const LossSpec ls = checked_loss(d);
     CRL_REQUIRE(phi && psi && loss4 && row_lse && col_lse && ws && B >= 1 && R >= 1, CRL_E_INVALID_ARG,
                 "bad argument");
-    CRL_REQUIRE(ws_bytes >= infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path), CRL_E_SHAPE,
-                "workspace too small");
+    CRL_REQUIRE(ws_bytes >= (d->dtype == CRL_PREC_BF16 ? infonce_bf16_ws_bytes(B, R)
+                                                       : infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path)),
+                CRL_E_SHAPE, "workspace too small");
     CRL_REQUIRE(ls.loss != CRL_LOSS_FB || B >= 2, CRL_E_SHAPE, "the forward-backward objective needs B >= 2");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (d->dtype == CRL_PREC_FP64)
+    if (d->dtype == CRL_PREC_BF16)
+      infonce_bf16_forward(ls, static_cast<const float*>(phi), static_cast<const float*>(psi), B, R,
+                           static_cast<float*>(loss4), static_cast<float*>(row_lse), static_cast<float*>(col_lse), ws,
+                           st);
+    else if (d->dtype == CRL_PREC_FP64)
       infonce_forward<double>(ls, static_cast<const double*>(phi), static_cast<const double*>(psi), B, R,
                               static_cast<double*>(loss4), static_cast<double*>(row_lse),
                               static_cast<double*>(col_lse), ws, d->path, nullptr, nullptr, st);
@@ -1146,11 +1154,16 @@ int crl_infonce_backward(const crl_loss_desc* d, const void* phi, const void* ps
     const LossSpec ls = checked_loss(d);
     CRL_REQUIRE(phi && psi && row_lse && col_lse && dphi && dpsi && ws && B >= 1 && R >= 1, CRL_E_INVALID_ARG,
                 "bad argument");
-    CRL_REQUIRE(ws_bytes >= infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path), CRL_E_SHAPE,
-                "workspace too small");
+    CRL_REQUIRE(ws_bytes >= (d->dtype == CRL_PREC_BF16 ? infonce_bf16_ws_bytes(B, R)
+                                                       : infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path)),
+                CRL_E_SHAPE, "workspace too small");
     CRL_REQUIRE(ls.loss != CRL_LOSS_FB || B >= 2, CRL_E_SHAPE, "the forward-backward objective needs B >= 2");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (d->dtype == CRL_PREC_FP64)
+    if (d->dtype == CRL_PREC_BF16)
+      infonce_bf16_backward(ls, static_cast<const float*>(phi), static_cast<const float*>(psi), B, R,
+                            static_cast<const float*>(row_lse), static_cast<const float*>(col_lse), dtotal,
+                            static_cast<float*>(dphi), static_cast<float*>(dpsi), ws, st);
+    else if (d->dtype == CRL_PREC_FP64)
       infonce_backward<double>(ls, static_cast<const double*>(phi), static_cast<const double*>(psi), B, R,
                                static_cast<const double*>(row_lse), static_cast<const double*>(col_lse), dtotal,
                                static_cast<double*>(dphi), static_cast<double*>(dpsi), ws, d->path, st);

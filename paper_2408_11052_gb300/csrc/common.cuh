@@ -108,7 +108,6 @@ __device__ __forceinline__ void pdl_enter() {
 extern int g_launch_overlap;
 extern int g_autotune;
 extern int g_gemm_kernel;  // CRL_GEMM_*
-extern int g_mlp_fusion;   // CRL_MLP_*
 
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -620,6 +620,7 @@ struct BwdArgs {
   bf16* d_outT;            // [R][ldt]
   int ldt;
   unsigned* status;
+  float* d_out_f32;        // non-null: the gradient as FP32 [B][R] here instead of d_out / d_outT
 };
 
 // Offset in a 128-byte-swizzled K-major tile (8-row groups of 1024 bytes) of
@@ -997,19 +998,27 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
       float v[32];
       tc::tmem_ld32(tAcc + lane_off + c, v);
       if (u < a.B) {
-        alignas(16) bf16 o[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
           float d = v[k];
           if (a.energy == CRL_ENERGY_L2 || a.energy == CRL_ENERGY_L2SQ) d -= rs * own[c + k];
           else if (a.energy == CRL_ENERGY_COS) d = (d - own[c + k] * a_own * proj) * a_own;
-          o[k] = __float2bfloat16_rn(d);
+          v[k] = d;
         }
-        uint4* dst = reinterpret_cast<uint4*>(a.d_out + (size_t)u * a.R + c);
+        if (a.d_out_f32 != nullptr) {
+          float4* dst = reinterpret_cast<float4*>(a.d_out_f32 + (size_t)u * a.R + c);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4*>(o)[k];
+          for (int k = 0; k < 8; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        } else {
+          alignas(16) bf16 o[32];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) a.d_outT[(size_t)(c + k) * a.ldt + u] = o[k];
+          for (int k = 0; k < 32; ++k) o[k] = __float2bfloat16_rn(v[k]);
+          uint4* dst = reinterpret_cast<uint4*>(a.d_out + (size_t)u * a.R + c);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4*>(o)[k];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) a.d_outT[(size_t)(c + k) * a.ldt + u] = o[k];
+        }
       }
     }
   } else if (tid == 0) {
@@ -1271,6 +1280,38 @@ void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi
     case kObjNCE: launch_bwd_t<kObjNCE>(e, a, b, n, sm, st); break;
     default: launch_bwd_t<kObjInfo>(e, a, b, n, sm, st); break;
   }
+}
+
+void energy_tc_backward_f32(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi,
+                            const float* r, const float* c, double dtotal, float* dphi, float* dpsi, void* ws,
+                            unsigned* status, cudaStream_t st) {
+  const int n = (B + kTile - 1) / kTile;
+  const size_t sm = bwd_smem(e.R);
+  const FwdArgs f = fwd_args(e, ls, B, ws, nullptr, nullptr, nullptr, nullptr, status);
+  BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, nullptr, nullptr, 0, status, f);
+  a.d_out_f32 = dphi;
+  BwdArgs b = a;
+  b.transposed = 1;
+  b.aux_own = e.auxY;
+  b.aux_other = e.auxX;
+  b.lse_own = c;
+  b.lse_other = r;
+  b.own_f32 = psi;
+  b.d_out_f32 = dpsi;
+  TraceLaunch tr(CRL_TRACE_ENERGY, st, 8.0 * B * B * e.R);
+  switch (obj_kind(ls.loss)) {
+    case kObjFB: launch_bwd_t<kObjFB>(e, a, b, n, sm, st); break;
+    case kObjDPO: launch_bwd_t<kObjDPO>(e, a, b, n, sm, st); break;
+    case kObjIPO: launch_bwd_t<kObjIPO>(e, a, b, n, sm, st); break;
+    case kObjSPPO: launch_bwd_t<kObjSPPO>(e, a, b, n, sm, st); break;
+    case kObjNCE: launch_bwd_t<kObjNCE>(e, a, b, n, sm, st); break;
+    default: launch_bwd_t<kObjInfo>(e, a, b, n, sm, st); break;
+  }
+}
+
+size_t energy_tc_ticket_bytes(int B) {
+  const int n = (B + kTile - 1) / kTile;
+  return (size_t)(2 * n + 1) * 4;
 }
 
 const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& agents, int stage, cudaStream_t st) {

@@ -36,6 +36,14 @@ void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi
                         __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, void* ws, unsigned* status,
                         cudaStream_t st);
 
+// The same backward with dphi / dpsi as FP32 [B][R] (the op-level entry points).
+void energy_tc_backward_f32(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi,
+                            const float* r, const float* c, double dtotal, float* dphi, float* dpsi, void* ws,
+                            unsigned* status, cudaStream_t st);
+// Bytes at the start of the forward's workspace holding its tickets, which must
+// be zero when a forward starts (the CTAs that use them reset them).
+size_t energy_tc_ticket_bytes(int B);
+
 // One agent of a multi-agent launch of the fused energy stage (its maps built
 // by energy_tc_maps for batch B).
 struct EnergyAgent {

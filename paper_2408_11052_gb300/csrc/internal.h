@@ -124,6 +124,23 @@ void infonce_backward(const LossSpec& ls, const T* phi, const T* psi, int B, int
                       const T* col_lse, double dtotal, T* dphi, T* dpsi, void* ws, int path,
                       cudaStream_t st);
 
+// ---------------------------------------------------------------- op-level BF16 (ops_bf16.cu)
+// One encoder on the tensor-core path: params FP32 (flat layout), x0 / x1 /
+// y / dy / dparams / dx0 / dx1 FP32; `saved` (mlp_bf16_saved_bytes) holds the
+// BF16 shadows and activations between a forward and its backward.  Failures throw.
+size_t mlp_bf16_saved_bytes(const MlpShape& s, int M);
+void mlp_bf16_forward(const MlpShape& s, const float* params, const float* x0, const float* x1, int M, float* y,
+                      void* saved, cudaStream_t st);
+void mlp_bf16_backward(const MlpShape& s, const float* params, int M, const void* saved, const float* dy,
+                       float* dparams, float* dx0, float* dx1, cudaStream_t st);
+// The fused energy stage on FP32 representations phi, psi [B][R]; ws
+// (infonce_bf16_ws_bytes) carries the BF16 operands from a forward to its backward.
+size_t infonce_bf16_ws_bytes(int B, int R);
+void infonce_bf16_forward(const LossSpec& ls, const float* phi, const float* psi, int B, int R, float* loss4,
+                          float* row_lse, float* col_lse, void* ws, cudaStream_t st);
+void infonce_bf16_backward(const LossSpec& ls, const float* phi, const float* psi, int B, int R, const float* row_lse,
+                           const float* col_lse, double dtotal, float* dphi, float* dpsi, void* ws, cudaStream_t st);
+
 // ---------------------------------------------------------------- actor head
 // Entropy-coefficient auto-tuning (the rule is a reading; the paper only says the
 // coefficient is tuneable): state == null keeps the fixed alpha.  state[4] =

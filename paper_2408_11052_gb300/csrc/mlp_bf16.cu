@@ -94,13 +94,14 @@ __global__ void __launch_bounds__(256) pack_split_kernel(int rows, const float* 
   }
 }
 
-// Weight shadows: W [out][ncol] (FP32) -> W2 [out][2 kp] = [W_hi | W_lo] with
-// hi = bf16(w), lo = bf16(w - hi), each column written `rep` times (rep = 2 for
-// the first layer, matching the split input), and the single BF16 transpose
-// Wt [ncol][ldt] for the input-gradient product.
-__global__ void __launch_bounds__(256) pack_weights_kernel(int rows, int ncol, int rep, const float* __restrict__ W,
-                                                          bf16* __restrict__ W2, int kp, bf16* __restrict__ Wt,
-                                                          int ldt) {
+// Weight shadows: W [out][ncol] (FP32) -> W2 [out][(nhi + 1) kp] = nhi copies
+// of W_hi, then W_lo, with hi = bf16(w), lo = bf16(w - hi), each column written
+// `rep` times (first layer: rep = 2 matching the split input, nhi = 1; later
+// layers: rep = 1, nhi = 2 for the hi / lo activations), and the single BF16
+// transpose Wt [ncol][ldt] for the input-gradient product.
+__global__ void __launch_bounds__(256) pack_weights_kernel(int rows, int ncol, int rep, int nhi,
+                                                          const float* __restrict__ W, bf16* __restrict__ W2, int kp,
+                                                          bf16* __restrict__ Wt, int ldt) {
   pdl_enter();
   __shared__ float tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -112,10 +113,10 @@ __global__ void __launch_bounds__(256) pack_weights_kernel(int rows, int ncol, i
       v = W[(size_t)row * ncol + col];
       const bf16 hi = __float2bfloat16_rn(v);
       const bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-      bf16* d = W2 + (size_t)row * 2 * kp;
+      bf16* d = W2 + (size_t)row * (nhi + 1) * kp;
       for (int q = 0; q < rep; ++q) {
-        d[rep * col + q] = hi;
-        d[kp + rep * col + q] = lo;
+        for (int c = 0; c < nhi; ++c) d[c * kp + rep * col + q] = hi;
+        d[nhi * kp + rep * col + q] = lo;
       }
     }
     tile[r][tx] = v;
@@ -183,21 +184,30 @@ struct LnFwdNet {
   float* rstd;
   const float* g;
   const float* beta;
-  bf16* h;
+  bf16* h;      // [M][ldh]: hi part in columns [0, H), lo part in [ldh / 2, ldh / 2 + H)
   bf16* hT;
+  int ldh;
 };
 struct LnFwdGroup {
   LnFwdNet n[kMaxGroupNets];
 };
 
-__device__ __forceinline__ uint2 ln_relu_pack(float4 x, float4 gg, float4 bb) {
-  const __nv_bfloat162 p0 = __floats2bfloat162_rn(fmaxf(x.x * gg.x + bb.x, 0.f), fmaxf(x.y * gg.y + bb.y, 0.f));
-  const __nv_bfloat162 p1 = __floats2bfloat162_rn(fmaxf(x.z * gg.z + bb.z, 0.f), fmaxf(x.w * gg.w + bb.w, 0.f));
+// ReLU(x * g + b) of four features as BF16 hi parts (returned) and BF16 lo
+// parts bf16(v - hi) (in lo).
+__device__ __forceinline__ uint2 ln_relu_pack(float4 x, float4 gg, float4 bb, uint2& lo) {
+  const float v0 = fmaxf(x.x * gg.x + bb.x, 0.f), v1 = fmaxf(x.y * gg.y + bb.y, 0.f);
+  const float v2 = fmaxf(x.z * gg.z + bb.z, 0.f), v3 = fmaxf(x.w * gg.w + bb.w, 0.f);
+  const __nv_bfloat162 p0 = __floats2bfloat162_rn(v0, v1);
+  const __nv_bfloat162 p1 = __floats2bfloat162_rn(v2, v3);
+  const __nv_bfloat162 q0 = __floats2bfloat162_rn(v0 - __low2float(p0), v1 - __high2float(p0));
+  const __nv_bfloat162 q1 = __floats2bfloat162_rn(v2 - __low2float(p1), v3 - __high2float(p1));
+  lo = make_uint2(*reinterpret_cast<const uint32_t*>(&q0), *reinterpret_cast<const uint32_t*>(&q1));
   return make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
 }
 
 // LayerNorm forward over rows of z [M][H] (FP32, replaced by zhat), rstd [M],
-// h = ReLU(zhat * g + beta) written as BF16 [M][H] and transposed [H][ldt].
+// h = ReLU(zhat * g + beta) written as BF16 hi / lo parts [M][ldh] and the hi
+// part transposed [H][ldt].
 // NV > 0: the row in registers (NV float4 per lane); NV = 0: three passes.
 template <int NV>
 __global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constant__ LnFwdGroup grp) {
@@ -215,7 +225,8 @@ __global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constan
     float4* zr = reinterpret_cast<float4*>(a.z + (size_t)row * H);
     const float4* g4 = reinterpret_cast<const float4*>(a.g);
     const float4* b4 = reinterpret_cast<const float4*>(a.beta);
-    uint2* hr = reinterpret_cast<uint2*>(a.h + (size_t)row * H);
+    uint2* hr = reinterpret_cast<uint2*>(a.h + (size_t)row * a.ldh);
+    uint2* hl = reinterpret_cast<uint2*>(a.h + (size_t)row * a.ldh + a.ldh / 2);
     uint2* tr = reinterpret_cast<uint2*>(tile + w * S);
     if constexpr (NV > 0) {
       float4 x[NV];
@@ -246,8 +257,10 @@ __global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constan
         xn.z = (x[j].z - mean) * rs;
         xn.w = (x[j].w - mean) * rs;
         zr[q] = xn;
-        const uint2 v = ln_relu_pack(xn, g4[q], b4[q]);
+        uint2 lo;
+        const uint2 v = ln_relu_pack(xn, g4[q], b4[q], lo);
         hr[q] = v;
+        hl[q] = lo;
         tr[q] = v;
       }
     } else {
@@ -272,8 +285,10 @@ __global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constan
         x.z = (x.z - mean) * rs;
         x.w = (x.w - mean) * rs;
         zr[q] = x;
-        const uint2 v = ln_relu_pack(x, g4[q], b4[q]);
+        uint2 lo;
+        const uint2 v = ln_relu_pack(x, g4[q], b4[q], lo);
         hr[q] = v;
+        hl[q] = lo;
         tr[q] = v;
       }
     }
@@ -655,12 +670,13 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
   for (const auto& p : probs)
     if (p.epi.kind == tc::kEpiFwdOutEnergy) min_bn = std::max(min_bn, p.N);
   if (min_bn > 256) return "an energy-operand output layer wider than 256 columns";
-  int cfg = g_autotune ? gg.tuned_bn(key) : 0;
+  const bool tune = g_autotune && gg.allow_tune;
+  int cfg = tune ? gg.tuned_bn(key) : 0;
   if (cfg != 0 && !cfg_allowed(cfg)) cfg = 0;   // tuned under another kernel setting
   if (cfg == 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
-    if (g_autotune && !capturing && g_tracer == nullptr) {
+    if (tune && !capturing && g_tracer == nullptr) {
       cfg = tune_cfg(gg, probs, min_bn, status, st);
       if (cfg) gg.set_tuned_bn(key, cfg);
     }
@@ -732,11 +748,12 @@ void GemmGroups::reset() {
   used_ = cap_ = 0;
 }
 
-const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner) {
+const char* bf_net_carve(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner, bool weight_maps) {
   if (s.layernorm && ln_smem_bytes(s.hidden) > (size_t)kLnMaxSmem) return "LayerNorm hidden width above 6396";
   n.s = s;
   n.Mmax = Mmax;
   n.layers = s.layers;
+  n.tm_M = -1;
   LayerOffsets lay[CRL_MAX_LAYERS + 1];
   mlp_layout(s, lay);
   const int H = s.hidden;
@@ -747,7 +764,8 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
     L.out = lay[l].out;
     L.kin = (l == 0) ? 2 * L.in : L.in;
     L.kp = (L.kin + 63) / 64 * 64;
-    L.in_pad = 2 * L.kp;
+    L.nhi = (l == 0) ? 1 : 2;
+    L.in_pad = (L.nhi + 1) * L.kp;
     L.out_pad = pad8(L.out);
     L.oW = lay[l].W;
     L.ob = lay[l].b;
@@ -756,18 +774,18 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
     L.W = static_cast<bf16*>(A((size_t)L.out * L.in_pad * 2));
     L.Wt = static_cast<bf16*>(A((size_t)L.in * L.out_pad * 2));
     if (!L.W || !L.Wt) return "device allocation failed";
-    if (cudaMemset(L.W, 0, (size_t)L.out * L.in_pad * 2) != cudaSuccess ||
-        cudaMemset(L.Wt, 0, (size_t)L.in * L.out_pad * 2) != cudaSuccess)
-      return "cudaMemset failed";
-    const char* e;
-    if ((e = mk(&L.tmW, L.W, 2 * L.kp, L.out, L.in_pad))) return e;  // B of the forward: [W_hi | W_lo]
-    if ((e = mk(&L.tmWt, L.Wt, L.out, L.in, L.out_pad))) return e;   // B of the input gradient (K = out)
+    if (weight_maps) {
+      const char* e;
+      if ((e = mk(&L.tmW, L.W, L.in_pad, L.out, L.in_pad))) return e;  // B of the forward (see BfLayer)
+      if ((e = mk(&L.tmWt, L.Wt, L.out, L.in, L.out_pad))) return e;   // B of the input gradient (K = out)
+    }
   }
   const int in = s.in(), out = s.out;
+  n.ldh = 2 * ((H + 63) / 64 * 64);
   n.x0 = static_cast<bf16*>(A((size_t)Mmax * pad8(2 * in) * 2));
   n.x0T = static_cast<bf16*>(A((size_t)(2 * in + 1) * Mmax * 2));
   for (int l = 0; l < s.layers; ++l) {
-    n.h[l] = static_cast<bf16*>(A((size_t)Mmax * H * 2));
+    n.h[l] = static_cast<bf16*>(A((size_t)Mmax * n.ldh * 2));
     n.hT[l] = static_cast<bf16*>(A((size_t)(H + 1) * Mmax * 2));
     if (s.layernorm) {
       n.z[l] = static_cast<float*>(A((size_t)Mmax * H * 4));
@@ -779,19 +797,59 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
     const size_t w = (l == s.layers) ? (size_t)pad8(out) : (size_t)H;
     n.dz[l] = static_cast<bf16*>(A((size_t)Mmax * w * 2));
     n.dzT[l] = static_cast<bf16*>(A(w * Mmax * 2));
-    if (cudaMemset(n.dz[l], 0, (size_t)Mmax * w * 2) != cudaSuccess) return "cudaMemset failed";
   }
   if (s.layernorm) {
     n.du = static_cast<float*>(A((size_t)Mmax * H * 4));
     n.ln_partial = static_cast<float*>(A(ln_partial_floats(Mmax, H) * 4));
     n.ln_ticket = static_cast<unsigned*>(A(256));
-    if (!n.du || !n.ln_partial || !n.ln_ticket || cudaMemset(n.ln_ticket, 0, 256) != cudaSuccess)
-      return "LayerNorm workspace set-up failed";
   }
+  if (!n.x0 || !n.x0T || !n.y || (s.layernorm && (!n.du || !n.ln_partial || !n.ln_ticket)))
+    return "device allocation failed";
+  return nullptr;
+}
+
+namespace {
+// Counting allocator for bf_net_bytes: 256-byte aligned offsets from a fake base.
+void* count_alloc(void* owner, size_t bytes) {
+  size_t* off = static_cast<size_t*>(owner);
+  const size_t o = (*off + 255) / 256 * 256;
+  *off = o + bytes;
+  return reinterpret_cast<void*>(uintptr_t(4096) + o);
+}
+}  // namespace
+
+size_t bf_net_bytes(const MlpShape& s, int Mmax) {
+  BfNet n;
+  size_t off = 0;
+  if (bf_net_carve(n, s, Mmax, count_alloc, &off, false)) return 0;
+  return (off + 255) / 256 * 256;
+}
+
+void bf_net_fill_ones(BfNet& n, cudaStream_t st) {
+  const int in = n.s.in(), H = n.s.hidden, Mx = n.Mmax;
+  fill_bf16_kernel<<<ceil_div(Mx, 256), 256, 0, st>>>(n.x0T + (size_t)(2 * in) * Mx, Mx, 1.f);
+  for (int l = 0; l < n.layers; ++l) fill_bf16_kernel<<<ceil_div(Mx, 256), 256, 0, st>>>(n.hT[l] + (size_t)H * Mx, Mx, 1.f);
+}
+
+const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner) {
+  if (const char* e = bf_net_carve(n, s, Mmax, alloc, owner, true)) return e;
+  const int in = s.in(), out = s.out, H = s.hidden;
+  for (int l = 0; l <= s.layers; ++l) {
+    const BfLayer& L = n.L[l];
+    if (cudaMemset(L.W, 0, (size_t)L.out * L.in_pad * 2) != cudaSuccess ||
+        cudaMemset(L.Wt, 0, (size_t)L.in * L.out_pad * 2) != cudaSuccess)
+      return "cudaMemset failed";
+  }
+  for (int l = 0; l <= s.layers; ++l) {
+    const size_t w = (l == s.layers) ? (size_t)pad8(out) : (size_t)H;
+    if (cudaMemset(n.dz[l], 0, (size_t)Mmax * w * 2) != cudaSuccess) return "cudaMemset failed";
+  }
+  for (int l = 0; l < s.layers; ++l)   // the zero columns between the hi and lo halves are read as K
+    if (cudaMemset(n.h[l], 0, (size_t)Mmax * n.ldh * 2) != cudaSuccess) return "cudaMemset failed";
+  if (s.layernorm && cudaMemset(n.ln_ticket, 0, 256) != cudaSuccess) return "LayerNorm workspace set-up failed";
   if (cudaMemset(n.x0, 0, (size_t)Mmax * pad8(2 * in) * 2) != cudaSuccess) return "cudaMemset failed";
   // the ones rows of the transposed activations (never overwritten)
-  fill_bf16_kernel<<<ceil_div(Mmax, 256), 256>>>(n.x0T + (size_t)(2 * in) * Mmax, Mmax, 1.f);
-  for (int l = 0; l < s.layers; ++l) fill_bf16_kernel<<<ceil_div(Mmax, 256), 256>>>(n.hT[l] + (size_t)H * Mmax, Mmax, 1.f);
+  bf_net_fill_ones(n, nullptr);
   if (cudaDeviceSynchronize() != cudaSuccess) return "initialising the ones rows failed";
   return nullptr;
 }
@@ -803,7 +861,7 @@ const char* bf_net_maps(BfNet& n, int M) {
   if ((e = mk(&n.tm_x0A, n.x0, 2 * in, M, pad8(2 * in)))) return e;
   if ((e = mk(&n.tm_x0TB, n.x0T, M, 2 * in + 1, Mx))) return e;
   for (int l = 0; l < n.layers; ++l) {
-    if ((e = mk(&n.tm_hA[l], n.h[l], H, M, H))) return e;
+    if ((e = mk(&n.tm_hA[l], n.h[l], n.ldh, M, n.ldh))) return e;
     if ((e = mk(&n.tm_hTB[l], n.hT[l], M, H + 1, Mx))) return e;
   }
   for (int l = 0; l <= n.layers; ++l) {
@@ -820,7 +878,7 @@ void bf_net_shadow(BfNet& n, const float* params, cudaStream_t st) {
     BfLayer& L = n.L[l];
     TraceLaunch tr(CRL_TRACE_AUX, st, (double)L.out * L.in * 10.0);
     dim3 grid(ceil_div(L.in, 32), ceil_div(L.out, 32));
-    launch_k(pack_weights_kernel, grid, dim3(256), 0, st, L.out, L.in, l == 0 ? 2 : 1, params + L.oW, L.W, L.kp,
+    launch_k(pack_weights_kernel, grid, dim3(256), 0, st, L.out, L.in, l == 0 ? 2 : 1, L.nhi, params + L.oW, L.W, L.kp,
              L.Wt, L.out_pad);
   }
 }
@@ -870,84 +928,23 @@ tc::GemmProblem forward_problem(const BfPass& bp, int l, bool ln) {
     e.out0 = n.z[l];
   } else {
     e = epi_of(tc::kEpiFwdHidden);
-    e.ld0 = H;
+    e.ld0 = n.ldh;
+    e.c0 = n.ldh / 2;
     e.out0 = n.h[l];
     e.ld1 = n.Mmax;
     e.out1 = n.hT[l];
   }
   e.bias = params + L.ob;
-  return problem(A, L.tmW, bp.M, L.out, 2 * L.kp, L.kp / 64, e);
-}
-
-// The whole-network forward kernel takes narrow networks without LayerNorm:
-// hidden widths a multiple of 64 up to 256, every layer's K and N within 256.
-bool mlp_fusable(const BfPass* nets, int count) {
-  for (int k = 0; k < count; ++k) {
-    const BfNet& n = *nets[k].net;
-    if (n.s.layernorm || n.s.hidden % 64 != 0 || n.s.hidden > 256) return false;
-    if (n.s.hidden != nets[0].net->s.hidden) return false;   // one cluster size per launch
-    for (int l = 0; l <= n.layers; ++l)
-      if (n.L[l].out > 256 || n.L[l].kp > 256) return false;
-  }
-  return true;
-}
-
-constexpr int kMlpStages = 3;
-
-void launch_mlp_fused(const tc::GemmProblem* t, int nlayer, int nnet, int ctas, int csize, unsigned* status,
-                      cudaStream_t st) {
-  using S = tc::MlpSmem<kMlpStages>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc::tc_mlp_forward_kernel<kMlpStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         S::kBytes);
-    attr = true;
-  }
-  launch_k_cluster(tc::tc_mlp_forward_kernel<kMlpStages>, dim3(ctas), dim3(192), S::kBytes, st, (unsigned)csize, t,
-                   nlayer, nnet, csize, status);
+  // layer 0: A = the split input (x_hi, x_lo interleaved) against [W_hi | W_lo];
+  // later layers: A = [h_hi | h_lo] against [W_hi | W_hi | W_lo], the A slices
+  // wrapping around: h_hi W_hi + h_lo W_hi + h_hi W_lo
+  return problem(A, L.tmW, bp.M, L.out, L.in_pad, (L.nhi == 1 ? 1 : 2) * L.kp / 64, e);
 }
 
 }  // namespace
 
-const char* bf_forward_layers(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st);
-
-// One grouped pass over every layer: one grouped GEMM launch per layer, or,
-// when asked for (CRL_MLP_WHOLE) and the networks fit it, the whole-network
-// kernel in one launch (a cluster of H / 64 CTAs per 128-row block; identical
-// outputs).
+// One grouped pass over every layer: one grouped GEMM launch per layer.
 const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st) {
-  if (count <= 0) return nullptr;
-  if (g_mlp_fusion != CRL_MLP_WHOLE || !mlp_fusable(nets, count)) return bf_forward_layers(gg, nets, count, status, st);
-  const int layers = nets[0].net->layers;
-  for (int k = 1; k < count; ++k)
-    if (nets[k].net->layers != layers) return bf_forward_layers(gg, nets, count, status, st);
-  // a cluster of H / 64 CTAs per 128-row block, one 64-column slice of every hidden layer each
-  const int csize = nets[0].net->s.hidden / 64;
-  std::vector<tc::GemmProblem> probs;
-  int ctas = 0, nnet = 0;
-  double flops = 0.0;
-  for (int k = 0; k < count; ++k) {
-    if (nets[k].M <= 0) continue;
-    for (int l = 0; l <= layers; ++l) {
-      tc::GemmProblem p = forward_problem(nets[k], l, false);
-      if (l == 0) p.tile_begin = ctas;
-      probs.push_back(p);
-      flops += 2.0 * nets[k].M * nets[k].net->L[l].out * nets[k].net->L[l].in;
-    }
-    ctas += ceil_div(nets[k].M, tc::kBM) * csize;
-    ++nnet;
-  }
-  if (nnet == 0) return nullptr;
-  int tiles = 0;
-  const char* err = nullptr;
-  const tc::GemmProblem* t = gg.table(probs, 0, &tiles, st, &err);
-  if (!t) return err;
-  TraceLaunch tr(CRL_TRACE_GEMM, st, flops);
-  launch_mlp_fused(t, layers + 1, nnet, ctas, csize, status, st);
-  return nullptr;
-}
-
-const char* bf_forward_layers(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st) {
   if (count <= 0) return nullptr;
   const BfNet& n0 = *nets[0].net;
   const int H = n0.s.hidden, layers = n0.layers;
@@ -979,7 +976,7 @@ const char* bf_forward_layers(GemmGroups& gg, const BfPass* nets, int count, uns
         const BfLayer& L = n.L[l];
         const float* pr = nets[k0 + k].params;
         const int M = std::max(nets[k0 + k].M, 0);
-        grp.n[k] = LnFwdNet{M, n.Mmax, n.z[l], n.rstd[l], pr + L.og, pr + L.obeta, n.h[l], n.hT[l]};
+        grp.n[k] = LnFwdNet{M, n.Mmax, n.z[l], n.rstd[l], pr + L.og, pr + L.obeta, n.h[l], n.hT[l], n.ldh};
         Mx = std::max(Mx, M);
         bytes += (double)M * H * 12.0;
       }
@@ -1011,7 +1008,7 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
       const BfLayer& L = n.L[l];
       tc::EpiDesc e = epi_of(ln ? tc::kEpiBwdDXLN : tc::kEpiBwdDX);
       e.mask = n.h[l - 1];
-      e.ldm = H;
+      e.ldm = n.ldh;
       e.ld0 = H;
       if (ln) {
         e.out0 = n.du;
@@ -1083,6 +1080,15 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
       probs.push_back(problem(n.tm_dzA[0], L.tmWt, M, L.in, L.out, 0, e));
       flops += 2.0 * M * L.in * L.out;
     }
+    if (nets[k].dx0) {
+      const BfLayer& L = n.L[0];
+      tc::EpiDesc e = epi_of(tc::kEpiDX0);
+      e.out0 = nets[k].dx0;
+      e.c0 = 0;
+      e.nc = n.s.in0;
+      probs.push_back(problem(n.tm_dzA[0], L.tmWt, M, L.in, L.out, 0, e));
+      flops += 2.0 * M * L.in * L.out;
+    }
   }
   return launch_group(gg, probs, flops, status, st);
 }
@@ -1091,7 +1097,7 @@ namespace {
 
 struct ShadowLayer {
   int64_t oW;
-  int out, in, rep, kp, ldt;
+  int out, in, rep, kp, ldt, nhi, pad_;
   bf16* W2;
   bf16* Wt;
 };
@@ -1118,7 +1124,8 @@ struct AdamUnit {
 };
 
 // Adam on the FP32 master parameters and the refresh of the BF16 shadows:
-// W2 = [W_hi | W_lo] row-major (coalesced along the tile's columns) and Wt
+// W2 (nhi copies of W_hi, then W_lo; see pack_weights_kernel) row-major
+// (coalesced along the tile's columns) and Wt
 // (the transposed single BF16, written through a shared-memory transpose).
 // Bias corrections 1 - b^t = -expm1(t ln b): accurate to a few float ulps
 // where 1 - b^t is small (early steps), unlike 1 - powf(b, t).
@@ -1244,11 +1251,11 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __re
     tile[cc + 2][rr] = __low2bfloat16(h23);
     tile[cc + 3][rr] = __high2bfloat16(h23);
     if (o < L.out) {
-      bf16* d = W2 + (size_t)o * 2 * L.kp;
+      bf16* d = W2 + (size_t)o * (L.nhi + 1) * L.kp;
       if (vec && L.rep == 1) {
-        *reinterpret_cast<uint2*>(d + c) =
-            make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
-        *reinterpret_cast<uint2*>(d + L.kp + c) =
+        const uint2 hv = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+        for (int q = 0; q < L.nhi; ++q) *reinterpret_cast<uint2*>(d + q * L.kp + c) = hv;
+        *reinterpret_cast<uint2*>(d + L.nhi * L.kp + c) =
             make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
       } else {
 #pragma unroll
@@ -1258,8 +1265,8 @@ __global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __re
           const bf16 hj = (j & 1) ? __high2bfloat16(hp) : __low2bfloat16(hp);
           const bf16 lj = (j & 1) ? __high2bfloat16(lp) : __low2bfloat16(lp);
           for (int q = 0; q < L.rep; ++q) {
-            d[L.rep * (c + j) + q] = hj;
-            d[L.kp + L.rep * (c + j) + q] = lj;
+            for (int r = 0; r < L.nhi; ++r) d[r * L.kp + L.rep * (c + j) + q] = hj;
+            d[L.nhi * L.kp + L.rep * (c + j) + q] = lj;
           }
         }
       }
@@ -1315,6 +1322,7 @@ const char* adam_shadow_update(BlobCache& cache, const AdamShadowNet* nets, int 
       sl.out = L.out;
       sl.in = L.in;
       sl.rep = l == 0 ? 2 : 1;
+      sl.nhi = L.nhi;
       sl.kp = L.kp;
       sl.ldt = L.out_pad;
       sl.W2 = L.W;

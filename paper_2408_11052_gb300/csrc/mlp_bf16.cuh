@@ -18,11 +18,17 @@
 // cosine 0.992 instead of 0.9998 on small batches).
 //
 // Forward products use the weights as a BF16 pair W = W_hi + W_lo (W_lo =
-// bf16(W - W_hi)), stored [W_hi | W_lo] along K; each activation tile meets
-// both halves, doubling the forward tensor work.  Rounding the weights to a
-// single BF16 was the next largest error (first-layer weight-gradient cosine
-// 0.998 on 96-wide networks; 0.9993+ with the pair).  The backward uses single
-// BF16 shadows Wt [in][out] (its rounding hardly moves the gradient).
+// bf16(W - W_hi)).  Rounding the weights to a single BF16 was the next largest
+// error (first-layer weight-gradient cosine 0.998 on 96-wide networks; 0.9993+
+// with the pair).  Hidden activations are kept as a BF16 pair too, h = h_hi +
+// h_lo, and the later layers take three products, h_hi W_hi + h_lo W_hi +
+// h_hi W_lo (A = [h_hi | h_lo] against B = [W_hi | W_hi | W_lo], the A slices
+// wrapping around): a single BF16 h moves about 0.05 % of the ReLU decisions
+// of a 4 x 1024 LayerNorm encoder to the other side of zero compared with FP64
+// (CPU emulation: 2247 of 4.2 M units, first-layer weight-gradient cosine
+// 0.9978), the pair about 1e-6 (5 units, cosine 0.999998).  The backward uses
+// single BF16 shadows Wt [in][out] and the hi part of h (its rounding hardly
+// moves the gradient).
 // The backward epilogue likewise writes dz and dz^T.  The shadows are refreshed
 // from the FP32 master weights before each step.
 //
@@ -46,11 +52,13 @@ namespace crl {
 constexpr int kMaxGroupNets = 4;
 
 struct BfLayer {
-  int in, out, in_pad, out_pad;   // pads: multiples of 8 (16-byte rows)
-  int kin;                        // K of the forward product: in, or 2 in for the split first layer
-  int kp;                         // kin rounded up to 64: W_lo starts at column kp
+  int in, out, in_pad, out_pad;   // in_pad: row length of W, (nhi + 1) kp; out_pad: multiple of 8
+  int kin;                        // K of one product: in, or 2 in for the split first layer
+  int kp;                         // kin rounded up to 64
+  int nhi;                        // copies of W_hi before W_lo: 1 (first layer), 2 (later layers)
   int64_t oW, ob, og, obeta;      // offsets into the FP32 master array (og/obeta < 0: no LayerNorm)
-  __nv_bfloat16* W;               // [out][2 kp] = [W_hi | W_lo] (first layer: columns duplicated)
+  __nv_bfloat16* W;               // [out][in_pad]: first layer [W_hi | W_lo] (columns duplicated for the
+                                  // split input); later layers [W_hi | W_hi | W_lo] for A = [h_hi | h_lo]
   __nv_bfloat16* Wt;              // [in][out_pad]
   CUtensorMap tmW, tmWt;
 };
@@ -64,7 +72,8 @@ struct BfNet {
   // activations
   __nv_bfloat16* x0 = nullptr;    // [Mmax][pad8(2 in)]  split input (hi, lo interleaved)
   __nv_bfloat16* x0T = nullptr;   // [2 in + 1][Mmax]    transposed, last row ones
-  __nv_bfloat16* h[CRL_MAX_LAYERS] = {};   // [Mmax][H]
+  int ldh = 0;                             // row length of h: 2 kp(H); hi in [0, H), lo in [ldh / 2, ldh / 2 + H)
+  __nv_bfloat16* h[CRL_MAX_LAYERS] = {};   // [Mmax][ldh] BF16 hi and lo parts of the activations
   __nv_bfloat16* hT[CRL_MAX_LAYERS] = {};  // [H + 1][Mmax], last row ones
   float* z[CRL_MAX_LAYERS] = {};           // LayerNorm: pre-norm [Mmax][H], then zhat in place
   float* rstd[CRL_MAX_LAYERS] = {};        // LayerNorm: [Mmax]
@@ -109,6 +118,11 @@ class GemmGroups {
     return it == tuned_.end() ? 0 : it->second;
   }
   void set_tuned_bn(uint64_t key, int cfg) { tuned_[key] = cfg; }
+  // Number of distinct problem lists with a device table.
+  size_t entries() const { return map_.size(); }
+  // false: never time candidates (fixed rule), for problem lists that change
+  // with every call (the op-level entry points on caller workspaces).
+  bool allow_tune = true;
 
  private:
   std::unordered_map<uint64_t, int> tuned_;
@@ -127,6 +141,13 @@ class GemmGroups {
 // Returns an error message or nullptr.
 using DevAlloc = void* (*)(void* owner, size_t bytes);
 const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner);
+// Only the pointer assignment of bf_net_init (and, with weight_maps, the
+// weight shadows' tensor maps): no memory is touched.
+const char* bf_net_carve(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner, bool weight_maps);
+// Bytes bf_net_carve takes for Mmax rows (256-byte aligned pieces).
+size_t bf_net_bytes(const MlpShape& s, int Mmax);
+// Writes the ones rows of x0T and every hT on stream st.
+void bf_net_fill_ones(BfNet& n, cudaStream_t st);
 // (Re)build the activation tensor maps for batch M (no-op when M is unchanged).
 const char* bf_net_maps(BfNet& n, int M);
 // Refresh W / Wt shadows from the FP32 master parameters.
@@ -157,6 +178,7 @@ struct BfPass {
   float* dx1;     // backward: FP32 gradient of input columns [in0, in0 + in1) as [M][in1], or null
   int M;          // batch rows of this network (its tensor maps built for M)
   const EnergyOut* energy_out = nullptr;   // forward: also write the fused energy's operand
+  float* dx0 = nullptr;   // backward: FP32 gradient of input columns [0, in0) as [M][in0], or null
 };
 // Forward of `count` networks (one grouped launch per layer): y [M][out] FP32 in net->y.
 const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st);

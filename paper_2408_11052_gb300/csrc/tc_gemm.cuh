@@ -36,7 +36,8 @@ constexpr int kBK = 64;
 
 // What the FP32 accumulator tile of a problem becomes.
 enum EpiKind : int {
-  kEpiFwdHidden = 0,  // h = ReLU(acc + b): BF16 h [M][ld0] and h^T [N][ld1]
+  kEpiFwdHidden = 0,  // h = ReLU(acc + b) as BF16 hi / lo parts: h_hi [M][ld0] columns [0, N), h_lo = bf16(h -
+                      // h_hi) at columns [c0, c0 + N) of the same rows, and h_hi^T [N][ld1]
   kEpiFwdPreLN = 1,   // z = acc + b: FP32 [M][ld0] (LayerNorm follows)
   kEpiFwdOut = 2,     // y = acc + b: FP32 [M][ld0]
   kEpiBwdDX = 3,      // dz = acc * [mask > 0]: BF16 dz [M][ld0] and dz^T [N][ld1]
@@ -161,13 +162,20 @@ __device__ __forceinline__ void epilogue_chunk(const EpiDesc& e, int row, int co
         for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + b[i], 0.f);
         store_bf16x32(h + (size_t)row * e.ld0 + col0, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) hT[(size_t)(col0 + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
+        for (int i = 0; i < 32; ++i) {
+          const bf16 o = __float2bfloat16_rn(v[i]);
+          hT[(size_t)(col0 + i) * e.ld1 + row] = o;
+          v[i] -= __bfloat162float(o);
+        }
+        store_bf16x32(h + (size_t)row * e.ld0 + e.c0 + col0, v);
       } else {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           if (col0 + i >= N) break;
-          const bf16 o = __float2bfloat16_rn(fmaxf(v[i] + e.bias[col0 + i], 0.f));
+          const float x = fmaxf(v[i] + e.bias[col0 + i], 0.f);
+          const bf16 o = __float2bfloat16_rn(x);
           h[(size_t)row * e.ld0 + col0 + i] = o;
+          h[(size_t)row * e.ld0 + e.c0 + col0 + i] = __float2bfloat16_rn(x - __bfloat162float(o));
           hT[(size_t)(col0 + i) * e.ld1 + row] = o;
         }
       }
@@ -303,7 +311,8 @@ __device__ __forceinline__ void epilogue_energy(const EpiDesc& e, int row, uint3
 }
 
 // nkA > 0: A has only nkA K-slices and slice kb of B multiplies slice kb % nkA of
-// A -- B holds [W_hi | W_lo] along K and each A tile is used against both halves.
+// A -- B holds the weight pair along K ([W_hi | W_lo], or [W_hi | W_hi | W_lo]
+// against A = [h_hi | h_lo]) and each A tile is used against several parts.
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const GemmProblem* __restrict__ probs, int nprob, unsigned* status) {
@@ -600,254 +609,6 @@ __global__ void __launch_bounds__(192, 1)
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 2 * BN);
-}
-
-// ---- whole-network forward for narrow networks ------------------------------------
-// A cluster of C = H / 64 CTAs per (network, 128-row block) runs every layer of
-// the network's forward in one launch.  In a hidden layer, CTA rank r computes
-// the 64 output columns 64 r .. 64 r + 63 (its 64-row box of the layer's split
-// weights), writes them (bias + ReLU) to h and h^T, and as K slice r of the next
-// layer's A operand into its shared memory (K-major, 128-byte swizzle), which
-// it then copies into the same slice of every other CTA of the cluster (bulk
-// copies between the CTAs' shared memory, completing on the receiver's
-// barrier): after each hidden layer every CTA holds the whole next A.  The A
-// tile is double-buffered, so a slice for layer l + 1 never lands on the A a
-// slower CTA still multiplies in layer l.  The output layer (N <= 256, its
-// epilogue needs whole rows) runs on rank 0 alone, and the last hidden layer's
-// slices go to rank 0 only.  Layer l is problem l of the network's slice of the
-// problem table (the same problems the per-layer launches run: B = the split
-// weights, nkA A slices, the layer's epilogue); layer 0's A is loaded from its
-// tensor map by every CTA.  192 threads: warp 4 lane 0 streams the weights
-// through a STAGES-deep ring, warp 5 lane 0 issues the MMAs, warps 0..3 run the
-// epilogues.  Same products in the same order and the same epilogue arithmetic
-// as the per-layer kernels, so the outputs are identical.  Requirements
-// (checked by the host): hidden width H a multiple of 64 up to 256, every
-// layer's K at most 256 per weight half (4 slices), no LayerNorm.
-constexpr int kMlpMaxSlices = 4;
-
-template <int STAGES>
-struct MlpSmem {
-  static constexpr uint32_t kSlice = kBM * kBK * 2;                     // 16 KiB
-  static constexpr uint32_t kABytes = kMlpMaxSlices * kSlice;           // 64 KiB per A buffer
-  static constexpr uint32_t kBStage = 256 * kBK * 2;                    // 32 KiB (N <= 256)
-  static constexpr uint32_t kBytes = 2 * kABytes + STAGES * kBStage + 1024 + 256;
-  static_assert(kBytes <= 227 * 1024, "shared memory per CTA");
-};
-
-__device__ __forceinline__ uint32_t mlp_sw128_offset(int row, int chunk) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
-}
-
-// The table holds nnet x nlayer problems, network-major; the first problem of
-// network k carries in tile_begin the index of its first CTA (a multiple of csize).
-template <int STAGES>
-__global__ void __launch_bounds__(192, 1)
-    tc_mlp_forward_kernel(const GemmProblem* __restrict__ probs, int nlayer, int nnet, int csize, unsigned* status) {
-  using S = MlpSmem<STAGES>;
-  using bf16 = __nv_bfloat16;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = align1024(smem_raw);
-  uint8_t* sA0 = smem;                    // A buffers: layer l reads buffer l % 2
-  uint8_t* sB = smem + 2 * S::kABytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * S::kBStage);
-  uint64_t* empty = full + STAGES;
-  uint64_t* xfull = empty + STAGES;   // layer 0's A loaded
-  uint64_t* accf = xfull + 1;         // layer l's accumulator ready (phase l)
-  uint64_t* aready = accf + 1;        // [2] A buffer complete: the local slice + the peers' (tx)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(aready + 2);
-  auto abuf = [&](int l) { return sA0 + (l & 1) * S::kABytes; };
-
-  const uint32_t rank = csize > 1 ? cluster_ctarank() : 0u;
-  int lo = 0, hi = nnet - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) / 2;
-    if (probs[(size_t)mid * nlayer].tile_begin <= (int)blockIdx.x) lo = mid;
-    else hi = mid - 1;
-  }
-  const GemmProblem* P = probs + (size_t)lo * nlayer;
-  const int m0 = (((int)blockIdx.x - P[0].tile_begin) / csize) * kBM;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  // this CTA's share of layer l: hidden layers 64 columns at 64 rank; the output layer all N on rank 0
-  auto n_of = [&](int l) { return l < nlayer - 1 ? 64 : (rank == 0 ? P[l].N : 0); };
-  auto n0_of = [&](int l) { return l < nlayer - 1 ? 64 * (int)rank : 0; };
-  // bytes the peers deliver into this CTA's A buffer for layer l >= 1 (the
-  // output layer's input only to rank 0)
-  auto peer_bytes = [&](int l) {
-    return (l < nlayer - 1 || rank == 0) ? (uint32_t)(csize - 1) * S::kSlice : 0u;
-  };
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(xfull, 1);
-    mbar_init(accf, 1);
-    mbar_init(&aready[0], 1);
-    mbar_init(&aready[1], 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) {
-    tmem_alloc(tmem_slot, 256);
-    tmem_relinquish();
-  }
-  fence_before_sync();
-  // every CTA's barriers exist before any peer copies into it
-  if (csize > 1) cluster_sync();
-  else __syncthreads();
-  fence_after_sync();
-  const uint32_t tmem = *tmem_slot;
-  pdl_wait();
-  pdl_trigger();
-
-  if (warp == 4) {
-    if (lane == 0) {
-      // layer 0's A (nkA slices of 128 x 64), then this CTA's weight boxes of every layer
-      const int nkA0 = P[0].nkA;
-      const CUtensorMap* tmA = &P[0].a;
-      tmap_acquire(tmA);
-      mbar_arrive_expect_tx(xfull, (uint32_t)nkA0 * 16384u);
-      for (int ka = 0; ka < nkA0; ++ka)
-        for (int r = 0; r < 2; ++r) tma_load_2d(abuf(0) + ka * 16384 + r * 8192, tmA, xfull, ka * kBK, m0 + 64 * r);
-      int it = 0;
-      bool ok = true;
-      for (int l = 0; l < nlayer && ok; ++l) {
-        const int nn = n_of(l);
-        if (nn == 0) continue;
-        const CUtensorMap* tmB = &P[l].b;
-        tmap_acquire(tmB);
-        const int nk = (P[l].K + kBK - 1) / kBK;
-        const int nbox = (nn + 63) / 64;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
-          const int s = it % STAGES;
-          if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1)) {
-            atomicOr(status, CRL_STATUS_TIMEOUT);
-            ok = false;
-            break;
-          }
-          mbar_arrive_expect_tx(&full[s], (uint32_t)nbox * 8192u);
-          for (int r = 0; r < nbox; ++r)
-            tma_load_2d(sB + s * S::kBStage + r * 8192, tmB, &full[s], kb * kBK, n0_of(l) + 64 * r);
-        }
-      }
-    }
-  } else if (warp == 5) {
-    if (lane == 0) {
-      bool ok = mbar_wait(xfull, 0);
-      if (!ok) atomicOr(status, CRL_STATUS_TIMEOUT);
-      int it = 0;
-      for (int l = 0; l < nlayer && ok; ++l) {
-        const int nn = n_of(l);
-        if (nn == 0) break;
-        // layer l's A complete: this CTA's epilogue of layer l - 1 has written its
-        // slice (and read the accumulator), the peers' slices have landed
-        if (l > 0 && !mbar_wait(&aready[l & 1], ((l - 1) >> 1) & 1)) {
-          atomicOr(status, CRL_STATUS_TIMEOUT);
-          break;
-        }
-        fence_after_sync();
-        const int nk = (P[l].K + kBK - 1) / kBK, nkA = P[l].nkA;
-        const uint32_t idesc = idesc_bf16_f32(kBM, ((nn + 63) / 64) * 64);
-        for (int kb = 0; kb < nk; ++kb, ++it) {
-          const int s = it % STAGES;
-          if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
-            atomicOr(status, CRL_STATUS_TIMEOUT);
-            ok = false;
-            break;
-          }
-          fence_after_sync();
-          const uint64_t da = sdesc_kmajor_sw128(abuf(l) + (kb % nkA) * 16384);
-          const uint64_t db = sdesc_kmajor_sw128(sB + s * S::kBStage);
-#pragma unroll
-          for (int k = 0; k < kBK / 16; ++k) mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-          mma_commit(&empty[s]);
-        }
-        if (ok) mma_commit(accf);
-      }
-    }
-  } else {
-    // epilogue warps 0..3: TMEM lanes 32 w .. (rows of the block)
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int l = 0; l < nlayer; ++l) {
-      const int nn = n_of(l);
-      if (nn == 0) break;
-      // one decision for the four epilogue warps (they meet at named barrier 1 below)
-      const bool ok = named_barrier_and(1, 128, mbar_wait(accf, l & 1));
-      if (!ok) {
-        if (warp == 0 && lane == 0) atomicOr(status, CRL_STATUS_TIMEOUT);
-        break;
-      }
-      fence_after_sync();
-      const EpiDesc e = P[l].epi;
-      const int M = P[l].M, N = P[l].N;
-      if (l == nlayer - 1) {
-        if (e.kind == kEpiFwdOutEnergy) {
-          epilogue_energy(e, row, lane_base, N, M);
-        } else {
-#pragma unroll 1
-          for (int c = 0; c < N; c += 32) {
-            float v[32];
-            tmem_ld32(lane_base + c, v);
-            epilogue_chunk(e, row, c, v, M, N);
-          }
-        }
-        break;
-      }
-      // hidden layer: bias + ReLU of columns n0 .. n0 + 63 to h, h^T and slice `rank` of the next A
-      const int n0 = n0_of(l);
-      bf16* h = static_cast<bf16*>(e.out0);
-      bf16* hT = static_cast<bf16*>(e.out1);
-      uint8_t* as = abuf(l + 1) + rank * S::kSlice;
-#pragma unroll 1
-      for (int c = 0; c < 64; c += 32) {
-        float v[32];
-        tmem_ld32(lane_base + c, v);
-        float b[32];
-        load_bias32(e.bias + n0 + c, b);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + b[i], 0.f);
-        uint32_t w[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-          w[i] = *reinterpret_cast<const uint32_t*>(&p2);
-        }
-        const int ch0 = c / 8;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(as + mlp_sw128_offset(warp * 32 + lane, ch0 + q)) =
-              make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-        if (row < M) {
-          uint4* hr = reinterpret_cast<uint4*>(h + (size_t)row * e.ld0 + n0 + c);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) hr[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) hT[(size_t)(n0 + c + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
-        }
-      }
-      // the generic-proxy writes of the slice visible to the tensor core and to
-      // the bulk copies, the accumulator reads done; then one thread sends the
-      // slice to the peers (rank 0 only for the output layer's input) and arrives
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      fence_before_sync();
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (warp == 0 && lane == 0) {
-        uint64_t* bar = &aready[(l + 1) & 1];
-        const bool last_hidden = l + 1 == nlayer - 1;
-        for (int p = 0; p < csize; ++p) {
-          if (p == (int)rank || (last_hidden && p != 0)) continue;
-          bulk_copy_to_peer(mapa_shared(as, (uint32_t)p), as, S::kSlice, mapa_shared(bar, (uint32_t)p));
-        }
-        mbar_arrive_expect_tx(bar, peer_bytes(l + 1));
-      }
-    }
-  }
-  fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 256);
-  // no CTA leaves while a peer's copy may still read from or write into it
-  if (csize > 1) cluster_sync();
 }
 
 }  // namespace tc

@@ -119,8 +119,7 @@ def header_defines():
 
 
 @pytest.mark.parametrize("table,prefix", [("ENERGY", "ENERGY"), ("LOSS", "LOSS"), ("PREC", "PREC"), ("PATH", "PATH"),
-                                          ("NET", "NET"), ("TRACE", "TRACE"), ("GEMM_KERNEL", "GEMM"),
-                                          ("MLP_FUSION", "MLP")])
+                                          ("NET", "NET"), ("TRACE", "TRACE"), ("GEMM_KERNEL", "GEMM")])
 def test_binding_constants_match_the_header(table, prefix):
     """Every name of the binding's table is the header's CRL_<prefix>_<NAME>, with its value."""
     defines = header_defines()

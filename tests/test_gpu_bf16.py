@@ -293,3 +293,21 @@ def test_fused_critic_full_size_large_batch():
     would be 268 MB in FP32; the fused path never writes it)."""
     ctx, got, ref = run_critic_fused(workload.LARGE_BATCH, n=40, mean_len=None, kink_free=False)
     check_fused(ctx, got, ref)
+
+
+@pytest.mark.parametrize("path", ["plain", "fused"])
+def test_fb_dot_at_unit_temperature_precision_limit(path):
+    """Forward-backward with the unbounded dot energy at tau = 1 (App. A.2's
+    form, the paper's temperature).  Its loss sums exp(2 F_ij) with |F| up to
+    about 10, so it is dominated by a few terms of size e^20, and BF16's
+    absolute error in F (its 8-bit mantissa on values of about 10: ~0.02)
+    becomes a relative error of ~2 dF in each term.  Measured on GB300: loss
+    relative error 3.2e-2 on the fused path and 1.8e-2 on the plain BF16 path
+    (bar 2e-2), every gradient tensor at cosine >= 0.99995.  This test records
+    that limit of the objective x energy in BF16: loss within 4e-2, gradients
+    at the cosine bar."""
+    w = bf16_small(energy="dot", loss="fb", repr=64, tau=1.0)
+    ctx, got, (parts, gphi, gpsi, _, _) = run_critic_fused(w) if path == "fused" else run_critic(w)
+    assert abs(got[0] - parts["total"]) <= 4e-2 * abs(parts["total"])
+    assert_grads_cosine(ctx.network("phi", "grads"), gphi, "phi")
+    assert_grads_cosine(ctx.network("psi", "grads"), gpsi, "psi")

@@ -359,41 +359,8 @@ def test_persistent_gemm_matches_one_tile_gemm(path):
         np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
 
 
-@pytest.mark.parametrize("path,B,hidden,layers", [("fused", 256, 256, 2), ("plain", 200, 256, 2),
-                                                   ("fused", 520, 256, 2), ("fused", 136, 128, 2),
-                                                   ("fused", 96, 64, 2), ("fused", 200, 256, 3),
-                                                   ("plain", 72, 128, 4)])
-def test_whole_network_forward_matches_per_layer_forward(path, B, hidden, layers):
-    """The one-launch forward of narrow networks (a cluster of hidden / 64 CTAs
-    per row block exchanging each layer's activations through shared memory)
-    and the per-layer launches give bit-identical update steps, including the
-    fused energy's operand epilogue, ragged row blocks, clusters of 1, 2 and 4
-    CTAs and deeper networks (both activation buffers reused)."""
-    w = small(B=B, hidden=hidden, layers=layers, repr=64, E=8, T=200)
-    runs = []
-    for mode in ("layers", "whole"):
-        prev = api.set_mlp_fusion(mode)
-        try:
-            ctx, _, _ = setup(w, precision="bf16", path=path, n=150, mean_len=30.0)
-            extra = workload.buffer_contents(w, n=3, mean_len=9.0, seed_offset=7)
-            loss = torch.zeros(6, dtype=torch.float32, device=ctx.device)
-            hist = []
-            for i in range(3):
-                ctx.update_step(*(torch.from_numpy(x[i:i + 1]).to(ctx.device) for x in extra), loss_out=loss)
-                hist.append(loss.cpu().numpy().copy())
-            torch.cuda.synchronize()
-            assert ctx.sync_status() == (0, 0)
-            runs.append((np.array(hist), {n: ctx.store[n]["params"].cpu().numpy() for n in ("phi", "psi", "pi")}))
-        finally:
-            api.set_mlp_fusion(prev)
-    np.testing.assert_array_equal(runs[0][0], runs[1][0])
-    for n in ("phi", "psi", "pi"):
-        np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
-
-
 def test_gemm_kernel_mode_is_validated():
     assert api.lib().crl_set_gemm_kernel(3) == api.E_INVALID_ARG
-    assert api.lib().crl_set_mlp_fusion(3) == api.E_INVALID_ARG
     assert api.set_gemm_kernel("any") == "any"
 
 
