@@ -208,6 +208,17 @@ def oracle_error(w, dev, arms, step=0):
                                              w.energy, tau, alpha)
     oracle_s = time.perf_counter() - t0
 
+    def kink_units(net, x, rel=1e-6):
+        """Hidden units whose pre-activation lies within rel x its layer's RMS of the
+        ReLU kink in the oracle's forward: FP32 arithmetic may put them on either side."""
+        _, cache = oracle.mlp.forward(net, x)
+        return int(sum((np.abs(c["u"]) < rel * np.sqrt((c["u"] ** 2).mean())).sum() for c in cache[:-1]))
+
+    kinks = {"phi": kink_units(n64["phi"], np.concatenate([s, a], 1)), "psi": kink_units(n64["psi"], g),
+             "pi": kink_units(n64["pi"], np.concatenate([s, g], 1)),
+             "phi_at_policy_action": kink_units(n64["phi"], np.concatenate([s, ref_a["a_new"]], 1)),
+             "threshold": "|pre-activation| < 1e-6 x its layer's RMS in the FP64 forward (FP32 may flip the ReLU)"}
+
     def tensors(got, ref, net):
         rows = []
         for li, (gl, rl) in enumerate(zip(got, ref)):
@@ -219,7 +230,8 @@ def oracle_error(w, dev, arms, step=0):
         return rows
 
     out = {"workload": w.name, "batch": f"relabel step {step} of the timed workload's buffer and networks",
-           "oracle": "FP64 numpy, materialised B x B", "oracle_s": oracle_s, "bars": ERROR_BARS}
+           "oracle": "FP64 numpy, materialised B x B", "oracle_s": oracle_s, "bars": ERROR_BARS,
+           "kink_units": kinks}
     for precision, path in arms:
         ctx = api.CRLContext(w, precision=precision, path=path)
         for k, v in nets.items():
@@ -242,9 +254,19 @@ def oracle_error(w, dev, arms, step=0):
              "grad_worst_rel_err": max(t["rel_err"] for t in grads),
              "grad_worst_cos": min(t["cos"] for t in grads), "grads": grads}
         bar = ERROR_BARS[key]
-        loss_ok = max(r["loss_rel_err"].values()) <= bar["loss_rel"]
-        grad_ok = r["grad_worst_cos"] >= bar["grad_cos"] if key == "bf16" else r["grad_worst_rel_err"] <= bar["grad_rel"]
-        r["within_bars"] = bool(loss_ok and grad_ok and r["relabel_indices_exact"] and rc == api.OK)
+
+        def within(tensors, losses):
+            loss_ok = max(r["loss_rel_err"][k] for k in losses) <= bar["loss_rel"]
+            if key == "bf16":
+                return loss_ok and min(t["cos"] for t in tensors) >= bar["grad_cos"]
+            return loss_ok and max(t["rel_err"] for t in tensors) <= bar["grad_rel"]
+
+        crit = [t for t in grads if not t["tensor"].startswith("pi.")]
+        act = [t for t in grads if t["tensor"].startswith("pi.")]
+        r["within_bars_critic"] = bool(within(crit, ("critic_total", "critic_fwd", "critic_bwd", "penalty")))
+        r["within_bars_actor"] = bool(within(act, ("actor",)))
+        r["within_bars"] = bool(r["within_bars_critic"] and r["within_bars_actor"] and r["relabel_indices_exact"]
+                                and rc == api.OK)
         out[f"{precision}_{path}"] = r
         ctx.close()
     return out

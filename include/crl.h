@@ -294,6 +294,18 @@ int crl_set_step(crl_ctx* ctx, uint64_t step);
  * bits) and clear it.  Returns CRL_E_NONFINITE / CRL_E_TIMEOUT when those bits
  * are set, CRL_OK otherwise. */
 int crl_sync_status(crl_ctx* ctx, void* stream, uint32_t* status);
+/* Bound of every device wait of the context's tensor-core kernels (GEMMs and
+ * fused energy stage), in nanoseconds; 0 restores the default of one second
+ * (library extension; the paper has no counterpart).  A wait that runs out
+ * sets CRL_STATUS_TIMEOUT; the kernel then waits (at most a second more) for
+ * its own copies and MMAs in flight, frees its tensor memory and returns, so
+ * the context stays usable: the outputs of that step are undefined and
+ * crl_sync_status reports CRL_E_TIMEOUT.  Limits below 100 us poll without
+ * suspending the waiting thread, so even a limit of a few nanoseconds runs
+ * out.  The limit lives in device memory next to the status word: captured
+ * step graphs see a new value on their next replay.  Synchronises the device
+ * (so not during stream capture: CRL_E_CUDA). */
+int crl_set_wait_limit_ns(crl_ctx* ctx, uint32_t ns);
 /* The entropy coefficient the next actor step will use: exp(log alpha) with
  * auto-tuning, else cfg.alpha.  Synchronous read. */
 int crl_get_alpha(crl_ctx* ctx, float* alpha);

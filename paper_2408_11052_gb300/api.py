@@ -84,6 +84,7 @@ _SIGNATURES = {
     "crl_get_step": (c_int32, [c_void_p, POINTER(c_uint64)]),
     "crl_set_step": (c_int32, [c_void_p, c_uint64]),
     "crl_sync_status": (c_int32, [c_void_p, c_void_p, POINTER(c_uint32)]),
+    "crl_set_wait_limit_ns": (c_int32, [c_void_p, c_uint32]),
     "crl_get_alpha": (c_int32, [c_void_p, POINTER(c_float)]),
     "crl_collect": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "crl_state_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
@@ -392,6 +393,10 @@ class CRLContext:
         if rc not in (OK, E_NONFINITE, E_TIMEOUT):
             check(rc, self.handle)
         return rc, v.value
+
+    def set_wait_limit_ns(self, ns):
+        """Bound of the tensor-core kernels' device waits in ns (0: the default, one second)."""
+        check(lib().crl_set_wait_limit_ns(self.handle, int(ns)), self.handle)
 
     def trace_start(self, kernel_class, max_launches=4096):
         """Time every launch of one kernel class (see TRACE) until ``trace_stop``."""

@@ -954,6 +954,15 @@ int crl_sync_status(crl_ctx* ctx, void* stream, uint32_t* status) {
   return CRL_OK;
 }
 
+int crl_set_wait_limit_ns(crl_ctx* ctx, uint32_t ns) {
+  return guarded(ctx, [&] {
+    CRL_REQUIRE(ctx, CRL_E_INVALID_ARG, "null context");
+    CRL_CHECK_CUDA(cudaDeviceSynchronize());
+    CRL_CHECK_CUDA(cudaMemcpy(&ctx->ctr->wait_ns, &ns, sizeof(ns), cudaMemcpyHostToDevice));
+    ctx->wait_ns = ns;
+  });
+}
+
 const char* crl_last_error(const crl_ctx* ctx) { return ctx ? ctx->err.c_str() : g_thread_error.c_str(); }
 
 int32_t crl_set_launch_overlap(int32_t enable) {

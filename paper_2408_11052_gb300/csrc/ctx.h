@@ -23,7 +23,9 @@ struct Counters {
   int t_critic;                  // Adam step counters (incremented by the loss kernels)
   int t_actor;
   unsigned status;               // CRL_STATUS_* bits
+  unsigned wait_ns;              // bounded-wait limit of the kernels (0: 1 s); read as the word after status
   unsigned ticket_actor;         // last-block ticket of the actor loss kernel (zero between launches)
+  unsigned pad_;
   double alpha[4];               // entropy-coefficient auto-tuning: log alpha, Adam m, v, alpha last used
 };
 
@@ -72,6 +74,7 @@ struct crl_ctx {
   int32_t size_host = 0;
   int64_t total_host = 0;
   Counters* ctr = nullptr;
+  uint32_t wait_ns = 0;     // host copy of ctr->wait_ns (crl_set_wait_limit_ns)
   bool bound = false;
   int bind_generation = 0;  // incremented by crl_bind_params and crl_set_logit_stats (sweeps rebuild)
   crl_net_ptrs nets[3]{};

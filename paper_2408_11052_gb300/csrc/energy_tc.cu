@@ -370,15 +370,18 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   const uint32_t tmem = *tmem_slot;
   pdl_wait();
   pdl_trigger();
+  const unsigned long long lim = tc::wait_limit(a.status);
 
   if (tid == 0) {
     // producer: chunk kb into stage kb % 2 once the MMAs of chunk kb - 2 are done with it
+    int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int st = kb & 1;
-      if (kb >= 2 && !tc::mbar_wait(&empty[st], ((kb >> 1) - 1) & 1)) {
+      if (kb >= 2 && !tc::mbar_wait(&empty[st], ((kb >> 1) - 1) & 1, lim)) {
         atomicOr(a.status, CRL_STATUS_TIMEOUT);
         break;
       }
+      ++issued;
       uint8_t* xs = smem + st * 32768;
       tc::mbar_arrive_expect_tx(&full[st], 32768u);
       for (int r = 0; r < 2; ++r) {
@@ -386,14 +389,14 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
         tc::tma_load_2d(xs + 16384 + r * 8192, tmY, &full[st], kb * 64, j0 + 64 * r);
       }
     }
+    // nothing may land in this CTA's shared memory after it reuses or leaves it
+    tc::drain_ring(full, 2, issued);
   } else if (tid == 32) {
     constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
-    bool good = true;
-    for (int kb = 0; kb < nk && good; ++kb) {
+    for (int kb = 0; kb < nk; ++kb) {
       const int st = kb & 1;
-      if (!tc::mbar_wait(&full[st], (kb >> 1) & 1)) {
+      if (!tc::mbar_wait(&full[st], (kb >> 1) & 1, lim)) {
         atomicOr(a.status, CRL_STATUS_TIMEOUT);
-        good = false;
         break;
       }
       tc::fence_after_sync();
@@ -404,7 +407,9 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
       for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
       if (kb + 2 < nk) tc::mma_commit(&empty[st]);
     }
-    if (good) tc::mma_commit(mma_bar);
+    // always: mma_bar completes once every MMA issued here has (after a timeout
+    // S is incomplete, and the status word says so)
+    tc::mma_commit(mma_bar);
   }
   __syncwarp();
   if (tid < kTile) s_ay[tid] = (j0 + tid < a.B) ? a.auxY[j0 + tid] : 0.f;
@@ -434,7 +439,7 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
       if (J == 0 && i < a.B) a.dpre[i] = d;
     }
   }
-  const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(mma_bar, 0) ? 1 : 0) != 0;
+  const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(mma_bar, 0, lim) ? 1 : 0) != 0;
   tc::fence_after_sync();
   // every warp must agree before the operand smem is reused for the F tile
   const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
@@ -560,6 +565,8 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
       cp[1] = s;
     }
   }
+  // S is freed only after every MMA writing it has completed
+  if (!all_ok && tid == 0) tc::mbar_wait(mma_bar, 0, tc::kDrainLimitNs);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
@@ -787,7 +794,8 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   uint64_t* yfull = bars + 1;  // [2]
   uint64_t* sfull = bars + 3;  // [2]
   uint64_t* hfree = bars + 5;  // acc(v) done: H and the tile's buffer are free
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6);
+  uint64_t* drain = bars + 6;  // every MMA of this CTA has completed (teardown)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7);
   constexpr uint32_t tcols = 512;  // S, S, acc (R <= 256)
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -808,6 +816,7 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
       tc::mbar_init(&sfull[b], 1);
     }
     tc::mbar_init(hfree, 1);
+    tc::mbar_init(drain, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -822,8 +831,11 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
   pdl_wait();
   pdl_trigger();
+  const unsigned long long lim = tc::wait_limit(a.status);
 
+  int last_loaded = -1;           // thread 0: the last other-side tile loaded
   auto load_other = [&](int v) {  // thread 0
+    last_loaded = v;
     uint8_t* dst = Ys + (v & 1) * tbytes;
     tc::mbar_arrive_expect_tx(&yfull[v & 1], tbytes);
     for (int kb = 0; kb < nk; ++kb)
@@ -831,7 +843,7 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
         tc::tma_load_2d(dst + kb * 16384 + rr * 8192, tmOther, &yfull[v & 1], kb * 64, v * kTile + 64 * rr);
   };
   auto issue_s = [&](int v) -> bool {  // thread 32: S(v) = own . other(v)^T into accumulator v % 2
-    if (!tc::mbar_wait(&yfull[v & 1], (v >> 1) & 1)) return false;
+    if (!tc::mbar_wait(&yfull[v & 1], (v >> 1) & 1, lim)) return false;
     tc::fence_after_sync();
     const uint8_t* ys = Ys + (v & 1) * tbytes;
     constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
@@ -853,7 +865,7 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     load_other(0);
     if (nV > 1) load_other(1);
   } else if (tid == 32) {
-    if (!tc::mbar_wait(xload, 0) || !issue_s(0)) atomicOr(a.status, CRL_STATUS_TIMEOUT);
+    if (!tc::mbar_wait(xload, 0, lim) || !issue_s(0)) atomicOr(a.status, CRL_STATUS_TIMEOUT);
   }
   __syncwarp();
 
@@ -898,13 +910,13 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     bool good = true;
     if (tid == 0 && vt >= 1) {
       // acc(vt - 1) done: H and the buffer of tile vt - 1 are free; tile vt + 1 goes there
-      good = tc::mbar_wait(hfree, (vt - 1) & 1);
+      good = tc::mbar_wait(hfree, (vt - 1) & 1, lim);
       if (good && vt + 1 < nV) load_other(vt + 1);
     }
     // coefficient tile H from S(vt): this thread's row r, columns 32 q .. 32 q + 31.
     // One barrier publishes the per-tile arrays and thread 0's wait; every warp
     // reaches every barrier (the decision to stop is block-wide).
-    good = (__all_sync(0xffffffffu, tc::mbar_wait(&sfull[b], (vt >> 1) & 1) ? 1 : 0) != 0) && good;
+    good = (__all_sync(0xffffffffu, tc::mbar_wait(&sfull[b], (vt >> 1) & 1, lim) ? 1 : 0) != 0) && good;
     ok = __syncthreads_and(good ? 1 : 0) != 0;
     if (!ok) break;
     tc::fence_after_sync();
@@ -971,7 +983,8 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     }
     __syncwarp();
   }
-  if (ok) ok = __all_sync(0xffffffffu, tc::mbar_wait(hfree, (nV - 1) & 1) ? 1 : 0) != 0;
+  if (tid == 32) tc::mma_commit(drain);   // completes once every MMA issued by this thread has
+  if (ok) ok = __all_sync(0xffffffffu, tc::mbar_wait(hfree, (nV - 1) & 1, lim) ? 1 : 0) != 0;
   // row sums of the four column groups
   s_red[q * kTile + r] = rowsum;
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
@@ -1023,6 +1036,16 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     }
   } else if (tid == 0) {
     atomicOr(a.status, CRL_STATUS_TIMEOUT);
+  }
+  if (tid == 0) {
+    // teardown: every load issued into this CTA's shared memory has landed and
+    // every MMA has completed before the TMEM is freed and the CTA exits
+    tc::mbar_wait(xload, 0, tc::kDrainLimitNs);
+    for (int b = 0; b < 2; ++b) {
+      const int v = (last_loaded & 1) == b ? last_loaded : last_loaded - 1;
+      if (v >= 0) tc::mbar_wait(&yfull[b], (uint32_t)((v >> 1) & 1), tc::kDrainLimitNs);
+    }
+    tc::mbar_wait(drain, 0, tc::kDrainLimitNs);
   }
   tc::fence_before_sync();
   __syncthreads();

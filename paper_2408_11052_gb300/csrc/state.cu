@@ -61,7 +61,7 @@ int crl_save_state(crl_ctx* ctx, void* host, size_t bytes) {
     StateHeader h;
     memset(&h, 0, sizeof(h));
     h.magic = kStateMagic;
-    h.version = 1;
+    h.version = 2;
     h.E = cf.E;
     h.T = cf.T;
     h.W = ctx->bd.W;
@@ -98,7 +98,7 @@ int crl_load_state(crl_ctx* ctx, const void* host, size_t bytes) {
     const crl_config& cf = ctx->cfg;
     StateHeader h;
     memcpy(&h, host, sizeof(h));
-    CRL_REQUIRE(h.magic == kStateMagic && h.version == 1, CRL_E_INVALID_ARG, "not a state blob of this library");
+    CRL_REQUIRE(h.magic == kStateMagic && h.version == 2, CRL_E_INVALID_ARG, "not a state blob of this library");
     CRL_REQUIRE(h.E == cf.E && h.T == cf.T && h.W == ctx->bd.W && h.D == cf.D && h.A == cf.A && h.G == cf.G,
                 CRL_E_SHAPE, "the state blob was saved from a context of other sizes");
     // the fill is min(total, T) and the device keeps total as int32 (the insert kernel's counter)
@@ -127,6 +127,8 @@ int crl_load_state(crl_ctx* ctx, const void* host, size_t bytes) {
       p += n;
     };
     h2d(ctx->ctr, sizeof(Counters));
+    // the wait limit is a setting of this context, not part of the saved state
+    CRL_CHECK_CUDA(cudaMemcpy(&ctx->ctr->wait_ns, &ctx->wait_ns, sizeof(uint32_t), cudaMemcpyHostToDevice));
     h2d(ctx->ep_start, E * 4);
     h2d(ctx->bstate, 2 * 4);
     h2d(ctx->rows, E * cf.T * (size_t)ctx->bd.W * 4);

@@ -25,7 +25,7 @@ struct crl_sweep {
   int grouped = 0;
   GemmGroups groups;
   BlobCache tables;
-  unsigned* status = nullptr;   // device status word of the launches shared by all agents
+  unsigned* status = nullptr;   // device status word of the launches shared by all agents, then their wait limit
   float* loss_all = nullptr;    // [n][6] float losses of the last step
   std::vector<int> generation;  // agents' bind generations the tables were built for
   cudaGraphExec_t graph = nullptr;
@@ -319,8 +319,9 @@ int crl_sweep_create(const crl_config* cfgs, int32_t n, int32_t grouped, crl_swe
       if (r != CRL_OK) throw Failure(r, std::string("agent ") + std::to_string(i) + ": " + crl_last_error(nullptr));
       sw->agents.push_back(c);
     }
-    CRL_CHECK_CUDA(cudaMalloc(&sw->status, sizeof(unsigned)));
-    CRL_CHECK_CUDA(cudaMemset(sw->status, 0, sizeof(unsigned)));
+    // the status word and, after it, the wait limit of the launches (0: the default)
+    CRL_CHECK_CUDA(cudaMalloc(&sw->status, 2 * sizeof(unsigned)));
+    CRL_CHECK_CUDA(cudaMemset(sw->status, 0, 2 * sizeof(unsigned)));
     CRL_CHECK_CUDA(cudaMalloc(&sw->loss_all, (size_t)6 * n * sizeof(float)));
     CRL_CHECK_CUDA(cudaMemset(sw->loss_all, 0, (size_t)6 * n * sizeof(float)));
   });

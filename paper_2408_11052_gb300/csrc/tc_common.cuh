@@ -4,7 +4,10 @@
 //
 // Every wait is bounded by a %globaltimer limit: a wait that gives up sets
 // CRL_STATUS_TIMEOUT in the device status word and the kernel tears down
-// (frees its TMEM) instead of spinning forever.
+// instead of spinning forever.  Teardown first waits (bounded again) for the
+// CTA's own tensor-memory copies and MMAs still in flight, then frees its TMEM.
+// The limit is the word after the status word (0: the default 1 s), set per
+// context with crl_set_wait_limit_ns.
 #pragma once
 
 #include <cuda.h>
@@ -17,7 +20,9 @@
 namespace crl {
 namespace tc {
 
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // default limit of a wait: 1 s
+constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // teardown: the CTA's own copies and MMAs
+constexpr unsigned long long kPollBelowNs = 100000ull;       // shorter limits poll without suspending
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -58,14 +63,49 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for phase `parity` of `bar`; false if it did not complete within the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Non-suspending test of phase `parity`.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of `bar`; false if it did not complete within
+// `limit` ns.  Limits below kPollBelowNs poll without suspending the thread, so
+// that a short limit runs out even where the phase would complete within one
+// suspension.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit) {
+  if (limit < kPollBelowNs) {
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_test_wait(bar, parity)) {
+      if (globaltimer() - t0 >= limit) return false;
+    }
+    return true;
+  }
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    if (globaltimer() - t0 > limit) return false;
   }
   return true;
+}
+// The wait limit of a launch: the word after its status word, 0 meaning the default.
+__device__ __forceinline__ unsigned long long wait_limit(const unsigned* status) {
+  const unsigned w = *reinterpret_cast<const volatile unsigned*>(status + 1);
+  return w ? (unsigned long long)w : kWaitLimitNs;
+}
+// Teardown of a producer thread: wait for the last loads issued into each of
+// the `stages` ring slots (`issued` loads in all, slot i % stages, phase i / stages).
+__device__ __forceinline__ void drain_ring(uint64_t* full, int stages, int issued) {
+  for (int s = 0; s < stages && s < issued; ++s) {
+    const int last = s + stages * ((issued - 1 - s) / stages);
+    mbar_wait(full + s, (uint32_t)((last / stages) & 1), kDrainLimitNs);
+  }
 }
 
 // ---- TMA ----------------------------------------------------------------------

@@ -368,15 +368,18 @@ __global__ void __launch_bounds__(128, 1)
   // operands come from the predecessor; the epilogue may overwrite what it read
   pdl_wait();
   pdl_trigger();
+  const unsigned long long lim = wait_limit(status);
 
   if (warp == 0 && lane == 0) {
     // TMA producer
+    int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % S::kStages;
-      if (kb >= S::kStages && !mbar_wait(&empty[s], ((kb / S::kStages) & 1) ^ 1)) {
+      if (kb >= S::kStages && !mbar_wait(&empty[s], ((kb / S::kStages) & 1) ^ 1, lim)) {
         atomicOr(status, CRL_STATUS_TIMEOUT);
         break;
       }
+      ++issued;
       mbar_arrive_expect_tx(&full[s], S::kStageBytes);
       // operands arrive as 64-row boxes (8 KiB each); stacked along rows they
       // form the same 128-byte-swizzled K-major tile as one tall box
@@ -388,15 +391,15 @@ __global__ void __launch_bounds__(128, 1)
       for (int r = 0; r < BN / 64; ++r)
         tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kb * kBK, n0 + 64 * r);
     }
+    // nothing may land in this CTA's shared memory after it exits
+    drain_ring(full, S::kStages, issued);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
-    bool ok = true;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % S::kStages;
-      if (!mbar_wait(&full[s], (kb / S::kStages) & 1)) {
+      if (!mbar_wait(&full[s], (kb / S::kStages) & 1, lim)) {
         atomicOr(status, CRL_STATUS_TIMEOUT);
-        ok = false;
         break;
       }
       fence_after_sync();
@@ -409,12 +412,14 @@ __global__ void __launch_bounds__(128, 1)
       }
       mma_commit(&empty[s]);
     }
-    if (ok) mma_commit(done);
+    // always: `done` completes once every MMA issued here has (after a timeout
+    // the accumulator is incomplete, and the status word says so)
+    mma_commit(done);
   }
   __syncwarp();
 
   // epilogue (tcgen05.ld is warp-collective: keep the decision warp-uniform)
-  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0) ? 1 : 0) != 0;
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, lim) ? 1 : 0) != 0;
   fence_after_sync();
   if (ok) {
     const EpiDesc e = P->epi;
@@ -434,6 +439,8 @@ __global__ void __launch_bounds__(128, 1)
   } else if (threadIdx.x == 0) {
     atomicOr(status, CRL_STATUS_TIMEOUT);
   }
+  // the accumulator is freed only after every MMA writing it has completed
+  if (!ok && threadIdx.x == 0) mbar_wait(done, 0, kDrainLimitNs);
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, S::kTmemCols);
@@ -474,7 +481,8 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* empty = full + S::kStages;
   uint64_t* accf = empty + S::kStages;  // [2] accumulator buffer ready (MMA -> epilogue)
   uint64_t* acce = accf + 2;            // [2] accumulator buffer free (epilogue -> MMA), 4 arrivals
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  uint64_t* drain = acce + 2;           // every MMA of this CTA has completed (teardown)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -491,6 +499,7 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 4);
     }
+    mbar_init(drain, 1);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -503,6 +512,7 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = *tmem_slot;
   pdl_wait();
   pdl_trigger();
+  const unsigned long long lim = wait_limit(status);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -520,7 +530,7 @@ __global__ void __launch_bounds__(192, 1)
         tmap_acquire(tmB);
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % S::kStages;
-          if (it >= S::kStages && !mbar_wait(&empty[s], ((it / S::kStages) & 1) ^ 1)) {
+          if (it >= S::kStages && !mbar_wait(&empty[s], ((it / S::kStages) & 1) ^ 1, lim)) {
             atomicOr(status, CRL_STATUS_TIMEOUT);
             ok = false;
             break;
@@ -535,6 +545,8 @@ __global__ void __launch_bounds__(192, 1)
             tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kb * kBK, n0 + 64 * r);
         }
       }
+      // `it` slices were issued (a timed-out one was not): let them all land
+      drain_ring(full, S::kStages, it);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -547,7 +559,7 @@ __global__ void __launch_bounds__(192, 1)
         const int nk = (P->K + kBK - 1) / kBK;
         const int buf = i & 1, use = i >> 1;
         // the epilogue of tile i - 2 must have read this buffer out
-        if (use > 0 && !mbar_wait(&acce[buf], (use - 1) & 1)) {
+        if (use > 0 && !mbar_wait(&acce[buf], (use - 1) & 1, lim)) {
           atomicOr(status, CRL_STATUS_TIMEOUT);
           break;
         }
@@ -555,7 +567,7 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t d = tmem + (uint32_t)(buf * BN);
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % S::kStages;
-          if (!mbar_wait(&full[s], (it / S::kStages) & 1)) {
+          if (!mbar_wait(&full[s], (it / S::kStages) & 1, lim)) {
             atomicOr(status, CRL_STATUS_TIMEOUT);
             ok = false;
             break;
@@ -569,6 +581,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         if (ok) mma_commit(&accf[buf]);
       }
+      mma_commit(drain);   // completes once every MMA issued above has
     }
   } else {
     // epilogue warps (tcgen05.ld is warp-collective: decisions stay warp-uniform)
@@ -576,7 +589,7 @@ __global__ void __launch_bounds__(192, 1)
     int i = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
       const int buf = i & 1, use = i >> 1;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[buf], use & 1) ? 1 : 0) != 0;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[buf], use & 1, lim) ? 1 : 0) != 0;
       if (!ok) {
         if (lane == 0) atomicOr(status, CRL_STATUS_TIMEOUT);
         break;
@@ -606,6 +619,8 @@ __global__ void __launch_bounds__(192, 1)
       if (lane == 0) mbar_arrive(&acce[buf]);
     }
   }
+  // no MMA may still write the accumulators when they are freed
+  if (threadIdx.x == 0) mbar_wait(drain, 0, kDrainLimitNs);
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 2 * BN);

@@ -126,9 +126,9 @@ def test_load_rejects_a_device_fill_that_disagrees_with_the_header():
     w = small(E=4, T=20, B=16)
     ctx = api.CRLContext(w)
     blob = ctx.save_state()
-    # header: magic (8 B), 8 int32, size_host, total_host (int64) = 56 B; counters 64 B;
+    # header: magic (8 B), 8 int32, size_host, total_host (int64) = 56 B; counters 72 B;
     # episode starts E int32; then the device fill {size, total} (int32)
-    off = 56 + 64 + 4 * w.E
+    off = 56 + 72 + 4 * w.E
     assert struct.unpack_from("<ii", blob, off) == (0, 0)
     corrupt = bytearray(blob)
     struct.pack_into("<ii", corrupt, off, w.T, 3)
