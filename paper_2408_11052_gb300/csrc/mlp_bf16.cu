@@ -641,7 +641,7 @@ int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, un
     if (!cfg_allowed(cfg)) continue;
     int tiles = 0;
     const char* err = nullptr;
-    const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err);
+    const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 0);
     if (!t || tiles == 0) continue;
     launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);  // warm-up
     cudaEventRecord(e0, st);
@@ -684,7 +684,7 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
   }
   int tiles = 0;
   const char* err = nullptr;
-  const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err);
+  const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 0);
   if (!t) return err;
   if (tiles == 0) return nullptr;
   TraceLaunch tr(CRL_TRACE_GEMM, st, flops);
@@ -695,13 +695,26 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
 }  // namespace
 
 const tc::GemmProblem* GemmGroups::table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles,
-                                         cudaStream_t st, const char** err) {
+                                         cudaStream_t st, const char** err, bool allow_split) {
+  // split-K: the problems that allow it take the same split, chosen so that the
+  // launch has about two CTAs per SM, with >= 8 K-slices per split
+  int split = 1;
+  if (allow_split && BN > 0) {
+    int mn = 0, cap = 0;
+    for (const auto& p : probs) {
+      mn += ceil_div(p.M, tc::kBM) * ceil_div(p.N, BN);
+      if (p.ksplit_cap > 1) cap = cap == 0 ? p.ksplit_cap : std::min(cap, p.ksplit_cap);
+    }
+    if (cap > 1) split = std::max(1, std::min(cap, (2 * sm_count()) / std::max(mn, 1)));
+  }
   int tiles = 0;
   for (auto& p : probs) {
     if (BN == 0) break;
     p.tiles_n = ceil_div(p.N, BN);
     p.tile_begin = tiles;
-    tiles += ceil_div(p.M, tc::kBM) * p.tiles_n;
+    const int nk = ceil_div(p.K, tc::kBK);
+    p.ksplit = (p.ksplit_cap > 1) ? std::max(1, std::min(split, nk / 8)) : 1;
+    tiles += ceil_div(p.M, tc::kBM) * p.tiles_n * p.ksplit;
   }
   *total_tiles = tiles;
   const size_t bytes = probs.size() * sizeof(tc::GemmProblem);
@@ -780,6 +793,20 @@ const char* bf_net_carve(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, 
       if ((e = mk(&L.tmWt, L.Wt, L.out, L.in, L.out_pad))) return e;   // B of the input gradient (K = out)
     }
   }
+  // split-K buffers of the weight gradients: K = the batch, split in up to 4
+  // parts of >= 2048 rows (smaller batches have enough tiles without it)
+  const int cap = std::max(1, std::min(4, Mmax / 2048));
+  for (int l = 0; l <= s.layers; ++l) {
+    BfLayer& L = n.L[l];
+    L.wsplit_cap = cap;
+    L.wpart = nullptr;
+    L.wtick = nullptr;
+    if (cap < 2) continue;
+    const int N = (l == 0) ? 2 * L.in + 1 : L.in + 1;   // the weight-gradient product's columns
+    L.wpart = static_cast<float*>(A((size_t)cap * round_up(L.out, 128) * round_up(N, 256) * 4));
+    L.wtick = static_cast<unsigned*>(A((size_t)round_up(ceil_div(L.out, 128) * ceil_div(N, 64), 64) * 4));
+    if (!L.wpart || !L.wtick) return "device allocation failed";
+  }
   const int in = s.in(), out = s.out;
   n.ldh = 2 * ((H + 63) / 64 * 64);
   n.x0 = static_cast<bf16*>(A((size_t)Mmax * pad8(2 * in) * 2));
@@ -839,6 +866,11 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
     if (cudaMemset(L.W, 0, (size_t)L.out * L.in_pad * 2) != cudaSuccess ||
         cudaMemset(L.Wt, 0, (size_t)L.in * L.out_pad * 2) != cudaSuccess)
       return "cudaMemset failed";
+    if (L.wtick) {
+      const int N = (l == 0) ? 2 * L.in + 1 : L.in + 1;
+      if (cudaMemset(L.wtick, 0, (size_t)round_up(ceil_div(L.out, 128) * ceil_div(N, 64), 64) * 4) != cudaSuccess)
+        return "cudaMemset failed";
+    }
   }
   for (int l = 0; l <= s.layers; ++l) {
     const size_t w = (l == s.layers) ? (size_t)pad8(out) : (size_t)H;
@@ -1068,6 +1100,11 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
         e.out1 = grads + L.ob;
         if (l == 0) probs.push_back(problem(n.tm_dzTA[0], n.tm_x0TB, L.out, 2 * L.in + 1, M, 0, e));
         else probs.push_back(problem(n.tm_dzTA[l], n.tm_hTB[l - 1], L.out, L.in + 1, M, 0, e));
+        if (L.wsplit_cap > 1) {
+          probs.back().ksplit_cap = L.wsplit_cap;
+          probs.back().part = L.wpart;
+          probs.back().tickets = L.wtick;
+        }
         flops += 2.0 * L.out * (L.in + 1) * M;
       }
     }

@@ -61,6 +61,11 @@ struct BfLayer {
                                   // split input); later layers [W_hi | W_hi | W_lo] for A = [h_hi | h_lo]
   __nv_bfloat16* Wt;              // [in][out_pad]
   CUtensorMap tmW, tmWt;
+  // split-K of the weight-gradient product (K = the batch): partial tiles and
+  // per-tile tickets, for batches large enough to split (wsplit_cap > 1)
+  int wsplit_cap;
+  float* wpart;
+  unsigned* wtick;
 };
 
 // One network's BF16 state for batches of up to Mmax rows.
@@ -107,8 +112,10 @@ class GemmGroups {
   // Fills tiles_n / tile_begin of `probs` for tile width BN and returns the
   // device table; nullptr (and *err) on failure.
   // BN = 0: the problems are uploaded as given (tiles_n / tile_begin untouched).
+  // allow_split: problems with ksplit_cap > 1 split K (the one-tile kernel
+  // only) so that the launch has about two CTAs per SM.
   const tc::GemmProblem* table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles, cudaStream_t st,
-                               const char** err);
+                               const char** err, bool allow_split = false);
   // Frees every table (synchronises the device) and forgets the tuned tile widths.
   void reset();
   // Autotuned configuration (16 x tile width + ring depth) of a problem list,

@@ -64,8 +64,12 @@ struct EpiDesc {
 struct GemmProblem {   // 128-byte aligned by its tensor maps
   CUtensorMap a, b;
   int M, N, K, nkA;   // nkA > 0: split-weight product (see tc_gemm_kernel)
-  int tiles_n, tile_begin, pad0, pad1;
+  int tiles_n, tile_begin;
+  int ksplit;         // > 1: K is split over ksplit CTAs per output tile (one-tile kernel only)
+  int ksplit_cap;     // the most splits the problem's buffers hold (the launch picks ksplit <= it)
   EpiDesc epi;
+  float* part;        // split-K partial tiles [tile][ksplit][128][BN] (FP32)
+  unsigned* tickets;  // split-K arrival count per output tile (zero between launches)
 };
 static_assert(alignof(GemmProblem) >= 64 && sizeof(GemmProblem) % 64 == 0, "problem tables hold aligned tensor maps");
 
@@ -335,14 +339,17 @@ __global__ void __launch_bounds__(128, 1)
     else hi = mid - 1;
   }
   const GemmProblem* P = probs + lo;
-  const int lt = t - P->tile_begin;
+  // split-K: ksplit consecutive CTAs share one output tile, each a K range
+  const int ksplit = P->ksplit > 1 ? P->ksplit : 1;
+  const int lt = (t - P->tile_begin) / ksplit, split = (t - P->tile_begin) % ksplit;
   const int M = P->M, N = P->N, K = P->K, nkA = P->nkA;
   const int m0 = (lt / P->tiles_n) * kBM, n0 = (lt % P->tiles_n) * BN;
   const CUtensorMap* tmA = &P->a;
   const CUtensorMap* tmB = &P->b;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int nk = (K + kBK - 1) / kBK;
+  const int nk_all = (K + kBK - 1) / kBK;
+  const int kb0 = split * nk_all / ksplit, nk = (split + 1) * nk_all / ksplit - kb0;
 
   if (threadIdx.x == 0) {
     tmap_acquire(tmA);
@@ -383,13 +390,14 @@ __global__ void __launch_bounds__(128, 1)
       mbar_arrive_expect_tx(&full[s], S::kStageBytes);
       // operands arrive as 64-row boxes (8 KiB each); stacked along rows they
       // form the same 128-byte-swizzled K-major tile as one tall box
-      const int ka = nkA > 0 ? kb % nkA : kb;
+      const int kg = kb0 + kb;
+      const int ka = nkA > 0 ? kg % nkA : kg;
 #pragma unroll
       for (int r = 0; r < kBM / 64; ++r)
         tma_load_2d(sA + s * S::kABytes + r * 8192, tmA, &full[s], ka * kBK, m0 + 64 * r);
 #pragma unroll
       for (int r = 0; r < BN / 64; ++r)
-        tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kb * kBK, n0 + 64 * r);
+        tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kg * kBK, n0 + 64 * r);
     }
     // nothing may land in this CTA's shared memory after it exits
     drain_ring(full, S::kStages, issued);
@@ -421,7 +429,49 @@ __global__ void __launch_bounds__(128, 1)
   // epilogue (tcgen05.ld is warp-collective: keep the decision warp-uniform)
   const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, lim) ? 1 : 0) != 0;
   fence_after_sync();
-  if (ok) {
+  if (ok && ksplit > 1) {
+    // split-K: store this split's FP32 partial tile; the last CTA of the tile to
+    // arrive adds the ksplit partials in split order (its own from TMEM) and
+    // runs the epilogue, so the result does not depend on which CTA is last
+    __shared__ int s_last;
+    const EpiDesc e = P->epi;
+    const int r = warp * 32 + lane, row = m0 + r;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const int ncol = (N - n0 < BN) ? N - n0 : BN;
+    float* part = P->part + (size_t)lt * ksplit * kBM * BN;
+#pragma unroll 1
+    for (int c = 0; c < ncol; c += 32) {
+      float v[32];
+      tmem_ld32(lane_base + c, v);
+      store_f32x32(part + ((size_t)split * kBM + r) * BN + c, v);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(P->tickets + lt, 1u) == (unsigned)ksplit - 1u) ? 1 : 0;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+#pragma unroll 1
+      for (int c = 0; c < ncol; c += 32) {
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        for (int q = 0; q < ksplit; ++q) {
+          const float4* src = reinterpret_cast<const float4*>(part + ((size_t)q * kBM + r) * BN + c);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float4 x = __ldcg(src + i);
+            v[4 * i] += x.x;
+            v[4 * i + 1] += x.y;
+            v[4 * i + 2] += x.z;
+            v[4 * i + 3] += x.w;
+          }
+        }
+        epilogue_chunk(e, row, n0 + c, v, M, N);
+      }
+      if (threadIdx.x == 0) P->tickets[lt] = 0u;
+    }
+  } else if (ok) {
     const EpiDesc e = P->epi;
     const int row = m0 + warp * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);

@@ -403,3 +403,30 @@ def test_pinned_host_inputs_equal_device_inputs(precision, path):
         np.testing.assert_array_equal(runs[0][0], other[0])
         for n in ("phi", "psi", "pi"):
             np.testing.assert_array_equal(runs[0][1][n], other[1][n])
+
+
+def test_split_k_weight_gradients_are_deterministic_and_match_the_oracle():
+    """Batch 4096 splits the weight-gradient products (K = the batch) in two: the
+    last CTA of each output tile adds the partial tiles in split order, so two
+    identical critic steps give identical bits, and the gradients stay at the
+    BF16 bars against the oracle."""
+    w = small(B=4096, hidden=256, repr=64, E=16, T=400)
+    ctx, nets, buf = setup(w, precision="bf16", path="fused", n=400, mean_len=None)
+    s, a, g, _ = ctx.sample(step=2)
+    runs = []
+    for _ in range(2):
+        loss = ctx.critic_step(s, a, g, apply_update=False).cpu().numpy()
+        runs.append((loss, {n: ctx.store[n]["grads"].cpu().numpy().copy() for n in ("phi", "psi")}))
+    assert ctx.sync_status() == (0, 0)
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    for n in ("phi", "psi"):
+        np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
+    s_o, a_o, g_o, _ = oracle.relabel.sample_relabel(buf, w.seed, 0, 2, w.B, w.goals(), w.gamma)
+    h = hp(w)
+    _, gphi, gpsi, _, _ = oracle.step.critic_loss_and_grad(nets["phi"], nets["psi"], s_o, a_o, g_o, w.energy, h["tau"],
+                                                           w.loss, w.sym_reduction, h["beta"], w.penalty_axis)
+    for net, ref in (("phi", gphi), ("psi", gpsi)):
+        for got_l, ref_l in zip(ctx.network(net, "grads"), ref):
+            for k in ref_l:
+                x, y = got_l[k].ravel(), ref_l[k].ravel()
+                assert x @ y / (np.linalg.norm(x) * np.linalg.norm(y)) >= 0.999, (net, k)
