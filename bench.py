@@ -261,10 +261,10 @@ def oracle_error(w, dev, arms, step=0):
                 return loss_ok and min(t["cos"] for t in tensors) >= bar["grad_cos"]
             return loss_ok and max(t["rel_err"] for t in tensors) <= bar["grad_rel"]
 
-        crit = [t for t in grads if not t["tensor"].startswith("pi.")]
-        act = [t for t in grads if t["tensor"].startswith("pi.")]
-        r["within_bars_critic"] = bool(within(crit, ("critic_total", "critic_fwd", "critic_bwd", "penalty")))
-        r["within_bars_actor"] = bool(within(act, ("actor",)))
+        crit_t = [t for t in grads if not t["tensor"].startswith("pi.")]
+        actor_t = [t for t in grads if t["tensor"].startswith("pi.")]
+        r["within_bars_critic"] = bool(within(crit_t, ("critic_total", "critic_fwd", "critic_bwd", "penalty")))
+        r["within_bars_actor"] = bool(within(actor_t, ("actor",)))
         r["within_bars"] = bool(r["within_bars_critic"] and r["within_bars_actor"] and r["relabel_indices_exact"]
                                 and rc == api.OK)
         out[f"{precision}_{path}"] = r

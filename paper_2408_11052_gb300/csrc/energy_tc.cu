@@ -187,15 +187,16 @@ constexpr int kThreads = 512;
 
 struct FwdArgs {
   int B, R, energy, obj;  // obj: the loss code
+  int n, C, nC;           // tiles per side; column tiles per chunk (at most 64) and chunks per row tile
   float inv_tau;
   const float* auxX;
   const float* auxY;
   const bf16* X;   // [B][R] operand rows (the DPO / IPO anchor F_ii)
   const bf16* Y;
-  float* objpart;  // [nJ][B][2] per-row objective partials over each column tile
+  float* objpart;  // [nC][B][2] per-row objective partials over each column chunk
   float* dpre;     // [B] the anchor F_ii of DPO / IPO (written by the J = 0 tiles)
   float* kd;       // [B] k_i of DPO / IPO (written by the row merges)
-  float* rowpart;  // [nJ][B][2]
+  float* rowpart;  // [nC][B][2] per-row (max, sum) over each column chunk
   float* colpart;  // [nI][B][2]
   float* diag;     // [B]
   unsigned* status;
@@ -206,7 +207,7 @@ struct FwdArgs {
   float* c_out;
   float* loss4;
   int* t_bump;
-  unsigned* tickets;  // [2 n + 1]: per row tile, per column tile, final (zero between launches)
+  unsigned* tickets;  // [2 n + 1]: per row tile (chunks), per column tile (row tiles), final (zero between launches)
   float* tile_part;   // [2][n][3]: per row / column tile (sum of (lse - diag), sum of lse^2, objective value)
 };
 
@@ -318,34 +319,88 @@ __device__ void finalize_loss(const FwdArgs& a, int n) {
   if (a.t_bump) *a.t_bump += 1;
 }
 
-// One 128 x 128 tile (row tile I, column tile J) of an n x n tile grid.
-// global_maps: the tensor maps live in a device table (acquire them first).
-// OBJ: the body also handles the objectives outside InfoNCE (a separate
-// instantiation keeps the InfoNCE one within 64 registers, two CTAs per SM).
+// ---- forward: one CTA per (row tile I, chunk of C column tiles) ------------------
+// 18 warps: warps 0..15 run the epilogue (warp w: TMEM lanes 32 (w % 4) .. + 31,
+// i.e. rows; columns 32 (w / 4) .. + 31 of each 128-wide tile), warp 16 lane 0
+// loads (the row tile X once, then the column tiles Y through a ring of 64-wide
+// K chunks), warp 17 issues the MMAs (S(t) = X Y(t)^T into TMEM buffer t % 2,
+// once the epilogue has read buffer t % 2 of tile t - 2) and owns the TMEM.
+// The epilogue of tile t runs while the MMAs of tile t + 1 fill the other
+// buffer.  Per warp and tile (a 32 x 32 block of F log2(e)): the block maximum
+// M_w is the reference of both sums, so each element takes one exp2:
+// e = 2^(f - M_w), the row sums add e along the thread's 32 columns and the
+// column sums add e down a warp-private shared tile.  When some element of the
+// block lies more than 100 (log2 units) below M_w, the block takes exact
+// per-row and per-column references instead (no term can underflow there).
+// Row statistics run on across the chunk's tiles in registers (online merge);
+// column statistics of the four row quarters merge in shared memory per tile.
+constexpr int kFwdEpiWarps = 16;
+constexpr int kFwdThreads = 32 * (kFwdEpiWarps + 2);
+constexpr int kFwdYStages = 4;     // 16 KiB K chunks of Y in flight
+constexpr float kFwdRange = 100.f;  // log2 units below the block maximum that the shared reference covers
+
+__device__ __forceinline__ void lse2_merge(float& m, float& s, float m2, float s2) {
+  if (s2 <= 0.f) return;
+  if (s <= 0.f) {
+    m = m2;
+    s = s2;
+    return;
+  }
+  const float M = fmaxf(m, m2);
+  s = s * ex2(m - M) + s2 * ex2(m2 - M);
+  m = M;
+}
+__device__ __forceinline__ float warp_min_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Shared memory of the forward (offsets from the 1024-aligned base).
+struct FwdSmem {
+  static constexpr size_t kX = 0;                                             // nk x 16 KiB row tile
+  static constexpr size_t kY = 4 * 16384;                                     // ring of Y chunks
+  static constexpr size_t kBlk = kY + (size_t)kFwdYStages * 16384;           // 16 x [32][33] warp blocks
+  static constexpr size_t kCol = kBlk + (size_t)kFwdEpiWarps * 32 * 33 * 4;  // [2][4][128] (ref, sum)
+  static constexpr size_t kRow = kCol + 2 * 4 * 128 * 2 * 4;                  // [4][128] (m, s)
+  static constexpr size_t kObj = kRow + 4 * 128 * 2 * 4;                      // [4][128] objective (v, k)
+  static constexpr size_t kD = kObj + 4 * 128 * 2 * 4;                        // [128] anchor F_ii
+  static constexpr size_t kBar = kD + 128 * 4;                                // barriers
+  static constexpr size_t kBytes = kBar + 16 * 8 + 1024;
+};
+static_assert(FwdSmem::kBytes <= 227 * 1024, "forward shared memory");
+
 template <bool OBJ>
 __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const FwdArgs& a, int I,
-                                         int J, int n, bool global_maps) {
+                                         int chunk, bool global_maps) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = tc::align1024(smem_raw);
+  const int n = a.n, C = a.C;
   const int nk = a.R / 64;
-  // operands: a two-stage ring of 64-wide K chunks (X chunk, then Y chunk, 16 KiB
-  // each), so that two CTAs fit on an SM at every repr; the F tile reuses it
-  const int nst = nk < 2 ? nk : 2;
-  float* Ft = reinterpret_cast<float*>(smem);  // reused after the MMA: [128][129]
-  const size_t opnd = (size_t)nst * 32768, ftile = (size_t)kTile * 129 * 4;
-  float* part = reinterpret_cast<float*>(smem + (opnd > ftile ? opnd : ftile));  // [2][4][128] (m, s)
-  float* opart = part + 2 * 4 * kTile;                                            // [2][4][128] objective
-  float* s_d = opart + 2 * 4 * kTile;                                             // [128] anchor F_ii
-  float* s_ay = s_d + kTile;                                                       // [128] column auxiliaries
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_ay + kTile);
-  uint64_t* full = bars;        // [2]
-  uint64_t* empty = bars + 2;   // [2]
-  uint64_t* mma_bar = bars + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
+  const int t0 = chunk * C, nt = min(C, n - t0);   // column tiles t0 .. t0 + nt - 1
+  uint8_t* Xs = smem + FwdSmem::kX;
+  uint8_t* Ys = smem + FwdSmem::kY;
+  float* blk_all = reinterpret_cast<float*>(smem + FwdSmem::kBlk);
+  float* colbuf = reinterpret_cast<float*>(smem + FwdSmem::kCol);
+  float* rowbuf = reinterpret_cast<float*>(smem + FwdSmem::kRow);
+  float* objbuf = reinterpret_cast<float*>(smem + FwdSmem::kObj);
+  float* s_d = reinterpret_cast<float*>(smem + FwdSmem::kD);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + FwdSmem::kBar);
+  uint64_t* xfull = bars;                          // [1]
+  uint64_t* yfull = bars + 1;                      // [kFwdYStages]
+  uint64_t* yempty = yfull + kFwdYStages;          // [kFwdYStages]
+  uint64_t* sfull = yempty + kFwdYStages;          // [2] S(t) in TMEM buffer t % 2
+  uint64_t* sfree = sfull + 2;                     // [2] the epilogue has read buffer t % 2 (16 arrivals)
+  uint64_t* drain = sfree + 2;                     // every MMA of this CTA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int lg = warp % 4, q = warp / 4;
-  const int i0 = I * kTile, j0 = J * kTile;
+  const int i0 = I * kTile;
   if (tid == 0) {
     if (global_maps) {
       tc::tmap_acquire(tmX);
@@ -353,15 +408,20 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
     }
     tc::prefetch_tmap(tmX);
     tc::prefetch_tmap(tmY);
-    for (int st = 0; st < 2; ++st) {
-      tc::mbar_init(&full[st], 1);
-      tc::mbar_init(&empty[st], 1);
+    tc::mbar_init(xfull, 1);
+    for (int s = 0; s < kFwdYStages; ++s) {
+      tc::mbar_init(&yfull[s], 1);
+      tc::mbar_init(&yempty[s], 1);
     }
-    tc::mbar_init(mma_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&sfull[b], 1);
+      tc::mbar_init(&sfree[b], kFwdEpiWarps);
+    }
+    tc::mbar_init(drain, 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) {
-    tc::tmem_alloc(tmem_slot, 128);
+  if (warp == kFwdEpiWarps + 1) {
+    tc::tmem_alloc(tmem_slot, 256);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -372,226 +432,315 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   pdl_trigger();
   const unsigned long long lim = tc::wait_limit(a.status);
 
-  if (tid == 0) {
-    // producer: chunk kb into stage kb % 2 once the MMAs of chunk kb - 2 are done with it
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int st = kb & 1;
-      if (kb >= 2 && !tc::mbar_wait(&empty[st], ((kb >> 1) - 1) & 1, lim)) {
-        atomicOr(a.status, CRL_STATUS_TIMEOUT);
-        break;
+  if (warp == kFwdEpiWarps) {
+    if (lane == 0) {
+      // the row tile once, then every column tile's K chunks through the ring
+      tc::mbar_arrive_expect_tx(xfull, (uint32_t)nk * 16384u);
+      for (int kb = 0; kb < nk; ++kb)
+        for (int r = 0; r < 2; ++r) tc::tma_load_2d(Xs + kb * 16384 + r * 8192, tmX, xfull, kb * 64, i0 + 64 * r);
+      int issued = 0;
+      bool ok = true;
+      for (int t = 0; t < nt && ok; ++t) {
+        const int j0 = (t0 + t) * kTile;
+        for (int kb = 0; kb < nk; ++kb) {
+          const int it = t * nk + kb, st = it % kFwdYStages;
+          if (it >= kFwdYStages && !tc::mbar_wait(&yempty[st], ((it / kFwdYStages) - 1) & 1, lim)) {
+            atomicOr(a.status, CRL_STATUS_TIMEOUT);
+            ok = false;
+            break;
+          }
+          ++issued;
+          tc::mbar_arrive_expect_tx(&yfull[st], 16384u);
+          for (int r = 0; r < 2; ++r)
+            tc::tma_load_2d(Ys + st * 16384 + r * 8192, tmY, &yfull[st], kb * 64, j0 + 64 * r);
+        }
       }
-      ++issued;
-      uint8_t* xs = smem + st * 32768;
-      tc::mbar_arrive_expect_tx(&full[st], 32768u);
-      for (int r = 0; r < 2; ++r) {
-        tc::tma_load_2d(xs + r * 8192, tmX, &full[st], kb * 64, i0 + 64 * r);
-        tc::tma_load_2d(xs + 16384 + r * 8192, tmY, &full[st], kb * 64, j0 + 64 * r);
-      }
+      // nothing may land in this CTA's shared memory after it leaves
+      tc::mbar_wait(xfull, 0, tc::kDrainLimitNs);
+      tc::drain_ring(yfull, kFwdYStages, issued);
     }
-    // nothing may land in this CTA's shared memory after it reuses or leaves it
-    tc::drain_ring(full, 2, issued);
-  } else if (tid == 32) {
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int st = kb & 1;
-      if (!tc::mbar_wait(&full[st], (kb >> 1) & 1, lim)) {
-        atomicOr(a.status, CRL_STATUS_TIMEOUT);
+  } else if (warp == kFwdEpiWarps + 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+      bool ok = tc::mbar_wait(xfull, 0, lim);
+      if (!ok) atomicOr(a.status, CRL_STATUS_TIMEOUT);
+      tc::fence_after_sync();
+      for (int t = 0; t < nt && ok; ++t) {
+        const int b = t & 1, use = t >> 1;
+        if (use > 0 && !tc::mbar_wait(&sfree[b], (use - 1) & 1, lim)) {
+          atomicOr(a.status, CRL_STATUS_TIMEOUT);
+          break;
+        }
+        tc::fence_after_sync();
+        for (int kb = 0; kb < nk; ++kb) {
+          const int it = t * nk + kb, st = it % kFwdYStages;
+          if (!tc::mbar_wait(&yfull[st], (it / kFwdYStages) & 1, lim)) {
+            atomicOr(a.status, CRL_STATUS_TIMEOUT);
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint64_t dx = tc::sdesc_kmajor_sw128(Xs + kb * 16384);
+          const uint64_t dy = tc::sdesc_kmajor_sw128(Ys + st * 16384);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            tc::mma_bf16(tmem + (uint32_t)(b * 128), dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
+          tc::mma_commit(&yempty[st]);
+        }
+        if (ok) tc::mma_commit(&sfull[b]);
+      }
+      tc::mma_commit(drain);   // completes once every MMA issued above has
+    }
+  } else {
+    // ---- epilogue warps
+    const int lg = warp % 4, q = warp / 4;
+    const int r = lg * 32 + lane, i = i0 + r;
+    const bool row_ok = i < a.B;
+    const float ax = row_ok ? a.auxX[i] : 0.f;
+    const float k1 = a.inv_tau * kLog2e;
+    float* blk = blk_all + warp * (32 * 33);
+    const bool anchored = OBJ && (a.obj == CRL_LOSS_DPO || a.obj == CRL_LOSS_IPO);
+    if (anchored) {
+      // the anchor F_ii of this CTA's rows: 4 threads per row, R / 4 columns of
+      // the BF16 operand rows each (8 per 16-byte load)
+      const int rr = tid / 4, part4 = tid % 4, ii = i0 + rr;
+      float sxy = 0.f;
+      if (ii < a.B) {
+        const int per = a.R / 4;
+        const uint4* xr = reinterpret_cast<const uint4*>(a.X + (size_t)ii * a.R + part4 * per);
+        const uint4* yr = reinterpret_cast<const uint4*>(a.Y + (size_t)ii * a.R + part4 * per);
+        for (int c = 0; c < per / 8; ++c) {
+          const uint4 xv = xr[c], yv = yr[c];
+          const bf16* xb = reinterpret_cast<const bf16*>(&xv);
+          const bf16* yb = reinterpret_cast<const bf16*>(&yv);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) sxy = fmaf(__bfloat162float(xb[e]), __bfloat162float(yb[e]), sxy);
+        }
+      }
+      sxy += __shfl_xor_sync(0xffffffffu, sxy, 1);
+      sxy += __shfl_xor_sync(0xffffffffu, sxy, 2);
+      if (part4 == 0) {
+        const float d = (ii < a.B) ? energy_of(a.energy, sxy, a.auxX[ii], a.auxY[ii], a.inv_tau) : 0.f;
+        s_d[rr] = d;
+        if (chunk == 0 && ii < a.B) a.dpre[ii] = d;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kFwdEpiWarps));
+    }
+    const float dpair = anchored ? s_d[r] : 0.f;
+    float row_m = -INFINITY, row_s = 0.f;   // this row's running (max, sum) over the chunk, log2 units
+    float vp = 0.f, kp = 0.f;               // objective partials of this row
+    bool good = true;
+    for (int t = 0; t < nt; ++t) {
+      const int b = t & 1;
+      const int J = t0 + t, j0 = J * kTile;
+      // one decision for the four warps of column group q (they share barriers below)
+      const bool ok_t = tc::mbar_wait(&sfull[b], (t >> 1) & 1, lim);
+      good = tc::named_barrier_and(2 + q, 128, ok_t);
+      if (!good) {
+        if (lane == 0) atomicOr(a.status, CRL_STATUS_TIMEOUT);
         break;
       }
       tc::fence_after_sync();
-      const uint8_t* xs = smem + st * 32768;
-      const uint64_t dx = tc::sdesc_kmajor_sw128(xs);
-      const uint64_t dy = tc::sdesc_kmajor_sw128(xs + 16384);
+      float v[32];
+      tc::tmem_ld32(tmem + (uint32_t)(b * 128) + ((uint32_t)(lg * 32) << 16) + q * 32, v);
+      // the buffer may take tile t + 2's MMAs once every warp has read it
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&sfree[b]);
+      // F log2(e) of row r, columns j0 + 32 q + k (-inf outside the batch)
+      const int jb = j0 + q * 32;
+      const int jn = row_ok ? min(32, a.B - jb) : 0;
+      float ay[32];
+      {
+        const float4* a4 = reinterpret_cast<const float4*>(a.auxY + jb);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
-      if (kb + 2 < nk) tc::mma_commit(&empty[st]);
-    }
-    // always: mma_bar completes once every MMA issued here has (after a timeout
-    // S is incomplete, and the status word says so)
-    tc::mma_commit(mma_bar);
-  }
-  __syncwarp();
-  if (tid < kTile) s_ay[tid] = (j0 + tid < a.B) ? a.auxY[j0 + tid] : 0.f;
-  const bool anchored = OBJ && (a.obj == CRL_LOSS_DPO || a.obj == CRL_LOSS_IPO);
-  if (anchored) {
-    // the anchor F_ii of this tile's rows while the MMA runs: 4 threads per row,
-    // each R / 4 columns of the BF16 operand rows (8 per 16-byte load)
-    const int rr = tid / 4, part4 = tid % 4, i = i0 + rr;
-    float sxy = 0.f;
-    if (i < a.B) {
-      const int per = a.R / 4;
-      const uint4* xr = reinterpret_cast<const uint4*>(a.X + (size_t)i * a.R + part4 * per);
-      const uint4* yr = reinterpret_cast<const uint4*>(a.Y + (size_t)i * a.R + part4 * per);
-      for (int c = 0; c < per / 8; ++c) {
-        const uint4 xv = xr[c], yv = yr[c];
-        const bf16* xb = reinterpret_cast<const bf16*>(&xv);
-        const bf16* yb = reinterpret_cast<const bf16*>(&yv);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) sxy = fmaf(__bfloat162float(xb[e]), __bfloat162float(yb[e]), sxy);
+        for (int k = 0; k < 8; ++k) {
+          const float4 x = (jb + 4 * k < a.B) ? __ldg(a4 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+          ay[4 * k] = x.x;
+          ay[4 * k + 1] = x.y;
+          ay[4 * k + 2] = x.z;
+          ay[4 * k + 3] = x.w;
+        }
       }
-    }
-    sxy += __shfl_xor_sync(0xffffffffu, sxy, 1);
-    sxy += __shfl_xor_sync(0xffffffffu, sxy, 2);
-    if (part4 == 0) {
-      const float d = (i < a.B) ? energy_of(a.energy, sxy, a.auxX[i], a.auxY[i], a.inv_tau) : 0.f;
-      s_d[rr] = d;
-      if (J == 0 && i < a.B) a.dpre[i] = d;
-    }
-  }
-  const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(mma_bar, 0, lim) ? 1 : 0) != 0;
-  tc::fence_after_sync();
-  // every warp must agree before the operand smem is reused for the F tile
-  const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
-  const int r = lg * 32 + lane;  // row of this thread within the tile
-  if (all_ok) {
-    // F log2(e) of this thread's row r and columns 32 q .. 32 q + 31 (interior
-    // tiles skip the bounds tests), the row's maximum and sum of 2^(F log2 e - max)
-    const int i = i0 + r;
-    const float ax = (i < a.B) ? a.auxX[i] : 0.f;
-    const float k1 = a.inv_tau * kLog2e;
-    const bool full = i0 + kTile <= a.B && j0 + kTile <= a.B;
-    const int jn = (i < a.B) ? min(32, a.B - (j0 + q * 32)) : 0;  // valid columns of the 32
-    float v[32];
-    tc::tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + q * 32, v);
-    float m2;
-    switch (a.energy) {
-      case CRL_ENERGY_L2: m2 = tile_row<0>(v, ax, s_ay + q * 32, k1, full, jn); break;
-      case CRL_ENERGY_L2SQ: m2 = tile_row<1>(v, ax, s_ay + q * 32, k1, full, jn); break;
-      default: m2 = tile_row<2>(v, ax, s_ay + q * 32, k1, full, jn); break;
-    }
-    float sum = 0.f;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      Ft[r * 129 + q * 32 + k] = v[k];
-      sum += ex2(v[k] - m2);
-    }
-    if (m2 == -INFINITY) sum = 0.f;
-    part[(0 * 4 + q) * kTile + r] = m2 * kLn2;
-    part[(1 * 4 + q) * kTile + r] = sum;
-    if (OBJ && a.obj >= CRL_LOSS_FB) {
-      // this row's objective terms over the thread's 32 columns, F = v[k] ln 2
-      // (one fully unrolled loop per objective keeps v[] in registers)
-#pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] *= kLn2;
-      float vp = 0.f, kp = 0.f;
-      const float d = anchored ? s_d[r] : 0.f;
-      const int jd = i - (j0 + q * 32);                              // the diagonal's column, if here
-      switch (a.obj) {
-        case CRL_LOSS_FB:
-#pragma unroll
-          for (int k = 0; k < 32; ++k)
-            if (k < jn && k != jd) vp += __expf(2.f * v[k]);
-          break;
-        case CRL_LOSS_DPO:
-#pragma unroll
-          for (int k = 0; k < 32; ++k)
-            if (k < jn) {
-              vp += softplusf(v[k] - d);
-              kp += sigmoidf_fast(v[k] - d);
-            }
-          break;
-        case CRL_LOSS_IPO:
-#pragma unroll
-          for (int k = 0; k < 32; ++k)
-            if (k < jn) {
-              const float t = d - v[k] - 1.f;
-              vp += t * t;
-              kp -= 2.f * t;
-            }
-          break;
-        case CRL_LOSS_SPPO:
-#pragma unroll
-          for (int k = 0; k < 32; ++k)
-            if (k < jn) vp += (v[k] + 1.f) * (v[k] + 1.f);
-          break;
-        default:  // NCE-binary
-#pragma unroll
-          for (int k = 0; k < 32; ++k)
-            if (k < jn) vp += softplusf(v[k]);
-          break;
+      float m;
+      const bool full = i0 + kTile <= a.B && j0 + kTile <= a.B;
+      switch (a.energy) {
+        case CRL_ENERGY_L2: m = tile_row<0>(v, ax, ay, k1, full, jn); break;
+        case CRL_ENERGY_L2SQ: m = tile_row<1>(v, ax, ay, k1, full, jn); break;
+        default: m = tile_row<2>(v, ax, ay, k1, full, jn); break;
       }
-      opart[(0 * 4 + q) * kTile + r] = vp;
-      opart[(1 * 4 + q) * kTile + r] = kp;
-    }
-  } else if (tid == 0) {
-    atomicOr(a.status, CRL_STATUS_TIMEOUT);
-  }
-  __syncthreads();
-  if (all_ok) {
-    if (tid < kTile) {
-      // merge the four column-group partials of row tid; a diagonal tile leaves F_ii
-      const int i = i0 + tid;
-      if (I == J && i < a.B) a.diag[i] = Ft[tid * 129 + tid] * kLn2;
-      float m = part[tid], s = part[4 * kTile + tid];
-      for (int g = 1; g < 4; ++g) lse_merge(m, s, part[g * kTile + tid], part[(4 + g) * kTile + tid]);
-      if (i < a.B) {
-        float* rp = a.rowpart + ((size_t)J * a.B + i) * 2;
-        rp[0] = m;
-        rp[1] = s;
-        if (OBJ && a.obj >= CRL_LOSS_FB) {
-          // the four column groups in order
-          float* op = a.objpart + ((size_t)J * a.B + i) * 2;
-          op[0] = opart[tid] + opart[kTile + tid] + opart[2 * kTile + tid] + opart[3 * kTile + tid];
-          op[1] = opart[4 * kTile + tid] + opart[5 * kTile + tid] + opart[6 * kTile + tid] + opart[7 * kTile + tid];
+      float mn = INFINITY;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) mn = fminf(mn, v[k] == -INFINITY ? INFINITY : v[k]);
+      if (J == I && q == lg) {
+        // F_ii: column r of this tile, the thread's element k = lane (selected, not indexed)
+        float dv = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) dv = (k == lane) ? v[k] : dv;
+        if (row_ok) a.diag[i] = dv * kLn2;
+      }
+      if (OBJ && a.obj >= CRL_LOSS_FB) {
+        // this row's objective terms over the 32 columns, F = v[k] ln 2
+        const int jd = i - jb;
+        switch (a.obj) {
+          case CRL_LOSS_FB:
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+              if (k < jn && k != jd) vp += ex2(2.f * v[k]);
+            break;
+          case CRL_LOSS_DPO:
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+              if (k < jn) {
+                const float x = v[k] * kLn2 - dpair;
+                vp += softplusf(x);
+                kp += sigmoidf_fast(x);
+              }
+            break;
+          case CRL_LOSS_IPO:
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+              if (k < jn) {
+                const float x = dpair - v[k] * kLn2 - 1.f;
+                vp += x * x;
+                kp -= 2.f * x;
+              }
+            break;
+          case CRL_LOSS_SPPO:
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+              if (k < jn) {
+                const float x = v[k] * kLn2 + 1.f;
+                vp += x * x;
+              }
+            break;
+          default:  // NCE-binary
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+              if (k < jn) vp += softplusf(v[k] * kLn2);
+            break;
+        }
+      }
+      const float Mw = warp_max_f(m);
+      const float mnw = warp_min_f(mn);
+      float cref, csum;   // this warp's column statistics of column 32 q + lane over its 32 rows
+      if (Mw == -INFINITY) {
+        cref = -INFINITY;   // the block lies outside the batch
+        csum = 0.f;
+      } else if (mnw >= Mw - kFwdRange) {
+        // one exp2 per element against the block maximum (no term underflows)
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const float e = ex2(v[k] - Mw);
+          s += e;
+          blk[lane * 33 + k] = e;
+        }
+        lse2_merge(row_m, row_s, Mw, s);
+        __syncwarp();
+        float c = 0.f;
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) c += blk[rr * 33 + lane];
+        cref = Mw;
+        csum = c;
+        __syncwarp();
+      } else {
+        // wide dynamic range: exact references per row and per column
+        float s = 0.f;
+        if (m != -INFINITY) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) s += ex2(v[k] - m);
+        }
+        lse2_merge(row_m, row_s, m, s);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) blk[lane * 33 + k] = v[k];
+        __syncwarp();
+        float cm = -INFINITY;
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) cm = fmaxf(cm, blk[rr * 33 + lane]);
+        float c = 0.f;
+        if (cm != -INFINITY) {
+#pragma unroll 8
+          for (int rr = 0; rr < 32; ++rr) c += ex2(blk[rr * 33 + lane] - cm);
+        }
+        cref = cm;
+        csum = c;
+        __syncwarp();
+      }
+      // merge the column statistics of the four row quarters of column group q
+      float* cb = colbuf + (size_t)b * (4 * 128 * 2);
+      cb[(lg * 128 + q * 32 + lane) * 2] = cref;
+      cb[(lg * 128 + q * 32 + lane) * 2 + 1] = csum;
+      asm volatile("bar.sync %0, 128;" ::"r"(2 + q));
+      if (lg == 0) {
+        float cm = cb[(q * 32 + lane) * 2], cs = cb[(q * 32 + lane) * 2 + 1];
+#pragma unroll
+        for (int g = 1; g < 4; ++g)
+          lse2_merge(cm, cs, cb[(g * 128 + q * 32 + lane) * 2], cb[(g * 128 + q * 32 + lane) * 2 + 1]);
+        const int j = jb + lane;
+        if (j < a.B) {
+          float* cp = a.colpart + ((size_t)I * a.B + j) * 2;
+          cp[0] = cs > 0.f ? cm * kLn2 : -INFINITY;
+          cp[1] = cs;
         }
       }
     }
-  }
-  __syncthreads();
-  if (all_ok) {
-    // column partials: thread (column c, row group g) over rows 32 g .. 32 g + 31
-    // (F log2 e in the tile; the partials in natural units like the rows')
-    const int c = tid % kTile, g = tid / kTile;
-    const float* col = Ft + (32 * g) * 129 + c;
-    float m2 = -INFINITY;
-#pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) m2 = fmaxf(m2, col[rr * 129]);
-    float sum = 0.f;
-#pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) sum += ex2(col[rr * 129] - m2);
-    if (m2 == -INFINITY) sum = 0.f;
-    part[g * kTile + c] = m2 * kLn2;
-    part[(4 + g) * kTile + c] = sum;
-  }
-  __syncthreads();
-  if (all_ok && tid < kTile) {
-    const int j = j0 + tid;
-    float m = part[tid], s = part[4 * kTile + tid];
-    for (int g = 1; g < 4; ++g) lse_merge(m, s, part[g * kTile + tid], part[(4 + g) * kTile + tid]);
-    if (j < a.B) {
-      float* cp = a.colpart + ((size_t)I * a.B + j) * 2;
-      cp[0] = m;
-      cp[1] = s;
+    // this row's statistics over the chunk: merge the four column groups
+    rowbuf[(q * 128 + r) * 2] = row_m;
+    rowbuf[(q * 128 + r) * 2 + 1] = row_s;
+    if (OBJ) {
+      objbuf[(q * 128 + r) * 2] = vp;
+      objbuf[(q * 128 + r) * 2 + 1] = kp;
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * kFwdEpiWarps));
+    if (good && q == 0 && row_ok) {
+      float mm = rowbuf[r * 2], ss = rowbuf[r * 2 + 1];
+      for (int g = 1; g < 4; ++g) lse2_merge(mm, ss, rowbuf[(g * 128 + r) * 2], rowbuf[(g * 128 + r) * 2 + 1]);
+      float* rp = a.rowpart + ((size_t)chunk * a.B + i) * 2;
+      rp[0] = ss > 0.f ? mm * kLn2 : -INFINITY;
+      rp[1] = ss;
+      if (OBJ && a.obj >= CRL_LOSS_FB) {
+        // the four column groups in order
+        float* op = a.objpart + ((size_t)chunk * a.B + i) * 2;
+        op[0] = objbuf[r * 2] + objbuf[(128 + r) * 2] + objbuf[(256 + r) * 2] + objbuf[(384 + r) * 2];
+        op[1] = objbuf[r * 2 + 1] + objbuf[(128 + r) * 2 + 1] + objbuf[(256 + r) * 2 + 1] +
+                objbuf[(384 + r) * 2 + 1];
+      }
     }
   }
-  // S is freed only after every MMA writing it has completed
-  if (!all_ok && tid == 0) tc::mbar_wait(mma_bar, 0, tc::kDrainLimitNs);
+  // teardown: every MMA has completed before the TMEM is freed
+  if (tid == 0) tc::mbar_wait(drain, 0, tc::kDrainLimitNs);
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 128);
-  // Finalize without any CTA waiting for another: the last CTA of row tile I
-  // merges its rows' partials, the last of column tile J its columns', and the
-  // CTA completing the last of the 2 n merges adds the tiles' loss partials.
-  __shared__ int s_row, s_col, s_fin;
+  if (warp == kFwdEpiWarps + 1) tc::tmem_dealloc(tmem, 256);
+  // Finalize without any CTA waiting for another: the last of the nC chunks of
+  // row tile I merges its rows' partials, the last of the n row tiles covering
+  // column tile J its columns', and the CTA completing the last of the 2 n
+  // merges adds the tiles' loss partials.
+  __shared__ int s_row, s_fin;
+  __shared__ int s_col[64];
   __threadfence();
   __syncthreads();
-  if (tid == 0) {
-    s_row = (atomicAdd(a.tickets + I, 1u) == (unsigned)n - 1u) ? 1 : 0;
-    s_col = (atomicAdd(a.tickets + n + J, 1u) == (unsigned)n - 1u) ? 1 : 0;
+  if (tid == 0) s_row = (atomicAdd(a.tickets + I, 1u) == (unsigned)a.nC - 1u) ? 1 : 0;
+  if (tid < nt) s_col[tid] = (atomicAdd(a.tickets + n + t0 + tid, 1u) == (unsigned)n - 1u) ? 1 : 0;
+  __syncthreads();
+  int ncol_merge = 0;
+  for (int t = 0; t < nt; ++t) ncol_merge += s_col[t];
+  if (!s_row && ncol_merge == 0) return;
+  __threadfence();
+  if (s_row) merge_tile(a, I, a.nC, false);
+  for (int t = 0; t < nt; ++t) {
+    if (!s_col[t]) continue;
+    __syncthreads();
+    merge_tile(a, t0 + t, n, true);
   }
-  __syncthreads();
-  if (!s_row && !s_col) return;
-  __threadfence();
-  if (s_row) merge_tile(a, I, n, false);
-  __syncthreads();
-  if (s_col) merge_tile(a, J, n, true);
   __threadfence();
   __syncthreads();
   if (tid == 0) {
     if (s_row) a.tickets[I] = 0u;
-    if (s_col) a.tickets[n + J] = 0u;
-    const unsigned add = (unsigned)(s_row + s_col);
+    for (int t = 0; t < nt; ++t)
+      if (s_col[t]) a.tickets[n + t0 + t] = 0u;
+    const unsigned add = (unsigned)(s_row + ncol_merge);
     s_fin = (atomicAdd(a.tickets + 2 * n, add) + add == (unsigned)(2 * n)) ? 1 : 0;
   }
   __syncthreads();
@@ -603,10 +752,10 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
 }
 
 template <bool OBJ>
-__global__ void __launch_bounds__(kThreads, 2) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                                   const __grid_constant__ CUtensorMap tmY,
-                                                                   const __grid_constant__ FwdArgs a) {
-  fwd_body<OBJ>(&tmX, &tmY, a, blockIdx.y, blockIdx.x, gridDim.x, false);
+__global__ void __launch_bounds__(kFwdThreads, 1) fwd_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                             const __grid_constant__ CUtensorMap tmY,
+                                                             const __grid_constant__ FwdArgs a) {
+  fwd_body<OBJ>(&tmX, &tmY, a, blockIdx.x / a.nC, blockIdx.x % a.nC, false);
 }
 
 // ---- backward ---------------------------------------------------------------------
@@ -1082,11 +1231,11 @@ __global__ void __launch_bounds__(1024) prep_multi_kernel(const EnergyTask* __re
 }
 
 template <bool OBJ>
-__global__ void __launch_bounds__(kThreads, 2) fwd_multi_kernel(const EnergyTask* __restrict__ tasks,
-                                                                         const int* __restrict__ begin, int n) {
+__global__ void __launch_bounds__(kFwdThreads, 1) fwd_multi_kernel(const EnergyTask* __restrict__ tasks,
+                                                                   const int* __restrict__ begin, int n) {
   int lb, nb;
   const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];
-  fwd_body<OBJ>(&t.tmX, &t.tmY, t.f, lb / t.n, lb % t.n, t.n, true);
+  fwd_body<OBJ>(&t.tmX, &t.tmY, t.f, lb / t.f.nC, lb % t.f.nC, true);
 }
 
 template <int OBJ>
@@ -1098,9 +1247,36 @@ __global__ void __launch_bounds__(kThreads, 1) bwd_multi_kernel(const EnergyTask
 }
 
 size_t fwd_smem(int R) {
-  const int nk = R / 64;
-  const size_t opnd = (size_t)(nk < 2 ? nk : 2) * 32768, ftile = (size_t)kTile * 129 * 4;
-  return (opnd > ftile ? opnd : ftile) + (2 * 2 * 4 + 2) * kTile * 4 + 1024 + 64;
+  (void)R;
+  return FwdSmem::kBytes;
+}
+
+int energy_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 152;
+  }
+  return n;
+}
+
+// Column tiles per forward CTA for an n x n tile grid: the chunk that minimises
+// (waves of n * ceil(n / C) CTAs at one CTA per SM) x (C + 3), the 3 standing
+// for a CTA's fixed cost (operand fill, last epilogue, merges) in tile times.
+int fwd_chunk_tiles(int n) {
+  const int sms = energy_sm_count();
+  int best = 1;
+  long long best_cost = -1;
+  for (int C = 1; C <= std::min(n, 64); ++C) {
+    const long long ctas = (long long)n * ((n + C - 1) / C);
+    const long long cost = ((ctas + sms - 1) / sms) * (C + 3);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = C;
+    }
+  }
+  return best;
 }
 size_t bwd_smem(int R) {
   // own tile, two other tiles, H (then the row-sum partials), three per-tile arrays, barriers, alignment
@@ -1124,6 +1300,9 @@ FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* 
   memset(&f, 0, sizeof(f));
   f.B = B;
   f.R = e.R;
+  f.n = n;
+  f.C = fwd_chunk_tiles(n);
+  f.nC = (n + f.C - 1) / f.C;
   f.energy = ls.energy;
   f.obj = ls.loss;
   f.inv_tau = (float)(1.0 / ls.tau);
@@ -1239,8 +1418,10 @@ void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, flo
     attr = true;
   }
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * B * e.R);
-  if (ls.loss >= CRL_LOSS_FB) launch_k(fwd_kernel<true>, dim3(n, n), dim3(kThreads), sm, st, e.tmX, e.tmY, a);
-  else launch_k(fwd_kernel<false>, dim3(n, n), dim3(kThreads), sm, st, e.tmX, e.tmY, a);
+  if (ls.loss >= CRL_LOSS_FB)
+    launch_k(fwd_kernel<true>, dim3(n * a.nC), dim3(kFwdThreads), sm, st, e.tmX, e.tmY, a);
+  else
+    launch_k(fwd_kernel<false>, dim3(n * a.nC), dim3(kFwdThreads), sm, st, e.tmX, e.tmY, a);
 }
 
 namespace {
@@ -1369,7 +1550,7 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     t.col.own_f32 = g.psi;
     t.col.d_out = g.dpsi;
     t.col.d_outT = g.dpsiT;
-    const int nb = stage == 0 ? 2 * ceil_div(g.B, 32) : (stage == 1 ? t.n * t.n : 2 * t.n);
+    const int nb = stage == 0 ? 2 * ceil_div(g.B, 32) : (stage == 1 ? t.n * t.f.nC : 2 * t.n);
     begin[i + 1] = begin[i] + nb;
     Rmax = std::max(Rmax, e.R);
     work += (stage == 1 ? 2.0 : 8.0) * g.B * g.B * e.R * (stage == 0 ? 0.0 : 1.0);
@@ -1391,8 +1572,8 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     }
     bool obj = false;
     for (const EnergyAgent& g : agents) obj = obj || g.ls.loss >= CRL_LOSS_FB;
-    if (obj) launch_k(fwd_multi_kernel<true>, dim3(begin[na]), dim3(kThreads), fwd_smem(Rmax), st, dt, db, na);
-    else launch_k(fwd_multi_kernel<false>, dim3(begin[na]), dim3(kThreads), fwd_smem(Rmax), st, dt, db, na);
+    if (obj) launch_k(fwd_multi_kernel<true>, dim3(begin[na]), dim3(kFwdThreads), fwd_smem(Rmax), st, dt, db, na);
+    else launch_k(fwd_multi_kernel<false>, dim3(begin[na]), dim3(kFwdThreads), fwd_smem(Rmax), st, dt, db, na);
   } else {
     // one launch per objective kind present (the agents of one kind in a table of their own)
     int kinds = 0;
