@@ -708,6 +708,7 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
       }
     }
   }
+  __syncwarp();   // the loader and MMA warps reconverge after their single-lane loops
   // teardown: every MMA has completed before the TMEM is freed
   if (tid == 0) tc::mbar_wait(drain, 0, tc::kDrainLimitNs);
   tc::fence_before_sync();
