@@ -238,36 +238,63 @@ __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2
   m = M;
 }
 
-// Merge the nJ partials of the 128 rows (col = false) or columns (col = true)
-// of tile T into the logsumexps and this tile's loss partials.  One block.
-__device__ void merge_tile(const FwdArgs& a, int T, int n, bool col) {
-  __shared__ float s_red[2][32];
-  const int B = a.B;
-  __shared__ float s_obj[32];
+// Merge the npart partials of the 128 rows (col = false) or columns (col = true)
+// of tile T into the logsumexps and this tile's loss partials.  One block of
+// 512 threads: thread (item k, quarter q) merges partials q, q + 4, ... of item
+// k (independent loads in flight), then the quarters merge in order.
+constexpr int kMergeThreads = 512;
+__device__ void merge_tile(const FwdArgs& a, int T, int npart, bool col) {
+  __shared__ float s_q[4][4][kTile];   // per quarter: m, s, objective v, objective k
+  __shared__ float s_red[3][kMergeThreads / 32];
+  const int B = a.B, n = a.n;
   const float* part = col ? a.colpart : a.rowpart;
   const bool objrows = !col && a.obj >= CRL_LOSS_FB;
-  float sd = 0.f, s2 = 0.f, so = 0.f;
-  for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
-    const int i = T * kTile + k;
-    if (i >= B) continue;
-    float m = -INFINITY, s = 0.f;
-    for (int P = 0; P < n; ++P) {
+  const int k = threadIdx.x % kTile, qd = threadIdx.x / kTile;
+  const int i = T * kTile + k;
+  float m = -INFINITY, s = 0.f, vp = 0.f, kp = 0.f;
+  if (i < B) {
+    int P = qd;
+    for (; P + 12 < npart; P += 16) {
+      float pm[4], ps[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float* p = part + ((size_t)(P + 4 * u) * B + i) * 2;
+        pm[u] = __ldcg(p);
+        ps[u] = __ldcg(p + 1);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) lse_merge(m, s, pm[u], ps[u]);
+    }
+    for (; P < npart; P += 4) {
       const float* p = part + ((size_t)P * B + i) * 2;
       lse_merge(m, s, __ldcg(p), __ldcg(p + 1));
+    }
+    if (objrows)
+      for (int Q = qd; Q < npart; Q += 4) {
+        const float* p = a.objpart + ((size_t)Q * B + i) * 2;
+        vp += __ldcg(p);
+        kp += __ldcg(p + 1);
+      }
+  }
+  s_q[qd][0][k] = m;
+  s_q[qd][1][k] = s;
+  s_q[qd][2][k] = vp;
+  s_q[qd][3][k] = kp;
+  __syncthreads();
+  float sd = 0.f, s2 = 0.f, so = 0.f;
+  if (qd == 0 && i < B) {
+    for (int g = 1; g < 4; ++g) {
+      lse_merge(m, s, s_q[g][0][k], s_q[g][1][k]);
+      vp += s_q[g][2][k];
+      kp += s_q[g][3][k];
     }
     const float l = m + __logf(s);
     (col ? a.c_out : a.r_out)[i] = l;
     const float d = __ldcg(a.diag + i);
-    sd += l - d;
-    s2 += l * l;
+    sd = l - d;
+    s2 = l * l;
     if (objrows) {
-      float vp = 0.f, kp = 0.f;
-      for (int P = 0; P < n; ++P) {
-        const float* p = a.objpart + ((size_t)P * B + i) * 2;
-        vp += __ldcg(p);
-        kp += __ldcg(p + 1);
-      }
-      so += objective_share(a.obj, B, vp, d);
+      so = objective_share(a.obj, B, vp, d);
       if (a.obj == CRL_LOSS_DPO || a.obj == CRL_LOSS_IPO) a.kd[i] = kp / ((float)B * (float)B);
     }
   }
@@ -278,17 +305,17 @@ __device__ void merge_tile(const FwdArgs& a, int T, int n, bool col) {
   if (lane == 0) {
     s_red[0][w] = sd;
     s_red[1][w] = s2;
-    s_obj[w] = so;
+    s_red[2][w] = so;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    for (int k = 0; k < (int)(blockDim.x / 32); ++k) {
-      a0 += s_red[0][k];
-      a1 += s_red[1][k];
-      a2 += s_obj[k];
+    for (int u = 0; u < kMergeThreads / 32; ++u) {
+      a0 += s_red[0][u];
+      a1 += s_red[1][u];
+      a2 += s_red[2][u];
     }
-    float* tp = a.tile_part + ((size_t)(col ? 1 : 0) * n + T) * 3;
+    float* tp = a.tile_part + ((size_t)(col ? n : 0) + T) * 3;
     tp[0] = a0;
     tp[1] = a1;
     tp[2] = a2;
@@ -318,6 +345,31 @@ __device__ void finalize_loss(const FwdArgs& a, int n) {
   if (a.status && !isfinite(total)) atomicOr(a.status, CRL_STATUS_NONFINITE);
   if (a.t_bump) *a.t_bump += 1;
 }
+
+// The forward's finalize: blocks [0, n) merge the row tiles' chunk partials,
+// blocks [n, 2 n) the column tiles' row-tile partials, and the block completing
+// the last merge adds the tiles' loss partials in tile order.
+__device__ __forceinline__ void fwd_finalize_body(const FwdArgs& a, int lb) {
+  const int n = a.n;
+  const bool col = lb >= n;
+  merge_tile(a, col ? lb - n : lb, col ? n : a.nC, col);
+  __shared__ int s_fin;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_fin = (atomicAdd(a.tickets + 2 * n, 1u) == (unsigned)(2 * n) - 1u) ? 1 : 0;
+  __syncthreads();
+  if (s_fin && threadIdx.x == 0) {
+    __threadfence();
+    finalize_loss(a, n);
+    a.tickets[2 * n] = 0u;
+  }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) fwd_finalize_kernel(const __grid_constant__ FwdArgs a) {
+  pdl_enter();
+  fwd_finalize_body(a, blockIdx.x);
+}
+
 
 // ---- forward: one CTA per (row tile I, chunk of C column tiles) ------------------
 // 18 warps: warps 0..15 run the epilogue (warp w: TMEM lanes 32 (w % 4) .. + 31,
@@ -714,42 +766,6 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
   tc::fence_before_sync();
   __syncthreads();
   if (warp == kFwdEpiWarps + 1) tc::tmem_dealloc(tmem, 256);
-  // Finalize without any CTA waiting for another: the last of the nC chunks of
-  // row tile I merges its rows' partials, the last of the n row tiles covering
-  // column tile J its columns', and the CTA completing the last of the 2 n
-  // merges adds the tiles' loss partials.
-  __shared__ int s_row, s_fin;
-  __shared__ int s_col[64];
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_row = (atomicAdd(a.tickets + I, 1u) == (unsigned)a.nC - 1u) ? 1 : 0;
-  if (tid < nt) s_col[tid] = (atomicAdd(a.tickets + n + t0 + tid, 1u) == (unsigned)n - 1u) ? 1 : 0;
-  __syncthreads();
-  int ncol_merge = 0;
-  for (int t = 0; t < nt; ++t) ncol_merge += s_col[t];
-  if (!s_row && ncol_merge == 0) return;
-  __threadfence();
-  if (s_row) merge_tile(a, I, a.nC, false);
-  for (int t = 0; t < nt; ++t) {
-    if (!s_col[t]) continue;
-    __syncthreads();
-    merge_tile(a, t0 + t, n, true);
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    if (s_row) a.tickets[I] = 0u;
-    for (int t = 0; t < nt; ++t)
-      if (s_col[t]) a.tickets[n + t0 + t] = 0u;
-    const unsigned add = (unsigned)(s_row + ncol_merge);
-    s_fin = (atomicAdd(a.tickets + 2 * n, add) + add == (unsigned)(2 * n)) ? 1 : 0;
-  }
-  __syncthreads();
-  if (s_fin && tid == 0) {
-    __threadfence();
-    finalize_loss(a, n);
-    a.tickets[2 * n] = 0u;
-  }
 }
 
 template <bool OBJ>
@@ -1239,6 +1255,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1) fwd_multi_kernel(const EnergyT
   fwd_body<OBJ>(&t.tmX, &t.tmY, t.f, lb / t.f.nC, lb % t.f.nC, true);
 }
 
+__global__ void __launch_bounds__(kMergeThreads) fwd_finalize_multi_kernel(const EnergyTask* __restrict__ tasks,
+                                                                          const int* __restrict__ begin, int n) {
+  pdl_enter();
+  int lb, nb;
+  const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];
+  fwd_finalize_body(t.f, lb);
+}
+
 template <int OBJ>
 __global__ void __launch_bounds__(kThreads, 1) bwd_multi_kernel(const EnergyTask* __restrict__ tasks,
                                                                const int* __restrict__ begin, int n) {
@@ -1423,6 +1447,7 @@ void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, flo
     launch_k(fwd_kernel<true>, dim3(n * a.nC), dim3(kFwdThreads), sm, st, e.tmX, e.tmY, a);
   else
     launch_k(fwd_kernel<false>, dim3(n * a.nC), dim3(kFwdThreads), sm, st, e.tmX, e.tmY, a);
+  launch_k(fwd_finalize_kernel, dim3(2 * n), dim3(kMergeThreads), 0, st, a);
 }
 
 namespace {
@@ -1575,6 +1600,12 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     for (const EnergyAgent& g : agents) obj = obj || g.ls.loss >= CRL_LOSS_FB;
     if (obj) launch_k(fwd_multi_kernel<true>, dim3(begin[na]), dim3(kFwdThreads), fwd_smem(Rmax), st, dt, db, na);
     else launch_k(fwd_multi_kernel<false>, dim3(begin[na]), dim3(kFwdThreads), fwd_smem(Rmax), st, dt, db, na);
+    // the merges: 2 n blocks per agent
+    std::vector<int> fb(na + 1, 0);
+    for (int i = 0; i < na; ++i) fb[i + 1] = fb[i] + 2 * tasks[i].n;
+    const int* dfb = cache.get(fb, st, &err);
+    if (!dfb) return err;
+    launch_k(fwd_finalize_multi_kernel, dim3(fb[na]), dim3(kMergeThreads), 0, st, dt, dfb, na);
   } else {
     // one launch per objective kind present (the agents of one kind in a table of their own)
     int kinds = 0;
