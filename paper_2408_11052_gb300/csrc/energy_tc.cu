@@ -1442,11 +1442,14 @@ void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, flo
     cudaFuncSetAttribute(fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
     attr = true;
   }
-  TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * B * e.R);
-  if (ls.loss >= CRL_LOSS_FB)
-    launch_k(fwd_kernel<true>, dim3(n * a.nC), dim3(kFwdThreads), sm, st, e.tmX, e.tmY, a);
-  else
-    launch_k(fwd_kernel<false>, dim3(n * a.nC), dim3(kFwdThreads), sm, st, e.tmX, e.tmY, a);
+  {
+    TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * B * e.R);
+    if (ls.loss >= CRL_LOSS_FB)
+      launch_k(fwd_kernel<true>, dim3(n * a.nC), dim3(kFwdThreads), sm, st, e.tmX, e.tmY, a);
+    else
+      launch_k(fwd_kernel<false>, dim3(n * a.nC), dim3(kFwdThreads), sm, st, e.tmX, e.tmY, a);
+  }
+  TraceLaunch trf(CRL_TRACE_ENERGY, st, 0.0);
   launch_k(fwd_finalize_kernel, dim3(2 * n), dim3(kMergeThreads), 0, st, a);
 }
 
@@ -1586,8 +1589,8 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
   if (!dt) return err;
   const int* db = cache.get(begin, st, &err);
   if (!db) return err;
-  TraceLaunch tr(CRL_TRACE_ENERGY, st, work);
   if (stage == 0) {
+    TraceLaunch tr(CRL_TRACE_ENERGY, st, work);
     launch_k(prep_multi_kernel, dim3(begin[na]), dim3(1024), 0, st, dt, db, na);
   } else if (stage == 1) {
     static bool attr = false;
@@ -1598,15 +1601,20 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     }
     bool obj = false;
     for (const EnergyAgent& g : agents) obj = obj || g.ls.loss >= CRL_LOSS_FB;
-    if (obj) launch_k(fwd_multi_kernel<true>, dim3(begin[na]), dim3(kFwdThreads), fwd_smem(Rmax), st, dt, db, na);
-    else launch_k(fwd_multi_kernel<false>, dim3(begin[na]), dim3(kFwdThreads), fwd_smem(Rmax), st, dt, db, na);
+    {
+      TraceLaunch tr(CRL_TRACE_ENERGY, st, work);
+      if (obj) launch_k(fwd_multi_kernel<true>, dim3(begin[na]), dim3(kFwdThreads), fwd_smem(Rmax), st, dt, db, na);
+      else launch_k(fwd_multi_kernel<false>, dim3(begin[na]), dim3(kFwdThreads), fwd_smem(Rmax), st, dt, db, na);
+    }
     // the merges: 2 n blocks per agent
     std::vector<int> fb(na + 1, 0);
     for (int i = 0; i < na; ++i) fb[i + 1] = fb[i] + 2 * tasks[i].n;
     const int* dfb = cache.get(fb, st, &err);
     if (!dfb) return err;
+    TraceLaunch trf(CRL_TRACE_ENERGY, st, 0.0);
     launch_k(fwd_finalize_multi_kernel, dim3(fb[na]), dim3(kMergeThreads), 0, st, dt, dfb, na);
   } else {
+    TraceLaunch tr(CRL_TRACE_ENERGY, st, work);
     // one launch per objective kind present (the agents of one kind in a table of their own)
     int kinds = 0;
     for (const EnergyAgent& g : agents) kinds |= 1 << obj_kind(g.ls.loss);
