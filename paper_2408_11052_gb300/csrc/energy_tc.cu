@@ -115,6 +115,21 @@ __device__ __forceinline__ float tile_row(float (&v)[32], float ax, const float*
   return m;
 }
 
+// An interior tile row (every column inside the batch): F log2(e) in place, its
+// maximum m and minimum mn, in one pass.
+template <int EK>
+__device__ __forceinline__ void tile_row_full(float (&v)[32], float ax, const float* __restrict__ ay, float k1,
+                                              float& m, float& mn) {
+  m = -INFINITY;
+  mn = INFINITY;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    v[k] = energy2<EK>(v[k], ax, ay[k], k1);
+    m = fmaxf(m, v[k]);
+    mn = fminf(mn, v[k]);
+  }
+}
+
 __device__ __forceinline__ float energy_of(int energy, float s, float ax, float ay, float inv_tau) {
   switch (energy) {
     case CRL_ENERGY_L2: return -sqrtf(fmaxf(ax + ay - 2.f * s, 0.f)) * inv_tau;
@@ -417,8 +432,8 @@ __device__ __forceinline__ float warp_max_f(float v) {
 struct FwdSmem {
   static constexpr size_t kX = 0;                                             // nk x 16 KiB row tile
   static constexpr size_t kY = 4 * 16384;                                     // ring of Y chunks
-  static constexpr size_t kBlk = kY + (size_t)kFwdYStages * 16384;           // 16 x [32][33] warp blocks
-  static constexpr size_t kCol = kBlk + (size_t)kFwdEpiWarps * 32 * 33 * 4;  // [2][4][128] (ref, sum)
+  static constexpr size_t kBlk = kY + (size_t)kFwdYStages * 16384;           // 16 x [32][32] warp blocks (swizzled)
+  static constexpr size_t kCol = kBlk + (size_t)kFwdEpiWarps * 32 * 32 * 4;  // [2][4][128] (ref, sum)
   static constexpr size_t kRow = kCol + 2 * 4 * 128 * 2 * 4;                  // [4][128] (m, s)
   static constexpr size_t kObj = kRow + 4 * 128 * 2 * 4;                      // [4][128] objective (v, k)
   static constexpr size_t kD = kObj + 4 * 128 * 2 * 4;                        // [128] anchor F_ii
@@ -550,7 +565,7 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
     const bool row_ok = i < a.B;
     const float ax = row_ok ? a.auxX[i] : 0.f;
     const float k1 = a.inv_tau * kLog2e;
-    float* blk = blk_all + warp * (32 * 33);
+    float* blk = blk_all + warp * (32 * 32);
     const bool anchored = OBJ && (a.obj == CRL_LOSS_DPO || a.obj == CRL_LOSS_IPO);
     if (anchored) {
       // the anchor F_ii of this CTA's rows: 4 threads per row, R / 4 columns of
@@ -614,16 +629,25 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
           ay[4 * k + 3] = x.w;
         }
       }
-      float m;
+      float m, mn;
       const bool full = i0 + kTile <= a.B && j0 + kTile <= a.B;
-      switch (a.energy) {
-        case CRL_ENERGY_L2: m = tile_row<0>(v, ax, ay, k1, full, jn); break;
-        case CRL_ENERGY_L2SQ: m = tile_row<1>(v, ax, ay, k1, full, jn); break;
-        default: m = tile_row<2>(v, ax, ay, k1, full, jn); break;
-      }
-      float mn = INFINITY;
+      if (full) {
+        // interior tile: energy, maximum and minimum in one pass
+        switch (a.energy) {
+          case CRL_ENERGY_L2: tile_row_full<0>(v, ax, ay, k1, m, mn); break;
+          case CRL_ENERGY_L2SQ: tile_row_full<1>(v, ax, ay, k1, m, mn); break;
+          default: tile_row_full<2>(v, ax, ay, k1, m, mn); break;
+        }
+      } else {
+        switch (a.energy) {
+          case CRL_ENERGY_L2: m = tile_row<0>(v, ax, ay, k1, false, jn); break;
+          case CRL_ENERGY_L2SQ: m = tile_row<1>(v, ax, ay, k1, false, jn); break;
+          default: m = tile_row<2>(v, ax, ay, k1, false, jn); break;
+        }
+        mn = INFINITY;
 #pragma unroll
-      for (int k = 0; k < 32; ++k) mn = fminf(mn, v[k] == -INFINITY ? INFINITY : v[k]);
+        for (int k = 0; k < 32; ++k) mn = fminf(mn, v[k] == -INFINITY ? INFINITY : v[k]);
+      }
       if (J == I && q == lg) {
         // F_ii: column r of this tile, the thread's element k = lane (selected, not indexed)
         float dv = 0.f;
@@ -680,19 +704,26 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
         cref = -INFINITY;   // the block lies outside the batch
         csum = 0.f;
       } else if (mnw >= Mw - kFwdRange) {
-        // one exp2 per element against the block maximum (no term underflows)
+        // one exp2 per element against the block maximum (no term underflows);
+        // row r of the block goes to blk[32 r + (k ^ sw(r))], sw(r) = 4 (r % 8):
+        // 16-byte stores along the row, conflict-free reads down a column
         float s = 0.f;
+        const int swz = (lane & 7) << 2;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const float e = ex2(v[k] - Mw);
-          s += e;
-          blk[lane * 33 + k] = e;
+        for (int k4 = 0; k4 < 8; ++k4) {
+          float4 e4;
+          e4.x = ex2(v[4 * k4] - Mw);
+          e4.y = ex2(v[4 * k4 + 1] - Mw);
+          e4.z = ex2(v[4 * k4 + 2] - Mw);
+          e4.w = ex2(v[4 * k4 + 3] - Mw);
+          s += (e4.x + e4.y) + (e4.z + e4.w);
+          *reinterpret_cast<float4*>(blk + lane * 32 + ((4 * k4) ^ swz)) = e4;
         }
         lse2_merge(row_m, row_s, Mw, s);
         __syncwarp();
         float c = 0.f;
 #pragma unroll 8
-        for (int rr = 0; rr < 32; ++rr) c += blk[rr * 33 + lane];
+        for (int rr = 0; rr < 32; ++rr) c += blk[rr * 32 + (lane ^ ((rr & 7) << 2))];
         cref = Mw;
         csum = c;
         __syncwarp();
@@ -704,16 +735,17 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
           for (int k = 0; k < 32; ++k) s += ex2(v[k] - m);
         }
         lse2_merge(row_m, row_s, m, s);
+        const int swz = (lane & 7) << 2;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) blk[lane * 33 + k] = v[k];
+        for (int k = 0; k < 32; ++k) blk[lane * 32 + (k ^ swz)] = v[k];
         __syncwarp();
         float cm = -INFINITY;
 #pragma unroll 8
-        for (int rr = 0; rr < 32; ++rr) cm = fmaxf(cm, blk[rr * 33 + lane]);
+        for (int rr = 0; rr < 32; ++rr) cm = fmaxf(cm, blk[rr * 32 + (lane ^ ((rr & 7) << 2))]);
         float c = 0.f;
         if (cm != -INFINITY) {
 #pragma unroll 8
-          for (int rr = 0; rr < 32; ++rr) c += ex2(blk[rr * 33 + lane] - cm);
+          for (int rr = 0; rr < 32; ++rr) c += ex2(blk[rr * 32 + (lane ^ ((rr & 7) << 2))] - cm);
         }
         cref = cm;
         csum = c;
