@@ -905,16 +905,17 @@ __device__ __forceinline__ float objective_coef(float f2, bool diag, float d_row
 // InfoNCE direction, a one-axis penalty) costs no exp2.
 // EDGE: the tile holds the diagonal or reaches past the batch (the per-pair
 // tests run); interior tiles skip them.
-template <int EK, int OBJ, int LIVE, bool EDGE>
-__device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, const float* s_aux,
-                                        const float* s_lse2, const float* s_koth, int q, int u, int v0, int B,
-                                        float& rowsum, uint32_t (&packed)[16]) {
+// NC consecutive columns cb .. cb + NC - 1 of the tile (NC = 16 or 32).
+template <int EK, int OBJ, int LIVE, bool EDGE, int NC>
+__device__ __forceinline__ void build_h(const float (&sv)[NC], const HCoef& hc, const float* s_aux,
+                                        const float* s_lse2, const float* s_koth, int cb, int u, int v0, int B,
+                                        float& rowsum, uint32_t (&packed)[NC / 2]) {
   // per-column constants of the other side, four columns per shared-memory load
   float cax[4], clse[4], ckoth[4];
 #pragma unroll
-  for (int k = 0; k < 32; k += 2) {
+  for (int k = 0; k < NC; k += 2) {
     if ((k & 3) == 0) {
-      const int c4 = q * 32 + k;
+      const int c4 = cb + k;
       if (EK != 2) *reinterpret_cast<float4*>(cax) = *reinterpret_cast<const float4*>(s_aux + c4);
       if (LIVE != 1) {
         *reinterpret_cast<float4*>(clse) = *reinterpret_cast<const float4*>(s_lse2 + c4);
@@ -924,7 +925,7 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
     float h2[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      const int cl = q * 32 + k + e;
+      const int cl = cb + k + e;
       const int v = v0 + cl;
       const int c = (k & 3) + e;
       const float sval = sv[k + e];
@@ -964,11 +965,33 @@ __device__ __forceinline__ void build_h(const float (&sv)[32], const HCoef& hc, 
 
 // lb in [0, 2 nrow): the row pass for lb < nrow, else the column pass.
 //
-// Pipeline over the other side's tiles v (buffer b = v % 2 for the tile and its
-// S accumulator): while the 16 warps turn S(v) into the coefficient tile, the
-// tensor core may still run acc(v - 1); as soon as acc(v - 1) is done, thread 0
-// loads tile v + 1 into the buffer it freed, and after acc(v) is issued thread
-// 32 issues S(v + 1) into the other TMEM accumulator.
+// 18 warps.  Warp 16 lane 0 loads the own tile once and the other side's tiles
+// into two buffers (tile v into buffer v % 2 once the MMAs of tile v - 2 are
+// done with it).  Warp 17 lane 0 issues the MMAs in whatever order their inputs
+// allow (polling): S(v) = own . other(v)^T into TMEM accumulator v % 2 once
+// tile v has landed and the builders have read S(v - 2), and the two halves of
+// acc += H(v) other(v) (K = 64 rows of the other tile each) as the builders
+// publish them.  The 16 builder warps turn S(v) into the BF16 coefficient tile
+// H one 64-column half at a time (warp w: rows 32 (w % 4) .., 16 columns of each
+// half): the accumulation of one half runs while the next half (or the next
+// tile's first half) is built, and S(v + 1) is ready before H(v) is done.
+constexpr int kBwdWarps = 16;
+constexpr int kBwdThreads = 32 * (kBwdWarps + 2);
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 template <int OBJ>
 __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorMap* tmY, const BwdArgs& row,
                                          const BwdArgs& col, int nrow, int lb, bool global_maps) {
@@ -982,23 +1005,24 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   const uint32_t tbytes = (uint32_t)nk * 16384;          // one operand tile
   uint8_t* Xs = smem;                                     // own tile                  nk x 16 KiB
   uint8_t* Ys = Xs + tbytes;                              // other tiles, 2 buffers    2 x nk x 16 KiB
-  uint8_t* Hs = Ys + 2 * tbytes;                          // H tile                    2 x 16 KiB
+  uint8_t* Hs = Ys + 2 * tbytes;                          // H halves                  2 x 16 KiB
   float* s_aux = reinterpret_cast<float*>(Hs + 2 * 16384);  // [128]
   float* s_lse2 = s_aux + kTile;                            // [128] other side's logsumexp x log2(e)
   float* s_koth = s_lse2 + kTile;                           // [128] other side's coefficient (see HCoef)
   float* s_red = reinterpret_cast<float*>(Hs);              // [4][128] partial sums (H is free by then)
   uint64_t* bars = reinterpret_cast<uint64_t*>(s_koth + kTile);
   uint64_t* xload = bars;
-  uint64_t* yfull = bars + 1;  // [2]
-  uint64_t* sfull = bars + 3;  // [2]
-  uint64_t* hfree = bars + 5;  // acc(v) done: H and the tile's buffer are free
-  uint64_t* drain = bars + 6;  // every MMA of this CTA has completed (teardown)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7);
+  uint64_t* yfull = bars + 1;   // [2] other tile v landed in buffer v % 2
+  uint64_t* sfull = bars + 3;   // [2] S(v) in accumulator v % 2
+  uint64_t* sfree = bars + 5;   // [2] the builders have read S(v) (one arrival)
+  uint64_t* hready = bars + 7;  // [2] half h of H(v) is in shared memory (one arrival)
+  uint64_t* hdone = bars + 9;   // [2] the accumulation of half h of H(v) is done (its region is free)
+  uint64_t* hfree = bars + 11;  // acc(v) done: the other tile's buffer is free
+  uint64_t* drain = bars + 12;  // every MMA of this CTA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 13);
   constexpr uint32_t tcols = 512;  // S, S, acc (R <= 256)
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int lg = warp % 4, q = warp / 4;
-  const int r = lg * 32 + lane;  // row of this thread within the tile
   const int u0 = (lb - (colpass ? nrow : 0)) * kTile;
   const int nV = (a.B + kTile - 1) / kTile;
   if (tid == 0) {
@@ -1012,12 +1036,15 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&yfull[b], 1);
       tc::mbar_init(&sfull[b], 1);
+      tc::mbar_init(&sfree[b], 1);
+      tc::mbar_init(&hready[b], 1);
+      tc::mbar_init(&hdone[b], 1);
     }
     tc::mbar_init(hfree, 1);
     tc::mbar_init(drain, 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) {
+  if (warp == kBwdWarps + 1) {
     tc::tmem_alloc(tmem_slot, tcols);
     tc::tmem_relinquish();
   }
@@ -1026,235 +1053,271 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const uint32_t tAcc = tmem + 256;
-  const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
   pdl_wait();
   pdl_trigger();
   const unsigned long long lim = tc::wait_limit(a.status);
 
-  int last_loaded = -1;           // thread 0: the last other-side tile loaded
-  auto load_other = [&](int v) {  // thread 0
-    last_loaded = v;
-    uint8_t* dst = Ys + (v & 1) * tbytes;
-    tc::mbar_arrive_expect_tx(&yfull[v & 1], tbytes);
-    for (int kb = 0; kb < nk; ++kb)
-      for (int rr = 0; rr < 2; ++rr)
-        tc::tma_load_2d(dst + kb * 16384 + rr * 8192, tmOther, &yfull[v & 1], kb * 64, v * kTile + 64 * rr);
-  };
-  auto issue_s = [&](int v) -> bool {  // thread 32: S(v) = own . other(v)^T into accumulator v % 2
-    if (!tc::mbar_wait(&yfull[v & 1], (v >> 1) & 1, lim)) return false;
-    tc::fence_after_sync();
-    const uint8_t* ys = Ys + (v & 1) * tbytes;
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
-    for (int kb = 0; kb < nk; ++kb) {
-      const uint64_t dx = tc::sdesc_kmajor_sw128(Xs + kb * 16384);
-      const uint64_t dy = tc::sdesc_kmajor_sw128(ys + kb * 16384);
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        tc::mma_bf16(tmem + (uint32_t)((v & 1) * 128), dx + 2 * k, dy + 2 * k, idesc, (kb | k) ? 1u : 0u);
-    }
-    tc::mma_commit(&sfull[v & 1]);
-    return true;
-  };
-  if (tid == 0) {
-    tc::mbar_arrive_expect_tx(xload, tbytes);
-    for (int kb = 0; kb < nk; ++kb)
-      for (int rr = 0; rr < 2; ++rr)
-        tc::tma_load_2d(Xs + kb * 16384 + rr * 8192, tmOwn, xload, kb * 64, u0 + 64 * rr);
-    load_other(0);
-    if (nV > 1) load_other(1);
-  } else if (tid == 32) {
-    if (!tc::mbar_wait(xload, 0, lim) || !issue_s(0)) atomicOr(a.status, CRL_STATUS_TIMEOUT);
-  }
-  __syncwarp();
-
-  const int u = u0 + r;
-  const float a_own = (u < a.B) ? a.aux_own[u] : 0.f;
-  const float l_own = (u < a.B) ? a.lse_own[u] : 0.f;
-  // loss weights of this side (row pass: forward direction and row penalty;
-  // column pass: backward direction and column penalty) and of the other
-  const float w_own = a.transposed ? a.w.wb : a.w.wf, p_own = a.transposed ? a.w.pc : a.w.pr;
-  const float w_oth = a.transposed ? a.w.wf : a.w.wb, p_oth = a.transposed ? a.w.pr : a.w.pc;
-  HCoef hc;
-  hc.a_own = a_own;
-  hc.l_own2 = l_own * kLog2e;
-  hc.k_own = a.scale * (w_own + 2.f * a.beta * p_own * l_own);
-  hc.k_diag = a.scale * (a.w.wf + a.w.wb);
-  const bool own_live = w_own != 0.f || (a.beta != 0.f && p_own != 0.f);
-  const bool oth_live = w_oth != 0.f || (a.beta != 0.f && p_oth != 0.f);
-  const int live = (own_live && oth_live) ? 0 : (oth_live ? 2 : 1);
-  hc.inv_tau = a.inv_tau;
-  hc.k1 = a.inv_tau * kLog2e;
-  constexpr bool kAnchored = OBJ == kObjDPO || OBJ == kObjIPO;
-  hc.d_own = (kAnchored && u < a.B) ? a.dpre[u] : 0.f;
-  hc.kd_own = (kAnchored && u < a.B) ? a.kd[u] : 0.f;
-  hc.dpre = a.dpre;
-  hc.kd = a.kd;
-  hc.dtotal = a.dtotal;
-  hc.c_bb = a.dtotal / ((float)a.B * (float)a.B);
-  hc.c_b = a.dtotal / (float)a.B;
-  hc.c_fb = a.B > 1 ? a.dtotal / ((float)a.B * (float)(a.B - 1)) : 0.f;
-  hc.transposed = a.transposed;
-  float rowsum = 0.f;
-  bool ok = true;
-  for (int vt = 0; vt < nV && ok; ++vt) {
-    const int v0 = vt * kTile, b = vt & 1;
-    if (tid < kTile) {
-      const int v = v0 + tid;
-      const float lo = (v < a.B) ? a.lse_other[v] : 0.f;
-      s_aux[tid] = (v < a.B) ? a.aux_other[v] : 0.f;
-      s_lse2[tid] = lo * kLog2e;
-      s_koth[tid] = a.scale * (w_oth + 2.f * a.beta * p_oth * lo);
-    }
-    bool good = true;
-    if (tid == 0 && vt >= 1) {
-      // acc(vt - 1) done: H and the buffer of tile vt - 1 are free; tile vt + 1 goes there
-      good = tc::mbar_wait(hfree, (vt - 1) & 1, lim);
-      if (good && vt + 1 < nV) load_other(vt + 1);
-    }
-    // coefficient tile H from S(vt): this thread's row r, columns 32 q .. 32 q + 31.
-    // One barrier publishes the per-tile arrays and thread 0's wait; every warp
-    // reaches every barrier (the decision to stop is block-wide).
-    good = (__all_sync(0xffffffffu, tc::mbar_wait(&sfull[b], (vt >> 1) & 1, lim) ? 1 : 0) != 0) && good;
-    ok = __syncthreads_and(good ? 1 : 0) != 0;
-    if (!ok) break;
-    tc::fence_after_sync();
-    {
-      float sv[32];
-      tc::tmem_ld32(tmem + (uint32_t)(b * 128) + lane_off + q * 32, sv);
-      uint32_t packed[16];
-#define CRL_BUILD_H(EK, LV, ED)                                                                     \
-  build_h<EK, OBJ, LV, (ED) || OBJ != kObjInfo>(sv, hc, s_aux, s_lse2, s_koth, q, u, v0, a.B, rowsum, packed)
-      const int ek = a.energy == CRL_ENERGY_L2 ? 0 : (a.energy == CRL_ENERGY_L2SQ ? 1 : 2);
-      // (the objectives outside InfoNCE always take the tested form: fewer instantiations)
-      const bool edge = OBJ != kObjInfo || u0 == v0 || u0 + kTile > a.B || v0 + kTile > a.B;
-      switch (2 * (3 * ek + live) + (edge ? 1 : 0)) {
-        case 0: CRL_BUILD_H(0, 0, false); break;
-        case 1: CRL_BUILD_H(0, 0, true); break;
-        case 2: CRL_BUILD_H(0, 1, false); break;
-        case 3: CRL_BUILD_H(0, 1, true); break;
-        case 4: CRL_BUILD_H(0, 2, false); break;
-        case 5: CRL_BUILD_H(0, 2, true); break;
-        case 6: CRL_BUILD_H(1, 0, false); break;
-        case 7: CRL_BUILD_H(1, 0, true); break;
-        case 8: CRL_BUILD_H(1, 1, false); break;
-        case 9: CRL_BUILD_H(1, 1, true); break;
-        case 10: CRL_BUILD_H(1, 2, false); break;
-        case 11: CRL_BUILD_H(1, 2, true); break;
-        case 12: CRL_BUILD_H(2, 0, false); break;
-        case 13: CRL_BUILD_H(2, 0, true); break;
-        case 14: CRL_BUILD_H(2, 1, false); break;
-        case 15: CRL_BUILD_H(2, 1, true); break;
-        case 16: CRL_BUILD_H(2, 2, false); break;
-        default: CRL_BUILD_H(2, 2, true); break;
+  if (warp == kBwdWarps) {
+    if (lane == 0) {
+      // loader: the own tile once, then other tile v into buffer v % 2
+      tc::mbar_arrive_expect_tx(xload, tbytes);
+      for (int kb = 0; kb < nk; ++kb)
+        for (int rr = 0; rr < 2; ++rr)
+          tc::tma_load_2d(Xs + kb * 16384 + rr * 8192, tmOwn, xload, kb * 64, u0 + 64 * rr);
+      int last = -1;
+      for (int v = 0; v < nV; ++v) {
+        if (v >= 2 && !tc::mbar_wait(hfree, (v - 2) & 1, lim)) {
+          atomicOr(a.status, CRL_STATUS_TIMEOUT);
+          break;
+        }
+        uint8_t* dst = Ys + (v & 1) * tbytes;
+        tc::mbar_arrive_expect_tx(&yfull[v & 1], tbytes);
+        for (int kb = 0; kb < nk; ++kb)
+          for (int rr = 0; rr < 2; ++rr)
+            tc::tma_load_2d(dst + kb * 16384 + rr * 8192, tmOther, &yfull[v & 1], kb * 64, v * kTile + 64 * rr);
+        last = v;
       }
-#undef CRL_BUILD_H
-      // columns 32 q .. +31 = K-block q / 2, 16-byte chunks (q % 2) * 4 .. +3
-      uint8_t* hb = Hs + (q / 2) * 16384;
-#pragma unroll
-      for (int c4 = 0; c4 < 4; ++c4) {
-        const uint4 val = make_uint4(packed[4 * c4], packed[4 * c4 + 1], packed[4 * c4 + 2], packed[4 * c4 + 3]);
-        *reinterpret_cast<uint4*>(hb + sw128_offset(r, (q % 2) * 4 + c4)) = val;
+      // nothing may land in this CTA's shared memory after it leaves
+      tc::mbar_wait(xload, 0, tc::kDrainLimitNs);
+      for (int b = 0; b < 2; ++b) {
+        const int v = (last & 1) == b ? last : last - 1;
+        if (v >= 0) tc::mbar_wait(&yfull[b], (uint32_t)((v >> 1) & 1), tc::kDrainLimitNs);
       }
     }
-    // make the generic-proxy H writes visible to the tensor core (and the S reads
-    // ordered before the next MMAs into this accumulator), then acc += H other(vt)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 32) {
-      // the tile in buffer b is the MN-major B operand (K = its 128 rows, N = R):
-      // K steps of 16 rows are 2048 bytes, R chunks of 64 columns 16 KiB apart
+  } else if (warp == kBwdWarps + 1) {
+    if (lane == 0) {
+      // MMA issuer: S(v) and the halves of acc(v), each as soon as its inputs are ready
+      constexpr uint32_t idesc_s = tc::idesc_bf16_f32(128, 128);
+      const uint32_t idesc_acc = tc::idesc_bf16_f32_bmn(128, a.R);
+      bool ok = tc::mbar_wait(xload, 0, lim);
+      if (!ok) atomicOr(a.status, CRL_STATUS_TIMEOUT);
       tc::fence_after_sync();
-      const uint8_t* ys = Ys + b * tbytes;
-      const uint32_t idesc = tc::idesc_bf16_f32_bmn(128, a.R);
-      for (int kb = 0; kb < 2; ++kb) {
-        const uint64_t dh = tc::sdesc_kmajor_sw128(Hs + kb * 16384);
+      int next_s = 0, next_h = 0;   // next S(v) to issue; next accumulation half (2 v + h)
+      unsigned long long t_idle = tc::globaltimer();
+      while (ok && (next_s < nV || next_h < 2 * nV)) {
+        bool progress = false;
+        if (next_s < nV && next_s <= next_h / 2 + 1) {
+          const int v = next_s, b = v & 1;
+          if (tc::mbar_test_wait(&yfull[b], (v >> 1) & 1) &&
+              (v < 2 || tc::mbar_test_wait(&sfree[b], ((v >> 1) - 1) & 1))) {
+            tc::fence_after_sync();
+            const uint8_t* ys = Ys + b * tbytes;
+            for (int kb = 0; kb < nk; ++kb) {
+              const uint64_t dx = tc::sdesc_kmajor_sw128(Xs + kb * 16384);
+              const uint64_t dy = tc::sdesc_kmajor_sw128(ys + kb * 16384);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint64_t dt = tc::sdesc_mnmajor_sw128(ys + kb * 8192 + k * 2048, 16384);
-          tc::mma_bf16(tAcc, dh + 2 * k, dt, idesc, (vt | kb | k) ? 1u : 0u);
+              for (int k = 0; k < 4; ++k)
+                tc::mma_bf16(tmem + (uint32_t)(b * 128), dx + 2 * k, dy + 2 * k, idesc_s, (kb | k) ? 1u : 0u);
+            }
+            tc::mma_commit(&sfull[b]);
+            ++next_s;
+            progress = true;
+          }
+        }
+        if (next_h < 2 * nV && next_h / 2 < next_s) {
+          const int v = next_h / 2, h = next_h % 2;
+          if (tc::mbar_test_wait(&hready[h], v & 1)) {
+            tc::fence_after_sync();
+            // half h of H (K = other rows 64 h .. 64 h + 63) times the other tile as the MN-major
+            // B operand: K steps of 16 rows are 2048 bytes, R chunks of 64 columns 16 KiB apart
+            const uint8_t* ys = Ys + (v & 1) * tbytes;
+            const uint64_t dh = tc::sdesc_kmajor_sw128(Hs + h * 16384);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t dt = tc::sdesc_mnmajor_sw128(ys + h * 8192 + k * 2048, 16384);
+              tc::mma_bf16(tAcc, dh + 2 * k, dt, idesc_acc, (v | h | k) ? 1u : 0u);
+            }
+            tc::mma_commit(&hdone[h]);
+            if (h == 1) tc::mma_commit(hfree);
+            ++next_h;
+            progress = true;
+          }
+        }
+        if (progress) {
+          t_idle = tc::globaltimer();
+        } else if (tc::globaltimer() - t_idle > lim) {
+          atomicOr(a.status, CRL_STATUS_TIMEOUT);
+          ok = false;
+        } else {
+          __nanosleep(32);   // leave the issue slots to the builder warps
         }
       }
-      tc::mma_commit(hfree);
-      // S(vt + 1) into the other accumulator (read out in the previous iteration)
-      if (vt + 1 < nV && !issue_s(vt + 1)) atomicOr(a.status, CRL_STATUS_TIMEOUT);
+      tc::mma_commit(drain);   // completes once every MMA issued above has
     }
-    __syncwarp();
-  }
-  if (tid == 32) tc::mma_commit(drain);   // completes once every MMA issued by this thread has
-  if (ok) ok = __all_sync(0xffffffffu, tc::mbar_wait(hfree, (nV - 1) & 1, lim) ? 1 : 0) != 0;
-  // row sums of the four column groups
-  s_red[q * kTile + r] = rowsum;
-  ok = __syncthreads_and(ok ? 1 : 0) != 0;
-  tc::fence_after_sync();
-  if (ok) {
-    const float rs = s_red[r] + s_red[kTile + r] + s_red[2 * kTile + r] + s_red[3 * kTile + r];
-    const float* own = a.own_f32 + (size_t)(u < a.B ? u : 0) * a.R;
-    float proj = 0.f;
-    if (a.energy == CRL_ENERGY_COS) {
-      // <x_hat, acc> over all R columns: partial per column group, then combined
-      float pp = 0.f;
+  } else {
+    // ---- builder warps
+    const int lg = warp % 4, q = warp / 4;
+    const int r = lg * 32 + lane;  // row of this thread within the tile
+    const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
+    const int u = u0 + r;
+    const float a_own = (u < a.B) ? a.aux_own[u] : 0.f;
+    const float l_own = (u < a.B) ? a.lse_own[u] : 0.f;
+    // loss weights of this side (row pass: forward direction and row penalty;
+    // column pass: backward direction and column penalty) and of the other
+    const float w_own = a.transposed ? a.w.wb : a.w.wf, p_own = a.transposed ? a.w.pc : a.w.pr;
+    const float w_oth = a.transposed ? a.w.wf : a.w.wb, p_oth = a.transposed ? a.w.pr : a.w.pc;
+    HCoef hc;
+    hc.a_own = a_own;
+    hc.l_own2 = l_own * kLog2e;
+    hc.k_own = a.scale * (w_own + 2.f * a.beta * p_own * l_own);
+    hc.k_diag = a.scale * (a.w.wf + a.w.wb);
+    const bool own_live = w_own != 0.f || (a.beta != 0.f && p_own != 0.f);
+    const bool oth_live = w_oth != 0.f || (a.beta != 0.f && p_oth != 0.f);
+    const int live = (own_live && oth_live) ? 0 : (oth_live ? 2 : 1);
+    hc.inv_tau = a.inv_tau;
+    hc.k1 = a.inv_tau * kLog2e;
+    constexpr bool kAnchored = OBJ == kObjDPO || OBJ == kObjIPO;
+    hc.d_own = (kAnchored && u < a.B) ? a.dpre[u] : 0.f;
+    hc.kd_own = (kAnchored && u < a.B) ? a.kd[u] : 0.f;
+    hc.dpre = a.dpre;
+    hc.kd = a.kd;
+    hc.dtotal = a.dtotal;
+    hc.c_bb = a.dtotal / ((float)a.B * (float)a.B);
+    hc.c_b = a.dtotal / (float)a.B;
+    hc.c_fb = a.B > 1 ? a.dtotal / ((float)a.B * (float)(a.B - 1)) : 0.f;
+    hc.transposed = a.transposed;
+    const int ek = a.energy == CRL_ENERGY_L2 ? 0 : (a.energy == CRL_ENERGY_L2SQ ? 1 : 2);
+    float rowsum = 0.f;
+    bool ok = true;
+    for (int vt = 0; vt < nV && ok; ++vt) {
+      const int v0 = vt * kTile, b = vt & 1;
+      if (tid < kTile) {
+        const int v = v0 + tid;
+        const float lo = (v < a.B) ? a.lse_other[v] : 0.f;
+        s_aux[tid] = (v < a.B) ? a.aux_other[v] : 0.f;
+        s_lse2[tid] = lo * kLog2e;
+        s_koth[tid] = a.scale * (w_oth + 2.f * a.beta * p_oth * lo);
+      }
+      bool good = true;
+      // half 0's region is free once the accumulation of tile vt - 1's half 0 is done
+      if (tid == 0 && vt >= 1) good = tc::mbar_wait(&hdone[0], (vt - 1) & 1, lim);
+      good = tc::mbar_wait(&sfull[b], (vt >> 1) & 1, lim) && good;
+      ok = tc::named_barrier_and(1, 32 * kBwdWarps, good);
+      if (!ok) break;
+      tc::fence_after_sync();
+      // (the objectives outside InfoNCE always take the tested form: fewer instantiations)
+      const bool edge = OBJ != kObjInfo || u0 == v0 || u0 + kTile > a.B || v0 + kTile > a.B;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int cb = 64 * h + 16 * q;   // this warp's 16 columns of half h
+        float sv[16];
+        tmem_ld16(tmem + (uint32_t)(b * 128) + lane_off + cb, sv);
+        uint32_t packed[8];
+#define CRL_BUILD_H(EK, LV, ED)                                                                            \
+  build_h<EK, OBJ, LV, (ED) || OBJ != kObjInfo, 16>(sv, hc, s_aux, s_lse2, s_koth, cb, u, v0, a.B, rowsum, \
+                                                    packed)
+        switch (2 * (3 * ek + live) + (edge ? 1 : 0)) {
+          case 0: CRL_BUILD_H(0, 0, false); break;
+          case 1: CRL_BUILD_H(0, 0, true); break;
+          case 2: CRL_BUILD_H(0, 1, false); break;
+          case 3: CRL_BUILD_H(0, 1, true); break;
+          case 4: CRL_BUILD_H(0, 2, false); break;
+          case 5: CRL_BUILD_H(0, 2, true); break;
+          case 6: CRL_BUILD_H(1, 0, false); break;
+          case 7: CRL_BUILD_H(1, 0, true); break;
+          case 8: CRL_BUILD_H(1, 1, false); break;
+          case 9: CRL_BUILD_H(1, 1, true); break;
+          case 10: CRL_BUILD_H(1, 2, false); break;
+          case 11: CRL_BUILD_H(1, 2, true); break;
+          case 12: CRL_BUILD_H(2, 0, false); break;
+          case 13: CRL_BUILD_H(2, 0, true); break;
+          case 14: CRL_BUILD_H(2, 1, false); break;
+          case 15: CRL_BUILD_H(2, 1, true); break;
+          case 16: CRL_BUILD_H(2, 2, false); break;
+          default: CRL_BUILD_H(2, 2, true); break;
+        }
+#undef CRL_BUILD_H
+        // columns 16 q .. 16 q + 15 of half h: 16-byte chunks 2 q, 2 q + 1 of the
+        // half's 128-byte-swizzled K-major tile
+        uint8_t* hb = Hs + h * 16384;
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+          const uint4 val = make_uint4(packed[4 * c2], packed[4 * c2 + 1], packed[4 * c2 + 2], packed[4 * c2 + 3]);
+          *reinterpret_cast<uint4*>(hb + sw128_offset(r, 2 * q + c2)) = val;
+        }
+        // make the generic-proxy H writes visible to the tensor core, then
+        // publish the half (after half 1, S(vt) has been read as well)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc::fence_before_sync();
+        bool next_ok = true;
+        if (h == 0 && tid == 0 && vt >= 1) next_ok = tc::mbar_wait(&hdone[1], (vt - 1) & 1, lim);
+        ok = tc::named_barrier_and(1, 32 * kBwdWarps, next_ok);
+        if (tid == 0) {
+          tc::mbar_arrive(&hready[h]);
+          if (h == 1) tc::mbar_arrive(&sfree[b]);
+        }
+        if (!ok) break;
+      }
+    }
+    if (!ok && tid == 0) atomicOr(a.status, CRL_STATUS_TIMEOUT);
+    // every accumulation done: the H regions become the row-sum partials
+    if (ok) ok = tc::mbar_wait(hfree, (nV - 1) & 1, lim);
+    ok = tc::named_barrier_and(1, 32 * kBwdWarps, ok);
+    s_red[q * kTile + r] = rowsum;
+    tc::fence_after_sync();
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * kBwdWarps));
+    if (ok) {
+      const float rs = s_red[r] + s_red[kTile + r] + s_red[2 * kTile + r] + s_red[3 * kTile + r];
+      const float* own = a.own_f32 + (size_t)(u < a.B ? u : 0) * a.R;
+      float proj = 0.f;
+      if (a.energy == CRL_ENERGY_COS) {
+        // <x_hat, acc> over all R columns: partial per column group, then combined
+        float pp = 0.f;
+        for (int c = q * 32; c < a.R; c += 128) {
+          float v[32];
+          tc::tmem_ld32(tAcc + lane_off + c, v);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) pp += own[c + k] * a_own * v[k];
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kBwdWarps));
+        s_red[q * kTile + r] = pp;
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kBwdWarps));
+        proj = s_red[r] + s_red[kTile + r] + s_red[2 * kTile + r] + s_red[3 * kTile + r];
+      }
       for (int c = q * 32; c < a.R; c += 128) {
         float v[32];
         tc::tmem_ld32(tAcc + lane_off + c, v);
+        if (u < a.B) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) pp += own[c + k] * a_own * v[k];
-      }
-      __syncthreads();
-      s_red[q * kTile + r] = pp;
-      __syncthreads();
-      proj = s_red[r] + s_red[kTile + r] + s_red[2 * kTile + r] + s_red[3 * kTile + r];
-    }
-    for (int c = q * 32; c < a.R; c += 128) {
-      float v[32];
-      tc::tmem_ld32(tAcc + lane_off + c, v);
-      if (u < a.B) {
+          for (int k = 0; k < 32; ++k) {
+            float d = v[k];
+            if (a.energy == CRL_ENERGY_L2 || a.energy == CRL_ENERGY_L2SQ) d -= rs * own[c + k];
+            else if (a.energy == CRL_ENERGY_COS) d = (d - own[c + k] * a_own * proj) * a_own;
+            v[k] = d;
+          }
+          if (a.d_out_f32 != nullptr) {
+            float4* dst = reinterpret_cast<float4*>(a.d_out_f32 + (size_t)u * a.R + c);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          float d = v[k];
-          if (a.energy == CRL_ENERGY_L2 || a.energy == CRL_ENERGY_L2SQ) d -= rs * own[c + k];
-          else if (a.energy == CRL_ENERGY_COS) d = (d - own[c + k] * a_own * proj) * a_own;
-          v[k] = d;
-        }
-        if (a.d_out_f32 != nullptr) {
-          float4* dst = reinterpret_cast<float4*>(a.d_out_f32 + (size_t)u * a.R + c);
+            for (int k = 0; k < 8; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          } else {
+            alignas(16) bf16 o[32];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-        } else {
-          alignas(16) bf16 o[32];
+            for (int k = 0; k < 32; ++k) o[k] = __float2bfloat16_rn(v[k]);
+            uint4* dst = reinterpret_cast<uint4*>(a.d_out + (size_t)u * a.R + c);
 #pragma unroll
-          for (int k = 0; k < 32; ++k) o[k] = __float2bfloat16_rn(v[k]);
-          uint4* dst = reinterpret_cast<uint4*>(a.d_out + (size_t)u * a.R + c);
+            for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4*>(o)[k];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4*>(o)[k];
-#pragma unroll
-          for (int k = 0; k < 32; ++k) a.d_outT[(size_t)(c + k) * a.ldt + u] = o[k];
+            for (int k = 0; k < 32; ++k) a.d_outT[(size_t)(c + k) * a.ldt + u] = o[k];
+          }
         }
       }
+    } else if (tid == 0) {
+      atomicOr(a.status, CRL_STATUS_TIMEOUT);
     }
-  } else if (tid == 0) {
-    atomicOr(a.status, CRL_STATUS_TIMEOUT);
   }
-  if (tid == 0) {
-    // teardown: every load issued into this CTA's shared memory has landed and
-    // every MMA has completed before the TMEM is freed and the CTA exits
-    tc::mbar_wait(xload, 0, tc::kDrainLimitNs);
-    for (int b = 0; b < 2; ++b) {
-      const int v = (last_loaded & 1) == b ? last_loaded : last_loaded - 1;
-      if (v >= 0) tc::mbar_wait(&yfull[b], (uint32_t)((v >> 1) & 1), tc::kDrainLimitNs);
-    }
-    tc::mbar_wait(drain, 0, tc::kDrainLimitNs);
-  }
+  __syncwarp();   // the loader and MMA warps reconverge after their single-lane loops
+  // teardown: every MMA has completed before the TMEM is freed
+  if (tid == 0) tc::mbar_wait(drain, 0, tc::kDrainLimitNs);
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, tcols);
+  if (warp == kBwdWarps + 1) tc::tmem_dealloc(tmem, tcols);
 }
 
 template <int OBJ>
-__global__ void __launch_bounds__(kThreads, 1) bwd_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                          const __grid_constant__ CUtensorMap tmY,
-                                                          const __grid_constant__ BwdArgs row,
-                                                          const __grid_constant__ BwdArgs col, int nrow) {
+__global__ void __launch_bounds__(kBwdThreads, 1) bwd_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                             const __grid_constant__ CUtensorMap tmY,
+                                                             const __grid_constant__ BwdArgs row,
+                                                             const __grid_constant__ BwdArgs col, int nrow) {
   bwd_body<OBJ>(&tmX, &tmY, row, col, nrow, blockIdx.x, false);
 }
 
@@ -1296,7 +1359,7 @@ __global__ void __launch_bounds__(kMergeThreads) fwd_finalize_multi_kernel(const
 }
 
 template <int OBJ>
-__global__ void __launch_bounds__(kThreads, 1) bwd_multi_kernel(const EnergyTask* __restrict__ tasks,
+__global__ void __launch_bounds__(kBwdThreads, 1) bwd_multi_kernel(const EnergyTask* __restrict__ tasks,
                                                                const int* __restrict__ begin, int n) {
   int lb, nb;
   const EnergyTask& t = tasks[segment_of(begin, n, blockIdx.x, lb, nb)];
@@ -1337,7 +1400,7 @@ int fwd_chunk_tiles(int n) {
 }
 size_t bwd_smem(int R) {
   // own tile, two other tiles, H (then the row-sum partials), three per-tile arrays, barriers, alignment
-  return (size_t)3 * (R / 64) * 16384 + 2 * 16384 + 3 * kTile * 4 + 64 + 1024;
+  return (size_t)3 * (R / 64) * 16384 + 2 * 16384 + 3 * kTile * 4 + 128 + 1024;
 }
 
 FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* loss4, float* r, float* c,
@@ -1493,7 +1556,7 @@ void launch_bwd_t(const EnergyTc& e, const BwdArgs& a, const BwdArgs& b, int n, 
     cudaFuncSetAttribute(bwd_kernel<OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(256));
     attr = true;
   }
-  launch_k(bwd_kernel<OBJ>, dim3(2 * n), dim3(kThreads), sm, st, e.tmX, e.tmY, a, b, n);
+  launch_k(bwd_kernel<OBJ>, dim3(2 * n), dim3(kBwdThreads), sm, st, e.tmX, e.tmY, a, b, n);
 }
 
 template <int OBJ>
@@ -1503,7 +1566,7 @@ void launch_bwd_multi_t(const EnergyTask* dt, const int* db, int na, int blocks,
     cudaFuncSetAttribute(bwd_multi_kernel<OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem(256));
     attr = true;
   }
-  launch_k(bwd_multi_kernel<OBJ>, dim3(blocks), dim3(kThreads), sm, st, dt, db, na);
+  launch_k(bwd_multi_kernel<OBJ>, dim3(blocks), dim3(kBwdThreads), sm, st, dt, db, na);
 }
 
 void launch_bwd_multi(int kind, const EnergyTask* dt, const int* db, int na, int blocks, size_t sm,
