@@ -905,21 +905,42 @@ __device__ __forceinline__ float objective_coef(float f2, bool diag, float d_row
 // InfoNCE direction, a one-axis penalty) costs no exp2.
 // EDGE: the tile holds the diagonal or reaches past the batch (the per-pair
 // tests run); interior tiles skip them.
-// NC consecutive columns cb .. cb + NC - 1 of the tile (NC = 16 or 32).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// NC consecutive columns cb .. cb + NC - 1 of the tile (NC = 16 or 32).  The
+// other side's per-column inputs come from global memory (every lane reads the
+// same 16 bytes: L1 broadcasts): aux_o = its auxiliaries, lse_o = its
+// logsumexps (LIVE != 1), with k_oth = kb_oth + k2_oth * lse.
 template <int EK, int OBJ, int LIVE, bool EDGE, int NC>
-__device__ __forceinline__ void build_h(const float (&sv)[NC], const HCoef& hc, const float* s_aux,
-                                        const float* s_lse2, const float* s_koth, int cb, int u, int v0, int B,
-                                        float& rowsum, uint32_t (&packed)[NC / 2]) {
-  // per-column constants of the other side, four columns per shared-memory load
+__device__ __forceinline__ void build_h(const float (&sv)[NC], const HCoef& hc, const float* __restrict__ aux_o,
+                                        const float* __restrict__ lse_o, float kb_oth, float k2_oth, int cb, int u,
+                                        int v0, int B, float& rowsum, uint32_t (&packed)[NC / 2]) {
   float cax[4], clse[4], ckoth[4];
 #pragma unroll
   for (int k = 0; k < NC; k += 2) {
     if ((k & 3) == 0) {
-      const int c4 = cb + k;
-      if (EK != 2) *reinterpret_cast<float4*>(cax) = *reinterpret_cast<const float4*>(s_aux + c4);
+      const int c4 = v0 + cb + k;
+      if (EDGE) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const bool in = c4 + e < B;
+          if (EK != 2) cax[e] = in ? __ldg(aux_o + c4 + e) : 0.f;
+          if (LIVE != 1) clse[e] = in ? __ldg(lse_o + c4 + e) : 0.f;
+        }
+      } else {
+        if (EK != 2) *reinterpret_cast<float4*>(cax) = __ldg(reinterpret_cast<const float4*>(aux_o + c4));
+        if (LIVE != 1) *reinterpret_cast<float4*>(clse) = __ldg(reinterpret_cast<const float4*>(lse_o + c4));
+      }
       if (LIVE != 1) {
-        *reinterpret_cast<float4*>(clse) = *reinterpret_cast<const float4*>(s_lse2 + c4);
-        *reinterpret_cast<float4*>(ckoth) = *reinterpret_cast<const float4*>(s_koth + c4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          ckoth[e] = fmaf(k2_oth, clse[e], kb_oth);
+          clse[e] *= kLog2e;
+        }
       }
     }
     float h2[2];
@@ -931,12 +952,12 @@ __device__ __forceinline__ void build_h(const float (&sv)[NC], const HCoef& hc, 
       const float sval = sv[k + e];
       float f2, fac;
       if (EK == 0) {
-        const float t = fmaxf(hc.a_own + cax[c] - 2.f * sval, 0.f);
-        const float rs = t >= 1e-24f ? rsqrtf(t) : 0.f;
+        const float t = fmaxf(fmaf(-2.f, sval, hc.a_own + cax[c]), 0.f);
+        const float rs = t >= 1e-24f ? rsqrt_approx(t) : 0.f;
         f2 = -(t * rs) * hc.k1;
         fac = hc.inv_tau * rs;
       } else if (EK == 1) {
-        const float t = fmaxf(hc.a_own + cax[c] - 2.f * sval, 0.f);
+        const float t = fmaxf(fmaf(-2.f, sval, hc.a_own + cax[c]), 0.f);
         f2 = -t * hc.k1;
         fac = 2.f * hc.inv_tau;
       } else {
@@ -1006,20 +1027,17 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
   uint8_t* Xs = smem;                                     // own tile                  nk x 16 KiB
   uint8_t* Ys = Xs + tbytes;                              // other tiles, 2 buffers    2 x nk x 16 KiB
   uint8_t* Hs = Ys + 2 * tbytes;                          // H halves                  2 x 16 KiB
-  float* s_aux = reinterpret_cast<float*>(Hs + 2 * 16384);  // [128]
-  float* s_lse2 = s_aux + kTile;                            // [128] other side's logsumexp x log2(e)
-  float* s_koth = s_lse2 + kTile;                           // [128] other side's coefficient (see HCoef)
   float* s_red = reinterpret_cast<float*>(Hs);              // [4][128] partial sums (H is free by then)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_koth + kTile);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Hs + 2 * 16384);
   uint64_t* xload = bars;
   uint64_t* yfull = bars + 1;   // [2] other tile v landed in buffer v % 2
   uint64_t* sfull = bars + 3;   // [2] S(v) in accumulator v % 2
-  uint64_t* sfree = bars + 5;   // [2] the builders have read S(v) (one arrival)
-  uint64_t* hready = bars + 7;  // [2] half h of H(v) is in shared memory (one arrival)
-  uint64_t* hdone = bars + 9;   // [2] the accumulation of half h of H(v) is done (its region is free)
-  uint64_t* hfree = bars + 11;  // acc(v) done: the other tile's buffer is free
-  uint64_t* drain = bars + 12;  // every MMA of this CTA has completed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 13);
+  uint64_t* sfree = bars + 5;   // [2] the 16 builder warps have read S(v)
+  uint64_t* hready = bars + 7;  // [2] the 16 builder warps have written half h of H(v)
+  uint64_t* hdone = bars + 9;   // [2] the accumulation of half h of H(v) is done (its region is free;
+                                //     after half 1 the other tile's buffer is free as well)
+  uint64_t* drain = bars + 11;  // every MMA of this CTA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
   constexpr uint32_t tcols = 512;  // S, S, acc (R <= 256)
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -1036,11 +1054,10 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&yfull[b], 1);
       tc::mbar_init(&sfull[b], 1);
-      tc::mbar_init(&sfree[b], 1);
-      tc::mbar_init(&hready[b], 1);
+      tc::mbar_init(&sfree[b], kBwdWarps);
+      tc::mbar_init(&hready[b], kBwdWarps);
       tc::mbar_init(&hdone[b], 1);
     }
-    tc::mbar_init(hfree, 1);
     tc::mbar_init(drain, 1);
     tc::fence_mbar_init();
   }
@@ -1066,7 +1083,7 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
           tc::tma_load_2d(Xs + kb * 16384 + rr * 8192, tmOwn, xload, kb * 64, u0 + 64 * rr);
       int last = -1;
       for (int v = 0; v < nV; ++v) {
-        if (v >= 2 && !tc::mbar_wait(hfree, (v - 2) & 1, lim)) {
+        if (v >= 2 && !tc::mbar_wait(&hdone[1], (v - 2) & 1, lim)) {
           atomicOr(a.status, CRL_STATUS_TIMEOUT);
           break;
         }
@@ -1128,7 +1145,6 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
               tc::mma_bf16(tAcc, dh + 2 * k, dt, idesc_acc, (v | h | k) ? 1u : 0u);
             }
             tc::mma_commit(&hdone[h]);
-            if (h == 1) tc::mma_commit(hfree);
             ++next_h;
             progress = true;
           }
@@ -1139,7 +1155,7 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
           atomicOr(a.status, CRL_STATUS_TIMEOUT);
           ok = false;
         } else {
-          __nanosleep(32);   // leave the issue slots to the builder warps
+          __nanosleep(128);   // leave the issue slots to the builder warps
         }
       }
       tc::mma_commit(drain);   // completes once every MMA issued above has
@@ -1177,35 +1193,33 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     hc.c_fb = a.B > 1 ? a.dtotal / ((float)a.B * (float)(a.B - 1)) : 0.f;
     hc.transposed = a.transposed;
     const int ek = a.energy == CRL_ENERGY_L2 ? 0 : (a.energy == CRL_ENERGY_L2SQ ? 1 : 2);
+    const float kb_oth = a.scale * w_oth, k2_oth = 2.f * a.scale * a.beta * p_oth;
     float rowsum = 0.f;
     bool ok = true;
+    // No block-wide barrier per tile: each warp waits for what it reads (S(vt),
+    // a free H region) and arrives on what it produces (S read, half written).
     for (int vt = 0; vt < nV && ok; ++vt) {
       const int v0 = vt * kTile, b = vt & 1;
-      if (tid < kTile) {
-        const int v = v0 + tid;
-        const float lo = (v < a.B) ? a.lse_other[v] : 0.f;
-        s_aux[tid] = (v < a.B) ? a.aux_other[v] : 0.f;
-        s_lse2[tid] = lo * kLog2e;
-        s_koth[tid] = a.scale * (w_oth + 2.f * a.beta * p_oth * lo);
-      }
-      bool good = true;
-      // half 0's region is free once the accumulation of tile vt - 1's half 0 is done
-      if (tid == 0 && vt >= 1) good = tc::mbar_wait(&hdone[0], (vt - 1) & 1, lim);
-      good = tc::mbar_wait(&sfull[b], (vt >> 1) & 1, lim) && good;
-      ok = tc::named_barrier_and(1, 32 * kBwdWarps, good);
+      ok = __all_sync(0xffffffffu, tc::mbar_wait(&sfull[b], (vt >> 1) & 1, lim) ? 1 : 0) != 0;
       if (!ok) break;
       tc::fence_after_sync();
       // (the objectives outside InfoNCE always take the tested form: fewer instantiations)
       const bool edge = OBJ != kObjInfo || u0 == v0 || u0 + kTile > a.B || v0 + kTile > a.B;
 #pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < 2 && ok; ++h) {
         const int cb = 64 * h + 16 * q;   // this warp's 16 columns of half h
         float sv[16];
         tmem_ld16(tmem + (uint32_t)(b * 128) + lane_off + cb, sv);
+        if (h == 1) {
+          // this warp is done with S(vt): the accumulator may take S(vt + 2)
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&sfree[b]);
+        }
         uint32_t packed[8];
-#define CRL_BUILD_H(EK, LV, ED)                                                                            \
-  build_h<EK, OBJ, LV, (ED) || OBJ != kObjInfo, 16>(sv, hc, s_aux, s_lse2, s_koth, cb, u, v0, a.B, rowsum, \
-                                                    packed)
+#define CRL_BUILD_H(EK, LV, ED)                                                                              \
+  build_h<EK, OBJ, LV, (ED) || OBJ != kObjInfo, 16>(sv, hc, a.aux_other, a.lse_other, kb_oth, k2_oth, cb, u, v0, \
+                                                    a.B, rowsum, packed)
         switch (2 * (3 * ek + live) + (edge ? 1 : 0)) {
           case 0: CRL_BUILD_H(0, 0, false); break;
           case 1: CRL_BUILD_H(0, 0, true); break;
@@ -1227,6 +1241,11 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
           default: CRL_BUILD_H(2, 2, true); break;
         }
 #undef CRL_BUILD_H
+        // half h's region is free once the accumulation of tile vt - 1's half h is done
+        if (vt >= 1) {
+          ok = __all_sync(0xffffffffu, tc::mbar_wait(&hdone[h], (vt - 1) & 1, lim) ? 1 : 0) != 0;
+          if (!ok) break;
+        }
         // columns 16 q .. 16 q + 15 of half h: 16-byte chunks 2 q, 2 q + 1 of the
         // half's 128-byte-swizzled K-major tile
         uint8_t* hb = Hs + h * 16384;
@@ -1235,23 +1254,16 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
           const uint4 val = make_uint4(packed[4 * c2], packed[4 * c2 + 1], packed[4 * c2 + 2], packed[4 * c2 + 3]);
           *reinterpret_cast<uint4*>(hb + sw128_offset(r, 2 * q + c2)) = val;
         }
-        // make the generic-proxy H writes visible to the tensor core, then
-        // publish the half (after half 1, S(vt) has been read as well)
+        // make the generic-proxy H writes visible to the tensor core, then publish
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc::fence_before_sync();
-        bool next_ok = true;
-        if (h == 0 && tid == 0 && vt >= 1) next_ok = tc::mbar_wait(&hdone[1], (vt - 1) & 1, lim);
-        ok = tc::named_barrier_and(1, 32 * kBwdWarps, next_ok);
-        if (tid == 0) {
-          tc::mbar_arrive(&hready[h]);
-          if (h == 1) tc::mbar_arrive(&sfree[b]);
-        }
-        if (!ok) break;
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&hready[h]);
       }
     }
-    if (!ok && tid == 0) atomicOr(a.status, CRL_STATUS_TIMEOUT);
+    if (!ok && lane == 0) atomicOr(a.status, CRL_STATUS_TIMEOUT);
     // every accumulation done: the H regions become the row-sum partials
-    if (ok) ok = tc::mbar_wait(hfree, (nV - 1) & 1, lim);
+    if (ok) ok = tc::mbar_wait(&hdone[1], (nV - 1) & 1, lim);
     ok = tc::named_barrier_and(1, 32 * kBwdWarps, ok);
     s_red[q * kTile + r] = rowsum;
     tc::fence_after_sync();
@@ -1400,7 +1412,8 @@ int fwd_chunk_tiles(int n) {
 }
 size_t bwd_smem(int R) {
   // own tile, two other tiles, H (then the row-sum partials), three per-tile arrays, barriers, alignment
-  return (size_t)3 * (R / 64) * 16384 + 2 * 16384 + 3 * kTile * 4 + 128 + 1024;
+  // own tile, two other tiles, the two H halves (then the row-sum partials), barriers, alignment
+  return (size_t)3 * (R / 64) * 16384 + 2 * 16384 + 128 + 1024;
 }
 
 FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* loss4, float* r, float* c,
