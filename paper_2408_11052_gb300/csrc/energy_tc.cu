@@ -845,6 +845,7 @@ struct HCoef {
   float a_own;    // own auxiliary (|x|^2 for the L2 energies)
   float l_own2;   // own logsumexp x log2(e)
   float k_own;    // scale (w_own + 2 beta p_own l_own)
+  float k_own_tau;  // k_own / tau
   float k_diag;   // scale (w_f + w_b): the positive pair's -1 terms
   float inv_tau;
   float k1;       // log2(e) / tau
@@ -950,6 +951,15 @@ __device__ __forceinline__ void build_h(const float (&sv)[NC], const HCoef& hc, 
       const int v = v0 + cl;
       const int c = (k & 3) + e;
       const float sval = sv[k + e];
+      if (EK == 0 && LIVE != 0 && !EDGE && OBJ == kObjInfo) {
+        // the common case (-L2, one live softmax term, interior tile, InfoNCE):
+        // h = 2^(-k1 d - l2) k / (tau d), with k / tau per row or per column
+        const float t = fmaxf(fmaf(-2.f, sval, hc.a_own + cax[c]), 0.f);
+        const float rs = t >= 1e-24f ? rsqrt_approx(t) : 0.f;
+        if (LIVE == 1) h2[e] = ex2(fmaf(-hc.k1, t * rs, -hc.l_own2)) * (hc.k_own_tau * rs);
+        else h2[e] = ex2(fmaf(-hc.k1, t * rs, -clse[c])) * (ckoth[c] * hc.inv_tau * rs);
+        continue;
+      }
       float f2, fac;
       if (EK == 0) {
         const float t = fmaxf(fmaf(-2.f, sval, hc.a_own + cax[c]), 0.f);
@@ -1176,6 +1186,7 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
     hc.a_own = a_own;
     hc.l_own2 = l_own * kLog2e;
     hc.k_own = a.scale * (w_own + 2.f * a.beta * p_own * l_own);
+    hc.k_own_tau = hc.k_own * a.inv_tau;
     hc.k_diag = a.scale * (a.w.wf + a.w.wb);
     const bool own_live = w_own != 0.f || (a.beta != 0.f && p_own != 0.f);
     const bool oth_live = w_oth != 0.f || (a.beta != 0.f && p_oth != 0.f);
