@@ -754,7 +754,7 @@ def build_parser():
     ap.add_argument("--energy", default=None, choices=["l2", "dot", "cos", "l2sq", "l1"],
                     help="energy function instead of the workload's")
     ap.add_argument("--alpha-autotune", action="store_true", help="learn the entropy coefficient")
-    ap.add_argument("--gemm-kernel", default="any", choices=["any", "one_tile", "persistent"],
+    ap.add_argument("--gemm-kernel", default="any", choices=["any", "one_tile", "persistent", "cta_pair"],
                     help="BF16 GEMM kernel family the autotuner may pick from")
     ap.add_argument("--oracle-rate", type=float, default=None, help=argparse.SUPPRESS)
     return ap

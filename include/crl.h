@@ -448,15 +448,19 @@ int32_t crl_set_autotune(int32_t enable);
 
 /* Which tensor-core GEMM kernels the grouped launches may use (process-wide;
  * library extension): CRL_GEMM_ANY (the default; the autotuner picks among
- * the one-tile and persistent kernels), CRL_GEMM_ONE_TILE (one CTA per output tile), CRL_GEMM_PERSISTENT (one
+ * all three), CRL_GEMM_ONE_TILE (one CTA per output tile), CRL_GEMM_PERSISTENT (one
  * CTA per SM walking the tiles, its epilogue overlapping the next tile's
- * main loop through a double-buffered TMEM accumulator).  All kernels give
- * identical outputs.  Without autotuning the fixed rule picks the tile width
- * and this setting the kernel (ANY: one tile per CTA).  Returns the previous
- * setting, or CRL_E_INVALID_ARG for an unknown mode. */
+ * main loop through a double-buffered TMEM accumulator), CRL_GEMM_CTA_PAIR
+ * (the persistent schedule over 256-row tiles, each computed by a cluster of
+ * two CTAs with tcgen05.mma.cta_group::2; every CTA loads its own half of the
+ * operands, no multicast).  All kernels give identical outputs.  Without
+ * autotuning the fixed rule picks the tile width and this setting the kernel
+ * (ANY: one tile per CTA).  Returns the previous setting, or
+ * CRL_E_INVALID_ARG for an unknown mode. */
 #define CRL_GEMM_ANY 0
 #define CRL_GEMM_ONE_TILE 1
 #define CRL_GEMM_PERSISTENT 2
+#define CRL_GEMM_CTA_PAIR 3
 int32_t crl_set_gemm_kernel(int32_t mode);
 
 

@@ -177,12 +177,12 @@ def set_autotune(enable):
     return bool(lib().crl_set_autotune(1 if enable else 0))
 
 
-GEMM_KERNEL = {"any": 0, "one_tile": 1, "persistent": 2}
+GEMM_KERNEL = {"any": 0, "one_tile": 1, "persistent": 2, "cta_pair": 3}
 
 
 def set_gemm_kernel(mode):
     """Process-wide: which tensor-core GEMM kernels the grouped launches may use
-    ("any", "one_tile" or "persistent").  Returns the previous mode's name."""
+    ("any", "one_tile", "persistent" or "cta_pair").  Returns the previous mode's name."""
     prev = lib().crl_set_gemm_kernel(GEMM_KERNEL[mode])
     return {v: k for k, v in GEMM_KERNEL.items()}[prev]
 

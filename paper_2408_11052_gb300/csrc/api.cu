@@ -978,7 +978,7 @@ int32_t crl_set_autotune(int32_t enable) {
 }
 
 int32_t crl_set_gemm_kernel(int32_t mode) {
-  if (mode < CRL_GEMM_ANY || mode > CRL_GEMM_PERSISTENT) return CRL_E_INVALID_ARG;
+  if (mode < CRL_GEMM_ANY || mode > CRL_GEMM_CTA_PAIR) return CRL_E_INVALID_ARG;
   const int32_t prev = g_gemm_kernel;
   g_gemm_kernel = mode;
   return prev;

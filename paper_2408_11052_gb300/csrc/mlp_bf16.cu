@@ -582,22 +582,54 @@ void launch_gemm_persistent(const tc::GemmProblem* table, int nprob, int tiles, 
            status);
 }
 
+// CTA-pair kernel: clusters of two CTAs, one cluster per pair of SMs at most
+// (as many as can be resident at once), walking the 256-row tiles.
+int pair_clusters_max(const void* kernel, size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * 64);
+  cfg.blockDim = dim3(224);
+  cfg.dynamicSmemBytes = smem;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = sm_count() / 2;
+  }
+  return n;
+}
+
+template <int BN, int STAGES>
+void launch_gemm_pair(const tc::GemmProblem* table, int nprob, int tiles, unsigned* status, cudaStream_t st) {
+  using S = tc::GemmPairSmem<BN, STAGES>;
+  static int clusters = 0;
+  if (clusters == 0) {
+    cudaFuncSetAttribute(tc::tc_gemm_pair_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+    clusters = pair_clusters_max(reinterpret_cast<const void*>(tc::tc_gemm_pair_kernel<BN, STAGES>), S::kBytes);
+  }
+  const int grid = 2 * std::min(tiles, clusters);
+  launch_k(tc::tc_gemm_pair_kernel<BN, STAGES>, dim3(grid), dim3(224), S::kBytes, st, table, nprob, tiles, status);
+}
+
 // A GEMM configuration: tile width, ring depth and kernel (0: one tile per CTA,
-// 1: persistent), coded as 8192 * kernel + 16 * BN + stages.
+// 1: persistent, 2: CTA pair with 256-row tiles), coded as 8192 * kernel + 16 * BN + stages.
 constexpr int gemm_cfg(int bn, int stages, int kernel = 0) { return 8192 * kernel + 16 * bn + stages; }
 constexpr int cfg_bn(int cfg) { return (cfg % 8192) / 16; }
 constexpr int cfg_kernel(int cfg) { return cfg / 8192; }
-// ANY tunes over the one-tile and persistent kernels.
+constexpr int cfg_bm(int cfg) { return cfg_kernel(cfg) == 2 ? 2 * tc::kBM : tc::kBM; }
+// ANY tunes over all three kernels.
 bool cfg_allowed(int cfg) {
   if (g_gemm_kernel == CRL_GEMM_ONE_TILE) return cfg_kernel(cfg) == 0;
   if (g_gemm_kernel == CRL_GEMM_PERSISTENT) return cfg_kernel(cfg) == 1;
+  if (g_gemm_kernel == CRL_GEMM_CTA_PAIR) return cfg_kernel(cfg) == 2;
   return true;
 }
-constexpr int kGemmCfgs[8] = {gemm_cfg(64, 4),    gemm_cfg(64, 8),     gemm_cfg(128, 3),    gemm_cfg(128, 6),
-                              gemm_cfg(256, 4),   gemm_cfg(64, 8, 1),  gemm_cfg(128, 6, 1), gemm_cfg(256, 4, 1)};
+constexpr int kGemmCfgs[10] = {gemm_cfg(64, 4),     gemm_cfg(64, 8),     gemm_cfg(128, 3),    gemm_cfg(128, 6),
+                               gemm_cfg(256, 4),    gemm_cfg(64, 8, 1),  gemm_cfg(128, 6, 1), gemm_cfg(256, 4, 1),
+                               gemm_cfg(128, 8, 2), gemm_cfg(256, 6, 2)};
 
 void launch_cfg(int cfg, const tc::GemmProblem* t, int nprob, int tiles, unsigned* status, cudaStream_t st) {
   switch (cfg) {
+    case gemm_cfg(128, 8, 2): launch_gemm_pair<128, 8>(t, nprob, tiles, status, st); break;
+    case gemm_cfg(256, 6, 2): launch_gemm_pair<256, 6>(t, nprob, tiles, status, st); break;
     case gemm_cfg(64, 8, 1): launch_gemm_persistent<64, 8>(t, nprob, tiles, status, st); break;
     case gemm_cfg(128, 6, 1): launch_gemm_persistent<128, 6>(t, nprob, tiles, status, st); break;
     case gemm_cfg(256, 4, 1): launch_gemm_persistent<256, 4>(t, nprob, tiles, status, st); break;
@@ -618,6 +650,7 @@ int heuristic_cfg(const std::vector<tc::GemmProblem>& probs, int min_bn) {
   const int bn = std::max(ctas128 >= 148 ? 128 : 64, min_bn <= 64 ? 64 : (min_bn <= 128 ? 128 : 256));
   if (g_gemm_kernel == CRL_GEMM_PERSISTENT)
     return bn == 256 ? gemm_cfg(256, 4, 1) : (bn == 128 ? gemm_cfg(128, 6, 1) : gemm_cfg(64, 8, 1));
+  if (g_gemm_kernel == CRL_GEMM_CTA_PAIR) return bn == 256 ? gemm_cfg(256, 6, 2) : gemm_cfg(128, 8, 2);
   return bn == 256 ? gemm_cfg(256, 4) : (bn == 128 ? gemm_cfg(128, 4) : gemm_cfg(64, 4));
 }
 
@@ -641,7 +674,7 @@ int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, un
     if (!cfg_allowed(cfg)) continue;
     int tiles = 0;
     const char* err = nullptr;
-    const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 0);
+    const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 0, cfg_bm(cfg));
     if (!t || tiles == 0) continue;
     launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);  // warm-up
     cudaEventRecord(e0, st);
@@ -684,7 +717,7 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
   }
   int tiles = 0;
   const char* err = nullptr;
-  const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 0);
+  const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 0, cfg_bm(cfg));
   if (!t) return err;
   if (tiles == 0) return nullptr;
   TraceLaunch tr(CRL_TRACE_GEMM, st, flops);
@@ -695,7 +728,7 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
 }  // namespace
 
 const tc::GemmProblem* GemmGroups::table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles,
-                                         cudaStream_t st, const char** err, bool allow_split) {
+                                         cudaStream_t st, const char** err, bool allow_split, int BM) {
   // split-K: the problems that allow it take the same split, chosen so that the
   // launch has about two CTAs per SM, with >= 8 K-slices per split
   int split = 1;
@@ -714,7 +747,7 @@ const tc::GemmProblem* GemmGroups::table(std::vector<tc::GemmProblem>& probs, in
     p.tile_begin = tiles;
     const int nk = ceil_div(p.K, tc::kBK);
     p.ksplit = (p.ksplit_cap > 1) ? std::max(1, std::min(split, nk / 8)) : 1;
-    tiles += ceil_div(p.M, tc::kBM) * p.tiles_n * p.ksplit;
+    tiles += ceil_div(p.M, BM) * p.tiles_n * p.ksplit;
   }
   *total_tiles = tiles;
   const size_t bytes = probs.size() * sizeof(tc::GemmProblem);

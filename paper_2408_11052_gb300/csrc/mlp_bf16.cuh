@@ -113,9 +113,10 @@ class GemmGroups {
   // device table; nullptr (and *err) on failure.
   // BN = 0: the problems are uploaded as given (tiles_n / tile_begin untouched).
   // allow_split: problems with ksplit_cap > 1 split K (the one-tile kernel
-  // only) so that the launch has about two CTAs per SM.
+  // only) so that the launch has about two CTAs per SM.  BM: tile rows (128,
+  // or 256 for the CTA-pair kernel).
   const tc::GemmProblem* table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles, cudaStream_t st,
-                               const char** err, bool allow_split = false);
+                               const char** err, bool allow_split = false, int BM = tc::kBM);
   // Frees every table (synchronises the device) and forgets the tuned tile widths.
   void reset();
   // Autotuned configuration (16 x tile width + ring depth) of a problem list,

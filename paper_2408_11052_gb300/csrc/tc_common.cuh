@@ -75,6 +75,38 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same two tests with cluster-scope acquire: for a barrier that another
+// CTA of the cluster arrives on (its writes before the arrive become visible).
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_test_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// One arrival on a barrier of another CTA of the cluster (`remote`: its
+// mapa_shared address).  Relaxed: what such an arrival announces was written
+// by the asynchronous proxy (TMA data, MMA results, TMEM reads) and had
+// completed when this thread observed it; a cluster-scope release would add a
+// memory barrier (measured as `membar` stalls) that orders nothing needed here.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t remote) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
 // Wait for phase `parity` of `bar`; false if it did not complete within
 // `limit` ns.  Limits below kPollBelowNs poll without suspending the thread, so
 // that a short limit runs out even where the phase would complete within one
@@ -91,6 +123,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
   const unsigned long long t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
     if (globaltimer() - t0 > limit) return false;
+  }
+  return true;
+}
+// mbar_wait for a barrier that another CTA of the cluster arrives on (polls
+// without suspending).
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, unsigned long long limit) {
+  if (mbar_test_wait_cluster(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_test_wait_cluster(bar, parity)) {
+    if (globaltimer() - t0 >= limit) return false;
   }
   return true;
 }
@@ -188,6 +230,20 @@ __device__ __forceinline__ void tmem_relinquish() {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
+// CTA-pair forms (a cluster of two CTAs on one TPC; every tcgen05 instruction
+// of such a kernel takes cta_group::2): one warp of EACH CTA of the pair
+// executes the allocation (the same columns in both CTAs' TMEM), the
+// relinquish and the deallocation.
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -245,6 +301,27 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+// CTA-pair MMA, issued by one thread of the even CTA: D (M = 256 rows, the
+// even CTA's TMEM lanes holding rows 0..127 and the odd CTA's rows 128..255,
+// at the same TMEM address) (+)= A * B^T, where each CTA supplies its 128
+// rows of A and its N / 2 rows of B at the same shared-memory offsets as the
+// descriptors name in the issuing CTA.
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive once on this CTA's `bar` when all previously issued CTA-pair MMAs of
+// this thread complete (their writes to both CTAs' TMEM and their reads of
+// both CTAs' shared memory).
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
 }
 // Arrive once on `bar` when all previously issued tcgen05 operations of this thread complete.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {

@@ -676,5 +676,269 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) tmem_dealloc(tmem, 2 * BN);
 }
 
+// CTA-pair variant: a cluster of two CTAs (on one TPC) computes 256 x BN
+// tiles with tcgen05.mma.cta_group::2, walking the tiles t = cluster,
+// cluster + clusters, ... like the persistent kernel.  Each CTA loads its own
+// operands into its own ring: 128 rows of A (the pair's rows 128 r ..) and
+// BN / 2 rows of B (columns BN / 2 r .. of the tile), so a pair moves half the
+// operand bytes of two one-SM tiles of the same work.  The even CTA issues
+// every MMA; its accumulator rows live in the even CTA's TMEM, the others in
+// the odd CTA's.  No multicast: the CTAs exchange plain mbarrier arrivals.
+//   warp 0 / lane 0 -- TMA producer of this CTA's ring;
+//   warp 1 / lane 0 -- even CTA: MMA issuer (waits for its own slot and the
+//                      odd CTA's `pfull` arrival); odd CTA: reports each
+//                      landed slot to the even CTA's `pfull`;
+//   warps 2..5      -- epilogue of this CTA's 128 rows from TMEM buffer i % 2;
+//                      all eight warps release the buffer on the even CTA's `acce`;
+//   warp 6 / lane 0 -- even CTA: passes each freed slot (`empty`) and each
+//                      finished accumulator (`accf`) on to the odd CTA.
+// The epilogue is the one-tile kernel's, so every kernel gives identical outputs
+// where the MMA sums each K = 16 slice the same way.
+template <int BN, int STAGES>
+struct GemmPairSmem {
+  static constexpr uint32_t kABytes = kBM * kBK * 2;         // 16 KiB: this CTA's 128 rows of A
+  static constexpr uint32_t kBBytes = (BN / 2) * kBK * 2;    // this CTA's BN / 2 rows of B
+  static constexpr uint32_t kStageBytes = kABytes + kBBytes;
+  static constexpr int kStages = STAGES;
+  // ring + barriers (full, empty, pfull [S]; accf, acce [2]; drain) + TMEM slot, plus 1 KiB for
+  // alignment and one more B half behind the ring, so that the last slot's B rows plus BN / 2
+  // rows stay inside this CTA's shared memory
+  static constexpr uint32_t kBytes = kStages * kStageBytes + kBBytes + 1024 + 512;
+  static constexpr uint32_t kTmemCols = 2 * BN;   // two accumulator buffers
+  static_assert(BN == 128 || BN == 256, "pair tiles are 256 x 128 or 256 x 256");
+  static_assert(kTmemCols <= 512, "TMEM columns");
+  static_assert(kBytes <= 227 * 1024, "shared memory per CTA");
+};
+
+template <int BN, int STAGES>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(224, 1)
+    tc_gemm_pair_kernel(const GemmProblem* __restrict__ probs, int nprob, int total, unsigned* status) {
+  using S = GemmPairSmem<BN, STAGES>;
+  constexpr int kPairM = 2 * kBM;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + S::kStages * S::kABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::kStages * S::kStageBytes + S::kBBytes);
+  uint64_t* empty = full + S::kStages;
+  uint64_t* pfull = empty + S::kStages;  // even CTA: the odd CTA's slot has landed
+  uint64_t* accf = pfull + S::kStages;   // [2] accumulator buffer ready
+  uint64_t* acce = accf + 2;             // [2] even CTA: buffer read out by all 8 epilogue warps
+  uint64_t* drain = acce + 2;            // every MMA of the pair has completed (teardown)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+
+  const uint32_t rank = cluster_ctarank();
+  const bool even = rank == 0;
+  const int cl = blockIdx.x / 2, ncl = gridDim.x / 2;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    if (cl < total) {   // the first tile's B rows of this CTA
+      const GemmProblem* P = find_problem(probs, nprob, cl);
+      tmap_acquire(&P->b);
+      prefetch_b_tile<BN / 2>(&P->b, P->K, P->N, ((cl - P->tile_begin) % P->tiles_n) * BN + (BN / 2) * rank);
+    }
+    for (int s = 0; s < S::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&pfull[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 8);
+    }
+    mbar_init(drain, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc_pair(tmem_slot, S::kTmemCols);
+    tmem_relinquish_pair();
+  }
+  fence_before_sync();
+  cluster_sync();   // both CTAs' barriers are initialised before any remote arrival
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  pdl_wait();
+  pdl_trigger();
+  const unsigned long long lim = wait_limit(status);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer; `it` counts K-slices over all tiles of this pair
+      int it = 0;
+      bool ok = true;
+      for (int t = cl; t < total && ok; t += ncl) {
+        const GemmProblem* P = find_problem(probs, nprob, t);
+        const int lt = t - P->tile_begin;
+        const int m0 = (lt / P->tiles_n) * kPairM + kBM * (int)rank;
+        const int n0 = (lt % P->tiles_n) * BN + (BN / 2) * (int)rank;
+        const int nk = (P->K + kBK - 1) / kBK, nkA = P->nkA;
+        const CUtensorMap* tmA = &P->a;
+        const CUtensorMap* tmB = &P->b;
+        tmap_acquire(tmA);
+        tmap_acquire(tmB);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % S::kStages;
+          if (it >= S::kStages) {
+            const bool got = even ? mbar_wait(&empty[s], ((it / S::kStages) & 1) ^ 1, lim)
+                                  : mbar_wait_cluster(&empty[s], ((it / S::kStages) & 1) ^ 1, lim);
+            if (!got) {
+              atomicOr(status, CRL_STATUS_TIMEOUT);
+              ok = false;
+              break;
+            }
+          }
+          mbar_arrive_expect_tx(&full[s], S::kStageBytes);
+          const int ka = nkA > 0 ? kb % nkA : kb;
+#pragma unroll
+          for (int r = 0; r < kBM / 64; ++r)
+            tma_load_2d(sA + s * S::kABytes + r * 8192, tmA, &full[s], ka * kBK, m0 + 64 * r);
+#pragma unroll
+          for (int r = 0; r < BN / 128; ++r)
+            tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kb * kBK, n0 + 64 * r);
+        }
+      }
+      drain_ring(full, S::kStages, it);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && even) {
+      // MMA issuer of the pair
+      constexpr uint32_t idesc = idesc_bf16_f32(kPairM, BN);
+      int it = 0, i = 0;
+      bool ok = true;
+      for (int t = cl; t < total && ok; t += ncl, ++i) {
+        const GemmProblem* P = find_problem(probs, nprob, t);
+        const int nk = (P->K + kBK - 1) / kBK;
+        const int buf = i & 1, use = i >> 1;
+        // all eight epilogue warps must have read out this buffer (tile i - 2)
+        if (use > 0 && !mbar_wait_cluster(&acce[buf], (use - 1) & 1, lim)) {
+          atomicOr(status, CRL_STATUS_TIMEOUT);
+          break;
+        }
+        fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % S::kStages;
+          const uint32_t par = (it / S::kStages) & 1;
+          if (!mbar_wait(&full[s], par, lim) || !mbar_wait_cluster(&pfull[s], par, lim)) {
+            atomicOr(status, CRL_STATUS_TIMEOUT);
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint64_t da = sdesc_kmajor_sw128(sA + s * S::kABytes);
+          const uint64_t db = sdesc_kmajor_sw128(sB + s * S::kBBytes);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            mma_bf16_pair(d, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          mma_commit_pair(&empty[s]);
+        }
+        if (ok) mma_commit_pair(&accf[buf]);
+      }
+      mma_commit_pair(drain);   // completes once every MMA issued above has
+    } else if (lane == 0) {
+      // odd CTA: report each landed slot to the MMA issuer
+      int it = 0;
+      bool ok = true;
+      for (int t = cl; t < total && ok; t += ncl) {
+        const GemmProblem* P = find_problem(probs, nprob, t);
+        const int nk = (P->K + kBK - 1) / kBK;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % S::kStages;
+          if (!mbar_wait(&full[s], (it / S::kStages) & 1, lim)) {
+            atomicOr(status, CRL_STATUS_TIMEOUT);
+            ok = false;
+            break;
+          }
+          mbar_arrive_remote(mapa_shared(&pfull[s], 0));
+        }
+      }
+    }
+  } else if (warp == 6) {
+    if (lane == 0 && even) {
+      // relay of the even CTA: every completed MMA slice frees the odd CTA's
+      // slot too, and every completed tile its accumulator rows (a thread of
+      // its own, so that no cluster-scope release waits behind the producer's
+      // copies or the epilogue's stores)
+      int it = 0, i = 0;
+      bool ok = true;
+      for (int t = cl; t < total && ok; t += ncl, ++i) {
+        const GemmProblem* P = find_problem(probs, nprob, t);
+        const int nk = (P->K + kBK - 1) / kBK;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % S::kStages;
+          if (!mbar_wait(&empty[s], (it / S::kStages) & 1, lim)) {
+            atomicOr(status, CRL_STATUS_TIMEOUT);
+            ok = false;
+            break;
+          }
+          mbar_arrive_remote(mapa_shared(&empty[s], 1));
+        }
+        if (!ok) break;
+        const int buf = i & 1, use = i >> 1;
+        if (!mbar_wait(&accf[buf], use & 1, lim)) {
+          atomicOr(status, CRL_STATUS_TIMEOUT);
+          break;
+        }
+        mbar_arrive_remote(mapa_shared(&accf[buf], 1));
+      }
+    }
+  } else {
+    // epilogue warps: this CTA's 128 rows of the pair's tile
+    const int eg = warp & 3;
+    int i = 0;
+    for (int t = cl; t < total; t += ncl, ++i) {
+      const int buf = i & 1, use = i >> 1;
+      const bool got = even ? mbar_wait(&accf[buf], use & 1, lim) : mbar_wait_cluster(&accf[buf], use & 1, lim);
+      const bool ok = __all_sync(0xffffffffu, got ? 1 : 0) != 0;
+      if (!ok) {
+        if (lane == 0) atomicOr(status, CRL_STATUS_TIMEOUT);
+        break;
+      }
+      fence_after_sync();
+      const GemmProblem* P = find_problem(probs, nprob, t);
+      const int lt = t - P->tile_begin;
+      const int m0 = (lt / P->tiles_n) * kPairM + kBM * (int)rank, n0 = (lt % P->tiles_n) * BN;
+      const int M = P->M, N = P->N;
+      const EpiDesc e = P->epi;
+      const int row = m0 + eg * 32 + lane;
+      const uint32_t lane_base = tmem + (uint32_t)(buf * BN) + ((uint32_t)(eg * 32) << 16);
+      const int ncol = (N - n0 < BN) ? N - n0 : BN;
+      if (e.kind == kEpiFwdOutEnergy) {
+        epilogue_energy(e, row, lane_base, ncol, M);
+      } else {
+#pragma unroll 1
+        for (int c = 0; c < ncol; c += 32) {
+          float v[32];
+          tmem_ld32(lane_base + c, v);
+          epilogue_chunk(e, row, n0 + c, v, M, N);
+        }
+      }
+      // release the buffer to the MMA issuer
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) {
+        if (even) mbar_arrive(&acce[buf]);
+        else mbar_arrive_remote(mapa_shared(&acce[buf], 0));
+      }
+    }
+  }
+  // teardown: no MMA may still write either CTA's accumulators when they are
+  // freed, and no remote arrival may reach a CTA that has left
+  fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (even) {
+      mbar_wait(drain, 0, kDrainLimitNs);
+      mbar_arrive_remote(mapa_shared(drain, 1));
+    } else {
+      mbar_wait_cluster(drain, 0, kDrainLimitNs);
+    }
+  }
+  fence_before_sync();
+  cluster_sync();
+  fence_after_sync();
+  if (warp == 0) tmem_dealloc_pair(tmem, S::kTmemCols);
+}
+
 }  // namespace tc
 }  // namespace crl

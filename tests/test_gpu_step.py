@@ -331,13 +331,15 @@ def test_update_step_matches_separate_calls(precision, path):
 @pytest.mark.parametrize("path", ["plain", "fused"])
 def test_persistent_gemm_matches_one_tile_gemm(path):
     """The persistent tensor-core GEMM (double-buffered TMEM, several tiles per CTA:
-    batch 2048 gives more tiles than SMs) and the one-tile kernel give bit-identical
-    update steps (fixed tile rule, so both run the same tile widths)."""
+    batch 2048 gives more tiles than SMs), the CTA-pair kernel (256-row tiles on
+    two SMs, tcgen05.mma.cta_group::2) and the one-tile kernel give bit-identical
+    update steps: each output element is the same sum of K = 16 slices whatever
+    the tile shape (fixed tile rule; batch 2048 takes no split-K)."""
     w = small(B=2048, hidden=512, repr=64, E=8, T=400)
     prev_tune = api.set_autotune(False)
     runs = []
     try:
-        for mode in ("one_tile", "persistent"):
+        for mode in ("one_tile", "persistent", "cta_pair"):
             prev = api.set_gemm_kernel(mode)
             try:
                 ctx, _, _ = setup(w, precision="bf16", path=path, n=300, mean_len=40.0)
@@ -354,13 +356,45 @@ def test_persistent_gemm_matches_one_tile_gemm(path):
                 api.set_gemm_kernel(prev)
     finally:
         api.set_autotune(prev_tune)
+    for r in runs[1:]:
+        np.testing.assert_array_equal(runs[0][0], r[0])
+        for n in ("phi", "psi", "pi"):
+            np.testing.assert_array_equal(runs[0][1][n], r[1][n], err_msg=n)
+
+
+@pytest.mark.parametrize("B,layernorm", [(520, False), (136, True)])
+def test_cta_pair_gemm_ragged_batches(B, layernorm):
+    """CTA-pair tiles over batches that end inside a 256-row tile (520 = 2 x 256 + 8:
+    the last pair's odd CTA holds no rows at all; 136: one pair, rows 128..135 in the
+    odd CTA) give the one-tile kernel's update steps bit for bit."""
+    w = small(B=B, hidden=256, repr=64, E=8, T=300, layernorm=layernorm)
+    prev_tune = api.set_autotune(False)
+    runs = []
+    try:
+        for mode in ("one_tile", "cta_pair"):
+            prev = api.set_gemm_kernel(mode)
+            try:
+                ctx, _, _ = setup(w, precision="bf16", path="fused", n=200, mean_len=30.0)
+                extra = workload.buffer_contents(w, n=2, mean_len=9.0, seed_offset=5)
+                loss = torch.zeros(6, dtype=torch.float32, device=ctx.device)
+                hist = []
+                for i in range(2):
+                    ctx.update_step(*(torch.from_numpy(x[i:i + 1]).to(ctx.device) for x in extra), loss_out=loss)
+                    hist.append(loss.cpu().numpy().copy())
+                torch.cuda.synchronize()
+                assert ctx.sync_status() == (0, 0)
+                runs.append((np.array(hist), {n: ctx.store[n]["params"].cpu().numpy() for n in ("phi", "psi", "pi")}))
+            finally:
+                api.set_gemm_kernel(prev)
+    finally:
+        api.set_autotune(prev_tune)
     np.testing.assert_array_equal(runs[0][0], runs[1][0])
     for n in ("phi", "psi", "pi"):
-        np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n])
+        np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n], err_msg=n)
 
 
 def test_gemm_kernel_mode_is_validated():
-    assert api.lib().crl_set_gemm_kernel(3) == api.E_INVALID_ARG
+    assert api.lib().crl_set_gemm_kernel(4) == api.E_INVALID_ARG
     assert api.set_gemm_kernel("any") == "any"
 
 

@@ -1,6 +1,6 @@
 """Failure detection without a GPU fault: the bounded device waits of the
-tensor-core kernels (grouped GEMMs, one-tile and persistent, and the fused
-energy stage).  A wait limit of one nanosecond makes the waits run out on
+tensor-core kernels (grouped GEMMs: one-tile, persistent and CTA-pair; the
+fused energy stage).  A wait limit of one nanosecond makes the waits run out on
 purpose: the step must return, crl_sync_status must report CRL_E_TIMEOUT, and
 after the limit is restored the same context must give exactly the results of
 a step that never timed out (the kernels drained their own copies and MMAs,
@@ -27,7 +27,7 @@ def critic_and_actor(ctx, s, a, g, eps):
     return lc.cpu().numpy().copy(), la.cpu().numpy().copy(), grads
 
 
-@pytest.mark.parametrize("kernel", ["one_tile", "persistent"])
+@pytest.mark.parametrize("kernel", ["one_tile", "persistent", "cta_pair"])
 @pytest.mark.parametrize("layernorm", [False, True])
 def test_waits_run_out_and_the_context_stays_usable(kernel, layernorm):
     w = small(B=256, hidden=256, repr=64, E=8, T=200, layernorm=layernorm)
