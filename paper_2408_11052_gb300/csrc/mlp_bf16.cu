@@ -650,7 +650,12 @@ int heuristic_cfg(const std::vector<tc::GemmProblem>& probs, int min_bn) {
   const int bn = std::max(ctas128 >= 148 ? 128 : 64, min_bn <= 64 ? 64 : (min_bn <= 128 ? 128 : 256));
   if (g_gemm_kernel == CRL_GEMM_PERSISTENT)
     return bn == 256 ? gemm_cfg(256, 4, 1) : (bn == 128 ? gemm_cfg(128, 6, 1) : gemm_cfg(64, 8, 1));
-  if (g_gemm_kernel == CRL_GEMM_CTA_PAIR) return bn == 256 ? gemm_cfg(256, 6, 2) : gemm_cfg(128, 8, 2);
+  if (g_gemm_kernel == CRL_GEMM_CTA_PAIR) {
+    // pair tiles want width: 256 columns wherever every problem has them
+    int nmin = 1 << 30;
+    for (const auto& p : probs) nmin = std::min(nmin, p.N);
+    return (bn == 256 || nmin >= 256) ? gemm_cfg(256, 6, 2) : gemm_cfg(128, 8, 2);
+  }
   return bn == 256 ? gemm_cfg(256, 4) : (bn == 128 ? gemm_cfg(128, 4) : gemm_cfg(64, 4));
 }
 
