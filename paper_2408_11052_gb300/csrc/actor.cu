@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) diag_energy_loss_kernel(const __grid_cons
   diag_energy_loss_body(p, blockIdx.x, gridDim.x);
 }
 
-// dz != null: the gradient is written as BF16 dz [B][ldz] and dz^T [2A][ldt]
+// dz != null: the gradient is written as BF16 dz [B][ldz]
 // (the policy network's output gradient) instead of dout.
 template <typename T>
 __device__ __forceinline__ void head_backward_body(const HeadBwdArgs<T>& p, int lb) {
@@ -166,8 +166,7 @@ __device__ __forceinline__ void head_backward_body(const HeadBwdArgs<T>& p, int 
   const T* __restrict__ da = p.da;
   T* __restrict__ dout = p.dout;
   __nv_bfloat16* __restrict__ dz = p.dz;
-  __nv_bfloat16* __restrict__ dzT = p.dzT;
-  const int ldz = p.ldz, ldt = p.ldt;
+  const int ldz = p.ldz;
   const int b = lb * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const T ab = T((p.alpha_used ? *p.alpha_used : alpha) / B);
@@ -186,8 +185,6 @@ __device__ __forceinline__ void head_backward_body(const HeadBwdArgs<T>& p, int 
       const __nv_bfloat16 hu = __float2bfloat16_rn((float)du), hl = __float2bfloat16_rn((float)dlv);
       dz[(size_t)b * ldz + d] = hu;
       dz[(size_t)b * ldz + A + d] = hl;
-      dzT[(size_t)d * ldt + b] = hu;
-      dzT[(size_t)(A + d) * ldt + b] = hl;
     } else {
       dout[(size_t)b * 2 * A + d] = du;
       dout[(size_t)b * 2 * A + A + d] = dlv;
@@ -285,10 +282,10 @@ void actor_energy_and_loss(const ActorSpec& as, const T* phi, const T* psi, cons
 
 template <typename T>
 void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used, const T* da, int B, T* dout,
-                         cudaStream_t st, __nv_bfloat16* dz, int ldz, __nv_bfloat16* dzT, int ldt) {
+                         cudaStream_t st, __nv_bfloat16* dz, int ldz) {
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 6);
-  const HeadBwdArgs<T> p{B,  as.A, as.alpha, pi_out, eps_used, da,
-                         dout, dz, ldz,     dzT,    ldt,      as.tune.state ? as.tune.state + 3 : nullptr};
+  const HeadBwdArgs<T> p{B, as.A, as.alpha, pi_out, eps_used, da, dout, dz, ldz,
+                         as.tune.state ? as.tune.state + 3 : nullptr};
   launch_k(head_backward_kernel<T>, dim3(ceil_div(B, 256)), dim3(256), 0, st, p);
 }
 
@@ -300,7 +297,7 @@ void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used
                                          void*, unsigned*, unsigned*, int*, unsigned long long*,                 \
                                          const unsigned long long*, cudaStream_t, __nv_bfloat16*, int);          \
   template void actor_head_backward<T>(const ActorSpec&, const T*, const T*, const T*, int, T*, cudaStream_t,    \
-                                       __nv_bfloat16*, int, __nv_bfloat16*, int);
+                                       __nv_bfloat16*, int);
 CRL_INST_ACTOR(float)
 CRL_INST_ACTOR(double)
 

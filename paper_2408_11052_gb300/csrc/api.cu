@@ -339,8 +339,7 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     bf_refresh(c, CRL_NET_PI, refresh, st);
   }
   // fused path: the encoders' output layers also write the energy's BF16 operands
-  const EnergyOut eo[2] = {{c->etc.X, c->etc.XT, c->etc.ldt, c->etc.auxX, cf.energy},
-                           {c->etc.Y, c->etc.YT, c->etc.ldt, c->etc.auxY, cf.energy}};
+  const EnergyOut eo[2] = {{c->etc.X, c->etc.auxX, cf.energy}, {c->etc.Y, c->etc.auxY, cf.energy}};
   BfPass fpass[3] = {pass[0], pass[1], pass[2]};
   if (c->fused) {
     fpass[0].energy_out = &eo[0];
@@ -359,8 +358,8 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     const char* e = energy_tc_maps(c->etc, B);
     if (e) throw Failure(CRL_E_CUDA, std::string("tensor map: ") + e);
     energy_tc_forward(c->etc, ls, B, loss, rl, cl, c->etc_ws, status, apply ? &c->ctr->t_critic : nullptr, st);
-    energy_tc_backward(c->etc, ls, B, P.y, Q.y, rl, cl, 1.0, P.dz[P.layers], P.dzT[P.layers], Q.dz[Q.layers],
-                       Q.dzT[Q.layers], P.Mmax, c->etc_ws, status, st);
+    energy_tc_backward(c->etc, ls, B, P.y, Q.y, rl, cl, 1.0, P.dz[P.layers], Q.dz[Q.layers], c->etc_ws, status,
+                       st);
   } else {
     infonce_forward<float>(ls, P.y, Q.y, B, cf.repr, loss, rl, cl, c->ws, CRL_PATH_PLAIN, status,
                            apply ? &c->ctr->t_critic : nullptr, st);
@@ -426,8 +425,7 @@ void actor_impl_bf16(crl_ctx* c, const float* s, const float* g, const float* ep
                                bump_step ? &c->ctr->step : nullptr, &c->ctr->last_step, st, P.dz[P.layers],
                                P.L[P.layers].out_pad);
   bf_check(bf_backward(c->groups, fwd, 1, status, st));
-  actor_head_backward<float>(as, PI.y, eps_used, da, B, nullptr, st, PI.dz[PI.layers], PI.L[PI.layers].out_pad,
-                             PI.dzT[PI.layers], PI.Mmax);
+  actor_head_backward<float>(as, PI.y, eps_used, da, B, nullptr, st, PI.dz[PI.layers], PI.L[PI.layers].out_pad);
   const BfPass pi_pass[1] = {{&PI, ppi, static_cast<float*>(c->nets[CRL_NET_PI].grads), nullptr, B}};
   bf_check(bf_backward(c->groups, pi_pass, 1, status, st));
   if (apply) {
@@ -520,7 +518,7 @@ RelabelArgs relabel_args(crl_ctx* c, uint64_t step, int B, float* s, float* a, f
   if (pack_bf16) {
     for (int k = 0; k < 3; ++k) {
       BfNet& n = c->bf[k];
-      ra.pack[k] = RelabelPack{n.x0, bf_net_x0_ld(n), n.x0T, n.Mmax};
+      ra.pack[k] = RelabelPack{n.x0, bf_net_x0_ld(n)};
     }
   }
   ra.spw = relabel_spw(B);
@@ -1036,7 +1034,7 @@ int crl_mlp_saved_bytes(const crl_mlp_desc* d, int32_t M, size_t* bytes) {
     MlpShape s{d->in0, d->in1, d->hidden, d->layers, d->out, d->layernorm ? 1 : 0};
     if (d->dtype == CRL_PREC_BF16) {
       *bytes = mlp_bf16_saved_bytes(s, M);
-      CRL_REQUIRE(*bytes > 0, CRL_E_UNSUPPORTED, "LayerNorm hidden width above 6396 on the BF16 path");
+      CRL_REQUIRE(*bytes > 0, CRL_E_UNSUPPORTED, "this MLP shape has no BF16 buffer layout");
     } else {
       *bytes = mlp_saved_bytes(s, M, dtype_size(d->dtype));
     }

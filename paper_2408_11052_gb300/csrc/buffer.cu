@@ -282,13 +282,12 @@ __device__ __forceinline__ void relabel_body(const BufferDev& bd, const RelabelA
       }
     }
     if (lane < ra.G) ra.g[(size_t)bj * ra.G + lane] = grow[ra.goal_idx[lane]];
-    // BF16 split packs of the network inputs (hi, lo interleaved; transposed copy)
+    // BF16 split packs of the network inputs (hi, lo interleaved)
     for (int kk = 0; kk < 3; ++kk) {
       const RelabelPack& pk = ra.pack[kk];
       if (pk.x0 == nullptr) continue;
       const int ncol = (kk == 0) ? DA : (kk == 1 ? ra.G : D + ra.G);
       __nv_bfloat16* x0 = static_cast<__nv_bfloat16*>(pk.x0);
-      __nv_bfloat16* xT = static_cast<__nv_bfloat16*>(pk.x0T);
       for (int c = lane; c < ncol; c += kWarp) {
         float v;
         if (kk == 0) v = row[c];
@@ -298,8 +297,6 @@ __device__ __forceinline__ void relabel_body(const BufferDev& bd, const RelabelA
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
         x0[(size_t)bj * pk.ld + 2 * c] = hi;
         x0[(size_t)bj * pk.ld + 2 * c + 1] = lo;
-        xT[(size_t)(2 * c) * pk.ldt + bj] = hi;
-        xT[(size_t)(2 * c + 1) * pk.ldt + bj] = lo;
       }
     }
   }
@@ -309,22 +306,11 @@ __device__ __forceinline__ void relabel_body(const BufferDev& bd, const RelabelA
 __device__ __host__ __forceinline__ int pack_cols(int k, int D, int A, int G) {
   return k == 0 ? D + A : (k == 1 ? G : D + G);
 }
-size_t relabel_pack_smem(const BufferDev& bd, const RelabelArgs& ra) {
-  size_t bytes = 0;
-  for (int k = 0; k < 3; ++k)
-    if (ra.pack[k].x0) bytes += (size_t)2 * pack_cols(k, bd.D, bd.A, ra.G) * 33 * 2;
-  return bytes;
-}
 
 // Relabel with the BF16 network-input packs (the update step): a block of 32
 // warps takes 32 consecutive samples, one per warp (lane 0 draws the indices,
-// the warp copies the row).  Each warp writes its sample's split inputs
-// row-major and stages them in shared memory ([2 c][33] per pack, padded
-// against bank conflicts); the block then writes the transposed copies with
-// each column's 32 samples contiguous.
+// the warp copies the row and writes its sample's split inputs row-major).
 __device__ __forceinline__ void relabel_pack_body(const BufferDev& bd, const RelabelArgs& ra, int lb) {
-  extern __shared__ __align__(16) unsigned char relabel_smem[];
-  __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(relabel_smem);
   const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
   const int b0 = lb * kWarp;
   const int b = b0 + w;
@@ -359,7 +345,6 @@ __device__ __forceinline__ void relabel_pack_body(const BufferDev& bd, const Rel
       else ra.a[(size_t)b * bd.A + (c - D)] = v;
     }
     if (lane < ra.G) ra.g[(size_t)b * ra.G + lane] = grow[ra.goal_idx[lane]];
-    __nv_bfloat16* sk = stage;
     for (int kk = 0; kk < 3; ++kk) {
       const RelabelPack& pk = ra.pack[kk];
       if (pk.x0 == nullptr) continue;
@@ -374,25 +359,8 @@ __device__ __forceinline__ void relabel_pack_body(const BufferDev& bd, const Rel
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
         x0[(size_t)b * pk.ld + 2 * c] = hi;
         x0[(size_t)b * pk.ld + 2 * c + 1] = lo;
-        sk[(2 * c) * 33 + w] = hi;
-        sk[(2 * c + 1) * 33 + w] = lo;
       }
-      sk += 2 * ncol * 33;
     }
-  }
-  __syncthreads();
-  const int nb = min(kWarp, ra.B - b0);
-  const __nv_bfloat16* sk = stage;
-  for (int kk = 0; kk < 3; ++kk) {
-    const RelabelPack& pk = ra.pack[kk];
-    if (pk.x0 == nullptr) continue;
-    const int rows = 2 * pack_cols(kk, D, bd.A, ra.G);
-    __nv_bfloat16* xT = static_cast<__nv_bfloat16*>(pk.x0T);
-    for (int idx = threadIdx.x; idx < rows * kWarp; idx += blockDim.x) {
-      const int col = idx / kWarp, j = idx % kWarp;
-      if (j < nb) xT[(size_t)col * pk.ldt + b0 + j] = sk[col * 33 + j];
-    }
-    sk += rows * 33;
   }
 }
 
@@ -454,13 +422,7 @@ void launch_relabel(const BufferDev& bd, const RelabelArgs& ra, cudaStream_t st)
   RelabelArgs r = ra;
   r.spw = relabel_spw(ra.B);
   if (relabel_packs(r)) {
-    const size_t smem = relabel_pack_smem(bd, r);
-    static size_t attr = 0;
-    if (smem > 48 * 1024 && smem > attr) {
-      cudaFuncSetAttribute(relabel_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = smem;
-    }
-    launch_k(relabel_pack_kernel, dim3(relabel_blocks(r)), dim3(1024), smem, st, bd, r);
+    launch_k(relabel_pack_kernel, dim3(relabel_blocks(r)), dim3(1024), 0, st, bd, r);
   } else {
     launch_k(relabel_kernel, dim3(relabel_blocks(r)), dim3(256), 0, st, bd, r);
   }

@@ -822,10 +822,8 @@ struct BwdArgs {
   const float* lse_other;  // c (row pass) or r (column pass)
   const float* own_f32;    // [B][R] FP32 representation (cos: unnormalised)
   bf16* d_out;             // [B][R]
-  bf16* d_outT;            // [R][ldt]
-  int ldt;
   unsigned* status;
-  float* d_out_f32;        // non-null: the gradient as FP32 [B][R] here instead of d_out / d_outT
+  float* d_out_f32;        // non-null: the gradient as FP32 [B][R] here instead of d_out
 };
 
 // Offset in a 128-byte-swizzled K-major tile (8-row groups of 1024 bytes) of
@@ -1319,8 +1317,6 @@ __device__ __forceinline__ void bwd_body(const CUtensorMap* tmX, const CUtensorM
             uint4* dst = reinterpret_cast<uint4*>(a.d_out + (size_t)u * a.R + c);
 #pragma unroll
             for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4*>(o)[k];
-#pragma unroll
-            for (int k = 0; k < 32; ++k) a.d_outT[(size_t)(c + k) * a.ldt + u] = o[k];
           }
         }
       }
@@ -1474,7 +1470,7 @@ FwdArgs fwd_args(const EnergyTc& e, const LossSpec& ls, int B, void* ws, float* 
 
 // Backward arguments of the row pass (own = phi), member by member into zeroed storage.
 BwdArgs bwd_args(const EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* r, const float* c,
-                 double dtotal, bf16* dphi, bf16* dphiT, int ldt, unsigned* status, const FwdArgs& f) {
+                 double dtotal, bf16* dphi, unsigned* status, const FwdArgs& f) {
   BwdArgs a;
   memset(&a, 0, sizeof(a));
   a.B = B;
@@ -1495,8 +1491,6 @@ BwdArgs bwd_args(const EnergyTc& e, const LossSpec& ls, int B, const float* phi,
   a.lse_other = c;
   a.own_f32 = phi;
   a.d_out = dphi;
-  a.d_outT = dphiT;
-  a.ldt = ldt;
   a.status = status;
   return a;
 }
@@ -1607,13 +1601,13 @@ void launch_bwd_multi(int kind, const EnergyTask* dt, const int* db, int na, int
 }  // namespace
 
 void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
-                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dphiT,
-                        __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, void* ws, unsigned* status,
+                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dpsi, void* ws,
+                        unsigned* status,
                         cudaStream_t st) {
   const int n = (B + kTile - 1) / kTile;
   const size_t sm = bwd_smem(e.R);
   const FwdArgs f = fwd_args(e, ls, B, ws, nullptr, nullptr, nullptr, nullptr, status);
-  const BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, dphi, dphiT, ldt, status, f);
+  const BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, dphi, status, f);
   BwdArgs b = a;
   b.transposed = 1;
   b.aux_own = e.auxY;
@@ -1622,7 +1616,6 @@ void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi
   b.lse_other = r;
   b.own_f32 = psi;
   b.d_out = dpsi;
-  b.d_outT = dpsiT;
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 8.0 * B * B * e.R);
   switch (obj_kind(ls.loss)) {
     case kObjFB: launch_bwd_t<kObjFB>(e, a, b, n, sm, st); break;
@@ -1640,7 +1633,7 @@ void energy_tc_backward_f32(EnergyTc& e, const LossSpec& ls, int B, const float*
   const int n = (B + kTile - 1) / kTile;
   const size_t sm = bwd_smem(e.R);
   const FwdArgs f = fwd_args(e, ls, B, ws, nullptr, nullptr, nullptr, nullptr, status);
-  BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, nullptr, nullptr, 0, status, f);
+  BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, nullptr, status, f);
   a.d_out_f32 = dphi;
   BwdArgs b = a;
   b.transposed = 1;
@@ -1688,7 +1681,7 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     t.s0 = PrepSide{g.phi, e.X, e.XT, e.auxX};
     t.s1 = PrepSide{g.psi, e.Y, e.YT, e.auxY};
     t.f = fwd_args(e, g.ls, g.B, g.ws, g.loss4, g.r, g.c, g.t_bump, g.status);
-    t.row = bwd_args(e, g.ls, g.B, g.phi, g.r, g.c, 1.0, g.dphi, g.dphiT, g.ldt, g.status, t.f);
+    t.row = bwd_args(e, g.ls, g.B, g.phi, g.r, g.c, 1.0, g.dphi, g.status, t.f);
     t.col = t.row;
     t.col.transposed = 1;
     t.col.aux_own = e.auxY;
@@ -1697,7 +1690,6 @@ const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& ag
     t.col.lse_other = g.r;
     t.col.own_f32 = g.psi;
     t.col.d_out = g.dpsi;
-    t.col.d_outT = g.dpsiT;
     const int nb = stage == 0 ? 2 * ceil_div(g.B, 32) : (stage == 1 ? t.n * t.f.nC : 2 * t.n);
     begin[i + 1] = begin[i] + nb;
     Rmax = std::max(Rmax, e.R);

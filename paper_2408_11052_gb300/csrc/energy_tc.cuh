@@ -29,12 +29,11 @@ void energy_tc_prepare(EnergyTc& e, const LossSpec& ls, const float* phi, const 
 // loss4 = {total, fwd, bwd, penalty}; r, c = row / column logsumexp.  ws: energy_tc_ws_bytes(B).
 void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, float* r, float* c, void* ws,
                        unsigned* status, int* t_bump, cudaStream_t st);
-// dphi / dpsi as BF16 [B][R] and transposed [R][ldt] (the encoders' dy layout), scaled by dtotal.
+// dphi / dpsi as BF16 [B][R] (the encoders' dy layout), scaled by dtotal.
 // ws: the forward's workspace (its anchors and diagonal coefficients for DPO / IPO).
 void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
-                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dphiT,
-                        __nv_bfloat16* dpsi, __nv_bfloat16* dpsiT, int ldt, void* ws, unsigned* status,
-                        cudaStream_t st);
+                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dpsi, void* ws,
+                        unsigned* status, cudaStream_t st);
 
 // The same backward with dphi / dpsi as FP32 [B][R] (the op-level entry points).
 void energy_tc_backward_f32(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi,
@@ -58,10 +57,7 @@ struct EnergyAgent {
   void* ws;           // energy_tc_ws_bytes(B), zeroed at creation
   int* t_bump;
   __nv_bfloat16* dphi;
-  __nv_bfloat16* dphiT;
   __nv_bfloat16* dpsi;
-  __nv_bfloat16* dpsiT;
-  int ldt;
   unsigned* status;
 };
 // stage 0: prepare, 1: forward (+ loss), 2: backward -- one launch over all agents.

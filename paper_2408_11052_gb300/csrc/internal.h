@@ -28,14 +28,11 @@ struct BufferDev {
 };
 
 // Optional BF16 packing of a network input by the relabel kernel: the split
-// (hi, lo) interleaved row-major copy x0 [Mmax][ld] and its transpose x0T
-// [2 in][ldt] (see mlp_bf16.cuh).  Source columns: kind 0 = concat(s, a),
-// 1 = g, 2 = concat(s, g).
+// (hi, lo) interleaved row-major copy x0 [Mmax][ld] (see mlp_bf16.cuh).
+// Source columns: kind 0 = concat(s, a), 1 = g, 2 = concat(s, g).
 struct RelabelPack {
   void* x0;
   int ld;
-  void* x0T;
-  int ldt;
 };
 
 struct RelabelArgs {
@@ -81,7 +78,6 @@ struct RelabelTask {
 int relabel_spw(int B);
 bool relabel_packs(const RelabelArgs& ra);
 int relabel_blocks(const RelabelArgs& ra);
-size_t relabel_pack_smem(const BufferDev& bd, const RelabelArgs& ra);  // shared memory of the pack kernels
 // tasks / begin: device tables (n tasks, n + 1 block offsets).  packs: every
 // task writes the BF16 input packs (smem: the largest task's relabel_pack_smem).
 void launch_relabel_multi(const RelabelTask* tasks, const int* begin, int n, int blocks, double bytes, bool packs,
@@ -209,8 +205,6 @@ struct HeadBwdArgs {
   T* dout;
   __nv_bfloat16* dz;                // optional BF16 output gradient (see actor_head_backward)
   int ldz;
-  __nv_bfloat16* dzT;
-  int ldt;
   const double* alpha_used;         // non-null: the alpha the actor loss used (overrides alpha)
 };
 // Diagonal energy, dphi (T, or BF16 into dz [B][ldz] when dz != null) and the
@@ -223,11 +217,10 @@ void actor_energy_and_loss(const ActorSpec& as, const T* phi, const T* psi, cons
                            T* dphi, T* fdiag, T* loss2, void* ws, unsigned* ticket, unsigned* status,
                            int* t_bump, unsigned long long* step_bump, const unsigned long long* last_step,
                            cudaStream_t st, __nv_bfloat16* dz = nullptr, int ldz = 0);
-// dz != null: the output gradient is written as BF16 dz [B][ldz] and dz^T [2A][ldt] instead of dout.
+// dz != null: the output gradient is written as BF16 dz [B][ldz] instead of dout.
 template <typename T>
 void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used, const T* da, int B,
-                         T* dout, cudaStream_t st, __nv_bfloat16* dz = nullptr, int ldz = 0,
-                         __nv_bfloat16* dzT = nullptr, int ldt = 0);
+                         T* dout, cudaStream_t st, __nv_bfloat16* dz = nullptr, int ldz = 0);
 
 class BlobCache;
 // Several agents in one launch each (float tasks of the BF16 path; tables cached in `cache`).

@@ -138,19 +138,14 @@ void pack(int rows, const float* s0, int ld0, int n0, const float* s1, int ld1, 
 // LayerNorm kernels: one warp per row, 8 rows per 256-thread block.  Rows of
 // up to 1024 values stay in registers (float4 pieces, lane-strided), so the
 // statistics and the output take one pass over global memory; wider rows loop
-// over global memory.  The block stages its BF16 output rows in shared memory
-// ([8][H + 4], padded against bank conflicts) and writes the transposed copy as
-// 16-byte pieces of 8 rows.
+// over global memory.
 constexpr int kLnRows = 8;
 constexpr int kLnRegVec = 8;   // float4 pieces per lane held in registers (H <= 1024)
-inline size_t ln_smem_bytes(int H) { return (size_t)kLnRows * (H + 4) * 2; }
 constexpr int kLnMaxSmem = 200 * 1024;
 inline int ln_vec(int H) { return (H + 127) / 128 <= kLnRegVec ? (H + 127) / 128 : 0; }
-// The backward's register path also stages the rows' du zhat and du ([2][8][H] FP32)
+// The backward's register path stages the rows' du zhat and du ([2][8][H] FP32)
 // for the column sums.
-inline size_t ln_bwd_smem_bytes(int H) {
-  return ((ln_smem_bytes(H) + 15) & ~(size_t)15) + (ln_vec(H) > 0 ? (size_t)2 * kLnRows * H * 4 : 0);
-}
+inline size_t ln_bwd_smem_bytes(int H) { return ln_vec(H) > 0 ? (size_t)2 * kLnRows * H * 4 : 0; }
 // Deterministic two-level reduction of the LayerNorm parameter gradients: the
 // blocks' column sums go in groups of ln_group(nblk) (at most 63 groups: one
 // ticket word each, plus one for the final level).
@@ -161,32 +156,14 @@ inline size_t ln_partial_floats(int Mmax, int H) {
   return (size_t)(nblk + ng) * 2 * H;
 }
 
-// Transposed store of the staged [8][H] BF16 tile (row stride H + 4) into
-// dst [H][ldt] at rows row0 .. row0 + 7 (clipped to M).
-__device__ __forceinline__ void ln_store_transposed(const bf16* tile, int H, bf16* dst, int ldt, int row0, int M) {
-  const int S = H + 4;
-  for (int c = threadIdx.x; c < H; c += blockDim.x) {
-    alignas(16) bf16 v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = tile[k * S + c];
-    bf16* d = dst + (size_t)c * ldt + row0;
-    if (row0 + 8 <= M) {
-      *reinterpret_cast<uint4*>(d) = *reinterpret_cast<const uint4*>(v);
-    } else {
-      for (int k = 0; k < M - row0; ++k) d[k] = v[k];
-    }
-  }
-}
-
 struct LnFwdNet {
-  int M, ldt;
+  int M;
   float* z;
   float* rstd;
   const float* g;
   const float* beta;
-  bf16* h;      // [M][ldh]: hi part in columns [0, H), lo part in [ldh / 2, ldh / 2 + H)
-  bf16* hT;
-  int ldh;
+  bf16* h;      // [M][ldh]: hi part in columns [0, H), lo part in [hlo, hlo + H)
+  int ldh, hlo;
 };
 struct LnFwdGroup {
   LnFwdNet n[kMaxGroupNets];
@@ -206,16 +183,13 @@ __device__ __forceinline__ uint2 ln_relu_pack(float4 x, float4 gg, float4 bb, ui
 }
 
 // LayerNorm forward over rows of z [M][H] (FP32, replaced by zhat), rstd [M],
-// h = ReLU(zhat * g + beta) written as BF16 hi / lo parts [M][ldh] and the hi
-// part transposed [H][ldt].
+// h = ReLU(zhat * g + beta) written as BF16 hi / lo parts [M][ldh].
 // NV > 0: the row in registers (NV float4 per lane); NV = 0: three passes.
 template <int NV>
 __global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constant__ LnFwdGroup grp) {
   pdl_enter();
-  extern __shared__ __align__(16) unsigned char ln_smem[];
-  bf16* tile = reinterpret_cast<bf16*>(ln_smem);
   const LnFwdNet& a = grp.n[blockIdx.y];
-  const int M = a.M, S = H + 4;
+  const int M = a.M;
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   const int row0 = blockIdx.x * kLnRows;
   if (row0 >= M) return;
@@ -226,8 +200,7 @@ __global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constan
     const float4* g4 = reinterpret_cast<const float4*>(a.g);
     const float4* b4 = reinterpret_cast<const float4*>(a.beta);
     uint2* hr = reinterpret_cast<uint2*>(a.h + (size_t)row * a.ldh);
-    uint2* hl = reinterpret_cast<uint2*>(a.h + (size_t)row * a.ldh + a.ldh / 2);
-    uint2* tr = reinterpret_cast<uint2*>(tile + w * S);
+    uint2* hl = reinterpret_cast<uint2*>(a.h + (size_t)row * a.ldh + a.hlo);
     if constexpr (NV > 0) {
       float4 x[NV];
       float s = 0.f;
@@ -258,10 +231,8 @@ __global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constan
         xn.w = (x[j].w - mean) * rs;
         zr[q] = xn;
         uint2 lo;
-        const uint2 v = ln_relu_pack(xn, g4[q], b4[q], lo);
-        hr[q] = v;
+        hr[q] = ln_relu_pack(xn, g4[q], b4[q], lo);
         hl[q] = lo;
-        tr[q] = v;
       }
     } else {
       float s = 0.f;
@@ -286,25 +257,20 @@ __global__ void __launch_bounds__(256) ln_fwd_kernel(int H, const __grid_constan
         x.w = (x.w - mean) * rs;
         zr[q] = x;
         uint2 lo;
-        const uint2 v = ln_relu_pack(x, g4[q], b4[q], lo);
-        hr[q] = v;
+        hr[q] = ln_relu_pack(x, g4[q], b4[q], lo);
         hl[q] = lo;
-        tr[q] = v;
       }
     }
   }
-  __syncthreads();
-  ln_store_transposed(tile, H, a.hT, a.ldt, row0, M);
 }
 
 struct LnBwdNet {
-  int M, ldt;
+  int M;
   const float* du;
   const float* zhat;
   const float* rstd;
   const float* g;
   bf16* dz;
-  bf16* dzT;
   float* dg;          // null: no LayerNorm parameter gradients
   float* db;
   float* partial;     // [nblk][2][H] per-block column sums (dg, db), then [ngroups][2][H] group sums
@@ -323,7 +289,7 @@ __device__ __forceinline__ uint2 ln_bwd_pack(float4 d, float4 z, float4 gg, floa
 }
 
 // LayerNorm backward: du (ReLU-masked, FP32) -> dz = rstd (g du - mean(g du) -
-// zhat mean(g du zhat)), written BF16 [M][H] and transposed; with dg / db the
+// zhat mean(g du zhat)), written BF16 [M][H]; with dg / db the
 // gain and shift gradients dg = sum_m du zhat, db = sum_m du: every block
 // writes its 8 rows' column sums; the last block of each group of blocks
 // (ticket) adds its group's sums in block order, and the last group to finish
@@ -332,12 +298,11 @@ template <int NV>
 __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constant__ LnBwdGroup grp) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char ln_smem[];
-  bf16* tile = reinterpret_cast<bf16*>(ln_smem);
-  // register path: [2][8][H] FP32 (du zhat, du) of the block's rows, after the tile
-  float* colbuf = reinterpret_cast<float*>(ln_smem + (((size_t)kLnRows * (H + 4) * 2 + 15) & ~(size_t)15));
+  // register path: [2][8][H] FP32 (du zhat, du) of the block's rows
+  float* colbuf = reinterpret_cast<float*>(ln_smem);
   __shared__ int s_last;
   const LnBwdNet& a = grp.n[blockIdx.y];
-  const int M = a.M, S = H + 4;
+  const int M = a.M;
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   const int row0 = blockIdx.x * kLnRows;
   const int nblk = (M + kLnRows - 1) / kLnRows;
@@ -350,7 +315,6 @@ __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constan
     const float4* zr = reinterpret_cast<const float4*>(a.zhat + (size_t)row * H);
     const float rs = a.rstd[row];
     uint2* out = reinterpret_cast<uint2*>(a.dz + (size_t)row * H);
-    uint2* tr = reinterpret_cast<uint2*>(tile + w * S);
     if constexpr (NV > 0) {
       float4 d[NV], z[NV];
       float s1 = 0.f, s2 = 0.f;
@@ -374,9 +338,7 @@ __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constan
       for (int j = 0; j < NV; ++j) {
         const int q = lane + 32 * j;
         if (q >= nv) continue;
-        const uint2 v = ln_bwd_pack(d[j], z[j], g4[q], s1, s2, rs);
-        out[q] = v;
-        tr[q] = v;
+        out[q] = ln_bwd_pack(d[j], z[j], g4[q], s1, s2, rs);
         if (a.dg != nullptr) {
           cz[q] = make_float4(d[j].x * z[j].x, d[j].y * z[j].y, d[j].z * z[j].z, d[j].w * z[j].w);
           cd[q] = d[j];
@@ -393,15 +355,12 @@ __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constan
       s1 = warp_sum(s1) / H;
       s2 = warp_sum(s2) / H;
       for (int q = lane; q < nv; q += 32) {
-        const uint2 v = ln_bwd_pack(dr[q], zr[q], g4[q], s1, s2, rs);
-        out[q] = v;
-        tr[q] = v;
+        out[q] = ln_bwd_pack(dr[q], zr[q], g4[q], s1, s2, rs);
       }
     }
   }
-  __syncthreads();
-  ln_store_transposed(tile, H, a.dzT, a.ldt, row0, M);
   if (a.dg == nullptr) return;
+  __syncthreads();
   // column sums of this block's rows (rows in order)
   const int rmax = min(kLnRows, M - row0);
   for (int c = threadIdx.x; c < H; c += blockDim.x) {
@@ -475,7 +434,7 @@ void launch_ln_fwd_t(int H, dim3 grid, cudaStream_t st, const LnFwdGroup& grp) {
     cudaFuncSetAttribute(ln_fwd_kernel<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLnMaxSmem);
     attr = true;
   }
-  launch_k(ln_fwd_kernel<NV>, grid, dim3(256), ln_smem_bytes(H), st, H, grp);
+  launch_k(ln_fwd_kernel<NV>, grid, dim3(256), 0, st, H, grp);
 }
 template <int NV>
 void launch_ln_bwd_t(int H, dim3 grid, cudaStream_t st, const LnBwdGroup& grp) {
@@ -502,9 +461,10 @@ void launch_ln_fwd(int H, dim3 grid, cudaStream_t st, const LnFwdGroup& grp) { C
 void launch_ln_bwd(int H, dim3 grid, cudaStream_t st, const LnBwdGroup& grp) { CRL_LN_DISPATCH(launch_ln_bwd_t) }
 #undef CRL_LN_DISPATCH
 
-__global__ void fill_bf16_kernel(bf16* p, size_t n, float v) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    p[i] = __float2bfloat16_rn(v);
+// One column of a row-major BF16 matrix: p[r * ld] = v for r < rows.
+__global__ void fill_col_bf16_kernel(bf16* p, int rows, int ld, float v) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
+    p[(size_t)r * ld] = __float2bfloat16_rn(v);
 }
 
 const char* mk(CUtensorMap* m, const void* base, int inner, int rows, int stride) {
@@ -800,7 +760,6 @@ void GemmGroups::reset() {
 }
 
 const char* bf_net_carve(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner, bool weight_maps) {
-  if (s.layernorm && ln_smem_bytes(s.hidden) > (size_t)kLnMaxSmem) return "LayerNorm hidden width above 6396";
   n.s = s;
   n.Mmax = Mmax;
   n.layers = s.layers;
@@ -846,12 +805,12 @@ const char* bf_net_carve(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, 
     if (!L.wpart || !L.wtick) return "device allocation failed";
   }
   const int in = s.in(), out = s.out;
-  n.ldh = 2 * ((H + 63) / 64 * 64);
-  n.x0 = static_cast<bf16*>(A((size_t)Mmax * pad8(2 * in) * 2));
-  n.x0T = static_cast<bf16*>(A((size_t)(2 * in + 1) * Mmax * 2));
+  const int Hp = (H + 63) / 64 * 64;
+  n.hlo = 2 * Hp;
+  n.ldh = 4 * Hp;
+  n.x0 = static_cast<bf16*>(A((size_t)Mmax * pad8(2 * in + 1) * 2));
   for (int l = 0; l < s.layers; ++l) {
     n.h[l] = static_cast<bf16*>(A((size_t)Mmax * n.ldh * 2));
-    n.hT[l] = static_cast<bf16*>(A((size_t)(H + 1) * Mmax * 2));
     if (s.layernorm) {
       n.z[l] = static_cast<float*>(A((size_t)Mmax * H * 4));
       n.rstd[l] = static_cast<float*>(A((size_t)Mmax * 4));
@@ -861,14 +820,13 @@ const char* bf_net_carve(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, 
   for (int l = 0; l <= s.layers; ++l) {
     const size_t w = (l == s.layers) ? (size_t)pad8(out) : (size_t)H;
     n.dz[l] = static_cast<bf16*>(A((size_t)Mmax * w * 2));
-    n.dzT[l] = static_cast<bf16*>(A(w * Mmax * 2));
   }
   if (s.layernorm) {
     n.du = static_cast<float*>(A((size_t)Mmax * H * 4));
     n.ln_partial = static_cast<float*>(A(ln_partial_floats(Mmax, H) * 4));
     n.ln_ticket = static_cast<unsigned*>(A(256));
   }
-  if (!n.x0 || !n.x0T || !n.y || (s.layernorm && (!n.du || !n.ln_partial || !n.ln_ticket)))
+  if (!n.x0 || !n.y || (s.layernorm && (!n.du || !n.ln_partial || !n.ln_ticket)))
     return "device allocation failed";
   return nullptr;
 }
@@ -892,8 +850,8 @@ size_t bf_net_bytes(const MlpShape& s, int Mmax) {
 
 void bf_net_fill_ones(BfNet& n, cudaStream_t st) {
   const int in = n.s.in(), H = n.s.hidden, Mx = n.Mmax;
-  fill_bf16_kernel<<<ceil_div(Mx, 256), 256, 0, st>>>(n.x0T + (size_t)(2 * in) * Mx, Mx, 1.f);
-  for (int l = 0; l < n.layers; ++l) fill_bf16_kernel<<<ceil_div(Mx, 256), 256, 0, st>>>(n.hT[l] + (size_t)H * Mx, Mx, 1.f);
+  fill_col_bf16_kernel<<<ceil_div(Mx, 256), 256, 0, st>>>(n.x0 + 2 * in, Mx, bf_net_x0_ld(n), 1.f);
+  for (int l = 0; l < n.layers; ++l) fill_col_bf16_kernel<<<ceil_div(Mx, 256), 256, 0, st>>>(n.h[l] + H, Mx, n.ldh, 1.f);
 }
 
 const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner) {
@@ -917,27 +875,27 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
   for (int l = 0; l < s.layers; ++l)   // the zero columns between the hi and lo halves are read as K
     if (cudaMemset(n.h[l], 0, (size_t)Mmax * n.ldh * 2) != cudaSuccess) return "cudaMemset failed";
   if (s.layernorm && cudaMemset(n.ln_ticket, 0, 256) != cudaSuccess) return "LayerNorm workspace set-up failed";
-  if (cudaMemset(n.x0, 0, (size_t)Mmax * pad8(2 * in) * 2) != cudaSuccess) return "cudaMemset failed";
-  // the ones rows of the transposed activations (never overwritten)
+  if (cudaMemset(n.x0, 0, (size_t)Mmax * pad8(2 * in + 1) * 2) != cudaSuccess) return "cudaMemset failed";
+  // the ones columns of the bias gradients (never overwritten)
   bf_net_fill_ones(n, nullptr);
-  if (cudaDeviceSynchronize() != cudaSuccess) return "initialising the ones rows failed";
+  if (cudaDeviceSynchronize() != cudaSuccess) return "initialising the ones columns failed";
   return nullptr;
 }
 
 const char* bf_net_maps(BfNet& n, int M) {
   if (n.tm_M == M) return nullptr;
-  const int in = n.s.in(), H = n.s.hidden, out = n.s.out, Mx = n.Mmax;
+  const int in = n.s.in(), H = n.s.hidden, out = n.s.out;
   const char* e;
-  if ((e = mk(&n.tm_x0A, n.x0, 2 * in, M, pad8(2 * in)))) return e;
-  if ((e = mk(&n.tm_x0TB, n.x0T, M, 2 * in + 1, Mx))) return e;
+  const int x0ld = bf_net_x0_ld(n);
+  if ((e = mk(&n.tm_x0A, n.x0, 2 * in, M, x0ld))) return e;
+  if ((e = mk(&n.tm_x0B, n.x0, 2 * in + 1, M, x0ld))) return e;
   for (int l = 0; l < n.layers; ++l) {
     if ((e = mk(&n.tm_hA[l], n.h[l], n.ldh, M, n.ldh))) return e;
-    if ((e = mk(&n.tm_hTB[l], n.hT[l], M, H + 1, Mx))) return e;
+    if ((e = mk(&n.tm_hB[l], n.h[l], H + 1, M, n.ldh))) return e;
   }
   for (int l = 0; l <= n.layers; ++l) {
     const int width = (l == n.layers) ? out : H, ld = (l == n.layers) ? pad8(out) : H;
     if ((e = mk(&n.tm_dzA[l], n.dz[l], width, M, ld))) return e;
-    if ((e = mk(&n.tm_dzTA[l], n.dzT[l], M, width, Mx))) return e;
   }
   n.tm_M = M;
   return nullptr;
@@ -953,19 +911,19 @@ void bf_net_shadow(BfNet& n, const float* params, cudaStream_t st) {
   }
 }
 
-int bf_net_x0_ld(const BfNet& n) { return pad8(2 * n.s.in()); }
+int bf_net_x0_ld(const BfNet& n) { return pad8(2 * n.s.in() + 1); }
 
 void bf_net_pack_input(BfNet& n, const float* x0, const float* x1, int M, cudaStream_t st) {
   const int in = n.s.in();
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)M * in * 12.0);
   dim3 grid(ceil_div(in, 32), ceil_div(M, 32));
   launch_k(pack_split_kernel, grid, dim3(256), 0, st, M, x0, n.s.in0, n.s.in0, x1, n.s.in1, n.s.in1, n.x0,
-           pad8(2 * in), n.x0T, n.Mmax);
+           bf_net_x0_ld(n), (bf16*)nullptr, 0);
 }
 
 void bf_net_load_dy(BfNet& n, const float* dy, int M, cudaStream_t st) {
   const int out = n.s.out;
-  pack(M, dy, out, out, nullptr, 0, 0, n.dz[n.layers], pad8(out), n.dzT[n.layers], n.Mmax, st);
+  pack(M, dy, out, out, nullptr, 0, 0, n.dz[n.layers], pad8(out), nullptr, 0, st);
 }
 
 namespace {
@@ -984,8 +942,6 @@ tc::GemmProblem forward_problem(const BfPass& bp, int l, bool ln) {
     e.ld0 = L.out;
     e.out0 = n.y;
     e.out1 = eo.X;
-    e.out2 = eo.XT;
-    e.ld1 = eo.ldt;
     e.aux = eo.aux;
     e.energy = eo.energy;
   } else if (l == layers) {
@@ -999,16 +955,19 @@ tc::GemmProblem forward_problem(const BfPass& bp, int l, bool ln) {
   } else {
     e = epi_of(tc::kEpiFwdHidden);
     e.ld0 = n.ldh;
-    e.c0 = n.ldh / 2;
+    e.c0 = n.hlo;
     e.out0 = n.h[l];
-    e.ld1 = n.Mmax;
-    e.out1 = n.hT[l];
   }
   e.bias = params + L.ob;
   // layer 0: A = the split input (x_hi, x_lo interleaved) against [W_hi | W_lo];
   // later layers: A = [h_hi | h_lo] against [W_hi | W_hi | W_lo], the A slices
   // wrapping around: h_hi W_hi + h_lo W_hi + h_hi W_lo
-  return problem(A, L.tmW, bp.M, L.out, L.in_pad, (L.nhi == 1 ? 1 : 2) * L.kp / 64, e);
+  tc::GemmProblem p = problem(A, L.tmW, bp.M, L.out, L.in_pad, (L.nhi == 1 ? 1 : 2) * L.kp / 64, e);
+  if (l > 0) {   // h_lo sits two 64-column blocks after h_hi's last slice
+    p.a_gap = L.kp / 64;
+    p.a_skip = L.kp / 64;
+  }
+  return p;
 }
 
 }  // namespace
@@ -1046,7 +1005,7 @@ const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* 
         const BfLayer& L = n.L[l];
         const float* pr = nets[k0 + k].params;
         const int M = std::max(nets[k0 + k].M, 0);
-        grp.n[k] = LnFwdNet{M, n.Mmax, n.z[l], n.rstd[l], pr + L.og, pr + L.obeta, n.h[l], n.hT[l], n.ldh};
+        grp.n[k] = LnFwdNet{M, n.z[l], n.rstd[l], pr + L.og, pr + L.obeta, n.h[l], n.ldh, n.hlo};
         Mx = std::max(Mx, M);
         bytes += (double)M * H * 12.0;
       }
@@ -1080,13 +1039,7 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
       e.mask = n.h[l - 1];
       e.ldm = n.ldh;
       e.ld0 = H;
-      if (ln) {
-        e.out0 = n.du;
-      } else {
-        e.out0 = n.dz[l - 1];
-        e.out1 = n.dzT[l - 1];
-        e.ld1 = n.Mmax;
-      }
+      e.out0 = ln ? static_cast<void*>(n.du) : static_cast<void*>(n.dz[l - 1]);
       probs.push_back(problem(n.tm_dzA[l], L.tmWt, M, H, L.out, 0, e));
       flops += 2.0 * M * H * L.out;
     }
@@ -1103,13 +1056,11 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
         const BfLayer& P = n.L[l - 1];
         const int M = std::max(bp.M, 0);
         grp.n[k] = LnBwdNet{M,
-                            n.Mmax,
                             n.du,
                             n.z[l - 1],
                             n.rstd[l - 1],
                             bp.params + P.og,
                             n.dz[l - 1],
-                            n.dzT[l - 1],
                             bp.grads ? bp.grads + P.og : nullptr,
                             bp.grads ? bp.grads + P.obeta : nullptr,
                             n.ln_partial,
@@ -1136,8 +1087,12 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
         e.kin = L.in;
         e.out0 = grads + L.oW;
         e.out1 = grads + L.ob;
-        if (l == 0) probs.push_back(problem(n.tm_dzTA[0], n.tm_x0TB, L.out, 2 * L.in + 1, M, 0, e));
-        else probs.push_back(problem(n.tm_dzTA[l], n.tm_hTB[l - 1], L.out, L.in + 1, M, 0, e));
+        // dW = dz^T [x | 1] with K = the batch: dz [M][out] and x [M][in + 1]
+        // are read as they are stored (MN-major), the ones column giving db
+        if (l == 0) probs.push_back(problem(n.tm_dzA[0], n.tm_x0B, L.out, 2 * L.in + 1, M, 0, e));
+        else probs.push_back(problem(n.tm_dzA[l], n.tm_hB[l - 1], L.out, L.in + 1, M, 0, e));
+        probs.back().a_mn = 1;
+        probs.back().b_mn = 1;
         if (L.wsplit_cap > 1) {
           probs.back().ksplit_cap = L.wsplit_cap;
           probs.back().part = L.wpart;

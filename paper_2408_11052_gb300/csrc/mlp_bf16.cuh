@@ -1,13 +1,14 @@
 // BF16 tensor-core MLP (encoders phi, psi and the policy pi): buffers and entry points.
 //
-// Every product is a "TN" GEMM on tcgen05 (both operands K-major, BF16 in,
-// FP32 accumulate in TMEM):
-//   forward      z_l  = h_{l-1} W_l^T          A = h_{l-1} [M][K],    B = W_l  [N][K]
-//   input grad   dh   = dz_l W_l               A = dz_l    [M][N],    B = Wt_l [K][N]
-//   weight grad  dW_l = dz_l^T [h_{l-1} | 1]   A = dz_l^T  [N][M],    B = h^T  [K+1][M]
-// so the forward epilogue writes each activation twice, row-major h [M][H]
-// and transposed h^T [H+1][M], whose last row is all ones: the weight-grad
-// GEMM then returns the bias gradient (sum over the batch) as its last column.
+// Every product is a GEMM on tcgen05 (BF16 in, FP32 accumulate in TMEM),
+// each operand read as it is stored:
+//   forward      z_l  = h_{l-1} W_l^T          A = h_{l-1} [M][K],      B = W_l  [N][K]   (K-major)
+//   input grad   dh   = dz_l W_l               A = dz_l    [M][N],      B = Wt_l [K][N]   (K-major)
+//   weight grad  dW_l = dz_l^T [h_{l-1} | 1]   A = dz_l    [batch][out], B = [h | 1] [batch][in + 1]
+//                                              (both MN-major: the batch is K)
+// The column of ones after h's hi part (after x0's split input) makes the
+// weight-gradient GEMM return the bias gradient (sum over the batch) as its
+// last column; no activation or gradient is stored twice.
 //
 // The network input (observations, actions, goals: O(1..10) values with a
 // large common component across the batch) is split into a BF16 high part and
@@ -75,27 +76,29 @@ struct BfNet {
   int layers = 0;
   BfLayer L[CRL_MAX_LAYERS + 1];
   // activations
-  __nv_bfloat16* x0 = nullptr;    // [Mmax][pad8(2 in)]  split input (hi, lo interleaved)
-  __nv_bfloat16* x0T = nullptr;   // [2 in + 1][Mmax]    transposed, last row ones
-  int ldh = 0;                             // row length of h: 2 kp(H); hi in [0, H), lo in [ldh / 2, ldh / 2 + H)
-  __nv_bfloat16* h[CRL_MAX_LAYERS] = {};   // [Mmax][ldh] BF16 hi and lo parts of the activations
-  __nv_bfloat16* hT[CRL_MAX_LAYERS] = {};  // [H + 1][Mmax], last row ones
+  // The weight-gradient products read x0 and h as MN-major operands (the
+  // batch is their K), so no transposed copy exists; the bias gradient comes
+  // from a column of ones after the hi part (x0: column 2 in, h: column H).
+  __nv_bfloat16* x0 = nullptr;    // [Mmax][pad8(2 in + 1)] split input (hi, lo interleaved), then ones
+  int ldh = 0;                    // row length of h: 2 kp(H) + 128
+  int hlo = 0;                    // column of h_lo: kp(H) + 128 (columns H .. hlo - 1: the ones column
+                                  // H, zeros elsewhere; the forward skips the 128 columns at kp(H))
+  __nv_bfloat16* h[CRL_MAX_LAYERS] = {};   // [Mmax][ldh] BF16 hi part [0, H) and lo part [hlo, hlo + H)
   float* z[CRL_MAX_LAYERS] = {};           // LayerNorm: pre-norm [Mmax][H], then zhat in place
   float* rstd[CRL_MAX_LAYERS] = {};        // LayerNorm: [Mmax]
   float* y = nullptr;                      // [Mmax][out] output (FP32)
   // backward: dz[l] = gradient at the output of layer l (pre-activation of a
   // hidden layer, y for l = layers), BF16 [Mmax][ld] with ld = H (hidden) or
-  // out_pad (output), and transposed [width][Mmax]
+  // out_pad (output)
   __nv_bfloat16* dz[CRL_MAX_LAYERS + 1] = {};
-  __nv_bfloat16* dzT[CRL_MAX_LAYERS + 1] = {};
   float* du = nullptr;                     // LayerNorm backward input [Mmax][H]
   float* ln_partial = nullptr;             // LayerNorm gain / shift gradient partials [Mmax/16][2][H]
   unsigned* ln_ticket = nullptr;           // their last-block ticket (zero between launches)
   // tensor maps, built for the batch size M of the last call
   int tm_M = -1;
-  CUtensorMap tm_x0A, tm_x0TB;
-  CUtensorMap tm_hA[CRL_MAX_LAYERS], tm_hTB[CRL_MAX_LAYERS];
-  CUtensorMap tm_dzA[CRL_MAX_LAYERS + 1], tm_dzTA[CRL_MAX_LAYERS + 1];
+  CUtensorMap tm_x0A, tm_x0B;    // A of the first layer; MN-major B of its weight gradient (2 in + 1 columns)
+  CUtensorMap tm_hA[CRL_MAX_LAYERS], tm_hB[CRL_MAX_LAYERS];   // the same for h (H + 1 columns)
+  CUtensorMap tm_dzA[CRL_MAX_LAYERS + 1];   // K-major A of the input gradient, MN-major A of the weight gradient
 };
 
 // Device problem tables of the grouped GEMM, one per distinct list of problems
@@ -154,25 +157,23 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
 const char* bf_net_carve(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, void* owner, bool weight_maps);
 // Bytes bf_net_carve takes for Mmax rows (256-byte aligned pieces).
 size_t bf_net_bytes(const MlpShape& s, int Mmax);
-// Writes the ones rows of x0T and every hT on stream st.
+// Writes the ones columns of x0 and every h on stream st.
 void bf_net_fill_ones(BfNet& n, cudaStream_t st);
 // (Re)build the activation tensor maps for batch M (no-op when M is unchanged).
 const char* bf_net_maps(BfNet& n, int M);
 // Refresh W / Wt shadows from the FP32 master parameters.
 void bf_net_shadow(BfNet& n, const float* params, cudaStream_t st);
-// Row length of x0 (the split input): pad8(2 in).
+// Row length of x0 (the split input and the ones column): pad8(2 in + 1).
 int bf_net_x0_ld(const BfNet& n);
-// Pack the FP32 input concat(x0 [M][in0], x1 [M][in1]) into x0 / x0T.
+// Pack the FP32 input concat(x0 [M][in0], x1 [M][in1]) into x0.
 void bf_net_pack_input(BfNet& n, const float* x0, const float* x1, int M, cudaStream_t st);
-// Store an FP32 gradient dy [M][out] into dz[layers] / dzT[layers] (BF16, both layouts).
+// Store an FP32 gradient dy [M][out] into dz[layers] (BF16).
 void bf_net_load_dy(BfNet& n, const float* dy, int M, cudaStream_t st);
 
 // The fused energy's BF16 operand written by an encoder's output layer (see
-// kEpiFwdOutEnergy): x [M][out], x^T [out][ldt], aux [M].
+// kEpiFwdOutEnergy): x [M][out], aux [M].
 struct EnergyOut {
   __nv_bfloat16* X;
-  __nv_bfloat16* XT;
-  int ldt;
   float* aux;
   int energy;
 };
@@ -190,7 +191,7 @@ struct BfPass {
 };
 // Forward of `count` networks (one grouped launch per layer): y [M][out] FP32 in net->y.
 const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st);
-// Backward of `count` networks from their dz[layers] / dzT[layers]: one grouped
+// Backward of `count` networks from their dz[layers]: one grouped
 // input-gradient launch per hidden layer, then one launch with every weight
 // gradient and first-layer input gradient.
 const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st);

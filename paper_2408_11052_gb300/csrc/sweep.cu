@@ -94,7 +94,6 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     std::vector<RelabelTask> tasks(na);
     std::vector<int> begin(na + 1, 0);
     double bytes = 0.0;
-    size_t smem = 0;
     for (int i = 0; i < na; ++i) {
       crl_ctx* c = sw->agents[i];
       const crl_config& cf = c->cfg;
@@ -103,7 +102,6 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
       tasks[i].bd = c->bd;
       tasks[i].ra = relabel_args(c, CRL_STEP_AUTO, cf.B, c->bs, c->ba, c->bg, nullptr, true);
       begin[i + 1] = begin[i] + relabel_blocks(tasks[i].ra);
-      smem = std::max(smem, relabel_pack_smem(c->bd, tasks[i].ra));
       bytes += cf.B * ((cf.D + cf.A + 1 + cf.G) * 4.0 + (cf.D + cf.A + cf.G) * 4.0);
     }
     const char* err = nullptr;
@@ -111,15 +109,15 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     sweep_check(dt ? nullptr : err);
     const int* db = sw->tables.get(begin, st, &err);
     sweep_check(db ? nullptr : err);
-    launch_relabel_multi(dt, db, na, begin[na], bytes, true, smem, st);
+    launch_relabel_multi(dt, db, na, begin[na], bytes, true, 0, st);
   }
   // ---- critic: phi, psi and pi forward (pi's parameters do not change before the actor step)
   std::vector<BfPass> fwd, bwd;
   std::vector<EnergyOut> eo(2 * na);
   for (int i = 0; i < na; ++i) {
     crl_ctx* c = sw->agents[i];
-    eo[2 * i] = EnergyOut{c->etc.X, c->etc.XT, c->etc.ldt, c->etc.auxX, c->cfg.energy};
-    eo[2 * i + 1] = EnergyOut{c->etc.Y, c->etc.YT, c->etc.ldt, c->etc.auxY, c->cfg.energy};
+    eo[2 * i] = EnergyOut{c->etc.X, c->etc.auxX, c->cfg.energy};
+    eo[2 * i + 1] = EnergyOut{c->etc.Y, c->etc.auxY, c->cfg.energy};
   }
   for (int i = 0; i < na; ++i) {
     crl_ctx* c = sw->agents[i];
@@ -151,8 +149,7 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     sweep_check(energy_tc_maps(c->etc, B));
     ea.push_back(EnergyAgent{&c->etc, loss_spec(c->cfg), B, P.y, Q.y, static_cast<float*>(c->loss),
                              static_cast<float*>(c->row_lse), static_cast<float*>(c->col_lse), c->etc_ws,
-                             &c->ctr->t_critic, P.dz[P.layers], P.dzT[P.layers], Q.dz[Q.layers], Q.dzT[Q.layers],
-                             P.Mmax, &c->ctr->status});
+                             &c->ctr->t_critic, P.dz[P.layers], Q.dz[Q.layers], &c->ctr->status});
   }
   // (the operands were written by the encoders' output layers: no prepare stage)
   for (int stage = 1; stage < 3; ++stage) sweep_check(energy_tc_multi(sw->tables, ea, stage, st));
@@ -251,8 +248,6 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
       h.dout = nullptr;
       h.dz = PI.dz[PI.layers];
       h.ldz = PI.L[PI.layers].out_pad;
-      h.dzT = PI.dzT[PI.layers];
-      h.ldt = PI.Mmax;
       h.alpha_used = cf.alpha_autotune ? c->ctr->alpha + 3 : nullptr;
       hb.push_back(h);
     }

@@ -17,8 +17,9 @@
 //                      into the FP32 accumulator in TMEM (128 lanes x BN cols);
 //   all 4 warps     -- epilogue: warp w reads TMEM lanes 32w..32w+31 (rows)
 //                      in chunks of 32 columns and applies the problem's
-//                      epilogue (vectorised row stores, coalesced transposed
-//                      stores).
+//                      epilogue (vectorised row stores).
+// Either operand may be stored MN-major instead (the weight gradients read the
+// activations and output gradients as they are stored: the batch is K).
 // Out-of-range rows and columns of the operands are zero-filled by TMA; the
 // epilogue clips its stores to M x N.
 #pragma once
@@ -37,16 +38,16 @@ constexpr int kBK = 64;
 // What the FP32 accumulator tile of a problem becomes.
 enum EpiKind : int {
   kEpiFwdHidden = 0,  // h = ReLU(acc + b) as BF16 hi / lo parts: h_hi [M][ld0] columns [0, N), h_lo = bf16(h -
-                      // h_hi) at columns [c0, c0 + N) of the same rows, and h_hi^T [N][ld1]
+                      // h_hi) at columns [c0, c0 + N) of the same rows
   kEpiFwdPreLN = 1,   // z = acc + b: FP32 [M][ld0] (LayerNorm follows)
   kEpiFwdOut = 2,     // y = acc + b: FP32 [M][ld0]
-  kEpiBwdDX = 3,      // dz = acc * [mask > 0]: BF16 dz [M][ld0] and dz^T [N][ld1]
+  kEpiBwdDX = 3,      // dz = acc * [mask > 0]: BF16 dz [M][ld0]
   kEpiBwdDXLN = 4,    // du = acc * [mask > 0]: FP32 [M][ld0]
   kEpiBwdDW = 5,      // dW [M][kin] (columns < kin), db [M] (column kin: the ones row)
   kEpiBwdDW0 = 6,     // split first layer: dW[m][c] = acc[2c] + acc[2c+1], db[m] = acc[2 kin]
   kEpiDX0 = 7,        // dx [M][nc] = acc columns [c0, c0 + nc)
   kEpiFwdOutEnergy = 8,  // output layer feeding the fused energy: y = acc + b FP32 [M][ld0], the BF16
-                         // energy operand x = y * s [M][N] (out1), optionally x^T [N][ld1] (out2), aux [M];
+                         // energy operand x = y * s [M][N] (out1), aux [M];
                          // s = 1 / |y| and aux = s for the cosine energy, else s = 1 and aux = |bf16(y)|^2.
                          // The tile must span the whole row (the launch picks BN >= N).
 };
@@ -64,6 +65,9 @@ struct EpiDesc {
 struct GemmProblem {   // 128-byte aligned by its tensor maps
   CUtensorMap a, b;
   int M, N, K, nkA;   // nkA > 0: split-weight product (see tc_gemm_kernel)
+  int a_mn, b_mn;     // operand stored MN-major ([K][M] / [K][N], the M / N index contiguous): its
+                      // tensor map's inner dimension is M / N, boxes {64 MN, 64 K}
+  int a_gap, a_skip;  // a_gap > 0 (K-major A): A's K slices from a_gap on sit a_skip 64-column blocks further
   int tiles_n, tile_begin;
   int ksplit;         // > 1: K is split over ksplit CTAs per output tile (one-tile kernel only)
   int ksplit_cap;     // the most splits the problem's buffers hold (the launch picks ksplit <= it)
@@ -145,6 +149,71 @@ __device__ __forceinline__ void prefetch_b_tile(const CUtensorMap* tmB, int K, i
       if (n0 + 64 * r < N) tma_prefetch_2d(tmB, kb * kBK, n0 + 64 * r);
 }
 
+// L2 prefetch of a tile's B operand in either storage order.
+template <int BN>
+__device__ __forceinline__ void prefetch_b(const GemmProblem* P, int n0) {
+  if (!P->b_mn) {
+    prefetch_b_tile<BN>(&P->b, P->K, P->N, n0);
+    return;
+  }
+  const int nk = (P->K + kBK - 1) / kBK;
+  for (int kb = 0; kb < nk && kb < 64; ++kb)
+#pragma unroll
+    for (int r = 0; r < BN / 64; ++r)
+      if (n0 + 64 * r < P->N) tma_prefetch_2d(&P->b, n0 + 64 * r, kb * kBK);
+}
+
+// TMA loads of K slice kb: 128 rows of A from row m0 and NB 64-row boxes of B
+// from row n0, each box landing 8 KiB after the previous.  K-major operands
+// come as {64 K, 64 rows} boxes (the slice's 128-byte rows), MN-major ones as
+// {64 MN, 64 K} boxes (64 K rows of 128 bytes per 64 M or N): in both cases a
+// box is an 8 KiB 128-byte-swizzled block.
+// The operand description of a problem, read into registers once per tile
+// (the loads' asm statements would otherwise force a reread per slice).
+struct SliceSrc {
+  const CUtensorMap* a;
+  const CUtensorMap* b;
+  int a_mn, b_mn, nkA, a_gap, a_skip;
+};
+__device__ __forceinline__ SliceSrc slice_src(const GemmProblem* P) {
+  return SliceSrc{&P->a, &P->b, P->a_mn, P->b_mn, P->nkA, P->a_gap, P->a_skip};
+}
+template <int NB>
+__device__ __forceinline__ void load_slice(const SliceSrc& P, uint8_t* a_dst, uint8_t* b_dst, uint64_t* bar, int kb,
+                                           int m0, int n0) {
+  const CUtensorMap* tmA = P.a;
+  const CUtensorMap* tmB = P.b;
+  if (P.a_mn) {
+#pragma unroll
+    for (int r = 0; r < kBM / 64; ++r) tma_load_2d(a_dst + r * 8192, tmA, bar, m0 + 64 * r, kb * kBK);
+  } else {
+    const int ka = P.nkA > 0 ? kb % P.nkA : kb;
+    const int kx = (P.a_gap > 0 && ka >= P.a_gap) ? ka + P.a_skip : ka;
+#pragma unroll
+    for (int r = 0; r < kBM / 64; ++r) tma_load_2d(a_dst + r * 8192, tmA, bar, kx * kBK, m0 + 64 * r);
+  }
+  if (P.b_mn) {
+#pragma unroll
+    for (int r = 0; r < NB; ++r) tma_load_2d(b_dst + r * 8192, tmB, bar, n0 + 64 * r, kb * kBK);
+  } else {
+#pragma unroll
+    for (int r = 0; r < NB; ++r) tma_load_2d(b_dst + r * 8192, tmB, bar, kb * kBK, n0 + 64 * r);
+  }
+}
+
+// Shared-memory descriptor of a slice's operand tile (K step 0) and the
+// increment of its address field per K step of 16: K-major +32 bytes along the
+// 128-byte rows, MN-major 16 K rows further (2 KiB; 64-element MN blocks 8 KiB
+// apart).  The MMA issuer adds k * step: no per-MMA descriptor arithmetic.
+__device__ __forceinline__ uint64_t slice_desc(const uint8_t* tile, bool mn) {
+  return mn ? sdesc_mnmajor_sw128(tile, 8192) : sdesc_kmajor_sw128(tile);
+}
+__device__ __forceinline__ uint32_t slice_step(bool mn) { return mn ? 2048u >> 4 : 32u >> 4; }
+// The instruction descriptor's operand-order bits (A: bit 15, B: bit 16; 1 = MN-major).
+__device__ __forceinline__ uint32_t idesc_major(uint32_t idesc, const GemmProblem* P) {
+  return idesc | ((P->a_mn ? 1u : 0u) << 15) | ((P->b_mn ? 1u : 0u) << 16);
+}
+
 // Epilogue of one 32-column chunk (columns col0 .. col0 + 31) of row `row`.
 // The full-chunk paths use 16-byte accesses; they need 16-byte aligned rows:
 // leading dimensions a multiple of 8 BF16 / 4 FP32 elements (hidden widths
@@ -158,7 +227,6 @@ __device__ __forceinline__ void epilogue_chunk(const EpiDesc& e, int row, int co
   switch (e.kind) {
     case kEpiFwdHidden: {
       bf16* h = static_cast<bf16*>(e.out0);
-      bf16* hT = static_cast<bf16*>(e.out1);
       if (full) {
         float b[32];
         load_bias32(e.bias + col0, b);
@@ -166,11 +234,7 @@ __device__ __forceinline__ void epilogue_chunk(const EpiDesc& e, int row, int co
         for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + b[i], 0.f);
         store_bf16x32(h + (size_t)row * e.ld0 + col0, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const bf16 o = __float2bfloat16_rn(v[i]);
-          hT[(size_t)(col0 + i) * e.ld1 + row] = o;
-          v[i] -= __bfloat162float(o);
-        }
+        for (int i = 0; i < 32; ++i) v[i] -= __bfloat162float(__float2bfloat16_rn(v[i]));
         store_bf16x32(h + (size_t)row * e.ld0 + e.c0 + col0, v);
       } else {
 #pragma unroll
@@ -180,7 +244,6 @@ __device__ __forceinline__ void epilogue_chunk(const EpiDesc& e, int row, int co
           const bf16 o = __float2bfloat16_rn(x);
           h[(size_t)row * e.ld0 + col0 + i] = o;
           h[(size_t)row * e.ld0 + e.c0 + col0 + i] = __float2bfloat16_rn(x - __bfloat162float(o));
-          hT[(size_t)(col0 + i) * e.ld1 + row] = o;
         }
       }
       break;
@@ -209,27 +272,16 @@ __device__ __forceinline__ void epilogue_chunk(const EpiDesc& e, int row, int co
         load_mask32(mrow + col0, on);
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = on[i] ? v[i] : 0.f;
-        if (e.kind == kEpiBwdDXLN) {
-          store_f32x32(static_cast<float*>(e.out0) + (size_t)row * e.ld0 + col0, v);
-        } else {
-          store_bf16x32(static_cast<bf16*>(e.out0) + (size_t)row * e.ld0 + col0, v);
-          bf16* dzT = static_cast<bf16*>(e.out1);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) dzT[(size_t)(col0 + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
-        }
+        if (e.kind == kEpiBwdDXLN) store_f32x32(static_cast<float*>(e.out0) + (size_t)row * e.ld0 + col0, v);
+        else store_bf16x32(static_cast<bf16*>(e.out0) + (size_t)row * e.ld0 + col0, v);
       } else {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int c = col0 + i;
           if (c >= N) break;
           const float x = __bfloat162float(mrow[c]) > 0.f ? v[i] : 0.f;
-          if (e.kind == kEpiBwdDXLN) {
-            static_cast<float*>(e.out0)[(size_t)row * e.ld0 + c] = x;
-          } else {
-            const bf16 o = __float2bfloat16_rn(x);
-            static_cast<bf16*>(e.out0)[(size_t)row * e.ld0 + c] = o;
-            static_cast<bf16*>(e.out1)[(size_t)c * e.ld1 + row] = o;
-          }
+          if (e.kind == kEpiBwdDXLN) static_cast<float*>(e.out0)[(size_t)row * e.ld0 + c] = x;
+          else static_cast<bf16*>(e.out0)[(size_t)row * e.ld0 + c] = __float2bfloat16_rn(x);
         }
       }
       break;
@@ -273,7 +325,7 @@ __device__ __forceinline__ void epilogue_chunk(const EpiDesc& e, int row, int co
 
 // The output layer feeding the fused energy (kEpiFwdOutEnergy): two passes over
 // this thread's row in TMEM (the tile holds all N columns): FP32 output and the
-// squared norm, then the scaled BF16 operand, row-major and transposed.
+// squared norm, then the scaled BF16 operand.
 __device__ __forceinline__ void epilogue_energy(const EpiDesc& e, int row, uint32_t lane_base, int N, int M) {
   using bf16 = __nv_bfloat16;
   const bool live = row < M;
@@ -297,7 +349,6 @@ __device__ __forceinline__ void epilogue_energy(const EpiDesc& e, int row, uint3
   const float scale = cosine ? rsqrtf(q) : 1.f;
   if (live) e.aux[row] = cosine ? scale : q;
   bf16* X = static_cast<bf16*>(e.out1);
-  bf16* XT = static_cast<bf16*>(e.out2);
 #pragma unroll 1
   for (int c = 0; c < N; c += 32) {
     float v[32];
@@ -308,9 +359,6 @@ __device__ __forceinline__ void epilogue_energy(const EpiDesc& e, int row, uint3
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = (v[i] + b[i]) * scale;
     store_bf16x32(X + (size_t)row * N + c, v);
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (XT) XT[(size_t)(c + i) * e.ld1 + row] = __float2bfloat16_rn(v[i]);
   }
 }
 
@@ -356,7 +404,7 @@ __global__ void __launch_bounds__(128, 1)
     tmap_acquire(tmB);
     prefetch_tmap(tmA);
     prefetch_tmap(tmB);
-    prefetch_b_tile<BN>(tmB, K, N, n0);
+    prefetch_b<BN>(P, n0);
     for (int s = 0; s < S::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
@@ -379,6 +427,7 @@ __global__ void __launch_bounds__(128, 1)
 
   if (warp == 0 && lane == 0) {
     // TMA producer
+    const SliceSrc src = slice_src(P);
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % S::kStages;
@@ -390,20 +439,15 @@ __global__ void __launch_bounds__(128, 1)
       mbar_arrive_expect_tx(&full[s], S::kStageBytes);
       // operands arrive as 64-row boxes (8 KiB each); stacked along rows they
       // form the same 128-byte-swizzled K-major tile as one tall box
-      const int kg = kb0 + kb;
-      const int ka = nkA > 0 ? kg % nkA : kg;
-#pragma unroll
-      for (int r = 0; r < kBM / 64; ++r)
-        tma_load_2d(sA + s * S::kABytes + r * 8192, tmA, &full[s], ka * kBK, m0 + 64 * r);
-#pragma unroll
-      for (int r = 0; r < BN / 64; ++r)
-        tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kg * kBK, n0 + 64 * r);
+      load_slice<BN / 64>(src, sA + s * S::kABytes, sB + s * S::kBBytes, &full[s], kb0 + kb, m0, n0);
     }
     // nothing may land in this CTA's shared memory after it exits
     drain_ring(full, S::kStages, issued);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
+    const uint32_t idesc = idesc_major(idesc_bf16_f32(kBM, BN), P);
+    const bool amn = P->a_mn != 0, bmn = P->b_mn != 0;
+    const uint32_t sa = slice_step(amn), sb = slice_step(bmn);
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % S::kStages;
       if (!mbar_wait(&full[s], (kb / S::kStages) & 1, lim)) {
@@ -411,13 +455,10 @@ __global__ void __launch_bounds__(128, 1)
         break;
       }
       fence_after_sync();
-      const uint64_t da = sdesc_kmajor_sw128(sA + s * S::kABytes);
-      const uint64_t db = sdesc_kmajor_sw128(sB + s * S::kBBytes);
+      const uint64_t da = slice_desc(sA + s * S::kABytes, amn), db = slice_desc(sB + s * S::kBBytes, bmn);
 #pragma unroll
-      for (int k = 0; k < kBK / 16; ++k) {
-        // +32 bytes along K per 16-element step: +2 in the (addr >> 4) field
-        mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-      }
+      for (int k = 0; k < kBK / 16; ++k)
+        mma_bf16(tmem, da + sa * k, db + sb * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
       mma_commit(&empty[s]);
     }
     // always: `done` completes once every MMA issued here has (after a timeout
@@ -539,7 +580,7 @@ __global__ void __launch_bounds__(192, 1)
     if ((int)blockIdx.x < total) {   // the first tile's B operand
       const GemmProblem* P = find_problem(probs, nprob, blockIdx.x);
       tmap_acquire(&P->b);
-      prefetch_b_tile<BN>(&P->b, P->K, P->N, (((int)blockIdx.x - P->tile_begin) % P->tiles_n) * BN);
+      prefetch_b<BN>(P, (((int)blockIdx.x - P->tile_begin) % P->tiles_n) * BN);
     }
     for (int s = 0; s < S::kStages; ++s) {
       mbar_init(&full[s], 1);
@@ -573,11 +614,10 @@ __global__ void __launch_bounds__(192, 1)
         const GemmProblem* P = find_problem(probs, nprob, t);
         const int lt = t - P->tile_begin;
         const int m0 = (lt / P->tiles_n) * kBM, n0 = (lt % P->tiles_n) * BN;
-        const int nk = (P->K + kBK - 1) / kBK, nkA = P->nkA;
-        const CUtensorMap* tmA = &P->a;
-        const CUtensorMap* tmB = &P->b;
-        tmap_acquire(tmA);
-        tmap_acquire(tmB);
+        const int nk = (P->K + kBK - 1) / kBK;
+        tmap_acquire(&P->a);
+        tmap_acquire(&P->b);
+        const SliceSrc src = slice_src(P);
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % S::kStages;
           if (it >= S::kStages && !mbar_wait(&empty[s], ((it / S::kStages) & 1) ^ 1, lim)) {
@@ -586,13 +626,7 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           mbar_arrive_expect_tx(&full[s], S::kStageBytes);
-          const int ka = nkA > 0 ? kb % nkA : kb;
-#pragma unroll
-          for (int r = 0; r < kBM / 64; ++r)
-            tma_load_2d(sA + s * S::kABytes + r * 8192, tmA, &full[s], ka * kBK, m0 + 64 * r);
-#pragma unroll
-          for (int r = 0; r < BN / 64; ++r)
-            tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kb * kBK, n0 + 64 * r);
+          load_slice<BN / 64>(src, sA + s * S::kABytes, sB + s * S::kBBytes, &full[s], kb, m0, n0);
         }
       }
       // `it` slices were issued (a timed-out one was not): let them all land
@@ -601,12 +635,14 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
-      constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
       int it = 0, i = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
         const GemmProblem* P = find_problem(probs, nprob, t);
         const int nk = (P->K + kBK - 1) / kBK;
+        const uint32_t idesc = idesc_major(idesc_bf16_f32(kBM, BN), P);
+        const bool amn = P->a_mn != 0, bmn = P->b_mn != 0;
+        const uint32_t sa = slice_step(amn), sb = slice_step(bmn);
         const int buf = i & 1, use = i >> 1;
         // the epilogue of tile i - 2 must have read this buffer out
         if (use > 0 && !mbar_wait(&acce[buf], (use - 1) & 1, lim)) {
@@ -623,10 +659,9 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           fence_after_sync();
-          const uint64_t da = sdesc_kmajor_sw128(sA + s * S::kABytes);
-          const uint64_t db = sdesc_kmajor_sw128(sB + s * S::kBBytes);
+          const uint64_t da = slice_desc(sA + s * S::kABytes, amn), db = slice_desc(sB + s * S::kBBytes, bmn);
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k) mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < kBK / 16; ++k) mma_bf16(d, da + sa * k, db + sb * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
           mma_commit(&empty[s]);
         }
         if (ok) mma_commit(&accf[buf]);
@@ -735,7 +770,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(224, 1)
     if (cl < total) {   // the first tile's B rows of this CTA
       const GemmProblem* P = find_problem(probs, nprob, cl);
       tmap_acquire(&P->b);
-      prefetch_b_tile<BN / 2>(&P->b, P->K, P->N, ((cl - P->tile_begin) % P->tiles_n) * BN + (BN / 2) * rank);
+      prefetch_b<BN / 2>(P, ((cl - P->tile_begin) % P->tiles_n) * BN + (BN / 2) * rank);
     }
     for (int s = 0; s < S::kStages; ++s) {
       mbar_init(&full[s], 1);
@@ -771,11 +806,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(224, 1)
         const int lt = t - P->tile_begin;
         const int m0 = (lt / P->tiles_n) * kPairM + kBM * (int)rank;
         const int n0 = (lt % P->tiles_n) * BN + (BN / 2) * (int)rank;
-        const int nk = (P->K + kBK - 1) / kBK, nkA = P->nkA;
-        const CUtensorMap* tmA = &P->a;
-        const CUtensorMap* tmB = &P->b;
-        tmap_acquire(tmA);
-        tmap_acquire(tmB);
+        const int nk = (P->K + kBK - 1) / kBK;
+        tmap_acquire(&P->a);
+        tmap_acquire(&P->b);
+        const SliceSrc src = slice_src(P);
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % S::kStages;
           if (it >= S::kStages) {
@@ -788,13 +822,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(224, 1)
             }
           }
           mbar_arrive_expect_tx(&full[s], S::kStageBytes);
-          const int ka = nkA > 0 ? kb % nkA : kb;
-#pragma unroll
-          for (int r = 0; r < kBM / 64; ++r)
-            tma_load_2d(sA + s * S::kABytes + r * 8192, tmA, &full[s], ka * kBK, m0 + 64 * r);
-#pragma unroll
-          for (int r = 0; r < BN / 128; ++r)
-            tma_load_2d(sB + s * S::kBBytes + r * 8192, tmB, &full[s], kb * kBK, n0 + 64 * r);
+          load_slice<BN / 128>(src, sA + s * S::kABytes, sB + s * S::kBBytes, &full[s], kb, m0, n0);
         }
       }
       drain_ring(full, S::kStages, it);
@@ -802,12 +830,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(224, 1)
   } else if (warp == 1) {
     if (lane == 0 && even) {
       // MMA issuer of the pair
-      constexpr uint32_t idesc = idesc_bf16_f32(kPairM, BN);
       int it = 0, i = 0;
       bool ok = true;
       for (int t = cl; t < total && ok; t += ncl, ++i) {
         const GemmProblem* P = find_problem(probs, nprob, t);
         const int nk = (P->K + kBK - 1) / kBK;
+        const uint32_t idesc = idesc_major(idesc_bf16_f32(kPairM, BN), P);
+        const bool amn = P->a_mn != 0, bmn = P->b_mn != 0;
+        const uint32_t sa = slice_step(amn), sb = slice_step(bmn);
         const int buf = i & 1, use = i >> 1;
         // all eight epilogue warps must have read out this buffer (tile i - 2)
         if (use > 0 && !mbar_wait_cluster(&acce[buf], (use - 1) & 1, lim)) {
@@ -825,11 +855,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(224, 1)
             break;
           }
           fence_after_sync();
-          const uint64_t da = sdesc_kmajor_sw128(sA + s * S::kABytes);
-          const uint64_t db = sdesc_kmajor_sw128(sB + s * S::kBBytes);
+          const uint64_t da = slice_desc(sA + s * S::kABytes, amn), db = slice_desc(sB + s * S::kBBytes, bmn);
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k)
-            mma_bf16_pair(d, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+            mma_bf16_pair(d, da + sa * k, db + sb * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
           mma_commit_pair(&empty[s]);
         }
         if (ok) mma_commit_pair(&accf[buf]);
