@@ -146,14 +146,12 @@ inline int ln_vec(int H) { return (H + 127) / 128 <= kLnRegVec ? (H + 127) / 128
 // The backward's register path stages the rows' du zhat and du ([2][8][H] FP32)
 // for the column sums.
 inline size_t ln_bwd_smem_bytes(int H) { return ln_vec(H) > 0 ? (size_t)2 * kLnRows * H * 4 : 0; }
-// Deterministic two-level reduction of the LayerNorm parameter gradients: the
-// blocks' column sums go in groups of ln_group(nblk) (at most 63 groups: one
-// ticket word each, plus one for the final level).
-__host__ __device__ inline int ln_group(int nblk) { return nblk <= 63 * 16 ? 16 : (nblk + 62) / 63; }
-inline size_t ln_partial_floats(int Mmax, int H) {
+// LayerNorm parameter gradients: every backward block writes its rows' column
+// sums of du zhat and du ([nblk][2][H] per layer); one launch after the
+// input-gradient chain adds them in block order (deterministic).
+inline size_t ln_partial_floats(int Mmax, int H, int layers) {
   const int nblk = (Mmax + kLnRows - 1) / kLnRows;
-  const int ng = (nblk + ln_group(nblk) - 1) / ln_group(nblk);
-  return (size_t)(nblk + ng) * 2 * H;
+  return (size_t)layers * nblk * 2 * H;
 }
 
 struct LnFwdNet {
@@ -271,10 +269,7 @@ struct LnBwdNet {
   const float* rstd;
   const float* g;
   bf16* dz;
-  float* dg;          // null: no LayerNorm parameter gradients
-  float* db;
-  float* partial;     // [nblk][2][H] per-block column sums (dg, db), then [ngroups][2][H] group sums
-  unsigned* ticket;   // [64], zero between launches: one per group, the last for the final level
+  float* partial;     // null: no LayerNorm parameter gradients; else [nblk][2][H] per-block column sums
 };
 struct LnBwdGroup {
   LnBwdNet n[kMaxGroupNets];
@@ -289,23 +284,19 @@ __device__ __forceinline__ uint2 ln_bwd_pack(float4 d, float4 z, float4 gg, floa
 }
 
 // LayerNorm backward: du (ReLU-masked, FP32) -> dz = rstd (g du - mean(g du) -
-// zhat mean(g du zhat)), written BF16 [M][H]; with dg / db the
-// gain and shift gradients dg = sum_m du zhat, db = sum_m du: every block
-// writes its 8 rows' column sums; the last block of each group of blocks
-// (ticket) adds its group's sums in block order, and the last group to finish
-// adds the group sums in group order.  NV as in the forward.
+// zhat mean(g du zhat)), written BF16 [M][H]; with `partial` every block also
+// writes its 8 rows' column sums of du zhat and du (for dg, db; added by
+// ln_param_reduce_kernel).  NV as in the forward.
 template <int NV>
 __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constant__ LnBwdGroup grp) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char ln_smem[];
   // register path: [2][8][H] FP32 (du zhat, du) of the block's rows
   float* colbuf = reinterpret_cast<float*>(ln_smem);
-  __shared__ int s_last;
   const LnBwdNet& a = grp.n[blockIdx.y];
   const int M = a.M;
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   const int row0 = blockIdx.x * kLnRows;
-  const int nblk = (M + kLnRows - 1) / kLnRows;
   if (row0 >= M) return;
   const int nv = H / 4;
   const float4* g4 = reinterpret_cast<const float4*>(a.g);
@@ -339,7 +330,7 @@ __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constan
         const int q = lane + 32 * j;
         if (q >= nv) continue;
         out[q] = ln_bwd_pack(d[j], z[j], g4[q], s1, s2, rs);
-        if (a.dg != nullptr) {
+        if (a.partial != nullptr) {
           cz[q] = make_float4(d[j].x * z[j].x, d[j].y * z[j].y, d[j].z * z[j].z, d[j].w * z[j].w);
           cd[q] = d[j];
         }
@@ -359,7 +350,7 @@ __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constan
       }
     }
   }
-  if (a.dg == nullptr) return;
+  if (a.partial == nullptr) return;
   __syncthreads();
   // column sums of this block's rows (rows in order)
   const int rmax = min(kLnRows, M - row0);
@@ -385,45 +376,33 @@ __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constan
     a.partial[((size_t)blockIdx.x * 2 + 0) * H + c] = sg;
     a.partial[((size_t)blockIdx.x * 2 + 1) * H + c] = sb;
   }
-  const int G = ln_group(nblk), ng = (nblk + G - 1) / G, grp_id = blockIdx.x / G;
-  const int k0 = grp_id * G, k1 = min(nblk, k0 + G);
-  float* gpart = a.partial + (size_t)nblk * 2 * H;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(a.ticket + grp_id, 1u) == (unsigned)(k1 - k0) - 1u) ? 1 : 0;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int c = threadIdx.x; c < H; c += blockDim.x) {
-    float sg = 0.f, sb = 0.f;
-#pragma unroll 16
-    for (int k = k0; k < k1; ++k) {
-      sg += __ldcg(a.partial + ((size_t)k * 2 + 0) * H + c);
-      sb += __ldcg(a.partial + ((size_t)k * 2 + 1) * H + c);
-    }
-    gpart[((size_t)grp_id * 2 + 0) * H + c] = sg;
-    gpart[((size_t)grp_id * 2 + 1) * H + c] = sb;
+}
+
+// dg = sum over the blocks of their du zhat column sums, db likewise, in block
+// order: one item per (network, LayerNorm layer) with gradients.
+struct LnReduceItem {
+  const float* partial;   // [nblk][2][H]
+  float* dg;
+  float* db;
+  int nblk;
+};
+constexpr int kMaxLnReduce = 64;
+struct LnReduceGroup {
+  LnReduceItem it[kMaxLnReduce];
+};
+__global__ void __launch_bounds__(256) ln_param_reduce_kernel(int H, const __grid_constant__ LnReduceGroup grp) {
+  pdl_enter();
+  const LnReduceItem& t = grp.it[blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= H) return;
+  float sg = 0.f, sb = 0.f;
+#pragma unroll 8
+  for (int k = 0; k < t.nblk; ++k) {
+    sg += t.partial[((size_t)k * 2 + 0) * H + c];
+    sb += t.partial[((size_t)k * 2 + 1) * H + c];
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    a.ticket[grp_id] = 0u;
-    s_last = (atomicAdd(a.ticket + 63, 1u) == (unsigned)ng - 1u) ? 1 : 0;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int c = threadIdx.x; c < H; c += blockDim.x) {
-    float sg = 0.f, sb = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < ng; ++k) {
-      sg += __ldcg(gpart + ((size_t)k * 2 + 0) * H + c);
-      sb += __ldcg(gpart + ((size_t)k * 2 + 1) * H + c);
-    }
-    a.dg[c] = sg;
-    a.db[c] = sb;
-  }
-  if (threadIdx.x == 0) a.ticket[63] = 0u;
+  t.dg[c] = sg;
+  t.db[c] = sb;
 }
 
 // LayerNorm launches with the register width chosen from H.
@@ -823,10 +802,9 @@ const char* bf_net_carve(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, 
   }
   if (s.layernorm) {
     n.du = static_cast<float*>(A((size_t)Mmax * H * 4));
-    n.ln_partial = static_cast<float*>(A(ln_partial_floats(Mmax, H) * 4));
-    n.ln_ticket = static_cast<unsigned*>(A(256));
+    n.ln_partial = static_cast<float*>(A(ln_partial_floats(Mmax, H, s.layers) * 4));
   }
-  if (!n.x0 || !n.y || (s.layernorm && (!n.du || !n.ln_partial || !n.ln_ticket)))
+  if (!n.x0 || !n.y || (s.layernorm && (!n.du || !n.ln_partial)))
     return "device allocation failed";
   return nullptr;
 }
@@ -874,7 +852,6 @@ const char* bf_net_init(BfNet& n, const MlpShape& s, int Mmax, DevAlloc alloc, v
   }
   for (int l = 0; l < s.layers; ++l)   // the zero columns between the hi and lo halves are read as K
     if (cudaMemset(n.h[l], 0, (size_t)Mmax * n.ldh * 2) != cudaSuccess) return "cudaMemset failed";
-  if (s.layernorm && cudaMemset(n.ln_ticket, 0, 256) != cudaSuccess) return "LayerNorm workspace set-up failed";
   if (cudaMemset(n.x0, 0, (size_t)Mmax * pad8(2 * in + 1) * 2) != cudaSuccess) return "cudaMemset failed";
   // the ones columns of the bias gradients (never overwritten)
   bf_net_fill_ones(n, nullptr);
@@ -1025,6 +1002,7 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
   for (int k = 1; k < count; ++k)
     if (nets[k].net->layers != layers || nets[k].net->s.hidden != H || (nets[k].net->s.layernorm != 0) != ln)
       return "the networks of a grouped pass differ in depth, hidden width or LayerNorm";
+  std::vector<LnReduceItem> ln_items;
   std::vector<tc::GemmProblem> probs;
   // input-gradient chain: dz[l] -> dz[l - 1]
   for (int l = layers; l >= 1; --l) {
@@ -1055,16 +1033,11 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
         BfNet& n = *bp.net;
         const BfLayer& P = n.L[l - 1];
         const int M = std::max(bp.M, 0);
-        grp.n[k] = LnBwdNet{M,
-                            n.du,
-                            n.z[l - 1],
-                            n.rstd[l - 1],
-                            bp.params + P.og,
-                            n.dz[l - 1],
-                            bp.grads ? bp.grads + P.og : nullptr,
-                            bp.grads ? bp.grads + P.obeta : nullptr,
-                            n.ln_partial,
-                            n.ln_ticket};
+        const int nblk = ceil_div(n.Mmax, kLnRows);
+        float* part = bp.grads ? n.ln_partial + (size_t)(l - 1) * nblk * 2 * H : nullptr;
+        grp.n[k] = LnBwdNet{M, n.du, n.z[l - 1], n.rstd[l - 1], bp.params + P.og, n.dz[l - 1], part};
+        if (part && M > 0) ln_items.push_back(LnReduceItem{part, bp.grads + P.og, bp.grads + P.obeta,
+                                                           ceil_div(M, kLnRows)});
         Mx = std::max(Mx, M);
         bytes += (double)M * H * (bp.grads ? 24.0 : 16.0);
       }
@@ -1072,6 +1045,19 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
       TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
       launch_ln_bwd(H, dim3(ceil_div(Mx, kLnRows), kc), st, grp);
     }
+  }
+  // the LayerNorm gain / shift gradients of every layer and network: block sums in order
+  for (size_t i0 = 0; i0 < ln_items.size(); i0 += kMaxLnReduce) {
+    const int ni = (int)std::min<size_t>(kMaxLnReduce, ln_items.size() - i0);
+    LnReduceGroup grp;
+    memset(&grp, 0, sizeof(grp));
+    double bytes = 0.0;
+    for (int i = 0; i < ni; ++i) {
+      grp.it[i] = ln_items[i0 + i];
+      bytes += (double)ln_items[i0 + i].nblk * 2 * H * 4;
+    }
+    TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
+    launch_k(ln_param_reduce_kernel, dim3(ceil_div(H, 256), ni), dim3(256), 0, st, H, grp);
   }
   // every weight gradient, and the first-layer input gradients, in one launch
   probs.clear();

@@ -92,8 +92,7 @@ struct BfNet {
   // out_pad (output)
   __nv_bfloat16* dz[CRL_MAX_LAYERS + 1] = {};
   float* du = nullptr;                     // LayerNorm backward input [Mmax][H]
-  float* ln_partial = nullptr;             // LayerNorm gain / shift gradient partials [Mmax/16][2][H]
-  unsigned* ln_ticket = nullptr;           // their last-block ticket (zero between launches)
+  float* ln_partial = nullptr;             // LayerNorm gain / shift gradient block sums [layers][Mmax/8][2][H]
   // tensor maps, built for the batch size M of the last call
   int tm_M = -1;
   CUtensorMap tm_x0A, tm_x0B;    // A of the first layer; MN-major B of its weight gradient (2 in + 1 columns)
