@@ -378,8 +378,8 @@ __global__ void __launch_bounds__(256) ln_bwd_kernel(int H, const __grid_constan
   }
 }
 
-// dg = sum over the blocks of their du zhat column sums, db likewise, in block
-// order: one item per (network, LayerNorm layer) with gradients.
+// dg = sum over the blocks of their du zhat column sums, db likewise, in a
+// fixed order: one item per (network, LayerNorm layer) with gradients.
 struct LnReduceItem {
   const float* partial;   // [nblk][2][H]
   float* dg;
@@ -390,19 +390,36 @@ constexpr int kMaxLnReduce = 64;
 struct LnReduceGroup {
   LnReduceItem it[kMaxLnReduce];
 };
+// A block takes 32 columns; its 8 warps add consecutive eighths of the block
+// sums, then warp 0 adds the 8 results in order.
 __global__ void __launch_bounds__(256) ln_param_reduce_kernel(int H, const __grid_constant__ LnReduceGroup grp) {
   pdl_enter();
+  __shared__ float red[2][8][32];
   const LnReduceItem& t = grp.it[blockIdx.y];
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= H) return;
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int c = blockIdx.x * 32 + lane;
+  const int per = (t.nblk + 7) / 8, k0 = w * per, k1 = min(t.nblk, k0 + per);
   float sg = 0.f, sb = 0.f;
-#pragma unroll 8
-  for (int k = 0; k < t.nblk; ++k) {
-    sg += t.partial[((size_t)k * 2 + 0) * H + c];
-    sb += t.partial[((size_t)k * 2 + 1) * H + c];
+  if (c < H) {
+#pragma unroll 4
+    for (int k = k0; k < k1; ++k) {
+      sg += t.partial[((size_t)k * 2 + 0) * H + c];
+      sb += t.partial[((size_t)k * 2 + 1) * H + c];
+    }
   }
-  t.dg[c] = sg;
-  t.db[c] = sb;
+  red[0][w][lane] = sg;
+  red[1][w][lane] = sb;
+  __syncthreads();
+  if (w == 0 && c < H) {
+    float g = 0.f, b = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      g += red[0][j][lane];
+      b += red[1][j][lane];
+    }
+    t.dg[c] = g;
+    t.db[c] = b;
+  }
 }
 
 // LayerNorm launches with the register width chosen from H.
@@ -1057,7 +1074,7 @@ const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned*
       bytes += (double)ln_items[i0 + i].nblk * 2 * H * 4;
     }
     TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
-    launch_k(ln_param_reduce_kernel, dim3(ceil_div(H, 256), ni), dim3(256), 0, st, H, grp);
+    launch_k(ln_param_reduce_kernel, dim3(ceil_div(H, 32), ni), dim3(256), 0, st, H, grp);
   }
   // every weight gradient, and the first-layer input gradients, in one launch
   probs.clear();
