@@ -909,6 +909,26 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// Two-lane FP32 arithmetic (one instruction for both lanes; each lane rounds
+// exactly as the scalar operation does).
+__device__ __forceinline__ float2 fma_x2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul_x2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
 
 // NC consecutive columns cb .. cb + NC - 1 of the tile (NC = 16 or 32).  The
 // other side's per-column inputs come from global memory (every lane reads the
@@ -943,46 +963,60 @@ __device__ __forceinline__ void build_h(const float (&sv)[NC], const HCoef& hc, 
       }
     }
     float h2[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int cl = cb + k + e;
-      const int v = v0 + cl;
-      const int c = (k & 3) + e;
-      const float sval = sv[k + e];
-      if (EK == 0 && LIVE != 0 && !EDGE && OBJ == kObjInfo) {
-        // the common case (-L2, one live softmax term, interior tile, InfoNCE):
-        // h = 2^(-k1 d - l2) k / (tau d), with k / tau per row or per column
-        const float t = fmaxf(fmaf(-2.f, sval, hc.a_own + cax[c]), 0.f);
-        const float rs = t >= 1e-24f ? rsqrt_approx(t) : 0.f;
-        if (LIVE == 1) h2[e] = ex2(fmaf(-hc.k1, t * rs, -hc.l_own2)) * (hc.k_own_tau * rs);
-        else h2[e] = ex2(fmaf(-hc.k1, t * rs, -clse[c])) * (ckoth[c] * hc.inv_tau * rs);
-        continue;
-      }
-      float f2, fac;
-      if (EK == 0) {
-        const float t = fmaxf(fmaf(-2.f, sval, hc.a_own + cax[c]), 0.f);
-        const float rs = t >= 1e-24f ? rsqrt_approx(t) : 0.f;
-        f2 = -(t * rs) * hc.k1;
-        fac = hc.inv_tau * rs;
-      } else if (EK == 1) {
-        const float t = fmaxf(fmaf(-2.f, sval, hc.a_own + cax[c]), 0.f);
-        f2 = -t * hc.k1;
-        fac = 2.f * hc.inv_tau;
+    if constexpr (EK == 0 && LIVE != 0 && !EDGE && OBJ == kObjInfo) {
+      // the common case (-L2, one live softmax term, interior tile, InfoNCE),
+      // both columns of the pair at once: h = 2^(-k1 d - l2) k / (tau d), with
+      // k / tau per row or per column
+      const int c = k & 3;
+      const float2 t2 = fma_x2(make_float2(-2.f, -2.f), make_float2(sv[k], sv[k + 1]),
+                               make_float2(hc.a_own + cax[c], hc.a_own + cax[c + 1]));
+      const float t0 = fmaxf(t2.x, 0.f), t1 = fmaxf(t2.y, 0.f);
+      const float2 rs = make_float2(t0 >= 1e-24f ? rsqrt_approx(t0) : 0.f, t1 >= 1e-24f ? rsqrt_approx(t1) : 0.f);
+      const float2 d = mul_x2(make_float2(t0, t1), rs);
+      float2 arg, fac;
+      if (LIVE == 1) {
+        arg = fma_x2(make_float2(-hc.k1, -hc.k1), d, make_float2(-hc.l_own2, -hc.l_own2));
+        fac = mul_x2(make_float2(hc.k_own_tau, hc.k_own_tau), rs);
       } else {
-        f2 = sval * hc.k1;
-        fac = hc.inv_tau;
+        arg = fma_x2(make_float2(-hc.k1, -hc.k1), d, make_float2(-clse[c], -clse[c + 1]));
+        fac = mul_x2(make_float2(ckoth[c] * hc.inv_tau, ckoth[c + 1] * hc.inv_tau), rs);
       }
-      float g;
-      if (LIVE == 1) g = ex2(f2 - hc.l_own2) * hc.k_own;
-      else if (LIVE == 2) g = ex2(f2 - clse[c]) * ckoth[c];
-      else g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - clse[c]) * ckoth[c]);
-      if (EDGE && u == v) g -= hc.k_diag;
-      if (OBJ != kObjInfo) {
-        const float d_row = hc.transposed ? (v < B ? __ldg(hc.dpre + v) : 0.f) : hc.d_own;
-        const float k_row = hc.transposed ? (v < B ? __ldg(hc.kd + v) : 0.f) : hc.kd_own;
-        g += objective_coef<OBJ>(f2, EDGE && u == v, d_row, k_row, hc);
+      const float2 hv = mul_x2(make_float2(ex2(arg.x), ex2(arg.y)), fac);
+      h2[0] = hv.x;
+      h2[1] = hv.y;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int cl = cb + k + e;
+        const int v = v0 + cl;
+        const int c = (k & 3) + e;
+        const float sval = sv[k + e];
+        float f2, fac;
+        if (EK == 0) {
+          const float t = fmaxf(fmaf(-2.f, sval, hc.a_own + cax[c]), 0.f);
+          const float rs = t >= 1e-24f ? rsqrt_approx(t) : 0.f;
+          f2 = -(t * rs) * hc.k1;
+          fac = hc.inv_tau * rs;
+        } else if (EK == 1) {
+          const float t = fmaxf(fmaf(-2.f, sval, hc.a_own + cax[c]), 0.f);
+          f2 = -t * hc.k1;
+          fac = 2.f * hc.inv_tau;
+        } else {
+          f2 = sval * hc.k1;
+          fac = hc.inv_tau;
+        }
+        float g;
+        if (LIVE == 1) g = ex2(f2 - hc.l_own2) * hc.k_own;
+        else if (LIVE == 2) g = ex2(f2 - clse[c]) * ckoth[c];
+        else g = fmaf(ex2(f2 - hc.l_own2), hc.k_own, ex2(f2 - clse[c]) * ckoth[c]);
+        if (EDGE && u == v) g -= hc.k_diag;
+        if (OBJ != kObjInfo) {
+          const float d_row = hc.transposed ? (v < B ? __ldg(hc.dpre + v) : 0.f) : hc.d_own;
+          const float k_row = hc.transposed ? (v < B ? __ldg(hc.kd + v) : 0.f) : hc.kd_own;
+          g += objective_coef<OBJ>(f2, EDGE && u == v, d_row, k_row, hc);
+        }
+        h2[e] = (!EDGE || (u < B && v < B)) ? g * fac : 0.f;
       }
-      h2[e] = (!EDGE || (u < B && v < B)) ? g * fac : 0.f;
     }
     const __nv_bfloat162 p2 = __floats2bfloat162_rn(h2[0], h2[1]);
     // the row sum takes the BF16-rounded coefficients the MMA multiplies, so
