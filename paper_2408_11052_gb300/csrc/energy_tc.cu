@@ -78,6 +78,35 @@ __device__ __forceinline__ float ex2(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// Two-lane FP32 arithmetic (one instruction for both lanes; each lane rounds
+// exactly as the scalar operation does).
+__device__ __forceinline__ float2 fma_x2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul_x2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 add_x2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -122,11 +151,26 @@ __device__ __forceinline__ void tile_row_full(float (&v)[32], float ax, const fl
                                               float& m, float& mn) {
   m = -INFINITY;
   mn = INFINITY;
+  if constexpr (EK == 0) {
+    // -L2, two columns per instruction (each lane rounds as energy2 does)
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    v[k] = energy2<EK>(v[k], ax, ay[k], k1);
-    m = fmaxf(m, v[k]);
-    mn = fminf(mn, v[k]);
+    for (int k = 0; k < 32; k += 2) {
+      const float2 t = fma_x2(make_float2(-2.f, -2.f), make_float2(v[k], v[k + 1]),
+                              add_x2(make_float2(ax, ax), make_float2(ay[k], ay[k + 1])));
+      const float2 f = mul_x2(make_float2(sqrt_approx(fmaxf(t.x, 0.f)), sqrt_approx(fmaxf(t.y, 0.f))),
+                              make_float2(-k1, -k1));
+      v[k] = f.x;
+      v[k + 1] = f.y;
+      m = fmaxf(m, fmaxf(f.x, f.y));
+      mn = fminf(mn, fminf(f.x, f.y));
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      v[k] = energy2<EK>(v[k], ax, ay[k], k1);
+      m = fmaxf(m, v[k]);
+      mn = fminf(mn, v[k]);
+    }
   }
 }
 
@@ -711,12 +755,15 @@ __device__ __forceinline__ void fwd_body(const CUtensorMap* tmX, const CUtensorM
         const int swz = (lane & 7) << 2;
 #pragma unroll
         for (int k4 = 0; k4 < 8; ++k4) {
+          const float2 d01 = add_x2(make_float2(v[4 * k4], v[4 * k4 + 1]), make_float2(-Mw, -Mw));
+          const float2 d23 = add_x2(make_float2(v[4 * k4 + 2], v[4 * k4 + 3]), make_float2(-Mw, -Mw));
           float4 e4;
-          e4.x = ex2(v[4 * k4] - Mw);
-          e4.y = ex2(v[4 * k4 + 1] - Mw);
-          e4.z = ex2(v[4 * k4 + 2] - Mw);
-          e4.w = ex2(v[4 * k4 + 3] - Mw);
-          s += (e4.x + e4.y) + (e4.z + e4.w);
+          e4.x = ex2(d01.x);
+          e4.y = ex2(d01.y);
+          e4.z = ex2(d23.x);
+          e4.w = ex2(d23.y);
+          const float2 p = add_x2(make_float2(e4.x, e4.z), make_float2(e4.y, e4.w));
+          s += p.x + p.y;
           *reinterpret_cast<float4*>(blk + lane * 32 + ((4 * k4) ^ swz)) = e4;
         }
         lse2_merge(row_m, row_s, Mw, s);
@@ -908,26 +955,6 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-// Two-lane FP32 arithmetic (one instruction for both lanes; each lane rounds
-// exactly as the scalar operation does).
-__device__ __forceinline__ float2 fma_x2(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-__device__ __forceinline__ float2 mul_x2(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
 }
 
 // NC consecutive columns cb .. cb + NC - 1 of the tile (NC = 16 or 32).  The
