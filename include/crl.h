@@ -167,7 +167,7 @@ typedef struct crl_config {
    * the relabelled goal of sample (b + 1) mod B (a goal of another, independently
    * drawn transition), else its own; the choice is (word 2 of the sample's
    * relabel Philox block) >> 32 < floor(alpha_rg 2^32).  The critic always
-   * takes the relabelled goals.  Grouped sweeps take alpha_rg = 0 only. */
+   * takes the relabelled goals (single agents and every kind of sweep). */
   float alpha_rg;
 } crl_config;
 

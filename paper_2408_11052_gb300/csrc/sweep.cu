@@ -111,6 +111,12 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     sweep_check(db ? nullptr : err);
     launch_relabel_multi(dt, db, na, begin[na], bytes, true, 0, st);
   }
+  // random-goal actor mix: the agents with alpha_rg > 0 draw their actors' goals
+  // now and take the single-agent path's unfused actor head (below)
+  for (crl_ctx* c : sw->agents)
+    if (c->cfg.alpha_rg > 0.f)
+      launch_actor_goals(c->cfg.B, c->cfg.G, c->bg, c->bg_act, c->cfg.seed, c->cfg.agent, &c->ctr->last_step,
+                         c->cfg.alpha_rg, st);
   // ---- critic: phi, psi and pi forward (pi's parameters do not change before the actor step)
   std::vector<BfPass> fwd, bwd;
   std::vector<EnergyOut> eo(2 * na);
@@ -160,6 +166,7 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
     std::vector<HeadFwdArgs<float>> hf;
     for (crl_ctx* c : sw->agents) {
       const crl_config& cf = c->cfg;
+      if (cf.alpha_rg > 0.f) continue;   // its head runs with the actor's own goals below
       BfNet& P = c->bf[CRL_NET_PHI];
       HeadFwdArgs<float> h;
       memset(&h, 0, sizeof(h));   // member by member: zeroed padding keys the device table
@@ -184,6 +191,30 @@ void body_grouped(crl_sweep* sw, cudaStream_t st) {
       an.push_back(adam_net_of(c, CRL_NET_PSI, &c->ctr->t_critic, c->cfg.lr_critic));
     }
     sweep_check(adam_shadow_update(sw->tables, an.data(), (int)an.size(), st, &hf));
+  }
+  // ---- actor, goal-mixing agents first: pi(s, g_actor) and psi(g_actor)
+  // inputs, pi's forward, the head's forward and phi's input (s, a')
+  {
+    std::vector<BfPass> pis;
+    for (crl_ctx* c : sw->agents) {
+      if (c->cfg.alpha_rg <= 0.f) continue;
+      const int B = c->cfg.B;
+      bf_net_pack_input(c->bf[CRL_NET_PI], c->bs, c->bg_act, B, st);
+      bf_net_pack_input(c->bf[CRL_NET_PSI], c->bg_act, nullptr, B, st);
+      pis.push_back({&c->bf[CRL_NET_PI], static_cast<const float*>(c->nets[CRL_NET_PI].params), nullptr, nullptr, B});
+    }
+    if (!pis.empty()) {
+      sweep_check(bf_forward(sw->groups, pis.data(), (int)pis.size(), status, st));
+      for (crl_ctx* c : sw->agents) {
+        if (c->cfg.alpha_rg <= 0.f) continue;
+        const crl_config& cf = c->cfg;
+        float* a_new = static_cast<float*>(c->a_new);
+        actor_head_forward<float>(actor_spec_of(c), c->bf[CRL_NET_PI].y, nullptr, &c->ctr->last_step, cf.seed,
+                                  cf.agent, cf.B, a_new, static_cast<float*>(c->logpi),
+                                  static_cast<float*>(c->eps_used), st);
+        bf_net_pack_input(c->bf[CRL_NET_PHI], c->bs, a_new, cf.B, st);
+      }
+    }
   }
   // ---- actor: phi and psi forward with the updated critic, diagonal energy +
   // loss, phi's input gradient, head backward, pi backward
@@ -303,8 +334,6 @@ int crl_sweep_create(const crl_config* cfgs, int32_t n, int32_t grouped, crl_swe
     if (grouped) {
       CRL_REQUIRE(c0.precision == CRL_PREC_BF16 && c0.path == CRL_PATH_FUSED, CRL_E_UNSUPPORTED,
                   "the grouped sweep runs the BF16 fused path");
-      for (int i = 0; i < n; ++i)
-        CRL_REQUIRE(cfgs[i].alpha_rg == 0.f, CRL_E_UNSUPPORTED, "the grouped sweep takes alpha_rg = 0 only");
     }
     sw = new crl_sweep();
     sw->grouped = grouped ? 1 : 0;
