@@ -357,7 +357,8 @@ void critic_impl_bf16(crl_ctx* c, const float* s, const float* a, const float* g
     // fused tcgen05 energy stage: no B x B matrix; the gradients land in the encoders' dy buffers
     const char* e = energy_tc_maps(c->etc, B);
     if (e) throw Failure(CRL_E_CUDA, std::string("tensor map: ") + e);
-    energy_tc_forward(c->etc, ls, B, loss, rl, cl, c->etc_ws, status, apply ? &c->ctr->t_critic : nullptr, st);
+    energy_tc_forward(c->etc, ls, B, P.y, Q.y, loss, rl, cl, c->etc_ws, status, apply ? &c->ctr->t_critic : nullptr,
+                      st);
     energy_tc_backward(c->etc, ls, B, P.y, Q.y, rl, cl, 1.0, P.dz[P.layers], Q.dz[Q.layers], c->etc_ws, status,
                        st);
   } else {
@@ -702,8 +703,9 @@ int crl_create(const crl_config* cfg, crl_ctx** out) {
       e.Y = static_cast<__nv_bfloat16*>(c->dalloc((size_t)B * R * 2));
       e.auxX = static_cast<float*>(c->dalloc((size_t)B * 4));
       e.auxY = static_cast<float*>(c->dalloc((size_t)B * 4));
-      c->etc_ws = c->dalloc(energy_tc_ws_bytes(B));
-      CRL_CHECK_CUDA(cudaMemset(c->etc_ws, 0, energy_tc_ws_bytes(B)));   // the finalize ticket starts at 0
+      const size_t ews = energy_tc_ws_bytes(loss_spec(cf), B, R);
+      c->etc_ws = c->dalloc(ews);
+      CRL_CHECK_CUDA(cudaMemset(c->etc_ws, 0, ews));   // the finalize ticket starts at 0
     }
     CRL_CHECK_CUDA(cudaDeviceSynchronize());
   });
@@ -1122,7 +1124,7 @@ int crl_infonce_workspace_bytes(const crl_loss_desc* d, int32_t B, int32_t R, si
   return guarded(nullptr, [&] {
     const LossSpec ls = checked_loss(d);
     CRL_REQUIRE(bytes && B >= 1 && R >= 1, CRL_E_INVALID_ARG, "bad argument");
-    *bytes = d->dtype == CRL_PREC_BF16 ? infonce_bf16_ws_bytes(B, R)
+    *bytes = d->dtype == CRL_PREC_BF16 ? infonce_bf16_ws_bytes(ls, B, R)
                                        : infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path);
   });
 }
@@ -1133,7 +1135,7 @@ int crl_infonce_forward(const crl_loss_desc* d, const void* phi, const void* psi
     const LossSpec ls = checked_loss(d);
     CRL_REQUIRE(phi && psi && loss4 && row_lse && col_lse && ws && B >= 1 && R >= 1, CRL_E_INVALID_ARG,
                 "bad argument");
-    CRL_REQUIRE(ws_bytes >= (d->dtype == CRL_PREC_BF16 ? infonce_bf16_ws_bytes(B, R)
+    CRL_REQUIRE(ws_bytes >= (d->dtype == CRL_PREC_BF16 ? infonce_bf16_ws_bytes(ls, B, R)
                                                        : infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path)),
                 CRL_E_SHAPE, "workspace too small");
     CRL_REQUIRE(ls.loss != CRL_LOSS_FB || B >= 2, CRL_E_SHAPE, "the forward-backward objective needs B >= 2");
@@ -1161,7 +1163,7 @@ int crl_infonce_backward(const crl_loss_desc* d, const void* phi, const void* ps
     const LossSpec ls = checked_loss(d);
     CRL_REQUIRE(phi && psi && row_lse && col_lse && dphi && dpsi && ws && B >= 1 && R >= 1, CRL_E_INVALID_ARG,
                 "bad argument");
-    CRL_REQUIRE(ws_bytes >= (d->dtype == CRL_PREC_BF16 ? infonce_bf16_ws_bytes(B, R)
+    CRL_REQUIRE(ws_bytes >= (d->dtype == CRL_PREC_BF16 ? infonce_bf16_ws_bytes(ls, B, R)
                                                        : infonce_ws_bytes(ls, B, R, dtype_size(d->dtype), d->path)),
                 CRL_E_SHAPE, "workspace too small");
     CRL_REQUIRE(ls.loss != CRL_LOSS_FB || B >= 2, CRL_E_SHAPE, "the forward-backward objective needs B >= 2");

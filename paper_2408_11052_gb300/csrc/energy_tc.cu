@@ -40,6 +40,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "energy_args.cuh"
 #include "energy_tc.cuh"
 #include "tc_common.cuh"
 #include "tc_host.h"
@@ -47,66 +48,10 @@
 
 namespace crl {
 
-using bf16 = __nv_bfloat16;
+using namespace fe;
 
 namespace {
 
-constexpr int kTile = 128;
-
-struct Weights {
-  float wf, wb, pr, pc;
-};
-
-// Weights of the InfoNCE directions (FlatNCE takes InfoNCE's gradient; the
-// other objectives none) and of the penalty axes.
-Weights loss_weights(const LossSpec& ls) {
-  Weights w{0, 0, 0, 0};
-  if (ls.loss == CRL_LOSS_FWD || ls.loss == CRL_LOSS_FLATNCE_FWD) w.wf = 1;
-  else if (ls.loss == CRL_LOSS_BWD || ls.loss == CRL_LOSS_FLATNCE_BWD) w.wb = 1;
-  else if (ls.loss == CRL_LOSS_SYM) w.wf = w.wb = (ls.sym_reduction == CRL_SYM_SUM) ? 1.f : 0.5f;
-  if (ls.penalty_axis == CRL_PENALTY_ROW) w.pr = 1;
-  else if (ls.penalty_axis == CRL_PENALTY_COL) w.pc = 1;
-  else w.pr = w.pc = 0.5f;
-  return w;
-}
-
-constexpr float kLog2e = 1.4426950408889634f;
-constexpr float kLn2 = 0.69314718055994531f;
-
-__device__ __forceinline__ float ex2(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-// Two-lane FP32 arithmetic (one instruction for both lanes; each lane rounds
-// exactly as the scalar operation does).
-__device__ __forceinline__ float2 fma_x2(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-__device__ __forceinline__ float2 mul_x2(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-__device__ __forceinline__ float2 add_x2(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -240,38 +185,7 @@ __global__ void __launch_bounds__(1024) prep_kernel(int B, int R, int energy, in
 }
 
 // ---- forward ----------------------------------------------------------------------
-// 512 threads: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows) and handles
-// columns 32 (w / 4) .. + 31 of the 128-wide tile.
-constexpr int kThreads = 512;
 
-struct FwdArgs {
-  int B, R, energy, obj;  // obj: the loss code
-  int n, C, nC;           // tiles per side; column tiles per chunk (at most 64) and chunks per row tile
-  float inv_tau;
-  const float* auxX;
-  const float* auxY;
-  const bf16* X;   // [B][R] operand rows (the DPO / IPO anchor F_ii)
-  const bf16* Y;
-  float* objpart;  // [nC][B][2] per-row objective partials over each column chunk
-  float* dpre;     // [B] the anchor F_ii of DPO / IPO (written by the J = 0 tiles)
-  float* kd;       // [B] k_i of DPO / IPO (written by the row merges)
-  float* rowpart;  // [nC][B][2] per-row (max, sum) over each column chunk
-  float* colpart;  // [nI][B][2]
-  float* diag;     // [B]
-  unsigned* status;
-  // finalize (run by the last CTA to finish)
-  Weights w;
-  float beta;
-  float* r_out;
-  float* c_out;
-  float* loss4;
-  int* t_bump;
-  unsigned* tickets;  // [2 n + 1]: per row tile (chunks), per column tile (row tiles), final (zero between launches)
-  float* tile_part;   // [2][n][3]: per row / column tile (sum of (lse - diag), sum of lse^2, objective value)
-};
-
-__device__ __forceinline__ float sigmoidf_fast(float x) { return __frcp_rn(1.f + __expf(-x)); }
-__device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.f) + log1pf(__expf(-fabsf(x))); }
 
 // Row u's share of the objective's value from its merged partials (vp: the sum
 // over j of the objective's pair terms; d: F_uu; see the plain path).
@@ -855,23 +769,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1) fwd_kernel(const __grid_consta
 }
 
 // ---- backward ---------------------------------------------------------------------
-struct BwdArgs {
-  int B, R, energy, transposed;  // transposed: own = psi (the column pass)
-  int obj;                       // the loss code
-  float inv_tau, beta, scale;    // scale = dtotal / B
-  float dtotal;
-  const float* dpre;             // [B] anchor F_ii of DPO / IPO (from the forward)
-  const float* kd;               // [B] k_i of DPO / IPO (from the forward)
-  Weights w;
-  const float* aux_own;
-  const float* aux_other;
-  const float* lse_own;    // r (row pass) or c (column pass)
-  const float* lse_other;  // c (row pass) or r (column pass)
-  const float* own_f32;    // [B][R] FP32 representation (cos: unnormalised)
-  bf16* d_out;             // [B][R]
-  unsigned* status;
-  float* d_out_f32;        // non-null: the gradient as FP32 [B][R] here instead of d_out
-};
 
 // Offset in a 128-byte-swizzled K-major tile (8-row groups of 1024 bytes) of
 // the 16-byte chunk `chunk` (8 BF16 along K) of row `row`.
@@ -886,57 +783,6 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int chunk) {
 // the TMEM accumulator.
 // CTAs [0, nrow) run the row pass (own = phi), CTAs [nrow, 2 nrow) the column pass (own = psi).
 // Per-row constants of the coefficient tile (own side = this thread's row).
-struct HCoef {
-  float a_own;    // own auxiliary (|x|^2 for the L2 energies)
-  float l_own2;   // own logsumexp x log2(e)
-  float k_own;    // scale (w_own + 2 beta p_own l_own)
-  float k_own_tau;  // k_own / tau
-  float k_diag;   // scale (w_f + w_b): the positive pair's -1 terms
-  float inv_tau;
-  float k1;       // log2(e) / tau
-  // objectives outside InfoNCE (OBJ > 0)
-  float d_own, kd_own;  // row pass: this row's anchor F_uu and k_u
-  const float* dpre;    // column pass: the rows' anchors and k (read per pair)
-  const float* kd;
-  float c_bb, c_b, c_fb;  // dtotal / B^2, dtotal / B, dtotal / (B (B - 1))
-  float dtotal;
-  int transposed;
-};
-
-// Objective kinds of the coefficient tile: 0 the InfoNCE family (FlatNCE
-// included), then forward-backward, DPO, IPO, SPPO, NCE-binary.
-enum : int { kObjInfo = 0, kObjFB, kObjDPO, kObjIPO, kObjSPPO, kObjNCE };
-inline int obj_kind(int loss) {
-  switch (loss) {
-    case CRL_LOSS_FB: return kObjFB;
-    case CRL_LOSS_DPO: return kObjDPO;
-    case CRL_LOSS_IPO: return kObjIPO;
-    case CRL_LOSS_SPPO: return kObjSPPO;
-    case CRL_LOSS_NCE_BINARY: return kObjNCE;
-    default: return kObjInfo;
-  }
-}
-
-// dtotal x (the objective's dL/dF_ij) for F = f2 / log2(e); the row of the pair
-// is u in the row pass and v in the column pass (d_row, k_row: its anchor F_ii
-// and k_i, the latter already divided by B^2).
-template <int OBJ>
-__device__ __forceinline__ float objective_coef(float f2, bool diag, float d_row, float k_row, const HCoef& hc) {
-  if (OBJ == kObjFB) return diag ? -ex2(f2) * hc.c_b : ex2(2.f * f2) * hc.c_fb;
-  const float F = f2 * (1.f / kLog2e);
-  float o;
-  if (OBJ == kObjDPO) {
-    o = __frcp_rn(1.f + ex2((d_row - F) * kLog2e)) * hc.c_bb;  // sigma(F - d)
-  } else if (OBJ == kObjIPO) {
-    o = -2.f * (d_row - F - 1.f) * hc.c_bb;
-  } else if (OBJ == kObjSPPO) {
-    o = 2.f * (F + 1.f) * hc.c_bb + (diag ? 2.f * (F - 1.f) * hc.c_b : 0.f);
-  } else {  // NCE-binary: sigma(F) - [i = j]
-    o = (__frcp_rn(1.f + ex2(-f2)) - (diag ? 1.f : 0.f)) * hc.c_bb;
-  }
-  if ((OBJ == kObjDPO || OBJ == kObjIPO) && diag) o -= k_row * hc.dtotal;
-  return o;
-}
 
 // dL/dF x (chain factor of the energy) for this thread's 32 columns 32 q ..:
 // with P_own = e^(F - l_own) and P_oth = e^(F - l_oth),
@@ -1567,18 +1413,25 @@ const char* mk(CUtensorMap* m, const void* base, int inner, int rows, int stride
 // Workspace of the forward: tickets [2 n + 1] (zeroed when the workspace is
 // created, reset by the CTAs that use them), tile loss partials [2][n][3],
 // rowpart [nJ][B][2], colpart [nI][B][2], diag [B], objpart [nJ][B][2],
-// dpre [B], kd [B].
-size_t energy_tc_ws_bytes(int B) {
+// dpre [B], kd [B]; for the -L1 energy then the backward's per-segment partial
+// gradients.
+size_t energy_tc_base_bytes(int B) {
   const int n = (B + kTile - 1) / kTile;
   return (size_t)round_up((2 * n + 1) * 4, 256) + (size_t)round_up(6 * n * 4, 256) +
          ((size_t)2 * n * B * 3 + 3 * (size_t)B) * sizeof(float);
 }
+size_t energy_tc_ws_bytes(const LossSpec& ls, int B, int R) {
+  const size_t base = energy_tc_base_bytes(B);
+  if (ls.energy != CRL_ENERGY_L1) return base;
+  return round_up(base, 256) + l1_part_floats(B, R) * sizeof(float);
+}
+namespace {
+float* l1_part(void* ws, int B) {
+  return reinterpret_cast<float*>(static_cast<char*>(ws) + round_up(energy_tc_base_bytes(B), 256));
+}
+}  // namespace
 
 bool energy_tc_supported(const LossSpec& ls, int B, int R, const char** why) {
-  if (ls.energy == CRL_ENERGY_L1) {
-    *why = "the fused path has no L1 energy";
-    return false;
-  }
   if (R % 64 != 0 || R > 256) {
     *why = "the fused path needs repr to be 64, 128, 192 or 256";
     return false;
@@ -1600,23 +1453,31 @@ const char* energy_tc_maps(EnergyTc& e, int B) {
 }
 
 void energy_tc_prepare(EnergyTc& e, const LossSpec& ls, const float* phi, const float* psi, int B, cudaStream_t st) {
+  if (ls.energy == CRL_ENERGY_L1) return;   // the -L1 tiles read the FP32 rows themselves
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 0.0);
   launch_k(prep_kernel, dim3(ceil_div(B, 32), 2), dim3(1024), 0, st, B, e.R, ls.energy, e.ldt,
            PrepSide{phi, e.X, e.XT, e.auxX}, PrepSide{psi, e.Y, e.YT, e.auxY});
 }
 
-void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, float* r, float* c, void* ws,
-                       unsigned* status, int* t_bump, cudaStream_t st) {
+void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, float* loss4,
+                       float* r, float* c, void* ws, unsigned* status, int* t_bump, cudaStream_t st) {
   const int n = (B + kTile - 1) / kTile;
   FwdArgs a = fwd_args(e, ls, B, ws, loss4, r, c, t_bump, status);
-  const size_t sm = fwd_smem(e.R);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
-    cudaFuncSetAttribute(fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
-    attr = true;
-  }
-  {
+  if (ls.energy == CRL_ENERGY_L1) {
+    // SIMT tiles, one column tile per chunk
+    a.C = 1;
+    a.nC = n;
+    a.phi = phi;
+    a.psi = psi;
+    l1_forward(a, st);
+  } else {
+    const size_t sm = fwd_smem(e.R);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
+      cudaFuncSetAttribute(fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(256));
+      attr = true;
+    }
     TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * B * e.R);
     if (ls.loss >= CRL_LOSS_FB)
       launch_k(fwd_kernel<true>, dim3(n * a.nC), dim3(kFwdThreads), sm, st, e.tmX, e.tmY, a);
@@ -1661,22 +1522,18 @@ void launch_bwd_multi(int kind, const EnergyTask* dt, const int* db, int na, int
 }
 }  // namespace
 
-void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
-                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dpsi, void* ws,
-                        unsigned* status,
-                        cudaStream_t st) {
+namespace {
+// Both passes: the tcgen05 backward, or the SIMT one for the -L1 energy.
+void backward_passes(const EnergyTc& e, const LossSpec& ls, int B, BwdArgs& a, BwdArgs& b, void* ws,
+                     cudaStream_t st) {
+  a.other_f32 = b.own_f32;
+  b.other_f32 = a.own_f32;
+  if (ls.energy == CRL_ENERGY_L1) {
+    l1_backward(a, b, l1_part(ws, B), st);
+    return;
+  }
   const int n = (B + kTile - 1) / kTile;
   const size_t sm = bwd_smem(e.R);
-  const FwdArgs f = fwd_args(e, ls, B, ws, nullptr, nullptr, nullptr, nullptr, status);
-  const BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, dphi, status, f);
-  BwdArgs b = a;
-  b.transposed = 1;
-  b.aux_own = e.auxY;
-  b.aux_other = e.auxX;
-  b.lse_own = c;
-  b.lse_other = r;
-  b.own_f32 = psi;
-  b.d_out = dpsi;
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 8.0 * B * B * e.R);
   switch (obj_kind(ls.loss)) {
     case kObjFB: launch_bwd_t<kObjFB>(e, a, b, n, sm, st); break;
@@ -1688,14 +1545,9 @@ void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi
   }
 }
 
-void energy_tc_backward_f32(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi,
-                            const float* r, const float* c, double dtotal, float* dphi, float* dpsi, void* ws,
-                            unsigned* status, cudaStream_t st) {
-  const int n = (B + kTile - 1) / kTile;
-  const size_t sm = bwd_smem(e.R);
-  const FwdArgs f = fwd_args(e, ls, B, ws, nullptr, nullptr, nullptr, nullptr, status);
-  BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, nullptr, status, f);
-  a.d_out_f32 = dphi;
+// The column pass's arguments from the row pass's: the roles of phi and psi
+// (and of r and c) exchanged.
+BwdArgs column_args(const EnergyTc& e, const BwdArgs& a, const float* psi, const float* r, const float* c) {
   BwdArgs b = a;
   b.transposed = 1;
   b.aux_own = e.auxY;
@@ -1703,16 +1555,29 @@ void energy_tc_backward_f32(EnergyTc& e, const LossSpec& ls, int B, const float*
   b.lse_own = c;
   b.lse_other = r;
   b.own_f32 = psi;
+  return b;
+}
+}  // namespace
+
+void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
+                        const float* c, double dtotal, __nv_bfloat16* dphi, __nv_bfloat16* dpsi, void* ws,
+                        unsigned* status, cudaStream_t st) {
+  const FwdArgs f = fwd_args(e, ls, B, ws, nullptr, nullptr, nullptr, nullptr, status);
+  BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, dphi, status, f);
+  BwdArgs b = column_args(e, a, psi, r, c);
+  b.d_out = dpsi;
+  backward_passes(e, ls, B, a, b, ws, st);
+}
+
+void energy_tc_backward_f32(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi,
+                            const float* r, const float* c, double dtotal, float* dphi, float* dpsi, void* ws,
+                            unsigned* status, cudaStream_t st) {
+  const FwdArgs f = fwd_args(e, ls, B, ws, nullptr, nullptr, nullptr, nullptr, status);
+  BwdArgs a = bwd_args(e, ls, B, phi, r, c, dtotal, nullptr, status, f);
+  a.d_out_f32 = dphi;
+  BwdArgs b = column_args(e, a, psi, r, c);
   b.d_out_f32 = dpsi;
-  TraceLaunch tr(CRL_TRACE_ENERGY, st, 8.0 * B * B * e.R);
-  switch (obj_kind(ls.loss)) {
-    case kObjFB: launch_bwd_t<kObjFB>(e, a, b, n, sm, st); break;
-    case kObjDPO: launch_bwd_t<kObjDPO>(e, a, b, n, sm, st); break;
-    case kObjIPO: launch_bwd_t<kObjIPO>(e, a, b, n, sm, st); break;
-    case kObjSPPO: launch_bwd_t<kObjSPPO>(e, a, b, n, sm, st); break;
-    case kObjNCE: launch_bwd_t<kObjNCE>(e, a, b, n, sm, st); break;
-    default: launch_bwd_t<kObjInfo>(e, a, b, n, sm, st); break;
-  }
+  backward_passes(e, ls, B, a, b, ws, st);
 }
 
 size_t energy_tc_ticket_bytes(int B) {
@@ -1720,7 +1585,18 @@ size_t energy_tc_ticket_bytes(int B) {
   return (size_t)(2 * n + 1) * 4;
 }
 
-const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& agents, int stage, cudaStream_t st) {
+const char* energy_tc_multi(BlobCache& cache, const std::vector<EnergyAgent>& all, int stage, cudaStream_t st) {
+  // the -L1 agents run their own SIMT launches; the rest share one launch per stage
+  std::vector<EnergyAgent> agents;
+  for (const EnergyAgent& g : all) {
+    if (g.ls.energy != CRL_ENERGY_L1) {
+      agents.push_back(g);
+    } else if (stage == 1) {
+      energy_tc_forward(*g.e, g.ls, g.B, g.phi, g.psi, g.loss4, g.r, g.c, g.ws, g.status, g.t_bump, st);
+    } else if (stage == 2) {
+      energy_tc_backward(*g.e, g.ls, g.B, g.phi, g.psi, g.r, g.c, 1.0, g.dphi, g.dpsi, g.ws, g.status, st);
+    }
+  }
   const int na = (int)agents.size();
   if (na == 0) return nullptr;
   std::vector<EnergyTask> tasks(na);

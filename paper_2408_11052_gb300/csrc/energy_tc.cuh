@@ -22,13 +22,17 @@ struct EnergyTc {
 };
 
 bool energy_tc_supported(const LossSpec& ls, int B, int R, const char** why);
-size_t energy_tc_ws_bytes(int B);
+// Bytes of the workspace of energy_tc_forward / energy_tc_backward.
+size_t energy_tc_ws_bytes(const LossSpec& ls, int B, int R);
 const char* energy_tc_maps(EnergyTc& e, int B);
-// phi, psi [B][R] FP32 -> BF16 operands, transposes and auxiliaries.
+// phi, psi [B][R] FP32 -> BF16 operands and auxiliaries (nothing for -L1,
+// whose tiles read phi and psi).
 void energy_tc_prepare(EnergyTc& e, const LossSpec& ls, const float* phi, const float* psi, int B, cudaStream_t st);
-// loss4 = {total, fwd, bwd, penalty}; r, c = row / column logsumexp.  ws: energy_tc_ws_bytes(B).
-void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, float* loss4, float* r, float* c, void* ws,
-                       unsigned* status, int* t_bump, cudaStream_t st);
+// loss4 = {total, fwd, bwd, penalty}; r, c = row / column logsumexp.  ws:
+// energy_tc_ws_bytes(ls, B, R).  phi, psi: the FP32 representations (read by
+// the -L1 energy; the others read the BF16 operands).
+void energy_tc_forward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, float* loss4,
+                       float* r, float* c, void* ws, unsigned* status, int* t_bump, cudaStream_t st);
 // dphi / dpsi as BF16 [B][R] (the encoders' dy layout), scaled by dtotal.
 // ws: the forward's workspace (its anchors and diagonal coefficients for DPO / IPO).
 void energy_tc_backward(EnergyTc& e, const LossSpec& ls, int B, const float* phi, const float* psi, const float* r,
@@ -54,7 +58,7 @@ struct EnergyAgent {
   float* loss4;
   float* r;
   float* c;
-  void* ws;           // energy_tc_ws_bytes(B), zeroed at creation
+  void* ws;           // energy_tc_ws_bytes(ls, B, R), zeroed at creation
   int* t_bump;
   __nv_bfloat16* dphi;
   __nv_bfloat16* dpsi;

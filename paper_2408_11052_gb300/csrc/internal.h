@@ -131,7 +131,7 @@ void mlp_bf16_backward(const MlpShape& s, const float* params, int M, const void
                        float* dparams, float* dx0, float* dx1, cudaStream_t st);
 // The fused energy stage on FP32 representations phi, psi [B][R]; ws
 // (infonce_bf16_ws_bytes) carries the BF16 operands from a forward to its backward.
-size_t infonce_bf16_ws_bytes(int B, int R);
+size_t infonce_bf16_ws_bytes(const LossSpec& ls, int B, int R);
 void infonce_bf16_forward(const LossSpec& ls, const float* phi, const float* psi, int B, int R, float* loss4,
                           float* row_lse, float* col_lse, void* ws, cudaStream_t st);
 void infonce_bf16_backward(const LossSpec& ls, const float* phi, const float* psi, int B, int R, const float* row_lse,

@@ -104,11 +104,11 @@ struct EnergyWs {
   void* ews;
   unsigned* status;
 };
-const char* carve_energy(EnergyWs& w, int B, int R, void* ws) {
+const char* carve_energy(EnergyWs& w, const LossSpec& ls, int B, int R, void* ws) {
   char* base = static_cast<char*>(ws);
   w.status = reinterpret_cast<unsigned*>(base);
   Carver c{base + kStatusBytes, 0};
-  w.ews = carve_piece(&c, energy_tc_ws_bytes(B));
+  w.ews = carve_piece(&c, energy_tc_ws_bytes(ls, B, R));
   w.e.R = R;
   w.e.Bmax = B;
   w.e.ldt = 0;
@@ -121,11 +121,19 @@ const char* carve_energy(EnergyWs& w, int B, int R, void* ws) {
   return energy_tc_maps(w.e, B);
 }
 
+// The -L1 tiles move rows in 16-byte pieces.
+void check_l1_alignment(const LossSpec& ls, const void* a, const void* b, const void* c, const void* d) {
+  if (ls.energy != CRL_ENERGY_L1) return;
+  const uintptr_t bits = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+                         reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d);
+  if (bits % 16 != 0) throw Failure(CRL_E_INVALID_ARG, "the fused -L1 energy needs 16-byte aligned rows");
+}
+
 }  // namespace
 
-size_t infonce_bf16_ws_bytes(int B, int R) {
+size_t infonce_bf16_ws_bytes(const LossSpec& ls, int B, int R) {
   Carver c{nullptr, 0};
-  carve_piece(&c, energy_tc_ws_bytes(B));
+  carve_piece(&c, energy_tc_ws_bytes(ls, B, R));
   carve_piece(&c, (size_t)B * R * 2);
   carve_piece(&c, (size_t)B * R * 2);
   carve_piece(&c, (size_t)B * 4);
@@ -137,21 +145,23 @@ void infonce_bf16_forward(const LossSpec& ls, const float* phi, const float* psi
                           float* row_lse, float* col_lse, void* ws, cudaStream_t st) {
   const char* why = nullptr;
   if (!energy_tc_supported(ls, B, R, &why)) throw Failure(CRL_E_UNSUPPORTED, why);
+  check_l1_alignment(ls, phi, psi, nullptr, nullptr);
   EnergyWs w;
-  if (const char* e = carve_energy(w, B, R, ws)) throw Failure(CRL_E_INVALID_ARG, e);
+  if (const char* e = carve_energy(w, ls, B, R, ws)) throw Failure(CRL_E_INVALID_ARG, e);
   // status word and tickets start at zero
   CRL_CHECK_CUDA(cudaMemsetAsync(ws, 0, kStatusBytes, st));
   CRL_CHECK_CUDA(cudaMemsetAsync(w.ews, 0, energy_tc_ticket_bytes(B), st));
   energy_tc_prepare(w.e, ls, phi, psi, B, st);
-  energy_tc_forward(w.e, ls, B, loss4, row_lse, col_lse, w.ews, w.status, nullptr, st);
+  energy_tc_forward(w.e, ls, B, phi, psi, loss4, row_lse, col_lse, w.ews, w.status, nullptr, st);
 }
 
 void infonce_bf16_backward(const LossSpec& ls, const float* phi, const float* psi, int B, int R, const float* row_lse,
                            const float* col_lse, double dtotal, float* dphi, float* dpsi, void* ws, cudaStream_t st) {
   const char* why = nullptr;
   if (!energy_tc_supported(ls, B, R, &why)) throw Failure(CRL_E_UNSUPPORTED, why);
+  check_l1_alignment(ls, phi, psi, dphi, dpsi);
   EnergyWs w;
-  if (const char* e = carve_energy(w, B, R, ws)) throw Failure(CRL_E_INVALID_ARG, e);
+  if (const char* e = carve_energy(w, ls, B, R, ws)) throw Failure(CRL_E_INVALID_ARG, e);
   energy_tc_backward_f32(w.e, ls, B, phi, psi, row_lse, col_lse, dtotal, dphi, dpsi, w.ews, w.status, st);
 }
 

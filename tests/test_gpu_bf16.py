@@ -184,7 +184,7 @@ def check_fused(ctx, got, ref):
     assert ctx.sync_status() == (0, 0)
 
 
-@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq"])
+@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq", "l1"])
 @pytest.mark.parametrize("loss", ["fwd", "bwd", "sym"])
 def test_fused_critic_matches_oracle(energy, loss):
     w = bf16_small(energy=energy, loss=loss, repr=64, tau=0.7 if energy == "cos" else 1.0)
@@ -223,7 +223,7 @@ def test_bf16_layernorm_rows_wider_than_registers(hidden):
 OBJECTIVES = ["flatnce_fwd", "flatnce_bwd", "fb", "dpo", "ipo", "sppo", "nce_binary"]
 
 
-@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq"])
+@pytest.mark.parametrize("energy", ["l2", "dot", "cos", "l2sq", "l1"])
 @pytest.mark.parametrize("loss", OBJECTIVES)
 def test_fused_critic_objectives_match_oracle(energy, loss):
     """The objectives outside InfoNCE on the fused tcgen05 path (App. A.2 / §5.2).

@@ -398,15 +398,13 @@ def test_gemm_kernel_mode_is_validated():
     assert api.set_gemm_kernel("any") == "any"
 
 
-def test_l1_energy_runs_on_the_plain_path_only():
-    """-L1 (App. A.2) has a plain-path backward; the fused BF16 path rejects it."""
+def test_l1_energy_runs_on_every_path():
+    """-L1 (App. A.2) trains on the plain paths and on the fused path (SIMT tiles)."""
     w = small(B=64, energy="l1")
     h = ctypes.c_void_p()
-    cfg = api.make_config(w, precision="bf16", path="fused", repr=64)
-    assert api.lib().crl_create(ctypes.byref(cfg), ctypes.byref(h)) == api.E_UNSUPPORTED
-    for precision in ("fp32", "bf16"):
-        cfg = api.make_config(w, precision=precision, path="plain")
-        assert api.lib().crl_create(ctypes.byref(cfg), ctypes.byref(h)) == api.OK
+    for precision, path, R in (("bf16", "fused", 64), ("fp32", "plain", w.repr), ("bf16", "plain", w.repr)):
+        cfg = api.make_config(w.with_(repr=R), precision=precision, path=path)
+        assert api.lib().crl_create(ctypes.byref(cfg), ctypes.byref(h)) == api.OK, (precision, path)
         api.lib().crl_destroy(h)
 
 

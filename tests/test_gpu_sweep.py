@@ -109,6 +109,13 @@ def test_grouped_sweep_with_random_goal_mix():
     run_and_compare(ws, "bf16", "fused", grouped=True, steps=3)
 
 
+def test_grouped_sweep_with_l1_agents():
+    """-L1 agents (their own SIMT energy launches) beside tcgen05 ones in one grouped sweep."""
+    ws = [w.with_(energy=e, loss=l) for w, e, l in zip(uneven_agents(), ("l1", "l2", "l1", "cos"),
+                                                       ("sym", "fwd", "dpo", "sym"))]
+    run_and_compare(ws, "bf16", "fused", grouped=True, steps=3)
+
+
 def test_grouped_sweep_of_32_agents_sampled():
     """The 32-agent sweep workload's shapes (batch 256..2048, obs 29 / 64 / 268,
     repr 64 / 128, 512 envs), short buffers; agents 0, 13 and 31 checked."""
