@@ -510,6 +510,8 @@ def run_arm(args, w, precision, path, dev, world, rank, flush, full):
         out["e2e_ms"] = max_over_ranks(e2e_ms, world)
     rc, status = ctx.sync_status()
     assert rc == api.OK, f"status {status}"
+    if full and precision == "bf16":
+        out["gemm_tuning"] = api.gemm_tuning_report(ctx.handle)
     ctx.close()
     return out
 
@@ -876,6 +878,10 @@ def main():
                           **main_arm["breakdown"]},
             "roofline": roof,
             "clocks": main_arm["clocks"]}
+    if main_arm.get("gemm_tuning") is not None:
+        line["gemm_tuning"] = {"note": "the tile autotuner's picks for this workload's grouped GEMM launches, "
+                                       "each candidate's faster time per launch over two timing rounds (us)",
+                               "groups": main_arm["gemm_tuning"]}
     if comparator is not None:
         line["comparator"] = comparator
     if error is not None:

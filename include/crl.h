@@ -112,7 +112,8 @@ extern "C" {
 #define CRL_PATH_PLAIN 0  /* one kernel per op; the B x B energy matrix in HBM */
 #define CRL_PATH_FUSED 1  /* fused kernels; the B x B matrix is never written   */
                           /* (BF16 only; repr 64 / 128 / 192 / 256, B a multiple
-                           * of 8; every energy but L1, which the plain path has) */
+                           * of 8; every energy: L1 on FP32 SIMT tiles over the
+                           * FP32 representations, the others on tcgen05) */
 /* networks */
 #define CRL_NET_PHI 0     /* phi(s, a): input concat(s, a), output repr        */
 #define CRL_NET_PSI 1     /* psi(g):    input g, output repr                   */
@@ -462,6 +463,20 @@ int32_t crl_set_autotune(int32_t enable);
 #define CRL_GEMM_PERSISTENT 2
 #define CRL_GEMM_CTA_PAIR 3
 int32_t crl_set_gemm_kernel(int32_t mode);
+
+/* What the tile autotuner measured (library extension; the paper has no
+ * counterpart).  Writes a NUL-terminated JSON array with one object per
+ * grouped GEMM problem list the context (or sweep) has tuned so far, in tuning
+ * order: "problems" (the list's length), "first_mnk" (M, N, K of its first
+ * problem), "gflop" (one launch's algorithmic work), "picked" (the kept
+ * configuration: kernel, tile rows x columns, ring depth) and "us" (each
+ * candidate's faster time per launch over the two timing rounds, in
+ * microseconds; -1 where it could not be timed).  *needed receives the bytes
+ * the report takes including the NUL; call with buf = NULL and len = 0 to ask
+ * for it.  Returns CRL_E_SHAPE (nothing written) when 0 < len < *needed.
+ * Host memory only; does not touch the device. */
+int32_t crl_gemm_tuning_report(crl_ctx* ctx, char* buf, size_t len, size_t* needed);
+int32_t crl_sweep_gemm_tuning_report(crl_sweep* sw, char* buf, size_t len, size_t* needed);
 
 
 /* ---- op-level entry points (stateless; used by torch.autograd.Function) ---

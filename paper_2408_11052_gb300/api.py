@@ -98,6 +98,8 @@ _SIGNATURES = {
     "crl_set_launch_overlap": (c_int32, [c_int32]),
     "crl_set_autotune": (c_int32, [c_int32]),
     "crl_set_gemm_kernel": (c_int32, [c_int32]),
+    "crl_gemm_tuning_report": (c_int32, [c_void_p, ctypes.c_char_p, c_size_t, POINTER(c_size_t)]),
+    "crl_sweep_gemm_tuning_report": (c_int32, [c_void_p, ctypes.c_char_p, c_size_t, POINTER(c_size_t)]),
     "crl_sweep_create": (c_int32, [POINTER(CrlConfig), c_int32, c_int32, POINTER(c_void_p)]),
     "crl_sweep_destroy": (c_int32, [c_void_p]),
     "crl_sweep_agent": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
@@ -185,6 +187,18 @@ def set_gemm_kernel(mode):
     ("any", "one_tile", "persistent" or "cta_pair").  Returns the previous mode's name."""
     prev = lib().crl_set_gemm_kernel(GEMM_KERNEL[mode])
     return {v: k for k, v in GEMM_KERNEL.items()}[prev]
+
+
+def gemm_tuning_report(handle, sweep=False):
+    """What the tile autotuner measured for a context (or, sweep=True, a sweep)
+    handle: a list of dicts, one per tuned grouped-GEMM problem list."""
+    import json
+    fn = lib().crl_sweep_gemm_tuning_report if sweep else lib().crl_gemm_tuning_report
+    need = c_size_t()
+    check(fn(handle, None, 0, byref(need)), None if sweep else handle)
+    buf = ctypes.create_string_buffer(need.value)
+    check(fn(handle, buf, need.value, byref(need)), None if sweep else handle)
+    return json.loads(buf.value.decode())
 
 
 def stream_handle(stream=None):

@@ -35,8 +35,29 @@ __global__ void __launch_bounds__(256) head_forward_kernel(const __grid_constant
 // finish (ticket) adds the partials in block order, so the result does not
 // depend on which block finishes last.  dz != null: dphi is written as BF16
 // [B][ldz] (the phi network's output gradient) instead of T.
+// Lane j owns the columns j, j + 32, ... of its row and sums them in that
+// order; rows up to kDiagRegCols columns stay in registers between the sums
+// and the gradient (one read of each row), wider rows are read twice.
+constexpr int kDiagRegCols = 256;
+
+template <typename T>
+__device__ __forceinline__ T diag_grad(int energy, T a, T b, T sxy, T nx, T ny, T dist) {
+  const T d = a - b;
+  switch (energy) {
+    case CRL_ENERGY_DOT: return b;
+    case CRL_ENERGY_COS: {
+      const T xh = a / nx, yh = b / ny;
+      return (yh - xh * (sxy / (nx * ny))) / nx;
+    }
+    case CRL_ENERGY_L2: return (dist >= T(1e-12)) ? -d / dist : T(0);
+    case CRL_ENERGY_L2SQ: return T(-2) * d;
+    default: return (d > T(0)) ? T(-1) : ((d < T(0)) ? T(1) : T(0));
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p, int lb, int nb) {
+  constexpr int kReg = kDiagRegCols / kWarp;
   __shared__ T s_a[8], s_l[8];
   __shared__ int s_last;
   const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
@@ -46,14 +67,37 @@ __device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p,
   if (i < B) {
     const T* x = p.phi + (size_t)i * R;
     const T* y = p.psi + (size_t)i * R;
+    const bool in_regs = R <= kDiagRegCols;
+    T xr[kReg], yr[kReg];
+    if (in_regs) {
+#pragma unroll
+      for (int u = 0; u < kReg; ++u) {
+        const int c = lane + kWarp * u;
+        xr[u] = c < R ? x[c] : T(0);
+        yr[u] = c < R ? y[c] : T(0);
+      }
+    }
     T sxy = 0, sxx = 0, syy = 0, sdd = 0, sad = 0;
-    for (int c = lane; c < R; c += kWarp) {
-      const T a = x[c], b = y[c], d = a - b;
-      sxy += a * b;
-      sxx += a * a;
-      syy += b * b;
-      sdd += d * d;
-      sad += fabs(d);
+    if (in_regs) {
+#pragma unroll
+      for (int u = 0; u < kReg; ++u) {
+        if (lane + kWarp * u >= R) break;
+        const T a = xr[u], b = yr[u], d = a - b;
+        sxy += a * b;
+        sxx += a * a;
+        syy += b * b;
+        sdd += d * d;
+        sad += fabs(d);
+      }
+    } else {
+      for (int c = lane; c < R; c += kWarp) {
+        const T a = x[c], b = y[c], d = a - b;
+        sxy += a * b;
+        sxx += a * a;
+        syy += b * b;
+        sdd += d * d;
+        sad += fabs(d);
+      }
     }
     sxy = warp_sum(sxy);
     sxx = warp_sum(sxx);
@@ -76,23 +120,22 @@ __device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p,
     const double alpha = p.tune.state ? exp(p.tune.state[0]) : p.alpha;
     term = T(alpha) * lpi - f;
     const T nx = dev_sqrt(sxx), ny = dev_sqrt(syy), dist = dev_sqrt(sdd);
-    for (int c = lane; c < R; c += kWarp) {
-      const T a = x[c], b = y[c], d = a - b;
-      T g;
-      switch (p.energy) {
-        case CRL_ENERGY_DOT: g = b; break;
-        case CRL_ENERGY_COS: {
-          const T xh = a / nx, yh = b / ny;
-          g = (yh - xh * (sxy / (nx * ny))) / nx;
-          break;
-        }
-        case CRL_ENERGY_L2: g = (dist >= T(1e-12)) ? -d / dist : T(0); break;
-        case CRL_ENERGY_L2SQ: g = T(-2) * d; break;
-        default: g = (d > T(0)) ? T(-1) : ((d < T(0)) ? T(1) : T(0)); break;
+    const T scale = ib * it;
+    if (in_regs) {
+#pragma unroll
+      for (int u = 0; u < kReg; ++u) {
+        const int c = lane + kWarp * u;
+        if (c >= R) break;
+        const T dv = scale * diag_grad<T>(p.energy, xr[u], yr[u], sxy, nx, ny, dist);
+        if (p.dz) p.dz[(size_t)i * p.ldz + c] = __float2bfloat16_rn((float)dv);
+        else p.dphi[(size_t)i * R + c] = dv;
       }
-      const T dv = ib * it * g;
-      if (p.dz) p.dz[(size_t)i * p.ldz + c] = __float2bfloat16_rn((float)dv);
-      else p.dphi[(size_t)i * R + c] = dv;
+    } else {
+      for (int c = lane; c < R; c += kWarp) {
+        const T dv = scale * diag_grad<T>(p.energy, x[c], y[c], sxy, nx, ny, dist);
+        if (p.dz) p.dz[(size_t)i * p.ldz + c] = __float2bfloat16_rn((float)dv);
+        else p.dphi[(size_t)i * R + c] = dv;
+      }
     }
   }
   if (lane == 0) {
@@ -115,10 +158,27 @@ __device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p,
   if (!s_last) return;
   __threadfence();
   __shared__ T sm[32];
+  // thread t adds the partials t, t + blockDim.x, ... in that order; the loads of
+  // a group of four are issued before their additions
   T a = 0, l = 0;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-    a += *((volatile T*)p.partial + 2 * k);
-    l += *((volatile T*)p.partial + 2 * k + 1);
+  const int nt = blockDim.x;
+  int k = threadIdx.x;
+  for (; k + 3 * nt < nb; k += 4 * nt) {
+    T pa[4], pl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pa[u] = __ldcg(p.partial + 2 * (k + u * nt));
+      pl[u] = __ldcg(p.partial + 2 * (k + u * nt) + 1);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a += pa[u];
+      l += pl[u];
+    }
+  }
+  for (; k < nb; k += nt) {
+    a += __ldcg(p.partial + 2 * k);
+    l += __ldcg(p.partial + 2 * k + 1);
   }
   a = block_sum(a, sm);
   l = block_sum(l, sm);
@@ -155,45 +215,39 @@ __global__ void __launch_bounds__(256) diag_energy_loss_kernel(const __grid_cons
   diag_energy_loss_body(p, blockIdx.x, gridDim.x);
 }
 
-// dz != null: the gradient is written as BF16 dz [B][ldz]
-// (the policy network's output gradient) instead of dout.
+// One thread per element (b, d) of the B x A action gradient, consecutive
+// threads along d then b (coalesced row segments).  dz != null: the gradient
+// is written as BF16 dz [B][ldz] (the policy network's output gradient)
+// instead of dout.
+constexpr int kHeadBwdThreads = 256;
 template <typename T>
 __device__ __forceinline__ void head_backward_body(const HeadBwdArgs<T>& p, int lb) {
   const int B = p.B, A = p.A;
-  const double alpha = p.alpha;
-  const T* __restrict__ out = p.out;
-  const T* __restrict__ eps_used = p.eps_used;
-  const T* __restrict__ da = p.da;
-  T* __restrict__ dout = p.dout;
-  __nv_bfloat16* __restrict__ dz = p.dz;
-  const int ldz = p.ldz;
-  const int b = lb * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  const T ab = T((p.alpha_used ? *p.alpha_used : alpha) / B);
-  for (int d = 0; d < A; ++d) {
-    const T mu = out[(size_t)b * 2 * A + d];
-    const T lraw = out[(size_t)b * 2 * A + A + d];
-    const T l = fmin(fmax(lraw, T(kLogStdMin)), T(kLogStdMax));
-    const T sigma = dev_exp(l);
-    const T e = eps_used[(size_t)b * A + d];
-    const T a = dev_tanh(mu + sigma * e);
-    const T du = da[(size_t)b * A + d] * (T(1) - a * a) + ab * T(2) * a;
-    const T dl = du * sigma * e - ab;
-    const bool inside = lraw > T(kLogStdMin) && lraw < T(kLogStdMax);
-    const T dlv = inside ? dl : T(0);
-    if (dz) {
-      const __nv_bfloat16 hu = __float2bfloat16_rn((float)du), hl = __float2bfloat16_rn((float)dlv);
-      dz[(size_t)b * ldz + d] = hu;
-      dz[(size_t)b * ldz + A + d] = hl;
-    } else {
-      dout[(size_t)b * 2 * A + d] = du;
-      dout[(size_t)b * 2 * A + A + d] = dlv;
-    }
+  const int idx = lb * kHeadBwdThreads + (int)threadIdx.x;
+  if (idx >= B * A) return;
+  const int b = idx / A, d = idx - b * A;
+  const T ab = T((p.alpha_used ? *p.alpha_used : p.alpha) / B);
+  const T mu = p.out[(size_t)b * 2 * A + d];
+  const T lraw = p.out[(size_t)b * 2 * A + A + d];
+  const T l = fmin(fmax(lraw, T(kLogStdMin)), T(kLogStdMax));
+  const T sigma = dev_exp(l);
+  const T e = p.eps_used[(size_t)b * A + d];
+  const T a = dev_tanh(mu + sigma * e);
+  const T du = p.da[(size_t)b * A + d] * (T(1) - a * a) + ab * T(2) * a;
+  const T dl = du * sigma * e - ab;
+  const bool inside = lraw > T(kLogStdMin) && lraw < T(kLogStdMax);
+  const T dlv = inside ? dl : T(0);
+  if (p.dz) {
+    p.dz[(size_t)b * p.ldz + d] = __float2bfloat16_rn((float)du);
+    p.dz[(size_t)b * p.ldz + A + d] = __float2bfloat16_rn((float)dlv);
+  } else {
+    p.dout[(size_t)b * 2 * A + d] = du;
+    p.dout[(size_t)b * 2 * A + A + d] = dlv;
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) head_backward_kernel(const __grid_constant__ HeadBwdArgs<T> p) {
+__global__ void __launch_bounds__(kHeadBwdThreads) head_backward_kernel(const __grid_constant__ HeadBwdArgs<T> p) {
   pdl_enter();
   head_backward_body(p, blockIdx.x);
 }
@@ -206,7 +260,7 @@ __global__ void __launch_bounds__(256) diag_energy_loss_multi_kernel(const Actor
   const int s = segment_of(begin, n, blockIdx.x, lb, nb);
   diag_energy_loss_body(tasks[s], lb, nb);
 }
-__global__ void __launch_bounds__(256) head_backward_multi_kernel(const HeadBwdArgs<float>* __restrict__ tasks,
+__global__ void __launch_bounds__(kHeadBwdThreads) head_backward_multi_kernel(const HeadBwdArgs<float>* __restrict__ tasks,
                                                                  const int* __restrict__ begin, int n) {
   pdl_enter();
   int lb, nb;
@@ -214,12 +268,17 @@ __global__ void __launch_bounds__(256) head_backward_multi_kernel(const HeadBwdA
   head_backward_body(tasks[s], lb);
 }
 
-// Device tables of `tasks` and their block offsets (rows_per_block rows per block).
-template <class Task>
-const char* multi_tables(BlobCache& cache, const std::vector<Task>& tasks, int rows_per_block, cudaStream_t st,
+// Device tables of `tasks` and their block offsets (items_per_block items per
+// block; a task has its batch B items, or B x A with PerAction).
+template <bool PerAction = false, class Task>
+const char* multi_tables(BlobCache& cache, const std::vector<Task>& tasks, int items_per_block, cudaStream_t st,
                          const Task** dt, const int** db, int* blocks) {
   std::vector<int> begin(tasks.size() + 1, 0);
-  for (size_t i = 0; i < tasks.size(); ++i) begin[i + 1] = begin[i] + ceil_div(tasks[i].B, rows_per_block);
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    int items = tasks[i].B;
+    if constexpr (PerAction) items *= tasks[i].A;
+    begin[i + 1] = begin[i] + ceil_div(items, items_per_block);
+  }
   *blocks = begin.back();
   const char* err = nullptr;
   if (!(*dt = cache.get(tasks, st, &err))) return err;
@@ -258,11 +317,11 @@ const char* actor_head_backward_multi(BlobCache& cache, const std::vector<HeadBw
   const HeadBwdArgs<float>* dt;
   const int* db;
   int blocks;
-  if (const char* err = multi_tables(cache, tasks, 256, st, &dt, &db, &blocks)) return err;
+  if (const char* err = multi_tables<true>(cache, tasks, kHeadBwdThreads, st, &dt, &db, &blocks)) return err;
   double bytes = 0.0;
   for (const auto& t : tasks) bytes += (double)t.B * t.A * 4.0 * 6;
   TraceLaunch tr(CRL_TRACE_AUX, st, bytes);
-  launch_k(head_backward_multi_kernel, dim3(blocks), dim3(256), 0, st, dt, db, (int)tasks.size());
+  launch_k(head_backward_multi_kernel, dim3(blocks), dim3(kHeadBwdThreads), 0, st, dt, db, (int)tasks.size());
   return nullptr;
 }
 
@@ -286,7 +345,7 @@ void actor_head_backward(const ActorSpec& as, const T* pi_out, const T* eps_used
   TraceLaunch tr(CRL_TRACE_AUX, st, (double)B * as.A * sizeof(T) * 6);
   const HeadBwdArgs<T> p{B, as.A, as.alpha, pi_out, eps_used, da, dout, dz, ldz,
                          as.tune.state ? as.tune.state + 3 : nullptr};
-  launch_k(head_backward_kernel<T>, dim3(ceil_div(B, 256)), dim3(256), 0, st, p);
+  launch_k(head_backward_kernel<T>, dim3(ceil_div(B * as.A, kHeadBwdThreads)), dim3(kHeadBwdThreads), 0, st, p);
 }
 
 #define CRL_INST_ACTOR(T)                                                                                        \

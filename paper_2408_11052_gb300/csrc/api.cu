@@ -984,6 +984,18 @@ int32_t crl_set_gemm_kernel(int32_t mode) {
   return prev;
 }
 
+int32_t crl_gemm_tuning_report(crl_ctx* ctx, char* buf, size_t len, size_t* needed) {
+  return guarded(ctx, [&] {
+    CRL_REQUIRE(ctx && needed, CRL_E_INVALID_ARG, "null argument");
+    const std::string js = gemm_tuning_json(ctx->groups);
+    *needed = js.size() + 1;
+    CRL_REQUIRE(buf != nullptr || len == 0, CRL_E_INVALID_ARG, "null buffer with a nonzero length");
+    if (len == 0) return;
+    CRL_REQUIRE(len >= js.size() + 1, CRL_E_SHAPE, "the report needs " + std::to_string(js.size() + 1) + " bytes");
+    memcpy(buf, js.c_str(), js.size() + 1);
+  });
+}
+
 int crl_trace_start(crl_ctx* ctx, int32_t kernel_class, int32_t max_launches) {
   return guarded(ctx, [&] {
     CRL_REQUIRE(ctx, CRL_E_INVALID_ARG, "null context");

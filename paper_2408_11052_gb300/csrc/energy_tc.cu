@@ -295,16 +295,32 @@ __device__ void merge_tile(const FwdArgs& a, int T, int npart, bool col) {
   }
 }
 
-// The loss parts from the 2 n tile partials, added in tile order.  One thread.
+// The loss parts from the 2 n tile partials, added in tile order.  The block
+// stages the partials in shared memory kFinTiles tiles at a time (all loads in
+// flight together) and thread 0 adds them in tile order.
+constexpr int kFinTiles = 256;
 __device__ void finalize_loss(const FwdArgs& a, int n) {
+  __shared__ float s_tp[kFinTiles][5];
   float af = 0.f, ar2 = 0.f, ab = 0.f, ac2 = 0.f, ao = 0.f;
-  for (int T = 0; T < n; ++T) {
-    af += __ldcg(a.tile_part + 3 * T);
-    ar2 += __ldcg(a.tile_part + 3 * T + 1);
-    ao += __ldcg(a.tile_part + 3 * T + 2);
-    ab += __ldcg(a.tile_part + 3 * (n + T));
-    ac2 += __ldcg(a.tile_part + 3 * (n + T) + 1);
+  for (int T0 = 0; T0 < n; T0 += kFinTiles) {
+    const int cnt = min(kFinTiles, n - T0);
+    for (int q = threadIdx.x; q < 5 * cnt; q += blockDim.x) {
+      const int T = T0 + q / 5, r = q % 5;
+      const float* src = r < 3 ? a.tile_part + 3 * T + r : a.tile_part + 3 * (n + T) + (r - 3);
+      s_tp[q / 5][r] = __ldcg(src);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int u = 0; u < cnt; ++u) {
+        af += s_tp[u][0];
+        ar2 += s_tp[u][1];
+        ao += s_tp[u][2];
+        ab += s_tp[u][3];
+        ac2 += s_tp[u][4];
+      }
+    __syncthreads();
   }
+  if (threadIdx.x != 0) return;
   const float inv = 1.f / a.B;
   const float lf = af * inv, lb = ab * inv;
   const float pen = a.beta * (a.w.pr * ar2 * inv + a.w.pc * ac2 * inv);
@@ -331,10 +347,10 @@ __device__ __forceinline__ void fwd_finalize_body(const FwdArgs& a, int lb) {
   __syncthreads();
   if (threadIdx.x == 0) s_fin = (atomicAdd(a.tickets + 2 * n, 1u) == (unsigned)(2 * n) - 1u) ? 1 : 0;
   __syncthreads();
-  if (s_fin && threadIdx.x == 0) {
+  if (s_fin) {   // block-uniform
     __threadfence();
     finalize_loss(a, n);
-    a.tickets[2 * n] = 0u;
+    if (threadIdx.x == 0) a.tickets[2 * n] = 0u;
   }
 }
 

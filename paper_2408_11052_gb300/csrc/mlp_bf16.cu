@@ -7,10 +7,12 @@
 // ReLU, W stored [out][in].
 #include <cuda_bf16.h>
 
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "actor_head.cuh"
@@ -618,39 +620,59 @@ int heuristic_cfg(const std::vector<tc::GemmProblem>& probs, int min_bn) {
 // Autotuner: time each candidate configuration (tile width, ring depth) on
 // the launch itself (every GEMM epilogue writes a pure function of inputs the
 // launch does not modify, so repeating it is harmless, and neither choice
-// changes any output value), keep the fastest.  Runs once per distinct problem
-// list, outside graph capture; returns 0 when it cannot measure (the caller
-// falls back to the fixed rule).
-int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, unsigned* status, cudaStream_t st) {
+// changes any output value), keep the fastest.  The candidates are timed in
+// two rounds (one warm-up and three timed launches each), and each keeps its
+// faster round, so that a clock ramp or a transient at the start of the first
+// round does not decide the pick.  Runs once per distinct problem list,
+// outside graph capture; returns 0 when it cannot measure (the caller falls
+// back to the fixed rule).
+int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, unsigned* status, cudaStream_t st,
+             double flops) {
+  constexpr int kRounds = 2, kReps = 3;
+  GemmGroups::TuneRecord rec = {};
+  for (int cfg : kGemmCfgs) {
+    if (cfg_bn(cfg) < min_bn || !cfg_allowed(cfg)) continue;
+    rec.cand[rec.ncand] = cfg;
+    rec.us[rec.ncand] = -1.f;
+    ++rec.ncand;
+  }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return 0;
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     return 0;
   }
-  int best = 0;
-  float best_ms = 0.f;
-  for (int cfg : kGemmCfgs) {
-    if (cfg_bn(cfg) < min_bn) continue;
-    if (!cfg_allowed(cfg)) continue;
-    int tiles = 0;
-    const char* err = nullptr;
-    const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 0, cfg_bm(cfg));
-    if (!t || tiles == 0) continue;
-    launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);  // warm-up
-    cudaEventRecord(e0, st);
-    for (int r = 0; r < 3; ++r) launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);
-    cudaEventRecord(e1, st);
-    float ms = 0.f;
-    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
-    if (best == 0 || ms < best_ms) {
-      best = cfg;
-      best_ms = ms;
+  for (int round = 0; round < kRounds; ++round) {
+    for (int c = 0; c < rec.ncand; ++c) {
+      const int cfg = rec.cand[c];
+      int tiles = 0;
+      const char* err = nullptr;
+      const tc::GemmProblem* t = gg.table(probs, cfg_bn(cfg), &tiles, st, &err, cfg_kernel(cfg) == 0, cfg_bm(cfg));
+      if (!t || tiles == 0) continue;
+      launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);  // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < kReps; ++r) launch_cfg(cfg, t, (int)probs.size(), tiles, status, st);
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+      const float us = 1000.f * ms / kReps;
+      if (rec.us[c] < 0.f || us < rec.us[c]) rec.us[c] = us;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return best;
+  int best = -1;
+  for (int c = 0; c < rec.ncand; ++c)
+    if (rec.us[c] >= 0.f && (best < 0 || rec.us[c] < rec.us[best])) best = c;
+  if (best < 0) return 0;
+  rec.cfg = rec.cand[best];
+  rec.nprob = (int)probs.size();
+  rec.M0 = probs[0].M;
+  rec.N0 = probs[0].N;
+  rec.K0 = probs[0].K;
+  rec.flops = flops;
+  gg.add_record(rec);
+  return rec.cfg;
 }
 
 // One grouped launch of `probs` with the tuned (or heuristic) tile width.
@@ -671,7 +693,7 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
     if (tune && !capturing && g_tracer == nullptr) {
-      cfg = tune_cfg(gg, probs, min_bn, status, st);
+      cfg = tune_cfg(gg, probs, min_bn, status, st, flops);
       if (cfg) gg.set_tuned_bn(key, cfg);
     }
     if (cfg == 0) cfg = heuristic_cfg(probs, min_bn);
@@ -687,6 +709,29 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
 }
 
 }  // namespace
+
+std::string gemm_tuning_json(const GemmGroups& gg) {
+  auto name = [](int cfg) {
+    static const char* const kinds[] = {"one_tile", "persistent", "cta_pair"};
+    char b[64];
+    snprintf(b, sizeof(b), "%s %dx%d s%d", kinds[cfg_kernel(cfg)], cfg_bm(cfg), cfg_bn(cfg), cfg % 16);
+    return std::string(b);
+  };
+  std::string js = "[";
+  char b[256];
+  for (size_t i = 0; i < gg.records().size(); ++i) {
+    const GemmGroups::TuneRecord& r = gg.records()[i];
+    snprintf(b, sizeof(b), "%s{\"problems\": %d, \"first_mnk\": [%d, %d, %d], \"gflop\": %.4f, \"picked\": \"%s\", \"us\": {",
+             i ? ", " : "", r.nprob, r.M0, r.N0, r.K0, r.flops * 1e-9, name(r.cfg).c_str());
+    js += b;
+    for (int c = 0; c < r.ncand; ++c) {
+      snprintf(b, sizeof(b), "%s\"%s\": %.2f", c ? ", " : "", name(r.cand[c]).c_str(), r.us[c]);
+      js += b;
+    }
+    js += "}}";
+  }
+  return js + "]";
+}
 
 const tc::GemmProblem* GemmGroups::table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles,
                                          cudaStream_t st, const char** err, bool allow_split, int BM) {
@@ -751,6 +796,7 @@ void GemmGroups::reset() {
   chunks_.clear();
   map_.clear();
   tuned_.clear();
+  records_.clear();
   cur_ = nullptr;
   used_ = cap_ = 0;
 }

@@ -41,6 +41,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -128,6 +129,18 @@ class GemmGroups {
     return it == tuned_.end() ? 0 : it->second;
   }
   void set_tuned_bn(uint64_t key, int cfg) { tuned_[key] = cfg; }
+  // What the autotuner measured for one problem list (crl_gemm_tuning_report).
+  struct TuneRecord {
+    int nprob;
+    int M0, N0, K0;          // the list's first problem
+    double flops;            // algorithmic work of one launch
+    int cfg;                 // the configuration kept
+    int ncand;
+    int cand[16];            // candidate configurations, in the order timed
+    float us[16];            // their best time per launch over the timing rounds
+  };
+  void add_record(const TuneRecord& r) { records_.push_back(r); }
+  const std::vector<TuneRecord>& records() const { return records_; }
   // Number of distinct problem lists with a device table.
   size_t entries() const { return map_.size(); }
   // false: never time candidates (fixed rule), for problem lists that change
@@ -136,6 +149,7 @@ class GemmGroups {
 
  private:
   std::unordered_map<uint64_t, int> tuned_;
+  std::vector<TuneRecord> records_;
   struct Entry {
     const tc::GemmProblem* dev;
     int tiles;
@@ -194,6 +208,9 @@ const char* bf_forward(GemmGroups& gg, const BfPass* nets, int count, unsigned* 
 // input-gradient launch per hidden layer, then one launch with every weight
 // gradient and first-layer input gradient.
 const char* bf_backward(GemmGroups& gg, const BfPass* nets, int count, unsigned* status, cudaStream_t st);
+// The autotuner's measurements of every problem list tuned in `gg`, as a JSON
+// array (crl_gemm_tuning_report).
+std::string gemm_tuning_json(const GemmGroups& gg);
 
 // Adam on the FP32 master parameters of several networks in one launch, also
 // refreshing each network's BF16 shadows (W_hi / W_lo and Wt) from the updated

@@ -485,6 +485,18 @@ int crl_sweep_sync_status(crl_sweep* sw, void* stream, uint32_t* status) {
   });
 }
 
+int32_t crl_sweep_gemm_tuning_report(crl_sweep* sw, char* buf, size_t len, size_t* needed) {
+  return sweep_guarded(sw, [&] {
+    CRL_REQUIRE(sw && needed, CRL_E_INVALID_ARG, "null argument");
+    const std::string js = gemm_tuning_json(sw->groups);
+    *needed = js.size() + 1;
+    CRL_REQUIRE(buf != nullptr || len == 0, CRL_E_INVALID_ARG, "null buffer with a nonzero length");
+    if (len == 0) return;
+    CRL_REQUIRE(len >= js.size() + 1, CRL_E_SHAPE, "the report needs " + std::to_string(js.size() + 1) + " bytes");
+    memcpy(buf, js.c_str(), js.size() + 1);
+  });
+}
+
 const char* crl_sweep_last_error(const crl_sweep* sw) { return sw ? sw->err.c_str() : crl_last_error(nullptr); }
 
 }  // extern "C"

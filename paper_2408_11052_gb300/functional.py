@@ -84,7 +84,8 @@ class InfoNCELoss(torch.autograd.Function):
     parts = {total, InfoNCE-fwd, InfoNCE-bwd, penalty} (not differentiable).
     The backward takes the incoming gradient of ``total`` as a host scalar.
     path "fused": float32 representations on the BF16 fused kernels (B a
-    multiple of 8, repr 64 / 128 / 192 / 256, any energy but L1).
+    multiple of 8, repr 64 / 128 / 192 / 256; the L1 energy runs on FP32 SIMT
+    tiles, the others on the tensor cores).
     """
 
     @staticmethod
