@@ -442,9 +442,12 @@ int32_t crl_set_launch_overlap(int32_t enable);
  * epilogue) times the tile widths 64, 128 and 256 on the launch itself
  * (repeating it is harmless: its outputs are a pure function of inputs it
  * does not modify) and keeps the fastest for that context or sweep; outputs
- * do not depend on the tile width.  enable = 0: a fixed rule (128-wide tiles
- * when they fill the GPU, else 64).  Never tunes during graph capture or
- * tracing.  Returns the previous setting. */
+ * do not depend on the pick.  (The weight gradients of batches of 4096 and
+ * more split the batch over several CTAs; the split follows from the
+ * problem's shape alone, and such a launch is tuned over the one-tile kernel
+ * only, the one that splits.)  enable = 0: a fixed rule (128-wide tiles when
+ * they fill the GPU, else 64).  Never tunes during graph capture or tracing.
+ * Returns the previous setting. */
 int32_t crl_set_autotune(int32_t enable);
 
 /* Which tensor-core GEMM kernels the grouped launches may use (process-wide;
@@ -454,7 +457,10 @@ int32_t crl_set_autotune(int32_t enable);
  * main loop through a double-buffered TMEM accumulator), CRL_GEMM_CTA_PAIR
  * (the persistent schedule over 256-row tiles, each computed by a cluster of
  * two CTAs with tcgen05.mma.cta_group::2; every CTA loads its own half of the
- * operands, no multicast).  All kernels give identical outputs.  Without
+ * operands, no multicast).  All kernels give identical outputs, except the
+ * weight gradients of batches of 4096 and more, which only the one-tile kernel
+ * splits over the batch (the other two sum them unsplit: the same values up
+ * to FP32 rounding).  Without
  * autotuning the fixed rule picks the tile width and this setting the kernel
  * (ANY: one tile per CTA).  Returns the previous setting, or
  * CRL_E_INVALID_ARG for an unknown mode. */

@@ -26,6 +26,8 @@ namespace crl {
 
 using bf16 = __nv_bfloat16;
 
+int list_split(const std::vector<tc::GemmProblem>& probs);
+
 namespace {
 
 constexpr float kLnEpsF = 1e-6f;
@@ -626,12 +628,12 @@ int heuristic_cfg(const std::vector<tc::GemmProblem>& probs, int min_bn) {
 // round does not decide the pick.  Runs once per distinct problem list,
 // outside graph capture; returns 0 when it cannot measure (the caller falls
 // back to the fixed rule).
-int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, unsigned* status, cudaStream_t st,
-             double flops) {
+int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, bool one_tile_only, unsigned* status,
+             cudaStream_t st, double flops) {
   constexpr int kRounds = 2, kReps = 3;
   GemmGroups::TuneRecord rec = {};
   for (int cfg : kGemmCfgs) {
-    if (cfg_bn(cfg) < min_bn || !cfg_allowed(cfg)) continue;
+    if (cfg_bn(cfg) < min_bn || !cfg_allowed(cfg) || (one_tile_only && cfg_kernel(cfg) != 0)) continue;
     rec.cand[rec.ncand] = cfg;
     rec.us[rec.ncand] = -1.f;
     ++rec.ncand;
@@ -686,6 +688,10 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
   for (const auto& p : probs)
     if (p.epi.kind == tc::kEpiFwdOutEnergy) min_bn = std::max(min_bn, p.N);
   if (min_bn > 256) return "an energy-operand output layer wider than 256 columns";
+  // a list that splits over K stays on the one-tile kernel whatever the timings
+  // say, so its outputs never depend on the pick (all one-tile widths give the
+  // same bits; the other kernels do not split)
+  const bool one_tile_only = list_split(probs) > 1;
   const bool tune = g_autotune && gg.allow_tune;
   int cfg = tune ? gg.tuned_bn(key) : 0;
   if (cfg != 0 && !cfg_allowed(cfg)) cfg = 0;   // tuned under another kernel setting
@@ -693,7 +699,7 @@ const char* launch_group(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, do
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
     if (tune && !capturing && g_tracer == nullptr) {
-      cfg = tune_cfg(gg, probs, min_bn, status, st, flops);
+      cfg = tune_cfg(gg, probs, min_bn, one_tile_only, status, st, flops);
       if (cfg) gg.set_tuned_bn(key, cfg);
     }
     if (cfg == 0) cfg = heuristic_cfg(probs, min_bn);
@@ -733,19 +739,28 @@ std::string gemm_tuning_json(const GemmGroups& gg) {
   return js + "]";
 }
 
+// Split-K factor of a problem list: the problems that allow it (ksplit_cap > 1)
+// take one split, chosen from the list's shape alone -- about two CTAs per SM
+// counted in 128 x 128 tiles -- so that it does not depend on the tile
+// configuration a launch runs with (the one-tile kernel splits; the others do
+// not, so a list that splits runs on the one-tile kernel only).
+int list_split(const std::vector<tc::GemmProblem>& probs) {
+  int mn = 0, cap = 0;
+  for (const auto& p : probs) {
+    mn += ceil_div(p.M, tc::kBM) * ceil_div(p.N, 128);
+    if (p.ksplit_cap > 1) cap = cap == 0 ? p.ksplit_cap : std::min(cap, p.ksplit_cap);
+  }
+  int split = cap > 1 ? std::max(1, std::min(cap, (2 * sm_count()) / std::max(mn, 1))) : 1;
+  // no problem splits into parts of fewer than 8 K-slices
+  bool any = false;
+  for (const auto& p : probs)
+    if (p.ksplit_cap > 1 && std::min(split, ceil_div(p.K, tc::kBK) / 8) > 1) any = true;
+  return any ? split : 1;
+}
+
 const tc::GemmProblem* GemmGroups::table(std::vector<tc::GemmProblem>& probs, int BN, int* total_tiles,
                                          cudaStream_t st, const char** err, bool allow_split, int BM) {
-  // split-K: the problems that allow it take the same split, chosen so that the
-  // launch has about two CTAs per SM, with >= 8 K-slices per split
-  int split = 1;
-  if (allow_split && BN > 0) {
-    int mn = 0, cap = 0;
-    for (const auto& p : probs) {
-      mn += ceil_div(p.M, tc::kBM) * ceil_div(p.N, BN);
-      if (p.ksplit_cap > 1) cap = cap == 0 ? p.ksplit_cap : std::min(cap, p.ksplit_cap);
-    }
-    if (cap > 1) split = std::max(1, std::min(cap, (2 * sm_count()) / std::max(mn, 1)));
-  }
+  const int split = (allow_split && BN > 0) ? list_split(probs) : 1;
   int tiles = 0;
   for (auto& p : probs) {
     if (BN == 0) break;
