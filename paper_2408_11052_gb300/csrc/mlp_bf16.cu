@@ -741,13 +741,13 @@ std::string gemm_tuning_json(const GemmGroups& gg) {
 
 // Split-K factor of a problem list: the problems that allow it (ksplit_cap > 1)
 // take one split, chosen from the list's shape alone -- about two CTAs per SM
-// counted in 128 x 128 tiles -- so that it does not depend on the tile
+// counted in 128 x 64 tiles -- so that it does not depend on the tile
 // configuration a launch runs with (the one-tile kernel splits; the others do
 // not, so a list that splits runs on the one-tile kernel only).
 int list_split(const std::vector<tc::GemmProblem>& probs) {
   int mn = 0, cap = 0;
   for (const auto& p : probs) {
-    mn += ceil_div(p.M, tc::kBM) * ceil_div(p.N, 128);
+    mn += ceil_div(p.M, tc::kBM) * ceil_div(p.N, 64);
     if (p.ksplit_cap > 1) cap = cap == 0 ? p.ksplit_cap : std::min(cap, p.ksplit_cap);
   }
   int split = cap > 1 ? std::max(1, std::min(cap, (2 * sm_count()) / std::max(mn, 1))) : 1;
