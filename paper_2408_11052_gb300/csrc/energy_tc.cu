@@ -827,22 +827,39 @@ template <int EK, int OBJ, int LIVE, bool EDGE, int NC>
 __device__ __forceinline__ void build_h(const float (&sv)[NC], const HCoef& hc, const float* __restrict__ aux_o,
                                         const float* __restrict__ lse_o, float kb_oth, float k2_oth, int cb, int u,
                                         int v0, int B, float& rowsum, uint32_t (&packed)[NC / 2]) {
-  float cax[4], clse[4], ckoth[4];
+  // the per-column inputs of four columns at a time, the next group's loads
+  // issued before this group's arithmetic
+  float cax[4], clse[4], ckoth[4], nax[4], nlse[4];
+  auto load4 = [&](int k, float (&ax)[4], float (&ls)[4]) {
+    const int c4 = v0 + cb + k;
+    if (EDGE) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool in = c4 + e < B;
+        if (EK != 2) ax[e] = in ? __ldg(aux_o + c4 + e) : 0.f;
+        if (LIVE != 1) ls[e] = in ? __ldg(lse_o + c4 + e) : 0.f;
+      }
+    } else {
+      if (EK != 2) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(aux_o + c4));
+        ax[0] = t.x, ax[1] = t.y, ax[2] = t.z, ax[3] = t.w;
+      }
+      if (LIVE != 1) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(lse_o + c4));
+        ls[0] = t.x, ls[1] = t.y, ls[2] = t.z, ls[3] = t.w;
+      }
+    }
+  };
+  load4(0, nax, nlse);
 #pragma unroll
   for (int k = 0; k < NC; k += 2) {
     if ((k & 3) == 0) {
-      const int c4 = v0 + cb + k;
-      if (EDGE) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const bool in = c4 + e < B;
-          if (EK != 2) cax[e] = in ? __ldg(aux_o + c4 + e) : 0.f;
-          if (LIVE != 1) clse[e] = in ? __ldg(lse_o + c4 + e) : 0.f;
-        }
-      } else {
-        if (EK != 2) *reinterpret_cast<float4*>(cax) = __ldg(reinterpret_cast<const float4*>(aux_o + c4));
-        if (LIVE != 1) *reinterpret_cast<float4*>(clse) = __ldg(reinterpret_cast<const float4*>(lse_o + c4));
+      for (int e = 0; e < 4; ++e) {
+        cax[e] = nax[e];
+        clse[e] = nlse[e];
       }
+      if (k + 4 < NC) load4(k + 4, nax, nlse);
       if (LIVE != 1) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
