@@ -368,6 +368,18 @@ def roofline_of(arm, w, precision, path):
         # below the launch's duration, the launch is latency-bound, not tensor-bound
         roof["note"] = (f"{per_launch / 1e6:.1f} MFLOP per launch = {per_launch / (peak * 1e12) * 1e6:.2f} us at the "
                         f"peak against {1e3 * tr_ms / max(n_tr, 1):.1f} us measured")
+        tuned = arm.get("gemm_tuning")
+        if cls == "gemm" and tuned:
+            # the tensor work as launched (the forward layers multiply BF16 hi / lo
+            # pairs), each tuned group once per step, over the same traced time
+            alg = sum(g["gflop"] for g in tuned)
+            issued = sum(g.get("issued_gflop", g["gflop"]) for g in tuned)
+            if alg > 0:
+                rate = achieved * issued / alg
+                roof["issued"] = {"tflops": rate, "frac": rate / peak, "per_algorithmic": issued / alg,
+                                  "note": "tensor work as launched: the forward layers' BF16 hi / lo input and "
+                                          "weight products (two to four per algorithmic product), from the "
+                                          "autotuner report, over the same traced launches"}
     elif cls in ("gemm", "energy"):
         achieved = tr_work / (tr_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",

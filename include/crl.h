@@ -474,7 +474,9 @@ int32_t crl_set_gemm_kernel(int32_t mode);
  * counterpart).  Writes a NUL-terminated JSON array with one object per
  * grouped GEMM problem list the context (or sweep) has tuned so far, in tuning
  * order: "problems" (the list's length), "first_mnk" (M, N, K of its first
- * problem), "gflop" (one launch's algorithmic work), "picked" (the kept
+ * problem), "gflop" (one launch's algorithmic work), "issued_gflop" (its
+ * tensor work as launched: the forward layers multiply BF16 hi / lo pairs of
+ * the input and the weights, two to four products per algorithmic one), "picked" (the kept
  * configuration: kernel, tile rows x columns, ring depth) and "us" (each
  * candidate's faster time per launch over the two timing rounds, in
  * microseconds; -1 where it could not be timed).  *needed receives the bytes

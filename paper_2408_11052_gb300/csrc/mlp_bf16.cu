@@ -673,6 +673,8 @@ int tune_cfg(GemmGroups& gg, std::vector<tc::GemmProblem>& probs, int min_bn, bo
   rec.N0 = probs[0].N;
   rec.K0 = probs[0].K;
   rec.flops = flops;
+  rec.issued = 0.0;
+  for (const auto& p : probs) rec.issued += 2.0 * p.M * p.N * p.K;
   gg.add_record(rec);
   return rec.cfg;
 }
@@ -727,8 +729,10 @@ std::string gemm_tuning_json(const GemmGroups& gg) {
   char b[256];
   for (size_t i = 0; i < gg.records().size(); ++i) {
     const GemmGroups::TuneRecord& r = gg.records()[i];
-    snprintf(b, sizeof(b), "%s{\"problems\": %d, \"first_mnk\": [%d, %d, %d], \"gflop\": %.4f, \"picked\": \"%s\", \"us\": {",
-             i ? ", " : "", r.nprob, r.M0, r.N0, r.K0, r.flops * 1e-9, name(r.cfg).c_str());
+    snprintf(b, sizeof(b),
+             "%s{\"problems\": %d, \"first_mnk\": [%d, %d, %d], \"gflop\": %.4f, \"issued_gflop\": %.4f, "
+             "\"picked\": \"%s\", \"us\": {",
+             i ? ", " : "", r.nprob, r.M0, r.N0, r.K0, r.flops * 1e-9, r.issued * 1e-9, name(r.cfg).c_str());
     js += b;
     for (int c = 0; c < r.ncand; ++c) {
       snprintf(b, sizeof(b), "%s\"%s\": %.2f", c ? ", " : "", name(r.cand[c]).c_str(), r.us[c]);

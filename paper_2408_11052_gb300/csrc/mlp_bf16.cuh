@@ -134,6 +134,8 @@ class GemmGroups {
     int nprob;
     int M0, N0, K0;          // the list's first problem
     double flops;            // algorithmic work of one launch
+    double issued;           // tensor work as launched: sum of 2 M N K over the problems, K counting
+                             // every BF16 product (hi / lo input and weight pairs)
     int cfg;                 // the configuration kept
     int ncand;
     int cand[16];            // candidate configurations, in the order timed
