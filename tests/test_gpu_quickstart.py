@@ -55,7 +55,7 @@ def test_quick_start_autograd_critic_loss():
     total, parts = functional.infonce_loss(phi, psi, energy="l2", loss="fwd", path="fused")
     total.backward()
     torch.cuda.synchronize()
-    assert math.isfinite(total.item()) and parts[1].item() > 0.0
+    assert math.isfinite(total.detach().item()) and parts[1].item() > 0.0
     assert phi.grad.shape == phi.shape and psi.grad.shape == psi.shape
     assert torch.isfinite(phi.grad).all() and torch.isfinite(psi.grad).all()
     # the L2 energy depends on phi_i - psi_j only, so shifting every row of both
