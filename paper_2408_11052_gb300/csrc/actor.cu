@@ -29,16 +29,21 @@ __global__ void __launch_bounds__(256) head_forward_kernel(const __grid_constant
   head_forward_body(p, blockIdx.x);
 }
 
-// f_i = f(phi_i, psi_i) / tau and dphi_i = -(1/B) df_i/dphi_i, one warp per
-// row (8 rows per block), and the loss loss2 = {mean(alpha log pi - f),
-// mean log pi}: each block writes its partial sums, and the last block to
-// finish (ticket) adds the partials in block order, so the result does not
-// depend on which block finishes last.  dz != null: dphi is written as BF16
-// [B][ldz] (the phi network's output gradient) instead of T.
+// f_i = f(phi_i, psi_i) / tau and dphi_i = -(1/B) df_i/dphi_i, 8 rows per
+// block of 4 warps (warp w: rows w and w + 4 of the block, side by side), and
+// the loss loss2 = {mean(alpha log pi - f), mean log pi}: each block writes its
+// partial sums (its rows in order), and the last block to finish (ticket) adds
+// the partials in block order, so the result does not depend on which block
+// finishes last.  dz != null: dphi is written as BF16 [B][ldz] (the phi
+// network's output gradient) instead of T.
 // Lane j owns the columns j, j + 32, ... of its row and sums them in that
 // order; rows up to kDiagRegCols columns stay in registers between the sums
-// and the gradient (one read of each row), wider rows are read twice.
+// and the gradient (one read of each row, the loads of both of the warp's rows
+// in flight together), wider rows are read twice, one row after the other.
+// (Two rows per warp keep a block of 8 rows to 4 warps: every block of a
+// batch-8192 launch is resident at once.)
 constexpr int kDiagRegCols = 256;
+constexpr int kDiagThreads = 128;   // 4 warps, 2 rows each
 
 template <typename T>
 __device__ __forceinline__ T diag_grad(int energy, T a, T b, T sxy, T nx, T ny, T dist) {
@@ -55,41 +60,96 @@ __device__ __forceinline__ T diag_grad(int energy, T a, T b, T sxy, T nx, T ny, 
   }
 }
 
+// f_i, dphi_i and alpha log pi_i - f_i of row i from its five column sums.
+template <typename T>
+__device__ __forceinline__ T diag_finish(const ActorLossArgs<T>& p, int i, int lane, T sxy, T sxx, T syy, T sdd, T sad,
+                                         T& f, T& nx, T& ny, T& dist) {
+  sxy = warp_sum(sxy);
+  sxx = warp_sum(sxx);
+  syy = warp_sum(syy);
+  sdd = warp_sum(sdd);
+  sad = warp_sum(sad);
+  const T it = T(1.0 / p.tau);
+  switch (p.energy) {
+    case CRL_ENERGY_DOT: f = sxy; break;
+    case CRL_ENERGY_COS: f = sxy / (dev_sqrt(sxx) * dev_sqrt(syy)); break;
+    case CRL_ENERGY_L2: f = -dev_sqrt(sdd); break;
+    case CRL_ENERGY_L2SQ: f = -sdd; break;
+    default: f = -sad; break;
+  }
+  f *= it;
+  if (lane == 0) p.fdiag[i] = f;
+  nx = dev_sqrt(sxx);
+  ny = dev_sqrt(syy);
+  dist = dev_sqrt(sdd);
+  return sxy;
+}
+
+template <typename T>
+__device__ __forceinline__ void diag_store(const ActorLossArgs<T>& p, int i, int c, T dv) {
+  if (p.dz) p.dz[(size_t)i * p.ldz + c] = __float2bfloat16_rn((float)dv);
+  else p.dphi[(size_t)i * p.R + c] = dv;
+}
+
 template <typename T>
 __device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p, int lb, int nb) {
   constexpr int kReg = kDiagRegCols / kWarp;
   __shared__ T s_a[8], s_l[8];
   __shared__ int s_last;
   const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
-  const int i = lb * 8 + w;
   const int B = p.B, R = p.R;
-  T term = 0, lpi = 0;
-  if (i < B) {
-    const T* x = p.phi + (size_t)i * R;
-    const T* y = p.psi + (size_t)i * R;
-    const bool in_regs = R <= kDiagRegCols;
-    T xr[kReg], yr[kReg];
-    if (in_regs) {
+  const int rows[2] = {lb * 8 + w, lb * 8 + w + 4};
+  T term[2] = {T(0), T(0)}, lpi[2] = {T(0), T(0)};
+  // every block reads log alpha before its ticket; the last block updates it after all tickets
+  const double alpha = p.tune.state ? exp(p.tune.state[0]) : p.alpha;
+  const T scale = T(-1.0 / B) * T(1.0 / p.tau);
+  if (R <= kDiagRegCols) {
+    T xr[2][kReg], yr[2][kReg];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = rows[q];
+      const T* x = p.phi + (size_t)(i < B ? i : 0) * R;
+      const T* y = p.psi + (size_t)(i < B ? i : 0) * R;
 #pragma unroll
       for (int u = 0; u < kReg; ++u) {
         const int c = lane + kWarp * u;
-        xr[u] = c < R ? x[c] : T(0);
-        yr[u] = c < R ? y[c] : T(0);
+        xr[q][u] = (i < B && c < R) ? x[c] : T(0);
+        yr[q][u] = (i < B && c < R) ? y[c] : T(0);
       }
     }
-    T sxy = 0, sxx = 0, syy = 0, sdd = 0, sad = 0;
-    if (in_regs) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = rows[q];
+      if (i >= B) continue;   // warp-uniform
+      T sxy = 0, sxx = 0, syy = 0, sdd = 0, sad = 0;
 #pragma unroll
       for (int u = 0; u < kReg; ++u) {
         if (lane + kWarp * u >= R) break;
-        const T a = xr[u], b = yr[u], d = a - b;
+        const T a = xr[q][u], b = yr[q][u], d = a - b;
         sxy += a * b;
         sxx += a * a;
         syy += b * b;
         sdd += d * d;
         sad += fabs(d);
       }
-    } else {
+      T f, nx, ny, dist;
+      sxy = diag_finish(p, i, lane, sxy, sxx, syy, sdd, sad, f, nx, ny, dist);
+      lpi[q] = p.logpi[i];
+      term[q] = T(alpha) * lpi[q] - f;
+#pragma unroll
+      for (int u = 0; u < kReg; ++u) {
+        const int c = lane + kWarp * u;
+        if (c >= R) break;
+        diag_store(p, i, c, scale * diag_grad<T>(p.energy, xr[q][u], yr[q][u], sxy, nx, ny, dist));
+      }
+    }
+  } else {
+    for (int q = 0; q < 2; ++q) {
+      const int i = rows[q];
+      if (i >= B) continue;   // warp-uniform
+      const T* x = p.phi + (size_t)i * R;
+      const T* y = p.psi + (size_t)i * R;
+      T sxy = 0, sxx = 0, syy = 0, sdd = 0, sad = 0;
       for (int c = lane; c < R; c += kWarp) {
         const T a = x[c], b = y[c], d = a - b;
         sxy += a * b;
@@ -98,49 +158,19 @@ __device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p,
         sdd += d * d;
         sad += fabs(d);
       }
-    }
-    sxy = warp_sum(sxy);
-    sxx = warp_sum(sxx);
-    syy = warp_sum(syy);
-    sdd = warp_sum(sdd);
-    sad = warp_sum(sad);
-    const T it = T(1.0 / p.tau), ib = T(-1.0 / B);
-    T f;
-    switch (p.energy) {
-      case CRL_ENERGY_DOT: f = sxy; break;
-      case CRL_ENERGY_COS: f = sxy / (dev_sqrt(sxx) * dev_sqrt(syy)); break;
-      case CRL_ENERGY_L2: f = -dev_sqrt(sdd); break;
-      case CRL_ENERGY_L2SQ: f = -sdd; break;
-      default: f = -sad; break;
-    }
-    f *= it;
-    if (lane == 0) p.fdiag[i] = f;
-    lpi = p.logpi[i];
-    // every block reads log alpha before its ticket; the last block updates it after all tickets
-    const double alpha = p.tune.state ? exp(p.tune.state[0]) : p.alpha;
-    term = T(alpha) * lpi - f;
-    const T nx = dev_sqrt(sxx), ny = dev_sqrt(syy), dist = dev_sqrt(sdd);
-    const T scale = ib * it;
-    if (in_regs) {
-#pragma unroll
-      for (int u = 0; u < kReg; ++u) {
-        const int c = lane + kWarp * u;
-        if (c >= R) break;
-        const T dv = scale * diag_grad<T>(p.energy, xr[u], yr[u], sxy, nx, ny, dist);
-        if (p.dz) p.dz[(size_t)i * p.ldz + c] = __float2bfloat16_rn((float)dv);
-        else p.dphi[(size_t)i * R + c] = dv;
-      }
-    } else {
-      for (int c = lane; c < R; c += kWarp) {
-        const T dv = scale * diag_grad<T>(p.energy, x[c], y[c], sxy, nx, ny, dist);
-        if (p.dz) p.dz[(size_t)i * p.ldz + c] = __float2bfloat16_rn((float)dv);
-        else p.dphi[(size_t)i * R + c] = dv;
-      }
+      T f, nx, ny, dist;
+      sxy = diag_finish(p, i, lane, sxy, sxx, syy, sdd, sad, f, nx, ny, dist);
+      lpi[q] = p.logpi[i];
+      term[q] = T(alpha) * lpi[q] - f;
+      for (int c = lane; c < R; c += kWarp)
+        diag_store(p, i, c, scale * diag_grad<T>(p.energy, x[c], y[c], sxy, nx, ny, dist));
     }
   }
   if (lane == 0) {
-    s_a[w] = term;
-    s_l[w] = lpi;
+    s_a[w] = term[0];
+    s_l[w] = lpi[0];
+    s_a[w + 4] = term[1];
+    s_l[w + 4] = lpi[1];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -210,7 +240,7 @@ __device__ __forceinline__ void diag_energy_loss_body(const ActorLossArgs<T>& p,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) diag_energy_loss_kernel(const __grid_constant__ ActorLossArgs<T> p) {
+__global__ void __launch_bounds__(kDiagThreads) diag_energy_loss_kernel(const __grid_constant__ ActorLossArgs<T> p) {
   pdl_enter();
   diag_energy_loss_body(p, blockIdx.x, gridDim.x);
 }
@@ -253,7 +283,7 @@ __global__ void __launch_bounds__(kHeadBwdThreads) head_backward_kernel(const __
 }
 
 // ---- several agents in one launch (BF16 path: float) ----------------------------
-__global__ void __launch_bounds__(256) diag_energy_loss_multi_kernel(const ActorLossArgs<float>* __restrict__ tasks,
+__global__ void __launch_bounds__(kDiagThreads) diag_energy_loss_multi_kernel(const ActorLossArgs<float>* __restrict__ tasks,
                                                                     const int* __restrict__ begin, int n) {
   pdl_enter();
   int lb, nb;
@@ -307,7 +337,7 @@ const char* actor_loss_multi(BlobCache& cache, const std::vector<ActorLossArgs<f
   double work = 0.0;
   for (const auto& t : tasks) work += 2.0 * t.B * t.R;
   TraceLaunch tr(CRL_TRACE_ENERGY, st, work);
-  launch_k(diag_energy_loss_multi_kernel, dim3(blocks), dim3(256), 0, st, dt, db, (int)tasks.size());
+  launch_k(diag_energy_loss_multi_kernel, dim3(blocks), dim3(kDiagThreads), 0, st, dt, db, (int)tasks.size());
   return nullptr;
 }
 
@@ -336,7 +366,7 @@ void actor_energy_and_loss(const ActorSpec& as, const T* phi, const T* psi, cons
                      dphi, dz,    ldz,       static_cast<T*>(ws), ticket, loss2, status, t_bump, step_bump,
                      last_step, as.tune};
   TraceLaunch tr(CRL_TRACE_ENERGY, st, 2.0 * B * R);
-  launch_k(diag_energy_loss_kernel<T>, dim3(ceil_div(B, 8)), dim3(256), 0, st, p);
+  launch_k(diag_energy_loss_kernel<T>, dim3(ceil_div(B, 8)), dim3(kDiagThreads), 0, st, p);
 }
 
 template <typename T>
