@@ -283,15 +283,15 @@ __global__ void __launch_bounds__(kHeadBwdThreads) head_backward_kernel(const __
 }
 
 // ---- several agents in one launch (BF16 path: float) ----------------------------
-__global__ void __launch_bounds__(kDiagThreads) diag_energy_loss_multi_kernel(const ActorLossArgs<float>* __restrict__ tasks,
-                                                                    const int* __restrict__ begin, int n) {
+__global__ void __launch_bounds__(kDiagThreads)
+    diag_energy_loss_multi_kernel(const ActorLossArgs<float>* __restrict__ tasks, const int* __restrict__ begin, int n) {
   pdl_enter();
   int lb, nb;
   const int s = segment_of(begin, n, blockIdx.x, lb, nb);
   diag_energy_loss_body(tasks[s], lb, nb);
 }
-__global__ void __launch_bounds__(kHeadBwdThreads) head_backward_multi_kernel(const HeadBwdArgs<float>* __restrict__ tasks,
-                                                                 const int* __restrict__ begin, int n) {
+__global__ void __launch_bounds__(kHeadBwdThreads)
+    head_backward_multi_kernel(const HeadBwdArgs<float>* __restrict__ tasks, const int* __restrict__ begin, int n) {
   pdl_enter();
   int lb, nb;
   const int s = segment_of(begin, n, blockIdx.x, lb, nb);

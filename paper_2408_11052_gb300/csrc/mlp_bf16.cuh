@@ -122,7 +122,7 @@ class GemmGroups {
                                const char** err, bool allow_split = false, int BM = tc::kBM);
   // Frees every table (synchronises the device) and forgets the tuned tile widths.
   void reset();
-  // Autotuned configuration (16 x tile width + ring depth) of a problem list,
+  // Autotuned configuration (8192 x kernel + 16 x tile width + ring depth) of a problem list,
   // keyed by its untiled content; 0 if none.
   int tuned_bn(uint64_t key) const {
     auto it = tuned_.find(key);
