@@ -41,6 +41,16 @@ const void* host_device_alias(const void* p) {
   return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
+PointerKind classify_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return PointerKind{true, nullptr};
+  }
+  if (at.type == cudaMemoryTypeHost) return PointerKind{true, at.devicePointer};
+  return PointerKind{at.type == cudaMemoryTypeUnregistered, nullptr};
+}
+
 bool is_host_pointer(const void* p) {
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
@@ -447,11 +457,11 @@ void insert_impl(crl_ctx* c, const float* obs, const float* act, const uint8_t* 
   const size_t ndone = (size_t)n * cf.E;
   // pinned host inputs: the insert kernel reads them in place through their
   // device alias (no copy); pageable host inputs: staged through device memory
-  const void* d_obs = is_host_pointer(obs) ? host_device_alias(obs) : nullptr;
-  const void* d_act = is_host_pointer(act) ? host_device_alias(act) : nullptr;
-  const void* d_done = is_host_pointer(done) ? host_device_alias(done) : nullptr;
-  const bool h_obs = is_host_pointer(obs) && !d_obs, h_act = is_host_pointer(act) && !d_act,
-             h_done = is_host_pointer(done) && !d_done;
+  const PointerKind k_obs = classify_pointer(obs), k_act = classify_pointer(act), k_done = classify_pointer(done);
+  const void* d_obs = k_obs.alias;
+  const void* d_act = k_act.alias;
+  const void* d_done = k_done.alias;
+  const bool h_obs = k_obs.host && !d_obs, h_act = k_act.host && !d_act, h_done = k_done.host && !d_done;
   if (d_obs) obs = static_cast<const float*>(d_obs);
   if (d_act) act = static_cast<const float*>(d_act);
   if (d_done) done = static_cast<const uint8_t*>(d_done);

@@ -54,6 +54,13 @@ inline void check_launch(const char* what) {
 bool is_host_pointer(const void* p);
 // The device address of pinned, mapped host memory, or nullptr (device, pageable or unknown memory).
 const void* host_device_alias(const void* p);
+// Both answers from one driver query: host = is_host_pointer(p), alias =
+// host_device_alias(p).
+struct PointerKind {
+  bool host;
+  const void* alias;
+};
+PointerKind classify_pointer(const void* p);
 size_t dtype_size(int precision);
 MlpShape net_shape(const crl_config& c, int net);
 void validate_config(const crl_config& c);

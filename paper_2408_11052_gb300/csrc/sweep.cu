@@ -401,8 +401,8 @@ int crl_sweep_update_step(crl_sweep* sw, const float* const* obs, const float* c
         CRL_REQUIRE(obs[i] && act[i] && done[i], CRL_E_INVALID_ARG, "obs, act and done must be non-null");
         const void* ptrs[3] = {obs[i], act[i], done[i]};
         for (int j = 0; j < 3; ++j) {
-          const void* q = ptrs[j];
-          if (is_host_pointer(q)) q = host_device_alias(q);
+          const PointerKind k = classify_pointer(ptrs[j]);
+          const void* q = k.host ? k.alias : ptrs[j];
           device = device && q != nullptr;
           in[3 * i + j] = q;
         }
