@@ -1233,7 +1233,7 @@ struct AdamUnit {
 // TW: the tile's columns (128 for large layers, 32 when the launch would
 // otherwise have too few blocks to hide memory latency).
 template <int TW>
-__global__ void __launch_bounds__(256) adam_shadow_kernel(const AdamNetDev* __restrict__ nets,
+__global__ void __launch_bounds__(256, 4) adam_shadow_kernel(const AdamNetDev* __restrict__ nets,
                                                           const AdamUnit* __restrict__ units, int nunits,
                                                           const HeadFwdArgs<float>* __restrict__ heads,
                                                           const int* __restrict__ head_begin, int nheads) {
